@@ -1,0 +1,402 @@
+#!/usr/bin/env python3
+"""Benchmark of batched HJCD-IK (arXiv 2510.07514) on GB300.
+
+One step = the whole method over one batch: seeds -> PO-CCD -> top-K and
+duplication -> PJ-IK -> collision filter -> ranking (one launch per phase),
+for 1000 target poses x 1000 seeds of the 7-DoF Panda with 60 link spheres in
+a scene of 200 spheres and 20 boxes.  Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hjcd|reference]
+
+`--impl reference` times the FP64 CPU oracle (the reference of this build) on
+the host cores for the same metric, each step a bounded sample of targets.
+Under torchrun every rank runs its own replica; rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "IK solves/s and candidates/s at 1 mm/0.01 rad; p50/p99 latency, served vs plain"
+UNIT = "solves/s"
+WORKLOAD = ("Panda 7-DoF (modified DH), 1000 targets x 1000 seeds in one batched launch per phase; "
+            "60 link spheres (r 0.04-0.08 m); scene of 200 spheres (r 0.02-0.15 m) + 20 boxes in a 1.5 m cube; "
+            "targets = FK of uniform in-limit samples kept collision-free; FP32")
+DATA = "synthetic: seeded generators (no datasets or trained weights involved)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("hjcd", "reference"), default="hjcd")
+    ap.add_argument("--targets", type=int, default=1000)
+    ap.add_argument("--seeds", type=int, default=1000)
+    ap.add_argument("--top-k", type=int, default=1)
+    ap.add_argument("--cpu-sample", type=int, default=96, help="targets in the timed oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (replicas: one process per GPU, no data-path collective)
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, value, device):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# algorithmic FP32 work per unit (FMA = 2 flops), counted from the kernels'
+# arithmetic for an n-joint chain; see the design notes for the derivation
+
+def flops_ccd_iter(n):
+    return 234 * n + 340
+
+
+def flops_lm_iter(n):
+    return 173 * n + 410
+
+
+def flops_fk_trial(n):
+    return 56 * n + 166
+
+
+FLOPS_SPHERE_TEST = 10
+FLOPS_BOX_TEST = 8
+
+
+def flops_collide_cand(n, n_sph):
+    return 18 * n_sph + 54 * n + 63
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2510_07514_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for ln in open(path):
+        f = ln.split()
+        if len(f) >= 3 and not ln.startswith("#") and f[0] == kernel and f[2] == src:
+            return float(f[1])
+    return None
+
+
+# ----------------------------------------------------------------------------
+
+def cpu_baseline(sample_targets: int, seeds: int) -> dict:
+    """The FP64 oracle, as it stands, on the host cores: a bounded sample of
+    the same workload (its own FK and collision checks choose the targets)."""
+    import oracle as orc
+    from paper_2510_07514_gb300 import inputs
+    wl = inputs.cfg2(sample_targets, seeds)
+    rob, sc = orc.Robot(wl.robot), orc.Scene(wl.scene)
+    pool = wl.theta_gen.astype(np.float32).astype(np.float64)
+    hit, _ = orc.collide(rob, sc, pool)
+    keep = pool[~hit][:sample_targets]
+    tg = orc.pose(rob, keep).astype(np.float32).astype(np.float64)
+    P = orc.make_params(wl.eps_pos, wl.eps_ori, seed=wl.seed)
+    t0 = time.perf_counter()
+    o = orc.solve(rob, sc, P, tg, seeds, 1)
+    dt = time.perf_counter() - t0
+    succ = float(np.mean((o["count"] > 0) & (o["err"][:, 0, 0] <= wl.eps_pos) & (o["err"][:, 0, 1] <= wl.eps_ori)))
+    return {"value": len(tg) / dt, "unit": UNIT, "cores": orc.threads(), "kind": "oracle",
+            "sample": f"{len(tg)} targets x {seeds} seeds of the same workload, FP64, OpenMP over candidates",
+            "seconds": dt, "success_rate": succ}
+
+
+def reference_arm(args):
+    world, rank, _ = dist_env()
+    dist = dist_init(world, "gloo")
+    if rank != 0:
+        barrier(dist)
+        return
+    import oracle as orc
+    from paper_2510_07514_gb300 import inputs
+    sample = max(1, min(args.cpu_sample // 4, args.targets))
+    wl = inputs.cfg2(sample * (args.steps + args.warmup), args.seeds)
+    rob, sc = orc.Robot(wl.robot), orc.Scene(wl.scene)
+    pool = wl.theta_gen.astype(np.float32).astype(np.float64)
+    hit, _ = orc.collide(rob, sc, pool)
+    keep = pool[~hit]
+    tg_all = orc.pose(rob, keep[: sample * (args.steps + args.warmup)]).astype(np.float32).astype(np.float64)
+    P = orc.make_params(wl.eps_pos, wl.eps_ori, seed=wl.seed)
+    times, succ = [], []
+    for s in range(args.warmup + args.steps):
+        tg = tg_all[s * sample:(s + 1) * sample]
+        t0 = time.perf_counter()
+        o = orc.solve(rob, sc, P, tg, args.seeds, args.top_k)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            succ.append(np.mean((o["count"] > 0) & (o["err"][:, 0, 0] <= wl.eps_pos) & (o["err"][:, 0, 1] <= wl.eps_ori)))
+    value = sample * len(times) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": DATA,
+        "config": {"workload": WORKLOAD, "targets_per_step": sample, "seeds_per_target": args.seeds,
+                   "top_k": args.top_k, "note": "each step is a bounded sample of the workload's targets"},
+        "success_rate": float(np.mean(succ)),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.threads(), "kind": "oracle",
+                         "sample": f"{sample} targets x {args.seeds} seeds per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    barrier(dist)
+
+
+def hjcd_arm(args):
+    world, rank, local = dist_env()
+    import torch
+    from paper_2510_07514_gb300 import api, build, hjcd, inputs
+    if not os.path.exists(hjcd.lib_path()):
+        build.build()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    wl = inputs.cfg2(args.targets, args.seeds)
+    rob = wl.robot
+    n, T, S, K = rob.n, args.targets, args.seeds, args.top_k
+    ctx = api.Context(local)
+    rid, sid = ctx.add_robot(rob), ctx.set_scene(wl.scene)
+
+    # targets: the library's own FK of joint samples its own collision check keeps
+    pool = torch.as_tensor(np.ascontiguousarray(wl.theta_gen.T), dtype=torch.float32, device=dev)
+    hit = ctx.collide(rid, sid, pool).bool()
+    keep = pool[:, ~hit][:, :T].contiguous()
+    assert keep.shape[1] == T, "not enough collision-free joint samples in the pool"
+    tg = ctx.fk(rid, keep).contiguous()
+    tg_host = tg.cpu().pin_memory()
+    out = (torch.empty((T, K, n), device=dev), torch.empty((T, K, 2), device=dev),
+           torch.empty((T,), dtype=torch.int32, device=dev))
+    hout = (torch.empty((T, K, n)).pin_memory(), torch.empty((T, K, 2)).pin_memory(),
+            torch.empty((T,), dtype=torch.int32).pin_memory())
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step(targets, outs):
+        ctx.solve(rid, sid, targets, S, K, wl.seed, n, wl.eps_pos, wl.eps_ori, stream=stream, out=outs)
+
+    hjcd.hjcd_set_profiling(ctx.h, True)
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(tg, out)
+    torch.cuda.synchronize(dev)
+
+    hjcd.hjcd_counters(ctx.h, reset=True)
+    l0 = hjcd.hjcd_launch_count(ctx.h)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    phases = []
+    barrier(dist, local)
+    torch.cuda.synchronize(dev)
+    for i in range(args.steps):
+        flush.zero_()
+        e0[i].record(stream)
+        step(tg, out)
+        e1[i].record(stream)
+        phases.append(hjcd.hjcd_phase_times(ctx.h))
+    torch.cuda.synchronize(dev)
+    barrier(dist, local)
+    clk = clocks.stop()
+    launches = hjcd.hjcd_launch_count(ctx.h) - l0
+    ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
+    cnt = hjcd.hjcd_counters(ctx.h, reset=True)
+    total_s = max_over_ranks(dist, sum(ms) / 1e3, dev)
+    value = world * T * args.steps / total_s
+
+    cnt_h, err_h = out[2].cpu().numpy(), out[1].cpu().numpy()
+    success = float(np.mean((cnt_h > 0) & (err_h[:, 0, 0] <= wl.eps_pos) & (err_h[:, 0, 1] <= wl.eps_ori)))
+
+    # end to end through the C ABI with host buffers (copies inside the region)
+    e2e_ms = []
+    for i in range(max(2, args.steps // 2) + 1):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        step(tg_host, hout)
+        t1 = time.perf_counter()
+        if i > 0:
+            e2e_ms.append(1e3 * (t1 - t0))
+    e2e_total = max_over_ranks(dist, sum(e2e_ms) / 1e3, dev)
+    e2e_value = world * T * len(e2e_ms) / e2e_total
+    h2d = T * 7 * 4 + 2 * (T + 1) * 8
+    d2h = T * K * (n + 2) * 4 + T * 4
+
+    # roofline of the dominant kernel
+    ph = np.mean(np.asarray(phases), axis=0)  # ccd, dup, lm, collide, rank, whole
+    names = ["po_ccd", "topk_dup", "pjik", "collide", "rank"]
+    dom = int(np.argmax(ph[:5]))
+    steps = args.steps
+    n_sph = len(rob.sph_body)
+    fl = {
+        "po_ccd": cnt[0] / steps * flops_ccd_iter(n),
+        "pjik": cnt[1] / steps * flops_lm_iter(n) + (cnt[2] - cnt[1]) / steps * flops_fk_trial(n),
+        "collide": (cnt[3] * FLOPS_SPHERE_TEST + cnt[6] * FLOPS_BOX_TEST) / steps
+                   + cnt[4] / steps * flops_collide_cand(n, n_sph),
+    }
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    dom_name = names[dom] if names[dom] in fl else max(fl, key=lambda k: fl[k] / max(ph[names.index(k)], 1e-9))
+    dom_ms = ph[names.index(dom_name)]
+    achieved = fl[dom_name] / (dom_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": recorded_traffic(dom_name),
+            "peak_note": f"FP32 CUDA-core peak from unit counts: {props.multi_processor_count} SMs x 128 lanes x 2 "
+                         f"x {sm_max:.0f} MHz (max SM clock); no FP32 peak in MEASURED_PEAKS.json",
+            "per_kernel": {k: {"ms": float(ph[names.index(k)]), "gflop": fl[k] / 1e9,
+                               "tflops": fl[k] / (ph[names.index(k)] * 1e-3) / 1e12} for k in fl}}
+    ffma = hjcd.hjcd_ffma_probe(ctx.h, 2048, stream)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": DATA,
+        "config": {"workload": WORKLOAD, "targets": T, "seeds_per_target": S, "top_k": K,
+                   "tolerance": "1 mm / 0.01 rad", "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "candidates_per_s": value * S, "success_rate": success,
+        "phase_ms": {nm: float(v) for nm, v in zip(names + ["step"], ph)},
+        "work_per_step": {"ccd_iters": cnt[0] / steps, "lm_iters": cnt[1] / steps, "lm_fk_passes": cnt[2] / steps,
+                          "sphere_tests": cnt[3] / steps, "box_tests": cnt[6] / steps,
+                          "collide_candidates": cnt[4] / steps},
+        "roofline": roof, "ffma_probe_tflops": ffma,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": float(np.mean(e2e_ms))},
+        "clocks": clk, "gpu_launches": int(launches),
+    }
+    ctx.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_sample, S)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    barrier(dist, local)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        hjcd_arm(args)
+
+
+if __name__ == "__main__":
+    main()

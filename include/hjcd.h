@@ -1,0 +1,254 @@
+/*
+ * hjcd.h -- C ABI of the GB300 (sm_103a) batched HJCD-IK library.
+ *
+ * HJCD-IK (arXiv 2510.07514) solves inverse kinematics for serial revolute
+ * chains by running many seeds per target pose through three stages
+ * (Sec. V, Alg. 2): an orientation-aware greedy coordinate descent (PO-CCD,
+ * Alg. 3), a Jacobian damped-least-squares polish (PJ-IK, Alg. 4) and a
+ * sphere-based collision filter (Sec. V-C); the collision-free survivors are
+ * ranked by residual.  Every stage runs in this library's own CUDA kernels.
+ *
+ * Conventions shared by every entry point
+ *   - Status: every call returns HJCD_OK (0) or a negative HJCD_E* code and
+ *     records a message readable with hjcd_last_error().  Nothing is written
+ *     to outputs when a call fails validation.
+ *   - Precision: all device arithmetic is IEEE binary32.
+ *   - Poses: 7 floats px py pz qw qx qy qz (metres; Hamilton quaternion).
+ *     Quaternions are normalised on entry; a zero quaternion is HJCD_EINVAL.
+ *   - Joint vectors on the device are structure-of-arrays: joint j of
+ *     candidate c lives at theta[j * ld + c] (ld >= number of candidates).
+ *   - Ownership: the caller owns every buffer it passes.  Robot and scene
+ *     tables are copied into device memory owned by the context when they are
+ *     created; later changes to the caller's arrays have no effect.
+ *   - Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *     Calls taking device buffers only enqueue work and return before it
+ *     completes; hjcd_solve with host buffers returns after its results have
+ *     been copied back.
+ *   - Threads: a context is used by one host thread at a time.
+ *   - Random draws: Philox4x32-10 keyed by the request seed, counter
+ *     (candidate, target, phase << 24 | iteration, block), so results do not
+ *     depend on how work is batched.
+ */
+#ifndef HJCD_H
+#define HJCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t hjcd_status;
+#define HJCD_OK 0
+#define HJCD_EINVAL (-1)    /* bad argument: size, pointer kind, id, limits */
+#define HJCD_ENOMEM (-2)    /* device (or host pinned) allocation failed */
+#define HJCD_ECUDA (-3)     /* a CUDA runtime call or kernel launch failed */
+#define HJCD_ETIMEOUT (-4)  /* a bounded device wait ran out; results invalid */
+#define HJCD_ENOTFOUND (-5) /* unknown robot or scene id */
+
+#define HJCD_MAX_DOF 24        /* joints per chain */
+#define HJCD_MAX_SPHERES 256   /* link spheres per robot */
+#define HJCD_MAX_SAMPLES 8192  /* seeds per target */
+#define HJCD_MAX_TOPK 64
+
+typedef struct hjcd_ctx hjcd_ctx;
+
+/* Parameter table of Alg. 2-4 (symbols of the paper in brackets).  Values
+ * are readings of the paper, which names them only symbolically. */
+typedef struct hjcd_params {
+    int32_t cd_max_iters;   /* PO-CCD iteration cap [max_iters] */
+    float cd_eps_pos2;      /* PO-CCD coarse break on |e_p|^2, m^2 [epsilon] */
+    float cd_eps_ori2;      /* PO-CCD coarse break on |omega|^2, rad^2 [nu] */
+    float cd_gamma_pos;     /* acceptance: position improvement, m [gamma] */
+    float cd_gamma_ori;     /* acceptance: orientation improvement, rad [gamma] */
+    float cd_sigma;         /* std of the PO-CCD rejection perturbation, rad [Sigma] */
+    float cd_delta0;        /* annealing delta(k) = delta0 * rho^k (Eq. ori_update) */
+    float cd_rho;
+    float proj_eps;         /* relative projected length below which Eq. theta_proj gives 0 */
+    int32_t dup_ratio;      /* K = max(1, floor(B / dup_ratio)) seeds kept [K] */
+    float dup_sigma;        /* std of the duplication perturbation, rad [Sigma] */
+    int32_t lm_max_iters;   /* PJ-IK iteration cap [max_iters] */
+    float lm_lambda;        /* damping of Eq. normal-eqs [lambda] */
+    float lm_trust_R;       /* trust region, rad [R] */
+    float lm_beta;          /* line-search ratio [beta] */
+    int32_t lm_A;           /* line-search depth [A] */
+    float lm_sigma;         /* std of the PJ-IK perturbation, rad [Sigma] */
+    float lm_gn_reg;        /* regulariser of the minimum-norm Gauss-Newton step (Eq. dogleg) */
+} hjcd_params;
+
+typedef struct hjcd_solve_opts {
+    float eps_pos;          /* success / PJ-IK break tolerance on |e_p|, m */
+    float eps_ori;          /* success / PJ-IK break tolerance on |omega|, rad */
+    int32_t n_samples;      /* seeds per target, M = B (Alg. 2); 1..HJCD_MAX_SAMPLES */
+    int32_t top_k;          /* ranked solutions returned per target, 1..HJCD_MAX_TOPK */
+    uint64_t seed;          /* request seed (Philox key) */
+    const hjcd_params* params;           /* NULL => hjcd_default_params() */
+    const int32_t* samples_per_target;   /* NULL => n_samples for all; else HOST array [n_targets] */
+} hjcd_solve_opts;
+
+/* ---- context -------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` (made current on this thread). */
+hjcd_status hjcd_init(int device, hjcd_ctx** out);
+/* Free every device buffer of the context.  NULL is ignored. */
+void hjcd_destroy(hjcd_ctx* ctx);
+/* Message of the last failed call on this context ("" if none).  The string
+ * stays valid until the next call on the context. */
+const char* hjcd_last_error(const hjcd_ctx* ctx);
+const char* hjcd_status_string(hjcd_status s);
+void hjcd_default_params(hjcd_params* out);
+
+/* ---- resident tables -------------------------------------------------------- */
+
+/* Register a serial revolute chain (Eq. fk).  Joint i contributes, in the
+ * modified-DH (Craig) convention, Rx(dh_alpha[i]) Tx(dh_a[i])
+ * Rz(theta_i + dh_theta_off[i]) Tz(dh_d[i]); `flange` (row-major 4x4 rigid
+ * transform) follows joint n.  Limits: q_lo[i] < q_hi[i].
+ * Collision model (Sec. V-C): n_spheres spheres; sphere s is attached to
+ * body sph_link[s] in 0..n+1 (0 = base, i = the body moved by joint i,
+ * n+1 = the flange frame) at sph_xyzr[4s..4s+2] in that body's frame with
+ * radius sph_xyzr[4s+3] > 0.  ignore_pairs: (n+2)x(n+2) row-major bytes,
+ * nonzero = the body pair is never checked for self-collision; NULL ignores
+ * exactly the pairs with |i - j| <= 1.  All arrays are HOST memory.
+ * Returns the new robot id in *robot_id. */
+hjcd_status hjcd_create_robot(hjcd_ctx* ctx, int n_dof,
+                              const float* dh_a, const float* dh_alpha, const float* dh_d,
+                              const float* dh_theta_off, const float flange[16],
+                              const float* q_lo, const float* q_hi,
+                              int n_spheres, const int32_t* sph_link, const float* sph_xyzr,
+                              const uint8_t* ignore_pairs, int32_t* robot_id);
+
+/* Create (scene_id_or_new < 0) or replace an obstacle scene: n_sph spheres
+ * (x y z r, r > 0) and n_box axis-aligned boxes (lo xyz, hi xyz, lo <= hi),
+ * HOST arrays.  Returns the id in *scene_id. */
+hjcd_status hjcd_set_scene(hjcd_ctx* ctx, int32_t scene_id_or_new, int n_sph, const float* sph_xyzr,
+                           int n_box, const float* box_lohi, int32_t* scene_id);
+
+/* ---- the whole method (Alg. 2) ------------------------------------------- */
+
+/* Solve n_targets poses (targets_pq, 7 floats each).  Per target: M seeds
+ * through PO-CCD, top-K + perturbed duplication to B, PJ-IK, the collision
+ * filter (self-collision when the robot has spheres, plus the scene when
+ * scene_id >= 0) and the ranking of the collision-free candidates by the score
+ * (|e_p|/eps_pos)^2 + (|omega|/eps_ori)^2.
+ * Outputs: out_q [n_targets][top_k][n] joint vectors, out_err
+ * [n_targets][top_k][2] (|e_p| m, |omega| rad), out_count [n_targets] the
+ * number of collision-free solutions written (0..top_k; 0 is not an error).
+ * Entries past out_count are left untouched.
+ * targets_pq and the three outputs may each be host or device pointers
+ * (detected per pointer).  With any host output the call synchronises the
+ * stream before returning. */
+hjcd_status hjcd_solve(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_targets,
+                       const float* targets_pq, const hjcd_solve_opts* opts,
+                       float* out_q, float* out_err, int32_t* out_count, void* stream);
+
+/* ---- stages (device buffers only) -------------------------------------------
+ * Candidates are described by `tgt[c]` (row of `targets_pq`) and `cand[c]`
+ * (index of the candidate inside its target, which keys its random streams).
+ * All pointers below are DEVICE pointers. */
+
+/* Eq. fk: flange pose of each candidate. */
+hjcd_status hjcd_fk(hjcd_ctx* ctx, int32_t robot_id, int64_t n_cand, const float* theta, int64_t ld,
+                    float* out_pq, void* stream);
+
+/* Alg. 3 line 3: seeds uniform inside the limits. */
+hjcd_status hjcd_sample_seeds(hjcd_ctx* ctx, int32_t robot_id, int64_t n_cand, const int32_t* tgt,
+                              const int32_t* cand, uint64_t seed, float* theta, int64_t ld, void* stream);
+
+/* Alg. 3: PO-CCD on each candidate.  theta_in == NULL samples the seeds
+ * (line 3); otherwise iterations k0 .. k0+n_iters-1 start from theta_in.
+ * theta_out may equal theta_in.  score/perr/oerr/iters (each may be NULL)
+ * receive the final score, |e_p|, |omega| and iterations executed.
+ * Trace (one iteration, n_iters == 1; any pointer may be NULL):
+ * dp/rp/dq/rq/th_hat are [n][ld]: per-joint position step and resulting
+ * |e_p|, orientation step and resulting |omega|, the proposed theta_hat;
+ * jp/jo the greedy joints, accepted the acceptance flag. */
+typedef struct hjcd_ccd_trace {
+    float* dp;
+    float* rp;
+    float* dq;
+    float* rq;
+    int32_t* jp;
+    int32_t* jo;
+    uint8_t* accepted;
+    float* th_hat;
+} hjcd_ccd_trace;
+hjcd_status hjcd_po_ccd(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const float* targets_pq,
+                        float eps_pos, float eps_ori, uint64_t seed, const hjcd_params* params,
+                        int64_t n_cand, const int32_t* tgt, const int32_t* cand,
+                        const float* theta_in, float* theta_out, int64_t ld, int k0, int n_iters,
+                        float* score, float* perr, float* oerr, int32_t* iters,
+                        const hjcd_ccd_trace* trace, void* stream);
+
+/* Alg. 2 lines 2-7 for each target t: the K = max(1, floor(M_t/ratio))
+ * lowest scores among its M_t = m_off[t+1]-m_off[t] seeds (ties to the lower
+ * index), each copied floor(M_t/K) times with N(0, dup_sigma^2) noise, copy r
+ * of kept seed i landing at b_off[t] + r*K + i.  m_off/b_off: [n_targets+1]
+ * int64 device arrays (b_off must follow that layout).  src_B (may be NULL)
+ * receives the source seed index inside the target. */
+hjcd_status hjcd_topk_dup(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const int64_t* m_off,
+                          const float* score_M, const float* theta_M, int64_t ld_M,
+                          const int64_t* b_off, float* theta_B, int64_t ld_B, int32_t* src_B,
+                          uint64_t seed, const hjcd_params* params, void* stream);
+
+/* Alg. 4: PJ-IK, iterations k0 .. k0+n_iters-1, theta updated in place.
+ * Trace (one iteration): J [6n][ld] (row r, joint i at (r*n+i)*ld + c),
+ * W [6][ld], d_lm [n][ld] the clamped LM step, branch (0 LM, 1 dogleg,
+ * 2 single-coordinate, 3 perturbation), alpha the accepted line-search step. */
+typedef struct hjcd_lm_trace {
+    float* J;
+    float* W;
+    float* d_lm;
+    int32_t* branch;
+    float* alpha;
+} hjcd_lm_trace;
+hjcd_status hjcd_pjik(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const float* targets_pq,
+                      float eps_pos, float eps_ori, uint64_t seed, const hjcd_params* params,
+                      int64_t n_cand, const int32_t* tgt, const int32_t* cand,
+                      float* theta, int64_t ld, int k0, int n_iters,
+                      float* score, float* perr, float* oerr, int32_t* iters,
+                      const hjcd_lm_trace* trace, void* stream);
+
+/* Sec. V-C: hit[c] = 1 when candidate c overlaps itself (non-ignored body
+ * pairs) or the scene (scene_id < 0: self-collision only).  Overlap of two
+ * spheres: |c1-c2|^2 < (r1+r2)^2; of a sphere and a box: squared distance of
+ * the centre to the box below r^2. */
+hjcd_status hjcd_collide(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int64_t n_cand,
+                         const float* theta, int64_t ld, uint8_t* hit, void* stream);
+
+/* Alg. 2 line 10: per target, the collision-free candidates (hit may be
+ * NULL) of b_off[t] .. b_off[t+1]-1 sorted by score (ties to the lower
+ * index), first top_k written as in hjcd_solve. */
+hjcd_status hjcd_rank(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const int64_t* b_off,
+                      const float* theta_B, int64_t ld, const float* score, const float* perr,
+                      const float* oerr, const uint8_t* hit, int top_k,
+                      float* out_q, float* out_err, int32_t* out_count, void* stream);
+
+/* ---- instrumentation ------------------------------------------------------ */
+
+/* Record CUDA events around each phase of hjcd_solve (0 = off). */
+hjcd_status hjcd_set_profiling(hjcd_ctx* ctx, int on);
+/* Milliseconds of the phases of the last profiled hjcd_solve: [0] PO-CCD,
+ * [1] top-K/dup, [2] PJ-IK, [3] collision, [4] rank, [5] whole call on the
+ * device.  Synchronises with that call's events. */
+hjcd_status hjcd_phase_times(hjcd_ctx* ctx, float ms[6]);
+/* Work counters accumulated by the kernels since the last reset:
+ * [0] PO-CCD iterations, [1] PJ-IK iterations, [2] forward-kinematics passes
+ * inside PJ-IK (frames + line-search/dogleg trials), [3] sphere-sphere tests
+ * executed by the collision kernel (self pairs and obstacle spheres), [4]
+ * candidates checked for collision, [5] PO-CCD candidates, [6] sphere-box
+ * tests.  Synchronises the device; ETIMEOUT when a bounded device wait ran
+ * out since the context was created. */
+hjcd_status hjcd_counters(hjcd_ctx* ctx, uint64_t out[8], int reset);
+/* Kernel launches issued by this context since creation. */
+int64_t hjcd_launch_count(const hjcd_ctx* ctx);
+/* FP32 FMA throughput probe: runs a dependent-chain FFMA kernel over every SM
+ * for `iters` inner iterations and returns the achieved FP32 TFLOP/s (an FMA
+ * counts 2) in *tflops. */
+hjcd_status hjcd_ffma_probe(hjcd_ctx* ctx, int iters, double* tflops, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

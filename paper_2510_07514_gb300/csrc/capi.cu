@@ -1,0 +1,911 @@
+// capi.cu -- the C ABI of include/hjcd.h: context, resident robot and scene
+// tables, the solve workspace, pointer-kind detection and the launch sequence
+// of Alg. 2 (PO-CCD -> top-K/duplication -> PJ-IK -> collision -> ranking).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hjcd_internal.cuh"
+
+namespace hjcd {
+size_t collide_smem_bytes(int n_sph, int n_osph, int n_obox);
+}
+
+using namespace hjcd;
+
+namespace {
+
+constexpr int kMaxSceneFloat4 = 10240;  // obstacle spheres + 2 * boxes staged in shared memory (160 KB)
+
+struct RobotRec {
+    RobotParams P{};
+    void* dbuf = nullptr;  // float4 spheres | int32 bodies | uint32 pair masks
+    float4* sph = nullptr;
+    int32_t* body = nullptr;
+    uint32_t* mask = nullptr;
+};
+
+struct SceneRec {
+    float4* buf = nullptr;
+    int n_sph = 0, n_box = 0;
+    size_t cap = 0;
+    bool live = false;
+};
+
+size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct hjcd_ctx {
+    int device = 0;
+    std::vector<RobotRec> robots;
+    std::vector<SceneRec> scenes;
+    std::string err;
+    char* ws = nullptr;  // device workspace
+    size_t ws_cap = 0;
+    char* pin = nullptr;  // pinned host staging
+    size_t pin_cap = 0;
+    cudaEvent_t ws_free = nullptr;   // recorded when the last call's device work on the workspace ends
+    cudaEvent_t pin_free = nullptr;  // recorded after the last copy out of the pinned staging
+    Counters* cnt = nullptr;
+    int32_t* err_flag = nullptr;
+    float* sink = nullptr;
+    bool profile = false;
+    cudaEvent_t ev[6] = {};
+    bool ev_valid = false;
+    int64_t launches = 0;
+};
+
+namespace {
+
+hjcd_status fail(hjcd_ctx* ctx, hjcd_status code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    return code;
+}
+
+#define HJCD_CUDA(ctx, call)                                                                         \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? HJCD_ENOMEM : HJCD_ECUDA, "%s: %s (%s)", \
+                        #call, cudaGetErrorString(e_), cudaGetErrorName(e_));                        \
+    } while (0)
+
+hjcd_status after_launch(hjcd_ctx* ctx, int kernels) {
+    ctx->launches += kernels;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, HJCD_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+    return HJCD_OK;
+}
+
+// 1 = device-accessible (device or managed), 0 = host, -1 = unknown pointer
+int pointer_kind(const void* p) {
+    if (!p) return -1;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return 1;
+    return 0;
+}
+
+bool pinned_host(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+hjcd_status make_current(hjcd_ctx* ctx) {
+    HJCD_CUDA(ctx, cudaSetDevice(ctx->device));
+    return HJCD_OK;
+}
+
+hjcd_status ensure_ws(hjcd_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->ws_cap) return HJCD_OK;
+    HJCD_CUDA(ctx, cudaEventSynchronize(ctx->ws_free));
+    if (ctx->ws) HJCD_CUDA(ctx, cudaFree(ctx->ws));
+    ctx->ws = nullptr;
+    ctx->ws_cap = 0;
+    const size_t cap = align_up(bytes + bytes / 4, 1 << 20);
+    HJCD_CUDA(ctx, cudaMalloc(&ctx->ws, cap));
+    ctx->ws_cap = cap;
+    return HJCD_OK;
+}
+
+hjcd_status ensure_pin(hjcd_ctx* ctx, size_t bytes) {
+    HJCD_CUDA(ctx, cudaEventSynchronize(ctx->pin_free));
+    if (bytes <= ctx->pin_cap) return HJCD_OK;
+    if (ctx->pin) HJCD_CUDA(ctx, cudaFreeHost(ctx->pin));
+    ctx->pin = nullptr;
+    ctx->pin_cap = 0;
+    const size_t cap = align_up(bytes + bytes / 4, 1 << 16);
+    HJCD_CUDA(ctx, cudaMallocHost(&ctx->pin, cap));
+    ctx->pin_cap = cap;
+    return HJCD_OK;
+}
+
+struct Carve {
+    size_t off = 0;
+    template <typename T>
+    size_t take(size_t count) {
+        const size_t o = off;
+        off = align_up(off + count * sizeof(T));
+        return o;
+    }
+};
+
+hjcd_status check_robot(hjcd_ctx* ctx, int32_t id, RobotRec** out) {
+    if (id < 0 || id >= (int32_t)ctx->robots.size()) return fail(ctx, HJCD_ENOTFOUND, "unknown robot id %d", id);
+    *out = &ctx->robots[id];
+    return HJCD_OK;
+}
+
+hjcd_status check_scene(hjcd_ctx* ctx, int32_t id, SceneRec** out) {
+    *out = nullptr;
+    if (id < 0) return HJCD_OK;
+    if (id >= (int32_t)ctx->scenes.size() || !ctx->scenes[id].live)
+        return fail(ctx, HJCD_ENOTFOUND, "unknown scene id %d", id);
+    *out = &ctx->scenes[id];
+    return HJCD_OK;
+}
+
+hjcd_status check_params(hjcd_ctx* ctx, const hjcd_params& P) {
+    if (P.cd_max_iters < 0 || P.lm_max_iters < 0 || P.cd_max_iters > (1 << 20) || P.lm_max_iters > (1 << 20))
+        return fail(ctx, HJCD_EINVAL, "iteration caps must be in [0, 2^20]");
+    if (P.dup_ratio < 1) return fail(ctx, HJCD_EINVAL, "dup_ratio must be >= 1");
+    if (P.lm_A < 0 || P.lm_A > 64) return fail(ctx, HJCD_EINVAL, "lm_A must be in [0, 64]");
+    if (!(P.lm_beta > 1.0f)) return fail(ctx, HJCD_EINVAL, "lm_beta must be > 1");
+    if (!(P.lm_lambda > 0.0f) || !(P.lm_trust_R > 0.0f) || !(P.lm_gn_reg > 0.0f))
+        return fail(ctx, HJCD_EINVAL, "lm_lambda, lm_trust_R and lm_gn_reg must be > 0");
+    if (!(P.cd_sigma >= 0.0f) || !(P.dup_sigma >= 0.0f) || !(P.lm_sigma >= 0.0f))
+        return fail(ctx, HJCD_EINVAL, "perturbation scales must be >= 0");
+    if (!(P.proj_eps >= 0.0f)) return fail(ctx, HJCD_EINVAL, "proj_eps must be >= 0");
+    return HJCD_OK;
+}
+
+int64_t dup_count(int64_t M, int ratio) {
+    if (M <= 0) return 0;
+    const int64_t K = std::max<int64_t>(1, M / ratio);
+    return K * (M / K);
+}
+
+// pack n device-resident 7-float targets into TargetDesc rows at `out`
+hjcd_status pack_device_targets(hjcd_ctx* ctx, const float* pq7, int T, float eps_pos, float eps_ori,
+                                uint64_t seed, TargetDesc* out, cudaStream_t st) {
+    launch_pack_targets(pq7, T, eps_pos, eps_ori, seed, nullptr, out, st);
+    return after_launch(ctx, 1);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hjcd_status_string(hjcd_status s) {
+    switch (s) {
+        case HJCD_OK: return "ok";
+        case HJCD_EINVAL: return "invalid argument";
+        case HJCD_ENOMEM: return "out of memory";
+        case HJCD_ECUDA: return "CUDA error";
+        case HJCD_ETIMEOUT: return "bounded device wait ran out";
+        case HJCD_ENOTFOUND: return "unknown id";
+        default: return "unknown status";
+    }
+}
+
+void hjcd_default_params(hjcd_params* o) {
+    if (!o) return;
+    o->cd_max_iters = 32;
+    o->cd_eps_pos2 = 0.01f * 0.01f;
+    o->cd_eps_ori2 = 0.1f * 0.1f;
+    o->cd_gamma_pos = 1e-4f;
+    o->cd_gamma_ori = 1e-3f;
+    o->cd_sigma = 0.05f;
+    o->cd_delta0 = 0.5f;
+    o->cd_rho = 0.9f;
+    o->proj_eps = 1e-6f;
+    o->dup_ratio = 4;
+    o->dup_sigma = 0.02f;
+    o->lm_max_iters = 20;
+    o->lm_lambda = 1e-3f;
+    o->lm_trust_R = 0.3f;
+    o->lm_beta = 2.0f;
+    o->lm_A = 4;
+    o->lm_sigma = 0.01f;
+    o->lm_gn_reg = 1e-6f;
+}
+
+hjcd_status hjcd_init(int device, hjcd_ctx** out) {
+    if (!out) return HJCD_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return HJCD_EINVAL;
+    }
+    hjcd_ctx* ctx = new hjcd_ctx();
+    ctx->device = device;
+    hjcd_status s = make_current(ctx);
+    if (s == HJCD_OK && (cudaEventCreateWithFlags(&ctx->ws_free, cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&ctx->pin_free, cudaEventDisableTiming) != cudaSuccess))
+        s = HJCD_ECUDA;
+    for (int i = 0; s == HJCD_OK && i < 6; ++i)
+        if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) s = HJCD_ECUDA;
+    if (s == HJCD_OK && (cudaMalloc(&ctx->cnt, sizeof(Counters)) != cudaSuccess ||
+                         cudaMalloc(&ctx->err_flag, sizeof(int32_t)) != cudaSuccess ||
+                         cudaMalloc(&ctx->sink, 4096 * sizeof(float)) != cudaSuccess))
+        s = HJCD_ENOMEM;
+    if (s == HJCD_OK && (cudaMemset(ctx->cnt, 0, sizeof(Counters)) != cudaSuccess ||
+                         cudaMemset(ctx->err_flag, 0, sizeof(int32_t)) != cudaSuccess))
+        s = HJCD_ECUDA;
+    if (s != HJCD_OK) {
+        cudaGetLastError();
+        hjcd_destroy(ctx);
+        return s;
+    }
+    *out = ctx;
+    return HJCD_OK;
+}
+
+void hjcd_destroy(hjcd_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto& r : ctx->robots)
+        if (r.dbuf) cudaFree(r.dbuf);
+    for (auto& s : ctx->scenes)
+        if (s.buf) cudaFree(s.buf);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->pin) cudaFreeHost(ctx->pin);
+    if (ctx->cnt) cudaFree(ctx->cnt);
+    if (ctx->err_flag) cudaFree(ctx->err_flag);
+    if (ctx->sink) cudaFree(ctx->sink);
+    if (ctx->ws_free) cudaEventDestroy(ctx->ws_free);
+    if (ctx->pin_free) cudaEventDestroy(ctx->pin_free);
+    for (auto& e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    cudaGetLastError();
+    delete ctx;
+}
+
+const char* hjcd_last_error(const hjcd_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+hjcd_status hjcd_create_robot(hjcd_ctx* ctx, int n, const float* dh_a, const float* dh_alpha, const float* dh_d,
+                              const float* dh_theta_off, const float flange[16], const float* q_lo,
+                              const float* q_hi, int n_spheres, const int32_t* sph_link, const float* sph_xyzr,
+                              const uint8_t* ignore_pairs, int32_t* robot_id) {
+    if (!ctx) return HJCD_EINVAL;
+    if (n < 1 || n > HJCD_MAX_DOF) return fail(ctx, HJCD_EINVAL, "n_dof %d outside [1, %d]", n, HJCD_MAX_DOF);
+    if (!dh_a || !dh_alpha || !dh_d || !flange || !q_lo || !q_hi || !robot_id)
+        return fail(ctx, HJCD_EINVAL, "null robot table");
+    if (n_spheres < 0 || n_spheres > HJCD_MAX_SPHERES)
+        return fail(ctx, HJCD_EINVAL, "n_spheres %d outside [0, %d]", n_spheres, HJCD_MAX_SPHERES);
+    if (n_spheres > 0 && (!sph_link || !sph_xyzr)) return fail(ctx, HJCD_EINVAL, "null sphere table");
+    if (pointer_kind(dh_a) == 1) return fail(ctx, HJCD_EINVAL, "robot tables must be host memory");
+    RobotRec rec;
+    RobotParams& P = rec.P;
+    P.n = n;
+    P.n_sph = n_spheres;
+    for (int i = 0; i < n; ++i) {
+        if (!(q_lo[i] < q_hi[i])) return fail(ctx, HJCD_EINVAL, "joint %d: q_lo must be < q_hi", i);
+        if (!std::isfinite(dh_a[i]) || !std::isfinite(dh_alpha[i]) || !std::isfinite(dh_d[i]))
+            return fail(ctx, HJCD_EINVAL, "joint %d: non-finite DH entry", i);
+        P.ca[i] = (float)std::cos((double)dh_alpha[i]);
+        P.sa[i] = (float)std::sin((double)dh_alpha[i]);
+        P.a[i] = dh_a[i];
+        P.d[i] = dh_d[i];
+        P.off[i] = dh_theta_off ? dh_theta_off[i] : 0.0f;
+        P.lo[i] = q_lo[i];
+        P.hi[i] = q_hi[i];
+    }
+    // flange: rigid transform check
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += (double)flange[4 * k + i] * flange[4 * k + j];
+            if (std::fabs(s - (i == j ? 1.0 : 0.0)) > 1e-4) return fail(ctx, HJCD_EINVAL, "flange rotation not orthonormal");
+        }
+    if (flange[12] != 0.0f || flange[13] != 0.0f || flange[14] != 0.0f || flange[15] != 1.0f)
+        return fail(ctx, HJCD_EINVAL, "flange last row must be 0 0 0 1");
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) P.fl_r[3 * i + j] = flange[4 * i + j];
+        P.fl_p[i] = flange[4 * i + 3];
+    }
+    const int nb = n + 2;
+    std::vector<float4> sph(n_spheres);
+    std::vector<int32_t> body(n_spheres);
+    for (int s = 0; s < n_spheres; ++s) {
+        if (sph_link[s] < 0 || sph_link[s] > n + 1) return fail(ctx, HJCD_EINVAL, "sphere %d: body outside [0, n+1]", s);
+        if (!(sph_xyzr[4 * s + 3] > 0.0f)) return fail(ctx, HJCD_EINVAL, "sphere %d: radius must be > 0", s);
+        sph[s] = make_float4(sph_xyzr[4 * s], sph_xyzr[4 * s + 1], sph_xyzr[4 * s + 2], sph_xyzr[4 * s + 3]);
+        body[s] = sph_link[s];
+    }
+    std::vector<uint32_t> mask(nb, 0u);
+    for (int i = 0; i < nb; ++i)
+        for (int j = 0; j < nb; ++j) {
+            const bool ign = ignore_pairs ? ignore_pairs[i * nb + j] != 0 : std::abs(i - j) <= 1;
+            if (i != j && !ign) mask[i] |= 1u << j;
+        }
+    hjcd_status st = make_current(ctx);
+    if (st) return st;
+    const size_t bytes = align_up(16 * (size_t)std::max(n_spheres, 1)) + align_up(4 * (size_t)std::max(n_spheres, 1)) +
+                         align_up(4 * (size_t)nb);
+    HJCD_CUDA(ctx, cudaMalloc(&rec.dbuf, bytes));
+    rec.sph = reinterpret_cast<float4*>(rec.dbuf);
+    rec.body = reinterpret_cast<int32_t*>((char*)rec.dbuf + align_up(16 * (size_t)std::max(n_spheres, 1)));
+    rec.mask = reinterpret_cast<uint32_t*>((char*)rec.body + align_up(4 * (size_t)std::max(n_spheres, 1)));
+    if (n_spheres > 0) {
+        HJCD_CUDA(ctx, cudaMemcpy(rec.sph, sph.data(), 16 * (size_t)n_spheres, cudaMemcpyHostToDevice));
+        HJCD_CUDA(ctx, cudaMemcpy(rec.body, body.data(), 4 * (size_t)n_spheres, cudaMemcpyHostToDevice));
+    }
+    HJCD_CUDA(ctx, cudaMemcpy(rec.mask, mask.data(), 4 * (size_t)nb, cudaMemcpyHostToDevice));
+    ctx->robots.push_back(rec);
+    *robot_id = (int32_t)ctx->robots.size() - 1;
+    return HJCD_OK;
+}
+
+hjcd_status hjcd_set_scene(hjcd_ctx* ctx, int32_t scene_id_or_new, int n_sph, const float* sph_xyzr, int n_box,
+                           const float* box_lohi, int32_t* scene_id) {
+    if (!ctx) return HJCD_EINVAL;
+    if (!scene_id || n_sph < 0 || n_box < 0 || (n_sph > 0 && !sph_xyzr) || (n_box > 0 && !box_lohi))
+        return fail(ctx, HJCD_EINVAL, "bad scene arguments");
+    const int nf4 = n_sph + 2 * n_box;
+    if (nf4 > kMaxSceneFloat4)
+        return fail(ctx, HJCD_EINVAL, "scene too large: spheres + 2*boxes = %d > %d", nf4, kMaxSceneFloat4);
+    if (scene_id_or_new >= (int32_t)ctx->scenes.size()) return fail(ctx, HJCD_ENOTFOUND, "unknown scene id %d", scene_id_or_new);
+    if ((n_sph > 0 && pointer_kind(sph_xyzr) == 1) || (n_box > 0 && pointer_kind(box_lohi) == 1))
+        return fail(ctx, HJCD_EINVAL, "scene tables must be host memory");
+    std::vector<float4> buf(std::max(nf4, 1));
+    for (int i = 0; i < n_sph; ++i) {
+        if (!(sph_xyzr[4 * i + 3] > 0.0f)) return fail(ctx, HJCD_EINVAL, "obstacle sphere %d: radius must be > 0", i);
+        buf[i] = make_float4(sph_xyzr[4 * i], sph_xyzr[4 * i + 1], sph_xyzr[4 * i + 2], sph_xyzr[4 * i + 3]);
+    }
+    for (int i = 0; i < n_box; ++i) {
+        const float* b = box_lohi + 6 * i;
+        if (!(b[0] <= b[3] && b[1] <= b[4] && b[2] <= b[5])) return fail(ctx, HJCD_EINVAL, "box %d: lo > hi", i);
+        buf[n_sph + 2 * i] = make_float4(b[0], b[1], b[2], 0.0f);
+        buf[n_sph + 2 * i + 1] = make_float4(b[3], b[4], b[5], 0.0f);
+    }
+    hjcd_status st = make_current(ctx);
+    if (st) return st;
+    int32_t id = scene_id_or_new;
+    if (id < 0) {
+        ctx->scenes.push_back(SceneRec{});
+        id = (int32_t)ctx->scenes.size() - 1;
+    }
+    SceneRec& S = ctx->scenes[id];
+    const size_t bytes = 16 * (size_t)std::max(nf4, 1);
+    if (bytes > S.cap) {
+        // an earlier solve may still read the old table
+        HJCD_CUDA(ctx, cudaDeviceSynchronize());
+        if (S.buf) HJCD_CUDA(ctx, cudaFree(S.buf));
+        S.buf = nullptr;
+        HJCD_CUDA(ctx, cudaMalloc(&S.buf, bytes));
+        S.cap = bytes;
+    } else {
+        HJCD_CUDA(ctx, cudaDeviceSynchronize());
+    }
+    HJCD_CUDA(ctx, cudaMemcpy(S.buf, buf.data(), bytes, cudaMemcpyHostToDevice));
+    S.n_sph = n_sph;
+    S.n_box = n_box;
+    S.live = true;
+    *scene_id = id;
+    return HJCD_OK;
+}
+
+hjcd_status hjcd_solve(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_targets, const float* targets_pq,
+                       const hjcd_solve_opts* opts, float* out_q, float* out_err, int32_t* out_count,
+                       void* stream) {
+    if (!ctx) return HJCD_EINVAL;
+    RobotRec* rob;
+    SceneRec* sc;
+    hjcd_status st;
+    if ((st = check_robot(ctx, robot_id, &rob))) return st;
+    if ((st = check_scene(ctx, scene_id, &sc))) return st;
+    if (!opts) return fail(ctx, HJCD_EINVAL, "null opts");
+    if (n_targets < 0) return fail(ctx, HJCD_EINVAL, "n_targets < 0");
+    if (n_targets == 0) return HJCD_OK;
+    if (!targets_pq || !out_q || !out_err || !out_count) return fail(ctx, HJCD_EINVAL, "null buffer");
+    if (!(opts->eps_pos > 0.0f) || !(opts->eps_ori > 0.0f)) return fail(ctx, HJCD_EINVAL, "tolerances must be > 0");
+    if (opts->top_k < 1 || opts->top_k > HJCD_MAX_TOPK) return fail(ctx, HJCD_EINVAL, "top_k outside [1, %d]", HJCD_MAX_TOPK);
+    hjcd_params P;
+    if (opts->params) P = *opts->params;
+    else hjcd_default_params(&P);
+    if ((st = check_params(ctx, P))) return st;
+    if ((st = make_current(ctx))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const RobotParams& R = rob->P;
+    const int n = R.n, T = n_targets, top_k = opts->top_k;
+
+    // per-target seed counts and offsets
+    std::vector<int64_t> off(2 * (size_t)(T + 1));
+    int64_t* m_off = off.data();
+    int64_t* b_off = off.data() + T + 1;
+    m_off[0] = b_off[0] = 0;
+    int max_m = 0, max_b = 0;
+    for (int t = 0; t < T; ++t) {
+        const int m = opts->samples_per_target ? opts->samples_per_target[t] : opts->n_samples;
+        if (m < 1 || m > HJCD_MAX_SAMPLES)
+            return fail(ctx, HJCD_EINVAL, "target %d: seed count %d outside [1, %d]", t, m, HJCD_MAX_SAMPLES);
+        const int64_t b = dup_count(m, P.dup_ratio);
+        m_off[t + 1] = m_off[t] + m;
+        b_off[t + 1] = b_off[t] + b;
+        max_m = std::max(max_m, m);
+        max_b = std::max(max_b, (int)b);
+    }
+    const int64_t CM = m_off[T], CB = b_off[T];
+
+    const bool dev_tgt = pointer_kind(targets_pq) == 1;
+    const bool dev_q = pointer_kind(out_q) == 1, dev_e = pointer_kind(out_err) == 1,
+               dev_c = pointer_kind(out_count) == 1;
+    if (!dev_tgt) {
+        for (int t = 0; t < T; ++t) {
+            const float* q = targets_pq + 7 * (size_t)t + 3;
+            const float nn = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+            if (!(nn > 0.0f) || !std::isfinite(nn)) return fail(ctx, HJCD_EINVAL, "target %d: zero quaternion", t);
+        }
+    }
+
+    // workspace
+    Carve cv;
+    const size_t o_tg = cv.take<TargetDesc>(T);
+    const size_t o_off = cv.take<int64_t>(2 * (size_t)(T + 1));
+    const size_t o_thM = cv.take<float>((size_t)n * CM);
+    const size_t o_sM = cv.take<float>(CM);
+    const size_t o_thB = cv.take<float>((size_t)n * CB);
+    const size_t o_sB = cv.take<float>(CB);
+    const size_t o_pB = cv.take<float>(CB);
+    const size_t o_oB = cv.take<float>(CB);
+    const size_t o_hB = cv.take<uint8_t>(CB);
+    const size_t o_t7 = cv.take<float>(dev_tgt ? 0 : 7 * (size_t)T);
+    const size_t o_q = cv.take<float>(dev_q ? 0 : (size_t)T * top_k * n);
+    const size_t o_e = cv.take<float>(dev_e ? 0 : (size_t)T * top_k * 2);
+    const size_t o_c = cv.take<int32_t>(dev_c ? 0 : (size_t)T);
+    if ((st = ensure_ws(ctx, cv.off))) return st;
+    HJCD_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ws_free, 0));
+    char* W = ctx->ws;
+    TargetDesc* d_tg = reinterpret_cast<TargetDesc*>(W + o_tg);
+    int64_t* d_moff = reinterpret_cast<int64_t*>(W + o_off);
+    int64_t* d_boff = d_moff + T + 1;
+    float* thM = reinterpret_cast<float*>(W + o_thM);
+    float* sM = reinterpret_cast<float*>(W + o_sM);
+    float* thB = reinterpret_cast<float*>(W + o_thB);
+    float* sB = reinterpret_cast<float*>(W + o_sB);
+    float* pB = reinterpret_cast<float*>(W + o_pB);
+    float* oB = reinterpret_cast<float*>(W + o_oB);
+    uint8_t* hB = reinterpret_cast<uint8_t*>(W + o_hB);
+    float* q_out = dev_q ? out_q : reinterpret_cast<float*>(W + o_q);
+    float* e_out = dev_e ? out_err : reinterpret_cast<float*>(W + o_e);
+    int32_t* c_out = dev_c ? out_count : reinterpret_cast<int32_t*>(W + o_c);
+
+    // host -> device: offsets (and targets when they are host memory) through pinned staging
+    const size_t pin_off = off.size() * sizeof(int64_t);
+    const size_t pin_tgt = dev_tgt ? 0 : 7 * sizeof(float) * (size_t)T;
+    if ((st = ensure_pin(ctx, align_up(pin_off) + pin_tgt))) return st;
+    std::memcpy(ctx->pin, off.data(), pin_off);
+    HJCD_CUDA(ctx, cudaMemcpyAsync(d_moff, ctx->pin, pin_off, cudaMemcpyHostToDevice, s));
+    const float* d_t7 = targets_pq;
+    if (!dev_tgt) {
+        float* t7 = reinterpret_cast<float*>(W + o_t7);
+        if (pinned_host(targets_pq)) {
+            HJCD_CUDA(ctx, cudaMemcpyAsync(t7, targets_pq, pin_tgt, cudaMemcpyHostToDevice, s));
+        } else {
+            std::memcpy(ctx->pin + align_up(pin_off), targets_pq, pin_tgt);
+            HJCD_CUDA(ctx, cudaMemcpyAsync(t7, ctx->pin + align_up(pin_off), pin_tgt, cudaMemcpyHostToDevice, s));
+        }
+        d_t7 = t7;
+    }
+    HJCD_CUDA(ctx, cudaEventRecord(ctx->pin_free, s));
+    HJCD_CUDA(ctx, cudaMemsetAsync(ctx->err_flag, 0, sizeof(int32_t), s));
+
+    const bool prof = ctx->profile;
+    if (prof) HJCD_CUDA(ctx, cudaEventRecord(ctx->ev[0], s));
+    launch_pack_targets(d_t7, T, opts->eps_pos, opts->eps_ori, opts->seed, nullptr, d_tg, s);
+    if ((st = after_launch(ctx, 1))) return st;
+
+    // Alg. 2 line 1: PO-CCD from uniform seeds
+    CcdArgs ca{};
+    ca.tg = d_tg;
+    ca.map = CandMap{nullptr, nullptr, d_moff, T};
+    ca.C = CM;
+    ca.ld = CM;
+    ca.th_in = nullptr;
+    ca.th_out = thM;
+    ca.score = sM;
+    ca.k0 = 0;
+    ca.n_iters = P.cd_max_iters;
+    ca.P = P;
+    ca.cnt = ctx->cnt;
+    launch_ccd(R, ca, false, s);
+    if ((st = after_launch(ctx, 1))) return st;
+    if (prof) HJCD_CUDA(ctx, cudaEventRecord(ctx->ev[1], s));
+
+    // lines 2-7: top-K and perturbed duplication
+    DupArgs da{d_tg, T, d_moff, sM, thM, CM, d_boff, thB, CB, nullptr, P.dup_ratio, P.dup_sigma};
+    launch_topk_dup(R, da, max_m, s);
+    if ((st = after_launch(ctx, 1))) return st;
+    if (prof) HJCD_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
+
+    // line 8: PJ-IK
+    LmArgs la{};
+    la.tg = d_tg;
+    la.map = CandMap{nullptr, nullptr, d_boff, T};
+    la.C = CB;
+    la.ld = CB;
+    la.th = thB;
+    la.score = sB;
+    la.perr = pB;
+    la.oerr = oB;
+    la.k0 = 0;
+    la.n_iters = P.lm_max_iters;
+    la.P = P;
+    la.cnt = ctx->cnt;
+    launch_lm(R, la, false, s);
+    if ((st = after_launch(ctx, 1))) return st;
+    if (prof) HJCD_CUDA(ctx, cudaEventRecord(ctx->ev[3], s));
+
+    // line 9: collision filter
+    const bool collide = R.n_sph > 0;
+    if (collide) {
+        CollideArgs cl{};
+        cl.rsph = rob->sph;
+        cl.rsph_body = rob->body;
+        cl.pair_mask = rob->mask;
+        cl.scene = sc ? sc->buf : nullptr;
+        cl.n_osph = sc ? sc->n_sph : 0;
+        cl.n_obox = sc ? sc->n_box : 0;
+        cl.C = CB;
+        cl.ld = CB;
+        cl.th = thB;
+        cl.hit = hB;
+        cl.cnt = ctx->cnt;
+        cl.err_flag = ctx->err_flag;
+        launch_collide(R, cl, s);
+        if ((st = after_launch(ctx, 1))) return st;
+    }
+    if (prof) HJCD_CUDA(ctx, cudaEventRecord(ctx->ev[4], s));
+
+    // line 10: rank the collision-free candidates
+    RankArgs ra{T, d_boff, thB, CB, sB, pB, oB, collide ? hB : nullptr, top_k, q_out, e_out, c_out};
+    launch_rank(R, ra, max_b, s);
+    if ((st = after_launch(ctx, 1))) return st;
+    if (prof) {
+        HJCD_CUDA(ctx, cudaEventRecord(ctx->ev[5], s));
+        ctx->ev_valid = true;
+    }
+
+    const bool sync = !dev_q || !dev_e || !dev_c;
+    if (!dev_q) HJCD_CUDA(ctx, cudaMemcpyAsync(out_q, q_out, sizeof(float) * (size_t)T * top_k * n, cudaMemcpyDeviceToHost, s));
+    if (!dev_e) HJCD_CUDA(ctx, cudaMemcpyAsync(out_err, e_out, sizeof(float) * (size_t)T * top_k * 2, cudaMemcpyDeviceToHost, s));
+    if (!dev_c) HJCD_CUDA(ctx, cudaMemcpyAsync(out_count, c_out, sizeof(int32_t) * (size_t)T, cudaMemcpyDeviceToHost, s));
+    HJCD_CUDA(ctx, cudaEventRecord(ctx->ws_free, s));
+    if (sync) {
+        HJCD_CUDA(ctx, cudaStreamSynchronize(s));
+        int32_t flag = 0;
+        HJCD_CUDA(ctx, cudaMemcpy(&flag, ctx->err_flag, sizeof flag, cudaMemcpyDeviceToHost));
+        if (flag) return fail(ctx, HJCD_ETIMEOUT, "collision kernel: staging wait ran out");
+    }
+    return HJCD_OK;
+}
+
+// ---- stages ----------------------------------------------------------------
+
+static hjcd_status stage_prologue(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const float* targets_pq,
+                                  float eps_pos, float eps_ori, uint64_t seed, const hjcd_params* params,
+                                  int64_t n_cand, const int32_t* tgt, const int32_t* cand, cudaStream_t s,
+                                  RobotRec** rob, hjcd_params* P, TargetDesc** d_tg) {
+    hjcd_status st;
+    if (!ctx) return HJCD_EINVAL;
+    if ((st = check_robot(ctx, robot_id, rob))) return st;
+    if (n_targets < 1 || !targets_pq || pointer_kind(targets_pq) != 1)
+        return fail(ctx, HJCD_EINVAL, "targets must be a device array of n_targets >= 1 poses");
+    if (n_cand < 0) return fail(ctx, HJCD_EINVAL, "n_cand < 0");
+    if (n_cand > 0 && (pointer_kind(tgt) != 1 || pointer_kind(cand) != 1))
+        return fail(ctx, HJCD_EINVAL, "tgt and cand must be device arrays");
+    if (!(eps_pos > 0.0f) || !(eps_ori > 0.0f)) return fail(ctx, HJCD_EINVAL, "tolerances must be > 0");
+    if (params) *P = *params;
+    else hjcd_default_params(P);
+    if ((st = check_params(ctx, *P))) return st;
+    if ((st = make_current(ctx))) return st;
+    if ((st = ensure_ws(ctx, align_up(sizeof(TargetDesc) * (size_t)n_targets)))) return st;
+    HJCD_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ws_free, 0));
+    *d_tg = reinterpret_cast<TargetDesc*>(ctx->ws);
+    return pack_device_targets(ctx, targets_pq, n_targets, eps_pos, eps_ori, seed, *d_tg, s);
+}
+
+static hjcd_status check_theta(hjcd_ctx* ctx, const void* p, int64_t n_cand, int64_t ld, const char* what) {
+    if (n_cand == 0) return HJCD_OK;
+    if (!p || pointer_kind(p) != 1) return fail(ctx, HJCD_EINVAL, "%s must be a device array", what);
+    if (ld < n_cand) return fail(ctx, HJCD_EINVAL, "%s: ld %lld < n_cand %lld", what, (long long)ld, (long long)n_cand);
+    return HJCD_OK;
+}
+
+hjcd_status hjcd_fk(hjcd_ctx* ctx, int32_t robot_id, int64_t n_cand, const float* theta, int64_t ld, float* out_pq,
+                    void* stream) {
+    if (!ctx) return HJCD_EINVAL;
+    RobotRec* rob;
+    hjcd_status st;
+    if ((st = check_robot(ctx, robot_id, &rob))) return st;
+    if ((st = check_theta(ctx, theta, n_cand, ld, "theta"))) return st;
+    if (n_cand > 0 && pointer_kind(out_pq) != 1) return fail(ctx, HJCD_EINVAL, "out_pq must be a device array");
+    if ((st = make_current(ctx))) return st;
+    launch_fk(rob->P, n_cand, theta, ld, out_pq, (cudaStream_t)stream);
+    return n_cand > 0 ? after_launch(ctx, 1) : HJCD_OK;
+}
+
+hjcd_status hjcd_sample_seeds(hjcd_ctx* ctx, int32_t robot_id, int64_t n_cand, const int32_t* tgt,
+                              const int32_t* cand, uint64_t seed, float* theta, int64_t ld, void* stream) {
+    if (!ctx) return HJCD_EINVAL;
+    RobotRec* rob;
+    hjcd_status st;
+    if ((st = check_robot(ctx, robot_id, &rob))) return st;
+    if ((st = check_theta(ctx, theta, n_cand, ld, "theta"))) return st;
+    if (n_cand == 0) return HJCD_OK;
+    if (pointer_kind(tgt) != 1 || pointer_kind(cand) != 1) return fail(ctx, HJCD_EINVAL, "tgt and cand must be device arrays");
+    if ((st = make_current(ctx))) return st;
+    launch_sample(rob->P, seed, CandMap{tgt, cand, nullptr, 0}, n_cand, theta, ld, (cudaStream_t)stream);
+    return after_launch(ctx, 1);
+}
+
+hjcd_status hjcd_po_ccd(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const float* targets_pq, float eps_pos,
+                        float eps_ori, uint64_t seed, const hjcd_params* params, int64_t n_cand, const int32_t* tgt,
+                        const int32_t* cand, const float* theta_in, float* theta_out, int64_t ld, int k0,
+                        int n_iters, float* score, float* perr, float* oerr, int32_t* iters,
+                        const hjcd_ccd_trace* trace, void* stream) {
+    RobotRec* rob;
+    hjcd_params P;
+    TargetDesc* d_tg;
+    cudaStream_t s = (cudaStream_t)stream;
+    hjcd_status st = stage_prologue(ctx, robot_id, n_targets, targets_pq, eps_pos, eps_ori, seed, params, n_cand,
+                                    tgt, cand, s, &rob, &P, &d_tg);
+    if (st) return st;
+    if (theta_in && (st = check_theta(ctx, theta_in, n_cand, ld, "theta_in"))) return st;
+    if ((st = check_theta(ctx, theta_out, n_cand, ld, "theta_out"))) return st;
+    if (k0 < 0 || n_iters < 0) return fail(ctx, HJCD_EINVAL, "k0 and n_iters must be >= 0");
+    if (trace && n_iters != 1) return fail(ctx, HJCD_EINVAL, "a trace needs n_iters == 1");
+    CcdArgs a{};
+    a.tg = d_tg;
+    a.map = CandMap{tgt, cand, nullptr, n_targets};
+    a.C = n_cand;
+    a.ld = ld;
+    a.th_in = theta_in;
+    a.th_out = theta_out;
+    a.score = score;
+    a.perr = perr;
+    a.oerr = oerr;
+    a.iters = iters;
+    a.k0 = k0;
+    a.n_iters = n_iters;
+    a.P = P;
+    if (trace) a.tr = *trace;
+    a.cnt = ctx->cnt;
+    launch_ccd(rob->P, a, trace != nullptr, s);
+    if ((st = after_launch(ctx, n_cand > 0 ? 1 : 0))) return st;
+    HJCD_CUDA(ctx, cudaEventRecord(ctx->ws_free, s));
+    return HJCD_OK;
+}
+
+hjcd_status hjcd_topk_dup(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const int64_t* m_off, const float* score_M,
+                          const float* theta_M, int64_t ld_M, const int64_t* b_off, float* theta_B, int64_t ld_B,
+                          int32_t* src_B, uint64_t seed, const hjcd_params* params, void* stream) {
+    if (!ctx) return HJCD_EINVAL;
+    RobotRec* rob;
+    hjcd_status st;
+    if ((st = check_robot(ctx, robot_id, &rob))) return st;
+    if (n_targets < 1) return fail(ctx, HJCD_EINVAL, "n_targets must be >= 1");
+    if (pointer_kind(m_off) != 1 || pointer_kind(b_off) != 1 || pointer_kind(score_M) != 1 ||
+        pointer_kind(theta_M) != 1 || pointer_kind(theta_B) != 1)
+        return fail(ctx, HJCD_EINVAL, "m_off, b_off, score_M, theta_M, theta_B must be device arrays");
+    hjcd_params P;
+    if (params) P = *params;
+    else hjcd_default_params(&P);
+    if ((st = check_params(ctx, P))) return st;
+    if ((st = make_current(ctx))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // read the offsets back once to size the sort and validate the layout
+    std::vector<int64_t> mo(n_targets + 1), bo(n_targets + 1);
+    HJCD_CUDA(ctx, cudaMemcpyAsync(mo.data(), m_off, sizeof(int64_t) * mo.size(), cudaMemcpyDeviceToHost, s));
+    HJCD_CUDA(ctx, cudaMemcpyAsync(bo.data(), b_off, sizeof(int64_t) * bo.size(), cudaMemcpyDeviceToHost, s));
+    HJCD_CUDA(ctx, cudaStreamSynchronize(s));
+    int max_m = 0;
+    for (int t = 0; t < n_targets; ++t) {
+        const int64_t m = mo[t + 1] - mo[t];
+        if (m < 0 || m > HJCD_MAX_SAMPLES) return fail(ctx, HJCD_EINVAL, "target %d: seed count outside [0, %d]", t, HJCD_MAX_SAMPLES);
+        if (bo[t + 1] - bo[t] != dup_count(m, P.dup_ratio)) return fail(ctx, HJCD_EINVAL, "target %d: b_off does not match the duplication layout", t);
+        max_m = std::max(max_m, (int)m);
+    }
+    if (mo[n_targets] > ld_M || bo[n_targets] > ld_B) return fail(ctx, HJCD_EINVAL, "ld smaller than the candidate count");
+    // a TargetDesc per target carrying only the key and the target index
+    if ((st = ensure_ws(ctx, align_up(sizeof(TargetDesc) * (size_t)n_targets)))) return st;
+    HJCD_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ws_free, 0));
+    TargetDesc* d_tg = reinterpret_cast<TargetDesc*>(ctx->ws);
+    std::vector<TargetDesc> h(n_targets);
+    for (int t = 0; t < n_targets; ++t) {
+        h[t] = TargetDesc{};
+        h[t].q[0] = 1.0f;
+        h[t].eps_pos = 1.0f;
+        h[t].eps_ori = 1.0f;
+        h[t].key[0] = (uint32_t)(seed & 0xffffffffu);
+        h[t].key[1] = (uint32_t)(seed >> 32);
+        h[t].t_local = t;
+    }
+    HJCD_CUDA(ctx, cudaMemcpyAsync(d_tg, h.data(), sizeof(TargetDesc) * h.size(), cudaMemcpyHostToDevice, s));
+    DupArgs a{d_tg, n_targets, m_off, score_M, theta_M, ld_M, b_off, theta_B, ld_B, src_B, P.dup_ratio, P.dup_sigma};
+    launch_topk_dup(rob->P, a, max_m, s);
+    if ((st = after_launch(ctx, 1))) return st;
+    HJCD_CUDA(ctx, cudaStreamSynchronize(s));  // the host staging of the key table must outlive the copy
+    HJCD_CUDA(ctx, cudaEventRecord(ctx->ws_free, s));
+    return HJCD_OK;
+}
+
+hjcd_status hjcd_pjik(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const float* targets_pq, float eps_pos,
+                      float eps_ori, uint64_t seed, const hjcd_params* params, int64_t n_cand, const int32_t* tgt,
+                      const int32_t* cand, float* theta, int64_t ld, int k0, int n_iters, float* score, float* perr,
+                      float* oerr, int32_t* iters, const hjcd_lm_trace* trace, void* stream) {
+    RobotRec* rob;
+    hjcd_params P;
+    TargetDesc* d_tg;
+    cudaStream_t s = (cudaStream_t)stream;
+    hjcd_status st = stage_prologue(ctx, robot_id, n_targets, targets_pq, eps_pos, eps_ori, seed, params, n_cand,
+                                    tgt, cand, s, &rob, &P, &d_tg);
+    if (st) return st;
+    if ((st = check_theta(ctx, theta, n_cand, ld, "theta"))) return st;
+    if (k0 < 0 || n_iters < 0) return fail(ctx, HJCD_EINVAL, "k0 and n_iters must be >= 0");
+    if (trace && n_iters != 1) return fail(ctx, HJCD_EINVAL, "a trace needs n_iters == 1");
+    LmArgs a{};
+    a.tg = d_tg;
+    a.map = CandMap{tgt, cand, nullptr, n_targets};
+    a.C = n_cand;
+    a.ld = ld;
+    a.th = theta;
+    a.score = score;
+    a.perr = perr;
+    a.oerr = oerr;
+    a.iters = iters;
+    a.k0 = k0;
+    a.n_iters = n_iters;
+    a.P = P;
+    if (trace) a.tr = *trace;
+    a.cnt = ctx->cnt;
+    launch_lm(rob->P, a, trace != nullptr, s);
+    if ((st = after_launch(ctx, n_cand > 0 ? 1 : 0))) return st;
+    HJCD_CUDA(ctx, cudaEventRecord(ctx->ws_free, s));
+    return HJCD_OK;
+}
+
+hjcd_status hjcd_collide(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int64_t n_cand, const float* theta,
+                         int64_t ld, uint8_t* hit, void* stream) {
+    if (!ctx) return HJCD_EINVAL;
+    RobotRec* rob;
+    SceneRec* sc;
+    hjcd_status st;
+    if ((st = check_robot(ctx, robot_id, &rob))) return st;
+    if ((st = check_scene(ctx, scene_id, &sc))) return st;
+    if ((st = check_theta(ctx, theta, n_cand, ld, "theta"))) return st;
+    if (n_cand == 0) return HJCD_OK;
+    if (pointer_kind(hit) != 1) return fail(ctx, HJCD_EINVAL, "hit must be a device array");
+    if ((st = make_current(ctx))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (rob->P.n_sph == 0) {
+        HJCD_CUDA(ctx, cudaMemsetAsync(hit, 0, (size_t)n_cand, s));
+        return HJCD_OK;
+    }
+    HJCD_CUDA(ctx, cudaMemsetAsync(ctx->err_flag, 0, sizeof(int32_t), s));
+    CollideArgs a{};
+    a.rsph = rob->sph;
+    a.rsph_body = rob->body;
+    a.pair_mask = rob->mask;
+    a.scene = sc ? sc->buf : nullptr;
+    a.n_osph = sc ? sc->n_sph : 0;
+    a.n_obox = sc ? sc->n_box : 0;
+    a.C = n_cand;
+    a.ld = ld;
+    a.th = theta;
+    a.hit = hit;
+    a.cnt = ctx->cnt;
+    a.err_flag = ctx->err_flag;
+    launch_collide(rob->P, a, s);
+    return after_launch(ctx, 1);
+}
+
+hjcd_status hjcd_rank(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const int64_t* b_off, const float* theta_B,
+                      int64_t ld, const float* score, const float* perr, const float* oerr, const uint8_t* hit,
+                      int top_k, float* out_q, float* out_err, int32_t* out_count, void* stream) {
+    if (!ctx) return HJCD_EINVAL;
+    RobotRec* rob;
+    hjcd_status st;
+    if ((st = check_robot(ctx, robot_id, &rob))) return st;
+    if (n_targets < 1 || top_k < 1 || top_k > HJCD_MAX_TOPK) return fail(ctx, HJCD_EINVAL, "bad n_targets or top_k");
+    if (pointer_kind(b_off) != 1 || pointer_kind(theta_B) != 1 || pointer_kind(score) != 1 ||
+        pointer_kind(perr) != 1 || pointer_kind(oerr) != 1 || (hit && pointer_kind(hit) != 1) ||
+        pointer_kind(out_q) != 1 || pointer_kind(out_err) != 1 || pointer_kind(out_count) != 1)
+        return fail(ctx, HJCD_EINVAL, "rank buffers must be device arrays");
+    if ((st = make_current(ctx))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int64_t> bo(n_targets + 1);
+    HJCD_CUDA(ctx, cudaMemcpyAsync(bo.data(), b_off, sizeof(int64_t) * bo.size(), cudaMemcpyDeviceToHost, s));
+    HJCD_CUDA(ctx, cudaStreamSynchronize(s));
+    int max_b = 0;
+    for (int t = 0; t < n_targets; ++t) {
+        const int64_t b = bo[t + 1] - bo[t];
+        if (b < 0 || b > HJCD_MAX_SAMPLES) return fail(ctx, HJCD_EINVAL, "target %d: candidate count outside [0, %d]", t, HJCD_MAX_SAMPLES);
+        max_b = std::max(max_b, (int)b);
+    }
+    if (bo[n_targets] > ld) return fail(ctx, HJCD_EINVAL, "ld smaller than the candidate count");
+    RankArgs a{n_targets, b_off, theta_B, ld, score, perr, oerr, hit, top_k, out_q, out_err, out_count};
+    launch_rank(rob->P, a, max_b, s);
+    return after_launch(ctx, 1);
+}
+
+// ---- instrumentation -----------------------------------------------------
+
+hjcd_status hjcd_set_profiling(hjcd_ctx* ctx, int on) {
+    if (!ctx) return HJCD_EINVAL;
+    ctx->profile = on != 0;
+    ctx->ev_valid = false;
+    return HJCD_OK;
+}
+
+hjcd_status hjcd_phase_times(hjcd_ctx* ctx, float ms[6]) {
+    if (!ctx || !ms) return HJCD_EINVAL;
+    if (!ctx->ev_valid) return fail(ctx, HJCD_EINVAL, "no profiled solve recorded");
+    HJCD_CUDA(ctx, cudaEventSynchronize(ctx->ev[5]));
+    for (int i = 0; i < 5; ++i) HJCD_CUDA(ctx, cudaEventElapsedTime(&ms[i], ctx->ev[i], ctx->ev[i + 1]));
+    HJCD_CUDA(ctx, cudaEventElapsedTime(&ms[5], ctx->ev[0], ctx->ev[5]));
+    return HJCD_OK;
+}
+
+hjcd_status hjcd_counters(hjcd_ctx* ctx, uint64_t out[8], int reset) {
+    if (!ctx || !out) return HJCD_EINVAL;
+    hjcd_status st;
+    if ((st = make_current(ctx))) return st;
+    HJCD_CUDA(ctx, cudaDeviceSynchronize());
+    Counters c;
+    HJCD_CUDA(ctx, cudaMemcpy(&c, ctx->cnt, sizeof c, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 8; ++i) out[i] = c.v[i];
+    if (reset) HJCD_CUDA(ctx, cudaMemset(ctx->cnt, 0, sizeof(Counters)));
+    int32_t flag = 0;
+    HJCD_CUDA(ctx, cudaMemcpy(&flag, ctx->err_flag, sizeof flag, cudaMemcpyDeviceToHost));
+    if (flag) return fail(ctx, HJCD_ETIMEOUT, "a bounded device wait ran out");
+    return HJCD_OK;
+}
+
+int64_t hjcd_launch_count(const hjcd_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+hjcd_status hjcd_ffma_probe(hjcd_ctx* ctx, int iters, double* tflops, void* stream) {
+    if (!ctx || !tflops || iters < 1) return HJCD_EINVAL;
+    hjcd_status st;
+    if ((st = make_current(ctx))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int blocks = sm_count() * 8;
+    cudaEvent_t a, b;
+    HJCD_CUDA(ctx, cudaEventCreate(&a));
+    HJCD_CUDA(ctx, cudaEventCreate(&b));
+    launch_ffma(ctx->sink, iters, blocks, s);  // warm-up
+    HJCD_CUDA(ctx, cudaEventRecord(a, s));
+    launch_ffma(ctx->sink, iters, blocks, s);
+    HJCD_CUDA(ctx, cudaEventRecord(b, s));
+    if ((st = after_launch(ctx, 2))) return st;
+    HJCD_CUDA(ctx, cudaEventSynchronize(b));
+    float ms = 0.0f;
+    HJCD_CUDA(ctx, cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    const double flops = (double)blocks * 256.0 * (double)iters * (double)ffma_flops_per_thread_iter();
+    *tflops = flops / ((double)ms * 1e-3) / 1e12;
+    return HJCD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,411 @@
+// hjcd_internal.cuh -- types and device math shared by the HJCD-IK kernels.
+//
+// All arithmetic is binary32.  Joint vectors are structure-of-arrays
+// (theta[j * ld + c]); robot tables travel as a by-value kernel parameter so
+// that their entries are constant-bank operands inside the unrolled joint
+// loops.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hjcd.h"
+
+namespace hjcd {
+
+constexpr int kMaxDof = HJCD_MAX_DOF;
+constexpr int kMaxBodies = HJCD_MAX_DOF + 2;
+
+// Philox stream phases (third counter word, high byte).
+enum : uint32_t { kPhaseSeed = 1, kPhaseCd = 2, kPhaseDup = 3, kPhaseLm = 4 };
+
+// Robot as seen by the kernels: modified-DH table with cos/sin of alpha,
+// limits, flange transform.  Passed by value (param space).
+struct RobotParams {
+    int32_t n;
+    int32_t n_sph;
+    float ca[kMaxDof], sa[kMaxDof], a[kMaxDof], d[kMaxDof], off[kMaxDof];
+    float lo[kMaxDof], hi[kMaxDof];
+    float fl_r[9];  // flange rotation, row-major
+    float fl_p[3];  // flange translation
+};
+
+// One target pose with its request's tolerances and random-stream key.
+struct __align__(16) TargetDesc {
+    float p[3];
+    float eps_pos;
+    float q[4];  // w x y z, unit
+    uint32_t key[2];
+    int32_t t_local;  // target index inside its request (keys the streams)
+    float eps_ori;
+};
+
+// Candidate -> (target row, candidate index inside the target).
+struct CandMap {
+    const int32_t* tgt;   // explicit [C], or null
+    const int32_t* cand;  // explicit [C]
+    const int64_t* off;   // [T+1] prefix offsets, used when tgt is null
+    int32_t T;
+
+    // false when an explicit target row is outside [0, T): the candidate is skipped
+    __device__ __forceinline__ bool lookup(int64_t c, int32_t& t, int32_t& s) const {
+        if (tgt) {
+            t = tgt[c];
+            s = cand[c];
+            return (uint32_t)t < (uint32_t)T;
+        }
+        int lo = 0, hi = T - 1;  // largest t with off[t] <= c
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (__ldg(off + mid) <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        t = lo;
+        s = (int32_t)(c - __ldg(off + lo));
+        return true;
+    }
+};
+
+// Device work counters (see hjcd_counters).
+struct Counters {
+    unsigned long long v[8];
+};
+
+// ----------------------------------------------------------------------------
+// small vector algebra
+
+struct V3 {
+    float x, y, z;
+};
+
+__device__ __forceinline__ V3 v3(float x, float y, float z) { return V3{x, y, z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return V3{a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return V3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator*(float s, V3 a) { return V3{s * a.x, s * a.y, s * a.z}; }
+// s * a + b with fused multiply-adds
+__device__ __forceinline__ V3 fma3(float s, V3 a, V3 b) {
+    return V3{fmaf(s, a.x, b.x), fmaf(s, a.y, b.y), fmaf(s, a.z, b.z)};
+}
+__device__ __forceinline__ float dot(V3 a, V3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+    return V3{fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x)};
+}
+
+__device__ __forceinline__ float clampf(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
+
+// sin and cos after reducing x to [-pi, pi] (Cody-Waite, 2*pi split into a
+// binary32 head and its residual), where the hardware approximation is
+// accurate to ~4e-7 absolute.
+__device__ __forceinline__ void sincos_red(float x, float* s, float* c) {
+    const float k = rintf(x * 0.159154943091895336f);
+    float r = fmaf(-k, 6.28318548202514648f, x);
+    r = fmaf(-k, -1.74845553e-07f, r);
+    __sincosf(r, s, c);
+}
+
+// ----------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11) and the maps to (0,1) and N(0,1)
+
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 rnd_block(const TargetDesc& T, uint32_t cand, uint32_t phase, uint32_t iter,
+                                           uint32_t block) {
+    return philox(make_uint4(cand, (uint32_t)T.t_local, (phase << 24) | (iter & 0xFFFFFFu), block), T.key[0],
+                  T.key[1]);
+}
+
+// ((x >> 9) + 1/2) * 2^-23: exact in binary32, inside (0, 1)
+__device__ __forceinline__ float u01(uint32_t x) { return ((float)(x >> 9) + 0.5f) * 1.1920928955078125e-07f; }
+
+// Box-Muller, cosine branch
+__device__ __forceinline__ float normal01(uint32_t a, uint32_t b) {
+    return sqrtf(-2.0f * logf(u01(a))) * cospif(2.0f * u01(b));
+}
+
+__device__ __forceinline__ uint32_t word(uint4 w, int i) { return i == 0 ? w.x : (i == 1 ? w.y : (i == 2 ? w.z : w.w)); }
+
+// n normals of one stream into out[0..n): normal j from words 2(j%2), 2(j%2)+1 of block j/2
+template <int NB>
+__device__ __forceinline__ void normals(const TargetDesc& T, uint32_t cand, uint32_t phase, uint32_t iter, int n,
+                                        float (&out)[NB]) {
+#pragma unroll
+    for (int b = 0; b < (NB + 1) / 2; ++b) {
+        if (2 * b < n) {
+            const uint4 w = rnd_block(T, cand, phase, iter, (uint32_t)b);
+            out[2 * b] = normal01(w.x, w.y);
+            if (2 * b + 1 < NB) out[2 * b + 1] = normal01(w.z, w.w);
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// forward kinematics (Eq. fk), modified DH in column form
+//
+// With C0 C1 C2 the columns of R_{0,i-1}: R_{0,i-1} Rx(alpha) has columns
+// C0, B1 = ca C1 + sa C2, B2 = ca C2 - sa C1; the origin moves by a C0 + d B2;
+// Rz(theta) then gives C0' = c C0 + s B1, C1' = c B1 - s C0, C2' = B2.  The
+// joint axis is B2 and the new origin lies on it.
+
+struct Frame {
+    V3 c0, c1, c2, p;
+};
+
+__device__ __forceinline__ Frame frame_identity() {
+    return Frame{v3(1.f, 0.f, 0.f), v3(0.f, 1.f, 0.f), v3(0.f, 0.f, 1.f), v3(0.f, 0.f, 0.f)};
+}
+
+__device__ __forceinline__ void fk_step(const RobotParams& R, int j, float theta, Frame& F) {
+    const float ca = R.ca[j], sa = R.sa[j];
+    const V3 b1 = fma3(ca, F.c1, sa * F.c2);
+    const V3 b2 = fma3(ca, F.c2, (-sa) * F.c1);
+    F.p = fma3(R.d[j], b2, fma3(R.a[j], F.c0, F.p));
+    float s, c;
+    sincos_red(theta + R.off[j], &s, &c);
+    const V3 n0 = fma3(c, F.c0, s * b1);
+    const V3 n1 = fma3(c, b1, (-s) * F.c0);
+    F.c0 = n0;
+    F.c1 = n1;
+    F.c2 = b2;
+}
+
+// flange frame from the last joint frame
+__device__ __forceinline__ Frame fk_flange(const RobotParams& R, const Frame& F) {
+    Frame E;
+    E.c0 = fma3(R.fl_r[6], F.c2, fma3(R.fl_r[3], F.c1, R.fl_r[0] * F.c0));
+    E.c1 = fma3(R.fl_r[7], F.c2, fma3(R.fl_r[4], F.c1, R.fl_r[1] * F.c0));
+    E.c2 = fma3(R.fl_r[8], F.c2, fma3(R.fl_r[5], F.c1, R.fl_r[2] * F.c0));
+    E.p = fma3(R.fl_p[2], F.c2, fma3(R.fl_p[1], F.c1, fma3(R.fl_p[0], F.c0, F.p)));
+    return E;
+}
+
+// Full chain: joint origins P[j] and axes Z[j] (KEEP), flange frame E.
+template <int NB, bool KEEP>
+__device__ __forceinline__ void fk_chain(const RobotParams& R, const float (&th)[NB], V3 (&P)[NB], V3 (&Z)[NB],
+                                         Frame& E) {
+    Frame F = frame_identity();
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        if (j < R.n) {
+            fk_step(R, j, th[j], F);
+            if (KEEP) {
+                P[j] = F.p;
+                Z[j] = F.c2;
+            }
+        }
+    }
+    E = fk_flange(R, F);
+}
+
+template <int NB>
+__device__ __forceinline__ Frame fk_ee(const RobotParams& R, const float (&th)[NB]) {
+    Frame F = frame_identity();
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        if (j < R.n) fk_step(R, j, th[j], F);
+    return fk_flange(R, F);
+}
+
+// ----------------------------------------------------------------------------
+// quaternions (w, x, y, z)
+
+struct Q4 {
+    float w;
+    V3 v;
+};
+
+// Unit quaternion of the rotation with columns c0 c1 c2 (Shepperd's method:
+// the largest of 4w^2, 4x^2, 4y^2, 4z^2 from the diagonal, the rest from the
+// off-diagonal sums), returned with w >= 0.
+__device__ __forceinline__ Q4 quat_from_frame(const Frame& E) {
+    const float m00 = E.c0.x, m10 = E.c0.y, m20 = E.c0.z;
+    const float m01 = E.c1.x, m11 = E.c1.y, m21 = E.c1.z;
+    const float m02 = E.c2.x, m12 = E.c2.y, m22 = E.c2.z;
+    const float tr = m00 + m11 + m22;
+    float w, x, y, z;
+    if (tr >= m00 && tr >= m11 && tr >= m22) {
+        const float s = 2.0f * sqrtf(1.0f + tr), r = 1.0f / s;
+        w = 0.25f * s;
+        x = (m21 - m12) * r;
+        y = (m02 - m20) * r;
+        z = (m10 - m01) * r;
+    } else if (m00 >= m11 && m00 >= m22) {
+        const float s = 2.0f * sqrtf(1.0f + m00 - m11 - m22), r = 1.0f / s;
+        w = (m21 - m12) * r;
+        x = 0.25f * s;
+        y = (m01 + m10) * r;
+        z = (m02 + m20) * r;
+    } else if (m11 >= m22) {
+        const float s = 2.0f * sqrtf(1.0f + m11 - m00 - m22), r = 1.0f / s;
+        w = (m02 - m20) * r;
+        x = (m01 + m10) * r;
+        y = 0.25f * s;
+        z = (m12 + m21) * r;
+    } else {
+        const float s = 2.0f * sqrtf(1.0f + m22 - m00 - m11), r = 1.0f / s;
+        w = (m10 - m01) * r;
+        x = (m02 + m20) * r;
+        y = (m12 + m21) * r;
+        z = 0.25f * s;
+    }
+    const float sg = (w < 0.0f) ? -1.0f : 1.0f;
+    return Q4{sg * w, v3(sg * x, sg * y, sg * z)};
+}
+
+__device__ __forceinline__ Q4 qmul(Q4 a, Q4 b) {
+    return Q4{a.w * b.w - dot(a.v, b.v), fma3(a.w, b.v, fma3(b.w, a.v, cross(a.v, b.v)))};
+}
+
+// q_err = q_t (x) q_e^-1 with the sign chosen so that w >= 0
+__device__ __forceinline__ Q4 quat_error(const TargetDesc& T, Q4 qe) {
+    const Q4 qt{T.q[0], v3(T.q[1], T.q[2], T.q[3])};
+    Q4 e = qmul(qt, Q4{qe.w, (-1.0f) * qe.v});
+    if (e.w < 0.0f) {
+        e.w = -e.w;
+        e.v = (-1.0f) * e.v;
+    }
+    return e;
+}
+
+// rotation angle of a (not necessarily unit-normalised) error quaternion,
+// 2 atan2(|v|, |w|): the norm of omega in Eq. quat_diff
+__device__ __forceinline__ float quat_angle(float w, float vv) { return 2.0f * atan2f(sqrtf(vv), fabsf(w)); }
+
+// omega of Eq. quat_diff
+__device__ __forceinline__ V3 quat_log(Q4 e) {
+    const float vv = dot(e.v, e.v);
+    const float f = (vv > 1e-30f) ? 2.0f * atan2f(sqrtf(vv), e.w) * rsqrtf(vv) : 2.0f / e.w;
+    return f * e.v;
+}
+
+// rotate x by the unit quaternion (ch, sh * z) (rotation about unit z by 2 atan2(sh, ch))
+__device__ __forceinline__ V3 rotate_half(V3 z, float sh, float ch, V3 x) {
+    const V3 u = sh * z;
+    const V3 t = 2.0f * cross(u, x);
+    return x + fma3(ch, t, cross(u, t));
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Grid for a grid-stride kernel: one thread (or warp) per item, capped at
+// `per_sm` blocks per SM.
+inline int sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+inline int grid_for(int64_t items, int per_block, int per_sm = 64) {
+    int64_t b = (items + per_block - 1) / per_block;
+    const int64_t cap = (int64_t)sm_count() * per_sm;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// ----------------------------------------------------------------------------
+// host-side launch entry points (defined in the kernel translation units)
+
+struct CcdArgs {
+    const TargetDesc* tg;
+    CandMap map;
+    int64_t C, ld;
+    const float* th_in;  // null: sample seeds
+    float* th_out;
+    float *score, *perr, *oerr;
+    int32_t* iters;
+    int k0, n_iters;
+    hjcd_params P;
+    hjcd_ccd_trace tr;
+    Counters* cnt;
+};
+
+struct LmArgs {
+    const TargetDesc* tg;
+    CandMap map;
+    int64_t C, ld;
+    float* th;
+    float *score, *perr, *oerr;
+    int32_t* iters;
+    int k0, n_iters;
+    hjcd_params P;
+    hjcd_lm_trace tr;
+    Counters* cnt;
+};
+
+struct DupArgs {
+    const TargetDesc* tg;
+    int32_t T;
+    const int64_t* m_off;
+    const float* score_M;
+    const float* th_M;
+    int64_t ld_M;
+    const int64_t* b_off;
+    float* th_B;
+    int64_t ld_B;
+    int32_t* src_B;
+    int32_t ratio;
+    float sigma;
+};
+
+struct RankArgs {
+    int32_t T;
+    const int64_t* b_off;
+    const float* th;
+    int64_t ld;
+    const float *score, *perr, *oerr;
+    const uint8_t* hit;
+    int top_k;
+    float* out_q;
+    float* out_err;
+    int32_t* out_count;
+};
+
+// Collision tables in device memory: robot spheres grouped by body
+// (float4 x y z r in the body frame), per-body [first, count) ranges and a
+// self-collision bitmask per body (bit b set: pair is checked); scene
+// spheres (float4) followed by boxes (two float4: lo.xyz, hi.xyz).
+struct CollideArgs {
+    const float4* rsph;       // [n_sph]
+    const int32_t* rsph_body; // [n_sph]
+    const uint32_t* pair_mask;// [n_bodies]: bit j of word i = check pair (i, j)
+    const float4* scene;      // [n_osph + 2 * n_obox], 16-byte aligned
+    int32_t n_osph, n_obox;
+    int64_t C, ld;
+    const float* th;
+    uint8_t* hit;
+    Counters* cnt;
+    int32_t* err_flag;        // set when the bounded wait for the staged tables runs out
+};
+
+void launch_pack_targets(const float* pq7, int T, float eps_pos, float eps_ori, uint64_t seed, const int32_t* t_local,
+                         TargetDesc* out, cudaStream_t st);
+void launch_fk(const RobotParams& R, int64_t C, const float* th, int64_t ld, float* out, cudaStream_t st);
+void launch_sample(const RobotParams& R, uint64_t seed, CandMap map, int64_t C, float* th, int64_t ld,
+                   cudaStream_t st);
+void launch_ccd(const RobotParams& R, const CcdArgs& A, bool trace, cudaStream_t st);
+void launch_lm(const RobotParams& R, const LmArgs& A, bool trace, cudaStream_t st);
+void launch_topk_dup(const RobotParams& R, const DupArgs& A, int max_m, cudaStream_t st);
+void launch_rank(const RobotParams& R, const RankArgs& A, int max_b, cudaStream_t st);
+void launch_collide(const RobotParams& R, const CollideArgs& A, cudaStream_t st);
+void launch_ffma(float* sink, int iters, int blocks, cudaStream_t st);
+int ffma_flops_per_thread_iter();
+
+}  // namespace hjcd

@@ -1,0 +1,189 @@
+// k_select.cu -- per-target selection: top-K and perturbed duplication
+// (Alg. 2 lines 2-7), ranking of the collision-free candidates (Alg. 2
+// line 10), and packing of target poses.
+//
+// One CTA per target sorts 64-bit keys (score bits << 32 | index) in shared
+// memory with a bitonic network; scores are non-negative, so their IEEE bit
+// patterns order like the values, and the index in the low word breaks ties
+// toward the lower candidate.  Invalid entries (padding, collisions, NaN)
+// get the all-ones key and sort last.
+#include "hjcd_internal.cuh"
+
+namespace hjcd {
+
+namespace {
+
+constexpr int kSelThreads = 512;
+constexpr uint64_t kNoKey = ~0ull;
+
+__device__ __forceinline__ uint64_t score_key(float s, uint32_t idx) {
+    if (!(s == s)) return kNoKey;  // NaN
+    const uint32_t bits = __float_as_uint(s + 0.0f);  // -0 -> +0
+    return ((uint64_t)bits << 32) | idx;
+}
+
+__device__ void bitonic_sort(uint64_t* keys, int N) {
+    for (int size = 2; size <= N; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < (N >> 1); i += blockDim.x) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const uint64_t a = keys[lo], b = keys[hi];
+                if ((a > b) == up) {
+                    keys[lo] = b;
+                    keys[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__device__ __forceinline__ int pow2_at_least(int m) {
+    int N = 1;
+    while (N < m) N <<= 1;
+    return N;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kSelThreads) k_topk_dup(const RobotParams R, const DupArgs A) {
+    extern __shared__ uint64_t keys[];
+    const int t = blockIdx.x;
+    const int64_t m0 = A.m_off[t];
+    const int M = (int)(A.m_off[t + 1] - m0);
+    if (M <= 0) return;
+    const int N = pow2_at_least(M);
+    for (int i = threadIdx.x; i < N; i += blockDim.x)
+        keys[i] = i < M ? score_key(A.score_M[m0 + i], (uint32_t)i) : kNoKey;
+    __syncthreads();
+    bitonic_sort(keys, N);
+
+    const int K = max(1, M / A.ratio), copies = M / K, B = K * copies;
+    const int64_t b0 = A.b_off[t];
+    const TargetDesc T = A.tg[t];
+    const int n = R.n;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        const int i = b % K;  // copy r = b / K of kept seed i
+        const uint32_t src = (uint32_t)(keys[i] & 0xffffffffu);
+        float z[NB];
+        normals<NB>(T, (uint32_t)b, kPhaseDup, 0, n, z);
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            if (j < n)
+                A.th_B[j * A.ld_B + b0 + b] =
+                    clampf(fmaf(A.sigma, z[j], A.th_M[j * A.ld_M + m0 + src]), R.lo[j], R.hi[j]);
+        if (A.src_B) A.src_B[b0 + b] = (int32_t)src;
+    }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kSelThreads) k_rank(const RobotParams R, const RankArgs A) {
+    extern __shared__ uint64_t keys[];
+    const int t = blockIdx.x;
+    const int64_t b0 = A.b_off[t];
+    const int B = (int)(A.b_off[t + 1] - b0);
+    int count = 0;
+    if (B > 0) {
+        const int N = pow2_at_least(B);
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            uint64_t k = kNoKey;
+            if (i < B && !(A.hit && A.hit[b0 + i])) {
+                const float sc = A.score[b0 + i];
+                if (sc < __int_as_float(0x7f800000)) k = score_key(sc, (uint32_t)i);  // finite only
+            }
+            keys[i] = k;
+        }
+        __syncthreads();
+        bitonic_sort(keys, N);
+        const int lim = min(A.top_k, B);
+        for (int r = 0; r < lim; ++r) count += keys[r] != kNoKey;
+        const int n = R.n;
+        for (int q = threadIdx.x; q < count * (n + 2); q += blockDim.x) {
+            const int r = q / (n + 2), j = q % (n + 2);
+            const int64_t g = b0 + (int64_t)(keys[r] & 0xffffffffu);
+            const int64_t o = (int64_t)t * A.top_k + r;
+            if (j < n) A.out_q[o * n + j] = A.th[j * A.ld + g];
+            else if (j == n) A.out_err[o * 2] = A.perr[g];
+            else A.out_err[o * 2 + 1] = A.oerr[g];
+        }
+    }
+    if (threadIdx.x == 0) A.out_count[t] = count;
+}
+
+__global__ void k_pack_targets(const float* pq7, int T, float eps_pos, float eps_ori, uint32_t k0, uint32_t k1,
+                               const int32_t* t_local, TargetDesc* out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const float* s = pq7 + 7 * (int64_t)t;
+    const float qw = s[3], qx = s[4], qy = s[5], qz = s[6];
+    const float nn = qw * qw + qx * qx + qy * qy + qz * qz;
+    const bool ok = nn > 0.0f && isfinite(nn);
+    const float r = ok ? rsqrtf(nn) : 0.0f;
+    TargetDesc d;
+    d.p[0] = s[0];
+    d.p[1] = s[1];
+    d.p[2] = s[2];
+    d.q[0] = ok ? qw * r : 1.0f;
+    d.q[1] = qx * r;
+    d.q[2] = qy * r;
+    d.q[3] = qz * r;
+    d.eps_pos = ok ? eps_pos : -1.0f;  // a zero quaternion marks the target invalid
+    d.eps_ori = eps_ori;
+    d.key[0] = k0;
+    d.key[1] = k1;
+    d.t_local = t_local ? t_local[t] : t;
+    out[t] = d;
+}
+
+int smem_for(int m) {
+    int N = 1;
+    while (N < m) N <<= 1;
+    return N * (int)sizeof(uint64_t);
+}
+
+template <typename K>
+void allow_smem(K kernel, int bytes) {
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+}  // namespace
+
+void launch_topk_dup(const RobotParams& R, const DupArgs& A, int max_m, cudaStream_t st) {
+    if (A.T <= 0 || max_m <= 0) return;
+    const int sm = smem_for(max_m);
+#define HJCD_DUP(NB)                                                            \
+    if (R.n <= NB) {                                                            \
+        allow_smem(k_topk_dup<NB>, sm);                                         \
+        k_topk_dup<NB><<<A.T, kSelThreads, sm, st>>>(R, A);                     \
+        return;                                                                 \
+    }
+    HJCD_DUP(8)
+    HJCD_DUP(16)
+    HJCD_DUP(24)
+#undef HJCD_DUP
+}
+
+void launch_rank(const RobotParams& R, const RankArgs& A, int max_b, cudaStream_t st) {
+    if (A.T <= 0) return;
+    const int sm = smem_for(max_b > 0 ? max_b : 1);
+#define HJCD_RANK(NB)                                                           \
+    if (R.n <= NB) {                                                            \
+        allow_smem(k_rank<NB>, sm);                                             \
+        k_rank<NB><<<A.T, kSelThreads, sm, st>>>(R, A);                         \
+        return;                                                                 \
+    }
+    HJCD_RANK(8)
+    HJCD_RANK(16)
+    HJCD_RANK(24)
+#undef HJCD_RANK
+}
+
+void launch_pack_targets(const float* pq7, int T, float eps_pos, float eps_ori, uint64_t seed, const int32_t* t_local,
+                         TargetDesc* out, cudaStream_t st) {
+    if (T <= 0) return;
+    k_pack_targets<<<(T + 127) / 128, 128, 0, st>>>(pq7, T, eps_pos, eps_ori, (uint32_t)(seed & 0xffffffffu),
+                                                    (uint32_t)(seed >> 32), t_local, out);
+}
+
+}  // namespace hjcd

@@ -1,0 +1,555 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Both sides receive the same inputs: every array is rounded to binary32 first
+and the oracle gets those values in double.  Floating-point outputs must agree
+within 1e-5 m / 1e-5 rad (per stage, from identical inputs).  Where a float
+decides a branch (greedy argmin, acceptance, line search), outputs are
+compared only when the oracle's decision margin exceeds 1e-5 (relative 1e-4
+for line-search costs); integer and index outputs are compared bit-exactly.
+Collision verdicts are compared bit-exactly where the oracle's verdict margin
+is at least 1e-6 m.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from paper_2510_07514_gb300 import api, build, hjcd, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+MARGIN = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def soa(theta):
+    """[C, n] host -> [n, C] device"""
+    return dev(np.ascontiguousarray(np.asarray(theta).T))
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def reach(r):
+    return max(1.0, float(np.sum(np.abs(r.a)) + np.sum(np.abs(r.d)) + 0.2))
+
+
+def robots():
+    rng = np.random.default_rng(21)
+    out = [("panda", inputs.panda())]
+    for n in (3, 12, 20, 24):
+        out.append((f"chain{n}", inputs.random_chain(rng, n)))
+    return out
+
+
+def _targets(orob, rng, T, lo, hi):
+    th = rng.uniform(lo, hi, (T, len(lo)))
+    return f32(orc.pose(orob, f32(th)))
+
+
+# ----------------------------------------------------------------------------
+# a2: forward kinematics
+
+@pytest.mark.parametrize("name,rob", robots())
+def test_fk_parity(ctx, name, rob):
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    rng = np.random.default_rng(1)
+    C = 4096 + 37  # several blocks and a ragged tail
+    th = f32(rng.uniform(rob.lo, rob.hi, (C, rob.n)))
+    got = host(ctx.fk(rid, soa(th)))
+    ref = orc.pose(orob, th)
+    tol = TOL * reach(rob) / 1.5 if rob.n > 7 else TOL
+    assert np.max(np.abs(got[:, :3] - ref[:, :3])) < tol
+    dots = np.abs(np.sum(got[:, 3:] * ref[:, 3:], axis=1))
+    ang = 2 * np.arccos(np.clip(dots, -1, 1))
+    assert np.max(ang) < tol * 2
+    assert np.all(got[:, 3] >= 0)
+
+
+def test_fk_empty(ctx):
+    rid = ctx.add_robot(inputs.panda())
+    th = torch.zeros((7, 0), device="cuda")
+    out = ctx.fk(rid, th)
+    assert out.shape == (0, 7)
+
+
+# ----------------------------------------------------------------------------
+# a1: seeds
+
+def test_seed_sampling_parity(ctx):
+    rob = inputs.panda()
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    T, S = 7, 301
+    tgt = np.repeat(np.arange(T), S).astype(np.int32)
+    cand = np.tile(np.arange(S), T).astype(np.int32)
+    seed = 0xDEADBEEF12345678
+    th = torch.empty((7, T * S), device="cuda")
+    hjcd.hjcd_sample_seeds(ctx.h, rid, T * S, dev(tgt, torch.int32), dev(cand, torch.int32), seed, th, T * S)
+    ref = orc.sample_seeds(orob, orc.make_params(seed=seed), tgt, cand)
+    assert np.max(np.abs(host(th).T - ref)) < 1e-6
+
+
+# ----------------------------------------------------------------------------
+# a3 + a4: one PO-CCD iteration, traced
+
+def _proj_lengths(orob, th, tgt_pose):
+    """|u_p| and |v_p| (m) of Eq. vec_proj for every joint (degenerate-projection guard)."""
+    n = orob.n
+    F = orc.fk_frames(orob, th)
+    pee = F[-1][:3, 3]
+    out = np.zeros((2, n))
+    for j in range(n):
+        z, p = F[j + 1][:3, 2], F[j + 1][:3, 3]
+        u, v = pee - p, tgt_pose[:3] - p
+        out[0, j] = np.linalg.norm(u - np.dot(u, z) * z)
+        out[1, j] = np.linalg.norm(v - np.dot(v, z) * z)
+    return out
+
+
+def _ccd_gpu(ctx, rid, n, tg, tgt, cand, th, k, params, seed):
+    C = len(tgt)
+    th_in = soa(th)
+    th_out = torch.empty_like(th_in)
+    buf = {k_: torch.zeros((n, C), device="cuda") for k_ in ("dp", "rp", "dq", "rq", "th_hat")}
+    ints = {k_: torch.zeros((C,), dtype=torch.int32, device="cuda") for k_ in ("jp", "jo")}
+    acc = torch.zeros((C,), dtype=torch.uint8, device="cuda")
+    tr = hjcd.hjcd_ccd_trace(*[hjcd.ptr(x) for x in (buf["dp"], buf["rp"], buf["dq"], buf["rq"], ints["jp"],
+                                                     ints["jo"], acc, buf["th_hat"])])
+    hjcd.hjcd_po_ccd(ctx.h, rid, len(tg), dev(tg), 1e-3, 1e-2, seed, params, C, dev(tgt, torch.int32),
+                     dev(cand, torch.int32), th_in, th_out, C, k, 1, trace=tr)
+    out = {k_: host(v).T for k_, v in buf.items()}
+    out.update({k_: host(v).astype(np.int64) for k_, v in ints.items()})
+    out["accepted"] = host(acc).astype(bool)
+    out["theta"] = host(th_out).T
+    return out
+
+
+@pytest.mark.parametrize("which", ["panda", "chain12", "chain20"])
+def test_ccd_iteration_trace_parity(ctx, which):
+    rob = dict(robots())[which]
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    rng = np.random.default_rng(2)
+    T, C, k, seed = 13, 2053, 3, 77
+    tg = _targets(orob, rng, T, rob.lo, rob.hi)
+    tgt = rng.integers(0, T, C).astype(np.int32)
+    cand = rng.integers(0, 4096, C).astype(np.int32)
+    th = f32(rng.uniform(rob.lo, rob.hi, (C, rob.n)))
+    P64 = orc.make_params(seed=seed)
+    g = _ccd_gpu(ctx, rid, rob.n, tg, tgt, cand, th, k, api.make_params(), seed)
+    o = orc.ccd_iteration(orob, P64, tg, tgt, cand, k, th)
+    tol = TOL * max(1.0, reach(rob) / 1.5)
+    # per-joint trial quantities, away from degenerate projections
+    good_j = np.ones((C, rob.n), bool)
+    for c in range(C):
+        pl = _proj_lengths(orob, th[c], tg[tgt[c]])
+        good_j[c] = (pl[0] > 0.05) & (pl[1] > 0.05)
+    assert good_j.mean() > 0.9
+    for key in ("dp", "rp"):
+        assert np.max(np.abs(g[key] - o[key])[good_j]) < tol, key
+    for key in ("dq", "rq"):
+        assert np.max(np.abs(g[key] - o[key])) < tol, key
+    # decisions where the oracle's margin is clear
+    robust = (o["margin_p"] > MARGIN) & (o["margin_o"] > MARGIN) & good_j.all(axis=1)
+    assert robust.mean() > 0.8
+    assert np.array_equal(g["jp"][robust], o["jp"][robust])
+    assert np.array_equal(g["jo"][robust], o["jo"][robust])
+    assert np.max(np.abs(g["th_hat"] - o["theta_hat"])[robust]) < tol
+    robust_a = robust & (o["margin_acc"] > MARGIN)
+    assert np.array_equal(g["accepted"][robust_a], o["accepted"][robust_a].astype(bool))
+    assert 0.05 < o["accepted"][robust_a].mean() < 0.99
+    assert np.max(np.abs(g["theta"] - o["theta"])[robust_a]) < tol
+
+
+def test_po_ccd_trajectories_match(ctx):
+    """Alg. 3 from sampled seeds for max_iters iterations: most candidates
+    follow the oracle's trajectory exactly (divergence needs a near-tie)."""
+    wl = inputs.cfg1()
+    rob = wl.robot
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    T, S = 16, 64
+    tg = f32(orc.pose(orob, f32(wl.theta_gen[:T])))
+    tgt = np.repeat(np.arange(T), S).astype(np.int32)
+    cand = np.tile(np.arange(S), T).astype(np.int32)
+    C = T * S
+    th = torch.empty((7, C), device="cuda")
+    score = torch.empty((C,), device="cuda")
+    perr = torch.empty((C,), device="cuda")
+    oerr = torch.empty((C,), device="cuda")
+    iters = torch.empty((C,), dtype=torch.int32, device="cuda")
+    P = api.make_params()
+    hjcd.hjcd_po_ccd(ctx.h, rid, T, dev(tg), wl.eps_pos, wl.eps_ori, wl.seed, P, C, dev(tgt, torch.int32),
+                     dev(cand, torch.int32), None, th, C, 0, P.cd_max_iters, score, perr, oerr, iters)
+    o = orc.po_ccd(orob, orc.make_params(wl.eps_pos, wl.eps_ori, seed=wl.seed), tg, tgt, cand)
+    same = np.max(np.abs(host(th).T - o["theta"]), axis=1) < 1e-4
+    assert same.mean() > 0.85
+    it = host(iters).astype(int)
+    assert np.mean(it[same] == o["iters"][same]) > 0.98
+    conv_g = (host(perr) ** 2 < P.cd_eps_pos2) & (host(oerr) ** 2 < P.cd_eps_ori2)
+    conv_o = (o["perr"] ** 2 < P.cd_eps_pos2) & (o["oerr"] ** 2 < P.cd_eps_ori2)
+    assert abs(conv_g.mean() - conv_o.mean()) < 0.03
+    sc = host(score)
+    assert np.allclose(sc[same], o["score"][same], rtol=1e-3, atol=1e-3)
+
+
+# ----------------------------------------------------------------------------
+# a5: top-K and perturbed duplication
+
+def test_topk_dup_parity(ctx):
+    rob = inputs.panda()
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    rng = np.random.default_rng(3)
+    Ms = np.array([64, 1, 3, 1000, 333, 4096], np.int64)
+    m_off = np.concatenate([[0], np.cumsum(Ms)])
+    score = np.round(rng.uniform(0, 4, m_off[-1]), 1).astype(np.float32)   # ties
+    score[::17] = np.float32(0.5)
+    thM = f32(rng.uniform(rob.lo, rob.hi, (m_off[-1], 7)))
+    seed = 99
+    P64 = orc.make_params(seed=seed)
+    o = orc.topk_dup(orob, P64, m_off, score.astype(np.float64), thM)
+    b_off = o["b_off"]
+    CB = int(b_off[-1])
+    thB = torch.empty((7, CB), device="cuda")
+    src = torch.empty((CB,), dtype=torch.int32, device="cuda")
+    hjcd.hjcd_topk_dup(ctx.h, rid, len(Ms), dev(m_off, torch.int64), dev(score), soa(thM), int(m_off[-1]),
+                       dev(b_off, torch.int64), thB, CB, src, seed, api.make_params())
+    assert np.array_equal(host(src).astype(np.int32), o["src"])
+    assert np.max(np.abs(host(thB).T - o["theta"])) < 1e-6
+
+
+# ----------------------------------------------------------------------------
+# a6: one PJ-IK iteration, traced
+
+def _lm_gpu(ctx, rid, n, tg, tgt, cand, th, k, params, seed):
+    C = len(tgt)
+    theta = soa(th)
+    J = torch.zeros((6 * n, C), device="cuda")
+    W = torch.zeros((6, C), device="cuda")
+    d = torch.zeros((n, C), device="cuda")
+    br = torch.zeros((C,), dtype=torch.int32, device="cuda")
+    al = torch.zeros((C,), device="cuda")
+    tr = hjcd.hjcd_lm_trace(*[hjcd.ptr(x) for x in (J, W, d, br, al)])
+    hjcd.hjcd_pjik(ctx.h, rid, len(tg), dev(tg), 1e-3, 1e-2, seed, params, C, dev(tgt, torch.int32),
+                   dev(cand, torch.int32), theta, C, k, 1, trace=tr)
+    return dict(J=host(J).T.reshape(C, 6, n), W=host(W).T, d_lm=host(d).T, branch=host(br).astype(int),
+                alpha=host(al), theta=host(theta).T)
+
+
+def _cond(J, W, lam):
+    Jw = W[:, None] * J
+    Dg = np.sum(Jw * Jw, axis=0) + 1e-9
+    Ah = Jw / np.sqrt(Dg)
+    ev = np.linalg.eigvalsh(Ah @ Ah.T + lam * np.eye(6))
+    return ev[-1] / ev[0]
+
+
+@pytest.mark.parametrize("which", ["panda", "chain12", "chain20"])
+def test_lm_iteration_trace_parity(ctx, which):
+    rob = dict(robots())[which]
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    rng = np.random.default_rng(4)
+    T, C, k, seed = 11, 1031, 0, 5
+    tth = rng.uniform(rob.lo, rob.hi, (T, rob.n))
+    tg = f32(orc.pose(orob, f32(tth)))
+    tgt = rng.integers(0, T, C).astype(np.int32)
+    cand = np.arange(C).astype(np.int32)
+    sig = np.where(np.arange(C) % 3 == 0, 0.3, 0.05)[:, None]
+    th = f32(np.clip(tth[tgt] + rng.normal(0, 1, (C, rob.n)) * sig, rob.lo, rob.hi))
+    P64 = orc.make_params(seed=seed)
+    g = _lm_gpu(ctx, rid, rob.n, tg, tgt, cand, th, k, api.make_params(), seed)
+    o = orc.lm_iteration(orob, P64, tg, tgt, cand, k, th)
+    tol = TOL * max(1.0, reach(rob) / 1.5)
+    assert np.max(np.abs(g["J"] - o["J"])) < tol
+    assert np.max(np.abs(g["W"] / o["W"] - 1)) < 1e-5
+    cond = np.array([_cond(o["J"][c], o["W"][c], P64.lm_lambda) for c in range(C)])
+    well = cond < 1e3
+    assert well.mean() > 0.7
+    assert np.max(np.abs(g["d_lm"] - o["d_lm"])[well]) < TOL
+    robust = well & (o["ls_margin"] > 1e-4)
+    assert robust.mean() > 0.6
+    assert np.array_equal(g["branch"][robust], o["branch"][robust])
+    assert np.array_equal(g["alpha"][robust], o["alpha"][robust].astype(np.float32).astype(np.float64))
+    assert np.max(np.abs(g["theta"] - o["theta"])[robust]) < TOL
+    assert set(np.unique(o["branch"][robust])) >= {0}
+
+
+def test_pjik_converges_like_the_oracle(ctx):
+    rob = inputs.panda()
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    rng = np.random.default_rng(5)
+    T, C = 32, 2048
+    tth = rng.uniform(rob.lo, rob.hi, (T, 7))
+    tg = f32(orc.pose(orob, f32(tth)))
+    tgt = np.repeat(np.arange(T), C // T).astype(np.int32)
+    cand = np.tile(np.arange(C // T), T).astype(np.int32)
+    th = f32(np.clip(tth[tgt] + rng.normal(0, 0.08, (C, 7)), rob.lo, rob.hi))
+    theta = soa(th)
+    perr = torch.empty((C,), device="cuda")
+    oerr = torch.empty((C,), device="cuda")
+    P = api.make_params()
+    hjcd.hjcd_pjik(ctx.h, rid, T, dev(tg), 1e-3, 1e-2, 7, P, C, dev(tgt, torch.int32), dev(cand, torch.int32),
+                   theta, C, 0, P.lm_max_iters, None, perr, oerr)
+    o = orc.pjik(orob, orc.make_params(seed=7), tg, tgt, cand, th)
+    ok_g = (host(perr) < 1e-3) & (host(oerr) < 1e-2)
+    ok_o = (o["perr"] < 1e-3) & (o["oerr"] < 1e-2)
+    assert abs(ok_g.mean() - ok_o.mean()) < 0.01
+    # every GPU result claimed converged is converged under the oracle's kinematics
+    gth = host(theta).T
+    for c in np.nonzero(ok_g)[0][:400]:
+        e = orc.residual(orob, gth[c], tg[tgt[c]])
+        assert np.linalg.norm(e[:3]) < 1e-3 + 1e-5 and np.linalg.norm(e[3:]) < 1e-2 + 1e-5
+    assert np.all(gth >= rob.lo - 1e-7) and np.all(gth <= rob.hi + 1e-7)
+
+
+# ----------------------------------------------------------------------------
+# a7: collision filter
+
+def _collision_case(rob, scene, C, seed):
+    rng = np.random.default_rng(seed)
+    return f32(rng.uniform(rob.lo, rob.hi, (C, rob.n)))
+
+
+@pytest.mark.parametrize("case", ["panda_scene", "panda_self", "chain20_scene"])
+def test_collision_verdict_parity(ctx, case):
+    if case.startswith("panda"):
+        rng = np.random.default_rng(inputs.CFG_SEED[2])
+        rob = inputs.panda_with_spheres(rng)
+        scene = inputs.random_scene(rng, 200, 20)
+    else:
+        rob = inputs.cfg3_chains()[5]
+        rng = np.random.default_rng(8)
+        scene = inputs.random_scene(rng, 100, 0, lo=(-2, -2, -1), hi=(2, 2, 2))
+    use_scene = not case.endswith("self")
+    rid = ctx.add_robot(rob)
+    sid = ctx.set_scene(scene) if use_scene else -1
+    orob = orc.Robot(rob)
+    osc = orc.Scene(scene) if use_scene else None
+    C = 6000 + 11
+    th = _collision_case(rob, scene, C, 9)
+    hit = host(ctx.collide(rid, sid, soa(th))).astype(bool)
+    ref, margin = orc.collide(orob, osc, th)
+    certain = margin >= 1e-6
+    assert certain.mean() > 0.99
+    assert np.array_equal(hit[certain], ref[certain])
+    assert 0.0 < ref.mean() < 1.0
+
+
+# ----------------------------------------------------------------------------
+# a8: ranking
+
+def test_rank_parity(ctx):
+    rob = inputs.panda()
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    rng = np.random.default_rng(10)
+    Bs = np.array([50, 1, 1000, 7, 4096], np.int64)
+    b_off = np.concatenate([[0], np.cumsum(Bs)])
+    CB = int(b_off[-1])
+    th = f32(rng.uniform(rob.lo, rob.hi, (CB, 7)))
+    score = np.round(rng.uniform(0, 3, CB), 1).astype(np.float32)
+    perr = rng.uniform(0, 1e-3, CB).astype(np.float32)
+    oerr = rng.uniform(0, 1e-2, CB).astype(np.float32)
+    hit = (rng.uniform(size=CB) < 0.6).astype(np.uint8)
+    hit[b_off[1]:b_off[2]] = 1
+    k = 16
+    T = len(Bs)
+    oq = torch.zeros((T, k, 7), device="cuda")
+    oe = torch.zeros((T, k, 2), device="cuda")
+    oc = torch.zeros((T,), dtype=torch.int32, device="cuda")
+    hjcd.hjcd_rank(ctx.h, rid, T, dev(b_off, torch.int64), soa(th), CB, dev(score), dev(perr), dev(oerr),
+                   dev(hit, torch.uint8), k, oq, oe, oc)
+    o = orc.rank(orob, b_off, th, score.astype(np.float64), f32(perr), f32(oerr), hit, k)
+    cnt = host(oc).astype(int)
+    assert np.array_equal(cnt, o["count"])
+    q, e = host(oq), host(oe)
+    for t in range(T):
+        assert np.array_equal(q[t, :cnt[t]], o["q"][t, :cnt[t]])
+        assert np.array_equal(e[t, :cnt[t]], o["err"][t, :cnt[t]])
+
+
+# ----------------------------------------------------------------------------
+# the whole method (Alg. 2)
+
+def _verify(orob, osc, rob, tg, q, err, cnt, eps_pos, eps_ori):
+    """Every returned solution: oracle errors equal the reported ones, inside
+    the limits, collision-free under brute force; returns the success mask."""
+    T = len(tg)
+    succ = np.zeros(T, bool)
+    for t in range(T):
+        for r in range(cnt[t]):
+            e = orc.residual(orob, q[t, r], tg[t])
+            assert abs(np.linalg.norm(e[:3]) - err[t, r, 0]) < 1e-5
+            assert abs(np.linalg.norm(e[3:]) - err[t, r, 1]) < 1e-5
+            assert np.all(q[t, r] >= rob.lo - 1e-7) and np.all(q[t, r] <= rob.hi + 1e-7)
+        if cnt[t] and len(rob.sph_body):
+            hit, margin = orc.collide(orob, osc, q[t, :cnt[t]])
+            assert not np.any(hit & (margin >= 1e-6))
+        succ[t] = cnt[t] > 0 and err[t, 0, 0] <= eps_pos and err[t, 0, 1] <= eps_ori
+    return succ
+
+
+def test_solve_open_world_matches_oracle(ctx):
+    """cfg1 workload shape (Panda, 64 seeds, no obstacles) on 200 targets."""
+    wl = inputs.cfg1()
+    rob = wl.robot
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    rng = np.random.default_rng(11)
+    T = 200
+    tg = f32(orc.pose(orob, f32(np.concatenate([wl.theta_gen, rng.uniform(rob.lo, rob.hi, (T - 16, 7))]))))
+    q, err, cnt = ctx.solve(rid, -1, dev(tg), wl.n_samples, 4, wl.seed, 7)
+    q, err, cnt = host(q), host(err), host(cnt).astype(int)
+    succ_g = _verify(orob, None, rob, tg, q, err, cnt, wl.eps_pos, wl.eps_ori)
+    o = orc.solve(orob, None, orc.make_params(wl.eps_pos, wl.eps_ori, seed=wl.seed), tg, wl.n_samples, 4)
+    succ_o = (o["count"] > 0) & (o["err"][:, 0, 0] <= wl.eps_pos) & (o["err"][:, 0, 1] <= wl.eps_ori)
+    assert abs(succ_g.mean() - succ_o.mean()) <= 0.01 + 1e-12
+    assert succ_g.mean() > 0.9
+
+
+def _cfg2_targets(ctx, rid, sid, orob, osc, wl, T):
+    """Targets from joint samples the oracle finds collision-free."""
+    pool = f32(wl.theta_gen)
+    hit, _ = orc.collide(orob, osc, pool[: 12 * T])
+    keep = pool[: 12 * T][~hit][:T]
+    assert len(keep) == T
+    return f32(orc.pose(orob, keep))
+
+
+def test_solve_with_obstacles_matches_oracle(ctx):
+    """cfg2 workload shape (Panda + 60 spheres, 200 spheres + 20 boxes) with
+    256 seeds on 100 targets."""
+    wl = inputs.cfg2(100, 256)
+    rob, sc = wl.robot, wl.scene
+    rid, sid = ctx.add_robot(rob), ctx.set_scene(sc)
+    orob, osc = orc.Robot(rob), orc.Scene(sc)
+    T, S, k = 100, 256, 4
+    tg = _cfg2_targets(ctx, rid, sid, orob, osc, wl, T)
+    q, err, cnt = ctx.solve(rid, sid, dev(tg), S, k, wl.seed, 7)
+    q, err, cnt = host(q), host(err), host(cnt).astype(int)
+    succ_g = _verify(orob, osc, rob, tg, q, err, cnt, wl.eps_pos, wl.eps_ori)
+    o = orc.solve(orob, osc, orc.make_params(wl.eps_pos, wl.eps_ori, seed=wl.seed), tg, S, k)
+    succ_o = (o["count"] > 0) & (o["err"][:, 0, 0] <= wl.eps_pos) & (o["err"][:, 0, 1] <= wl.eps_ori)
+    assert abs(succ_g.mean() - succ_o.mean()) <= 0.02 + 1e-12
+    assert succ_g.mean() > 0.8
+
+
+def test_solve_full_size_sampled_verification(ctx):
+    """cfg2 at full size (1000 targets x 1000 seeds, one batched launch per
+    phase, as the benchmark runs it): every solution of a sample of targets
+    is re-verified by the oracle."""
+    wl = inputs.cfg2()
+    rob, sc = wl.robot, wl.scene
+    rid, sid = ctx.add_robot(rob), ctx.set_scene(sc)
+    orob, osc = orc.Robot(rob), orc.Scene(sc)
+    tg = _cfg2_targets(ctx, rid, sid, orob, osc, wl, wl.n_targets)
+    q, err, cnt = ctx.solve(rid, sid, dev(tg), wl.n_samples, 16, wl.seed, 7)
+    q, err, cnt = host(q), host(err), host(cnt).astype(int)
+    idx = np.random.default_rng(12).choice(wl.n_targets, 24, replace=False)
+    succ = _verify(orob, osc, rob, tg[idx], q[idx], err[idx], cnt[idx], wl.eps_pos, wl.eps_ori)
+    assert succ.mean() > 0.8
+    # ranking invariants over all targets
+    for t in range(wl.n_targets):
+        s = err[t, :cnt[t], 0] ** 2 / 1e-6 + err[t, :cnt[t], 1] ** 2 / 1e-4
+        assert np.all(np.diff(s) >= -1e-3 * np.maximum(s[1:], 1e-6))
+
+
+# ----------------------------------------------------------------------------
+# boundary behaviour
+
+def test_host_and_device_buffers_give_identical_results(ctx):
+    wl = inputs.cfg1()
+    rid = ctx.add_robot(wl.robot)
+    orob = orc.Robot(wl.robot)
+    tg = f32(orc.pose(orob, f32(wl.theta_gen)))
+    a = ctx.solve(rid, -1, dev(tg), 64, 4, wl.seed, 7)
+    hq = torch.zeros((16, 4, 7)).pin_memory()
+    he = torch.zeros((16, 4, 2)).pin_memory()
+    hc = torch.zeros((16,), dtype=torch.int32)
+    ctx.solve(rid, -1, torch.as_tensor(tg, dtype=torch.float32), 64, 4, wl.seed, 7, out=(hq, he, hc))
+    assert torch.equal(a[0].cpu(), hq) and torch.equal(a[1].cpu(), he) and torch.equal(a[2].cpu(), hc)
+    b = ctx.solve(rid, -1, dev(tg), 64, 4, wl.seed, 7)
+    assert all(torch.equal(x, y) for x, y in zip(a, b))
+
+
+def test_edge_cases(ctx):
+    rob = inputs.panda()
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    tg = f32(orc.pose(orob, f32(inputs.cfg1().theta_gen[:3])))
+    # no targets
+    o = ctx.opts(8, 1, 0)
+    hjcd.hjcd_solve(ctx.h, rid, -1, 0, None, o, None, None, None)
+    # one seed per target: K = 1, B = 1
+    q, err, cnt = ctx.solve(rid, -1, dev(tg), 1, 3, 1, 7)
+    assert np.all(host(cnt) == 1)
+    # top_k above B returns B solutions
+    q, err, cnt = ctx.solve(rid, -1, dev(tg), 6, 64, 1, 7)
+    assert np.all(host(cnt) == 6)
+    # the largest seed count
+    q, err, cnt = ctx.solve(rid, -1, dev(tg[:2]), hjcd.HJCD_MAX_SAMPLES, 2, 1, 7)
+    assert np.all(host(cnt) == 2)
+    # argument errors
+    with pytest.raises(hjcd.HjcdError) as ei:
+        ctx.solve(rid, -1, dev(tg), hjcd.HJCD_MAX_SAMPLES + 1, 1, 1, 7)
+    assert ei.value.status == hjcd.HJCD_EINVAL
+    with pytest.raises(hjcd.HjcdError) as ei:
+        ctx.solve(rid + 100, -1, dev(tg), 8, 1, 1, 7)
+    assert ei.value.status == hjcd.HJCD_ENOTFOUND
+    with pytest.raises(hjcd.HjcdError) as ei:
+        ctx.solve(rid, 12345, dev(tg), 8, 1, 1, 7)
+    assert ei.value.status == hjcd.HJCD_ENOTFOUND
+    bad = tg.copy()
+    bad[1, 3:] = 0
+    with pytest.raises(hjcd.HjcdError) as ei:
+        ctx.solve(rid, -1, torch.as_tensor(bad, dtype=torch.float32), 8, 1, 1, 7,
+                  out=(torch.zeros((3, 1, 7)), torch.zeros((3, 1, 2)), torch.zeros((3,), dtype=torch.int32)))
+    assert ei.value.status == hjcd.HJCD_EINVAL
+    # a zero quaternion on the device marks that target unsolved
+    q, err, cnt = ctx.solve(rid, -1, dev(bad), 8, 1, 1, 7)
+    assert list(host(cnt).astype(int)) == [1, 0, 1]
+    with pytest.raises(hjcd.HjcdError):
+        ctx.solve(rid, -1, dev(tg), 8, 1, 1, 7, params=api.make_params(dup_ratio=0))
+    # robot table validation
+    bad_rob = inputs.panda()
+    bad_rob.lo = bad_rob.hi.copy()
+    with pytest.raises(hjcd.HjcdError):
+        ctx.add_robot(bad_rob)
+
+
+def test_long_chain_solves(ctx):
+    rob = inputs.random_chain(np.random.default_rng(13), 24)
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    tg = f32(orc.pose(orob, f32(np.random.default_rng(14).uniform(rob.lo, rob.hi, (8, 24)))))
+    q, err, cnt = ctx.solve(rid, -1, dev(tg), 256, 2, 3, 24)
+    q, err, cnt = host(q), host(err), host(cnt).astype(int)
+    succ = _verify(orob, None, rob, tg, q, err, cnt, 1e-3, 1e-2)
+    assert succ.mean() >= 0.75
