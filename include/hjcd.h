@@ -75,6 +75,7 @@ typedef struct hjcd_params {
     int32_t lm_A;           /* line-search depth [A] */
     float lm_sigma;         /* std of the PJ-IK perturbation, rad [Sigma] */
     float lm_gn_reg;        /* regulariser of the minimum-norm Gauss-Newton step (Eq. dogleg) */
+    float cd_tie;           /* greedy joint choice: a later joint wins only if better by more than this (m / rad) */
 } hjcd_params;
 
 typedef struct hjcd_solve_opts {

@@ -58,6 +58,7 @@ class Params(ct.Structure):
         ("lm_lambda", ct.c_double), ("lm_trust_R", ct.c_double), ("lm_beta", ct.c_double),
         ("lm_A", ct.c_int32),
         ("lm_sigma", ct.c_double), ("lm_gn_reg", ct.c_double),
+        ("cd_tie", ct.c_double),
         ("key", ct.c_uint32 * 2),
     ]
 

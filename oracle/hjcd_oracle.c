@@ -551,16 +551,19 @@ static int ccd_iteration(const orc_robot* R, const orc_params* P, const double t
     }
 
     /* Alg. 3 line 9: greedy choice of the best position and orientation update
-     * (smallest resulting residual; ties go to the lower joint index) */
+     * (smallest resulting residual).  Reading of "argmin" for ties: joints are
+     * scanned from the base and a later joint replaces the current choice only
+     * when its residual is lower by more than cd_tie, so updates that are equal
+     * up to rounding (e.g. parallel joint axes) go to the lower joint index.
+     * The margins record how close each of these comparisons came to flipping. */
     int jp = 0, jo = 0;
-    for (int j = 1; j < n; ++j) {
-        if (Rp[j] < Rp[jp]) jp = j;
-        if (Rq[j] < Rq[jo]) jo = j;
-    }
     double gp = INFINITY, go = INFINITY;
-    for (int j = 0; j < n; ++j) {
-        if (j != jp) gp = fmin(gp, Rp[j] - Rp[jp]);
-        if (j != jo) go = fmin(go, Rq[j] - Rq[jo]);
+    for (int j = 1; j < n; ++j) {
+        double mp = Rp[j] - (Rp[jp] - P->cd_tie), mo = Rq[j] - (Rq[jo] - P->cd_tie);
+        gp = fmin(gp, fabs(mp));
+        go = fmin(go, fabs(mo));
+        if (mp < 0.0) jp = j;
+        if (mo < 0.0) jo = j;
     }
 
     /* Alg. 3 line 10: apply both; on the same joint keep the larger step */

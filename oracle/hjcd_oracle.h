@@ -41,6 +41,7 @@ typedef struct {
     double lm_lambda, lm_trust_R, lm_beta;
     int32_t lm_A;
     double lm_sigma, lm_gn_reg;
+    double cd_tie;                      /* tie tolerance of the greedy joint choice */
     uint32_t key[2];                    /* Philox key = request seed (lo, hi) */
 } orc_params;
 

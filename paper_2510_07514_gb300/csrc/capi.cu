@@ -173,6 +173,7 @@ hjcd_status check_params(hjcd_ctx* ctx, const hjcd_params& P) {
     if (!(P.cd_sigma >= 0.0f) || !(P.dup_sigma >= 0.0f) || !(P.lm_sigma >= 0.0f))
         return fail(ctx, HJCD_EINVAL, "perturbation scales must be >= 0");
     if (!(P.proj_eps >= 0.0f)) return fail(ctx, HJCD_EINVAL, "proj_eps must be >= 0");
+    if (!(P.cd_tie >= 0.0f)) return fail(ctx, HJCD_EINVAL, "cd_tie must be >= 0");
     return HJCD_OK;
 }
 
@@ -225,6 +226,7 @@ void hjcd_default_params(hjcd_params* o) {
     o->lm_A = 4;
     o->lm_sigma = 0.01f;
     o->lm_gn_reg = 1e-6f;
+    o->cd_tie = 1e-6f;
 }
 
 hjcd_status hjcd_init(int device, hjcd_ctx** out) {

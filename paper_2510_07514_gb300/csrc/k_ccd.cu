@@ -80,8 +80,10 @@ __global__ void __launch_bounds__(128) k_ccd(const RobotParams R, const CcdArgs 
             const int k = A.k0 + kk;
             const float ep0 = sqrtf(ep2);
 
-            // lines 6-8: one position and one orientation proposal per joint
-            float best_p = 0.0f, dP = 0.0f, bo_num = 0.0f, bo_den = 1.0f, dO = 0.0f;
+            // lines 6-9: one position and one orientation proposal per joint and the
+            // greedy choice; a later joint replaces the choice only when its trial
+            // residual is lower by more than cd_tie
+            float best_p = 0.0f, dP = 0.0f, best_o = 0.0f, dO = 0.0f;
             int jp = 0, jo = 0;
             V3 Pp = v3(0.f, 0.f, 0.f), Zp = Pp, Po = Pp, Zo = Pp;
             const float phi = eo;
@@ -106,9 +108,9 @@ __global__ void __launch_bounds__(128) k_ccd(const RobotParams R, const CcdArgs 
                     __sincosf(d, &sd, &cd);
                     // target minus the end effector rotated about joint j by d
                     const V3 r = fma3(vz - uz, z, fma3(-sd, zxu, fma3(-cd, up, vp)));
-                    const float rp2 = dot(r, r);
-                    if (j == 0 || rp2 < best_p) {
-                        best_p = rp2;
+                    const float rp = sqrtf(dot(r, r));
+                    if (j == 0 || rp < best_p - P.cd_tie) {
+                        best_p = rp;
                         jp = j;
                         dP = d;
                         Pp = Pj[j];
@@ -124,10 +126,9 @@ __global__ void __launch_bounds__(128) k_ccd(const RobotParams R, const CcdArgs 
                     __sincosf(0.5f * dq, &sh, &ch);
                     const float w2 = fmaf(qerr.w, ch, sh * az);
                     const V3 v2 = fma3(ch, qerr.v, (-sh) * fma3(qerr.w, z, cross(qerr.v, z)));
-                    const float num = dot(v2, v2), den = w2 * w2;  // tan^2 of half the residual angle
-                    if (j == 0 || num * bo_den < bo_num * den) {
-                        bo_num = num;
-                        bo_den = den;
+                    const float rq = quat_angle(w2, dot(v2, v2));
+                    if (j == 0 || rq < best_o - P.cd_tie) {
+                        best_o = rq;
                         jo = j;
                         dO = dq;
                         Po = Pj[j];
@@ -135,9 +136,9 @@ __global__ void __launch_bounds__(128) k_ccd(const RobotParams R, const CcdArgs 
                     }
                     if (TRACE && kk == 0) {
                         if (A.tr.dp) A.tr.dp[j * A.ld + c] = d;
-                        if (A.tr.rp) A.tr.rp[j * A.ld + c] = sqrtf(rp2);
+                        if (A.tr.rp) A.tr.rp[j * A.ld + c] = rp;
                         if (A.tr.dq) A.tr.dq[j * A.ld + c] = dq;
-                        if (A.tr.rq) A.tr.rq[j * A.ld + c] = 2.0f * atan2f(sqrtf(num), fabsf(w2));
+                        if (A.tr.rq) A.tr.rq[j * A.ld + c] = rq;
                     }
                 }
             }

@@ -271,6 +271,24 @@ def test_ccd_orientation_step_closed_form():
             assert tr["dp"][0, 0] == pytest.approx(phi0, abs=1e-12)   # position step hits the target point
 
 
+def test_ccd_greedy_ties_go_to_the_lower_joint():
+    """A planar chain has parallel joint axes: every joint's orientation
+    update is the same rotation, so the orientation choice is an exact tie
+    that must go to joint 0; position choices are ordinary argmins."""
+    rob = orc.Robot(inputs.planar([0.5, 0.4, 0.3, 0.2]))
+    P = orc.make_params(seed=8)
+    rng = np.random.default_rng(7)
+    C = 64
+    tg = _targets(rob, rng, C)
+    th = rng.uniform(-1.0, 1.0, (C, 4))
+    tr = orc.ccd_iteration(rob, P, tg, np.arange(C), np.zeros(C), 0, th)
+    for c in range(C):
+        assert np.ptp(tr["rq"][c]) < 1e-12
+        assert tr["jo"][c] == 0
+        if tr["margin_p"][c] > 1e-9:
+            assert tr["jp"][c] == int(np.argmin(tr["rp"][c]))
+
+
 def _normal_stream(P, cand, tgt, phase, it, n):
     key = (P.key[0], P.key[1])
     out = []
@@ -291,8 +309,10 @@ def test_ccd_selection_acceptance_and_perturbation(panda):
     tr = orc.ccd_iteration(panda, P, tg, tgt_idx, cand, k, th)
     n_acc = 0
     for c in range(C):
-        assert tr["jp"][c] == int(np.argmin(tr["rp"][c]))
-        assert tr["jo"][c] == int(np.argmin(tr["rq"][c]))
+        if tr["margin_p"][c] > P.cd_tie:
+            assert tr["jp"][c] == int(np.argmin(tr["rp"][c]))
+        if tr["margin_o"][c] > P.cd_tie:
+            assert tr["jo"][c] == int(np.argmin(tr["rq"][c]))
         jp, jo = tr["jp"][c], tr["jo"][c]
         hat = th[c].copy()
         if jp != jo:
