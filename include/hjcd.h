@@ -72,7 +72,7 @@ typedef struct hjcd_params {
     float lm_lambda;        /* damping of Eq. normal-eqs [lambda] */
     float lm_trust_R;       /* trust region, rad [R] */
     float lm_beta;          /* line-search ratio [beta] */
-    int32_t lm_A;           /* line-search depth [A] */
+    int32_t lm_A;           /* line-search depth [A], 0..31 */
     float lm_sigma;         /* std of the PJ-IK perturbation, rad [Sigma] */
     float lm_gn_reg;        /* regulariser of the minimum-norm Gauss-Newton step (Eq. dogleg) */
     float cd_tie;           /* greedy joint choice: a later joint wins only if better by more than this (m / rad) */

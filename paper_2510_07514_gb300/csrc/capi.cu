@@ -53,6 +53,7 @@ struct hjcd_ctx {
     cudaEvent_t pin_free = nullptr;  // recorded after the last copy out of the pinned staging
     Counters* cnt = nullptr;
     int32_t* err_flag = nullptr;
+    unsigned long long* queue = nullptr;  // work-queue heads of the persistent kernels
     float* sink = nullptr;
     bool profile = false;
     cudaEvent_t ev[6] = {};
@@ -166,7 +167,7 @@ hjcd_status check_params(hjcd_ctx* ctx, const hjcd_params& P) {
     if (P.cd_max_iters < 0 || P.lm_max_iters < 0 || P.cd_max_iters > (1 << 20) || P.lm_max_iters > (1 << 20))
         return fail(ctx, HJCD_EINVAL, "iteration caps must be in [0, 2^20]");
     if (P.dup_ratio < 1) return fail(ctx, HJCD_EINVAL, "dup_ratio must be >= 1");
-    if (P.lm_A < 0 || P.lm_A > 64) return fail(ctx, HJCD_EINVAL, "lm_A must be in [0, 64]");
+    if (P.lm_A < 0 || P.lm_A > 31) return fail(ctx, HJCD_EINVAL, "lm_A must be in [0, 31]");
     if (!(P.lm_beta > 1.0f)) return fail(ctx, HJCD_EINVAL, "lm_beta must be > 1");
     if (!(P.lm_lambda > 0.0f) || !(P.lm_trust_R > 0.0f) || !(P.lm_gn_reg > 0.0f))
         return fail(ctx, HJCD_EINVAL, "lm_lambda, lm_trust_R and lm_gn_reg must be > 0");
@@ -226,7 +227,7 @@ void hjcd_default_params(hjcd_params* o) {
     o->lm_A = 4;
     o->lm_sigma = 0.01f;
     o->lm_gn_reg = 1e-6f;
-    o->cd_tie = 1e-6f;
+    o->cd_tie = 1e-4f;
 }
 
 hjcd_status hjcd_init(int device, hjcd_ctx** out) {
@@ -247,6 +248,7 @@ hjcd_status hjcd_init(int device, hjcd_ctx** out) {
         if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) s = HJCD_ECUDA;
     if (s == HJCD_OK && (cudaMalloc(&ctx->cnt, sizeof(Counters)) != cudaSuccess ||
                          cudaMalloc(&ctx->err_flag, sizeof(int32_t)) != cudaSuccess ||
+                         cudaMalloc(&ctx->queue, 8 * sizeof(unsigned long long)) != cudaSuccess ||
                          cudaMalloc(&ctx->sink, 4096 * sizeof(float)) != cudaSuccess))
         s = HJCD_ENOMEM;
     if (s == HJCD_OK && (cudaMemset(ctx->cnt, 0, sizeof(Counters)) != cudaSuccess ||
@@ -273,6 +275,7 @@ void hjcd_destroy(hjcd_ctx* ctx) {
     if (ctx->pin) cudaFreeHost(ctx->pin);
     if (ctx->cnt) cudaFree(ctx->cnt);
     if (ctx->err_flag) cudaFree(ctx->err_flag);
+    if (ctx->queue) cudaFree(ctx->queue);
     if (ctx->sink) cudaFree(ctx->sink);
     if (ctx->ws_free) cudaEventDestroy(ctx->ws_free);
     if (ctx->pin_free) cudaEventDestroy(ctx->pin_free);
@@ -554,6 +557,8 @@ hjcd_status hjcd_solve(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_
     la.n_iters = P.lm_max_iters;
     la.P = P;
     la.cnt = ctx->cnt;
+    la.queue = ctx->queue;
+    HJCD_CUDA(ctx, cudaMemsetAsync(ctx->queue, 0, sizeof(unsigned long long), s));
     launch_lm(R, la, false, s);
     if ((st = after_launch(ctx, 1))) return st;
     if (prof) HJCD_CUDA(ctx, cudaEventRecord(ctx->ev[3], s));
@@ -781,6 +786,8 @@ hjcd_status hjcd_pjik(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const floa
     a.P = P;
     if (trace) a.tr = *trace;
     a.cnt = ctx->cnt;
+    a.queue = ctx->queue;
+    HJCD_CUDA(ctx, cudaMemsetAsync(ctx->queue, 0, sizeof(unsigned long long), s));
     launch_lm(rob->P, a, trace != nullptr, s);
     if ((st = after_launch(ctx, n_cand > 0 ? 1 : 0))) return st;
     HJCD_CUDA(ctx, cudaEventRecord(ctx->ws_free, s));

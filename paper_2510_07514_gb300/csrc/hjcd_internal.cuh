@@ -134,18 +134,12 @@ __device__ __forceinline__ float normal01(uint32_t a, uint32_t b) {
 
 __device__ __forceinline__ uint32_t word(uint4 w, int i) { return i == 0 ? w.x : (i == 1 ? w.y : (i == 2 ? w.z : w.w)); }
 
-// n normals of one stream into out[0..n): normal j from words 2(j%2), 2(j%2)+1 of block j/2
-template <int NB>
-__device__ __forceinline__ void normals(const TargetDesc& T, uint32_t cand, uint32_t phase, uint32_t iter, int n,
-                                        float (&out)[NB]) {
-#pragma unroll
-    for (int b = 0; b < (NB + 1) / 2; ++b) {
-        if (2 * b < n) {
-            const uint4 w = rnd_block(T, cand, phase, iter, (uint32_t)b);
-            out[2 * b] = normal01(w.x, w.y);
-            if (2 * b + 1 < NB) out[2 * b + 1] = normal01(w.z, w.w);
-        }
-    }
+// the pair of normals of block b of a stream: normal 2b from words (x, y),
+// normal 2b+1 from words (z, w)
+__device__ __forceinline__ float2 normal_pair(const TargetDesc& T, uint32_t cand, uint32_t phase, uint32_t iter,
+                                              int b) {
+    const uint4 w = rnd_block(T, cand, phase, iter, (uint32_t)b);
+    return make_float2(normal01(w.x, w.y), normal01(w.z, w.w));
 }
 
 // ----------------------------------------------------------------------------
@@ -188,30 +182,13 @@ __device__ __forceinline__ Frame fk_flange(const RobotParams& R, const Frame& F)
     return E;
 }
 
-// Full chain: joint origins P[j] and axes Z[j] (KEEP), flange frame E.
-template <int NB, bool KEEP>
-__device__ __forceinline__ void fk_chain(const RobotParams& R, const float (&th)[NB], V3 (&P)[NB], V3 (&Z)[NB],
-                                         Frame& E) {
+// Flange frame of the joint vector theta[j * stride] (joint loop not
+// unrolled: the kernels keep their code small enough for the instruction
+// cache, with per-joint state in shared memory).
+__device__ __forceinline__ Frame fk_ee_col(const RobotParams& R, const float* th, int stride) {
     Frame F = frame_identity();
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-        if (j < R.n) {
-            fk_step(R, j, th[j], F);
-            if (KEEP) {
-                P[j] = F.p;
-                Z[j] = F.c2;
-            }
-        }
-    }
-    E = fk_flange(R, F);
-}
-
-template <int NB>
-__device__ __forceinline__ Frame fk_ee(const RobotParams& R, const float (&th)[NB]) {
-    Frame F = frame_identity();
-#pragma unroll
-    for (int j = 0; j < NB; ++j)
-        if (j < R.n) fk_step(R, j, th[j], F);
+#pragma unroll 1
+    for (int j = 0; j < R.n; ++j) fk_step(R, j, th[j * stride], F);
     return fk_flange(R, F);
 }
 
@@ -348,6 +325,7 @@ struct LmArgs {
     hjcd_params P;
     hjcd_lm_trace tr;
     Counters* cnt;
+    unsigned long long* queue;  // candidate queue head, zero at launch
 };
 
 struct DupArgs {

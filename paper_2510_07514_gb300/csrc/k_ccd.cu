@@ -10,32 +10,45 @@
 // residual is the composition of the two joint rotations applied to the
 // current end-effector pose (the more distal joint first), so acceptance
 // needs no second kinematics pass.
+//
+// Each thread keeps its joint vector and the joint origins/axes of the last
+// kinematics pass in a column of shared memory ([quantity][thread], so the
+// accesses of a warp hit 32 different banks); joint loops are not unrolled,
+// which keeps the kernel small enough for the instruction cache at any n.
 #include "hjcd_internal.cuh"
 
 namespace hjcd {
 
 namespace {
 
-template <int NB>
-__device__ __forceinline__ void sample_seed(const RobotParams& R, const TargetDesc& T, uint32_t s,
-                                            float (&th)[NB]) {
+constexpr int kCcdThreads = 128;
+
+// shared-memory column of a thread: theta[n], then (px py pz zx zy zz) per joint
+struct Col {
+    float* base;
+    int n;
+    __device__ __forceinline__ float& th(int j) const { return base[j * kCcdThreads]; }
+    __device__ __forceinline__ float* fr(int j) const { return base + (n + 6 * j) * kCcdThreads; }
+};
+
+__device__ __forceinline__ void sample_seed(const RobotParams& R, const TargetDesc& T, uint32_t s, const Col& col) {
+#pragma unroll 1
+    for (int b = 0; 4 * b < R.n; ++b) {
+        const uint4 w = rnd_block(T, s, kPhaseSeed, 0, (uint32_t)b);
 #pragma unroll
-    for (int b = 0; b < (NB + 3) / 4; ++b) {
-        if (4 * b < R.n) {
-            const uint4 w = rnd_block(T, s, kPhaseSeed, 0, (uint32_t)b);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int j = 4 * b + q;
-                if (j < NB && j < R.n) th[j] = fmaf(u01(word(w, q)), R.hi[j] - R.lo[j], R.lo[j]);
-            }
+        for (int q = 0; q < 4; ++q) {
+            const int j = 4 * b + q;
+            if (j < R.n) col.th(j) = fmaf(u01(word(w, q)), R.hi[j] - R.lo[j], R.lo[j]);
         }
     }
 }
 
-template <int NB, bool TRACE>
-__global__ void __launch_bounds__(128) k_ccd(const RobotParams R, const CcdArgs A) {
+template <bool TRACE>
+__global__ void __launch_bounds__(kCcdThreads, 4) k_ccd(const RobotParams R, const CcdArgs A) {
+    extern __shared__ float sm[];
     const hjcd_params& P = A.P;
     const int n = R.n;
+    const Col col{sm + threadIdx.x, n};
     const float pe2 = P.proj_eps * P.proj_eps;
     unsigned long long n_it = 0, n_cand = 0;
 
@@ -47,15 +60,11 @@ __global__ void __launch_bounds__(128) k_ccd(const RobotParams R, const CcdArgs 
         const V3 pt = v3(T.p[0], T.p[1], T.p[2]);
         ++n_cand;
 
-        float th[NB];
-#pragma unroll
-        for (int j = 0; j < NB; ++j) th[j] = 0.0f;
         if (A.th_in) {
-#pragma unroll
-            for (int j = 0; j < NB; ++j)
-                if (j < n) th[j] = A.th_in[j * A.ld + c];
+#pragma unroll 1
+            for (int j = 0; j < n; ++j) col.th(j) = A.th_in[j * A.ld + c];
         } else {
-            sample_seed<NB>(R, T, (uint32_t)s, th);
+            sample_seed(R, T, (uint32_t)s, col);
         }
 
         float delta_k = P.cd_delta0 * powf(P.cd_rho, (float)A.k0);
@@ -64,9 +73,20 @@ __global__ void __launch_bounds__(128) k_ccd(const RobotParams R, const CcdArgs 
         const bool valid = T.eps_pos > 0.0f;
 
         for (int kk = 0; valid; ++kk) {
-            V3 Pj[NB], Zj[NB];
-            Frame E;
-            fk_chain<NB, true>(R, th, Pj, Zj, E);
+            // kinematics with frames
+            Frame F = frame_identity();
+#pragma unroll 1
+            for (int j = 0; j < n; ++j) {
+                fk_step(R, j, col.th(j), F);
+                float* f = col.fr(j);
+                f[0 * kCcdThreads] = F.p.x;
+                f[1 * kCcdThreads] = F.p.y;
+                f[2 * kCcdThreads] = F.p.z;
+                f[3 * kCcdThreads] = F.c2.x;
+                f[4 * kCcdThreads] = F.c2.y;
+                f[5 * kCcdThreads] = F.c2.z;
+            }
+            const Frame E = fk_flange(R, F);
             const Q4 qerr = quat_error(T, quat_from_frame(E));
             const V3 e = pt - E.p;
             ep2 = dot(e, e);
@@ -87,59 +107,60 @@ __global__ void __launch_bounds__(128) k_ccd(const RobotParams R, const CcdArgs 
             int jp = 0, jo = 0;
             V3 Pp = v3(0.f, 0.f, 0.f), Zp = Pp, Po = Pp, Zo = Pp;
             const float phi = eo;
-#pragma unroll
-            for (int j = 0; j < NB; ++j) {
-                if (j < n) {
-                    const V3 z = Zj[j];
-                    const V3 u = E.p - Pj[j];
-                    const V3 v = pt - Pj[j];
-                    const float uz = dot(u, z), vz = dot(v, z);
-                    const V3 up = fma3(-uz, z, u);
-                    const V3 vp = fma3(-vz, z, v);
-                    const float nu2 = dot(u, u), nv2 = dot(v, v);
-                    const float nup2 = dot(up, up), nvp2 = dot(vp, vp);
-                    const V3 zxu = cross(z, up);
-                    // Eq. theta_proj, signed about the axis: atan2(z.(up x vp), up.vp) = atan2(zxu.vp, up.vp)
-                    const float cs = dot(up, vp), sn = dot(zxu, vp);
-                    const bool deg = nu2 < 1e-24f || nv2 < 1e-24f || nup2 <= pe2 * nu2 || nvp2 <= pe2 * nv2;
-                    float d = deg ? 0.0f : atan2f(sn, cs);
-                    d = clampf(th[j] + d, R.lo[j], R.hi[j]) - th[j];
-                    float sd, cd;
-                    __sincosf(d, &sd, &cd);
-                    // target minus the end effector rotated about joint j by d
-                    const V3 r = fma3(vz - uz, z, fma3(-sd, zxu, fma3(-cd, up, vp)));
-                    const float rp = sqrtf(dot(r, r));
-                    if (j == 0 || rp < best_p - P.cd_tie) {
-                        best_p = rp;
-                        jp = j;
-                        dP = d;
-                        Pp = Pj[j];
-                        Zp = z;
-                    }
-                    // Eq. ori_update: delta(k) sgn(a.z) phi; the error quaternion composed with
-                    // the inverse joint rotation [cos(d/2), -sin(d/2) z]
-                    const float az = dot(qerr.v, z);
-                    const float sg = (az > 0.0f) ? 1.0f : ((az < 0.0f) ? -1.0f : 0.0f);
-                    float dq = delta_k * sg * phi;
-                    dq = clampf(th[j] + dq, R.lo[j], R.hi[j]) - th[j];
-                    float sh, ch;
-                    __sincosf(0.5f * dq, &sh, &ch);
-                    const float w2 = fmaf(qerr.w, ch, sh * az);
-                    const V3 v2 = fma3(ch, qerr.v, (-sh) * fma3(qerr.w, z, cross(qerr.v, z)));
-                    const float rq = quat_angle(w2, dot(v2, v2));
-                    if (j == 0 || rq < best_o - P.cd_tie) {
-                        best_o = rq;
-                        jo = j;
-                        dO = dq;
-                        Po = Pj[j];
-                        Zo = z;
-                    }
-                    if (TRACE && kk == 0) {
-                        if (A.tr.dp) A.tr.dp[j * A.ld + c] = d;
-                        if (A.tr.rp) A.tr.rp[j * A.ld + c] = rp;
-                        if (A.tr.dq) A.tr.dq[j * A.ld + c] = dq;
-                        if (A.tr.rq) A.tr.rq[j * A.ld + c] = rq;
-                    }
+#pragma unroll 1
+            for (int j = 0; j < n; ++j) {
+                const float* f = col.fr(j);
+                const V3 pj = v3(f[0 * kCcdThreads], f[1 * kCcdThreads], f[2 * kCcdThreads]);
+                const V3 z = v3(f[3 * kCcdThreads], f[4 * kCcdThreads], f[5 * kCcdThreads]);
+                const float thj = col.th(j), lo = R.lo[j], hi = R.hi[j];
+                const V3 u = E.p - pj;
+                const V3 v = pt - pj;
+                const float uz = dot(u, z), vz = dot(v, z);
+                const V3 up = fma3(-uz, z, u);
+                const V3 vp = fma3(-vz, z, v);
+                const float nu2 = dot(u, u), nv2 = dot(v, v);
+                const float nup2 = dot(up, up), nvp2 = dot(vp, vp);
+                const V3 zxu = cross(z, up);
+                // Eq. theta_proj, signed about the axis: atan2(z.(up x vp), up.vp) = atan2(zxu.vp, up.vp)
+                const float cs = dot(up, vp), sn = dot(zxu, vp);
+                const bool deg = nu2 < 1e-24f || nv2 < 1e-24f || nup2 <= pe2 * nu2 || nvp2 <= pe2 * nv2;
+                float d = deg ? 0.0f : atan2f(sn, cs);
+                d = clampf(thj + d, lo, hi) - thj;
+                float sd, cd;
+                __sincosf(d, &sd, &cd);
+                // target minus the end effector rotated about joint j by d
+                const V3 r = fma3(vz - uz, z, fma3(-sd, zxu, fma3(-cd, up, vp)));
+                const float rp = sqrtf(dot(r, r));
+                if (j == 0 || rp < best_p - P.cd_tie) {
+                    best_p = rp;
+                    jp = j;
+                    dP = d;
+                    Pp = pj;
+                    Zp = z;
+                }
+                // Eq. ori_update: delta(k) sgn(a.z) phi; the error quaternion composed with
+                // the inverse joint rotation [cos(d/2), -sin(d/2) z]
+                const float az = dot(qerr.v, z);
+                const float sg = (az > 0.0f) ? 1.0f : ((az < 0.0f) ? -1.0f : 0.0f);
+                float dq = delta_k * sg * phi;
+                dq = clampf(thj + dq, lo, hi) - thj;
+                float sh, ch;
+                __sincosf(0.5f * dq, &sh, &ch);
+                const float w2 = fmaf(qerr.w, ch, sh * az);
+                const V3 v2 = fma3(ch, qerr.v, (-sh) * fma3(qerr.w, z, cross(qerr.v, z)));
+                const float rq = quat_angle(w2, dot(v2, v2));
+                if (j == 0 || rq < best_o - P.cd_tie) {
+                    best_o = rq;
+                    jo = j;
+                    dO = dq;
+                    Po = pj;
+                    Zo = z;
+                }
+                if (TRACE && kk == 0) {
+                    if (A.tr.dp) A.tr.dp[j * A.ld + c] = d;
+                    if (A.tr.rp) A.tr.rp[j * A.ld + c] = rp;
+                    if (A.tr.dq) A.tr.dq[j * A.ld + c] = dq;
+                    if (A.tr.rq) A.tr.rq[j * A.ld + c] = rq;
                 }
             }
 
@@ -171,30 +192,31 @@ __global__ void __launch_bounds__(128) k_ccd(const RobotParams R, const CcdArgs 
                 if (A.tr.jo) A.tr.jo[c] = jo;
                 if (A.tr.accepted) A.tr.accepted[c] = acc ? 1 : 0;
                 if (A.tr.th_hat) {
-#pragma unroll
-                    for (int j = 0; j < NB; ++j)
-                        if (j < n) A.tr.th_hat[j * A.ld + c] = th[j] + (j == jp ? aP : 0.0f) + (j == jo ? aO : 0.0f);
+#pragma unroll 1
+                    for (int j = 0; j < n; ++j)
+                        A.tr.th_hat[j * A.ld + c] = col.th(j) + (j == jp ? aP : 0.0f) + (j == jo ? aO : 0.0f);
                 }
             }
             if (acc) {
-#pragma unroll
-                for (int j = 0; j < NB; ++j) th[j] += (j == jp ? aP : 0.0f) + (j == jo ? aO : 0.0f);
+                col.th(jp) += aP;
+                col.th(jo) += aO;
             } else {
                 // line 12: theta + N(0, sigma^2 I), kept inside the limits
-                float z[NB];
-                normals<NB>(T, (uint32_t)s, kPhaseCd, (uint32_t)k, n, z);
-#pragma unroll
-                for (int j = 0; j < NB; ++j)
-                    if (j < n) th[j] = clampf(fmaf(P.cd_sigma, z[j], th[j]), R.lo[j], R.hi[j]);
+#pragma unroll 1
+                for (int b = 0; 2 * b < n; ++b) {
+                    const float2 z = normal_pair(T, (uint32_t)s, kPhaseCd, (uint32_t)k, b);
+                    const int j0 = 2 * b, j1 = 2 * b + 1;
+                    col.th(j0) = clampf(fmaf(P.cd_sigma, z.x, col.th(j0)), R.lo[j0], R.hi[j0]);
+                    if (j1 < n) col.th(j1) = clampf(fmaf(P.cd_sigma, z.y, col.th(j1)), R.lo[j1], R.hi[j1]);
+                }
             }
             delta_k *= P.cd_rho;
             ++n_it;
         }
 
         if (A.th_out) {
-#pragma unroll
-            for (int j = 0; j < NB; ++j)
-                if (j < n) A.th_out[j * A.ld + c] = th[j];
+#pragma unroll 1
+            for (int j = 0; j < n; ++j) A.th_out[j * A.ld + c] = col.th(j);
         }
         const float ep = sqrtf(ep2);
         if (A.score) {
@@ -215,9 +237,10 @@ __global__ void __launch_bounds__(128) k_ccd(const RobotParams R, const CcdArgs 
     }
 }
 
-template <int NB>
-__global__ void __launch_bounds__(128) k_sample(const RobotParams R, uint32_t k0, uint32_t k1, CandMap map, int64_t C,
-                                                float* th_out, int64_t ld) {
+__global__ void __launch_bounds__(kCcdThreads) k_sample(const RobotParams R, uint32_t k0, uint32_t k1, CandMap map,
+                                                        int64_t C, float* th_out, int64_t ld) {
+    extern __shared__ float sm[];
+    const Col col{sm + threadIdx.x, R.n};
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
         int32_t t, s;
         map.lookup(c, t, s);  // only the row index keys the stream
@@ -225,39 +248,38 @@ __global__ void __launch_bounds__(128) k_sample(const RobotParams R, uint32_t k0
         T.key[0] = k0;
         T.key[1] = k1;
         T.t_local = t;
-        float th[NB];
-        sample_seed<NB>(R, T, (uint32_t)s, th);
-#pragma unroll
-        for (int j = 0; j < NB; ++j)
-            if (j < R.n) th_out[j * ld + c] = th[j];
+        sample_seed(R, T, (uint32_t)s, col);
+#pragma unroll 1
+        for (int j = 0; j < R.n; ++j) th_out[j * ld + c] = col.th(j);
     }
+}
+
+template <bool TRACE>
+void launch_ccd_t(const RobotParams& R, const CcdArgs& A, cudaStream_t st) {
+    const size_t smem = sizeof(float) * 7 * R.n * kCcdThreads;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_ccd<TRACE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(float) * 7 * kMaxDof * kCcdThreads));
+        attr = true;
+    }
+    k_ccd<TRACE><<<grid_for(A.C, kCcdThreads, 16), kCcdThreads, smem, st>>>(R, A);
 }
 
 }  // namespace
 
 void launch_ccd(const RobotParams& R, const CcdArgs& A, bool trace, cudaStream_t st) {
     if (A.C <= 0) return;
-    const int g = grid_for(A.C, 128);
-#define HJCD_CCD(NB)                                                   \
-    if (R.n <= NB) {                                                   \
-        if (trace) k_ccd<NB, true><<<g, 128, 0, st>>>(R, A);           \
-        else k_ccd<NB, false><<<g, 128, 0, st>>>(R, A);                \
-        return;                                                        \
-    }
-    HJCD_CCD(8)
-    HJCD_CCD(16)
-    HJCD_CCD(24)
-#undef HJCD_CCD
+    if (trace) launch_ccd_t<true>(R, A, st);
+    else launch_ccd_t<false>(R, A, st);
 }
 
 void launch_sample(const RobotParams& R, uint64_t seed, CandMap map, int64_t C, float* th, int64_t ld,
                    cudaStream_t st) {
     if (C <= 0) return;
-    const int g = grid_for(C, 128);
     const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
-    if (R.n <= 8) k_sample<8><<<g, 128, 0, st>>>(R, k0, k1, map, C, th, ld);
-    else if (R.n <= 16) k_sample<16><<<g, 128, 0, st>>>(R, k0, k1, map, C, th, ld);
-    else k_sample<24><<<g, 128, 0, st>>>(R, k0, k1, map, C, th, ld);
+    k_sample<<<grid_for(C, kCcdThreads), kCcdThreads, sizeof(float) * R.n * kCcdThreads, st>>>(R, k0, k1, map, C,
+                                                                                               th, ld);
 }
 
 }  // namespace hjcd

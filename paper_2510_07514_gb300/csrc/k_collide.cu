@@ -68,7 +68,7 @@ __device__ __forceinline__ float4 to_world(const Frame& F, float4 s) {
     return make_float4(w.x, w.y, w.z, s.w);
 }
 
-template <int NB, int SPL>
+template <int SPL>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const RobotParams R, const CollideArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int n_obj4 = A.n_osph + 2 * A.n_obox;
@@ -125,23 +125,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const RobotPara
     const int n = R.n;
     const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
     for (int64_t c = (int64_t)blockIdx.x * kWarpsPerBlock + warp; c < A.C; c += nwarps) {
-        float th[NB];
-#pragma unroll
-        for (int j = 0; j < NB; ++j) th[j] = (j < n) ? A.th[j * A.ld + c] : 0.0f;
-
         // world positions of this lane's spheres
         float4 ws[SPL];
 #pragma unroll
         for (int q = 0; q < SPL; ++q) ws[q] = ls[q];  // body 0: the base frame is the world frame
         Frame F = frame_identity();
+#pragma unroll 1
+        for (int j = 0; j < n; ++j) {
+            fk_step(R, j, A.th[j * A.ld + c], F);
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            if (j < n) {
-                fk_step(R, j, th[j], F);
-#pragma unroll
-                for (int q = 0; q < SPL; ++q)
-                    if (lb[q] == j + 1) ws[q] = to_world(F, ls[q]);
-            }
+            for (int q = 0; q < SPL; ++q)
+                if (lb[q] == j + 1) ws[q] = to_world(F, ls[q]);
         }
         const Frame E = fk_flange(R, F);
 #pragma unroll
@@ -224,25 +218,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const RobotPara
     }
 }
 
-template <int NB, int SPL>
+template <int SPL>
 void launch_collide_t(const RobotParams& R, const CollideArgs& A, cudaStream_t st) {
     const size_t smem = 16 * (size_t)(A.n_osph + 2 * A.n_obox) + 16 + (size_t)kWarpsPerBlock * R.n_sph * 16 +
                         (size_t)R.n_sph * 4;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_collide<NB, SPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncSetAttribute(k_collide<SPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         attr_set = true;
     }
     const int g = grid_for(A.C, kWarpsPerBlock, 8);
-    k_collide<NB, SPL><<<g, kWarpsPerBlock * 32, smem, st>>>(R, A);
-}
-
-template <int NB>
-void launch_collide_nb(const RobotParams& R, const CollideArgs& A, cudaStream_t st) {
-    if (R.n_sph <= 32) launch_collide_t<NB, 1>(R, A, st);
-    else if (R.n_sph <= 64) launch_collide_t<NB, 2>(R, A, st);
-    else if (R.n_sph <= 128) launch_collide_t<NB, 4>(R, A, st);
-    else launch_collide_t<NB, 8>(R, A, st);
+    k_collide<SPL><<<g, kWarpsPerBlock * 32, smem, st>>>(R, A);
 }
 
 }  // namespace
@@ -253,9 +239,10 @@ size_t collide_smem_bytes(int n_sph, int n_osph, int n_obox) {
 
 void launch_collide(const RobotParams& R, const CollideArgs& A, cudaStream_t st) {
     if (A.C <= 0 || R.n_sph <= 0) return;
-    if (R.n <= 8) launch_collide_nb<8>(R, A, st);
-    else if (R.n <= 16) launch_collide_nb<16>(R, A, st);
-    else launch_collide_nb<24>(R, A, st);
+    if (R.n_sph <= 32) launch_collide_t<1>(R, A, st);
+    else if (R.n_sph <= 64) launch_collide_t<2>(R, A, st);
+    else if (R.n_sph <= 128) launch_collide_t<4>(R, A, st);
+    else launch_collide_t<8>(R, A, st);
 }
 
 }  // namespace hjcd

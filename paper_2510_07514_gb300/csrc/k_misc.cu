@@ -6,14 +6,13 @@ namespace hjcd {
 
 namespace {
 
-template <int NB>
 __global__ void __launch_bounds__(128) k_fk(const RobotParams R, int64_t C, const float* th_in, int64_t ld,
                                             float* out) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
-        float th[NB];
-#pragma unroll
-        for (int j = 0; j < NB; ++j) th[j] = (j < R.n) ? th_in[j * ld + c] : 0.0f;
-        const Frame E = fk_ee<NB>(R, th);
+        Frame F = frame_identity();
+#pragma unroll 1
+        for (int j = 0; j < R.n; ++j) fk_step(R, j, th_in[j * ld + c], F);
+        const Frame E = fk_flange(R, F);
         const Q4 q = quat_from_frame(E);
         float* o = out + 7 * c;
         o[0] = E.p.x;
@@ -50,10 +49,7 @@ __global__ void __launch_bounds__(256) k_ffma(float* sink, int iters) {
 
 void launch_fk(const RobotParams& R, int64_t C, const float* th, int64_t ld, float* out, cudaStream_t st) {
     if (C <= 0) return;
-    const int g = grid_for(C, 128);
-    if (R.n <= 8) k_fk<8><<<g, 128, 0, st>>>(R, C, th, ld, out);
-    else if (R.n <= 16) k_fk<16><<<g, 128, 0, st>>>(R, C, th, ld, out);
-    else k_fk<24><<<g, 128, 0, st>>>(R, C, th, ld, out);
+    k_fk<<<grid_for(C, 128), 128, 0, st>>>(R, C, th, ld, out);
 }
 
 void launch_ffma(float* sink, int iters, int blocks, cudaStream_t st) { k_ffma<<<blocks, 256, 0, st>>>(sink, iters); }

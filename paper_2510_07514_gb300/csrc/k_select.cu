@@ -46,7 +46,6 @@ __device__ __forceinline__ int pow2_at_least(int m) {
     return N;
 }
 
-template <int NB>
 __global__ void __launch_bounds__(kSelThreads) k_topk_dup(const RobotParams R, const DupArgs A) {
     extern __shared__ uint64_t keys[];
     const int t = blockIdx.x;
@@ -66,18 +65,21 @@ __global__ void __launch_bounds__(kSelThreads) k_topk_dup(const RobotParams R, c
     for (int b = threadIdx.x; b < B; b += blockDim.x) {
         const int i = b % K;  // copy r = b / K of kept seed i
         const uint32_t src = (uint32_t)(keys[i] & 0xffffffffu);
-        float z[NB];
-        normals<NB>(T, (uint32_t)b, kPhaseDup, 0, n, z);
+#pragma unroll 1
+        for (int q = 0; 2 * q < n; ++q) {
+            const float2 z = normal_pair(T, (uint32_t)b, kPhaseDup, 0, q);
 #pragma unroll
-        for (int j = 0; j < NB; ++j)
-            if (j < n)
-                A.th_B[j * A.ld_B + b0 + b] =
-                    clampf(fmaf(A.sigma, z[j], A.th_M[j * A.ld_M + m0 + src]), R.lo[j], R.hi[j]);
+            for (int h = 0; h < 2; ++h) {
+                const int j = 2 * q + h;
+                if (j < n)
+                    A.th_B[j * A.ld_B + b0 + b] =
+                        clampf(fmaf(A.sigma, h ? z.y : z.x, A.th_M[j * A.ld_M + m0 + src]), R.lo[j], R.hi[j]);
+            }
+        }
         if (A.src_B) A.src_B[b0 + b] = (int32_t)src;
     }
 }
 
-template <int NB>
 __global__ void __launch_bounds__(kSelThreads) k_rank(const RobotParams R, const RankArgs A) {
     extern __shared__ uint64_t keys[];
     const int t = blockIdx.x;
@@ -152,31 +154,15 @@ void allow_smem(K kernel, int bytes) {
 void launch_topk_dup(const RobotParams& R, const DupArgs& A, int max_m, cudaStream_t st) {
     if (A.T <= 0 || max_m <= 0) return;
     const int sm = smem_for(max_m);
-#define HJCD_DUP(NB)                                                            \
-    if (R.n <= NB) {                                                            \
-        allow_smem(k_topk_dup<NB>, sm);                                         \
-        k_topk_dup<NB><<<A.T, kSelThreads, sm, st>>>(R, A);                     \
-        return;                                                                 \
-    }
-    HJCD_DUP(8)
-    HJCD_DUP(16)
-    HJCD_DUP(24)
-#undef HJCD_DUP
+    allow_smem(k_topk_dup, sm);
+    k_topk_dup<<<A.T, kSelThreads, sm, st>>>(R, A);
 }
 
 void launch_rank(const RobotParams& R, const RankArgs& A, int max_b, cudaStream_t st) {
     if (A.T <= 0) return;
     const int sm = smem_for(max_b > 0 ? max_b : 1);
-#define HJCD_RANK(NB)                                                           \
-    if (R.n <= NB) {                                                            \
-        allow_smem(k_rank<NB>, sm);                                             \
-        k_rank<NB><<<A.T, kSelThreads, sm, st>>>(R, A);                         \
-        return;                                                                 \
-    }
-    HJCD_RANK(8)
-    HJCD_RANK(16)
-    HJCD_RANK(24)
-#undef HJCD_RANK
+    allow_smem(k_rank, sm);
+    k_rank<<<A.T, kSelThreads, sm, st>>>(R, A);
 }
 
 void launch_pack_targets(const float* pq7, int T, float eps_pos, float eps_ori, uint64_t seed, const int32_t* t_local,
