@@ -144,6 +144,40 @@ hjcd_status hjcd_solve(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_
                        const float* targets_pq, const hjcd_solve_opts* opts,
                        float* out_q, float* out_err, int32_t* out_count, void* stream);
 
+/* ---- the whole method without allocation ------------------------------------- */
+
+/* Bytes of the file-scope device array that serves as the scratch of
+ * hjcd_solve_noalloc.  A call needs 48 T + 16 (T + 1) + 12 for the targets,
+ * offsets and flags, plus (4 n + 4) M + (4 n + 13) B bytes and a little
+ * alignment for T targets of M seeds (B per hjcd_topk_dup, B = M for the
+ * default ratio) and n joints: about 200k candidates of a 7-joint arm. */
+#define HJCD_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* hjcd_solve for callers that cannot allocate device memory while they run:
+ * real-time control loops whose latency budget rules out cudaMalloc (it may
+ * block until the device is idle), and processes whose device memory belongs
+ * to another allocator.  The paper has no counterpart.
+ * Same arguments and results as hjcd_solve, with these differences:
+ *   - targets_pq, out_q, out_err and out_count must be DEVICE pointers, and
+ *     opts->samples_per_target must be NULL (every target uses n_samples);
+ *   - the scratch is one file-scope device array of
+ *     HJCD_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds
+ *     until the process exits; a call needing more returns HJCD_EINVAL;
+ *   - the call allocates nothing (no cudaMalloc, cudaFree, pinned or pooled
+ *     memory): it only enqueues work on `stream` and returns;
+ *   - every call shares that array and finds the previous call's contents in
+ *     it (what must start at zero is cleared on the stream), so calls that
+ *     overlap on the GPU -- on different streams, or from several contexts --
+ *     race and corrupt each other's results;
+ *   - the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture begins;
+ *   - work counters are not updated, and a staging wait of the collision
+ *     kernel that runs out is not reported (the call does not synchronise). */
+hjcd_status hjcd_solve_noalloc(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_targets,
+                               const float* targets_pq, const hjcd_solve_opts* opts,
+                               float* out_q, float* out_err, int32_t* out_count, void* stream);
+
 /* ---- stages (device buffers only) -------------------------------------------
  * Candidates are described by `tgt[c]` (row of `targets_pq`) and `cand[c]`
  * (index of the candidate inside its target, which keys its random streams).

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -918,3 +919,159 @@ hjcd_status hjcd_ffma_probe(hjcd_ctx* ctx, int iters, double* tflops, void* stre
 }
 
 }  // extern "C"
+
+// ---- allocation-free solve ----------------------------------------------------
+//
+// hjcd_solve_noalloc keeps all of its scratch in the file-scope device array
+// below.  Host code cannot use the array's name as an address (there it
+// denotes a host-side stand-in), so the device address is looked up once per
+// device with cudaGetSymbolAddress and passed to the kernels.
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[HJCD_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// device address of g_noalloc_scratch on `device` (current), looked up on first use
+hjcd_status noalloc_scratch(hjcd_ctx* ctx, int device, char** out) {
+    if (device < 0 || device >= kNoallocMaxDevices) return fail(ctx, HJCD_EINVAL, "device ordinal %d unsupported", device);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(ctx, HJCD_ECUDA, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
+        g_noalloc_addr[device] = p;
+    }
+    *out = static_cast<char*>(g_noalloc_addr[device]);
+    return HJCD_OK;
+}
+
+// per-target seed and candidate offsets for a uniform seed count
+__global__ void k_uniform_offsets(int64_t* m_off, int64_t* b_off, int T, int64_t M, int64_t B) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= T; t += gridDim.x * blockDim.x) {
+        m_off[t] = (int64_t)t * M;
+        b_off[t] = (int64_t)t * B;
+    }
+}
+
+}  // namespace
+
+extern "C" hjcd_status hjcd_solve_noalloc(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_targets,
+                                          const float* targets_pq, const hjcd_solve_opts* opts, float* out_q,
+                                          float* out_err, int32_t* out_count, void* stream) {
+    if (!ctx) return HJCD_EINVAL;
+    RobotRec* rob;
+    SceneRec* sc;
+    hjcd_status st;
+    if ((st = check_robot(ctx, robot_id, &rob))) return st;
+    if ((st = check_scene(ctx, scene_id, &sc))) return st;
+    if (!opts) return fail(ctx, HJCD_EINVAL, "null opts");
+    if (n_targets < 0) return fail(ctx, HJCD_EINVAL, "n_targets < 0");
+    if (n_targets == 0) return HJCD_OK;
+    if (opts->samples_per_target)
+        return fail(ctx, HJCD_EINVAL, "hjcd_solve_noalloc takes a uniform n_samples (samples_per_target must be NULL)");
+    if (pointer_kind(targets_pq) != 1 || pointer_kind(out_q) != 1 || pointer_kind(out_err) != 1 ||
+        pointer_kind(out_count) != 1)
+        return fail(ctx, HJCD_EINVAL, "hjcd_solve_noalloc needs device pointers for targets and outputs");
+    if (!(opts->eps_pos > 0.0f) || !(opts->eps_ori > 0.0f)) return fail(ctx, HJCD_EINVAL, "tolerances must be > 0");
+    if (opts->top_k < 1 || opts->top_k > HJCD_MAX_TOPK) return fail(ctx, HJCD_EINVAL, "top_k outside [1, %d]", HJCD_MAX_TOPK);
+    if (opts->n_samples < 1 || opts->n_samples > HJCD_MAX_SAMPLES)
+        return fail(ctx, HJCD_EINVAL, "n_samples outside [1, %d]", HJCD_MAX_SAMPLES);
+    hjcd_params P;
+    if (opts->params) P = *opts->params;
+    else hjcd_default_params(&P);
+    if ((st = check_params(ctx, P))) return st;
+    if ((st = make_current(ctx))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const RobotParams& R = rob->P;
+    const int n = R.n, T = n_targets, top_k = opts->top_k, M = opts->n_samples;
+    const int64_t B = dup_count(M, P.dup_ratio);
+    const int64_t CM = (int64_t)T * M, CB = (int64_t)T * B;
+
+    // layout inside the static scratch
+    Carve cv;
+    const size_t o_tg = cv.take<TargetDesc>(T);
+    const size_t o_off = cv.take<int64_t>(2 * (size_t)(T + 1));
+    const size_t o_thM = cv.take<float>((size_t)n * CM);
+    const size_t o_sM = cv.take<float>(CM);
+    const size_t o_thB = cv.take<float>((size_t)n * CB);
+    const size_t o_sB = cv.take<float>(CB);
+    const size_t o_pB = cv.take<float>(CB);
+    const size_t o_oB = cv.take<float>(CB);
+    const size_t o_hB = cv.take<uint8_t>(CB);
+    const size_t o_q = cv.take<unsigned long long>(1);
+    const size_t o_f = cv.take<int32_t>(1);
+    if (cv.off > HJCD_NOALLOC_SCRATCH_BYTES)
+        return fail(ctx, HJCD_EINVAL, "hjcd_solve_noalloc: %d targets x %d seeds need %zu bytes of scratch, "
+                    "the static scratch holds %u", T, M, cv.off, (unsigned)HJCD_NOALLOC_SCRATCH_BYTES);
+    char* W = nullptr;
+    if ((st = noalloc_scratch(ctx, ctx->device, &W))) return st;
+    TargetDesc* d_tg = reinterpret_cast<TargetDesc*>(W + o_tg);
+    int64_t* d_moff = reinterpret_cast<int64_t*>(W + o_off);
+    int64_t* d_boff = d_moff + T + 1;
+    float* thM = reinterpret_cast<float*>(W + o_thM);
+    float* sM = reinterpret_cast<float*>(W + o_sM);
+    float* thB = reinterpret_cast<float*>(W + o_thB);
+    float* sB = reinterpret_cast<float*>(W + o_sB);
+    float* pB = reinterpret_cast<float*>(W + o_pB);
+    float* oB = reinterpret_cast<float*>(W + o_oB);
+    uint8_t* hB = reinterpret_cast<uint8_t*>(W + o_hB);
+    unsigned long long* queue = reinterpret_cast<unsigned long long*>(W + o_q);
+    int32_t* flag = reinterpret_cast<int32_t*>(W + o_f);
+
+    // the previous call's contents are still there: clear what must start at zero
+    HJCD_CUDA(ctx, cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s));
+    HJCD_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
+    k_uniform_offsets<<<(T + 256) / 256, 256, 0, s>>>(d_moff, d_boff, T, M, B);
+    launch_pack_targets(targets_pq, T, opts->eps_pos, opts->eps_ori, opts->seed, nullptr, d_tg, s);
+    if ((st = after_launch(ctx, 2))) return st;
+
+    CcdArgs ca{};
+    ca.tg = d_tg;
+    ca.map = CandMap{nullptr, nullptr, d_moff, T};
+    ca.C = CM;
+    ca.ld = CM;
+    ca.th_out = thM;
+    ca.score = sM;
+    ca.n_iters = P.cd_max_iters;
+    ca.P = P;
+    launch_ccd(R, ca, false, s);
+    DupArgs da{d_tg, T, d_moff, sM, thM, CM, d_boff, thB, CB, nullptr, P.dup_ratio, P.dup_sigma};
+    launch_topk_dup(R, da, M, s);
+    LmArgs la{};
+    la.tg = d_tg;
+    la.map = CandMap{nullptr, nullptr, d_boff, T};
+    la.C = CB;
+    la.ld = CB;
+    la.th = thB;
+    la.score = sB;
+    la.perr = pB;
+    la.oerr = oB;
+    la.n_iters = P.lm_max_iters;
+    la.P = P;
+    la.queue = queue;
+    launch_lm(R, la, false, s);
+    const bool collide = R.n_sph > 0;
+    if (collide) {
+        CollideArgs cl{};
+        cl.rsph = rob->sph;
+        cl.rsph_body = rob->body;
+        cl.pair_mask = rob->mask;
+        cl.scene = sc ? sc->buf : nullptr;
+        cl.n_osph = sc ? sc->n_sph : 0;
+        cl.n_obox = sc ? sc->n_box : 0;
+        cl.C = CB;
+        cl.ld = CB;
+        cl.th = thB;
+        cl.hit = hB;
+        cl.err_flag = flag;
+        launch_collide(R, cl, s);
+    }
+    RankArgs ra{T, d_boff, thB, CB, sB, pB, oB, collide ? hB : nullptr, top_k, out_q, out_err, out_count};
+    launch_rank(R, ra, (int)B, s);
+    return after_launch(ctx, collide ? 5 : 4);
+}

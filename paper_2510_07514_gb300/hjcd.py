@@ -31,6 +31,7 @@ EXPORTS = (
     "hjcd_create_robot", "hjcd_set_scene", "hjcd_solve", "hjcd_fk", "hjcd_sample_seeds",
     "hjcd_po_ccd", "hjcd_topk_dup", "hjcd_pjik", "hjcd_collide", "hjcd_rank",
     "hjcd_set_profiling", "hjcd_phase_times", "hjcd_counters", "hjcd_launch_count", "hjcd_ffma_probe",
+    "hjcd_solve_noalloc",
 )
 
 
@@ -84,6 +85,7 @@ _SIGS = {
     "hjcd_create_robot": (_ST, [_V, _I, _V, _V, _V, _V, _V, _V, _V, _I, _V, _V, _V, ct.POINTER(_I32)]),
     "hjcd_set_scene": (_ST, [_V, _I32, _I, _V, _I, _V, ct.POINTER(_I32)]),
     "hjcd_solve": (_ST, [_V, _I32, _I32, _I, _V, ct.POINTER(hjcd_solve_opts), _V, _V, _V, _V]),
+    "hjcd_solve_noalloc": (_ST, [_V, _I32, _I32, _I, _V, ct.POINTER(hjcd_solve_opts), _V, _V, _V, _V]),
     "hjcd_fk": (_ST, [_V, _I32, _I64, _V, _I64, _V, _V]),
     "hjcd_sample_seeds": (_ST, [_V, _I32, _I64, _V, _V, _U64, _V, _I64, _V]),
     "hjcd_po_ccd": (_ST, [_V, _I32, _I, _V, _F, _F, _U64, ct.POINTER(hjcd_params), _I64, _V, _V, _V, _V, _I64,
@@ -199,6 +201,14 @@ def hjcd_solve(ctx, robot_id, scene_id, n_targets, targets_pq, opts: hjcd_solve_
                stream=None) -> None:
     _check(ctx, load().hjcd_solve(ctx, int(robot_id), int(scene_id), int(n_targets), ptr(targets_pq),
                                   ct.byref(opts), ptr(out_q), ptr(out_err), ptr(out_count), stream_handle(stream)))
+
+
+def hjcd_solve_noalloc(ctx, robot_id, scene_id, n_targets, targets_pq, opts: hjcd_solve_opts, out_q, out_err,
+                       out_count, stream=None) -> None:
+    """hjcd_solve without allocation (device buffers; scratch in a static device array)."""
+    _check(ctx, load().hjcd_solve_noalloc(ctx, int(robot_id), int(scene_id), int(n_targets), ptr(targets_pq),
+                                          ct.byref(opts), ptr(out_q), ptr(out_err), ptr(out_count),
+                                          stream_handle(stream)))
 
 
 def hjcd_fk(ctx, robot_id, n_cand, theta, ld, out_pq, stream=None) -> None:
