@@ -110,8 +110,9 @@ void hjcd_default_params(hjcd_params* out);
  * body sph_link[s] in 0..n+1 (0 = base, i = the body moved by joint i,
  * n+1 = the flange frame) at sph_xyzr[4s..4s+2] in that body's frame with
  * radius sph_xyzr[4s+3] > 0.  ignore_pairs: (n+2)x(n+2) row-major bytes,
- * nonzero = the body pair is never checked for self-collision; NULL ignores
- * exactly the pairs with |i - j| <= 1.  All arrays are HOST memory.
+ * nonzero = the body pair is never checked for self-collision (either entry
+ * of a pair marks it); NULL ignores exactly the pairs with |i - j| <= 1.
+ * All arrays are HOST memory.
  * Returns the new robot id in *robot_id. */
 hjcd_status hjcd_create_robot(hjcd_ctx* ctx, int n_dof,
                               const float* dh_a, const float* dh_alpha, const float* dh_d,

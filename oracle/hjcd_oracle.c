@@ -81,8 +81,9 @@ orc_robot* orc_robot_new(int n, const double* a, const double* alpha, const doub
     for (int i = 0; i < nb; ++i)
         for (int j = 0; j < nb; ++j) {
             int v;
-            if (ignore) v = ignore[i * nb + j] != 0;
-            else v = abs(i - j) <= 1; /* default: adjacent bodies are never checked */
+            /* either entry of the matrix marks the pair; default: adjacent bodies are never checked */
+            if (ignore) v = ignore[i * nb + j] != 0 || ignore[j * nb + i] != 0;
+            else v = abs(i - j) <= 1;
             R->ignore[i * MAXB + j] = (uint8_t)v;
         }
     return R;

@@ -12,22 +12,25 @@
 
 #include "hjcd_internal.cuh"
 
-namespace hjcd {
-size_t collide_smem_bytes(int n_sph, int n_osph, int n_obox);
-}
-
 using namespace hjcd;
 
 namespace {
 
 constexpr int kMaxSceneFloat4 = 10240;  // obstacle spheres + 2 * boxes staged in shared memory (160 KB)
 
+// Collision tables of a robot in one device buffer: spheres sorted by body
+// (float4, body frame), their bodies, per-body [first, count) ranges, a
+// bounding ("coarse") sphere per body and the list of body pairs checked for
+// self-collision.
 struct RobotRec {
     RobotParams P{};
-    void* dbuf = nullptr;  // float4 spheres | int32 bodies | uint32 pair masks
+    void* dbuf = nullptr;
     float4* sph = nullptr;
     int32_t* body = nullptr;
-    uint32_t* mask = nullptr;
+    int2* range = nullptr;
+    float4* coarse = nullptr;
+    int2* pairs = nullptr;
+    int n_pairs = 0;
 };
 
 struct SceneRec {
@@ -330,33 +333,74 @@ hjcd_status hjcd_create_robot(hjcd_ctx* ctx, int n, const float* dh_a, const flo
         P.fl_p[i] = flange[4 * i + 3];
     }
     const int nb = n + 2;
-    std::vector<float4> sph(n_spheres);
-    std::vector<int32_t> body(n_spheres);
     for (int s = 0; s < n_spheres; ++s) {
         if (sph_link[s] < 0 || sph_link[s] > n + 1) return fail(ctx, HJCD_EINVAL, "sphere %d: body outside [0, n+1]", s);
         if (!(sph_xyzr[4 * s + 3] > 0.0f)) return fail(ctx, HJCD_EINVAL, "sphere %d: radius must be > 0", s);
-        sph[s] = make_float4(sph_xyzr[4 * s], sph_xyzr[4 * s + 1], sph_xyzr[4 * s + 2], sph_xyzr[4 * s + 3]);
-        body[s] = sph_link[s];
     }
-    std::vector<uint32_t> mask(nb, 0u);
-    for (int i = 0; i < nb; ++i)
-        for (int j = 0; j < nb; ++j) {
-            const bool ign = ignore_pairs ? ignore_pairs[i * nb + j] != 0 : std::abs(i - j) <= 1;
-            if (i != j && !ign) mask[i] |= 1u << j;
+    // spheres grouped by body (stable), per-body ranges
+    std::vector<float4> sph;
+    std::vector<int32_t> body;
+    std::vector<int2> range(nb, make_int2(0, 0));
+    for (int b = 0; b < nb; ++b) {
+        range[b].x = (int)sph.size();
+        for (int s = 0; s < n_spheres; ++s)
+            if (sph_link[s] == b) {
+                sph.push_back(make_float4(sph_xyzr[4 * s], sph_xyzr[4 * s + 1], sph_xyzr[4 * s + 2], sph_xyzr[4 * s + 3]));
+                body.push_back(b);
+            }
+        range[b].y = (int)sph.size() - range[b].x;
+    }
+    // Bounding sphere of each body's spheres (centre of their bounding box, radius padded by
+    // 1e-5 m + 1e-6 relative so binary32 rounding of the transforms cannot hide a fine overlap):
+    // a fine sphere overlaps an obstacle only if its body's bounding sphere does.
+    std::vector<float4> coarse(nb, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int b = 0; b < nb; ++b) {
+        if (!range[b].y) continue;
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int i = range[b].x; i < range[b].x + range[b].y; ++i) {
+            const double c[3] = {sph[i].x, sph[i].y, sph[i].z};
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = std::min(lo[k], c[k]);
+                hi[k] = std::max(hi[k], c[k]);
+            }
         }
+        const double m[3] = {0.5 * (lo[0] + hi[0]), 0.5 * (lo[1] + hi[1]), 0.5 * (lo[2] + hi[2])};
+        double r = 0.0;
+        for (int i = range[b].x; i < range[b].x + range[b].y; ++i) {
+            const double dx = sph[i].x - m[0], dy = sph[i].y - m[1], dz = sph[i].z - m[2];
+            r = std::max(r, std::sqrt(dx * dx + dy * dy + dz * dz) + (double)sph[i].w);
+        }
+        coarse[b] = make_float4((float)m[0], (float)m[1], (float)m[2], (float)(r * (1.0 + 1e-6) + 1e-5));
+    }
+    // body pairs checked for self-collision: not ignored, spheres on both
+    std::vector<int2> pairs;
+    for (int i = 0; i < nb; ++i)
+        for (int j = i + 1; j < nb; ++j) {
+            const bool ign = ignore_pairs ? (ignore_pairs[i * nb + j] != 0 || ignore_pairs[j * nb + i] != 0)
+                                          : std::abs(i - j) <= 1;
+            if (!ign && range[i].y && range[j].y) pairs.push_back(make_int2(i, j));
+        }
+    rec.n_pairs = (int)pairs.size();
     hjcd_status st = make_current(ctx);
     if (st) return st;
-    const size_t bytes = align_up(16 * (size_t)std::max(n_spheres, 1)) + align_up(4 * (size_t)std::max(n_spheres, 1)) +
-                         align_up(4 * (size_t)nb);
+    const size_t ns1 = std::max<size_t>(sph.size(), 1), np1 = std::max<size_t>(pairs.size(), 1);
+    const size_t o_body = align_up(16 * ns1), o_range = o_body + align_up(4 * ns1),
+                 o_coarse = o_range + align_up(8 * (size_t)nb), o_pairs = o_coarse + align_up(16 * (size_t)nb),
+                 bytes = o_pairs + align_up(8 * np1);
     HJCD_CUDA(ctx, cudaMalloc(&rec.dbuf, bytes));
-    rec.sph = reinterpret_cast<float4*>(rec.dbuf);
-    rec.body = reinterpret_cast<int32_t*>((char*)rec.dbuf + align_up(16 * (size_t)std::max(n_spheres, 1)));
-    rec.mask = reinterpret_cast<uint32_t*>((char*)rec.body + align_up(4 * (size_t)std::max(n_spheres, 1)));
-    if (n_spheres > 0) {
-        HJCD_CUDA(ctx, cudaMemcpy(rec.sph, sph.data(), 16 * (size_t)n_spheres, cudaMemcpyHostToDevice));
-        HJCD_CUDA(ctx, cudaMemcpy(rec.body, body.data(), 4 * (size_t)n_spheres, cudaMemcpyHostToDevice));
+    char* base = static_cast<char*>(rec.dbuf);
+    rec.sph = reinterpret_cast<float4*>(base);
+    rec.body = reinterpret_cast<int32_t*>(base + o_body);
+    rec.range = reinterpret_cast<int2*>(base + o_range);
+    rec.coarse = reinterpret_cast<float4*>(base + o_coarse);
+    rec.pairs = reinterpret_cast<int2*>(base + o_pairs);
+    if (!sph.empty()) {
+        HJCD_CUDA(ctx, cudaMemcpy(rec.sph, sph.data(), 16 * sph.size(), cudaMemcpyHostToDevice));
+        HJCD_CUDA(ctx, cudaMemcpy(rec.body, body.data(), 4 * body.size(), cudaMemcpyHostToDevice));
     }
-    HJCD_CUDA(ctx, cudaMemcpy(rec.mask, mask.data(), 4 * (size_t)nb, cudaMemcpyHostToDevice));
+    HJCD_CUDA(ctx, cudaMemcpy(rec.range, range.data(), 8 * (size_t)nb, cudaMemcpyHostToDevice));
+    HJCD_CUDA(ctx, cudaMemcpy(rec.coarse, coarse.data(), 16 * (size_t)nb, cudaMemcpyHostToDevice));
+    if (!pairs.empty()) HJCD_CUDA(ctx, cudaMemcpy(rec.pairs, pairs.data(), 8 * pairs.size(), cudaMemcpyHostToDevice));
     ctx->robots.push_back(rec);
     *robot_id = (int32_t)ctx->robots.size() - 1;
     return HJCD_OK;
@@ -570,7 +614,10 @@ hjcd_status hjcd_solve(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_
         CollideArgs cl{};
         cl.rsph = rob->sph;
         cl.rsph_body = rob->body;
-        cl.pair_mask = rob->mask;
+        cl.range = rob->range;
+        cl.coarse = rob->coarse;
+        cl.pairs = rob->pairs;
+        cl.n_pairs = rob->n_pairs;
         cl.scene = sc ? sc->buf : nullptr;
         cl.n_osph = sc ? sc->n_sph : 0;
         cl.n_obox = sc ? sc->n_box : 0;
@@ -816,7 +863,10 @@ hjcd_status hjcd_collide(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int6
     CollideArgs a{};
     a.rsph = rob->sph;
     a.rsph_body = rob->body;
-    a.pair_mask = rob->mask;
+    a.range = rob->range;
+    a.coarse = rob->coarse;
+    a.pairs = rob->pairs;
+    a.n_pairs = rob->n_pairs;
     a.scene = sc ? sc->buf : nullptr;
     a.n_osph = sc ? sc->n_sph : 0;
     a.n_obox = sc ? sc->n_box : 0;
@@ -1060,7 +1110,10 @@ extern "C" hjcd_status hjcd_solve_noalloc(hjcd_ctx* ctx, int32_t robot_id, int32
         CollideArgs cl{};
         cl.rsph = rob->sph;
         cl.rsph_body = rob->body;
-        cl.pair_mask = rob->mask;
+        cl.range = rob->range;
+        cl.coarse = rob->coarse;
+        cl.pairs = rob->pairs;
+        cl.n_pairs = rob->n_pairs;
         cl.scene = sc ? sc->buf : nullptr;
         cl.n_osph = sc ? sc->n_sph : 0;
         cl.n_obox = sc ? sc->n_box : 0;

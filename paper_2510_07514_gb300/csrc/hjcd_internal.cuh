@@ -357,13 +357,17 @@ struct RankArgs {
 };
 
 // Collision tables in device memory: robot spheres grouped by body
-// (float4 x y z r in the body frame), per-body [first, count) ranges and a
-// self-collision bitmask per body (bit b set: pair is checked); scene
-// spheres (float4) followed by boxes (two float4: lo.xyz, hi.xyz).
+// (float4 x y z r in the body frame) with their bodies, per-body
+// [first, count) ranges and bounding spheres, the body pairs checked for
+// self-collision; scene spheres (float4) followed by boxes (two float4:
+// lo.xyz, hi.xyz).
 struct CollideArgs {
-    const float4* rsph;       // [n_sph]
+    const float4* rsph;       // [n_sph], grouped by body
     const int32_t* rsph_body; // [n_sph]
-    const uint32_t* pair_mask;// [n_bodies]: bit j of word i = check pair (i, j)
+    const int2* range;        // [n_bodies]: first sphere, count
+    const float4* coarse;     // [n_bodies]: bounding sphere in the body frame (r = 0: no spheres)
+    const int2* pairs;        // [n_pairs]: body pairs checked for self-collision
+    int32_t n_pairs;
     const float4* scene;      // [n_osph + 2 * n_obox], 16-byte aligned
     int32_t n_osph, n_obox;
     int64_t C, ld;

@@ -1,13 +1,22 @@
 // k_collide.cu -- sphere collision filter (Sec. V-C), one warp per candidate.
 //
-// Each lane owns up to SPL of the robot's link spheres (sphere lane + 32 q).
-// Every lane walks the kinematic chain for the candidate and moves its own
-// spheres into the world frame; the warp publishes them to shared memory for
-// the self-collision pairs.  Obstacles (spheres, then boxes) are staged once
-// per CTA into shared memory by a single bulk asynchronous copy (TMA,
-// cp.async.bulk) completing on an mbarrier, and are read by the whole warp
-// as broadcasts.  The warp votes after every few obstacles and stops at the
-// first overlap -- a candidate is discarded as soon as any pair overlaps.
+// Two levels, as in the paper's coarse-then-fine check: every body carries a
+// bounding sphere of its link spheres, and a body's fine spheres are tested
+// against an obstacle (or another body's spheres) only when the bounding
+// spheres overlap.  The bounding radii are padded beyond binary32 rounding, so
+// the verdict is the brute-force verdict over all fine pairs.
+//
+// Per candidate: every lane walks the kinematic chain and moves its own fine
+// spheres (sphere lane + 32 q of the body-grouped table) and, on lane b, the
+// bounding sphere of body b into the world frame; the warp publishes them to
+// shared memory.  Self pairs: lanes over the checked body pairs for the
+// bounding test; the fine sphere pairs of each overlapping body pair are
+// spread over the warp.  Obstacles: lanes over obstacles (32 at a time) for
+// the bounding test of one body; the overlapping obstacles are compacted into
+// a list and their fine tests (list x the body's spheres) spread over the
+// warp.  The warp stops at the first overlap.  Obstacles (spheres, then boxes)
+// are staged once per CTA into shared memory by one bulk asynchronous copy
+// (TMA, cp.async.bulk) completing on an mbarrier.
 //
 // Overlap: |c1 - c2|^2 < (r1 + r2)^2 for spheres; for a box, the squared
 // distance from the centre to its clamp into the box below r^2.
@@ -68,67 +77,105 @@ __device__ __forceinline__ float4 to_world(const Frame& F, float4 s) {
     return make_float4(w.x, w.y, w.z, s.w);
 }
 
+__device__ __forceinline__ bool sph_sph(float4 a, float4 b) {
+    const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z, rr = a.w + b.w;
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rr * rr;
+}
+
+__device__ __forceinline__ bool sph_box(float4 a, float4 lo, float4 hi) {
+    const float dx = a.x - clampf(a.x, lo.x, hi.x);
+    const float dy = a.y - clampf(a.y, lo.y, hi.y);
+    const float dz = a.z - clampf(a.z, lo.z, hi.z);
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < a.w * a.w;
+}
+
+// shared-memory layout of a CTA
+struct CollideSmem {
+    float4* scene;   // [n_osph + 2 n_obox]
+    uint64_t* bar;
+    int2* range;     // [nb]
+    int2* pairs;     // [n_pairs]
+    float4* wsph;    // per warp: [ns] world fine spheres
+    float4* wco;     // per warp: [nb] world bounding spheres
+    int* list;       // per warp: [32] compacted obstacle / pair indices
+};
+
+struct CollideLayout {
+    uint32_t bar, range, pairs, warp, warp_bytes, total;
+};
+
+__host__ __device__ __forceinline__ CollideLayout collide_smem_layout(int n_obj4, int nb, int n_pairs, int ns) {
+    CollideLayout L;
+    L.bar = 16u * (uint32_t)n_obj4;
+    L.range = L.bar + 16u;
+    L.pairs = L.range + 8u * (uint32_t)nb;
+    L.warp = (L.pairs + 8u * (uint32_t)n_pairs + 15u) / 16u * 16u;
+    L.warp_bytes = 16u * (uint32_t)(ns + nb) + 4u * 32u;
+    L.total = L.warp + kWarpsPerBlock * L.warp_bytes;
+    return L;
+}
+
 template <int SPL>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const RobotParams R, const CollideArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int n_obj4 = A.n_osph + 2 * A.n_obox;
-    const int ns = R.n_sph;
-    float4* scene = reinterpret_cast<float4*>(smem);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 16 * (size_t)n_obj4);
-    float4* wall = reinterpret_cast<float4*>(smem + 16 * (size_t)n_obj4 + 16);
-    int32_t* sbody = reinterpret_cast<int32_t*>(wall + kWarpsPerBlock * ns);
+    const int ns = R.n_sph, n = R.n, nb = R.n + 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4* wsph = wall + warp * ns;
+    const unsigned lt = (1u << lane) - 1u;
+    const CollideLayout L = collide_smem_layout(n_obj4, nb, A.n_pairs, ns);
+    CollideSmem S;
+    S.scene = reinterpret_cast<float4*>(smem);
+    S.bar = reinterpret_cast<uint64_t*>(smem + L.bar);
+    S.range = reinterpret_cast<int2*>(smem + L.range);
+    S.pairs = reinterpret_cast<int2*>(smem + L.pairs);
+    unsigned char* wb = smem + L.warp + warp * L.warp_bytes;
+    S.wsph = reinterpret_cast<float4*>(wb);
+    S.wco = S.wsph + ns;
+    S.list = reinterpret_cast<int*>(S.wco + nb);
 
-    // stage the obstacles with one bulk copy; the sphere-to-body table with plain loads
+    // stage the obstacles with one bulk copy; the small robot tables with plain loads
     const uint32_t bytes = 16u * (uint32_t)n_obj4;
-    if (threadIdx.x == 0) mbar_init(bar, 1);
+    if (threadIdx.x == 0) mbar_init(S.bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
         if (bytes > 0) {
-            mbar_arrive_expect_tx(bar, bytes);
-            bulk_g2s(scene, A.scene, bytes, bar);
+            mbar_arrive_expect_tx(S.bar, bytes);
+            bulk_g2s(S.scene, A.scene, bytes, S.bar);
         } else {
-            mbar_arrive(bar);
+            mbar_arrive(S.bar);
         }
     }
-    for (int i = threadIdx.x; i < ns; i += blockDim.x) sbody[i] = A.rsph_body[i];
-    bool staged = mbar_wait_bounded(bar, 0);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) S.range[i] = A.range[i];
+    for (int i = threadIdx.x; i < A.n_pairs; i += blockDim.x) S.pairs[i] = A.pairs[i];
+    const bool staged = mbar_wait_bounded(S.bar, 0);
     if (__syncthreads_or(!staged)) {
         // give up: flag the error, give the copy one more bounded wait, return
         if (threadIdx.x == 0) {
             atomicExch(A.err_flag, 1);
-            mbar_wait_bounded(bar, 0);
+            mbar_wait_bounded(S.bar, 0);
         }
         return;
     }
 
-    // this lane's spheres (body frame), bodies and self-collision masks
+    // this lane's fine spheres (body frame) and bodies; its bounding sphere (body lane)
     float4 ls[SPL];
     int lb[SPL];
-    uint32_t pm[SPL];
 #pragma unroll
     for (int q = 0; q < SPL; ++q) {
         const int i = lane + 32 * q;
-        if (i < ns) {
-            ls[q] = A.rsph[i];
-            lb[q] = sbody[i];
-            pm[q] = A.pair_mask[lb[q]];
-        } else {
-            ls[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            lb[q] = -1;
-            pm[q] = 0u;
-        }
+        lb[q] = i < ns ? A.rsph_body[i] : -1;
+        ls[q] = i < ns ? A.rsph[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    const float4 lco = lane < nb ? A.coarse[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
 
     unsigned long long tests = 0, btests = 0, ncand = 0;
-    const int n = R.n;
     const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
     for (int64_t c = (int64_t)blockIdx.x * kWarpsPerBlock + warp; c < A.C; c += nwarps) {
-        // world positions of this lane's spheres
+        // world frame: body 0 is the base (identity)
         float4 ws[SPL];
 #pragma unroll
-        for (int q = 0; q < SPL; ++q) ws[q] = ls[q];  // body 0: the base frame is the world frame
+        for (int q = 0; q < SPL; ++q) ws[q] = ls[q];
+        float4 wc = lco;
         Frame F = frame_identity();
 #pragma unroll 1
         for (int j = 0; j < n; ++j) {
@@ -136,92 +183,125 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const RobotPara
 #pragma unroll
             for (int q = 0; q < SPL; ++q)
                 if (lb[q] == j + 1) ws[q] = to_world(F, ls[q]);
+            if (lane == j + 1) wc = to_world(F, lco);
         }
         const Frame E = fk_flange(R, F);
 #pragma unroll
         for (int q = 0; q < SPL; ++q) {
             if (lb[q] == n + 1) ws[q] = to_world(E, ls[q]);
-            if (lb[q] >= 0) wsph[lane + 32 * q] = ws[q];
+            if (lb[q] >= 0) S.wsph[lane + 32 * q] = ws[q];
         }
+        if (lane == n + 1) wc = to_world(E, lco);
+        if (lane < nb) S.wco[lane] = wc;
         __syncwarp();
 
         bool hit = false;
-        unsigned long long my_tests = 0;
-        // self-collision: each unordered pair (i < j) of spheres on bodies not ignored
-        for (int j = 0; j < ns; ++j) {
-            const float4 o = wsph[j];
-            const int bj = sbody[j];
-#pragma unroll
-            for (int q = 0; q < SPL; ++q) {
-                if (lane + 32 * q < j && ((pm[q] >> bj) & 1u)) {
-                    const float dx = ws[q].x - o.x, dy = ws[q].y - o.y, dz = ws[q].z - o.z;
-                    const float rr = ws[q].w + o.w;
-                    hit |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rr * rr;
-                    ++my_tests;
+        unsigned long long t_s = 0, t_b = 0;  // tests of this candidate (uniform over the warp)
+
+        // self-collision: bounding test per checked body pair, fine pairs spread over the warp
+        for (int p0 = 0; p0 < A.n_pairs && !hit; p0 += 32) {
+            const int p = p0 + lane;
+            int2 pr = make_int2(0, 0);
+            bool ch = false;
+            if (p < A.n_pairs) {
+                pr = S.pairs[p];
+                ch = sph_sph(S.wco[pr.x], S.wco[pr.y]);
+            }
+            t_s += (unsigned long long)min(32, A.n_pairs - p0);
+            unsigned m = __ballot_sync(0xffffffffu, ch);
+            while (m) {
+                const int src = __ffs(m) - 1;
+                m &= m - 1u;
+                const int ba = __shfl_sync(0xffffffffu, pr.x, src), bb = __shfl_sync(0xffffffffu, pr.y, src);
+                const int2 ra = S.range[ba], rb = S.range[bb];
+                const int items = ra.y * rb.y;
+                bool h = false;
+                for (int w = lane; w < items; w += 32) {
+                    const int i = w / rb.y;
+                    h |= sph_sph(S.wsph[ra.x + i], S.wsph[rb.x + (w - i * rb.y)]);
+                }
+                t_s += (unsigned long long)items;
+                if (__any_sync(0xffffffffu, h)) {
+                    hit = true;
+                    break;
                 }
             }
         }
-        hit = __any_sync(0xffffffffu, hit);
-        int o_sph = 0, o_box = 0;
-        if (!hit) {
-            for (int o = 0; o < A.n_osph; ++o) {
-                const float4 s = scene[o];
-#pragma unroll
-                for (int q = 0; q < SPL; ++q) {
-                    if (lb[q] >= 0) {
-                        const float dx = ws[q].x - s.x, dy = ws[q].y - s.y, dz = ws[q].z - s.z;
-                        const float rr = ws[q].w + s.w;
-                        hit |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rr * rr;
-                    }
+
+        // obstacle spheres: 32 obstacles at a time, one body at a time
+        for (int o0 = 0; o0 < A.n_osph && !hit; o0 += 32) {
+            const int o = o0 + lane;
+            const bool valid = o < A.n_osph;
+            const float4 s = valid ? S.scene[o] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int nvalid = min(32, A.n_osph - o0);
+            for (int b = 0; b < nb && !hit; ++b) {
+                const int2 rg = S.range[b];
+                if (rg.y == 0) continue;
+                const bool ch = valid && sph_sph(S.wco[b], s);
+                t_s += (unsigned long long)nvalid;
+                const unsigned m = __ballot_sync(0xffffffffu, ch);
+                if (!m) continue;
+                if (ch) S.list[__popc(m & lt)] = o;
+                __syncwarp();
+                const int items = __popc(m) * rg.y;
+                bool h = false;
+                for (int w = lane; w < items; w += 32) {
+                    const int k = w / rg.y;
+                    h |= sph_sph(S.wsph[rg.x + (w - k * rg.y)], S.scene[S.list[k]]);
                 }
-                ++o_sph;
-                if ((o & 7) == 7 && __any_sync(0xffffffffu, hit)) break;
+                t_s += (unsigned long long)items;
+                hit = __any_sync(0xffffffffu, h);
+                __syncwarp();
             }
-            hit = __any_sync(0xffffffffu, hit);
         }
-        if (!hit) {
-            const float4* box = scene + A.n_osph;
-            for (int o = 0; o < A.n_obox; ++o) {
-                const float4 lo = box[2 * o], hi = box[2 * o + 1];
-#pragma unroll
-                for (int q = 0; q < SPL; ++q) {
-                    if (lb[q] >= 0) {
-                        const float dx = ws[q].x - clampf(ws[q].x, lo.x, hi.x);
-                        const float dy = ws[q].y - clampf(ws[q].y, lo.y, hi.y);
-                        const float dz = ws[q].z - clampf(ws[q].z, lo.z, hi.z);
-                        hit |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < ws[q].w * ws[q].w;
-                    }
+
+        // obstacle boxes
+        const float4* box = S.scene + A.n_osph;
+        for (int o0 = 0; o0 < A.n_obox && !hit; o0 += 32) {
+            const int o = o0 + lane;
+            const bool valid = o < A.n_obox;
+            const float4 lo = valid ? box[2 * o] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 hi = valid ? box[2 * o + 1] : lo;
+            const int nvalid = min(32, A.n_obox - o0);
+            for (int b = 0; b < nb && !hit; ++b) {
+                const int2 rg = S.range[b];
+                if (rg.y == 0) continue;
+                const bool ch = valid && sph_box(S.wco[b], lo, hi);
+                t_b += (unsigned long long)nvalid;
+                const unsigned m = __ballot_sync(0xffffffffu, ch);
+                if (!m) continue;
+                if (ch) S.list[__popc(m & lt)] = o;
+                __syncwarp();
+                const int items = __popc(m) * rg.y;
+                bool h = false;
+                for (int w = lane; w < items; w += 32) {
+                    const int k = w / rg.y, bo = S.list[k];
+                    h |= sph_box(S.wsph[rg.x + (w - k * rg.y)], box[2 * bo], box[2 * bo + 1]);
                 }
-                ++o_box;
-                if ((o & 7) == 7 && __any_sync(0xffffffffu, hit)) break;
+                t_b += (unsigned long long)items;
+                hit = __any_sync(0xffffffffu, h);
+                __syncwarp();
             }
-            hit = __any_sync(0xffffffffu, hit);
         }
+
         if (lane == 0) {
             A.hit[c] = hit ? 1 : 0;
-            tests += (unsigned long long)o_sph * (unsigned long long)ns;
-            btests += (unsigned long long)o_box * (unsigned long long)ns;
+            tests += t_s;
+            btests += t_b;
             ++ncand;
         }
-        tests += my_tests;
         __syncwarp();
     }
-    if (A.cnt) {
-        tests = warp_sum(tests);
-        btests = warp_sum(btests);
-        ncand = warp_sum(ncand);
-        if (lane == 0) {
-            atomicAdd(&A.cnt->v[3], tests);
-            atomicAdd(&A.cnt->v[6], btests);
-            atomicAdd(&A.cnt->v[4], ncand);
-        }
+    if (A.cnt && lane == 0) {
+        atomicAdd(&A.cnt->v[3], tests);
+        atomicAdd(&A.cnt->v[6], btests);
+        atomicAdd(&A.cnt->v[4], ncand);
     }
 }
 
 template <int SPL>
 void launch_collide_t(const RobotParams& R, const CollideArgs& A, cudaStream_t st) {
-    const size_t smem = 16 * (size_t)(A.n_osph + 2 * A.n_obox) + 16 + (size_t)kWarpsPerBlock * R.n_sph * 16 +
-                        (size_t)R.n_sph * 4;
+    const size_t smem = collide_smem_layout(A.n_osph + 2 * A.n_obox, R.n + 2, A.n_pairs, R.n_sph).total;
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_collide<SPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -232,10 +312,6 @@ void launch_collide_t(const RobotParams& R, const CollideArgs& A, cudaStream_t s
 }
 
 }  // namespace
-
-size_t collide_smem_bytes(int n_sph, int n_osph, int n_obox) {
-    return 16 * (size_t)(n_osph + 2 * n_obox) + 16 + (size_t)kWarpsPerBlock * n_sph * 16 + (size_t)n_sph * 4;
-}
 
 void launch_collide(const RobotParams& R, const CollideArgs& A, cudaStream_t st) {
     if (A.C <= 0 || R.n_sph <= 0) return;
