@@ -150,7 +150,7 @@ class ClockSampler:
 # arithmetic for an n-joint chain; see the design notes for the derivation
 
 def flops_ccd_iter(n):
-    return 234 * n + 340
+    return 314 * n + 340
 
 
 def flops_lm_iter(n):

@@ -75,7 +75,7 @@ typedef struct hjcd_params {
     int32_t lm_A;           /* line-search depth [A], 0..31 */
     float lm_sigma;         /* std of the PJ-IK perturbation, rad [Sigma] */
     float lm_gn_reg;        /* regulariser of the minimum-norm Gauss-Newton step (Eq. dogleg) */
-    float cd_tie;           /* greedy joint choice: a later joint wins only if better by more than this (m / rad) */
+    float cd_tie;           /* greedy joint choice: a later joint wins only if its score is lower by this fraction */
 } hjcd_params;
 
 typedef struct hjcd_solve_opts {
@@ -197,9 +197,12 @@ hjcd_status hjcd_sample_seeds(hjcd_ctx* ctx, int32_t robot_id, int64_t n_cand, c
  * theta_out may equal theta_in.  score/perr/oerr/iters (each may be NULL)
  * receive the final score, |e_p|, |omega| and iterations executed.
  * Trace (one iteration, n_iters == 1; any pointer may be NULL):
- * dp/rp/dq/rq/th_hat are [n][ld]: per-joint position step and resulting
- * |e_p|, orientation step and resulting |omega|, the proposed theta_hat;
- * jp/jo the greedy joints, accepted the acceptance flag. */
+ * dp/rp/op, dq/pq/rq and th_hat are [n][ld]: per joint the position step
+ * and the |e_p| and |omega| it leaves, the orientation step and the |e_p| and
+ * |omega| it leaves, and the proposed theta_hat; jp/jo the greedy joints
+ * (argmin of the score (|e_p|/eps_pos)^2 + (|omega|/eps_ori)^2 over the
+ * trials of each kind, a later joint winning only when lower by more than the
+ * fraction cd_tie), accepted the acceptance flag. */
 typedef struct hjcd_ccd_trace {
     float* dp;
     float* rp;
@@ -209,6 +212,8 @@ typedef struct hjcd_ccd_trace {
     int32_t* jo;
     uint8_t* accepted;
     float* th_hat;
+    float* op;
+    float* pq;
 } hjcd_ccd_trace;
 hjcd_status hjcd_po_ccd(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const float* targets_pq,
                         float eps_pos, float eps_ori, uint64_t seed, const hjcd_params* params,

@@ -89,7 +89,7 @@ _SIGS = {
     "orc_fk_batch": (None, [_P, ct.c_int64, _D, _D]),
     "orc_sample_seeds": (None, [_P, ct.POINTER(Params), ct.c_int64, _I32, _I32, _D]),
     "orc_ccd_iteration_batch": (None, [_P, ct.POINTER(Params), _D, ct.c_int64, _I32, _I32, ct.c_int,
-                                       _D, _D, _D, _D, _D, _D, _I32, _I32, _U8, _D, _D, _D, _D, _U8]),
+                                       _D, _D, _D, _D, _D, _D, _D, _D, _I32, _I32, _U8, _D, _D, _D, _D, _U8]),
     "orc_po_ccd_batch": (None, [_P, ct.POINTER(Params), _D, ct.c_int64, _I32, _I32, _D, _D, _D, _D, _I32]),
     "orc_dup_layout": (ct.c_int64, [ct.c_int64, ct.c_int32, _I64, _I64]),
     "orc_topk_dup": (None, [_P, ct.POINTER(Params), ct.c_int64, _I64, _D, _D, _I64, _D, _I32]),
@@ -274,17 +274,21 @@ def sample_seeds(rob: Robot, P: Params, tgt, cand) -> np.ndarray:
 
 
 def ccd_iteration(rob: Robot, P: Params, targets, tgt, cand, k: int, theta) -> dict:
-    """One PO-CCD iteration per candidate, with its trace."""
+    """One PO-CCD iteration per candidate, with its trace: per joint the position
+    step dp and the position / orientation error it leaves (rp, op), the
+    orientation step dq and the errors it leaves (pq, rq)."""
     t, c = _idx(tgt, cand)
     C, n = len(t), rob.n
     tg = _f64(targets, (-1, 7))
     th = _f64(theta, (C, n))
-    o = dict(theta=np.zeros((C, n)), dp=np.zeros((C, n)), rp=np.zeros((C, n)), dq=np.zeros((C, n)),
-             rq=np.zeros((C, n)), jp=np.zeros(C, np.int32), jo=np.zeros(C, np.int32),
+    o = dict(theta=np.zeros((C, n)), dp=np.zeros((C, n)), rp=np.zeros((C, n)), op=np.zeros((C, n)),
+             dq=np.zeros((C, n)), pq=np.zeros((C, n)), rq=np.zeros((C, n)),
+             jp=np.zeros(C, np.int32), jo=np.zeros(C, np.int32),
              accepted=np.zeros(C, np.uint8), theta_hat=np.zeros((C, n)), margin_p=np.zeros(C),
              margin_o=np.zeros(C), margin_acc=np.zeros(C), converged=np.zeros(C, np.uint8))
     lib().orc_ccd_iteration_batch(rob.ptr, ct.byref(P), _d(tg), C, _i32(t), _i32(c), int(k), _d(th),
-                                  _d(o["theta"]), _d(o["dp"]), _d(o["rp"]), _d(o["dq"]), _d(o["rq"]),
+                                  _d(o["theta"]), _d(o["dp"]), _d(o["rp"]), _d(o["op"]), _d(o["dq"]), _d(o["pq"]),
+                                  _d(o["rq"]),
                                   _i32(o["jp"]), _i32(o["jo"]), _u8(o["accepted"]), _d(o["theta_hat"]),
                                   _d(o["margin_p"]), _d(o["margin_o"]), _d(o["margin_acc"]),
                                   _u8(o["converged"]))

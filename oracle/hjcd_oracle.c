@@ -504,9 +504,11 @@ static double ccd_position_delta(const double pee[3], const double pt[3], const 
 
 /* One iteration k of Alg. 3 for one candidate (theta updated in place).
  * Returns 1 when the coarse tolerance of line 14 holds after the update. */
+static double score_of(const orc_params* P, double ep, double eo);
+
 static int ccd_iteration(const orc_robot* R, const orc_params* P, const double tgt[7], uint32_t t,
-                         uint32_t c, int k, double* th, double* dp, double* rp, double* dq,
-                         double* rq, int32_t* jp_out, int32_t* jo_out, uint8_t* acc_out,
+                         uint32_t c, int k, double* th, double* dp, double* ep_p, double* eo_p, double* dq,
+                         double* ep_q, double* eo_q, int32_t* jp_out, int32_t* jo_out, uint8_t* acc_out,
                          double* th_hat_out, double* mp_out, double* mo_out, double* ma_out) {
     const int n = R->n;
     double F[MAXB * 16], pee[3], Rm[9], qe[4], qt[4], pt[3] = {tgt[0], tgt[1], tgt[2]};
@@ -528,7 +530,9 @@ static int ccd_iteration(const orc_robot* R, const orc_params* P, const double t
         for (int i = 0; i < 3; ++i) ahat[i] = qerr[1 + i] / sh;
     double delta_k = P->cd_delta0 * pow(P->cd_rho, (double)k);
 
-    double Dp[ORC_MAXN], Rp[ORC_MAXN], Dq[ORC_MAXN], Rq[ORC_MAXN], trial[ORC_MAXN], tmp;
+    /* lines 6-8: per joint, a position update and an orientation update, and the
+     * task residual r (position and orientation error) after each of them */
+    double Dp[ORC_MAXN], Pp[ORC_MAXN], Op[ORC_MAXN], Dq[ORC_MAXN], Pq[ORC_MAXN], Oq[ORC_MAXN], trial[ORC_MAXN];
     for (int j = 0; j < n; ++j) {
         double pj[3], rj[3];
         frame_pos(F + 16 * (j + 1), pj);
@@ -539,7 +543,7 @@ static int ccd_iteration(const orc_robot* R, const orc_params* P, const double t
         Dp[j] = clampd(th[j] + dpos, R->lo[j], R->hi[j]) - th[j];
         memcpy(trial, th, (size_t)n * sizeof(double));
         trial[j] += Dp[j];
-        pos_ori_err(R, trial, tgt, &Rp[j], &tmp);
+        pos_ori_err(R, trial, tgt, &Pp[j], &Op[j]);
 
         /* orientation update (Eq. ori_update), sgn(0) = 0 */
         double s = dot3(ahat, rj);
@@ -548,23 +552,34 @@ static int ccd_iteration(const orc_robot* R, const orc_params* P, const double t
         Dq[j] = clampd(th[j] + dori, R->lo[j], R->hi[j]) - th[j];
         memcpy(trial, th, (size_t)n * sizeof(double));
         trial[j] += Dq[j];
-        pos_ori_err(R, trial, tgt, &tmp, &Rq[j]);
+        pos_ori_err(R, trial, tgt, &Pq[j], &Oq[j]);
     }
 
-    /* Alg. 3 line 9: greedy choice of the best position and orientation update
-     * (smallest resulting residual).  Reading of "argmin" for ties: joints are
-     * scanned from the base and a later joint replaces the current choice only
-     * when its residual is lower by more than cd_tie, so updates that are equal
-     * up to rounding (e.g. parallel joint axes) go to the lower joint index.
-     * The margins record how close each of these comparisons came to flipping. */
+    /* Alg. 3 line 9: greedy choice of the best position update and the best
+     * orientation update.  Reading: each trial is judged by the task residual it
+     * leaves (line 7 computes the full r), through its scalar form, the score
+     * (|e_p|/eps_pos)^2 + (|omega|/eps_ori)^2 used for every ranking.  Ties: joints
+     * are scanned from the base and a later joint replaces the current choice
+     * only when its score is lower by more than the relative tolerance cd_tie,
+     * so updates equal up to rounding (joints sharing axis and origin) go to the
+     * lower joint index.  The margins record, relative to the score, how close
+     * each of these comparisons came to flipping. */
     int jp = 0, jo = 0;
     double gp = INFINITY, go = INFINITY;
+    double sp_best = score_of(P, Pp[0], Op[0]), so_best = score_of(P, Pq[0], Oq[0]);
     for (int j = 1; j < n; ++j) {
-        double mp = Rp[j] - (Rp[jp] - P->cd_tie), mo = Rq[j] - (Rq[jo] - P->cd_tie);
-        gp = fmin(gp, fabs(mp));
-        go = fmin(go, fabs(mo));
-        if (mp < 0.0) jp = j;
-        if (mo < 0.0) jo = j;
+        double sp = score_of(P, Pp[j], Op[j]), so = score_of(P, Pq[j], Oq[j]);
+        double mp = sp - sp_best * (1.0 - P->cd_tie), mo = so - so_best * (1.0 - P->cd_tie);
+        gp = fmin(gp, fabs(mp) / fmax(sp_best, 1e-300));
+        go = fmin(go, fabs(mo) / fmax(so_best, 1e-300));
+        if (mp < 0.0) {
+            jp = j;
+            sp_best = sp;
+        }
+        if (mo < 0.0) {
+            jo = j;
+            so_best = so;
+        }
     }
 
     /* Alg. 3 line 10: apply both; on the same joint keep the larger step */
@@ -587,9 +602,11 @@ static int ccd_iteration(const orc_robot* R, const orc_params* P, const double t
     int acc = (mA > 0.0) || (mB > 0.0);
 
     if (dp) memcpy(dp, Dp, (size_t)n * sizeof(double));
-    if (rp) memcpy(rp, Rp, (size_t)n * sizeof(double));
+    if (ep_p) memcpy(ep_p, Pp, (size_t)n * sizeof(double));
+    if (eo_p) memcpy(eo_p, Op, (size_t)n * sizeof(double));
     if (dq) memcpy(dq, Dq, (size_t)n * sizeof(double));
-    if (rq) memcpy(rq, Rq, (size_t)n * sizeof(double));
+    if (ep_q) memcpy(ep_q, Pq, (size_t)n * sizeof(double));
+    if (eo_q) memcpy(eo_q, Oq, (size_t)n * sizeof(double));
     if (jp_out) *jp_out = jp;
     if (jo_out) *jo_out = jo;
     if (acc_out) *acc_out = (uint8_t)acc;
@@ -616,7 +633,7 @@ static int ccd_iteration(const orc_robot* R, const orc_params* P, const double t
 void orc_ccd_iteration_batch(const orc_robot* R, const orc_params* P, const double* targets,
                              int64_t C, const int32_t* tgt, const int32_t* cand, int k,
                              const double* th_in, double* th_out,
-                             double* dp, double* rp, double* dq, double* rq,
+                             double* dp, double* ep_p, double* eo_p, double* dq, double* ep_q, double* eo_q,
                              int32_t* jp, int32_t* jo, uint8_t* accepted, double* th_hat,
                              double* margin_p, double* margin_o, double* margin_acc,
                              uint8_t* converged) {
@@ -626,8 +643,8 @@ void orc_ccd_iteration_batch(const orc_robot* R, const orc_params* P, const doub
         double th[ORC_MAXN];
         memcpy(th, th_in + c * n, (size_t)n * sizeof(double));
         int conv = ccd_iteration(R, P, targets + 7 * (int64_t)tgt[c], (uint32_t)tgt[c], (uint32_t)cand[c], k, th,
-                                 dp ? dp + c * n : NULL, rp ? rp + c * n : NULL,
-                                 dq ? dq + c * n : NULL, rq ? rq + c * n : NULL,
+                                 dp ? dp + c * n : NULL, ep_p ? ep_p + c * n : NULL, eo_p ? eo_p + c * n : NULL,
+                                 dq ? dq + c * n : NULL, ep_q ? ep_q + c * n : NULL, eo_q ? eo_q + c * n : NULL,
                                  jp ? jp + c : NULL, jo ? jo + c : NULL,
                                  accepted ? accepted + c : NULL, th_hat ? th_hat + c * n : NULL,
                                  margin_p ? margin_p + c : NULL, margin_o ? margin_o + c : NULL,
@@ -654,8 +671,8 @@ void orc_po_ccd_batch(const orc_robot* R, const orc_params* P, const double* tar
         sample_seed(R, P, (uint32_t)tgt[c], (uint32_t)cand[c], th);
         int it = P->cd_max_iters;
         for (int k = 0; k < P->cd_max_iters; ++k) {
-            if (ccd_iteration(R, P, T, (uint32_t)tgt[c], (uint32_t)cand[c], k, th, NULL, NULL, NULL,
-                              NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL)) {
+            if (ccd_iteration(R, P, T, (uint32_t)tgt[c], (uint32_t)cand[c], k, th, NULL, NULL, NULL, NULL,
+                              NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL)) {
                 it = k + 1;
                 break;
             }

@@ -41,7 +41,7 @@ typedef struct {
     double lm_lambda, lm_trust_R, lm_beta;
     int32_t lm_A;
     double lm_sigma, lm_gn_reg;
-    double cd_tie;                      /* tie tolerance of the greedy joint choice */
+    double cd_tie;                      /* relative tie tolerance of the greedy joint choice */
     uint32_t key[2];                    /* Philox key = request seed (lo, hi) */
 } orc_params;
 
@@ -78,7 +78,7 @@ void orc_sample_seeds(const orc_robot* R, const orc_params* P, int64_t C,
 void orc_ccd_iteration_batch(const orc_robot* R, const orc_params* P, const double* targets,
                              int64_t C, const int32_t* tgt, const int32_t* cand, int k,
                              const double* th_in, double* th_out,
-                             double* dp, double* rp, double* dq, double* rq,
+                             double* dp, double* ep_p, double* eo_p, double* dq, double* ep_q, double* eo_q,
                              int32_t* jp, int32_t* jo, uint8_t* accepted, double* th_hat,
                              double* margin_p, double* margin_o, double* margin_acc,
                              uint8_t* converged);

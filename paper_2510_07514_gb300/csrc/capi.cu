@@ -178,7 +178,7 @@ hjcd_status check_params(hjcd_ctx* ctx, const hjcd_params& P) {
     if (!(P.cd_sigma >= 0.0f) || !(P.dup_sigma >= 0.0f) || !(P.lm_sigma >= 0.0f))
         return fail(ctx, HJCD_EINVAL, "perturbation scales must be >= 0");
     if (!(P.proj_eps >= 0.0f)) return fail(ctx, HJCD_EINVAL, "proj_eps must be >= 0");
-    if (!(P.cd_tie >= 0.0f)) return fail(ctx, HJCD_EINVAL, "cd_tie must be >= 0");
+    if (!(P.cd_tie >= 0.0f && P.cd_tie < 1.0f)) return fail(ctx, HJCD_EINVAL, "cd_tie must be in [0, 1)");
     return HJCD_OK;
 }
 
@@ -220,8 +220,8 @@ void hjcd_default_params(hjcd_params* o) {
     o->cd_gamma_ori = 1e-3f;
     o->cd_sigma = 0.05f;
     o->cd_delta0 = 0.5f;
-    o->cd_rho = 0.9f;
-    o->proj_eps = 1e-6f;
+    o->cd_rho = 0.97f;
+    o->proj_eps = 1e-4f;
     o->dup_ratio = 4;
     o->dup_sigma = 0.02f;
     o->lm_max_iters = 20;

@@ -3,10 +3,10 @@
 //
 // Per iteration one forward-kinematics pass gives every joint's origin and
 // axis.  The 2n trial updates are evaluated in O(1) each: rotating joint j by
-// d moves the end effector about the axis (Rodrigues), so the position trial
-// residual follows from the projected vectors of Eq. vec_proj, and the
-// orientation trial residual from composing the error quaternion with the
-// joint rotation.  The proposed theta_hat changes at most two joints; its
+// d moves the end effector about the axis (Rodrigues) and composes the error
+// quaternion with the joint rotation, so both parts of each trial's task
+// residual follow from the projected vectors of Eq. vec_proj and one half-angle
+// sine/cosine.  The proposed theta_hat changes at most two joints; its
 // residual is the composition of the two joint rotations applied to the
 // current end-effector pose (the more distal joint first), so acceptance
 // needs no second kinematics pass.
@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(kCcdThreads, 4) k_ccd(const RobotParams R, con
     const int n = R.n;
     const Col col{sm + threadIdx.x, n};
     const float pe2 = P.proj_eps * P.proj_eps;
+    const float one_m_tie = 1.0f - P.cd_tie;
     unsigned long long n_it = 0, n_cand = 0;
 
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < A.C;
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(kCcdThreads, 4) k_ccd(const RobotParams R, con
         }
 
         float delta_k = P.cd_delta0 * powf(P.cd_rho, (float)A.k0);
+        const float inv_p2 = 1.0f / (T.eps_pos * T.eps_pos), inv_o2 = 1.0f / (T.eps_ori * T.eps_ori);
         int iters = A.n_iters;
         float ep2 = 0.0f, eo = 0.0f;
         const bool valid = T.eps_pos > 0.0f;
@@ -100,9 +102,10 @@ __global__ void __launch_bounds__(kCcdThreads, 4) k_ccd(const RobotParams R, con
             const int k = A.k0 + kk;
             const float ep0 = sqrtf(ep2);
 
-            // lines 6-9: one position and one orientation proposal per joint and the
-            // greedy choice; a later joint replaces the choice only when its trial
-            // residual is lower by more than cd_tie
+            // lines 6-9: one position and one orientation proposal per joint, the
+            // task residual each leaves, and the greedy choice by its score
+            // (|e_p|/eps_pos)^2 + (|omega|/eps_ori)^2; a later joint replaces the
+            // choice only when its score is lower by more than the fraction cd_tie
             float best_p = 0.0f, dP = 0.0f, best_o = 0.0f, dO = 0.0f;
             int jp = 0, jo = 0;
             V3 Pp = v3(0.f, 0.f, 0.f), Zp = Pp, Po = Pp, Zo = Pp;
@@ -121,36 +124,46 @@ __global__ void __launch_bounds__(kCcdThreads, 4) k_ccd(const RobotParams R, con
                 const float nu2 = dot(u, u), nv2 = dot(v, v);
                 const float nup2 = dot(up, up), nvp2 = dot(vp, vp);
                 const V3 zxu = cross(z, up);
+                // rotating joint j by x: the end effector moves to pj + uz z + cos x up + sin x (z x up),
+                // the error quaternion becomes qerr [cos(x/2), -sin(x/2) z]
+                const V3 r0 = fma3(vz - uz, z, vp);
+                const float az = dot(qerr.v, z);
+                const V3 qz = fma3(qerr.w, z, cross(qerr.v, z));
+
                 // Eq. theta_proj, signed about the axis: atan2(z.(up x vp), up.vp) = atan2(zxu.vp, up.vp)
                 const float cs = dot(up, vp), sn = dot(zxu, vp);
                 const bool deg = nu2 < 1e-24f || nv2 < 1e-24f || nup2 <= pe2 * nu2 || nvp2 <= pe2 * nv2;
                 float d = deg ? 0.0f : atan2f(sn, cs);
                 d = clampf(thj + d, lo, hi) - thj;
-                float sd, cd;
-                __sincosf(d, &sd, &cd);
-                // target minus the end effector rotated about joint j by d
-                const V3 r = fma3(vz - uz, z, fma3(-sd, zxu, fma3(-cd, up, vp)));
-                const float rp = sqrtf(dot(r, r));
-                if (j == 0 || rp < best_p - P.cd_tie) {
-                    best_p = rp;
+                float sh, ch;
+                __sincosf(0.5f * d, &sh, &ch);
+                V3 r = fma3(-2.0f * sh * ch, zxu, fma3(-fmaf(-2.0f * sh, sh, 1.0f), up, r0));
+                const float rp2 = dot(r, r);
+                float w2 = fmaf(qerr.w, ch, sh * az);
+                V3 v2 = fma3(ch, qerr.v, (-sh) * qz);
+                const float op = quat_angle(w2, dot(v2, v2));
+                const float sp = fmaf(rp2, inv_p2, op * op * inv_o2);
+                if (j == 0 || sp < best_p * one_m_tie) {
+                    best_p = sp;
                     jp = j;
                     dP = d;
                     Pp = pj;
                     Zp = z;
                 }
-                // Eq. ori_update: delta(k) sgn(a.z) phi; the error quaternion composed with
-                // the inverse joint rotation [cos(d/2), -sin(d/2) z]
-                const float az = dot(qerr.v, z);
+
+                // Eq. ori_update: delta(k) sgn(a.z) phi
                 const float sg = (az > 0.0f) ? 1.0f : ((az < 0.0f) ? -1.0f : 0.0f);
                 float dq = delta_k * sg * phi;
                 dq = clampf(thj + dq, lo, hi) - thj;
-                float sh, ch;
                 __sincosf(0.5f * dq, &sh, &ch);
-                const float w2 = fmaf(qerr.w, ch, sh * az);
-                const V3 v2 = fma3(ch, qerr.v, (-sh) * fma3(qerr.w, z, cross(qerr.v, z)));
+                r = fma3(-2.0f * sh * ch, zxu, fma3(-fmaf(-2.0f * sh, sh, 1.0f), up, r0));
+                const float pq2 = dot(r, r);
+                w2 = fmaf(qerr.w, ch, sh * az);
+                v2 = fma3(ch, qerr.v, (-sh) * qz);
                 const float rq = quat_angle(w2, dot(v2, v2));
-                if (j == 0 || rq < best_o - P.cd_tie) {
-                    best_o = rq;
+                const float so = fmaf(pq2, inv_p2, rq * rq * inv_o2);
+                if (j == 0 || so < best_o * one_m_tie) {
+                    best_o = so;
                     jo = j;
                     dO = dq;
                     Po = pj;
@@ -158,8 +171,10 @@ __global__ void __launch_bounds__(kCcdThreads, 4) k_ccd(const RobotParams R, con
                 }
                 if (TRACE && kk == 0) {
                     if (A.tr.dp) A.tr.dp[j * A.ld + c] = d;
-                    if (A.tr.rp) A.tr.rp[j * A.ld + c] = rp;
+                    if (A.tr.rp) A.tr.rp[j * A.ld + c] = sqrtf(rp2);
+                    if (A.tr.op) A.tr.op[j * A.ld + c] = op;
                     if (A.tr.dq) A.tr.dq[j * A.ld + c] = dq;
+                    if (A.tr.pq) A.tr.pq[j * A.ld + c] = sqrtf(pq2);
                     if (A.tr.rq) A.tr.rq[j * A.ld + c] = rq;
                 }
             }

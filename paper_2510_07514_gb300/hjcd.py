@@ -61,7 +61,8 @@ class hjcd_solve_opts(ct.Structure):
 
 
 class hjcd_ccd_trace(ct.Structure):
-    _fields_ = [(k, ct.c_void_p) for k in ("dp", "rp", "dq", "rq", "jp", "jo", "accepted", "th_hat")]
+    _fields_ = [(k, ct.c_void_p) for k in ("dp", "rp", "dq", "rq", "jp", "jo", "accepted", "th_hat",
+                                                   "op", "pq")]
 
 
 class hjcd_lm_trace(ct.Structure):

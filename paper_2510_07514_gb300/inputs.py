@@ -44,9 +44,9 @@ DEFAULT_PARAMS = dict(
     cd_gamma_ori=1e-3,        # gamma along orientation (rad)
     cd_sigma=0.05,            # Sigma = sigma^2 I of the rejection perturbation (rad)
     cd_delta0=0.5,            # delta(k) = delta0 * rho^k  (Eq. ori_update)
-    cd_rho=0.9,
-    proj_eps=1e-6,            # projected-vector length (relative) below which Eq. theta_proj gives 0
-    cd_tie=1e-4,              # greedy choice: a later joint wins only if better by more than this (m / rad)
+    cd_rho=0.97,
+    proj_eps=1e-4,            # projected-vector length (relative) below which Eq. theta_proj gives 0
+    cd_tie=1e-4,              # greedy choice: a later joint wins only if its score is lower by this fraction
     # Top-K and duplication (Alg. 2 lines 2-7)
     dup_ratio=4,              # K = max(1, floor(B / dup_ratio))
     dup_sigma=0.02,           # Sigma of the duplication perturbation (rad)

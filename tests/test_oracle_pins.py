@@ -272,21 +272,36 @@ def test_ccd_orientation_step_closed_form():
 
 
 def test_ccd_greedy_ties_go_to_the_lower_joint():
-    """A planar chain has parallel joint axes: every joint's orientation
-    update is the same rotation, so the orientation choice is an exact tie
-    that must go to joint 0; position choices are ordinary argmins."""
-    rob = orc.Robot(inputs.planar([0.5, 0.4, 0.3, 0.2]))
+    """Planar chain with a zero-length link between joints 1 and 2: the two
+    joints share axis and origin, so their position updates and their
+    orientation updates are the same rotation and leave the same residual.
+    That exact tie must go to joint 1, never to joint 2.  Parallel axes also
+    make every orientation update leave the same orientation error.  Limits
+    too wide to bind keep the clamp from telling the two joints apart."""
+    chain = inputs.planar([0.5, 0.0, 0.4, 0.3])
+    chain.lo, chain.hi = np.full(4, -10.0), np.full(4, 10.0)
+    rob = orc.Robot(chain)
     P = orc.make_params(seed=8)
     rng = np.random.default_rng(7)
     C = 64
     tg = _targets(rob, rng, C)
     th = rng.uniform(-1.0, 1.0, (C, 4))
     tr = orc.ccd_iteration(rob, P, tg, np.arange(C), np.zeros(C), 0, th)
+    picked_1 = 0
     for c in range(C):
         assert np.ptp(tr["rq"][c]) < 1e-12
-        assert tr["jo"][c] == 0
+        for key in ("rp", "op", "pq", "rq"):
+            assert tr[key][c, 1] == pytest.approx(tr[key][c, 2], abs=1e-12)
+        assert tr["jp"][c] != 2 and tr["jo"][c] != 2
+        picked_1 += int(tr["jp"][c] == 1) + int(tr["jo"][c] == 1)
+        sp = _score(P, tr["rp"][c], tr["op"][c])
         if tr["margin_p"][c] > 1e-9:
-            assert tr["jp"][c] == int(np.argmin(tr["rp"][c]))
+            assert sp[tr["jp"][c]] <= sp.min() * (1 + 1e-9)
+    assert picked_1 > 0
+
+
+def _score(P, ep, eo):
+    return (np.asarray(ep) / P.eps_pos) ** 2 + (np.asarray(eo) / P.eps_ori) ** 2
 
 
 def _normal_stream(P, cand, tgt, phase, it, n):
@@ -309,11 +324,25 @@ def test_ccd_selection_acceptance_and_perturbation(panda):
     tr = orc.ccd_iteration(panda, P, tg, tgt_idx, cand, k, th)
     n_acc = 0
     for c in range(C):
+        # Alg. 3 line 9: greedy argmin of the residual score each trial leaves
+        sp = _score(P, tr["rp"][c], tr["op"][c])
+        so = _score(P, tr["pq"][c], tr["rq"][c])
         if tr["margin_p"][c] > P.cd_tie:
-            assert tr["jp"][c] == int(np.argmin(tr["rp"][c]))
+            assert tr["jp"][c] == int(np.argmin(sp))
         if tr["margin_o"][c] > P.cd_tie:
-            assert tr["jo"][c] == int(np.argmin(tr["rq"][c]))
+            assert tr["jo"][c] == int(np.argmin(so))
         jp, jo = tr["jp"][c], tr["jo"][c]
+        for j in range(7):      # the trial errors are those of the stepped configuration
+            t1 = th[c].copy()
+            t1[j] += tr["dp"][c, j]
+            e = orc.residual(panda, t1, tg[c])
+            assert tr["rp"][c, j] == pytest.approx(np.linalg.norm(e[:3]), abs=1e-12)
+            assert tr["op"][c, j] == pytest.approx(np.linalg.norm(e[3:]), abs=1e-12)
+            t1 = th[c].copy()
+            t1[j] += tr["dq"][c, j]
+            e = orc.residual(panda, t1, tg[c])
+            assert tr["pq"][c, j] == pytest.approx(np.linalg.norm(e[:3]), abs=1e-12)
+            assert tr["rq"][c, j] == pytest.approx(np.linalg.norm(e[3:]), abs=1e-12)
         hat = th[c].copy()
         if jp != jo:
             hat[jp] += tr["dp"][c, jp]
