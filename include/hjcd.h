@@ -188,12 +188,12 @@ hjcd_status hjcd_solve_noalloc(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id
 hjcd_status hjcd_fk(hjcd_ctx* ctx, int32_t robot_id, int64_t n_cand, const float* theta, int64_t ld,
                     float* out_pq, void* stream);
 
-/* Alg. 3 line 3: seeds uniform inside the limits. */
+/* Alg. 3, seeding: seeds uniform inside the limits. */
 hjcd_status hjcd_sample_seeds(hjcd_ctx* ctx, int32_t robot_id, int64_t n_cand, const int32_t* tgt,
                               const int32_t* cand, uint64_t seed, float* theta, int64_t ld, void* stream);
 
 /* Alg. 3: PO-CCD on each candidate.  theta_in == NULL samples the seeds
- * (line 3); otherwise iterations k0 .. k0+n_iters-1 start from theta_in.
+ * (its seeding step); otherwise iterations k0 .. k0+n_iters-1 start from theta_in.
  * theta_out may equal theta_in.  score/perr/oerr/iters (each may be NULL)
  * receive the final score, |e_p|, |omega| and iterations executed.
  * Trace (one iteration, n_iters == 1; any pointer may be NULL):
@@ -222,7 +222,7 @@ hjcd_status hjcd_po_ccd(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const fl
                         float* score, float* perr, float* oerr, int32_t* iters,
                         const hjcd_ccd_trace* trace, void* stream);
 
-/* Alg. 2 lines 2-7 for each target t: the K = max(1, floor(M_t/ratio))
+/* Alg. 2, top-K and duplication, for each target t: the K = max(1, floor(M_t/ratio))
  * lowest scores among its M_t = m_off[t+1]-m_off[t] seeds (ties to the lower
  * index), each copied floor(M_t/K) times with N(0, dup_sigma^2) noise, copy r
  * of kept seed i landing at b_off[t] + r*K + i.  m_off/b_off: [n_targets+1]
@@ -258,7 +258,7 @@ hjcd_status hjcd_pjik(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const floa
 hjcd_status hjcd_collide(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int64_t n_cand,
                          const float* theta, int64_t ld, uint8_t* hit, void* stream);
 
-/* Alg. 2 line 10: per target, the collision-free candidates (hit may be
+/* Alg. 2, final ranking: per target, the collision-free candidates (hit may be
  * NULL) of b_off[t] .. b_off[t+1]-1 sorted by score (ties to the lower
  * index), first top_k written as in hjcd_solve. */
 hjcd_status hjcd_rank(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const int64_t* b_off,

@@ -447,7 +447,7 @@ void orc_fk_batch(const orc_robot* R, int64_t C, const double* th, double* pq) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Alg. 3 line 3: seeds uniform inside the joint limits                     */
+/* Alg. 3, seeding: seeds uniform inside the joint limits                  */
 
 static void sample_seed(const orc_robot* R, const orc_params* P, uint32_t t, uint32_t c, double* th) {
     for (int j = 0; j < R->n; ++j) {
@@ -503,7 +503,7 @@ static double ccd_position_delta(const double pee[3], const double pt[3], const 
 }
 
 /* One iteration k of Alg. 3 for one candidate (theta updated in place).
- * Returns 1 when the coarse tolerance of line 14 holds after the update. */
+ * Returns 1 when the coarse tolerance of Alg. 3 holds after the update. */
 static double score_of(const orc_params* P, double ep, double eo);
 
 static int ccd_iteration(const orc_robot* R, const orc_params* P, const double tgt[7], uint32_t t,
@@ -530,7 +530,7 @@ static int ccd_iteration(const orc_robot* R, const orc_params* P, const double t
         for (int i = 0; i < 3; ++i) ahat[i] = qerr[1 + i] / sh;
     double delta_k = P->cd_delta0 * pow(P->cd_rho, (double)k);
 
-    /* lines 6-8: per joint, a position update and an orientation update, and the
+    /* Alg. 3: per joint, a position update and an orientation update, and the
      * task residual r (position and orientation error) after each of them */
     double Dp[ORC_MAXN], Pp[ORC_MAXN], Op[ORC_MAXN], Dq[ORC_MAXN], Pq[ORC_MAXN], Oq[ORC_MAXN], trial[ORC_MAXN];
     for (int j = 0; j < n; ++j) {
@@ -555,9 +555,9 @@ static int ccd_iteration(const orc_robot* R, const orc_params* P, const double t
         pos_ori_err(R, trial, tgt, &Pq[j], &Oq[j]);
     }
 
-    /* Alg. 3 line 9: greedy choice of the best position update and the best
+    /* Alg. 3, greedy choice of the best position update and the best
      * orientation update.  Reading: each trial is judged by the task residual it
-     * leaves (line 7 computes the full r), through its scalar form, the score
+     * leaves (Alg. 3 computes the full r of each trial), through its scalar form, the score
      * (|e_p|/eps_pos)^2 + (|omega|/eps_ori)^2 used for every ranking.  Ties: joints
      * are scanned from the base and a later joint replaces the current choice
      * only when its score is lower by more than the relative tolerance cd_tie,
@@ -582,7 +582,7 @@ static int ccd_iteration(const orc_robot* R, const orc_params* P, const double t
         }
     }
 
-    /* Alg. 3 line 10: apply both; on the same joint keep the larger step */
+    /* Alg. 3: apply both; on the same joint keep the larger step */
     double th_hat[ORC_MAXN];
     memcpy(th_hat, th, (size_t)n * sizeof(double));
     if (jp != jo) {
@@ -594,7 +594,7 @@ static int ccd_iteration(const orc_robot* R, const orc_params* P, const double t
         else th_hat[jo] += Dq[jo];
     }
 
-    /* Alg. 3 line 11, read as: accept when the position error or the
+    /* Alg. 3 acceptance, read as: accept when the position error or the
      * orientation error drops by more than its threshold gamma */
     double ep1, eo1;
     pos_ori_err(R, th_hat, tgt, &ep1, &eo1);
@@ -618,13 +618,13 @@ static int ccd_iteration(const orc_robot* R, const orc_params* P, const double t
     if (acc) {
         memcpy(th, th_hat, (size_t)n * sizeof(double));
     } else {
-        /* Alg. 3 line 12: random perturbation N(0, sigma^2 I), kept in the limits */
+        /* Alg. 3 rejection: random perturbation N(0, sigma^2 I), kept in the limits */
         for (int j = 0; j < n; ++j)
             th[j] = clampd(th[j] + P->cd_sigma * rnd_normal(P, c, t, PHASE_CD, (uint32_t)k, j),
                            R->lo[j], R->hi[j]);
     }
 
-    /* Alg. 3 line 14: coarse tolerance on the squared norms */
+    /* Alg. 3 break: coarse tolerance on the squared norms */
     double ep2, eo2;
     pos_ori_err(R, th, tgt, &ep2, &eo2);
     return (ep2 * ep2 < P->cd_eps_pos2) && (eo2 * eo2 < P->cd_eps_ori2);
@@ -688,7 +688,7 @@ void orc_po_ccd_batch(const orc_robot* R, const orc_params* P, const double* tar
 }
 
 /* ------------------------------------------------------------------------ */
-/* Alg. 2 lines 2-7: top-K by residual score and perturbed duplication       */
+/* Alg. 2: top-K by residual score and perturbed duplication               */
 
 /* K = max(1, floor(M / ratio)) seeds kept, each copied floor(M / K) times. */
 int64_t orc_dup_layout(int64_t M, int32_t ratio, int64_t* K, int64_t* copies) {
@@ -715,7 +715,7 @@ void orc_topk_dup(const orc_robot* R, const orc_params* P, int64_t T, const int6
         orc_dup_layout(M, P->dup_ratio, &K, &copies);
         uint8_t* taken = (uint8_t*)calloc((size_t)(M > 0 ? M : 1), 1);
         int64_t* sel = (int64_t*)malloc((size_t)(K > 0 ? K : 1) * sizeof(int64_t));
-        /* lines 3-6: K successive argmins, each removed from the set */
+        /* K successive argmins, each removed from the set */
         for (int64_t i = 0; i < K; ++i) {
             int64_t best = -1;
             for (int64_t m = 0; m < M; ++m) {
@@ -725,7 +725,7 @@ void orc_topk_dup(const orc_robot* R, const orc_params* P, int64_t T, const int6
             sel[i] = best;
             taken[best] = 1;
         }
-        /* lines 7-9: floor(B/K) perturbed copies of the K kept seeds */
+        /* floor(B/K) perturbed copies of the K kept seeds */
         for (int64_t r = 0; r < copies; ++r)
             for (int64_t i = 0; i < K; ++i) {
                 int64_t b = r * K + i;
@@ -747,7 +747,7 @@ void orc_topk_dup(const orc_robot* R, const orc_params* P, int64_t T, const int6
 /* Eq. normal-eqs, read as ((WJ)^T (WJ) + lambda D) step = (WJ)^T W r with
  * D = diag((WJ)^T (WJ)) (+1e-9) and r = target - current (the printed minus
  * sign belongs to the opposite residual convention), followed by the
- * elementwise trust region of Alg. 4 line 7.  Jw = W J is 6 x n, b = W r. */
+ * elementwise trust region of Alg. 4.  Jw = W J is 6 x n, b = W r. */
 void orc_lm_step(int n, const double* Jw, const double* b, double lambda, double R, double* step) {
     double A[ORC_MAXN * ORC_MAXN], g[ORC_MAXN];
     for (int i = 0; i < n; ++i) {
@@ -860,7 +860,7 @@ static double line_search(const lm_ctx* L, const double* th, const double* step,
 }
 
 /* One iteration k of Alg. 4 (theta updated in place).  Returns 1 when the
- * tolerance of line 16 holds after the update. */
+ * tolerance of Alg. 4 holds after the update. */
 static int lm_iteration(const orc_robot* R, const orc_params* P, const double tgt[7], uint32_t t,
                         uint32_t c, int k, double* th, double* J_out, double* W_out, double* dlm_out,
                         int32_t* branch_out, double* alpha_out, double* margin_out) {
@@ -885,7 +885,7 @@ static int lm_iteration(const orc_robot* R, const orc_params* P, const double tg
     }
     double cost0 = 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2] + b[3] * b[3] + b[4] * b[4] + b[5] * b[5]);
 
-    /* Eq. normal-eqs (see orc_lm_step), then the trust region of line 7 */
+    /* Eq. normal-eqs (see orc_lm_step), then the trust region of Alg. 4 */
     double g[ORC_MAXN], step[ORC_MAXN];
     for (int i = 0; i < n; ++i) {
         g[i] = 0.0;
@@ -929,7 +929,7 @@ static int lm_iteration(const orc_robot* R, const orc_params* P, const double tg
                 branch = BR_SINGLE;
                 alpha = a2;
             } else {
-                /* Alg. 4 line 15: random perturbation */
+                /* Alg. 4: random perturbation when every update fails */
                 for (int j = 0; j < n; ++j)
                     th[j] = clampd(th[j] + P->lm_sigma * rnd_normal(P, c, t, PHASE_LM, (uint32_t)k, j),
                                    R->lo[j], R->hi[j]);
@@ -944,7 +944,7 @@ static int lm_iteration(const orc_robot* R, const orc_params* P, const double tg
     if (alpha_out) *alpha_out = alpha;
     if (margin_out) *margin_out = margin;
 
-    /* Alg. 4 line 16 */
+    /* Alg. 4 break */
     double ep, eo;
     pos_ori_err(R, th, tgt, &ep, &eo);
     return (ep < P->eps_pos) && (eo < P->eps_ori);
@@ -1064,7 +1064,7 @@ void orc_collide_batch(const orc_robot* R, const orc_scene* S, int64_t C, const 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Alg. 2 line 10: collision-free candidates ranked by score                */
+/* Alg. 2, final step: collision-free candidates ranked by score           */
 
 void orc_rank(const orc_robot* R, int64_t T, const int64_t* b_off, const double* th_B,
               const double* score, const double* perr, const double* oerr, const uint8_t* hit,
@@ -1125,16 +1125,16 @@ void orc_solve(const orc_robot* R, const orc_scene* S, const orc_params* P, int6
             tg[m] = (int32_t)t;
             cd[m] = (int32_t)(m - m_off[t]);
         }
-    orc_po_ccd_batch(R, P, targets, CM, tg, cd, thM, sM, NULL, NULL, NULL);  /* line 1 */
-    orc_topk_dup(R, P, T, m_off, sM, thM, b_off, thB, NULL);                   /* lines 2-7 */
+    orc_po_ccd_batch(R, P, targets, CM, tg, cd, thM, sM, NULL, NULL, NULL);  /* PO-CCD */
+    orc_topk_dup(R, P, T, m_off, sM, thM, b_off, thB, NULL);                   /* top-K, duplication */
     for (int64_t t = 0; t < T; ++t)
         for (int64_t b = b_off[t]; b < b_off[t + 1]; ++b) {
             tg[b] = (int32_t)t;
             cd[b] = (int32_t)(b - b_off[t]);
         }
-    orc_pjik_batch(R, P, targets, CB, tg, cd, thB, sB, pB, oB, NULL);         /* line 8 */
-    if (R->n_sph > 0) orc_collide_batch(R, S, CB, thB, hB, NULL);              /* line 9 */
-    orc_rank(R, T, b_off, thB, sB, pB, oB, hB, top_k, out_q, out_err, out_count); /* line 10 */
+    orc_pjik_batch(R, P, targets, CB, tg, cd, thB, sB, pB, oB, NULL);         /* PJ-IK */
+    if (R->n_sph > 0) orc_collide_batch(R, S, CB, thB, hB, NULL);              /* collision filter */
+    orc_rank(R, T, b_off, thB, sB, pB, oB, hB, top_k, out_q, out_err, out_count); /* ranking */
 
     free(m_off);
     free(b_off);

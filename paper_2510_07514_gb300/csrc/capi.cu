@@ -565,7 +565,7 @@ hjcd_status hjcd_solve(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_
     launch_pack_targets(d_t7, T, opts->eps_pos, opts->eps_ori, opts->seed, nullptr, d_tg, s);
     if ((st = after_launch(ctx, 1))) return st;
 
-    // Alg. 2 line 1: PO-CCD from uniform seeds
+    // Alg. 2: PO-CCD from uniform seeds
     CcdArgs ca{};
     ca.tg = d_tg;
     ca.map = CandMap{nullptr, nullptr, d_moff, T};
@@ -582,13 +582,13 @@ hjcd_status hjcd_solve(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_
     if ((st = after_launch(ctx, 1))) return st;
     if (prof) HJCD_CUDA(ctx, cudaEventRecord(ctx->ev[1], s));
 
-    // lines 2-7: top-K and perturbed duplication
+    // top-K and perturbed duplication
     DupArgs da{d_tg, T, d_moff, sM, thM, CM, d_boff, thB, CB, nullptr, P.dup_ratio, P.dup_sigma};
     launch_topk_dup(R, da, max_m, s);
     if ((st = after_launch(ctx, 1))) return st;
     if (prof) HJCD_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
 
-    // line 8: PJ-IK
+    // PJ-IK
     LmArgs la{};
     la.tg = d_tg;
     la.map = CandMap{nullptr, nullptr, d_boff, T};
@@ -608,7 +608,7 @@ hjcd_status hjcd_solve(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_
     if ((st = after_launch(ctx, 1))) return st;
     if (prof) HJCD_CUDA(ctx, cudaEventRecord(ctx->ev[3], s));
 
-    // line 9: collision filter
+    // collision filter
     const bool collide = R.n_sph > 0;
     if (collide) {
         CollideArgs cl{};
@@ -632,7 +632,7 @@ hjcd_status hjcd_solve(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_
     }
     if (prof) HJCD_CUDA(ctx, cudaEventRecord(ctx->ev[4], s));
 
-    // line 10: rank the collision-free candidates
+    // rank the collision-free candidates
     RankArgs ra{T, d_boff, thB, CB, sB, pB, oB, collide ? hB : nullptr, top_k, q_out, e_out, c_out};
     launch_rank(R, ra, max_b, s);
     if ((st = after_launch(ctx, 1))) return st;

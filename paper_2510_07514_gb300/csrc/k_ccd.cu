@@ -1,4 +1,4 @@
-// k_ccd.cu -- seed sampling (Alg. 3 line 3) and PO-CCD iterations (Sec. IV,
+// k_ccd.cu -- seed sampling (Alg. 3) and PO-CCD iterations (Sec. IV,
 // Alg. 3), one candidate per thread.
 //
 // Per iteration one forward-kinematics pass gives every joint's origin and
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kCcdThreads, 4) k_ccd(const RobotParams R, con
             const V3 e = pt - E.p;
             ep2 = dot(e, e);
             eo = quat_angle(qerr.w, dot(qerr.v, qerr.v));
-            // Alg. 3 line 14, checked after each update
+            // Alg. 3 coarse break, checked after each update
             if (kk > 0 && ep2 < P.cd_eps_pos2 && eo * eo < P.cd_eps_ori2) {
                 iters = kk;
                 break;
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kCcdThreads, 4) k_ccd(const RobotParams R, con
             const int k = A.k0 + kk;
             const float ep0 = sqrtf(ep2);
 
-            // lines 6-9: one position and one orientation proposal per joint, the
+            // one position and one orientation proposal per joint, the
             // task residual each leaves, and the greedy choice by its score
             // (|e_p|/eps_pos)^2 + (|omega|/eps_ori)^2; a later joint replaces the
             // choice only when its score is lower by more than the fraction cd_tie
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kCcdThreads, 4) k_ccd(const RobotParams R, con
                 }
             }
 
-            // line 10: apply both; on the same joint the larger step
+            // apply both; on the same joint the larger step
             float aP = dP, aO = dO;
             if (jp == jo) {
                 if (fabsf(dP) >= fabsf(dO)) aO = 0.0f;
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kCcdThreads, 4) k_ccd(const RobotParams R, con
             const V3 e1 = pt - x;
             const float ep1 = sqrtf(dot(e1, e1));
             const float eo1 = quat_angle(q1.w, dot(q1.v, q1.v));
-            // line 11 (reading: an improvement above gamma in position or in orientation)
+            // acceptance (reading: an improvement above gamma in position or in orientation)
             const bool acc = (ep0 - ep1 > P.cd_gamma_pos) || (eo - eo1 > P.cd_gamma_ori);
 
             if (TRACE && kk == 0) {
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kCcdThreads, 4) k_ccd(const RobotParams R, con
                 col.th(jp) += aP;
                 col.th(jo) += aO;
             } else {
-                // line 12: theta + N(0, sigma^2 I), kept inside the limits
+                // rejection: theta + N(0, sigma^2 I), kept inside the limits
 #pragma unroll 1
                 for (int b = 0; 2 * b < n; ++b) {
                     const float2 z = normal_pair(T, (uint32_t)s, kPhaseCd, (uint32_t)k, b);

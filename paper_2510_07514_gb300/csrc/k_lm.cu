@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kLmWarps * 32, 4) k_lm(const RobotParams R, co
             const V3 epv = pt - E.p;
             const float ep = sqrtf(dot(epv, epv)), eo = sqrtf(dot(om, om));
             if ((kk > 0 && ep < T.eps_pos && eo < T.eps_ori) || kk == A.n_iters) {
-                // Alg. 4 line 16 (checked after each update) or the iteration cap
+                // Alg. 4 break (checked after each update) or the iteration cap
 #pragma unroll 1
                 for (int j = 0; j < n; ++j) A.th[j * A.ld + c] = S.th(j, lane);
                 if (A.score) {
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kLmWarps * 32, 4) k_lm(const RobotParams R, co
                 has = false;
             } else {
                 act = true;
-                // line 3: Jacobian columns z_i x (P_ee - P_i), z_i (in place), and the row norms
+                // Jacobian columns z_i x (P_ee - P_i), z_i (in place), and the row norms
                 float rn[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll 1
                 for (int i = 0; i < n; ++i) {
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kLmWarps * 32, 4) k_lm(const RobotParams R, co
                 }
                 S.cost0(lane) = 0.5f * cost0;
                 S.t(lane) = t;
-                // line 4: the push-through LM step on the weighted Jacobian
+                // the push-through LM step on the weighted Jacobian
                 float M[21], inv[6], y[6];
 #pragma unroll
                 for (int q = 0; q < 21; ++q) M[q] = 0.0f;
@@ -305,14 +305,14 @@ __global__ void __launch_bounds__(kLmWarps * 32, 4) k_lm(const RobotParams R, co
                         a = fmaf(v, y[r], a);
                         dd = fmaf(v, v, dd);
                     }
-                    const float st = clampf(a / dd, -Rt, Rt);  // line 5
+                    const float st = clampf(a / dd, -Rt, Rt);  // trust region
                     S.d(i, lane) = st;
                     if (TRACE && kk == 0 && A.tr.d_lm) A.tr.d_lm[i * A.ld + c] = st;
                 }
             }
         }
 
-        // ---- lines 6-8: line search; the full step by its owner, the rest spread ----
+        // ---- line search; the full step by its owner, the rest spread ----
         int branch = 3;
         float alpha_acc = 0.0f;
         if (act) {
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kLmWarps * 32, 4) k_lm(const RobotParams R, co
             }
         }
 
-        // ---- lines 9-11: dogleg (owner) ----
+        // ---- dogleg (owner) ----
         if (act && branch != 0) {
             float b[6];
 #pragma unroll
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(kLmWarps * 32, 4) k_lm(const RobotParams R, co
                     q2 = fmaf(v, v, q2);
                 }
                 S.d(i, lane) = fmaf(wgn, dgn, wgd * g);
-                if (fabsf(g) > gbest) {  // single-coordinate choice, for line 12
+                if (fabsf(g) > gbest) {  // single-coordinate choice
                     gbest = fabsf(g);
                     is = i;
                     gsel = g;
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(kLmWarps * 32, 4) k_lm(const RobotParams R, co
                 take_step(R, S, lane, 1.0f);
                 branch = 1;
             } else {
-                // lines 12-14: the joint with the largest |g_i|, a 1-D Gauss-Newton step on
+                // single coordinate: the joint with the largest |g_i|, a 1-D Gauss-Newton step on
                 // it clamped to R; its line-search trials are spread over the warp below
                 const float sstep = cn > 0.0f ? clampf(gsel / cn, -Rt, Rt) : 0.0f;
 #pragma unroll 1
@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(kLmWarps * 32, 4) k_lm(const RobotParams R, co
             }
         }
         if (act && branch == 3) {
-            // line 15: random perturbation
+            // random perturbation when every update fails
             const uint32_t k = (uint32_t)(A.k0 + kk);
 #pragma unroll 1
             for (int q = 0; 2 * q < n; ++q) {

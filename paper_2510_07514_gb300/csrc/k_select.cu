@@ -1,6 +1,6 @@
 // k_select.cu -- per-target selection: top-K and perturbed duplication
-// (Alg. 2 lines 2-7), ranking of the collision-free candidates (Alg. 2
-// line 10), and packing of target poses.
+// (Alg. 2), ranking of the collision-free candidates (Alg. 2, final
+// step), and packing of target poses.
 //
 // One CTA per target sorts 64-bit keys (score bits << 32 | index) in shared
 // memory with a bitonic network; scores are non-negative, so their IEEE bit

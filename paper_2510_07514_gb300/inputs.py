@@ -47,7 +47,7 @@ DEFAULT_PARAMS = dict(
     cd_rho=0.97,
     proj_eps=1e-4,            # projected-vector length (relative) below which Eq. theta_proj gives 0
     cd_tie=1e-4,              # greedy choice: a later joint wins only if its score is lower by this fraction
-    # Top-K and duplication (Alg. 2 lines 2-7)
+    # Top-K and duplication (Alg. 2)
     dup_ratio=4,              # K = max(1, floor(B / dup_ratio))
     dup_sigma=0.02,           # Sigma of the duplication perturbation (rad)
     # PJ-IK (Alg. 4)

@@ -197,7 +197,7 @@ def test_ccd_iteration_trace_parity(ctx, which):
     assert np.all(np.abs(g["op"] - o["op"]) < tol_j)
     for key in ("dq", "pq", "rq"):
         assert np.max(np.abs(g[key] - o[key])) < tol, key
-    # Greedy choices where no comparison of Alg. 3 line 9 is within reach of
+    # Greedy choices where no comparison of the greedy choice of Alg. 3 is within reach of
     # rounding: every other trial's score differs from the chosen one's by more
     # than the tie band plus twice the score error the trial errors allow
     # (d s = 2 |e_p| d|e_p| / eps_p^2 + 2 |w| d|w| / eps_o^2 + squares).

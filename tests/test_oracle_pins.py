@@ -324,7 +324,7 @@ def test_ccd_selection_acceptance_and_perturbation(panda):
     tr = orc.ccd_iteration(panda, P, tg, tgt_idx, cand, k, th)
     n_acc = 0
     for c in range(C):
-        # Alg. 3 line 9: greedy argmin of the residual score each trial leaves
+        # Alg. 3: greedy argmin of the residual score each trial leaves
         sp = _score(P, tr["rp"][c], tr["op"][c])
         so = _score(P, tr["pq"][c], tr["rq"][c])
         if tr["margin_p"][c] > P.cd_tie:
@@ -370,7 +370,7 @@ def test_ccd_selection_acceptance_and_perturbation(panda):
 
 
 # ----------------------------------------------------------------------------
-# top-K and duplication (Alg. 2 lines 2-7)
+# top-K and duplication (Alg. 2)
 
 def test_dup_layout():
     assert orc.dup_layout(1000, 4) == (250, 4, 1000)
@@ -584,7 +584,7 @@ def test_collision_matches_pairwise_distances():
 
 
 # ----------------------------------------------------------------------------
-# ranking (Alg. 2 line 10) and the whole method
+# ranking (Alg. 2) and the whole method
 
 def test_rank_matches_sorted_collision_free(panda):
     rng = np.random.default_rng(18)
