@@ -51,6 +51,7 @@ typedef int32_t hjcd_status;
 #define HJCD_MAX_SPHERES 256   /* link spheres per robot */
 #define HJCD_MAX_SAMPLES 8192  /* seeds per target */
 #define HJCD_MAX_TOPK 64
+#define HJCD_MAX_BATCH_ROBOTS 16  /* distinct robots in one hjcd_solve_batch call */
 
 typedef struct hjcd_ctx hjcd_ctx;
 
@@ -137,7 +138,7 @@ hjcd_status hjcd_set_scene(hjcd_ctx* ctx, int32_t scene_id_or_new, int n_sph, co
  * Outputs: out_q [n_targets][top_k][n] joint vectors, out_err
  * [n_targets][top_k][2] (|e_p| m, |omega| rad), out_count [n_targets] the
  * number of collision-free solutions written (0..top_k; 0 is not an error).
- * Entries past out_count are left untouched.
+ * Rows past out_count are NaN.
  * targets_pq and the three outputs may each be host or device pointers
  * (detected per pointer).  With any host output the call synchronises the
  * stream before returning. */
@@ -145,10 +146,42 @@ hjcd_status hjcd_solve(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_
                        const float* targets_pq, const hjcd_solve_opts* opts,
                        float* out_q, float* out_err, int32_t* out_count, void* stream);
 
+/* One request of a batch.  scene_id >= 0 names a resident scene; with
+ * scene_id < 0 the request brings its own obstacles (HOST arrays, copied with
+ * the batch): n_inline_spheres x y z r (r > 0) and n_inline_boxes lo xyz,
+ * hi xyz (zero of both: no obstacles).  opts as for hjcd_solve; of
+ * opts.params only the iteration caps cd_max_iters and lm_max_iters are taken
+ * (the other parameters are the batch's). */
+typedef struct hjcd_batch_item {
+    int32_t robot_id;
+    int32_t scene_id;
+    int32_t n_inline_spheres;
+    int32_t n_inline_boxes;
+    const float* inline_spheres;
+    const float* inline_boxes;
+    int32_t n_targets;
+    int32_t pad_;
+    const float* targets_pq;
+    hjcd_solve_opts opts;
+    float* out_q;
+    float* out_err;
+    int32_t* out_count;
+} hjcd_batch_item;
+
+/* Alg. 2 for several requests at once -- different robots (at most
+ * HJCD_MAX_BATCH_ROBOTS distinct), scenes, seed counts, tolerances, top_k and
+ * iteration caps -- packed into one launch per phase.  Every request's
+ * results are those hjcd_solve gives it alone with the same parameters: each
+ * target row keys its random streams by its request's seed and its index
+ * inside the request.  Outputs per item as for hjcd_solve; with any host
+ * output the call synchronises the stream. */
+hjcd_status hjcd_solve_batch(hjcd_ctx* ctx, int n_items, const hjcd_batch_item* items,
+                             const hjcd_params* params, void* stream);
+
 /* ---- the whole method without allocation ------------------------------------- */
 
 /* Bytes of the file-scope device array that serves as the scratch of
- * hjcd_solve_noalloc.  A call needs 48 T + 16 (T + 1) + 12 for the targets,
+ * hjcd_solve_noalloc.  A call needs 64 T + 16 (T + 1) + 12 for the targets,
  * offsets and flags, plus (4 n + 4) M + (4 n + 13) B bytes and a little
  * alignment for T targets of M seeds (B per hjcd_topk_dup, B = M for the
  * default ratio) and n joints: about 200k candidates of a 7-joint arm. */

@@ -89,6 +89,36 @@ class Context:
         hjcd.hjcd_solve(self.h, robot_id, scene_id, T, targets, o, out[0], out[1], out[2], stream)
         return out
 
+    def batch_item(self, robot_id: int, scene_id: int, targets, n_samples: int, top_k: int, seed: int, n_dof: int,
+                   eps_pos=1e-3, eps_ori=1e-2, params=None, samples_per_target=None, spheres=None, boxes=None,
+                   device=None):
+        """An hjcd_batch_item with freshly allocated outputs (returned beside it).
+        `spheres` [k, 4] / `boxes` [k, 6] give the request's own obstacles
+        (scene_id < 0).  Outputs live on `device` (default: the targets')."""
+        T = int(targets.shape[0])
+        dev = targets.device if device is None else device
+        out = (torch.empty((T, top_k, n_dof), dtype=torch.float32, device=dev),
+               torch.empty((T, top_k, 2), dtype=torch.float32, device=dev),
+               torch.zeros((T,), dtype=torch.int32, device=dev))
+        it = hjcd.hjcd_batch_item()
+        it.robot_id, it.scene_id, it.n_targets = int(robot_id), int(scene_id), T
+        it.targets_pq = hjcd.ptr(targets)
+        it.opts = self.opts(n_samples, top_k, seed, eps_pos, eps_ori, params, samples_per_target)
+        if spheres is not None and len(spheres):
+            sp = _f32(spheres, (-1,))
+            self._keep.append(sp)
+            it.n_inline_spheres, it.inline_spheres = len(spheres), sp.ctypes.data
+        if boxes is not None and len(boxes):
+            bx = _f32(boxes, (-1,))
+            self._keep.append(bx)
+            it.n_inline_boxes, it.inline_boxes = len(boxes), bx.ctypes.data
+        it.out_q, it.out_err, it.out_count = (hjcd.ptr(x) for x in out)
+        self._keep.append(targets)
+        return it, out
+
+    def solve_batch(self, items, params=None, stream=None) -> None:
+        hjcd.hjcd_solve_batch(self.h, items, params, stream)
+
     def fk(self, robot_id: int, theta_soa: torch.Tensor, stream=None) -> torch.Tensor:
         """Flange poses [C, 7] of joint vectors given as a device tensor [n, C]."""
         C = int(theta_soa.shape[1])

@@ -1,6 +1,7 @@
 // capi.cu -- the C ABI of include/hjcd.h: context, resident robot and scene
-// tables, the solve workspace, pointer-kind detection and the launch sequence
-// of Alg. 2 (PO-CCD -> top-K/duplication -> PJ-IK -> collision -> ranking).
+// tables, pointer-kind detection, the whole-method entry points (one request,
+// or a batch packed into one launch per phase; wave.cu) and the stage entry
+// points.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -10,62 +11,11 @@
 #include <string>
 #include <vector>
 
-#include "hjcd_internal.cuh"
+#include "host.h"
 
 using namespace hjcd;
 
-namespace {
-
-constexpr int kMaxSceneFloat4 = 10240;  // obstacle spheres + 2 * boxes staged in shared memory (160 KB)
-
-// Collision tables of a robot in one device buffer: spheres sorted by body
-// (float4, body frame), their bodies, per-body [first, count) ranges, a
-// bounding ("coarse") sphere per body and the list of body pairs checked for
-// self-collision.
-struct RobotRec {
-    RobotParams P{};
-    void* dbuf = nullptr;
-    float4* sph = nullptr;
-    int32_t* body = nullptr;
-    int2* range = nullptr;
-    float4* coarse = nullptr;
-    int2* pairs = nullptr;
-    int n_pairs = 0;
-};
-
-struct SceneRec {
-    float4* buf = nullptr;
-    int n_sph = 0, n_box = 0;
-    size_t cap = 0;
-    bool live = false;
-};
-
-size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
-
-}  // namespace
-
-struct hjcd_ctx {
-    int device = 0;
-    std::vector<RobotRec> robots;
-    std::vector<SceneRec> scenes;
-    std::string err;
-    char* ws = nullptr;  // device workspace
-    size_t ws_cap = 0;
-    char* pin = nullptr;  // pinned host staging
-    size_t pin_cap = 0;
-    cudaEvent_t ws_free = nullptr;   // recorded when the last call's device work on the workspace ends
-    cudaEvent_t pin_free = nullptr;  // recorded after the last copy out of the pinned staging
-    Counters* cnt = nullptr;
-    int32_t* err_flag = nullptr;
-    unsigned long long* queue = nullptr;  // work-queue heads of the persistent kernels
-    float* sink = nullptr;
-    bool profile = false;
-    cudaEvent_t ev[6] = {};
-    bool ev_valid = false;
-    int64_t launches = 0;
-};
-
-namespace {
+namespace hjcd {
 
 hjcd_status fail(hjcd_ctx* ctx, hjcd_status code, const char* fmt, ...) {
     char buf[512];
@@ -77,14 +27,6 @@ hjcd_status fail(hjcd_ctx* ctx, hjcd_status code, const char* fmt, ...) {
     return code;
 }
 
-#define HJCD_CUDA(ctx, call)                                                                         \
-    do {                                                                                             \
-        cudaError_t e_ = (call);                                                                     \
-        if (e_ != cudaSuccess)                                                                       \
-            return fail(ctx, e_ == cudaErrorMemoryAllocation ? HJCD_ENOMEM : HJCD_ECUDA, "%s: %s (%s)", \
-                        #call, cudaGetErrorString(e_), cudaGetErrorName(e_));                        \
-    } while (0)
-
 hjcd_status after_launch(hjcd_ctx* ctx, int kernels) {
     ctx->launches += kernels;
     cudaError_t e = cudaGetLastError();
@@ -92,7 +34,7 @@ hjcd_status after_launch(hjcd_ctx* ctx, int kernels) {
     return HJCD_OK;
 }
 
-// 1 = device-accessible (device or managed), 0 = host, -1 = unknown pointer
+// 1 = device-accessible (device or managed), 0 = host, -1 = null
 int pointer_kind(const void* p) {
     if (!p) return -1;
     cudaPointerAttributes a;
@@ -142,16 +84,6 @@ hjcd_status ensure_pin(hjcd_ctx* ctx, size_t bytes) {
     return HJCD_OK;
 }
 
-struct Carve {
-    size_t off = 0;
-    template <typename T>
-    size_t take(size_t count) {
-        const size_t o = off;
-        off = align_up(off + count * sizeof(T));
-        return o;
-    }
-};
-
 hjcd_status check_robot(hjcd_ctx* ctx, int32_t id, RobotRec** out) {
     if (id < 0 || id >= (int32_t)ctx->robots.size()) return fail(ctx, HJCD_ENOTFOUND, "unknown robot id %d", id);
     *out = &ctx->robots[id];
@@ -168,8 +100,8 @@ hjcd_status check_scene(hjcd_ctx* ctx, int32_t id, SceneRec** out) {
 }
 
 hjcd_status check_params(hjcd_ctx* ctx, const hjcd_params& P) {
-    if (P.cd_max_iters < 0 || P.lm_max_iters < 0 || P.cd_max_iters > (1 << 20) || P.lm_max_iters > (1 << 20))
-        return fail(ctx, HJCD_EINVAL, "iteration caps must be in [0, 2^20]");
+    if (P.cd_max_iters < 0 || P.lm_max_iters < 0 || P.cd_max_iters > 32767 || P.lm_max_iters > 32767)
+        return fail(ctx, HJCD_EINVAL, "iteration caps must be in [0, 32767]");
     if (P.dup_ratio < 1) return fail(ctx, HJCD_EINVAL, "dup_ratio must be >= 1");
     if (P.lm_A < 0 || P.lm_A > 31) return fail(ctx, HJCD_EINVAL, "lm_A must be in [0, 31]");
     if (!(P.lm_beta > 1.0f)) return fail(ctx, HJCD_EINVAL, "lm_beta must be > 1");
@@ -188,11 +120,29 @@ int64_t dup_count(int64_t M, int ratio) {
     return K * (M / K);
 }
 
-// pack n device-resident 7-float targets into TargetDesc rows at `out`
-hjcd_status pack_device_targets(hjcd_ctx* ctx, const float* pq7, int T, float eps_pos, float eps_ori,
-                                uint64_t seed, TargetDesc* out, cudaStream_t st) {
-    launch_pack_targets(pq7, T, eps_pos, eps_ori, seed, nullptr, out, st);
-    return after_launch(ctx, 1);
+RobotSet single_robot_set(const RobotRec& r) {
+    return RobotSet{r.d_params, r.d_dev, 1, r.P.n, r.P.n_sph, r.n_pairs};
+}
+
+}  // namespace hjcd
+
+namespace {
+
+// a target-row template for the stage entry points: robot 0, no scene
+TargetDesc stage_template(float eps_pos, float eps_ori, uint64_t seed, int cd_iters, int lm_iters, int top_k,
+                          int scene) {
+    TargetDesc d{};
+    d.q[0] = 1.0f;
+    d.eps_pos = eps_pos;
+    d.eps_ori = eps_ori;
+    d.key[0] = (uint32_t)(seed & 0xffffffffu);
+    d.key[1] = (uint32_t)(seed >> 32);
+    d.robot = 0;
+    d.scene = scene;
+    d.cd_iters = (int16_t)cd_iters;
+    d.lm_iters = (int16_t)lm_iters;
+    d.top_k = top_k;
+    return d;
 }
 
 }  // namespace
@@ -269,12 +219,13 @@ hjcd_status hjcd_init(int device, hjcd_ctx** out) {
 
 void hjcd_destroy(hjcd_ctx* ctx) {
     if (!ctx) return;
+    server_stop(ctx);
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     for (auto& r : ctx->robots)
         if (r.dbuf) cudaFree(r.dbuf);
-    for (auto& s : ctx->scenes)
-        if (s.buf) cudaFree(s.buf);
+    for (auto& sc : ctx->scenes)
+        if (sc.buf) cudaFree(sc.buf);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->pin) cudaFreeHost(ctx->pin);
     if (ctx->cnt) cudaFree(ctx->cnt);
@@ -384,23 +335,31 @@ hjcd_status hjcd_create_robot(hjcd_ctx* ctx, int n, const float* dh_a, const flo
     hjcd_status st = make_current(ctx);
     if (st) return st;
     const size_t ns1 = std::max<size_t>(sph.size(), 1), np1 = std::max<size_t>(pairs.size(), 1);
-    const size_t o_body = align_up(16 * ns1), o_range = o_body + align_up(4 * ns1),
+    const size_t o_dev = align_up(sizeof(RobotParams)), o_sph = o_dev + align_up(sizeof(RobotDev)),
+                 o_body = o_sph + align_up(16 * ns1), o_range = o_body + align_up(4 * ns1),
                  o_coarse = o_range + align_up(8 * (size_t)nb), o_pairs = o_coarse + align_up(16 * (size_t)nb),
                  bytes = o_pairs + align_up(8 * np1);
     HJCD_CUDA(ctx, cudaMalloc(&rec.dbuf, bytes));
     char* base = static_cast<char*>(rec.dbuf);
-    rec.sph = reinterpret_cast<float4*>(base);
-    rec.body = reinterpret_cast<int32_t*>(base + o_body);
-    rec.range = reinterpret_cast<int2*>(base + o_range);
-    rec.coarse = reinterpret_cast<float4*>(base + o_coarse);
-    rec.pairs = reinterpret_cast<int2*>(base + o_pairs);
+    rec.d_params = reinterpret_cast<RobotParams*>(base);
+    rec.d_dev = reinterpret_cast<RobotDev*>(base + o_dev);
+    rec.dev.sph = reinterpret_cast<const float4*>(base + o_sph);
+    rec.dev.body = reinterpret_cast<const int32_t*>(base + o_body);
+    rec.dev.range = reinterpret_cast<const int2*>(base + o_range);
+    rec.dev.coarse = reinterpret_cast<const float4*>(base + o_coarse);
+    rec.dev.pairs = reinterpret_cast<const int2*>(base + o_pairs);
+    rec.dev.n_pairs = rec.n_pairs;
+    rec.dev.n_sph = n_spheres;
+    HJCD_CUDA(ctx, cudaMemcpy(rec.d_params, &rec.P, sizeof(RobotParams), cudaMemcpyHostToDevice));
+    HJCD_CUDA(ctx, cudaMemcpy(rec.d_dev, &rec.dev, sizeof(RobotDev), cudaMemcpyHostToDevice));
     if (!sph.empty()) {
-        HJCD_CUDA(ctx, cudaMemcpy(rec.sph, sph.data(), 16 * sph.size(), cudaMemcpyHostToDevice));
-        HJCD_CUDA(ctx, cudaMemcpy(rec.body, body.data(), 4 * body.size(), cudaMemcpyHostToDevice));
+        HJCD_CUDA(ctx, cudaMemcpy(base + o_sph, sph.data(), 16 * sph.size(), cudaMemcpyHostToDevice));
+        HJCD_CUDA(ctx, cudaMemcpy(base + o_body, body.data(), 4 * body.size(), cudaMemcpyHostToDevice));
     }
-    HJCD_CUDA(ctx, cudaMemcpy(rec.range, range.data(), 8 * (size_t)nb, cudaMemcpyHostToDevice));
-    HJCD_CUDA(ctx, cudaMemcpy(rec.coarse, coarse.data(), 16 * (size_t)nb, cudaMemcpyHostToDevice));
-    if (!pairs.empty()) HJCD_CUDA(ctx, cudaMemcpy(rec.pairs, pairs.data(), 8 * pairs.size(), cudaMemcpyHostToDevice));
+    HJCD_CUDA(ctx, cudaMemcpy(base + o_range, range.data(), 8 * (size_t)nb, cudaMemcpyHostToDevice));
+    HJCD_CUDA(ctx, cudaMemcpy(base + o_coarse, coarse.data(), 16 * (size_t)nb, cudaMemcpyHostToDevice));
+    if (!pairs.empty()) HJCD_CUDA(ctx, cudaMemcpy(base + o_pairs, pairs.data(), 8 * pairs.size(), cudaMemcpyHostToDevice));
+    std::lock_guard<std::mutex> lock(ctx->api_mu);
     ctx->robots.push_back(rec);
     *robot_id = (int32_t)ctx->robots.size() - 1;
     return HJCD_OK;
@@ -430,35 +389,62 @@ hjcd_status hjcd_set_scene(hjcd_ctx* ctx, int32_t scene_id_or_new, int n_sph, co
     }
     hjcd_status st = make_current(ctx);
     if (st) return st;
+    std::lock_guard<std::mutex> lock(ctx->api_mu);
     int32_t id = scene_id_or_new;
     if (id < 0) {
         ctx->scenes.push_back(SceneRec{});
         id = (int32_t)ctx->scenes.size() - 1;
     }
     SceneRec& S = ctx->scenes[id];
-    const size_t bytes = 16 * (size_t)std::max(nf4, 1);
+    const size_t bytes = 16 + 16 * (size_t)std::max(nf4, 1);  // descriptor, then the obstacles
+    // an earlier solve may still read the old table
+    HJCD_CUDA(ctx, cudaDeviceSynchronize());
     if (bytes > S.cap) {
-        // an earlier solve may still read the old table
-        HJCD_CUDA(ctx, cudaDeviceSynchronize());
         if (S.buf) HJCD_CUDA(ctx, cudaFree(S.buf));
         S.buf = nullptr;
+        S.cap = 0;
         HJCD_CUDA(ctx, cudaMalloc(&S.buf, bytes));
         S.cap = bytes;
-    } else {
-        HJCD_CUDA(ctx, cudaDeviceSynchronize());
     }
-    HJCD_CUDA(ctx, cudaMemcpy(S.buf, buf.data(), bytes, cudaMemcpyHostToDevice));
-    S.n_sph = n_sph;
-    S.n_box = n_box;
+    static_assert(sizeof(SceneDev) == 16, "scene descriptor is one 16-byte slot");
+    char* base = static_cast<char*>(S.buf);
+    S.d_dev = reinterpret_cast<SceneDev*>(base);
+    S.dev = SceneDev{reinterpret_cast<const float4*>(base + 16), n_sph, n_box};
+    HJCD_CUDA(ctx, cudaMemcpy(base, &S.dev, sizeof(SceneDev), cudaMemcpyHostToDevice));
+    HJCD_CUDA(ctx, cudaMemcpy(base + 16, buf.data(), 16 * (size_t)std::max(nf4, 1), cudaMemcpyHostToDevice));
     S.live = true;
     *scene_id = id;
     return HJCD_OK;
 }
 
-hjcd_status hjcd_solve(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_targets, const float* targets_pq,
-                       const hjcd_solve_opts* opts, float* out_q, float* out_err, int32_t* out_count,
-                       void* stream) {
-    if (!ctx) return HJCD_EINVAL;
+// one request (or a batch) through the context's own workspace; synchronises
+// when an output is host memory
+static hjcd_status solve_items(hjcd_ctx* ctx, const WaveItem* items, int n_items, const hjcd_params& P,
+                               cudaStream_t s) {
+    hjcd_status st;
+    WavePlan W;
+    if ((st = plan_wave(ctx, items, n_items, P, &W))) return st;
+    if (W.T == 0) return HJCD_OK;
+    if ((st = ensure_ws(ctx, W.bytes))) return st;
+    if ((st = ensure_pin(ctx, W.head))) return st;
+    HJCD_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ws_free, 0));
+    const bool prof = ctx->profile;
+    if ((st = run_wave(ctx, W, items, P, ctx->ws, ctx->pin, s, prof ? ctx->ev : nullptr))) return st;
+    HJCD_CUDA(ctx, cudaEventRecord(ctx->pin_free, s));
+    HJCD_CUDA(ctx, cudaEventRecord(ctx->ws_free, s));
+    if (prof) ctx->ev_valid = true;
+    if (W.host_out) {
+        HJCD_CUDA(ctx, cudaStreamSynchronize(s));
+        int32_t flag = 0;
+        HJCD_CUDA(ctx, cudaMemcpy(&flag, wave_flag(W, ctx->ws), sizeof flag, cudaMemcpyDeviceToHost));
+        if (flag) return fail(ctx, HJCD_ETIMEOUT, "collision kernel: staging wait ran out");
+    }
+    return HJCD_OK;
+}
+
+static hjcd_status item_from(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_targets, const float* targets_pq,
+                             const hjcd_solve_opts* opts, float* out_q, float* out_err, int32_t* out_count,
+                             WaveItem* it) {
     RobotRec* rob;
     SceneRec* sc;
     hjcd_status st;
@@ -466,193 +452,75 @@ hjcd_status hjcd_solve(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_
     if ((st = check_scene(ctx, scene_id, &sc))) return st;
     if (!opts) return fail(ctx, HJCD_EINVAL, "null opts");
     if (n_targets < 0) return fail(ctx, HJCD_EINVAL, "n_targets < 0");
+    *it = WaveItem{};
+    it->rob = rob;
+    it->scene = sc;
+    it->T = n_targets;
+    it->targets = targets_pq;
+    it->spt = opts->samples_per_target;
+    it->n_samples = opts->n_samples;
+    it->eps_pos = opts->eps_pos;
+    it->eps_ori = opts->eps_ori;
+    it->seed = opts->seed;
+    it->top_k = opts->top_k;
+    it->cd_iters = -1;
+    it->lm_iters = -1;
+    it->out_q = out_q;
+    it->out_err = out_err;
+    it->out_count = out_count;
+    return HJCD_OK;
+}
+
+hjcd_status hjcd_solve(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_targets, const float* targets_pq,
+                       const hjcd_solve_opts* opts, float* out_q, float* out_err, int32_t* out_count,
+                       void* stream) {
+    if (!ctx) return HJCD_EINVAL;
+    hjcd_status st;
+    WaveItem it;
+    if ((st = item_from(ctx, robot_id, scene_id, n_targets, targets_pq, opts, out_q, out_err, out_count, &it)))
+        return st;
     if (n_targets == 0) return HJCD_OK;
-    if (!targets_pq || !out_q || !out_err || !out_count) return fail(ctx, HJCD_EINVAL, "null buffer");
-    if (!(opts->eps_pos > 0.0f) || !(opts->eps_ori > 0.0f)) return fail(ctx, HJCD_EINVAL, "tolerances must be > 0");
-    if (opts->top_k < 1 || opts->top_k > HJCD_MAX_TOPK) return fail(ctx, HJCD_EINVAL, "top_k outside [1, %d]", HJCD_MAX_TOPK);
     hjcd_params P;
     if (opts->params) P = *opts->params;
     else hjcd_default_params(&P);
     if ((st = check_params(ctx, P))) return st;
     if ((st = make_current(ctx))) return st;
-    cudaStream_t s = (cudaStream_t)stream;
-    const RobotParams& R = rob->P;
-    const int n = R.n, T = n_targets, top_k = opts->top_k;
+    return solve_items(ctx, &it, 1, P, (cudaStream_t)stream);
+}
 
-    // per-target seed counts and offsets
-    std::vector<int64_t> off(2 * (size_t)(T + 1));
-    int64_t* m_off = off.data();
-    int64_t* b_off = off.data() + T + 1;
-    m_off[0] = b_off[0] = 0;
-    int max_m = 0, max_b = 0;
-    for (int t = 0; t < T; ++t) {
-        const int m = opts->samples_per_target ? opts->samples_per_target[t] : opts->n_samples;
-        if (m < 1 || m > HJCD_MAX_SAMPLES)
-            return fail(ctx, HJCD_EINVAL, "target %d: seed count %d outside [1, %d]", t, m, HJCD_MAX_SAMPLES);
-        const int64_t b = dup_count(m, P.dup_ratio);
-        m_off[t + 1] = m_off[t] + m;
-        b_off[t + 1] = b_off[t] + b;
-        max_m = std::max(max_m, m);
-        max_b = std::max(max_b, (int)b);
-    }
-    const int64_t CM = m_off[T], CB = b_off[T];
-
-    const bool dev_tgt = pointer_kind(targets_pq) == 1;
-    const bool dev_q = pointer_kind(out_q) == 1, dev_e = pointer_kind(out_err) == 1,
-               dev_c = pointer_kind(out_count) == 1;
-    if (!dev_tgt) {
-        for (int t = 0; t < T; ++t) {
-            const float* q = targets_pq + 7 * (size_t)t + 3;
-            const float nn = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
-            if (!(nn > 0.0f) || !std::isfinite(nn)) return fail(ctx, HJCD_EINVAL, "target %d: zero quaternion", t);
+hjcd_status hjcd_solve_batch(hjcd_ctx* ctx, int n_items, const hjcd_batch_item* items, const hjcd_params* params,
+                             void* stream) {
+    if (!ctx) return HJCD_EINVAL;
+    if (n_items < 0 || (n_items > 0 && !items)) return fail(ctx, HJCD_EINVAL, "bad item list");
+    if (n_items == 0) return HJCD_OK;
+    hjcd_status st;
+    hjcd_params P;
+    if (params) P = *params;
+    else hjcd_default_params(&P);
+    if ((st = check_params(ctx, P))) return st;
+    std::vector<WaveItem> w(n_items);
+    for (int i = 0; i < n_items; ++i) {
+        const hjcd_batch_item& b = items[i];
+        if ((st = item_from(ctx, b.robot_id, b.scene_id, b.n_targets, b.targets_pq, &b.opts, b.out_q, b.out_err,
+                            b.out_count, &w[i])))
+            return st;
+        if (b.scene_id < 0) {
+            w[i].inl_nsph = b.n_inline_spheres;
+            w[i].inl_sph = b.inline_spheres;
+            w[i].inl_nbox = b.n_inline_boxes;
+            w[i].inl_box = b.inline_boxes;
+            if ((b.n_inline_spheres > 0 && pointer_kind(b.inline_spheres) == 1) ||
+                (b.n_inline_boxes > 0 && pointer_kind(b.inline_boxes) == 1))
+                return fail(ctx, HJCD_EINVAL, "item %d: inline obstacles must be host memory", i);
+        }
+        if (b.opts.params) {
+            if ((st = check_params(ctx, *b.opts.params))) return st;
+            w[i].cd_iters = b.opts.params->cd_max_iters;
+            w[i].lm_iters = b.opts.params->lm_max_iters;
         }
     }
-
-    // workspace
-    Carve cv;
-    const size_t o_tg = cv.take<TargetDesc>(T);
-    const size_t o_off = cv.take<int64_t>(2 * (size_t)(T + 1));
-    const size_t o_thM = cv.take<float>((size_t)n * CM);
-    const size_t o_sM = cv.take<float>(CM);
-    const size_t o_thB = cv.take<float>((size_t)n * CB);
-    const size_t o_sB = cv.take<float>(CB);
-    const size_t o_pB = cv.take<float>(CB);
-    const size_t o_oB = cv.take<float>(CB);
-    const size_t o_hB = cv.take<uint8_t>(CB);
-    const size_t o_t7 = cv.take<float>(dev_tgt ? 0 : 7 * (size_t)T);
-    const size_t o_q = cv.take<float>(dev_q ? 0 : (size_t)T * top_k * n);
-    const size_t o_e = cv.take<float>(dev_e ? 0 : (size_t)T * top_k * 2);
-    const size_t o_c = cv.take<int32_t>(dev_c ? 0 : (size_t)T);
-    if ((st = ensure_ws(ctx, cv.off))) return st;
-    HJCD_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ws_free, 0));
-    char* W = ctx->ws;
-    TargetDesc* d_tg = reinterpret_cast<TargetDesc*>(W + o_tg);
-    int64_t* d_moff = reinterpret_cast<int64_t*>(W + o_off);
-    int64_t* d_boff = d_moff + T + 1;
-    float* thM = reinterpret_cast<float*>(W + o_thM);
-    float* sM = reinterpret_cast<float*>(W + o_sM);
-    float* thB = reinterpret_cast<float*>(W + o_thB);
-    float* sB = reinterpret_cast<float*>(W + o_sB);
-    float* pB = reinterpret_cast<float*>(W + o_pB);
-    float* oB = reinterpret_cast<float*>(W + o_oB);
-    uint8_t* hB = reinterpret_cast<uint8_t*>(W + o_hB);
-    float* q_out = dev_q ? out_q : reinterpret_cast<float*>(W + o_q);
-    float* e_out = dev_e ? out_err : reinterpret_cast<float*>(W + o_e);
-    int32_t* c_out = dev_c ? out_count : reinterpret_cast<int32_t*>(W + o_c);
-
-    // host -> device: offsets (and targets when they are host memory) through pinned staging
-    const size_t pin_off = off.size() * sizeof(int64_t);
-    const size_t pin_tgt = dev_tgt ? 0 : 7 * sizeof(float) * (size_t)T;
-    if ((st = ensure_pin(ctx, align_up(pin_off) + pin_tgt))) return st;
-    std::memcpy(ctx->pin, off.data(), pin_off);
-    HJCD_CUDA(ctx, cudaMemcpyAsync(d_moff, ctx->pin, pin_off, cudaMemcpyHostToDevice, s));
-    const float* d_t7 = targets_pq;
-    if (!dev_tgt) {
-        float* t7 = reinterpret_cast<float*>(W + o_t7);
-        if (pinned_host(targets_pq)) {
-            HJCD_CUDA(ctx, cudaMemcpyAsync(t7, targets_pq, pin_tgt, cudaMemcpyHostToDevice, s));
-        } else {
-            std::memcpy(ctx->pin + align_up(pin_off), targets_pq, pin_tgt);
-            HJCD_CUDA(ctx, cudaMemcpyAsync(t7, ctx->pin + align_up(pin_off), pin_tgt, cudaMemcpyHostToDevice, s));
-        }
-        d_t7 = t7;
-    }
-    HJCD_CUDA(ctx, cudaEventRecord(ctx->pin_free, s));
-    HJCD_CUDA(ctx, cudaMemsetAsync(ctx->err_flag, 0, sizeof(int32_t), s));
-
-    const bool prof = ctx->profile;
-    if (prof) HJCD_CUDA(ctx, cudaEventRecord(ctx->ev[0], s));
-    launch_pack_targets(d_t7, T, opts->eps_pos, opts->eps_ori, opts->seed, nullptr, d_tg, s);
-    if ((st = after_launch(ctx, 1))) return st;
-
-    // Alg. 2: PO-CCD from uniform seeds
-    CcdArgs ca{};
-    ca.tg = d_tg;
-    ca.map = CandMap{nullptr, nullptr, d_moff, T};
-    ca.C = CM;
-    ca.ld = CM;
-    ca.th_in = nullptr;
-    ca.th_out = thM;
-    ca.score = sM;
-    ca.k0 = 0;
-    ca.n_iters = P.cd_max_iters;
-    ca.P = P;
-    ca.cnt = ctx->cnt;
-    launch_ccd(R, ca, false, s);
-    if ((st = after_launch(ctx, 1))) return st;
-    if (prof) HJCD_CUDA(ctx, cudaEventRecord(ctx->ev[1], s));
-
-    // top-K and perturbed duplication
-    DupArgs da{d_tg, T, d_moff, sM, thM, CM, d_boff, thB, CB, nullptr, P.dup_ratio, P.dup_sigma};
-    launch_topk_dup(R, da, max_m, s);
-    if ((st = after_launch(ctx, 1))) return st;
-    if (prof) HJCD_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
-
-    // PJ-IK
-    LmArgs la{};
-    la.tg = d_tg;
-    la.map = CandMap{nullptr, nullptr, d_boff, T};
-    la.C = CB;
-    la.ld = CB;
-    la.th = thB;
-    la.score = sB;
-    la.perr = pB;
-    la.oerr = oB;
-    la.k0 = 0;
-    la.n_iters = P.lm_max_iters;
-    la.P = P;
-    la.cnt = ctx->cnt;
-    la.queue = ctx->queue;
-    HJCD_CUDA(ctx, cudaMemsetAsync(ctx->queue, 0, sizeof(unsigned long long), s));
-    launch_lm(R, la, false, s);
-    if ((st = after_launch(ctx, 1))) return st;
-    if (prof) HJCD_CUDA(ctx, cudaEventRecord(ctx->ev[3], s));
-
-    // collision filter
-    const bool collide = R.n_sph > 0;
-    if (collide) {
-        CollideArgs cl{};
-        cl.rsph = rob->sph;
-        cl.rsph_body = rob->body;
-        cl.range = rob->range;
-        cl.coarse = rob->coarse;
-        cl.pairs = rob->pairs;
-        cl.n_pairs = rob->n_pairs;
-        cl.scene = sc ? sc->buf : nullptr;
-        cl.n_osph = sc ? sc->n_sph : 0;
-        cl.n_obox = sc ? sc->n_box : 0;
-        cl.C = CB;
-        cl.ld = CB;
-        cl.th = thB;
-        cl.hit = hB;
-        cl.cnt = ctx->cnt;
-        cl.err_flag = ctx->err_flag;
-        launch_collide(R, cl, s);
-        if ((st = after_launch(ctx, 1))) return st;
-    }
-    if (prof) HJCD_CUDA(ctx, cudaEventRecord(ctx->ev[4], s));
-
-    // rank the collision-free candidates
-    RankArgs ra{T, d_boff, thB, CB, sB, pB, oB, collide ? hB : nullptr, top_k, q_out, e_out, c_out};
-    launch_rank(R, ra, max_b, s);
-    if ((st = after_launch(ctx, 1))) return st;
-    if (prof) {
-        HJCD_CUDA(ctx, cudaEventRecord(ctx->ev[5], s));
-        ctx->ev_valid = true;
-    }
-
-    const bool sync = !dev_q || !dev_e || !dev_c;
-    if (!dev_q) HJCD_CUDA(ctx, cudaMemcpyAsync(out_q, q_out, sizeof(float) * (size_t)T * top_k * n, cudaMemcpyDeviceToHost, s));
-    if (!dev_e) HJCD_CUDA(ctx, cudaMemcpyAsync(out_err, e_out, sizeof(float) * (size_t)T * top_k * 2, cudaMemcpyDeviceToHost, s));
-    if (!dev_c) HJCD_CUDA(ctx, cudaMemcpyAsync(out_count, c_out, sizeof(int32_t) * (size_t)T, cudaMemcpyDeviceToHost, s));
-    HJCD_CUDA(ctx, cudaEventRecord(ctx->ws_free, s));
-    if (sync) {
-        HJCD_CUDA(ctx, cudaStreamSynchronize(s));
-        int32_t flag = 0;
-        HJCD_CUDA(ctx, cudaMemcpy(&flag, ctx->err_flag, sizeof flag, cudaMemcpyDeviceToHost));
-        if (flag) return fail(ctx, HJCD_ETIMEOUT, "collision kernel: staging wait ran out");
-    }
-    return HJCD_OK;
+    if ((st = make_current(ctx))) return st;
+    return solve_items(ctx, w.data(), n_items, P, (cudaStream_t)stream);
 }
 
 // ---- stages ----------------------------------------------------------------
@@ -677,7 +545,8 @@ static hjcd_status stage_prologue(hjcd_ctx* ctx, int32_t robot_id, int n_targets
     if ((st = ensure_ws(ctx, align_up(sizeof(TargetDesc) * (size_t)n_targets)))) return st;
     HJCD_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ws_free, 0));
     *d_tg = reinterpret_cast<TargetDesc*>(ctx->ws);
-    return pack_device_targets(ctx, targets_pq, n_targets, eps_pos, eps_ori, seed, *d_tg, s);
+    launch_pack_targets(targets_pq, n_targets, nullptr, stage_template(eps_pos, eps_ori, seed, 0, 0, 1, -1), *d_tg, s);
+    return after_launch(ctx, 1);
 }
 
 static hjcd_status check_theta(hjcd_ctx* ctx, const void* p, int64_t n_cand, int64_t ld, const char* what) {
@@ -731,6 +600,7 @@ hjcd_status hjcd_po_ccd(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const fl
     if (k0 < 0 || n_iters < 0) return fail(ctx, HJCD_EINVAL, "k0 and n_iters must be >= 0");
     if (trace && n_iters != 1) return fail(ctx, HJCD_EINVAL, "a trace needs n_iters == 1");
     CcdArgs a{};
+    a.rs = single_robot_set(*rob);
     a.tg = d_tg;
     a.map = CandMap{tgt, cand, nullptr, n_targets};
     a.C = n_cand;
@@ -746,7 +616,7 @@ hjcd_status hjcd_po_ccd(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const fl
     a.P = P;
     if (trace) a.tr = *trace;
     a.cnt = ctx->cnt;
-    launch_ccd(rob->P, a, trace != nullptr, s);
+    launch_ccd(a, trace != nullptr, s);
     if ((st = after_launch(ctx, n_cand > 0 ? 1 : 0))) return st;
     HJCD_CUDA(ctx, cudaEventRecord(ctx->ws_free, s));
     return HJCD_OK;
@@ -782,23 +652,19 @@ hjcd_status hjcd_topk_dup(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const 
         max_m = std::max(max_m, (int)m);
     }
     if (mo[n_targets] > ld_M || bo[n_targets] > ld_B) return fail(ctx, HJCD_EINVAL, "ld smaller than the candidate count");
-    // a TargetDesc per target carrying only the key and the target index
+    // a TargetDesc per target carrying only the key, the target index and robot 0
     if ((st = ensure_ws(ctx, align_up(sizeof(TargetDesc) * (size_t)n_targets)))) return st;
     HJCD_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ws_free, 0));
     TargetDesc* d_tg = reinterpret_cast<TargetDesc*>(ctx->ws);
     std::vector<TargetDesc> h(n_targets);
     for (int t = 0; t < n_targets; ++t) {
-        h[t] = TargetDesc{};
-        h[t].q[0] = 1.0f;
-        h[t].eps_pos = 1.0f;
-        h[t].eps_ori = 1.0f;
-        h[t].key[0] = (uint32_t)(seed & 0xffffffffu);
-        h[t].key[1] = (uint32_t)(seed >> 32);
+        h[t] = stage_template(1.0f, 1.0f, seed, 0, 0, 1, -1);
         h[t].t_local = t;
     }
     HJCD_CUDA(ctx, cudaMemcpyAsync(d_tg, h.data(), sizeof(TargetDesc) * h.size(), cudaMemcpyHostToDevice, s));
-    DupArgs a{d_tg, n_targets, m_off, score_M, theta_M, ld_M, b_off, theta_B, ld_B, src_B, P.dup_ratio, P.dup_sigma};
-    launch_topk_dup(rob->P, a, max_m, s);
+    DupArgs a{single_robot_set(*rob), d_tg, n_targets, m_off, score_M, theta_M, ld_M, b_off, theta_B, ld_B, src_B,
+              P.dup_ratio, P.dup_sigma};
+    launch_topk_dup(a, max_m, s);
     if ((st = after_launch(ctx, 1))) return st;
     HJCD_CUDA(ctx, cudaStreamSynchronize(s));  // the host staging of the key table must outlive the copy
     HJCD_CUDA(ctx, cudaEventRecord(ctx->ws_free, s));
@@ -820,6 +686,7 @@ hjcd_status hjcd_pjik(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const floa
     if (k0 < 0 || n_iters < 0) return fail(ctx, HJCD_EINVAL, "k0 and n_iters must be >= 0");
     if (trace && n_iters != 1) return fail(ctx, HJCD_EINVAL, "a trace needs n_iters == 1");
     LmArgs a{};
+    a.rs = single_robot_set(*rob);
     a.tg = d_tg;
     a.map = CandMap{tgt, cand, nullptr, n_targets};
     a.C = n_cand;
@@ -836,7 +703,7 @@ hjcd_status hjcd_pjik(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const floa
     a.cnt = ctx->cnt;
     a.queue = ctx->queue;
     HJCD_CUDA(ctx, cudaMemsetAsync(ctx->queue, 0, sizeof(unsigned long long), s));
-    launch_lm(rob->P, a, trace != nullptr, s);
+    launch_lm(a, trace != nullptr, s);
     if ((st = after_launch(ctx, n_cand > 0 ? 1 : 0))) return st;
     HJCD_CUDA(ctx, cudaEventRecord(ctx->ws_free, s));
     return HJCD_OK;
@@ -861,22 +728,17 @@ hjcd_status hjcd_collide(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int6
     }
     HJCD_CUDA(ctx, cudaMemsetAsync(ctx->err_flag, 0, sizeof(int32_t), s));
     CollideArgs a{};
-    a.rsph = rob->sph;
-    a.rsph_body = rob->body;
-    a.range = rob->range;
-    a.coarse = rob->coarse;
-    a.pairs = rob->pairs;
-    a.n_pairs = rob->n_pairs;
-    a.scene = sc ? sc->buf : nullptr;
-    a.n_osph = sc ? sc->n_sph : 0;
-    a.n_obox = sc ? sc->n_box : 0;
+    a.rs = single_robot_set(*rob);
+    a.scenes = sc ? sc->d_dev : nullptr;
+    a.n_scenes = sc ? 1 : 0;
+    a.max_obj4 = sc ? sc->dev.n_sph + 2 * sc->dev.n_box : 0;
     a.C = n_cand;
     a.ld = ld;
     a.th = theta;
     a.hit = hit;
     a.cnt = ctx->cnt;
     a.err_flag = ctx->err_flag;
-    launch_collide(rob->P, a, s);
+    launch_collide(a, s);
     return after_launch(ctx, 1);
 }
 
@@ -904,8 +766,9 @@ hjcd_status hjcd_rank(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const int6
         max_b = std::max(max_b, (int)b);
     }
     if (bo[n_targets] > ld) return fail(ctx, HJCD_EINVAL, "ld smaller than the candidate count");
-    RankArgs a{n_targets, b_off, theta_B, ld, score, perr, oerr, hit, top_k, out_q, out_err, out_count};
-    launch_rank(rob->P, a, max_b, s);
+    RankArgs a{single_robot_set(*rob), nullptr, n_targets, b_off, theta_B, ld, score, perr, oerr, hit, top_k,
+               nullptr, out_q, out_err, out_count};
+    launch_rank(a, max_b, s);
     return after_launch(ctx, 1);
 }
 
@@ -942,7 +805,7 @@ hjcd_status hjcd_counters(hjcd_ctx* ctx, uint64_t out[8], int reset) {
     return HJCD_OK;
 }
 
-int64_t hjcd_launch_count(const hjcd_ctx* ctx) { return ctx ? ctx->launches : 0; }
+int64_t hjcd_launch_count(const hjcd_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
 
 hjcd_status hjcd_ffma_probe(hjcd_ctx* ctx, int iters, double* tflops, void* stream) {
     if (!ctx || !tflops || iters < 1) return HJCD_EINVAL;
@@ -1077,10 +940,15 @@ extern "C" hjcd_status hjcd_solve_noalloc(hjcd_ctx* ctx, int32_t robot_id, int32
     HJCD_CUDA(ctx, cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s));
     HJCD_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
     k_uniform_offsets<<<(T + 256) / 256, 256, 0, s>>>(d_moff, d_boff, T, M, B);
-    launch_pack_targets(targets_pq, T, opts->eps_pos, opts->eps_ori, opts->seed, nullptr, d_tg, s);
+    launch_pack_targets(targets_pq, T, nullptr,
+                        stage_template(opts->eps_pos, opts->eps_ori, opts->seed, P.cd_max_iters, P.lm_max_iters, top_k,
+                                       sc ? 0 : -1),
+                        d_tg, s);
     if ((st = after_launch(ctx, 2))) return st;
 
+    const RobotSet rs = single_robot_set(*rob);
     CcdArgs ca{};
+    ca.rs = rs;
     ca.tg = d_tg;
     ca.map = CandMap{nullptr, nullptr, d_moff, T};
     ca.C = CM;
@@ -1089,10 +957,11 @@ extern "C" hjcd_status hjcd_solve_noalloc(hjcd_ctx* ctx, int32_t robot_id, int32
     ca.score = sM;
     ca.n_iters = P.cd_max_iters;
     ca.P = P;
-    launch_ccd(R, ca, false, s);
-    DupArgs da{d_tg, T, d_moff, sM, thM, CM, d_boff, thB, CB, nullptr, P.dup_ratio, P.dup_sigma};
-    launch_topk_dup(R, da, M, s);
+    launch_ccd(ca, false, s);
+    DupArgs da{rs, d_tg, T, d_moff, sM, thM, CM, d_boff, thB, CB, nullptr, P.dup_ratio, P.dup_sigma};
+    launch_topk_dup(da, M, s);
     LmArgs la{};
+    la.rs = rs;
     la.tg = d_tg;
     la.map = CandMap{nullptr, nullptr, d_boff, T};
     la.C = CB;
@@ -1104,27 +973,25 @@ extern "C" hjcd_status hjcd_solve_noalloc(hjcd_ctx* ctx, int32_t robot_id, int32
     la.n_iters = P.lm_max_iters;
     la.P = P;
     la.queue = queue;
-    launch_lm(R, la, false, s);
+    launch_lm(la, false, s);
     const bool collide = R.n_sph > 0;
     if (collide) {
         CollideArgs cl{};
-        cl.rsph = rob->sph;
-        cl.rsph_body = rob->body;
-        cl.range = rob->range;
-        cl.coarse = rob->coarse;
-        cl.pairs = rob->pairs;
-        cl.n_pairs = rob->n_pairs;
-        cl.scene = sc ? sc->buf : nullptr;
-        cl.n_osph = sc ? sc->n_sph : 0;
-        cl.n_obox = sc ? sc->n_box : 0;
+        cl.rs = rs;
+        cl.scenes = sc ? sc->d_dev : nullptr;
+        cl.n_scenes = sc ? 1 : 0;
+        cl.max_obj4 = sc ? sc->dev.n_sph + 2 * sc->dev.n_box : 0;
+        cl.tg = d_tg;
+        cl.map = CandMap{nullptr, nullptr, d_boff, T};
         cl.C = CB;
         cl.ld = CB;
         cl.th = thB;
         cl.hit = hB;
         cl.err_flag = flag;
-        launch_collide(R, cl, s);
+        launch_collide(cl, s);
     }
-    RankArgs ra{T, d_boff, thB, CB, sB, pB, oB, collide ? hB : nullptr, top_k, out_q, out_err, out_count};
-    launch_rank(R, ra, (int)B, s);
+    RankArgs ra{rs, d_tg, T, d_boff, thB, CB, sB, pB, oB, collide ? hB : nullptr, top_k, nullptr,
+                out_q, out_err, out_count};
+    launch_rank(ra, (int)B, s);
     return after_launch(ctx, collide ? 5 : 4);
 }

@@ -1,9 +1,9 @@
 // hjcd_internal.cuh -- types and device math shared by the HJCD-IK kernels.
 //
 // All arithmetic is binary32.  Joint vectors are structure-of-arrays
-// (theta[j * ld + c]); robot tables travel as a by-value kernel parameter so
-// that their entries are constant-bank operands inside the unrolled joint
-// loops.
+// (theta[j * ld + c]).  One launch may mix robots and scenes: every target
+// row names its robot and scene in the launch's tables, and the kernels copy
+// the (small) kinematic tables of the launch's robots into shared memory.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -15,12 +15,13 @@ namespace hjcd {
 
 constexpr int kMaxDof = HJCD_MAX_DOF;
 constexpr int kMaxBodies = HJCD_MAX_DOF + 2;
+constexpr int kMaxLaunchRobots = HJCD_MAX_BATCH_ROBOTS;  // robots one launch can mix
 
 // Philox stream phases (third counter word, high byte).
 enum : uint32_t { kPhaseSeed = 1, kPhaseCd = 2, kPhaseDup = 3, kPhaseLm = 4 };
 
 // Robot as seen by the kernels: modified-DH table with cos/sin of alpha,
-// limits, flange transform.  Passed by value (param space).
+// limits, flange transform (728 bytes).
 struct RobotParams {
     int32_t n;
     int32_t n_sph;
@@ -29,8 +30,41 @@ struct RobotParams {
     float fl_r[9];  // flange rotation, row-major
     float fl_p[3];  // flange translation
 };
+static_assert(sizeof(RobotParams) % 8 == 0, "RobotParams is copied to shared memory in 8-byte words");
 
-// One target pose with its request's tolerances and random-stream key.
+// Collision tables of a robot in device memory: spheres grouped by body
+// (float4 x y z r in the body frame) with their bodies, per-body
+// [first, count) ranges and bounding spheres, the body pairs checked for
+// self-collision.
+struct RobotDev {
+    const float4* sph;    // [n_sph], grouped by body
+    const int32_t* body;  // [n_sph]
+    const int2* range;    // [n + 2]: first sphere, count
+    const float4* coarse; // [n + 2]: bounding sphere in the body frame (r = 0: no spheres)
+    const int2* pairs;    // [n_pairs]
+    int32_t n_pairs;
+    int32_t n_sph;
+};
+
+// Obstacles of a scene in device memory: spheres (float4) followed by boxes
+// (two float4: lo.xyz, hi.xyz); 16-byte aligned.
+struct SceneDev {
+    const float4* obj;
+    int32_t n_sph, n_box;
+};
+
+// The robots of one launch and the maxima the kernels size shared memory by.
+struct RobotSet {
+    const RobotParams* rp;  // [n] (device)
+    const RobotDev* rd;     // [n] (device; read by the collision kernel only)
+    int32_t n;
+    int32_t n_max;          // largest DoF
+    int32_t ns_max;         // most link spheres
+    int32_t pairs_max;      // most self-collision body pairs
+};
+
+// One target pose with its request's tolerances, random-stream key, robot,
+// scene and iteration caps (64 bytes).
 struct __align__(16) TargetDesc {
     float p[3];
     float eps_pos;
@@ -38,7 +72,26 @@ struct __align__(16) TargetDesc {
     uint32_t key[2];
     int32_t t_local;  // target index inside its request (keys the streams)
     float eps_ori;
+    int32_t robot;     // row of the launch's RobotSet
+    int32_t scene;     // row of the launch's scene table, -1: no obstacles
+    int16_t cd_iters;  // PO-CCD iteration cap
+    int16_t lm_iters;  // PJ-IK iteration cap
+    int32_t top_k;     // solutions returned
 };
+static_assert(sizeof(TargetDesc) == 64, "TargetDesc layout");
+
+// Copy the launch's robot tables into shared memory (all threads of the CTA
+// take part; ends with a barrier).
+__device__ __forceinline__ const RobotParams* stage_robots(void* smem, const RobotSet& rs) {
+    const uint2* src = reinterpret_cast<const uint2*>(rs.rp);
+    uint2* dst = reinterpret_cast<uint2*>(smem);
+    const int words = rs.n * (int)(sizeof(RobotParams) / 8);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+    return reinterpret_cast<const RobotParams*>(smem);
+}
+
+__host__ __device__ constexpr size_t robots_smem_bytes(int n) { return (sizeof(RobotParams) * (size_t)n + 15) / 16 * 16; }
 
 // Candidate -> (target row, candidate index inside the target).
 struct CandMap {
@@ -301,6 +354,7 @@ inline int grid_for(int64_t items, int per_block, int per_sm = 64) {
 // host-side launch entry points (defined in the kernel translation units)
 
 struct CcdArgs {
+    RobotSet rs;
     const TargetDesc* tg;
     CandMap map;
     int64_t C, ld;
@@ -308,20 +362,21 @@ struct CcdArgs {
     float* th_out;
     float *score, *perr, *oerr;
     int32_t* iters;
-    int k0, n_iters;
+    int k0, n_iters;  // n_iters < 0: each target's cd_iters
     hjcd_params P;
     hjcd_ccd_trace tr;
     Counters* cnt;
 };
 
 struct LmArgs {
+    RobotSet rs;
     const TargetDesc* tg;
     CandMap map;
     int64_t C, ld;
     float* th;
     float *score, *perr, *oerr;
     int32_t* iters;
-    int k0, n_iters;
+    int k0, n_iters;  // n_iters < 0: each target's lm_iters
     hjcd_params P;
     hjcd_lm_trace tr;
     Counters* cnt;
@@ -329,6 +384,7 @@ struct LmArgs {
 };
 
 struct DupArgs {
+    RobotSet rs;
     const TargetDesc* tg;
     int32_t T;
     const int64_t* m_off;
@@ -343,7 +399,13 @@ struct DupArgs {
     float sigma;
 };
 
+// Output of target t: solutions at out_q + qe_off[2t] (top_k rows of its
+// robot's n), errors at out_err + qe_off[2t+1] (top_k pairs).  With tg null
+// every target takes top_k and robot 0; with qe_off null the blocks are
+// contiguous in target order.
 struct RankArgs {
+    RobotSet rs;
+    const TargetDesc* tg;
     int32_t T;
     const int64_t* b_off;
     const float* th;
@@ -351,25 +413,24 @@ struct RankArgs {
     const float *score, *perr, *oerr;
     const uint8_t* hit;
     int top_k;
+    const int64_t* qe_off;
     float* out_q;
     float* out_err;
     int32_t* out_count;
 };
 
-// Collision tables in device memory: robot spheres grouped by body
-// (float4 x y z r in the body frame) with their bodies, per-body
-// [first, count) ranges and bounding spheres, the body pairs checked for
-// self-collision; scene spheres (float4) followed by boxes (two float4:
-// lo.xyz, hi.xyz).
+// Collision filter of C candidates.  With tg null every candidate is robot 0
+// against scene 0 (if any); otherwise candidate c belongs to target row
+// map(c), whose robot and scene it uses.  A launch with a single scene
+// stages it into shared memory; with several, obstacles are read from the
+// scene tables directly.
 struct CollideArgs {
-    const float4* rsph;       // [n_sph], grouped by body
-    const int32_t* rsph_body; // [n_sph]
-    const int2* range;        // [n_bodies]: first sphere, count
-    const float4* coarse;     // [n_bodies]: bounding sphere in the body frame (r = 0: no spheres)
-    const int2* pairs;        // [n_pairs]: body pairs checked for self-collision
-    int32_t n_pairs;
-    const float4* scene;      // [n_osph + 2 * n_obox], 16-byte aligned
-    int32_t n_osph, n_obox;
+    RobotSet rs;
+    const SceneDev* scenes;   // [n_scenes] (device)
+    int32_t n_scenes;
+    int32_t max_obj4;         // largest n_sph + 2 n_box over the scenes
+    const TargetDesc* tg;
+    CandMap map;
     int64_t C, ld;
     const float* th;
     uint8_t* hit;
@@ -377,16 +438,19 @@ struct CollideArgs {
     int32_t* err_flag;        // set when the bounded wait for the staged tables runs out
 };
 
-void launch_pack_targets(const float* pq7, int T, float eps_pos, float eps_ori, uint64_t seed, const int32_t* t_local,
-                         TargetDesc* out, cudaStream_t st);
+// Fill p and q of the target rows from [T][7] poses (quaternion normalised; a
+// zero or non-finite one marks the row invalid with eps_pos = -1).  With meta
+// non-null the other fields come from meta[t], else from tmpl with t_local = t.
+void launch_pack_targets(const float* pq7, int T, const TargetDesc* meta, const TargetDesc& tmpl, TargetDesc* out,
+                         cudaStream_t st);
 void launch_fk(const RobotParams& R, int64_t C, const float* th, int64_t ld, float* out, cudaStream_t st);
 void launch_sample(const RobotParams& R, uint64_t seed, CandMap map, int64_t C, float* th, int64_t ld,
                    cudaStream_t st);
-void launch_ccd(const RobotParams& R, const CcdArgs& A, bool trace, cudaStream_t st);
-void launch_lm(const RobotParams& R, const LmArgs& A, bool trace, cudaStream_t st);
-void launch_topk_dup(const RobotParams& R, const DupArgs& A, int max_m, cudaStream_t st);
-void launch_rank(const RobotParams& R, const RankArgs& A, int max_b, cudaStream_t st);
-void launch_collide(const RobotParams& R, const CollideArgs& A, cudaStream_t st);
+void launch_ccd(const CcdArgs& A, bool trace, cudaStream_t st);
+void launch_lm(const LmArgs& A, bool trace, cudaStream_t st);
+void launch_topk_dup(const DupArgs& A, int max_m, cudaStream_t st);
+void launch_rank(const RankArgs& A, int max_b, cudaStream_t st);
+void launch_collide(const CollideArgs& A, cudaStream_t st);
 void launch_ffma(float* sink, int iters, int blocks, cudaStream_t st);
 int ffma_flops_per_thread_iter();
 

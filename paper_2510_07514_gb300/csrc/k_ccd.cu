@@ -15,6 +15,8 @@
 // kinematics pass in a column of shared memory ([quantity][thread], so the
 // accesses of a warp hit 32 different banks); joint loops are not unrolled,
 // which keeps the kernel small enough for the instruction cache at any n.
+// The robot tables of the launch sit in shared memory in front of the
+// columns; each candidate uses its target's robot.
 #include "hjcd_internal.cuh"
 
 namespace hjcd {
@@ -44,11 +46,11 @@ __device__ __forceinline__ void sample_seed(const RobotParams& R, const TargetDe
 }
 
 template <bool TRACE>
-__global__ void __launch_bounds__(kCcdThreads, 4) k_ccd(const RobotParams R, const CcdArgs A) {
-    extern __shared__ float sm[];
+__global__ void __launch_bounds__(kCcdThreads, 4) k_ccd(const CcdArgs A) {
+    extern __shared__ __align__(16) float sm[];
+    const RobotParams* rob = stage_robots(sm, A.rs);
+    float* const colbase = sm + robots_smem_bytes(A.rs.n) / sizeof(float) + threadIdx.x;
     const hjcd_params& P = A.P;
-    const int n = R.n;
-    const Col col{sm + threadIdx.x, n};
     const float pe2 = P.proj_eps * P.proj_eps;
     const float one_m_tie = 1.0f - P.cd_tie;
     unsigned long long n_it = 0, n_cand = 0;
@@ -58,6 +60,9 @@ __global__ void __launch_bounds__(kCcdThreads, 4) k_ccd(const RobotParams R, con
         int32_t t, s;
         if (!A.map.lookup(c, t, s)) continue;
         const TargetDesc T = A.tg[t];
+        const RobotParams& R = rob[T.robot];
+        const int n = R.n;
+        const Col col{colbase, n};
         const V3 pt = v3(T.p[0], T.p[1], T.p[2]);
         ++n_cand;
 
@@ -68,9 +73,10 @@ __global__ void __launch_bounds__(kCcdThreads, 4) k_ccd(const RobotParams R, con
             sample_seed(R, T, (uint32_t)s, col);
         }
 
+        const int cap = A.n_iters >= 0 ? A.n_iters : T.cd_iters;
         float delta_k = P.cd_delta0 * powf(P.cd_rho, (float)A.k0);
         const float inv_p2 = 1.0f / (T.eps_pos * T.eps_pos), inv_o2 = 1.0f / (T.eps_ori * T.eps_ori);
-        int iters = A.n_iters;
+        int iters = cap;
         float ep2 = 0.0f, eo = 0.0f;
         const bool valid = T.eps_pos > 0.0f;
 
@@ -98,7 +104,7 @@ __global__ void __launch_bounds__(kCcdThreads, 4) k_ccd(const RobotParams R, con
                 iters = kk;
                 break;
             }
-            if (kk == A.n_iters) break;
+            if (kk == cap) break;
             const int k = A.k0 + kk;
             const float ep0 = sqrtf(ep2);
 
@@ -270,23 +276,23 @@ __global__ void __launch_bounds__(kCcdThreads) k_sample(const RobotParams R, uin
 }
 
 template <bool TRACE>
-void launch_ccd_t(const RobotParams& R, const CcdArgs& A, cudaStream_t st) {
-    const size_t smem = sizeof(float) * 7 * R.n * kCcdThreads;
+void launch_ccd_t(const CcdArgs& A, cudaStream_t st) {
+    const size_t smem = robots_smem_bytes(A.rs.n) + sizeof(float) * 7 * A.rs.n_max * kCcdThreads;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_ccd<TRACE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(float) * 7 * kMaxDof * kCcdThreads));
+                             (int)(robots_smem_bytes(kMaxLaunchRobots) + sizeof(float) * 7 * kMaxDof * kCcdThreads));
         attr = true;
     }
-    k_ccd<TRACE><<<grid_for(A.C, kCcdThreads, 16), kCcdThreads, smem, st>>>(R, A);
+    k_ccd<TRACE><<<grid_for(A.C, kCcdThreads, 16), kCcdThreads, smem, st>>>(A);
 }
 
 }  // namespace
 
-void launch_ccd(const RobotParams& R, const CcdArgs& A, bool trace, cudaStream_t st) {
+void launch_ccd(const CcdArgs& A, bool trace, cudaStream_t st) {
     if (A.C <= 0) return;
-    if (trace) launch_ccd_t<true>(R, A, st);
-    else launch_ccd_t<false>(R, A, st);
+    if (trace) launch_ccd_t<true>(A, st);
+    else launch_ccd_t<false>(A, st);
 }
 
 void launch_sample(const RobotParams& R, uint64_t seed, CandMap map, int64_t C, float* th, int64_t ld,

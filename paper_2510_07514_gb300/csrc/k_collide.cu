@@ -14,9 +14,13 @@
 // spread over the warp.  Obstacles: lanes over obstacles (32 at a time) for
 // the bounding test of one body; the overlapping obstacles are compacted into
 // a list and their fine tests (list x the body's spheres) spread over the
-// warp.  The warp stops at the first overlap.  Obstacles (spheres, then boxes)
-// are staged once per CTA into shared memory by one bulk asynchronous copy
-// (TMA, cp.async.bulk) completing on an mbarrier.
+// warp.  The warp stops at the first overlap.  When the launch has a single
+// scene, its obstacles (spheres, then boxes) are staged once per CTA into
+// shared memory by one bulk asynchronous copy (TMA, cp.async.bulk) completing
+// on an mbarrier; a launch mixing scenes reads each candidate's obstacles from
+// its scene table.  Each candidate uses its target's robot: the kinematic
+// tables of the launch's robots sit in shared memory, a warp reloads its
+// lanes' link spheres when its candidate's robot changes.
 //
 // Overlap: |c1 - c2|^2 < (r1 + r2)^2 for spheres; for a box, the squared
 // distance from the centre to its clamp into the box below r^2.
@@ -89,88 +93,126 @@ __device__ __forceinline__ bool sph_box(float4 a, float4 lo, float4 hi) {
     return fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < a.w * a.w;
 }
 
-// shared-memory layout of a CTA
-struct CollideSmem {
-    float4* scene;   // [n_osph + 2 n_obox]
-    uint64_t* bar;
-    int2* range;     // [nb]
-    int2* pairs;     // [n_pairs]
-    float4* wsph;    // per warp: [ns] world fine spheres
-    float4* wco;     // per warp: [nb] world bounding spheres
-    int* list;       // per warp: [32] compacted obstacle / pair indices
-};
-
+// shared-memory layout of a CTA: staged obstacles, mbarrier, robot tables,
+// then per warp the world-frame fine spheres, bounding spheres and a list
 struct CollideLayout {
-    uint32_t bar, range, pairs, warp, warp_bytes, total;
+    uint32_t bar, robots, warp, warp_bytes, total;
 };
 
-__host__ __device__ __forceinline__ CollideLayout collide_smem_layout(int n_obj4, int nb, int n_pairs, int ns) {
+__host__ __device__ __forceinline__ CollideLayout collide_smem_layout(int n_obj4, int n_robots, int nb, int ns) {
     CollideLayout L;
     L.bar = 16u * (uint32_t)n_obj4;
-    L.range = L.bar + 16u;
-    L.pairs = L.range + 8u * (uint32_t)nb;
-    L.warp = (L.pairs + 8u * (uint32_t)n_pairs + 15u) / 16u * 16u;
+    L.robots = L.bar + 16u;
+    L.warp = L.robots + (uint32_t)robots_smem_bytes(n_robots);
     L.warp_bytes = 16u * (uint32_t)(ns + nb) + 4u * 32u;
     L.total = L.warp + kWarpsPerBlock * L.warp_bytes;
     return L;
 }
 
-template <int SPL>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const RobotParams R, const CollideArgs A) {
+template <int SPL, bool STAGED>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int n_obj4 = A.n_osph + 2 * A.n_obox;
-    const int ns = R.n_sph, n = R.n, nb = R.n + 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const CollideLayout L = collide_smem_layout(n_obj4, nb, A.n_pairs, ns);
-    CollideSmem S;
-    S.scene = reinterpret_cast<float4*>(smem);
-    S.bar = reinterpret_cast<uint64_t*>(smem + L.bar);
-    S.range = reinterpret_cast<int2*>(smem + L.range);
-    S.pairs = reinterpret_cast<int2*>(smem + L.pairs);
-    unsigned char* wb = smem + L.warp + warp * L.warp_bytes;
-    S.wsph = reinterpret_cast<float4*>(wb);
-    S.wco = S.wsph + ns;
-    S.list = reinterpret_cast<int*>(S.wco + nb);
-
-    // stage the obstacles with one bulk copy; the small robot tables with plain loads
-    const uint32_t bytes = 16u * (uint32_t)n_obj4;
-    if (threadIdx.x == 0) mbar_init(S.bar, 1);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (bytes > 0) {
-            mbar_arrive_expect_tx(S.bar, bytes);
-            bulk_g2s(S.scene, A.scene, bytes, S.bar);
-        } else {
-            mbar_arrive(S.bar);
-        }
-    }
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) S.range[i] = A.range[i];
-    for (int i = threadIdx.x; i < A.n_pairs; i += blockDim.x) S.pairs[i] = A.pairs[i];
-    const bool staged = mbar_wait_bounded(S.bar, 0);
-    if (__syncthreads_or(!staged)) {
-        // give up: flag the error, give the copy one more bounded wait, return
-        if (threadIdx.x == 0) {
-            atomicExch(A.err_flag, 1);
-            mbar_wait_bounded(S.bar, 0);
-        }
+    const SceneDev sc0 = A.n_scenes > 0 ? A.scenes[0] : SceneDev{nullptr, 0, 0};
+    const int n_obj4 = STAGED ? sc0.n_sph + 2 * sc0.n_box : 0;
+    if (n_obj4 > (STAGED ? A.max_obj4 : 0)) {  // the scene outgrew the shared memory the host sized
+        if (threadIdx.x == 0) atomicExch(A.err_flag, 2);
         return;
     }
+    const int nb_max = A.rs.n_max + 2;
+    const CollideLayout L = collide_smem_layout(n_obj4, A.rs.n, nb_max, A.rs.ns_max);
+    float4* s_scene = reinterpret_cast<float4*>(smem);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
+    unsigned char* wb = smem + L.warp + warp * L.warp_bytes;
+    float4* wsph = reinterpret_cast<float4*>(wb);
+    float4* wco = wsph + A.rs.ns_max;
+    int* list = reinterpret_cast<int*>(wco + nb_max);
 
-    // this lane's fine spheres (body frame) and bodies; its bounding sphere (body lane)
+    // stage the obstacles with one bulk copy, the robots' kinematic tables with plain loads
+    const uint32_t bytes = 16u * (uint32_t)n_obj4;
+    if (STAGED) {
+        if (threadIdx.x == 0) mbar_init(bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (bytes > 0) {
+                mbar_arrive_expect_tx(bar, bytes);
+                bulk_g2s(s_scene, sc0.obj, bytes, bar);
+            } else {
+                mbar_arrive(bar);
+            }
+        }
+    }
+    const RobotParams* rob = stage_robots(smem + L.robots, A.rs);
+    if (STAGED) {
+        const bool staged = mbar_wait_bounded(bar, 0);
+        if (__syncthreads_or(!staged)) {
+            // give up: flag the error, give the copy one more bounded wait, return
+            if (threadIdx.x == 0) {
+                atomicExch(A.err_flag, 1);
+                mbar_wait_bounded(bar, 0);
+            }
+            return;
+        }
+    }
+
+    // this lane's fine spheres (body frame) and bodies, its bounding sphere
+    // (body lane), for the robot of the warp's current candidate
     float4 ls[SPL];
     int lb[SPL];
-#pragma unroll
-    for (int q = 0; q < SPL; ++q) {
-        const int i = lane + 32 * q;
-        lb[q] = i < ns ? A.rsph_body[i] : -1;
-        ls[q] = i < ns ? A.rsph[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    const float4 lco = lane < nb ? A.coarse[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 lco = make_float4(0.f, 0.f, 0.f, 0.f);
+    int cur = -1, n = 0, nb = 0, ns = 0, n_pairs = 0;
+    RobotDev rd{};
 
     unsigned long long tests = 0, btests = 0, ncand = 0;
     const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
     for (int64_t c = (int64_t)blockIdx.x * kWarpsPerBlock + warp; c < A.C; c += nwarps) {
+        int rid = 0, sid = A.n_scenes > 0 ? 0 : -1;
+        if (A.tg) {
+            int32_t t, s;
+            bool ok = A.map.lookup(c, t, s);
+            if (ok) {
+                const TargetDesc& Td = A.tg[t];
+                rid = Td.robot;
+                sid = Td.scene;
+                ok = Td.eps_pos > 0.0f;
+            }
+            if (!ok) {  // no such target, or an invalid one: never ranked
+                if (lane == 0) A.hit[c] = 1;
+                continue;
+            }
+        }
+        if (rid != cur) {
+            cur = rid;
+            rd = A.rs.rd[rid];
+            n = rob[rid].n;
+            nb = n + 2;
+            ns = rd.n_sph;
+            n_pairs = rd.n_pairs;
+#pragma unroll
+            for (int q = 0; q < SPL; ++q) {
+                const int i = lane + 32 * q;
+                lb[q] = i < ns ? __ldg(rd.body + i) : -1;
+                ls[q] = i < ns ? __ldg(rd.sph + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            lco = lane < nb ? __ldg(rd.coarse + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const RobotParams& R = rob[rid];
+        const float4* obj = nullptr;
+        int n_osph = 0, n_obox = 0;
+        if (sid >= 0) {
+            if (STAGED) {
+                obj = s_scene;
+                n_osph = sc0.n_sph;
+                n_obox = sc0.n_box;
+            } else {
+                const SceneDev sd = A.scenes[sid];
+                obj = sd.obj;
+                n_osph = sd.n_sph;
+                n_obox = sd.n_box;
+            }
+        }
+
         // world frame: body 0 is the base (identity)
         float4 ws[SPL];
 #pragma unroll
@@ -189,36 +231,36 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const RobotPara
 #pragma unroll
         for (int q = 0; q < SPL; ++q) {
             if (lb[q] == n + 1) ws[q] = to_world(E, ls[q]);
-            if (lb[q] >= 0) S.wsph[lane + 32 * q] = ws[q];
+            if (lb[q] >= 0) wsph[lane + 32 * q] = ws[q];
         }
         if (lane == n + 1) wc = to_world(E, lco);
-        if (lane < nb) S.wco[lane] = wc;
+        if (lane < nb) wco[lane] = wc;
         __syncwarp();
 
         bool hit = false;
         unsigned long long t_s = 0, t_b = 0;  // tests of this candidate (uniform over the warp)
 
         // self-collision: bounding test per checked body pair, fine pairs spread over the warp
-        for (int p0 = 0; p0 < A.n_pairs && !hit; p0 += 32) {
+        for (int p0 = 0; p0 < n_pairs && !hit; p0 += 32) {
             const int p = p0 + lane;
             int2 pr = make_int2(0, 0);
             bool ch = false;
-            if (p < A.n_pairs) {
-                pr = S.pairs[p];
-                ch = sph_sph(S.wco[pr.x], S.wco[pr.y]);
+            if (p < n_pairs) {
+                pr = __ldg(rd.pairs + p);
+                ch = sph_sph(wco[pr.x], wco[pr.y]);
             }
-            t_s += (unsigned long long)min(32, A.n_pairs - p0);
+            t_s += (unsigned long long)min(32, n_pairs - p0);
             unsigned m = __ballot_sync(0xffffffffu, ch);
             while (m) {
                 const int src = __ffs(m) - 1;
                 m &= m - 1u;
                 const int ba = __shfl_sync(0xffffffffu, pr.x, src), bb = __shfl_sync(0xffffffffu, pr.y, src);
-                const int2 ra = S.range[ba], rb = S.range[bb];
+                const int2 ra = __ldg(rd.range + ba), rb = __ldg(rd.range + bb);
                 const int items = ra.y * rb.y;
                 bool h = false;
                 for (int w = lane; w < items; w += 32) {
                     const int i = w / rb.y;
-                    h |= sph_sph(S.wsph[ra.x + i], S.wsph[rb.x + (w - i * rb.y)]);
+                    h |= sph_sph(wsph[ra.x + i], wsph[rb.x + (w - i * rb.y)]);
                 }
                 t_s += (unsigned long long)items;
                 if (__any_sync(0xffffffffu, h)) {
@@ -229,25 +271,25 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const RobotPara
         }
 
         // obstacle spheres: 32 obstacles at a time, one body at a time
-        for (int o0 = 0; o0 < A.n_osph && !hit; o0 += 32) {
+        for (int o0 = 0; o0 < n_osph && !hit; o0 += 32) {
             const int o = o0 + lane;
-            const bool valid = o < A.n_osph;
-            const float4 s = valid ? S.scene[o] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const int nvalid = min(32, A.n_osph - o0);
+            const bool valid = o < n_osph;
+            const float4 s = valid ? obj[o] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int nvalid = min(32, n_osph - o0);
             for (int b = 0; b < nb && !hit; ++b) {
-                const int2 rg = S.range[b];
+                const int2 rg = __ldg(rd.range + b);
                 if (rg.y == 0) continue;
-                const bool ch = valid && sph_sph(S.wco[b], s);
+                const bool ch = valid && sph_sph(wco[b], s);
                 t_s += (unsigned long long)nvalid;
                 const unsigned m = __ballot_sync(0xffffffffu, ch);
                 if (!m) continue;
-                if (ch) S.list[__popc(m & lt)] = o;
+                if (ch) list[__popc(m & lt)] = o;
                 __syncwarp();
                 const int items = __popc(m) * rg.y;
                 bool h = false;
                 for (int w = lane; w < items; w += 32) {
                     const int k = w / rg.y;
-                    h |= sph_sph(S.wsph[rg.x + (w - k * rg.y)], S.scene[S.list[k]]);
+                    h |= sph_sph(wsph[rg.x + (w - k * rg.y)], obj[list[k]]);
                 }
                 t_s += (unsigned long long)items;
                 hit = __any_sync(0xffffffffu, h);
@@ -256,27 +298,27 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const RobotPara
         }
 
         // obstacle boxes
-        const float4* box = S.scene + A.n_osph;
-        for (int o0 = 0; o0 < A.n_obox && !hit; o0 += 32) {
+        const float4* box = obj + n_osph;
+        for (int o0 = 0; o0 < n_obox && !hit; o0 += 32) {
             const int o = o0 + lane;
-            const bool valid = o < A.n_obox;
+            const bool valid = o < n_obox;
             const float4 lo = valid ? box[2 * o] : make_float4(0.f, 0.f, 0.f, 0.f);
             const float4 hi = valid ? box[2 * o + 1] : lo;
-            const int nvalid = min(32, A.n_obox - o0);
+            const int nvalid = min(32, n_obox - o0);
             for (int b = 0; b < nb && !hit; ++b) {
-                const int2 rg = S.range[b];
+                const int2 rg = __ldg(rd.range + b);
                 if (rg.y == 0) continue;
-                const bool ch = valid && sph_box(S.wco[b], lo, hi);
+                const bool ch = valid && sph_box(wco[b], lo, hi);
                 t_b += (unsigned long long)nvalid;
                 const unsigned m = __ballot_sync(0xffffffffu, ch);
                 if (!m) continue;
-                if (ch) S.list[__popc(m & lt)] = o;
+                if (ch) list[__popc(m & lt)] = o;
                 __syncwarp();
                 const int items = __popc(m) * rg.y;
                 bool h = false;
                 for (int w = lane; w < items; w += 32) {
-                    const int k = w / rg.y, bo = S.list[k];
-                    h |= sph_box(S.wsph[rg.x + (w - k * rg.y)], box[2 * bo], box[2 * bo + 1]);
+                    const int k = w / rg.y, bo = list[k];
+                    h |= sph_box(wsph[rg.x + (w - k * rg.y)], box[2 * bo], box[2 * bo + 1]);
                 }
                 t_b += (unsigned long long)items;
                 hit = __any_sync(0xffffffffu, h);
@@ -299,26 +341,35 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const RobotPara
     }
 }
 
-template <int SPL>
-void launch_collide_t(const RobotParams& R, const CollideArgs& A, cudaStream_t st) {
-    const size_t smem = collide_smem_layout(A.n_osph + 2 * A.n_obox, R.n + 2, A.n_pairs, R.n_sph).total;
+template <int SPL, bool STAGED>
+void launch_collide_t(const CollideArgs& A, int n_obj4, cudaStream_t st) {
+    const size_t smem = collide_smem_layout(STAGED ? n_obj4 : 0, A.rs.n, A.rs.n_max + 2, A.rs.ns_max).total;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_collide<SPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncSetAttribute(k_collide<SPL, STAGED>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         attr_set = true;
     }
     const int g = grid_for(A.C, kWarpsPerBlock, 8);
-    k_collide<SPL><<<g, kWarpsPerBlock * 32, smem, st>>>(R, A);
+    k_collide<SPL, STAGED><<<g, kWarpsPerBlock * 32, smem, st>>>(A);
+}
+
+template <bool STAGED>
+void launch_collide_s(const CollideArgs& A, int n_obj4, cudaStream_t st) {
+    const int ns = A.rs.ns_max;
+    if (ns <= 32) launch_collide_t<1, STAGED>(A, n_obj4, st);
+    else if (ns <= 64) launch_collide_t<2, STAGED>(A, n_obj4, st);
+    else if (ns <= 128) launch_collide_t<4, STAGED>(A, n_obj4, st);
+    else launch_collide_t<8, STAGED>(A, n_obj4, st);
 }
 
 }  // namespace
 
-void launch_collide(const RobotParams& R, const CollideArgs& A, cudaStream_t st) {
-    if (A.C <= 0 || R.n_sph <= 0) return;
-    if (R.n_sph <= 32) launch_collide_t<1>(R, A, st);
-    else if (R.n_sph <= 64) launch_collide_t<2>(R, A, st);
-    else if (R.n_sph <= 128) launch_collide_t<4>(R, A, st);
-    else launch_collide_t<8>(R, A, st);
+// A single scene is staged (its object count, n_sph + 2 n_box, is given by
+// max_obj4); several are read from their tables.
+void launch_collide(const CollideArgs& A, cudaStream_t st) {
+    if (A.C <= 0 || A.rs.ns_max <= 0) return;
+    if (A.n_scenes == 1) launch_collide_s<true>(A, A.max_obj4, st);
+    else launch_collide_s<false>(A, 0, st);
 }
 
 }  // namespace hjcd

@@ -24,8 +24,11 @@
 // that lowered its cost -- the same step the sequential search accepts.
 // Per-lane state (joint vector, trial direction, weighted Jacobian, W, W r,
 // cost, target row, trial outcomes) lives in shared memory as structure of
-// arrays over the lanes; joint loops are not unrolled, which keeps the
-// kernel small enough for the instruction cache at any n.
+// arrays over the lanes, laid out for the largest chain of the launch; joint
+// loops are not unrolled, which keeps the kernel small enough for the
+// instruction cache at any n.  Each candidate uses its target's robot (the
+// launch's robot tables sit in shared memory), also when another lane
+// evaluates one of its trials.
 #include <algorithm>
 
 #include "hjcd_internal.cuh"
@@ -42,7 +45,8 @@ __host__ __device__ constexpr int tri(int r, int c) { return r * (r + 1) / 2 + c
 // words of per-warp shared state for an n-joint chain
 __host__ __device__ constexpr int lm_warp_words(int n) { return (8 * n + 14) * 32 + kMaxTrials * 32 / 4 + 32; }
 
-// Per-warp state, field[...][lane] (each lane's own accesses conflict-free).
+// Per-warp state, field[...][lane] (each lane's own accesses conflict-free);
+// n is the layout's chain length (the launch's largest).
 struct LmW {
     float* f;
     int n;
@@ -139,7 +143,7 @@ __device__ __forceinline__ void take_step(const RobotParams& R, const LmW& S, in
 }
 
 // Trials i = i0 .. A of every lane in `mask`, spread over the warp; results in S.ok(i, lane).
-__device__ __forceinline__ unsigned long long warp_trials(const RobotParams& R, const TargetDesc* tg, const LmW& S,
+__device__ __forceinline__ unsigned long long warp_trials(const RobotParams* rob, const TargetDesc* tg, const LmW& S,
                                                           unsigned mask, int lane, int i0, int A, float beta) {
     const int per = A + 1 - i0;
     if (!mask || per <= 0) return 0;
@@ -150,7 +154,7 @@ __device__ __forceinline__ unsigned long long warp_trials(const RobotParams& R, 
     for (int w = lane; w < items; w += 32) {
         const int s = S.list(w / per), i = i0 + w % per;
         const TargetDesc Ts = tg[S.t(s)];
-        S.ok(i, s) = trial_cost(R, Ts, S, s, ls_alpha(i, beta)) < S.cost0(s) ? 1 : 0;
+        S.ok(i, s) = trial_cost(rob[Ts.robot], Ts, S, s, ls_alpha(i, beta)) < S.cost0(s) ? 1 : 0;
         ++cnt;
     }
     __syncwarp();
@@ -158,11 +162,11 @@ __device__ __forceinline__ unsigned long long warp_trials(const RobotParams& R, 
 }
 
 template <bool TRACE>
-__global__ void __launch_bounds__(kLmWarps * 32, 4) k_lm(const RobotParams R, const LmArgs A) {
+__global__ void __launch_bounds__(kLmWarps * 32, 4) k_lm(const LmArgs A) {
     extern __shared__ __align__(16) float smem_f[];
+    const RobotParams* rob = stage_robots(smem_f, A.rs);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = R.n;
-    const LmW S{smem_f + warp * lm_warp_words(n), n};
+    const LmW S{smem_f + robots_smem_bytes(A.rs.n) / sizeof(float) + warp * lm_warp_words(A.rs.n_max), A.rs.n_max};
 
     const hjcd_params& P = A.P;
     const float Rt = P.lm_trust_R;
@@ -170,7 +174,7 @@ __global__ void __launch_bounds__(kLmWarps * 32, 4) k_lm(const RobotParams R, co
 
     bool has = false;
     int64_t c = 0;
-    int32_t t = 0, s = 0, kk = 0;
+    int32_t t = 0, s = 0, kk = 0, cap = 0;
     TargetDesc T{};
 
     for (;;) {
@@ -186,15 +190,17 @@ __global__ void __launch_bounds__(kLmWarps * 32, 4) k_lm(const RobotParams R, co
                 if (c < A.C && A.map.lookup(c, t, s)) {
                     T = A.tg[t];
                     kk = 0;
+                    cap = A.n_iters >= 0 ? A.n_iters : T.lm_iters;
                     if (T.eps_pos > 0.0f) {
                         has = true;
+                        const int nl = rob[T.robot].n;
 #pragma unroll 1
-                        for (int j = 0; j < n; ++j) S.th(j, lane) = A.th[j * A.ld + c];
+                        for (int j = 0; j < nl; ++j) S.th(j, lane) = A.th[j * A.ld + c];
                     } else {  // invalid target: no iterations, infinite score
                         if (A.score) A.score[c] = __int_as_float(0x7f800000);
                         if (A.perr) A.perr[c] = 0.0f;
                         if (A.oerr) A.oerr[c] = 0.0f;
-                        if (A.iters) A.iters[c] = A.n_iters;
+                        if (A.iters) A.iters[c] = cap;
                     }
                 }
             }
@@ -206,6 +212,8 @@ __global__ void __launch_bounds__(kLmWarps * 32, 4) k_lm(const RobotParams R, co
         }
 
         // ---- phase A: kinematics with frames, residual, LM step (owner) ----
+        const RobotParams& R = rob[T.robot];
+        const int n = R.n;
         bool act = false;
         if (has) {
             // joint origins and axes are parked in the lane's J slots
@@ -226,7 +234,7 @@ __global__ void __launch_bounds__(kLmWarps * 32, 4) k_lm(const RobotParams R, co
             const V3 om = quat_log(quat_error(T, quat_from_frame(E)));
             const V3 epv = pt - E.p;
             const float ep = sqrtf(dot(epv, epv)), eo = sqrtf(dot(om, om));
-            if ((kk > 0 && ep < T.eps_pos && eo < T.eps_ori) || kk == A.n_iters) {
+            if ((kk > 0 && ep < T.eps_pos && eo < T.eps_ori) || kk == cap) {
                 // Alg. 4 break (checked after each update) or the iteration cap
 #pragma unroll 1
                 for (int j = 0; j < n; ++j) A.th[j * A.ld + c] = S.th(j, lane);
@@ -324,7 +332,7 @@ __global__ void __launch_bounds__(kLmWarps * 32, 4) k_lm(const RobotParams R, co
             }
         }
         unsigned fail = __ballot_sync(0xffffffffu, act && branch != 0);
-        n_fk += warp_trials(R, A.tg, S, fail, lane, 1, P.lm_A, P.lm_beta);
+        n_fk += warp_trials(rob, A.tg, S, fail, lane, 1, P.lm_A, P.lm_beta);
         if (act && branch != 0) {
             for (int i = 1; i <= P.lm_A; ++i) {
                 if (S.ok(i, lane)) {
@@ -442,7 +450,7 @@ __global__ void __launch_bounds__(kLmWarps * 32, 4) k_lm(const RobotParams R, co
             }
         }
         fail = __ballot_sync(0xffffffffu, act && branch == 3);
-        n_fk += warp_trials(R, A.tg, S, fail, lane, 0, P.lm_A, P.lm_beta);
+        n_fk += warp_trials(rob, A.tg, S, fail, lane, 0, P.lm_A, P.lm_beta);
         if (act && branch == 3) {
             for (int i = 0; i <= P.lm_A; ++i) {
                 if (S.ok(i, lane)) {
@@ -485,12 +493,13 @@ __global__ void __launch_bounds__(kLmWarps * 32, 4) k_lm(const RobotParams R, co
 }
 
 template <bool TRACE>
-void launch_lm_t(const LmArgs& A, const RobotParams& R, cudaStream_t st) {
-    const size_t smem = sizeof(float) * (size_t)lm_warp_words(R.n) * kLmWarps;
+void launch_lm_t(const LmArgs& A, cudaStream_t st) {
+    const size_t smem = robots_smem_bytes(A.rs.n) + sizeof(float) * (size_t)lm_warp_words(A.rs.n_max) * kLmWarps;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_lm<TRACE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(float) * lm_warp_words(kMaxDof) * kLmWarps));
+                             (int)(robots_smem_bytes(kMaxLaunchRobots) +
+                                   sizeof(float) * lm_warp_words(kMaxDof) * kLmWarps));
         attr = true;
     }
     int per_sm = 0;
@@ -498,15 +507,15 @@ void launch_lm_t(const LmArgs& A, const RobotParams& R, cudaStream_t st) {
     if (per_sm < 1) per_sm = 1;
     const int64_t want = (A.C + 32 * kLmWarps - 1) / (32 * kLmWarps);
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * per_sm));
-    k_lm<TRACE><<<g, kLmWarps * 32, smem, st>>>(R, A);
+    k_lm<TRACE><<<g, kLmWarps * 32, smem, st>>>(A);
 }
 
 }  // namespace
 
-void launch_lm(const RobotParams& R, const LmArgs& A, bool trace, cudaStream_t st) {
+void launch_lm(const LmArgs& A, bool trace, cudaStream_t st) {
     if (A.C <= 0) return;
-    if (trace) launch_lm_t<true>(A, R, st);
-    else launch_lm_t<false>(A, R, st);
+    if (trace) launch_lm_t<true>(A, st);
+    else launch_lm_t<false>(A, st);
 }
 
 }  // namespace hjcd

@@ -46,7 +46,7 @@ __device__ __forceinline__ int pow2_at_least(int m) {
     return N;
 }
 
-__global__ void __launch_bounds__(kSelThreads) k_topk_dup(const RobotParams R, const DupArgs A) {
+__global__ void __launch_bounds__(kSelThreads) k_topk_dup(const DupArgs A) {
     extern __shared__ uint64_t keys[];
     const int t = blockIdx.x;
     const int64_t m0 = A.m_off[t];
@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(kSelThreads) k_topk_dup(const RobotParams R, c
     const int K = max(1, M / A.ratio), copies = M / K, B = K * copies;
     const int64_t b0 = A.b_off[t];
     const TargetDesc T = A.tg[t];
+    const RobotParams& R = A.rs.rp[T.robot];
     const int n = R.n;
     for (int b = threadIdx.x; b < B; b += blockDim.x) {
         const int i = b % K;  // copy r = b / K of kept seed i
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(kSelThreads) k_topk_dup(const RobotParams R, c
     }
 }
 
-__global__ void __launch_bounds__(kSelThreads) k_rank(const RobotParams R, const RankArgs A) {
+__global__ void __launch_bounds__(kSelThreads) k_rank(const RankArgs A) {
     extern __shared__ uint64_t keys[];
     const int t = blockIdx.x;
     const int64_t b0 = A.b_off[t];
@@ -98,23 +99,25 @@ __global__ void __launch_bounds__(kSelThreads) k_rank(const RobotParams R, const
         }
         __syncthreads();
         bitonic_sort(keys, N);
-        const int lim = min(A.top_k, B);
+        const int top_k = A.tg ? A.tg[t].top_k : A.top_k;
+        const int n = A.rs.rp[A.tg ? A.tg[t].robot : 0].n;
+        const int lim = min(top_k, B);
         for (int r = 0; r < lim; ++r) count += keys[r] != kNoKey;
-        const int n = R.n;
+        float* oq = A.out_q + (A.qe_off ? A.qe_off[2 * t] : (int64_t)t * top_k * n);
+        float* oe = A.out_err + (A.qe_off ? A.qe_off[2 * t + 1] : (int64_t)t * top_k * 2);
         for (int q = threadIdx.x; q < count * (n + 2); q += blockDim.x) {
             const int r = q / (n + 2), j = q % (n + 2);
             const int64_t g = b0 + (int64_t)(keys[r] & 0xffffffffu);
-            const int64_t o = (int64_t)t * A.top_k + r;
-            if (j < n) A.out_q[o * n + j] = A.th[j * A.ld + g];
-            else if (j == n) A.out_err[o * 2] = A.perr[g];
-            else A.out_err[o * 2 + 1] = A.oerr[g];
+            if (j < n) oq[r * n + j] = A.th[j * A.ld + g];
+            else if (j == n) oe[r * 2] = A.perr[g];
+            else oe[r * 2 + 1] = A.oerr[g];
         }
     }
     if (threadIdx.x == 0) A.out_count[t] = count;
 }
 
-__global__ void k_pack_targets(const float* pq7, int T, float eps_pos, float eps_ori, uint32_t k0, uint32_t k1,
-                               const int32_t* t_local, TargetDesc* out) {
+__global__ void k_pack_targets(const float* pq7, int T, const TargetDesc* meta, const TargetDesc tmpl,
+                               TargetDesc* out) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     const float* s = pq7 + 7 * (int64_t)t;
@@ -123,6 +126,12 @@ __global__ void k_pack_targets(const float* pq7, int T, float eps_pos, float eps
     const bool ok = nn > 0.0f && isfinite(nn);
     const float r = ok ? rsqrtf(nn) : 0.0f;
     TargetDesc d;
+    if (meta) {
+        d = meta[t];
+    } else {
+        d = tmpl;
+        d.t_local = t;
+    }
     d.p[0] = s[0];
     d.p[1] = s[1];
     d.p[2] = s[2];
@@ -130,11 +139,7 @@ __global__ void k_pack_targets(const float* pq7, int T, float eps_pos, float eps
     d.q[1] = qx * r;
     d.q[2] = qy * r;
     d.q[3] = qz * r;
-    d.eps_pos = ok ? eps_pos : -1.0f;  // a zero quaternion marks the target invalid
-    d.eps_ori = eps_ori;
-    d.key[0] = k0;
-    d.key[1] = k1;
-    d.t_local = t_local ? t_local[t] : t;
+    if (!ok) d.eps_pos = -1.0f;  // a zero quaternion marks the target invalid
     out[t] = d;
 }
 
@@ -151,25 +156,24 @@ void allow_smem(K kernel, int bytes) {
 
 }  // namespace
 
-void launch_topk_dup(const RobotParams& R, const DupArgs& A, int max_m, cudaStream_t st) {
+void launch_topk_dup(const DupArgs& A, int max_m, cudaStream_t st) {
     if (A.T <= 0 || max_m <= 0) return;
     const int sm = smem_for(max_m);
     allow_smem(k_topk_dup, sm);
-    k_topk_dup<<<A.T, kSelThreads, sm, st>>>(R, A);
+    k_topk_dup<<<A.T, kSelThreads, sm, st>>>(A);
 }
 
-void launch_rank(const RobotParams& R, const RankArgs& A, int max_b, cudaStream_t st) {
+void launch_rank(const RankArgs& A, int max_b, cudaStream_t st) {
     if (A.T <= 0) return;
     const int sm = smem_for(max_b > 0 ? max_b : 1);
     allow_smem(k_rank, sm);
-    k_rank<<<A.T, kSelThreads, sm, st>>>(R, A);
+    k_rank<<<A.T, kSelThreads, sm, st>>>(A);
 }
 
-void launch_pack_targets(const float* pq7, int T, float eps_pos, float eps_ori, uint64_t seed, const int32_t* t_local,
-                         TargetDesc* out, cudaStream_t st) {
+void launch_pack_targets(const float* pq7, int T, const TargetDesc* meta, const TargetDesc& tmpl, TargetDesc* out,
+                         cudaStream_t st) {
     if (T <= 0) return;
-    k_pack_targets<<<(T + 127) / 128, 128, 0, st>>>(pq7, T, eps_pos, eps_ori, (uint32_t)(seed & 0xffffffffu),
-                                                    (uint32_t)(seed >> 32), t_local, out);
+    k_pack_targets<<<(T + 127) / 128, 128, 0, st>>>(pq7, T, meta, tmpl, out);
 }
 
 }  // namespace hjcd

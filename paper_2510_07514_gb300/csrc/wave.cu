@@ -1,0 +1,327 @@
+// wave.cu -- one packed solve over several requests (robots, scenes, seed
+// counts and tolerances may all differ): Alg. 2 as one launch per phase over
+// every target of the wave.
+//
+// Every target row carries its robot and scene (rows of the wave's tables),
+// its request's tolerances, random-stream key and target index inside the
+// request, so a request's results do not depend on what it is packed with.
+//
+// Device layout of a wave (one workspace):
+//   head  robot kinematic tables | robot collision descriptors | scene
+//         descriptors | target rows | seed offsets m_off | candidate offsets
+//         b_off | output offsets | target poses [T][7] | inline obstacles
+//         (written in pinned host memory, copied with one transfer)
+//   PO-CCD joint vectors [n_max][CM] and scores [CM]
+//   PJ-IK joint vectors [n_max][CB], scores, errors, collision verdicts [CB]
+//   outputs (each request's block as it wants it), queue head, error flag
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "host.h"
+
+namespace hjcd {
+
+hjcd_status plan_wave(hjcd_ctx* ctx, const WaveItem* items, int n_items, const hjcd_params& P, WavePlan* out) {
+    WavePlan& W = *out;
+    W = WavePlan{};
+    W.n_items = n_items;
+    W.item_robot.resize(n_items);
+    W.item_scene.resize(n_items);
+    W.item_t0.resize(n_items);
+    W.item_q0.resize(n_items);
+    W.item_e0.resize(n_items);
+    W.dev_tgt.resize(n_items);
+    W.dev_q.resize(n_items);
+    W.dev_e.resize(n_items);
+    W.dev_c.resize(n_items);
+    size_t inl_bytes = 0;
+    for (int i = 0; i < n_items; ++i) {
+        const WaveItem& it = items[i];
+        if (!it.rob) return fail(ctx, HJCD_EINVAL, "item %d: no robot", i);
+        if (it.T < 0) return fail(ctx, HJCD_EINVAL, "item %d: n_targets < 0", i);
+        if (it.T > 0 && (!it.targets || !it.out_q || !it.out_err || !it.out_count))
+            return fail(ctx, HJCD_EINVAL, "item %d: null buffer", i);
+        if (!(it.eps_pos > 0.0f) || !(it.eps_ori > 0.0f)) return fail(ctx, HJCD_EINVAL, "item %d: tolerances must be > 0", i);
+        if (it.top_k < 1 || it.top_k > HJCD_MAX_TOPK) return fail(ctx, HJCD_EINVAL, "item %d: top_k outside [1, %d]", i, HJCD_MAX_TOPK);
+        if (it.inl_nsph < 0 || it.inl_nbox < 0 || (it.inl_nsph > 0 && !it.inl_sph) || (it.inl_nbox > 0 && !it.inl_box))
+            return fail(ctx, HJCD_EINVAL, "item %d: bad inline scene", i);
+        if (it.cd_iters > 32767 || it.lm_iters > 32767) return fail(ctx, HJCD_EINVAL, "item %d: iteration caps above 32767", i);
+        // robot table of the wave
+        int r = -1;
+        for (int k = 0; k < (int)W.robots.size(); ++k)
+            if (W.robots[k] == it.rob) r = k;
+        if (r < 0) {
+            if ((int)W.robots.size() == kMaxLaunchRobots)
+                return fail(ctx, HJCD_EINVAL, "more than %d distinct robots in one batch", kMaxLaunchRobots);
+            r = (int)W.robots.size();
+            W.robots.push_back(it.rob);
+        }
+        W.item_robot[i] = r;
+        // scene table: resident scenes once each, inline scenes one per item
+        int sidx = -1;
+        if (it.scene) {
+            for (int k = 0; k < (int)W.scenes.size(); ++k)
+                if (W.scenes[k].res == it.scene) sidx = k;
+            if (sidx < 0) {
+                sidx = (int)W.scenes.size();
+                W.scenes.push_back({it.scene, i, 0, it.scene->dev.n_sph, it.scene->dev.n_box});
+            }
+        } else if (it.inl_nsph + it.inl_nbox > 0) {
+            for (int k = 0; k < it.inl_nsph; ++k)
+                if (!(it.inl_sph[4 * k + 3] > 0.0f)) return fail(ctx, HJCD_EINVAL, "item %d: obstacle sphere %d radius must be > 0", i, k);
+            for (int k = 0; k < it.inl_nbox; ++k) {
+                const float* b = it.inl_box + 6 * k;
+                if (!(b[0] <= b[3] && b[1] <= b[4] && b[2] <= b[5])) return fail(ctx, HJCD_EINVAL, "item %d: box %d lo > hi", i, k);
+            }
+            sidx = (int)W.scenes.size();
+            W.scenes.push_back({nullptr, i, inl_bytes, it.inl_nsph, it.inl_nbox});
+            inl_bytes += align_up(16 * (size_t)(it.inl_nsph + 2 * it.inl_nbox), 16);
+        }
+        W.item_scene[i] = sidx;
+        W.dev_tgt[i] = it.T > 0 && pointer_kind(it.targets) == 1;
+        W.dev_q[i] = it.T > 0 && pointer_kind(it.out_q) == 1;
+        W.dev_e[i] = it.T > 0 && pointer_kind(it.out_err) == 1;
+        W.dev_c[i] = it.T > 0 && pointer_kind(it.out_count) == 1;
+        W.host_out = W.host_out || (it.T > 0 && (!W.dev_q[i] || !W.dev_e[i] || !W.dev_c[i]));
+        if (it.T > 0 && !W.dev_tgt[i]) {
+            for (int t = 0; t < it.T; ++t) {
+                const float* q = it.targets + 7 * (size_t)t + 3;
+                const float nn = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+                if (!(nn > 0.0f) || !std::isfinite(nn)) return fail(ctx, HJCD_EINVAL, "item %d target %d: zero quaternion", i, t);
+            }
+        }
+        // seeds and candidates
+        W.item_t0[i] = W.T;
+        W.item_q0[i] = W.q_total;
+        W.item_e0[i] = W.e_total;
+        for (int t = 0; t < it.T; ++t) {
+            const int m = it.spt ? it.spt[t] : it.n_samples;
+            if (m < 1 || m > HJCD_MAX_SAMPLES)
+                return fail(ctx, HJCD_EINVAL, "item %d target %d: seed count %d outside [1, %d]", i, t, m, HJCD_MAX_SAMPLES);
+            const int64_t b = dup_count(m, P.dup_ratio);
+            W.CM += m;
+            W.CB += b;
+            W.max_m = std::max(W.max_m, m);
+            W.max_b = std::max(W.max_b, (int)b);
+        }
+        if ((int64_t)W.T + it.T > (int64_t)(1 << 30)) return fail(ctx, HJCD_EINVAL, "too many targets in one batch");
+        W.T += it.T;
+        W.q_total += (int64_t)it.T * it.top_k * it.rob->P.n;
+        W.e_total += (int64_t)it.T * it.top_k * 2;
+    }
+    W.NR = (int)W.robots.size();
+    W.NS = (int)W.scenes.size();
+    for (const RobotRec* r : W.robots) {
+        W.n_max = std::max(W.n_max, r->P.n);
+        W.ns_max = std::max(W.ns_max, r->P.n_sph);
+        W.pairs_max = std::max(W.pairs_max, r->n_pairs);
+    }
+    for (const auto& e : W.scenes) W.obj4_max = std::max(W.obj4_max, e.nsph + 2 * e.nbox);
+
+    Carve cv;
+    W.o_rp = cv.take<RobotParams>(std::max(W.NR, 1));
+    W.o_rd = cv.take<RobotDev>(std::max(W.NR, 1));
+    W.o_sd = cv.take<SceneDev>(std::max(W.NS, 1));
+    W.o_tg = cv.take<TargetDesc>(W.T);
+    W.o_moff = cv.take<int64_t>((size_t)W.T + 1);
+    W.o_boff = cv.take<int64_t>((size_t)W.T + 1);
+    W.o_qe = cv.take<int64_t>(2 * (size_t)W.T);
+    W.o_pq7 = cv.take<float>(7 * (size_t)W.T);
+    W.o_inl = cv.take<char>(inl_bytes);
+    W.head = cv.off;
+    W.o_thM = cv.take<float>((size_t)W.n_max * W.CM);
+    W.o_sM = cv.take<float>(W.CM);
+    W.o_thB = cv.take<float>((size_t)W.n_max * W.CB);
+    W.o_sB = cv.take<float>(W.CB);
+    W.o_pB = cv.take<float>(W.CB);
+    W.o_oB = cv.take<float>(W.CB);
+    W.o_hB = cv.take<uint8_t>(W.CB);
+    W.o_q = cv.take<float>(W.q_total);
+    W.o_e = cv.take<float>(W.e_total);
+    W.o_c = cv.take<int32_t>(W.T);
+    W.o_qf = cv.take<unsigned long long>(2);  // queue head, error flag
+    W.bytes = cv.off;
+    return HJCD_OK;
+}
+
+hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, const hjcd_params& P, char* ws,
+                     char* pin, cudaStream_t s, cudaEvent_t* ev) {
+    if (W.T == 0) return HJCD_OK;
+    hjcd_status st;
+    // ---- pinned image of the head ----
+    RobotParams* h_rp = reinterpret_cast<RobotParams*>(pin + W.o_rp);
+    RobotDev* h_rd = reinterpret_cast<RobotDev*>(pin + W.o_rd);
+    SceneDev* h_sd = reinterpret_cast<SceneDev*>(pin + W.o_sd);
+    TargetDesc* h_tg = reinterpret_cast<TargetDesc*>(pin + W.o_tg);
+    int64_t* h_moff = reinterpret_cast<int64_t*>(pin + W.o_moff);
+    int64_t* h_boff = reinterpret_cast<int64_t*>(pin + W.o_boff);
+    int64_t* h_qe = reinterpret_cast<int64_t*>(pin + W.o_qe);
+    float* h_pq7 = reinterpret_cast<float*>(pin + W.o_pq7);
+    for (int r = 0; r < W.NR; ++r) {
+        h_rp[r] = W.robots[r]->P;
+        h_rd[r] = W.robots[r]->dev;
+    }
+    for (int k = 0; k < W.NS; ++k) {
+        const auto& e = W.scenes[k];
+        if (e.res) {
+            h_sd[k] = e.res->dev;
+        } else {
+            const WaveItem& it = items[e.item];
+            float4* o = reinterpret_cast<float4*>(pin + W.o_inl + e.off);
+            for (int q = 0; q < it.inl_nsph; ++q)
+                o[q] = make_float4(it.inl_sph[4 * q], it.inl_sph[4 * q + 1], it.inl_sph[4 * q + 2], it.inl_sph[4 * q + 3]);
+            for (int q = 0; q < it.inl_nbox; ++q) {
+                const float* b = it.inl_box + 6 * q;
+                o[it.inl_nsph + 2 * q] = make_float4(b[0], b[1], b[2], 0.0f);
+                o[it.inl_nsph + 2 * q + 1] = make_float4(b[3], b[4], b[5], 0.0f);
+            }
+            h_sd[k] = SceneDev{reinterpret_cast<const float4*>(ws + W.o_inl + e.off), e.nsph, e.nbox};
+        }
+    }
+    h_moff[0] = h_boff[0] = 0;
+    for (int i = 0; i < W.n_items; ++i) {
+        const WaveItem& it = items[i];
+        const int n = it.rob->P.n;
+        const int cd = it.cd_iters >= 0 ? it.cd_iters : P.cd_max_iters;
+        const int lm = it.lm_iters >= 0 ? it.lm_iters : P.lm_max_iters;
+        for (int t = 0; t < it.T; ++t) {
+            const int g = W.item_t0[i] + t;
+            TargetDesc d{};
+            d.eps_pos = it.eps_pos;
+            d.eps_ori = it.eps_ori;
+            d.key[0] = (uint32_t)(it.seed & 0xffffffffu);
+            d.key[1] = (uint32_t)(it.seed >> 32);
+            d.t_local = t;
+            d.robot = W.item_robot[i];
+            d.scene = W.item_scene[i];
+            d.cd_iters = (int16_t)cd;
+            d.lm_iters = (int16_t)lm;
+            d.top_k = it.top_k;
+            h_tg[g] = d;
+            const int m = it.spt ? it.spt[t] : it.n_samples;
+            h_moff[g + 1] = h_moff[g] + m;
+            h_boff[g + 1] = h_boff[g] + dup_count(m, P.dup_ratio);
+            h_qe[2 * g] = W.item_q0[i] + (int64_t)t * it.top_k * n;
+            h_qe[2 * g + 1] = W.item_e0[i] + (int64_t)t * it.top_k * 2;
+        }
+        if (!W.dev_tgt[i] && it.T > 0)
+            std::memcpy(h_pq7 + 7 * (size_t)W.item_t0[i], it.targets, sizeof(float) * 7 * (size_t)it.T);
+    }
+
+    // ---- host -> device ----
+    HJCD_CUDA(ctx, cudaMemcpyAsync(ws, pin, W.head, cudaMemcpyHostToDevice, s));
+    for (int i = 0; i < W.n_items; ++i)
+        if (W.dev_tgt[i] && items[i].T > 0)
+            HJCD_CUDA(ctx, cudaMemcpyAsync(ws + W.o_pq7 + sizeof(float) * 7 * (size_t)W.item_t0[i], items[i].targets,
+                                           sizeof(float) * 7 * (size_t)items[i].T, cudaMemcpyDeviceToDevice, s));
+    HJCD_CUDA(ctx, cudaMemsetAsync(ws + W.o_qf, 0, 16, s));
+    HJCD_CUDA(ctx, cudaMemsetAsync(ws + W.o_q, 0xff, sizeof(float) * (size_t)W.q_total, s));  // unfilled rows: NaN
+    HJCD_CUDA(ctx, cudaMemsetAsync(ws + W.o_e, 0xff, sizeof(float) * (size_t)W.e_total, s));
+
+    TargetDesc* d_tg = reinterpret_cast<TargetDesc*>(ws + W.o_tg);
+    const int64_t* d_moff = reinterpret_cast<const int64_t*>(ws + W.o_moff);
+    const int64_t* d_boff = reinterpret_cast<const int64_t*>(ws + W.o_boff);
+    float* thM = reinterpret_cast<float*>(ws + W.o_thM);
+    float* sM = reinterpret_cast<float*>(ws + W.o_sM);
+    float* thB = reinterpret_cast<float*>(ws + W.o_thB);
+    float* sB = reinterpret_cast<float*>(ws + W.o_sB);
+    float* pB = reinterpret_cast<float*>(ws + W.o_pB);
+    float* oB = reinterpret_cast<float*>(ws + W.o_oB);
+    uint8_t* hB = reinterpret_cast<uint8_t*>(ws + W.o_hB);
+    unsigned long long* queue = reinterpret_cast<unsigned long long*>(ws + W.o_qf);
+    RobotSet rs{reinterpret_cast<const RobotParams*>(ws + W.o_rp), reinterpret_cast<const RobotDev*>(ws + W.o_rd),
+                W.NR, W.n_max, W.ns_max, W.pairs_max};
+
+    if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[0], s));
+    launch_pack_targets(reinterpret_cast<const float*>(ws + W.o_pq7), W.T, d_tg, TargetDesc{}, d_tg, s);
+    if ((st = after_launch(ctx, 1))) return st;
+
+    // Alg. 2: PO-CCD from uniform seeds
+    CcdArgs ca{};
+    ca.rs = rs;
+    ca.tg = d_tg;
+    ca.map = CandMap{nullptr, nullptr, d_moff, W.T};
+    ca.C = W.CM;
+    ca.ld = W.CM;
+    ca.th_out = thM;
+    ca.score = sM;
+    ca.n_iters = -1;
+    ca.P = P;
+    ca.cnt = ctx->cnt;
+    launch_ccd(ca, false, s);
+    if ((st = after_launch(ctx, 1))) return st;
+    if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[1], s));
+
+    // top-K and perturbed duplication
+    DupArgs da{rs, d_tg, W.T, d_moff, sM, thM, W.CM, d_boff, thB, W.CB, nullptr, P.dup_ratio, P.dup_sigma};
+    launch_topk_dup(da, W.max_m, s);
+    if ((st = after_launch(ctx, 1))) return st;
+    if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[2], s));
+
+    // PJ-IK
+    LmArgs la{};
+    la.rs = rs;
+    la.tg = d_tg;
+    la.map = CandMap{nullptr, nullptr, d_boff, W.T};
+    la.C = W.CB;
+    la.ld = W.CB;
+    la.th = thB;
+    la.score = sB;
+    la.perr = pB;
+    la.oerr = oB;
+    la.n_iters = -1;
+    la.P = P;
+    la.cnt = ctx->cnt;
+    la.queue = queue;
+    launch_lm(la, false, s);
+    if ((st = after_launch(ctx, 1))) return st;
+    if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[3], s));
+
+    // collision filter
+    const bool collide = W.ns_max > 0;
+    if (collide) {
+        CollideArgs cl{};
+        cl.rs = rs;
+        cl.scenes = reinterpret_cast<const SceneDev*>(ws + W.o_sd);
+        cl.n_scenes = W.NS;
+        cl.max_obj4 = W.obj4_max;
+        cl.tg = d_tg;
+        cl.map = CandMap{nullptr, nullptr, d_boff, W.T};
+        cl.C = W.CB;
+        cl.ld = W.CB;
+        cl.th = thB;
+        cl.hit = hB;
+        cl.cnt = ctx->cnt;
+        cl.err_flag = wave_flag(W, ws);
+        launch_collide(cl, s);
+        if ((st = after_launch(ctx, 1))) return st;
+    }
+    if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[4], s));
+
+    // rank the collision-free candidates
+    float* q_out = reinterpret_cast<float*>(ws + W.o_q);
+    float* e_out = reinterpret_cast<float*>(ws + W.o_e);
+    int32_t* c_out = reinterpret_cast<int32_t*>(ws + W.o_c);
+    RankArgs ra{rs, d_tg, W.T, d_boff, thB, W.CB, sB, pB, oB, collide ? hB : nullptr, 0,
+                reinterpret_cast<const int64_t*>(ws + W.o_qe), q_out, e_out, c_out};
+    launch_rank(ra, W.max_b, s);
+    if ((st = after_launch(ctx, 1))) return st;
+    if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[5], s));
+
+    // each request's results to its own buffers
+    for (int i = 0; i < W.n_items; ++i) {
+        const WaveItem& it = items[i];
+        if (it.T == 0) continue;
+        const size_t nq = (size_t)it.T * it.top_k * it.rob->P.n, ne = (size_t)it.T * it.top_k * 2;
+        HJCD_CUDA(ctx, cudaMemcpyAsync(it.out_q, q_out + W.item_q0[i], sizeof(float) * nq,
+                                       W.dev_q[i] ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        HJCD_CUDA(ctx, cudaMemcpyAsync(it.out_err, e_out + W.item_e0[i], sizeof(float) * ne,
+                                       W.dev_e[i] ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        HJCD_CUDA(ctx, cudaMemcpyAsync(it.out_count, c_out + W.item_t0[i], sizeof(int32_t) * (size_t)it.T,
+                                       W.dev_c[i] ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    }
+    return HJCD_OK;
+}
+
+}  // namespace hjcd

@@ -24,6 +24,7 @@ HJCD_MAX_DOF = 24
 HJCD_MAX_SPHERES = 256
 HJCD_MAX_SAMPLES = 8192
 HJCD_MAX_TOPK = 64
+HJCD_MAX_BATCH_ROBOTS = 16
 
 # Every function the header declares (checked by the test-suite against include/hjcd.h).
 EXPORTS = (
@@ -31,7 +32,7 @@ EXPORTS = (
     "hjcd_create_robot", "hjcd_set_scene", "hjcd_solve", "hjcd_fk", "hjcd_sample_seeds",
     "hjcd_po_ccd", "hjcd_topk_dup", "hjcd_pjik", "hjcd_collide", "hjcd_rank",
     "hjcd_set_profiling", "hjcd_phase_times", "hjcd_counters", "hjcd_launch_count", "hjcd_ffma_probe",
-    "hjcd_solve_noalloc",
+    "hjcd_solve_noalloc", "hjcd_solve_batch",
 )
 
 
@@ -57,6 +58,15 @@ class hjcd_solve_opts(ct.Structure):
     _fields_ = [
         ("eps_pos", ct.c_float), ("eps_ori", ct.c_float), ("n_samples", ct.c_int32), ("top_k", ct.c_int32),
         ("seed", ct.c_uint64), ("params", ct.POINTER(hjcd_params)), ("samples_per_target", ct.c_void_p),
+    ]
+
+
+class hjcd_batch_item(ct.Structure):
+    _fields_ = [
+        ("robot_id", ct.c_int32), ("scene_id", ct.c_int32), ("n_inline_spheres", ct.c_int32),
+        ("n_inline_boxes", ct.c_int32), ("inline_spheres", ct.c_void_p), ("inline_boxes", ct.c_void_p),
+        ("n_targets", ct.c_int32), ("pad_", ct.c_int32), ("targets_pq", ct.c_void_p), ("opts", hjcd_solve_opts),
+        ("out_q", ct.c_void_p), ("out_err", ct.c_void_p), ("out_count", ct.c_void_p),
     ]
 
 
@@ -87,6 +97,7 @@ _SIGS = {
     "hjcd_set_scene": (_ST, [_V, _I32, _I, _V, _I, _V, ct.POINTER(_I32)]),
     "hjcd_solve": (_ST, [_V, _I32, _I32, _I, _V, ct.POINTER(hjcd_solve_opts), _V, _V, _V, _V]),
     "hjcd_solve_noalloc": (_ST, [_V, _I32, _I32, _I, _V, ct.POINTER(hjcd_solve_opts), _V, _V, _V, _V]),
+    "hjcd_solve_batch": (_ST, [_V, _I, ct.POINTER(hjcd_batch_item), ct.POINTER(hjcd_params), _V]),
     "hjcd_fk": (_ST, [_V, _I32, _I64, _V, _I64, _V, _V]),
     "hjcd_sample_seeds": (_ST, [_V, _I32, _I64, _V, _V, _U64, _V, _I64, _V]),
     "hjcd_po_ccd": (_ST, [_V, _I32, _I, _V, _F, _F, _U64, ct.POINTER(hjcd_params), _I64, _V, _V, _V, _V, _I64,
@@ -210,6 +221,13 @@ def hjcd_solve_noalloc(ctx, robot_id, scene_id, n_targets, targets_pq, opts: hjc
     _check(ctx, load().hjcd_solve_noalloc(ctx, int(robot_id), int(scene_id), int(n_targets), ptr(targets_pq),
                                           ct.byref(opts), ptr(out_q), ptr(out_err), ptr(out_count),
                                           stream_handle(stream)))
+
+
+def hjcd_solve_batch(ctx, items, params=None, stream=None) -> None:
+    """Solve several requests (a sequence of hjcd_batch_item) in one launch per phase."""
+    arr = (hjcd_batch_item * len(items))(*items)
+    _check(ctx, load().hjcd_solve_batch(ctx, len(items), arr, ct.byref(params) if params is not None else None,
+                                        stream_handle(stream)))
 
 
 def hjcd_fk(ctx, robot_id, n_cand, theta, ld, out_pq, stream=None) -> None:

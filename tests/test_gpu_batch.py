@@ -1,0 +1,213 @@
+"""Packed batches (hjcd_solve_batch): requests of different robots, scenes
+(resident, inline, none), seed counts, tolerances, top_k and iteration caps
+in one launch per phase.
+
+A request's results must not depend on what it is packed with: each target
+row keys its random streams by its request's seed and its index inside the
+request, so the batch and the request alone give the same bits.  The mixed
+batch is also checked against the oracle (every solution re-verified, success
+rates compared).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from paper_2510_07514_gb300 import api, build, hjcd, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    orc.build()
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def _robots():
+    chains = inputs.cfg3_chains()
+    return [inputs.panda_with_spheres(np.random.default_rng(5)), chains[1], chains[3], chains[5], inputs.panda()]
+
+
+def _mix_specs():
+    """(robot, scene kind, T, seeds, top_k, eps_pos, eps_ori, seed, caps)"""
+    return [
+        (0, "resident", 9, 256, 4, 1e-3, 1e-2, 11, None),
+        (1, "inline", 7, [32, 40, 64, 100, 33, 256, 48], 2, 1e-3, 1e-2, 12, None),
+        (2, "none", 5, 128, 1, 2e-3, 2e-2, 13, (12, 10)),
+        (3, "inline", 4, 64, 3, 1e-3, 1e-2, 14, None),
+        (4, "none", 6, 96, 5, 1e-3, 1e-2, 15, (20, 30)),
+        (0, "resident", 3, 512, 2, 1e-3, 1e-2, 16, None),
+        (1, "none", 2, 77, 1, 5e-4, 5e-3, 17, None),
+    ]
+
+
+def _setup(ctx):
+    rng = np.random.default_rng(41)
+    robs = _robots()
+    rids = [ctx.add_robot(r) for r in robs]
+    scene = inputs.random_scene(rng, 60, 6)
+    sid = ctx.set_scene(scene)
+    reqs = []
+    for (ri, kind, T, seeds, k, ep, eo, seed, caps) in _mix_specs():
+        rob = robs[ri]
+        th = rng.uniform(rob.lo, rob.hi, (T, rob.n))
+        tg = f32(orc.pose(orc.Robot(rob), f32(th)))
+        inl = inputs.random_scene(rng, 25, 3) if kind == "inline" else None
+        params = api.make_params(cd_max_iters=caps[0], lm_max_iters=caps[1]) if caps else None
+        reqs.append(dict(ri=ri, kind=kind, T=T, seeds=seeds, k=k, ep=ep, eo=eo, seed=seed, caps=caps,
+                         tg=tg, inl=inl, params=params))
+    return robs, rids, scene, sid, reqs
+
+
+def _item(ctx, rids, sid, robs, r, device="cuda"):
+    spt = r["seeds"] if isinstance(r["seeds"], list) else None
+    n = r["seeds"] if spt is None else 0
+    scene_id = sid if r["kind"] == "resident" else -1
+    sph = r["inl"].sph_xyzr if r["inl"] is not None else None
+    box = r["inl"].box_lohi if r["inl"] is not None else None
+    tg = dev(r["tg"]) if device == "cuda" else torch.as_tensor(np.ascontiguousarray(r["tg"]), dtype=torch.float32)
+    return ctx.batch_item(rids[r["ri"]], scene_id, tg, max(n, 1), r["k"], r["seed"], robs[r["ri"]].n,
+                          r["ep"], r["eo"], r["params"], spt, sph, box)
+
+
+def _same(a, b):
+    qa, ea, ca = (host(x) for x in a)
+    qb, eb, cb = (host(x) for x in b)
+    assert np.array_equal(ca, cb)
+    for t in range(len(ca)):
+        c = int(ca[t])
+        assert np.array_equal(qa[t, :c], qb[t, :c])
+        assert np.array_equal(ea[t, :c], eb[t, :c])
+        assert np.all(np.isnan(qa[t, c:])) and np.all(np.isnan(qb[t, c:]))
+
+
+def test_each_request_is_the_same_alone_and_in_the_mix(ctx):
+    robs, rids, scene, sid, reqs = _setup(ctx)
+    pairs = [_item(ctx, rids, sid, robs, r) for r in reqs]
+    ctx.solve_batch([p[0] for p in pairs])
+    for r, (it, out) in zip(reqs, pairs):
+        alone_it, alone_out = _item(ctx, rids, sid, robs, r)
+        ctx.solve_batch([alone_it])
+        _same(out, alone_out)
+        if r["kind"] != "inline" and not isinstance(r["seeds"], list):
+            # and through the one-request entry point
+            q, e, c = ctx.solve(rids[r["ri"]], sid if r["kind"] == "resident" else -1, dev(r["tg"]), r["seeds"],
+                                r["k"], r["seed"], robs[r["ri"]].n, r["ep"], r["eo"],
+                                r["params"] if r["params"] is not None else api.make_params())
+            _same(out, (q, e, c))
+    # reversed order packs the requests differently: same bits again
+    pairs2 = [_item(ctx, rids, sid, robs, r) for r in reqs[::-1]]
+    ctx.solve_batch([p[0] for p in pairs2])
+    for (it, out), (it2, out2) in zip(pairs, pairs2[::-1]):
+        _same(out, out2)
+
+
+def test_host_outputs_and_host_targets_in_a_batch(ctx):
+    robs, rids, scene, sid, reqs = _setup(ctx)
+    pd = [_item(ctx, rids, sid, robs, r) for r in reqs]
+    ph = [_item(ctx, rids, sid, robs, r, device="cpu") for r in reqs]
+    ctx.solve_batch([p[0] for p in pd])
+    ctx.solve_batch([p[0] for p in ph])
+    for (a, oa), (b, ob) in zip(pd, ph):
+        _same(oa, ob)
+
+
+def _verify(orob, osc, rob, tg, q, err, cnt, eps_pos, eps_ori):
+    T = len(tg)
+    succ = np.zeros(T, bool)
+    for t in range(T):
+        for r in range(cnt[t]):
+            e = orc.residual(orob, q[t, r], tg[t])
+            assert abs(np.linalg.norm(e[:3]) - err[t, r, 0]) < 1e-5
+            assert abs(np.linalg.norm(e[3:]) - err[t, r, 1]) < 1e-5
+            assert np.all(q[t, r] >= rob.lo - 1e-7) and np.all(q[t, r] <= rob.hi + 1e-7)
+        if cnt[t] and len(rob.sph_body):
+            hit, margin = orc.collide(orob, osc, q[t, :cnt[t]])
+            assert not np.any(hit & (margin >= 1e-6))
+        succ[t] = cnt[t] > 0 and err[t, 0, 0] <= eps_pos and err[t, 0, 1] <= eps_ori
+    return succ
+
+
+def test_mixed_batch_matches_the_oracle(ctx):
+    """Three robots (Panda with spheres and a resident scene, a 7-DoF and a
+    12-DoF random chain with their own inline scenes) in one batch; targets
+    are poses of configurations the oracle finds collision-free."""
+    rng = np.random.default_rng(43)
+    chains = inputs.cfg3_chains()
+    robs = [inputs.panda_with_spheres(np.random.default_rng(5)), chains[1], chains[3]]
+    rids = [ctx.add_robot(r) for r in robs]
+    scene = inputs.random_scene(rng, 80, 8)
+    sid = ctx.set_scene(scene)
+    T, S, k = 48, 128, 2
+    items, outs, meta = [], [], []
+    for i, rob in enumerate(robs):
+        sc = scene if i == 0 else inputs.random_scene(rng, 40, 4)
+        orob, osc = orc.Robot(rob), orc.Scene(sc)
+        pool = f32(rng.uniform(rob.lo, rob.hi, (40 * T, rob.n)))
+        hit, _ = orc.collide(orob, osc, pool)
+        keep = pool[~hit][:T]
+        assert len(keep) == T
+        tg = f32(orc.pose(orob, keep))
+        it, out = ctx.batch_item(rids[i], sid if i == 0 else -1, dev(tg), S, k, 100 + i, rob.n,
+                                 spheres=None if i == 0 else sc.sph_xyzr, boxes=None if i == 0 else sc.box_lohi)
+        items.append(it)
+        outs.append(out)
+        meta.append((rob, orob, osc, tg))
+    ctx.solve_batch(items)
+    sg, so = [], []
+    for i, (rob, orob, osc, tg) in enumerate(meta):
+        q, e, c = (host(x) for x in outs[i])
+        c = c.astype(int)
+        sg.append(_verify(orob, osc, rob, tg, q, e, c, 1e-3, 1e-2))
+        o = orc.solve(orob, osc, orc.make_params(1e-3, 1e-2, seed=100 + i), tg, S, k)
+        so.append((o["count"] > 0) & (o["err"][:, 0, 0] <= 1e-3) & (o["err"][:, 0, 1] <= 1e-2))
+    sg, so = np.concatenate(sg), np.concatenate(so)
+    assert abs(sg.mean() - so.mean()) <= 0.04 + 1e-12, (sg.mean(), so.mean())
+    assert sg.mean() > 0.5
+
+
+def test_batch_edge_cases(ctx):
+    robs, rids, scene, sid, reqs = _setup(ctx)
+    # an empty request inside a batch, and an empty batch
+    it, out = _item(ctx, rids, sid, robs, reqs[0])
+    empty = hjcd.hjcd_batch_item()
+    empty.robot_id, empty.scene_id, empty.n_targets = rids[0], -1, 0
+    empty.opts = ctx.opts(64, 1, 0)
+    ctx.solve_batch([empty, it, empty])
+    a_it, a_out = _item(ctx, rids, sid, robs, reqs[0])
+    ctx.solve_batch([a_it])
+    _same(out, a_out)
+    ctx.solve_batch([])
+    # unknown robot, too many distinct robots
+    bad = hjcd.hjcd_batch_item()
+    bad.robot_id, bad.scene_id, bad.n_targets = 10 ** 6, -1, 0
+    bad.opts = ctx.opts(64, 1, 0)
+    with pytest.raises(hjcd.HjcdError) as ei:
+        ctx.solve_batch([bad])
+    assert ei.value.status == hjcd.HJCD_ENOTFOUND
+    many = [ctx.add_robot(inputs.planar([0.3, 0.2])) for _ in range(hjcd.HJCD_MAX_BATCH_ROBOTS + 1)]
+    tg = dev(f32(orc.pose(orc.Robot(inputs.planar([0.3, 0.2])), np.zeros((1, 2)))))
+    its = [ctx.batch_item(r, -1, tg, 8, 1, 0, 2)[0] for r in many]
+    with pytest.raises(hjcd.HjcdError) as ei:
+        ctx.solve_batch(its)
+    assert ei.value.status == hjcd.HJCD_EINVAL
+    ctx.solve_batch(its[:hjcd.HJCD_MAX_BATCH_ROBOTS])
