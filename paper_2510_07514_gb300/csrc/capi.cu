@@ -124,6 +124,18 @@ RobotSet single_robot_set(const RobotRec& r) {
     return RobotSet{r.d_params, r.d_dev, 1, r.P.n, r.P.n_sph, r.n_pairs};
 }
 
+void collide_uniform(CollideArgs& a, const RobotRec& r, const SceneRec* sc) {
+    a.rs = single_robot_set(r);
+    a.scenes = sc ? sc->d_dev : nullptr;
+    a.n_scenes = sc ? 1 : 0;
+    a.max_obj4 = sc ? sc->dev.n_sph + 2 * sc->dev.n_box : 0;
+    a.uniform = 1;
+    a.u_n = r.P.n;
+    a.u_pairs = r.n_pairs;
+    a.u_osph = sc ? sc->dev.n_sph : 0;
+    a.u_obox = sc ? sc->dev.n_box : 0;
+}
+
 }  // namespace hjcd
 
 namespace {
@@ -728,10 +740,7 @@ hjcd_status hjcd_collide(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int6
     }
     HJCD_CUDA(ctx, cudaMemsetAsync(ctx->err_flag, 0, sizeof(int32_t), s));
     CollideArgs a{};
-    a.rs = single_robot_set(*rob);
-    a.scenes = sc ? sc->d_dev : nullptr;
-    a.n_scenes = sc ? 1 : 0;
-    a.max_obj4 = sc ? sc->dev.n_sph + 2 * sc->dev.n_box : 0;
+    collide_uniform(a, *rob, sc);
     a.C = n_cand;
     a.ld = ld;
     a.th = theta;
@@ -977,10 +986,7 @@ extern "C" hjcd_status hjcd_solve_noalloc(hjcd_ctx* ctx, int32_t robot_id, int32
     const bool collide = R.n_sph > 0;
     if (collide) {
         CollideArgs cl{};
-        cl.rs = rs;
-        cl.scenes = sc ? sc->d_dev : nullptr;
-        cl.n_scenes = sc ? 1 : 0;
-        cl.max_obj4 = sc ? sc->dev.n_sph + 2 * sc->dev.n_box : 0;
+        collide_uniform(cl, *rob, sc);
         cl.tg = d_tg;
         cl.map = CandMap{nullptr, nullptr, d_boff, T};
         cl.C = CB;

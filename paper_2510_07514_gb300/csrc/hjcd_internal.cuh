@@ -419,9 +419,9 @@ struct RankArgs {
     int32_t* out_count;
 };
 
-// Collision filter of C candidates.  With tg null every candidate is robot 0
-// against scene 0 (if any); otherwise candidate c belongs to target row
-// map(c), whose robot and scene it uses.  A launch with a single scene
+// Collision filter of C candidates.  With tg null or uniform set every
+// candidate is robot 0 against scene 0 (if any); otherwise candidate c belongs
+// to target row map(c), whose robot and scene it uses (an invalid row: hit).  A launch with a single scene
 // stages it into shared memory; with several, obstacles are read from the
 // scene tables directly.
 struct CollideArgs {
@@ -429,6 +429,9 @@ struct CollideArgs {
     const SceneDev* scenes;   // [n_scenes] (device)
     int32_t n_scenes;
     int32_t max_obj4;         // largest n_sph + 2 n_box over the scenes
+    int32_t uniform;          // every candidate: robot 0 and scene 0 (if any) -- no per-candidate lookup
+    // with uniform set: robot 0's DoF and checked body pairs, scene 0's obstacle counts (0 without a scene)
+    int32_t u_n, u_pairs, u_osph, u_obox;
     const TargetDesc* tg;
     CandMap map;
     int64_t C, ld;

@@ -103,6 +103,8 @@ hjcd_status check_scene(hjcd_ctx* ctx, int32_t id, SceneRec** out);
 hjcd_status check_params(hjcd_ctx* ctx, const hjcd_params& P);
 int64_t dup_count(int64_t M, int ratio);
 RobotSet single_robot_set(const RobotRec& r);
+// collision arguments of a launch where every candidate is robot r against scene sc (or none)
+void collide_uniform(CollideArgs& a, const RobotRec& r, const SceneRec* sc);
 
 // ---- packed solve of several requests ("wave") ---------------------------------
 

@@ -31,6 +31,7 @@ namespace hjcd {
 namespace {
 
 constexpr int kWarpsPerBlock = 8;
+constexpr int kMaxStagedObj4 = 10240;  // obstacle float4s staged in shared memory (160 KB)
 constexpr uint32_t kWaitLimit = 1u << 22;  // try_wait polls before the staged tables are given up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -76,6 +77,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 
+// an obstacle: from shared memory (staged scene) or through the read-only cache
+template <bool STAGED>
+__device__ __forceinline__ float4 ld_obj(const float4* p, int i) {
+    if (STAGED) return p[i];
+    return __ldg(p + i);
+}
+
 __device__ __forceinline__ float4 to_world(const Frame& F, float4 s) {
     const V3 w = fma3(s.z, F.c2, fma3(s.y, F.c1, fma3(s.x, F.c0, F.p)));
     return make_float4(w.x, w.y, w.z, s.w);
@@ -99,18 +107,23 @@ struct CollideLayout {
     uint32_t bar, robots, warp, warp_bytes, total;
 };
 
-__host__ __device__ __forceinline__ CollideLayout collide_smem_layout(int n_obj4, int n_robots, int nb, int ns) {
+// per warp: world fine spheres [ns], world bounding spheres [nb], the robot's
+// body ranges [nb] and checked body pairs [n_pairs], a list of 32 indices
+__host__ __device__ __forceinline__ CollideLayout collide_smem_layout(int n_obj4, int n_robots, int nb, int ns,
+                                                                      int n_pairs) {
     CollideLayout L;
     L.bar = 16u * (uint32_t)n_obj4;
     L.robots = L.bar + 16u;
     L.warp = L.robots + (uint32_t)robots_smem_bytes(n_robots);
-    L.warp_bytes = 16u * (uint32_t)(ns + nb) + 4u * 32u;
+    L.warp_bytes = (16u * (uint32_t)(ns + nb) + 8u * (uint32_t)(nb + n_pairs) + 4u * 32u + 15u) / 16u * 16u;
     L.total = L.warp + kWarpsPerBlock * L.warp_bytes;
     return L;
 }
 
-template <int SPL, bool STAGED>
+
+template <int SPL, bool UNIFORM>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideArgs A) {
+    constexpr bool STAGED = UNIFORM;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -121,13 +134,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
         return;
     }
     const int nb_max = A.rs.n_max + 2;
-    const CollideLayout L = collide_smem_layout(n_obj4, A.rs.n, nb_max, A.rs.ns_max);
+    const CollideLayout L = collide_smem_layout(n_obj4, A.rs.n, nb_max, A.rs.ns_max, A.rs.pairs_max);
     float4* s_scene = reinterpret_cast<float4*>(smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
     unsigned char* wb = smem + L.warp + warp * L.warp_bytes;
     float4* wsph = reinterpret_cast<float4*>(wb);
     float4* wco = wsph + A.rs.ns_max;
-    int* list = reinterpret_cast<int*>(wco + nb_max);
+    int2* wrange = reinterpret_cast<int2*>(wco + nb_max);
+    int2* wpairs = wrange + nb_max;
+    int* list = reinterpret_cast<int*>(wpairs + A.rs.pairs_max);
 
     // stage the obstacles with one bulk copy, the robots' kinematic tables with plain loads
     const uint32_t bytes = 16u * (uint32_t)n_obj4;
@@ -161,56 +176,60 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
     float4 ls[SPL];
     int lb[SPL];
     float4 lco = make_float4(0.f, 0.f, 0.f, 0.f);
-    int cur = -1, n = 0, nb = 0, ns = 0, n_pairs = 0;
-    RobotDev rd{};
+    int cur = -1, n_m = 0, pairs_m = 0;  // robot of a mixed launch: DoF, checked pairs
 
     unsigned long long tests = 0, btests = 0, ncand = 0;
     const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
+    int rid = 0, sid = 0;
+    bool tvalid = true;
     for (int64_t c = (int64_t)blockIdx.x * kWarpsPerBlock + warp; c < A.C; c += nwarps) {
-        int rid = 0, sid = A.n_scenes > 0 ? 0 : -1;
-        if (A.tg) {
+        if (!UNIFORM && A.tg) {
             int32_t t, s;
-            bool ok = A.map.lookup(c, t, s);
-            if (ok) {
+            tvalid = A.map.lookup(c, t, s);
+            if (tvalid) {
                 const TargetDesc& Td = A.tg[t];
                 rid = Td.robot;
                 sid = Td.scene;
-                ok = Td.eps_pos > 0.0f;
+                tvalid = Td.eps_pos > 0.0f;
             }
-            if (!ok) {  // no such target, or an invalid one: never ranked
-                if (lane == 0) A.hit[c] = 1;
-                continue;
-            }
+        } else if (!UNIFORM) {
+            sid = A.n_scenes > 0 ? 0 : -1;
+        }
+        if (!tvalid) {  // no such target, or an invalid one: never ranked
+            if (lane == 0) A.hit[c] = 1;
+            continue;
         }
         if (rid != cur) {
             cur = rid;
-            rd = A.rs.rd[rid];
-            n = rob[rid].n;
-            nb = n + 2;
-            ns = rd.n_sph;
-            n_pairs = rd.n_pairs;
+            const RobotDev rd = A.rs.rd[rid];
+            n_m = rob[rid].n;
+            pairs_m = rd.n_pairs;
+            const int ns = rd.n_sph, nbr = n_m + 2;
 #pragma unroll
             for (int q = 0; q < SPL; ++q) {
                 const int i = lane + 32 * q;
                 lb[q] = i < ns ? __ldg(rd.body + i) : -1;
                 ls[q] = i < ns ? __ldg(rd.sph + i) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            lco = lane < nb ? __ldg(rd.coarse + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+            lco = lane < nbr ? __ldg(rd.coarse + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+            __syncwarp();
+            for (int i = lane; i < nbr; i += 32) wrange[i] = __ldg(rd.range + i);
+            for (int i = lane; i < pairs_m; i += 32) wpairs[i] = __ldg(rd.pairs + i);
+            __syncwarp();
         }
         const RobotParams& R = rob[rid];
-        const float4* obj = nullptr;
+        const int n = UNIFORM ? A.u_n : n_m, nb = n + 2, n_pairs = UNIFORM ? A.u_pairs : pairs_m;
+        // obstacles: the staged copy (shared memory) or the scene's table (global, read-only path)
+        const float4* obj = s_scene;
         int n_osph = 0, n_obox = 0;
-        if (sid >= 0) {
-            if (STAGED) {
-                obj = s_scene;
-                n_osph = sc0.n_sph;
-                n_obox = sc0.n_box;
-            } else {
-                const SceneDev sd = A.scenes[sid];
-                obj = sd.obj;
-                n_osph = sd.n_sph;
-                n_obox = sd.n_box;
-            }
+        if (UNIFORM) {
+            n_osph = A.u_osph;
+            n_obox = A.u_obox;
+        } else if (sid >= 0) {
+            const SceneDev sd = A.scenes[sid];
+            obj = sd.obj;
+            n_osph = sd.n_sph;
+            n_obox = sd.n_box;
         }
 
         // world frame: body 0 is the base (identity)
@@ -246,7 +265,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
             int2 pr = make_int2(0, 0);
             bool ch = false;
             if (p < n_pairs) {
-                pr = __ldg(rd.pairs + p);
+                pr = wpairs[p];
                 ch = sph_sph(wco[pr.x], wco[pr.y]);
             }
             t_s += (unsigned long long)min(32, n_pairs - p0);
@@ -255,7 +274,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
                 const int src = __ffs(m) - 1;
                 m &= m - 1u;
                 const int ba = __shfl_sync(0xffffffffu, pr.x, src), bb = __shfl_sync(0xffffffffu, pr.y, src);
-                const int2 ra = __ldg(rd.range + ba), rb = __ldg(rd.range + bb);
+                const int2 ra = wrange[ba], rb = wrange[bb];
                 const int items = ra.y * rb.y;
                 bool h = false;
                 for (int w = lane; w < items; w += 32) {
@@ -274,10 +293,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
         for (int o0 = 0; o0 < n_osph && !hit; o0 += 32) {
             const int o = o0 + lane;
             const bool valid = o < n_osph;
-            const float4 s = valid ? obj[o] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 s = valid ? ld_obj<STAGED>(obj, o) : make_float4(0.f, 0.f, 0.f, 0.f);
             const int nvalid = min(32, n_osph - o0);
             for (int b = 0; b < nb && !hit; ++b) {
-                const int2 rg = __ldg(rd.range + b);
+                const int2 rg = wrange[b];
                 if (rg.y == 0) continue;
                 const bool ch = valid && sph_sph(wco[b], s);
                 t_s += (unsigned long long)nvalid;
@@ -289,7 +308,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
                 bool h = false;
                 for (int w = lane; w < items; w += 32) {
                     const int k = w / rg.y;
-                    h |= sph_sph(wsph[rg.x + (w - k * rg.y)], obj[list[k]]);
+                    h |= sph_sph(wsph[rg.x + (w - k * rg.y)], ld_obj<STAGED>(obj, list[k]));
                 }
                 t_s += (unsigned long long)items;
                 hit = __any_sync(0xffffffffu, h);
@@ -302,11 +321,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
         for (int o0 = 0; o0 < n_obox && !hit; o0 += 32) {
             const int o = o0 + lane;
             const bool valid = o < n_obox;
-            const float4 lo = valid ? box[2 * o] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 hi = valid ? box[2 * o + 1] : lo;
+            const float4 lo = valid ? ld_obj<STAGED>(box, 2 * o) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 hi = valid ? ld_obj<STAGED>(box, 2 * o + 1) : lo;
             const int nvalid = min(32, n_obox - o0);
             for (int b = 0; b < nb && !hit; ++b) {
-                const int2 rg = __ldg(rd.range + b);
+                const int2 rg = wrange[b];
                 if (rg.y == 0) continue;
                 const bool ch = valid && sph_box(wco[b], lo, hi);
                 t_b += (unsigned long long)nvalid;
@@ -318,7 +337,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
                 bool h = false;
                 for (int w = lane; w < items; w += 32) {
                     const int k = w / rg.y, bo = list[k];
-                    h |= sph_box(wsph[rg.x + (w - k * rg.y)], box[2 * bo], box[2 * bo + 1]);
+                    h |= sph_box(wsph[rg.x + (w - k * rg.y)], ld_obj<STAGED>(box, 2 * bo), ld_obj<STAGED>(box, 2 * bo + 1));
                 }
                 t_b += (unsigned long long)items;
                 hit = __any_sync(0xffffffffu, h);
@@ -341,35 +360,40 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
     }
 }
 
-template <int SPL, bool STAGED>
+template <int SPL, bool UNIFORM>
 void launch_collide_t(const CollideArgs& A, int n_obj4, cudaStream_t st) {
-    const size_t smem = collide_smem_layout(STAGED ? n_obj4 : 0, A.rs.n, A.rs.n_max + 2, A.rs.ns_max).total;
+    const size_t smem =
+        collide_smem_layout(UNIFORM ? n_obj4 : 0, A.rs.n, A.rs.n_max + 2, A.rs.ns_max, A.rs.pairs_max).total;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_collide<SPL, STAGED>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncSetAttribute(k_collide<SPL, UNIFORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         attr_set = true;
     }
     const int g = grid_for(A.C, kWarpsPerBlock, 8);
-    k_collide<SPL, STAGED><<<g, kWarpsPerBlock * 32, smem, st>>>(A);
+    k_collide<SPL, UNIFORM><<<g, kWarpsPerBlock * 32, smem, st>>>(A);
 }
 
-template <bool STAGED>
+template <bool UNIFORM>
 void launch_collide_s(const CollideArgs& A, int n_obj4, cudaStream_t st) {
     const int ns = A.rs.ns_max;
-    if (ns <= 32) launch_collide_t<1, STAGED>(A, n_obj4, st);
-    else if (ns <= 64) launch_collide_t<2, STAGED>(A, n_obj4, st);
-    else if (ns <= 128) launch_collide_t<4, STAGED>(A, n_obj4, st);
-    else launch_collide_t<8, STAGED>(A, n_obj4, st);
+    if (ns <= 32) launch_collide_t<1, UNIFORM>(A, n_obj4, st);
+    else if (ns <= 64) launch_collide_t<2, UNIFORM>(A, n_obj4, st);
+    else if (ns <= 128) launch_collide_t<4, UNIFORM>(A, n_obj4, st);
+    else launch_collide_t<8, UNIFORM>(A, n_obj4, st);
 }
 
 }  // namespace
 
-// A single scene is staged (its object count, n_sph + 2 n_box, is given by
-// max_obj4); several are read from their tables.
+// One robot and one scene (or none) for every candidate, with the scene small
+// enough to stage: the uniform kernel (scene staged into shared memory, counts
+// as launch parameters); otherwise the mixed kernel.
 void launch_collide(const CollideArgs& A, cudaStream_t st) {
     if (A.C <= 0 || A.rs.ns_max <= 0) return;
-    if (A.n_scenes == 1) launch_collide_s<true>(A, A.max_obj4, st);
-    else launch_collide_s<false>(A, 0, st);
+    if (A.uniform && A.rs.n == 1 && A.n_scenes <= 1 && A.max_obj4 <= kMaxStagedObj4) {
+        launch_collide_s<true>(A, A.n_scenes == 1 ? A.max_obj4 : 0, st);
+    } else {
+        launch_collide_s<false>(A, 0, st);
+    }
 }
 
 }  // namespace hjcd

@@ -286,6 +286,15 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
         cl.scenes = reinterpret_cast<const SceneDev*>(ws + W.o_sd);
         cl.n_scenes = W.NS;
         cl.max_obj4 = W.obj4_max;
+        bool same_scene = true;  // one robot and the same scene for every request
+        for (int i = 1; i < W.n_items; ++i) same_scene = same_scene && W.item_scene[i] == W.item_scene[0];
+        cl.uniform = W.NR == 1 && same_scene && (W.NS == 0 || W.item_scene[0] == 0);
+        if (cl.uniform) {
+            cl.u_n = W.robots[0]->P.n;
+            cl.u_pairs = W.robots[0]->n_pairs;
+            cl.u_osph = W.NS ? W.scenes[0].nsph : 0;
+            cl.u_obox = W.NS ? W.scenes[0].nbox : 0;
+        }
         cl.tg = d_tg;
         cl.map = CandMap{nullptr, nullptr, d_boff, W.T};
         cl.C = W.CB;
