@@ -178,6 +178,51 @@ typedef struct hjcd_batch_item {
 hjcd_status hjcd_solve_batch(hjcd_ctx* ctx, int n_items, const hjcd_batch_item* items,
                              const hjcd_params* params, void* stream);
 
+/* ---- serving: continuous batching ------------------------------------------ */
+
+/* Serving loop of a context (Sec. I and Sec. VI motivate interactive use; the
+ * paper has no serving layer).  One scheduler thread packs the pending
+ * requests, in arrival order, into batches (one launch per phase, as
+ * hjcd_solve_batch) and runs each batch on one of max_inflight streams as
+ * soon as one is free: requests arriving while others run are admitted as
+ * streams and memory free up, and their work overlaps on the device.  A
+ * batch holds at most max_batch_requests requests, max_batch_seeds PO-CCD
+ * seeds and memory_budget / max_inflight bytes of device workspace; a request
+ * that does not fit that share alone fails with HJCD_ENOMEM.  Zero fields take
+ * the defaults (2 streams, 256 requests, 2^20 seeds, a quarter of the free
+ * device memory).  params: the batch parameters (NULL: defaults); a request's
+ * own opts.params contributes its iteration caps.  With max_inflight = 1 and
+ * max_batch_requests = 1 the loop is the plain one-request-per-launch path. */
+typedef struct hjcd_server_opts {
+    int32_t max_inflight;
+    int32_t max_batch_requests;
+    int64_t max_batch_seeds;
+    uint64_t memory_budget;
+    const hjcd_params* params;
+} hjcd_server_opts;
+
+/* Outcome and timing of a finished request (host steady clock). */
+typedef struct hjcd_request_info {
+    hjcd_status status;        /* HJCD_OK, or why the request failed */
+    int32_t batch_requests;    /* requests in the batch it ran in */
+    double queued_ms;          /* submit -> launch of its batch */
+    double total_ms;           /* submit -> results in the caller's buffers */
+} hjcd_request_info;
+
+hjcd_status hjcd_server_start(hjcd_ctx* ctx, const hjcd_server_opts* opts);
+/* Finish every submitted request, then stop (hjcd_destroy does the same). */
+hjcd_status hjcd_server_stop(hjcd_ctx* ctx);
+/* Queue one request (fields as for hjcd_solve_batch; targets, outputs HOST
+ * memory).  The inputs are copied before the call returns; the outputs must
+ * stay valid until the request is reported done.  *request_id identifies it. */
+hjcd_status hjcd_submit(hjcd_ctx* ctx, const hjcd_batch_item* req, int64_t* request_id);
+/* *done = 1 once the request's results are in its buffers (info, if not NULL,
+ * then filled); a finished request is reported once, after which its id is
+ * unknown. */
+hjcd_status hjcd_poll(hjcd_ctx* ctx, int64_t request_id, int32_t* done, hjcd_request_info* info);
+/* Block until the request is done (HJCD_ETIMEOUT after timeout_s seconds). */
+hjcd_status hjcd_wait(hjcd_ctx* ctx, int64_t request_id, double timeout_s, hjcd_request_info* info);
+
 /* ---- the whole method without allocation ------------------------------------- */
 
 /* Bytes of the file-scope device array that serves as the scratch of

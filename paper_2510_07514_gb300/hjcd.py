@@ -33,6 +33,7 @@ EXPORTS = (
     "hjcd_po_ccd", "hjcd_topk_dup", "hjcd_pjik", "hjcd_collide", "hjcd_rank",
     "hjcd_set_profiling", "hjcd_phase_times", "hjcd_counters", "hjcd_launch_count", "hjcd_ffma_probe",
     "hjcd_solve_noalloc", "hjcd_solve_batch",
+    "hjcd_server_start", "hjcd_server_stop", "hjcd_submit", "hjcd_poll", "hjcd_wait",
 )
 
 
@@ -70,6 +71,18 @@ class hjcd_batch_item(ct.Structure):
     ]
 
 
+class hjcd_server_opts(ct.Structure):
+    _fields_ = [
+        ("max_inflight", ct.c_int32), ("max_batch_requests", ct.c_int32), ("max_batch_seeds", ct.c_int64),
+        ("memory_budget", ct.c_uint64), ("params", ct.POINTER(hjcd_params)),
+    ]
+
+
+class hjcd_request_info(ct.Structure):
+    _fields_ = [("status", ct.c_int32), ("batch_requests", ct.c_int32), ("queued_ms", ct.c_double),
+                ("total_ms", ct.c_double)]
+
+
 class hjcd_ccd_trace(ct.Structure):
     _fields_ = [(k, ct.c_void_p) for k in ("dp", "rp", "dq", "rq", "jp", "jo", "accepted", "th_hat",
                                                    "op", "pq")]
@@ -98,6 +111,11 @@ _SIGS = {
     "hjcd_solve": (_ST, [_V, _I32, _I32, _I, _V, ct.POINTER(hjcd_solve_opts), _V, _V, _V, _V]),
     "hjcd_solve_noalloc": (_ST, [_V, _I32, _I32, _I, _V, ct.POINTER(hjcd_solve_opts), _V, _V, _V, _V]),
     "hjcd_solve_batch": (_ST, [_V, _I, ct.POINTER(hjcd_batch_item), ct.POINTER(hjcd_params), _V]),
+    "hjcd_server_start": (_ST, [_V, ct.POINTER(hjcd_server_opts)]),
+    "hjcd_server_stop": (_ST, [_V]),
+    "hjcd_submit": (_ST, [_V, ct.POINTER(hjcd_batch_item), ct.POINTER(_I64)]),
+    "hjcd_poll": (_ST, [_V, _I64, ct.POINTER(_I32), ct.POINTER(hjcd_request_info)]),
+    "hjcd_wait": (_ST, [_V, _I64, ct.c_double, ct.POINTER(hjcd_request_info)]),
     "hjcd_fk": (_ST, [_V, _I32, _I64, _V, _I64, _V, _V]),
     "hjcd_sample_seeds": (_ST, [_V, _I32, _I64, _V, _V, _U64, _V, _I64, _V]),
     "hjcd_po_ccd": (_ST, [_V, _I32, _I, _V, _F, _F, _U64, ct.POINTER(hjcd_params), _I64, _V, _V, _V, _V, _I64,
@@ -228,6 +246,37 @@ def hjcd_solve_batch(ctx, items, params=None, stream=None) -> None:
     arr = (hjcd_batch_item * len(items))(*items)
     _check(ctx, load().hjcd_solve_batch(ctx, len(items), arr, ct.byref(params) if params is not None else None,
                                         stream_handle(stream)))
+
+
+def hjcd_server_start(ctx, max_inflight=0, max_batch_requests=0, max_batch_seeds=0, memory_budget=0,
+                      params=None) -> None:
+    o = hjcd_server_opts(int(max_inflight), int(max_batch_requests), int(max_batch_seeds), int(memory_budget),
+                         ct.pointer(params) if params is not None else None)
+    _check(ctx, load().hjcd_server_start(ctx, ct.byref(o)))
+
+
+def hjcd_server_stop(ctx) -> None:
+    _check(ctx, load().hjcd_server_stop(ctx))
+
+
+def hjcd_submit(ctx, item: hjcd_batch_item) -> int:
+    rid = _I64()
+    _check(ctx, load().hjcd_submit(ctx, ct.byref(item), ct.byref(rid)))
+    return rid.value
+
+
+def hjcd_poll(ctx, request_id) -> hjcd_request_info | None:
+    """The request's info once it is done, else None."""
+    done = _I32()
+    info = hjcd_request_info()
+    _check(ctx, load().hjcd_poll(ctx, int(request_id), ct.byref(done), ct.byref(info)))
+    return info if done.value else None
+
+
+def hjcd_wait(ctx, request_id, timeout_s: float = 60.0) -> hjcd_request_info:
+    info = hjcd_request_info()
+    _check(ctx, load().hjcd_wait(ctx, int(request_id), float(timeout_s), ct.byref(info)))
+    return info
 
 
 def hjcd_fk(ctx, robot_id, n_cand, theta, ld, out_pq, stream=None) -> None:
