@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--top-k", type=int, default=1)
     ap.add_argument("--cpu-sample", type=int, default=96, help="targets in the timed oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--uneven-steps", type=int, default=3, help="timed steps of the uneven 8-chain batch (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=4.0,
+                    help="length of the served Poisson trace at 2000 req/s (0: skip the serving comparison)")
     return ap.parse_args()
 
 
@@ -256,6 +259,151 @@ def reference_arm(args):
     barrier(dist)
 
 
+def collision_free_targets(ctx, rid, sid, rob, pool, count, dev):
+    """FK of the first `count` joint samples of `pool` the library finds collision-free."""
+    import torch
+    th = torch.as_tensor(np.ascontiguousarray(pool.T), dtype=torch.float32, device=dev)
+    hit = ctx.collide(rid, sid, th).bool() if len(rob.sph_body) else torch.zeros(th.shape[1], dtype=torch.bool,
+                                                                                  device=dev)
+    keep = th[:, ~hit][:, :count].contiguous()
+    return ctx.fk(rid, keep).contiguous(), int(keep.shape[1]), float((~hit).float().mean())
+
+
+def uneven_leg(ctx, args, dev, stream):
+    """The uneven batch: 8 random chains x 500 targets, per-target seed counts
+    log-uniform in [32, 4096], one scene, packed into one launch per phase."""
+    import torch
+    from paper_2510_07514_gb300 import hjcd, inputs
+    wl = inputs.cfg3()
+    sid = ctx.set_scene(wl.scene)
+    items, outs, accept = [], [], []
+    for i, rob in enumerate(wl.robots):
+        rid = ctx.add_robot(rob)
+        tg, got, acc = collision_free_targets(ctx, rid, sid, rob, wl.pools[i], wl.n_targets, dev)
+        accept.append(acc)
+        if got < wl.n_targets:
+            return {"skipped": f"chain {i}: only {got} collision-free samples of {len(wl.pools[i])}"}
+        it, out = ctx.batch_item(rid, sid, tg, 1, 1, wl.seed + i, rob.n, wl.eps_pos, wl.eps_ori,
+                                 samples_per_target=wl.samples[i])
+        items.append(it)
+        outs.append(out)
+    C = int(sum(int(s.sum()) for s in wl.samples))
+    T = wl.n_targets * len(wl.robots)
+    for _ in range(2):
+        ctx.solve_batch(items, stream=stream)
+    torch.cuda.synchronize(dev)
+    l0 = hjcd.hjcd_launch_count(ctx.h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.uneven_steps):
+        ctx.solve_batch(items, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.uneven_steps
+    succ = []
+    for out in outs:
+        c, e = out[2].cpu().numpy(), out[1].cpu().numpy()
+        succ.append((c > 0) & (e[:, 0, 0] <= wl.eps_pos) & (e[:, 0, 1] <= wl.eps_ori))
+    return {"workload": wl.name, "dofs": [r.n for r in wl.robots], "link_spheres": [len(r.sph_body) for r in wl.robots],
+            "targets": T, "seeds": C, "ms_per_step": ms, "solves_per_s": T / (ms * 1e-3),
+            "candidates_per_s": C / (ms * 1e-3), "success_rate": float(np.mean(np.concatenate(succ))),
+            "collision_free_fraction_of_samples": accept,
+            "launches_per_step": (hjcd.hjcd_launch_count(ctx.h) - l0) / args.uneven_steps}
+
+
+def _serve_run(ctx, reqs, trace, idx, rate_scale, server_kw):
+    """Submit requests idx at the trace's arrival times (divided by rate_scale)
+    to a server started with server_kw; per-request latency and throughput."""
+    from paper_2510_07514_gb300 import hjcd
+    hjcd.hjcd_server_start(ctx.h, **server_kw)
+    ids, t_sub = [], []
+    try:
+        t0 = time.perf_counter()
+        base = trace.t[idx[0]] / rate_scale
+        for k in idx:
+            due = t0 + trace.t[k] / rate_scale - base
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                if due - now > 2e-3:
+                    time.sleep(due - now - 1e-3)
+            t_sub.append(time.perf_counter())
+            ids.append(hjcd.hjcd_submit(ctx.h, reqs[k][0]))
+        infos = [hjcd.hjcd_wait(ctx.h, i, 600.0) for i in ids]
+    finally:
+        hjcd.hjcd_server_stop(ctx.h)
+    lat = np.array([inf.total_ms for inf in infos])
+    done = np.array(t_sub) + lat / 1e3
+    span = float(done.max() - t_sub[0])
+    T = int(sum(trace.n_targets[k] for k in idx))
+    ok = all(inf.status == 0 for inf in infos)
+    succ = []
+    for k in idx:
+        c, e = reqs[k][1][2].numpy(), reqs[k][1][1].numpy()
+        succ.append((c > 0) & (e[:, 0, 0] <= 1e-3) & (e[:, 0, 1] <= 1e-2))
+    return {"requests": len(idx), "offered_req_per_s": float(len(idx) / max(trace.t[idx[-1]] / rate_scale - base, 1e-9)),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "solves_per_s": T / span, "req_per_s": len(idx) / span,
+            "mean_batch_requests": float(np.mean([inf.batch_requests for inf in infos])),
+            "success_rate": float(np.mean(np.concatenate(succ))), "all_ok": ok}
+
+
+def serving_leg(ctx, args, dev):
+    """Served (continuous batching) vs plain (one request per launch sequence)
+    on the Poisson trace of 1-8 targets x 32-4096 seeds requests for four
+    resident chains, each request with its own 0-500-sphere scene."""
+    import torch
+    from paper_2510_07514_gb300 import api, inputs
+    chains = inputs.cfg3_chains()
+    rids = [ctx.add_robot(chains[i]) for i in inputs.CFG4_ROBOTS]
+    tpls = inputs.cfg4_templates()
+    banks = []
+    for tp in tpls:
+        sid = ctx.set_scene(tp.scene)
+        rob = chains[inputs.CFG4_ROBOTS[tp.robot]]
+        tg, got, _ = collision_free_targets(ctx, rids[tp.robot], sid, rob, tp.pool, 8, dev)
+        banks.append(tg.cpu().numpy())
+    rate = 2000.0
+    trace = inputs.cfg4_trace(rate, args.serve_seconds, len(tpls))
+    # templates whose scene leaves no collision-free sample are replaced by the next usable one
+    usable = [i for i in range(len(tpls)) if len(banks[i]) > 0]
+    reqs = []
+    for k in range(len(trace.t)):
+        j = int(trace.template[k])
+        if len(banks[j]) == 0:
+            j = usable[j % len(usable)]
+        tp, bank = tpls[j], banks[j]
+        T = int(min(trace.n_targets[k], len(bank)))
+        trace.n_targets[k] = T
+        rob = chains[inputs.CFG4_ROBOTS[tp.robot]]
+        tg = torch.as_tensor(np.ascontiguousarray(bank[:T]), dtype=torch.float32)
+        reqs.append(ctx.batch_item(rids[tp.robot], -1, tg, int(trace.seeds[k]), 1, int(trace.seed[k]), rob.n,
+                                   spheres=tp.scene.sph_xyzr, boxes=None, device=torch.device("cpu")))
+    idx = np.arange(len(trace.t))
+    served = _serve_run(ctx, reqs, trace, idx, 1.0, dict(max_inflight=3))
+    # plain path: the same requests one launch sequence at a time; slower offered rates until its p99
+    # is no worse than the served p99 (each run on the first requests of the trace, about 1.5 s)
+    plain_runs = []
+    scale = 1.0
+    for _ in range(7):
+        n_req = int(min(len(idx), max(200, rate * scale * 1.5)))
+        r = _serve_run(ctx, reqs, trace, idx[:n_req], scale, dict(max_inflight=1, max_batch_requests=1))
+        r["rate_scale"] = scale
+        plain_runs.append(r)
+        if r["p99_ms"] <= served["p99_ms"]:
+            break
+        scale /= 2.0
+    match = [r for r in plain_runs if r["p99_ms"] <= served["p99_ms"]]
+    ref = max(match, key=lambda r: r["solves_per_s"]) if match else plain_runs[-1]
+    return {"trace": f"Poisson {rate:.0f} req/s for {args.serve_seconds:g} s; 1-8 targets, 32-4096 seeds, "
+                     "4 resident chains (7/12/16/20 DoF), own scene of 0-500 spheres per request",
+            "templates_usable": f"{len(usable)} of {len(tpls)}",
+            "served": served, "plain": plain_runs,
+            "served_over_plain_at_equal_p99": served["solves_per_s"] / ref["solves_per_s"],
+            "plain_reached_served_p99": bool(match)}
+
+
 def hjcd_arm(args):
     world, rank, local = dist_env()
     import torch
@@ -380,6 +528,10 @@ def hjcd_arm(args):
                 "ms_per_step": float(np.mean(e2e_ms))},
         "clocks": clk, "gpu_launches": int(launches),
     }
+    if world == 1 and args.uneven_steps > 0:
+        line["uneven_batch"] = uneven_leg(ctx, args, dev, stream)
+    if world == 1 and args.serve_seconds > 0:
+        line["serving"] = serving_leg(ctx, args, dev)
     ctx.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample, S)

@@ -310,3 +310,75 @@ def cfg3_chains() -> list[Robot]:
         counts = rng.integers(6, 13, dof + 1)
         out.append(add_link_spheres(rng, rob, counts, 0.02, 0.05))
     return out
+
+
+@dataclass
+class MultiWorkload:
+    """Uneven batch: several robots, each with a pool of joint samples from
+    which collision-free targets are drawn, per-target seed counts, one scene."""
+    name: str
+    robots: list
+    scene: Scene
+    pools: list                 # per robot: joint samples (filter with the scene)
+    n_targets: int              # per robot
+    samples: list               # per robot: seed count per target
+    seed: int
+    eps_pos: float = 1e-3
+    eps_ori: float = 1e-2
+
+
+def cfg3(n_targets: int = 500, pool_factor: int = 40, lo: int = 32, hi: int = 4096) -> MultiWorkload:
+    """The eight random chains (6-20 DoF, 6-12 link spheres per body), 500
+    targets each, seed counts log-uniform in [32, 4096] per target, a scene of
+    100 obstacle spheres (cfg2's distributions)."""
+    rng = np.random.default_rng(CFG_SEED[3] + 100)
+    chains = cfg3_chains()
+    scene = random_scene(rng, 100, 0)
+    pools = [joint_samples(rng, r, n_targets * pool_factor) for r in chains]
+    samples = [log_uniform_counts(rng, n_targets, lo, hi) for _ in chains]
+    return MultiWorkload(f"8 chains x {n_targets} targets, seeds log-uniform [{lo}, {hi}], 100 obstacle spheres",
+                         chains, scene, pools, n_targets, samples, CFG_SEED[3])
+
+
+CFG4_ROBOTS = (1, 3, 4, 5)  # rows of cfg3_chains(): 7, 12, 16 and 20 DoF
+
+
+@dataclass
+class ServingTemplate:
+    """One request shape of the serving trace: a robot (row of CFG4_ROBOTS),
+    its own scene and a pool of joint samples to draw collision-free targets from."""
+    robot: int
+    scene: Scene
+    pool: np.ndarray
+
+
+def cfg4_templates(count: int = 64, pool: int = 256) -> list:
+    """Request templates: robot uniform over the four resident chains, scene
+    of U{0..500} obstacle spheres (cfg2's distributions), joint-sample pool."""
+    rng = np.random.default_rng(CFG_SEED[4])
+    chains = cfg3_chains()
+    out = []
+    for _ in range(count):
+        r = int(rng.integers(0, len(CFG4_ROBOTS)))
+        sc = random_scene(rng, int(rng.integers(0, 501)), 0)
+        out.append(ServingTemplate(r, sc, joint_samples(rng, chains[CFG4_ROBOTS[r]], pool)))
+    return out
+
+
+@dataclass
+class ServingTrace:
+    """Poisson arrivals: time (s), template, target count (1-8), seeds per
+    target (log-uniform [32, 4096], one count per request), request seed."""
+    t: np.ndarray
+    template: np.ndarray
+    n_targets: np.ndarray
+    seeds: np.ndarray
+    seed: np.ndarray
+
+
+def cfg4_trace(rate: float = 2000.0, duration: float = 60.0, n_templates: int = 64, salt: int = 0) -> ServingTrace:
+    rng = np.random.default_rng(CFG_SEED[4] + 1 + salt)
+    n = int(rng.poisson(rate * duration))
+    t = np.sort(rng.uniform(0.0, duration, n))
+    return ServingTrace(t, rng.integers(0, n_templates, n), rng.integers(1, 9, n), log_uniform_counts(rng, n, 32, 4096),
+                        rng.integers(0, 2 ** 63 - 1, n, dtype=np.int64))
