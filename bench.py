@@ -300,6 +300,24 @@ def uneven_leg(ctx, args, dev, stream):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / args.uneven_steps
+    # the same batch captured as one CUDA graph; host wall time per step, direct call vs replay
+    g = hjcd.hjcd_graph_create(ctx.h, items)
+    try:
+        hjcd.hjcd_graph_launch(ctx.h, g, stream)
+        torch.cuda.synchronize(dev)
+        wall = {"direct": [], "graph": []}
+        for _ in range(args.uneven_steps):
+            t0 = time.perf_counter()
+            ctx.solve_batch(items, stream=stream)
+            torch.cuda.synchronize(dev)
+            wall["direct"].append(time.perf_counter() - t0)
+            t0 = time.perf_counter()
+            hjcd.hjcd_graph_launch(ctx.h, g, stream)
+            torch.cuda.synchronize(dev)
+            wall["graph"].append(time.perf_counter() - t0)
+        hjcd.hjcd_graph_check(ctx.h, g)
+    finally:
+        hjcd.hjcd_graph_destroy(g)
     succ = []
     for out in outs:
         c, e = out[2].cpu().numpy(), out[1].cpu().numpy()
@@ -308,6 +326,8 @@ def uneven_leg(ctx, args, dev, stream):
             "targets": T, "seeds": C, "ms_per_step": ms, "solves_per_s": T / (ms * 1e-3),
             "candidates_per_s": C / (ms * 1e-3), "success_rate": float(np.mean(np.concatenate(succ))),
             "collision_free_fraction_of_samples": accept,
+            "wall_ms_direct": 1e3 * float(np.median(wall["direct"])),
+            "wall_ms_graph_replay": 1e3 * float(np.median(wall["graph"])),
             "launches_per_step": (hjcd.hjcd_launch_count(ctx.h) - l0) / args.uneven_steps}
 
 

@@ -178,6 +178,25 @@ typedef struct hjcd_batch_item {
 hjcd_status hjcd_solve_batch(hjcd_ctx* ctx, int n_items, const hjcd_batch_item* items,
                              const hjcd_params* params, void* stream);
 
+/* ---- a batch captured as a CUDA graph ----------------------------------------- */
+
+/* A fixed batch (robots, scenes, seed counts, tolerances, seeds, top_k and
+ * caps as in hjcd_solve_batch) captured once, with its own workspace, as one
+ * CUDA graph of the whole launch sequence; each hjcd_graph_launch replays it
+ * on `stream`, reading the targets from the items' buffers at replay time and
+ * writing their outputs, so a control loop that re-solves new poses of the
+ * same shape pays no planning or launch overhead.  Targets and outputs must be
+ * DEVICE buffers that stay valid for the graph's life; the inline obstacles
+ * and seed-count arrays are copied at creation.  Replays of one graph must not
+ * overlap in time (they share the workspace).  The paper has no counterpart. */
+typedef struct hjcd_graph hjcd_graph;
+hjcd_status hjcd_graph_create(hjcd_ctx* ctx, int n_items, const hjcd_batch_item* items,
+                              const hjcd_params* params, hjcd_graph** out);
+hjcd_status hjcd_graph_launch(hjcd_graph* graph, void* stream);
+/* Wait for the last replay and report a bounded device wait that ran out. */
+hjcd_status hjcd_graph_check(hjcd_graph* graph);
+void hjcd_graph_destroy(hjcd_graph* graph);
+
 /* ---- serving: continuous batching ------------------------------------------ */
 
 /* Serving loop of a context (Sec. I and Sec. VI motivate interactive use; the

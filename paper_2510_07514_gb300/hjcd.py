@@ -34,6 +34,7 @@ EXPORTS = (
     "hjcd_set_profiling", "hjcd_phase_times", "hjcd_counters", "hjcd_launch_count", "hjcd_ffma_probe",
     "hjcd_solve_noalloc", "hjcd_solve_batch",
     "hjcd_server_start", "hjcd_server_stop", "hjcd_submit", "hjcd_poll", "hjcd_wait",
+    "hjcd_graph_create", "hjcd_graph_launch", "hjcd_graph_check", "hjcd_graph_destroy",
 )
 
 
@@ -112,6 +113,10 @@ _SIGS = {
     "hjcd_solve_noalloc": (_ST, [_V, _I32, _I32, _I, _V, ct.POINTER(hjcd_solve_opts), _V, _V, _V, _V]),
     "hjcd_solve_batch": (_ST, [_V, _I, ct.POINTER(hjcd_batch_item), ct.POINTER(hjcd_params), _V]),
     "hjcd_server_start": (_ST, [_V, ct.POINTER(hjcd_server_opts)]),
+    "hjcd_graph_create": (_ST, [_V, _I, ct.POINTER(hjcd_batch_item), ct.POINTER(hjcd_params), ct.POINTER(_V)]),
+    "hjcd_graph_launch": (_ST, [_V, _V]),
+    "hjcd_graph_check": (_ST, [_V]),
+    "hjcd_graph_destroy": (None, [_V]),
     "hjcd_server_stop": (_ST, [_V]),
     "hjcd_submit": (_ST, [_V, ct.POINTER(hjcd_batch_item), ct.POINTER(_I64)]),
     "hjcd_poll": (_ST, [_V, _I64, ct.POINTER(_I32), ct.POINTER(hjcd_request_info)]),
@@ -246,6 +251,27 @@ def hjcd_solve_batch(ctx, items, params=None, stream=None) -> None:
     arr = (hjcd_batch_item * len(items))(*items)
     _check(ctx, load().hjcd_solve_batch(ctx, len(items), arr, ct.byref(params) if params is not None else None,
                                         stream_handle(stream)))
+
+
+def hjcd_graph_create(ctx, items, params=None) -> int:
+    """Capture a batch (device targets and outputs) as a replayable graph; returns its handle."""
+    arr = (hjcd_batch_item * len(items))(*items)
+    g = _V()
+    _check(ctx, load().hjcd_graph_create(ctx, len(items), arr, ct.byref(params) if params is not None else None,
+                                         ct.byref(g)))
+    return g.value
+
+
+def hjcd_graph_launch(ctx, graph, stream=None) -> None:
+    _check(ctx, load().hjcd_graph_launch(graph, stream_handle(stream)))
+
+
+def hjcd_graph_check(ctx, graph) -> None:
+    _check(ctx, load().hjcd_graph_check(graph))
+
+
+def hjcd_graph_destroy(graph) -> None:
+    load().hjcd_graph_destroy(graph)
 
 
 def hjcd_server_start(ctx, max_inflight=0, max_batch_requests=0, max_batch_seeds=0, memory_budget=0,

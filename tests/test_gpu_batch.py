@@ -211,3 +211,43 @@ def test_batch_edge_cases(ctx):
         ctx.solve_batch(its)
     assert ei.value.status == hjcd.HJCD_EINVAL
     ctx.solve_batch(its[:hjcd.HJCD_MAX_BATCH_ROBOTS])
+
+
+def test_graph_replay_equals_the_batch_and_follows_new_targets(ctx):
+    robs, rids, scene, sid, reqs = _setup(ctx)
+    pairs = [_item(ctx, rids, sid, robs, r) for r in reqs]
+    g = hjcd.hjcd_graph_create(ctx.h, [p[0] for p in pairs])
+    try:
+        hjcd.hjcd_graph_launch(ctx.h, g)
+        hjcd.hjcd_graph_check(ctx.h, g)
+        for r, (it, out) in zip(reqs, pairs):
+            a_it, a_out = _item(ctx, rids, sid, robs, r)
+            ctx.solve_batch([a_it])
+            _same(out, a_out)
+        # new poses written into the same target buffers: the replay solves them
+        rng = np.random.default_rng(77)
+        new = []
+        for r, (it, out) in zip(reqs, pairs):
+            rob = robs[r["ri"]]
+            tg = f32(orc.pose(orc.Robot(rob), f32(rng.uniform(rob.lo, rob.hi, (r["T"], rob.n)))))
+            t_dev = torch.as_tensor(np.ascontiguousarray(tg), dtype=torch.float32)
+            torch.cuda.synchronize()
+            ctx_keep = [k for k in ctx._keep if isinstance(k, torch.Tensor) and k.data_ptr() == it.targets_pq]
+            assert ctx_keep, "target buffer of the item not found"
+            ctx_keep[0].copy_(t_dev)
+            q = dict(r)
+            q["tg"] = tg
+            new.append(q)
+        for _ in range(2):
+            hjcd.hjcd_graph_launch(ctx.h, g)
+        hjcd.hjcd_graph_check(ctx.h, g)
+        for r, (it, out) in zip(new, pairs):
+            a_it, a_out = _item(ctx, rids, sid, robs, r)
+            ctx.solve_batch([a_it])
+            _same(out, a_out)
+    finally:
+        hjcd.hjcd_graph_destroy(g)
+    h_it, _ = _item(ctx, rids, sid, robs, reqs[0], device="cpu")
+    with pytest.raises(hjcd.HjcdError) as ei:
+        hjcd.hjcd_graph_create(ctx.h, [h_it])
+    assert ei.value.status == hjcd.HJCD_EINVAL
