@@ -197,6 +197,33 @@ hjcd_status hjcd_graph_launch(hjcd_graph* graph, void* stream);
 hjcd_status hjcd_graph_check(hjcd_graph* graph);
 void hjcd_graph_destroy(hjcd_graph* graph);
 
+/* ---- launch configuration and autotuning --------------------------------------- */
+
+/* Candidates per CTA of the PO-CCD kernel (64, 128 or 256) and warps per CTA
+ * of the PJ-IK kernel (2, 4 or 8) for every later launch of the context.
+ * Results do not depend on them. */
+hjcd_status hjcd_set_launch_config(hjcd_ctx* ctx, int32_t ccd_block, int32_t lm_warps);
+
+typedef struct hjcd_tune_report {
+    int32_t ccd_block, lm_warps;        /* launch configuration picked (now set on the context) */
+    int32_t cd_max_iters, lm_max_iters; /* iteration caps picked (in *tuned) */
+    float success_rate;                 /* of the picked caps on the calibration batch */
+    float best_success_rate;            /* best rate of any swept caps */
+    double ms;                          /* median time of the calibration batch with the picks */
+    int32_t trials;                     /* configurations timed */
+} hjcd_tune_report;
+
+/* Autotune on a calibration batch (items as for hjcd_solve_batch; their
+ * outputs are not written, top_k is taken as 1).  First every launch
+ * configuration is timed and the fastest set on the context; then PO-CCD
+ * sweep counts {8, 12, 16, 24, 32, 48} x PJ-IK caps {8, 12, 16, 20, 30} are
+ * timed and the fastest pair whose success rate is within success_tol of the
+ * best swept rate goes to *tuned (base, or the defaults, with those caps).
+ * Each configuration: one warm-up and the median of `repeats` (0: 3) solves.
+ * The paper tunes nothing; it states its iteration caps as parameters. */
+hjcd_status hjcd_autotune(hjcd_ctx* ctx, int n_items, const hjcd_batch_item* items, const hjcd_params* base,
+                          float success_tol, int32_t repeats, hjcd_params* tuned, hjcd_tune_report* report);
+
 /* ---- serving: continuous batching ------------------------------------------ */
 
 /* Serving loop of a context (Sec. I and Sec. VI motivate interactive use; the

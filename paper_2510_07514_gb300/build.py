@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB_DIR = os.path.join(HERE, "lib")
 OBJ_DIR = os.path.join(LIB_DIR, "obj")
 LIB_PATH = os.path.join(LIB_DIR, "libhjcd.so")
-SOURCES = ["capi.cu", "wave.cu", "serve.cu", "graph.cu", "k_ccd.cu", "k_lm.cu", "k_select.cu", "k_collide.cu", "k_misc.cu"]
+SOURCES = ["capi.cu", "wave.cu", "serve.cu", "graph.cu", "tune.cu", "k_ccd.cu", "k_lm.cu", "k_select.cu", "k_collide.cu", "k_misc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                 "-I", INCLUDE, "-I", CSRC]

@@ -366,6 +366,7 @@ struct CcdArgs {
     hjcd_params P;
     hjcd_ccd_trace tr;
     Counters* cnt;
+    int32_t block;  // threads (candidates) per CTA: 64, 128 (default, also for 0) or 256
 };
 
 struct LmArgs {
@@ -381,6 +382,7 @@ struct LmArgs {
     hjcd_lm_trace tr;
     Counters* cnt;
     unsigned long long* queue;  // candidate queue head, zero at launch
+    int32_t warps;  // warps per CTA: 2, 4 (default, also for 0) or 8
 };
 
 struct DupArgs {

@@ -64,6 +64,8 @@ struct hjcd_ctx {
     cudaEvent_t ev[6] = {};
     bool ev_valid = false;
     std::atomic<int64_t> launches{0};
+    int32_t ccd_block = 128;  // launch configuration (hjcd_set_launch_config, hjcd_autotune)
+    int32_t lm_warps = 4;
     std::mutex api_mu;  // robots/scenes tables against the serving thread
     hjcd::Server* server = nullptr;  // owned; freed by server_stop
 };
@@ -122,7 +124,7 @@ struct WaveItem {
     float eps_pos = 0.0f, eps_ori = 0.0f;
     uint64_t seed = 0;
     int top_k = 1;
-    int cd_iters = 0, lm_iters = 0;
+    int cd_iters = -1, lm_iters = -1;  // < 0: the batch parameters' caps
     float* out_q = nullptr;  // [T][top_k][n], host or device
     float* out_err = nullptr;  // [T][top_k][2]
     int32_t* out_count = nullptr;  // [T]

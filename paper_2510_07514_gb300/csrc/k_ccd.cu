@@ -23,16 +23,19 @@ namespace hjcd {
 
 namespace {
 
-constexpr int kCcdThreads = 128;
+constexpr int kCcdThreads = 128;  // default CTA size (candidates per CTA); 64 and 256 also built
 
-// shared-memory column of a thread: theta[n], then (px py pz zx zy zz) per joint
-struct Col {
+// shared-memory column of a thread in a CTA of TH threads: theta[n], then
+// (px py pz zx zy zz) per joint
+template <int TH>
+struct ColT {
     float* base;
     int n;
-    __device__ __forceinline__ float& th(int j) const { return base[j * kCcdThreads]; }
-    __device__ __forceinline__ float* fr(int j) const { return base + (n + 6 * j) * kCcdThreads; }
+    __device__ __forceinline__ float& th(int j) const { return base[j * TH]; }
+    __device__ __forceinline__ float* fr(int j) const { return base + (n + 6 * j) * TH; }
 };
 
+template <class Col>
 __device__ __forceinline__ void sample_seed(const RobotParams& R, const TargetDesc& T, uint32_t s, const Col& col) {
 #pragma unroll 1
     for (int b = 0; 4 * b < R.n; ++b) {
@@ -45,8 +48,10 @@ __device__ __forceinline__ void sample_seed(const RobotParams& R, const TargetDe
     }
 }
 
-template <bool TRACE>
-__global__ void __launch_bounds__(kCcdThreads, 4) k_ccd(const CcdArgs A) {
+template <bool TRACE, int TH>
+__global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
+    using Col = ColT<TH>;
+    constexpr int kCcdThreads = TH;
     extern __shared__ __align__(16) float sm[];
     const RobotParams* rob = stage_robots(sm, A.rs);
     float* const colbase = sm + robots_smem_bytes(A.rs.n) / sizeof(float) + threadIdx.x;
@@ -261,7 +266,7 @@ __global__ void __launch_bounds__(kCcdThreads, 4) k_ccd(const CcdArgs A) {
 __global__ void __launch_bounds__(kCcdThreads) k_sample(const RobotParams R, uint32_t k0, uint32_t k1, CandMap map,
                                                         int64_t C, float* th_out, int64_t ld) {
     extern __shared__ float sm[];
-    const Col col{sm + threadIdx.x, R.n};
+    const ColT<kCcdThreads> col{sm + threadIdx.x, R.n};
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
         int32_t t, s;
         map.lookup(c, t, s);  // only the row index keys the stream
@@ -275,24 +280,31 @@ __global__ void __launch_bounds__(kCcdThreads) k_sample(const RobotParams R, uin
     }
 }
 
-template <bool TRACE>
+template <bool TRACE, int TH>
 void launch_ccd_t(const CcdArgs& A, cudaStream_t st) {
-    const size_t smem = robots_smem_bytes(A.rs.n) + sizeof(float) * 7 * A.rs.n_max * kCcdThreads;
+    const size_t smem = robots_smem_bytes(A.rs.n) + sizeof(float) * 7 * A.rs.n_max * TH;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_ccd<TRACE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(robots_smem_bytes(kMaxLaunchRobots) + sizeof(float) * 7 * kMaxDof * kCcdThreads));
+        cudaFuncSetAttribute(k_ccd<TRACE, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(robots_smem_bytes(kMaxLaunchRobots) + sizeof(float) * 7 * kMaxDof * TH));
         attr = true;
     }
-    k_ccd<TRACE><<<grid_for(A.C, kCcdThreads, 16), kCcdThreads, smem, st>>>(A);
+    k_ccd<TRACE, TH><<<grid_for(A.C, TH, 16 * 128 / TH), TH, smem, st>>>(A);
+}
+
+template <bool TRACE>
+void launch_ccd_b(const CcdArgs& A, cudaStream_t st) {
+    if (A.block == 64) launch_ccd_t<TRACE, 64>(A, st);
+    else if (A.block == 256) launch_ccd_t<TRACE, 256>(A, st);
+    else launch_ccd_t<TRACE, 128>(A, st);
 }
 
 }  // namespace
 
 void launch_ccd(const CcdArgs& A, bool trace, cudaStream_t st) {
     if (A.C <= 0) return;
-    if (trace) launch_ccd_t<true>(A, st);
-    else launch_ccd_t<false>(A, st);
+    if (trace) launch_ccd_b<true>(A, st);
+    else launch_ccd_b<false>(A, st);
 }
 
 void launch_sample(const RobotParams& R, uint64_t seed, CandMap map, int64_t C, float* th, int64_t ld,

@@ -37,7 +37,7 @@ namespace hjcd {
 
 namespace {
 
-constexpr int kLmWarps = 4;
+constexpr int kLmWarps = 4;  // default warps per CTA; 2 and 8 also built
 constexpr int kMaxTrials = 32;  // A + 1 <= 32 (validated by the host)
 
 __host__ __device__ constexpr int tri(int r, int c) { return r * (r + 1) / 2 + c; }
@@ -161,8 +161,8 @@ __device__ __forceinline__ unsigned long long warp_trials(const RobotParams* rob
     return cnt;
 }
 
-template <bool TRACE>
-__global__ void __launch_bounds__(kLmWarps * 32, 4) k_lm(const LmArgs A) {
+template <bool TRACE, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
     extern __shared__ __align__(16) float smem_f[];
     const RobotParams* rob = stage_robots(smem_f, A.rs);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -492,30 +492,37 @@ __global__ void __launch_bounds__(kLmWarps * 32, 4) k_lm(const LmArgs A) {
     }
 }
 
-template <bool TRACE>
+template <bool TRACE, int WARPS>
 void launch_lm_t(const LmArgs& A, cudaStream_t st) {
-    const size_t smem = robots_smem_bytes(A.rs.n) + sizeof(float) * (size_t)lm_warp_words(A.rs.n_max) * kLmWarps;
+    const size_t smem = robots_smem_bytes(A.rs.n) + sizeof(float) * (size_t)lm_warp_words(A.rs.n_max) * WARPS;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_lm<TRACE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_lm<TRACE, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(robots_smem_bytes(kMaxLaunchRobots) +
-                                   sizeof(float) * lm_warp_words(kMaxDof) * kLmWarps));
+                                   sizeof(float) * lm_warp_words(kMaxDof) * WARPS));
         attr = true;
     }
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lm<TRACE>, kLmWarps * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lm<TRACE, WARPS>, WARPS * 32, smem);
     if (per_sm < 1) per_sm = 1;
-    const int64_t want = (A.C + 32 * kLmWarps - 1) / (32 * kLmWarps);
+    const int64_t want = (A.C + 32 * WARPS - 1) / (32 * WARPS);
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * per_sm));
-    k_lm<TRACE><<<g, kLmWarps * 32, smem, st>>>(A);
+    k_lm<TRACE, WARPS><<<g, WARPS * 32, smem, st>>>(A);
+}
+
+template <bool TRACE>
+void launch_lm_w(const LmArgs& A, cudaStream_t st) {
+    if (A.warps == 2) launch_lm_t<TRACE, 2>(A, st);
+    else if (A.warps == 8) launch_lm_t<TRACE, 8>(A, st);
+    else launch_lm_t<TRACE, kLmWarps>(A, st);
 }
 
 }  // namespace
 
 void launch_lm(const LmArgs& A, bool trace, cudaStream_t st) {
     if (A.C <= 0) return;
-    if (trace) launch_lm_t<true>(A, st);
-    else launch_lm_t<false>(A, st);
+    if (trace) launch_lm_w<true>(A, st);
+    else launch_lm_w<false>(A, st);
 }
 
 }  // namespace hjcd

@@ -249,6 +249,7 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
     ca.n_iters = -1;
     ca.P = P;
     ca.cnt = ctx->cnt;
+    ca.block = ctx->ccd_block;
     launch_ccd(ca, false, s);
     if ((st = after_launch(ctx, 1))) return st;
     if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[1], s));
@@ -274,6 +275,7 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
     la.P = P;
     la.cnt = ctx->cnt;
     la.queue = queue;
+    la.warps = ctx->lm_warps;
     launch_lm(la, false, s);
     if ((st = after_launch(ctx, 1))) return st;
     if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[3], s));

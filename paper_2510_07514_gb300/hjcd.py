@@ -35,6 +35,7 @@ EXPORTS = (
     "hjcd_solve_noalloc", "hjcd_solve_batch",
     "hjcd_server_start", "hjcd_server_stop", "hjcd_submit", "hjcd_poll", "hjcd_wait",
     "hjcd_graph_create", "hjcd_graph_launch", "hjcd_graph_check", "hjcd_graph_destroy",
+    "hjcd_set_launch_config", "hjcd_autotune",
 )
 
 
@@ -84,6 +85,12 @@ class hjcd_request_info(ct.Structure):
                 ("total_ms", ct.c_double)]
 
 
+class hjcd_tune_report(ct.Structure):
+    _fields_ = [("ccd_block", ct.c_int32), ("lm_warps", ct.c_int32), ("cd_max_iters", ct.c_int32),
+                ("lm_max_iters", ct.c_int32), ("success_rate", ct.c_float), ("best_success_rate", ct.c_float),
+                ("ms", ct.c_double), ("trials", ct.c_int32)]
+
+
 class hjcd_ccd_trace(ct.Structure):
     _fields_ = [(k, ct.c_void_p) for k in ("dp", "rp", "dq", "rq", "jp", "jo", "accepted", "th_hat",
                                                    "op", "pq")]
@@ -113,6 +120,9 @@ _SIGS = {
     "hjcd_solve_noalloc": (_ST, [_V, _I32, _I32, _I, _V, ct.POINTER(hjcd_solve_opts), _V, _V, _V, _V]),
     "hjcd_solve_batch": (_ST, [_V, _I, ct.POINTER(hjcd_batch_item), ct.POINTER(hjcd_params), _V]),
     "hjcd_server_start": (_ST, [_V, ct.POINTER(hjcd_server_opts)]),
+    "hjcd_set_launch_config": (_ST, [_V, _I32, _I32]),
+    "hjcd_autotune": (_ST, [_V, _I, ct.POINTER(hjcd_batch_item), ct.POINTER(hjcd_params), _F, _I32,
+                            ct.POINTER(hjcd_params), ct.POINTER(hjcd_tune_report)]),
     "hjcd_graph_create": (_ST, [_V, _I, ct.POINTER(hjcd_batch_item), ct.POINTER(hjcd_params), ct.POINTER(_V)]),
     "hjcd_graph_launch": (_ST, [_V, _V]),
     "hjcd_graph_check": (_ST, [_V]),
@@ -251,6 +261,19 @@ def hjcd_solve_batch(ctx, items, params=None, stream=None) -> None:
     arr = (hjcd_batch_item * len(items))(*items)
     _check(ctx, load().hjcd_solve_batch(ctx, len(items), arr, ct.byref(params) if params is not None else None,
                                         stream_handle(stream)))
+
+
+def hjcd_set_launch_config(ctx, ccd_block: int, lm_warps: int) -> None:
+    _check(ctx, load().hjcd_set_launch_config(ctx, int(ccd_block), int(lm_warps)))
+
+
+def hjcd_autotune(ctx, items, base=None, success_tol: float = 0.01, repeats: int = 3):
+    """(tuned hjcd_params, hjcd_tune_report) for a calibration batch."""
+    arr = (hjcd_batch_item * len(items))(*items)
+    tuned, rep = hjcd_params(), hjcd_tune_report()
+    _check(ctx, load().hjcd_autotune(ctx, len(items), arr, ct.byref(base) if base is not None else None,
+                                     float(success_tol), int(repeats), ct.byref(tuned), ct.byref(rep)))
+    return tuned, rep
 
 
 def hjcd_graph_create(ctx, items, params=None) -> int:

@@ -251,3 +251,44 @@ def test_graph_replay_equals_the_batch_and_follows_new_targets(ctx):
     with pytest.raises(hjcd.HjcdError) as ei:
         hjcd.hjcd_graph_create(ctx.h, [h_it])
     assert ei.value.status == hjcd.HJCD_EINVAL
+
+
+def test_launch_configuration_does_not_change_results(ctx):
+    robs, rids, scene, sid, reqs = _setup(ctx)
+    ref = None
+    try:
+        for blk, wp in ((128, 4), (64, 2), (256, 8), (64, 8), (256, 2)):
+            hjcd.hjcd_set_launch_config(ctx.h, blk, wp)
+            pairs = [_item(ctx, rids, sid, robs, r) for r in reqs]
+            ctx.solve_batch([p[0] for p in pairs])
+            if ref is None:
+                ref = pairs
+            else:
+                for (a, oa), (b, ob) in zip(ref, pairs):
+                    _same(oa, ob)
+        with pytest.raises(hjcd.HjcdError):
+            hjcd.hjcd_set_launch_config(ctx.h, 96, 4)
+    finally:
+        hjcd.hjcd_set_launch_config(ctx.h, 128, 4)
+
+
+def test_autotune_picks_a_valid_configuration(ctx):
+    wl = inputs.cfg1()
+    rid = ctx.add_robot(wl.robot)
+    rng = np.random.default_rng(51)
+    tg = f32(orc.pose(orc.Robot(wl.robot), f32(rng.uniform(wl.robot.lo, wl.robot.hi, (64, 7)))))
+    it, _ = ctx.batch_item(rid, -1, dev(tg), 128, 1, 3, 7)
+    try:
+        tuned, rep = hjcd.hjcd_autotune(ctx.h, [it], None, 0.02, 2)
+        assert rep.ccd_block in (64, 128, 256) and rep.lm_warps in (2, 4, 8)
+        assert rep.cd_max_iters in (8, 12, 16, 24, 32, 48) and rep.lm_max_iters in (8, 12, 16, 20, 30)
+        assert (tuned.cd_max_iters, tuned.lm_max_iters) == (rep.cd_max_iters, rep.lm_max_iters)
+        assert rep.success_rate >= rep.best_success_rate - 0.02 - 1e-6
+        assert rep.trials == 9 + 30 and rep.ms > 0
+        # the tuned parameters solve the calibration batch at the reported success rate
+        q, e, c = ctx.solve(rid, -1, dev(tg), 128, 1, 3, 7, params=tuned)
+        e, c = host(e), host(c)
+        succ = np.mean((c > 0) & (e[:, 0, 0] <= 1e-3) & (e[:, 0, 1] <= 1e-2))
+        assert abs(succ - rep.success_rate) < 1e-6
+    finally:
+        hjcd.hjcd_set_launch_config(ctx.h, 128, 4)
