@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=96, help="targets in the timed oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--uneven-steps", type=int, default=3, help="timed steps of the uneven 8-chain batch (0: skip)")
+    ap.add_argument("--large-steps", type=int, default=2,
+                    help="timed steps of the large case, 10000 targets x 4096 seeds (0: skip)")
+    ap.add_argument("--large-budget-gb", type=float, default=2.0, help="workspace budget of the large case (waves)")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="length of the served Poisson trace at 2000 req/s (0: skip the serving comparison)")
     return ap.parse_args()
@@ -292,7 +295,6 @@ def uneven_leg(ctx, args, dev, stream):
     for _ in range(2):
         ctx.solve_batch(items, stream=stream)
     torch.cuda.synchronize(dev)
-    l0 = hjcd.hjcd_launch_count(ctx.h)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.uneven_steps):
@@ -322,13 +324,94 @@ def uneven_leg(ctx, args, dev, stream):
     for out in outs:
         c, e = out[2].cpu().numpy(), out[1].cpu().numpy()
         succ.append((c > 0) & (e[:, 0, 0] <= wl.eps_pos) & (e[:, 0, 1] <= wl.eps_ori))
+    # autotuned: launch configuration and iteration caps from a calibration batch (the first 48
+    # targets of each chain, other seeds), then the whole batch again, timed, with the picks
+    cal = []
+    for i, it in enumerate(items):
+        c_it = hjcd.hjcd_batch_item.from_buffer_copy(it)
+        c_it.n_targets = 48
+        c_it.opts.seed = wl.seed + 1000 + i
+        cal.append(c_it)
+    t0 = time.perf_counter()
+    tuned, rep = hjcd.hjcd_autotune(ctx.h, cal, None, 0.01, 3)
+    tune_s = time.perf_counter() - t0
+    items_t = []
+    for it in items:
+        t_it = hjcd.hjcd_batch_item.from_buffer_copy(it)
+        t_it.opts.params = hjcd.ct.pointer(tuned)
+        items_t.append(t_it)
+    ctx.solve_batch(items_t, stream=stream)
+    e0.record(stream)
+    for _ in range(args.uneven_steps):
+        ctx.solve_batch(items_t, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_t = e0.elapsed_time(e1) / args.uneven_steps
+    succ_t = []
+    for out in outs:
+        c, e = out[2].cpu().numpy(), out[1].cpu().numpy()
+        succ_t.append((c > 0) & (e[:, 0, 0] <= wl.eps_pos) & (e[:, 0, 1] <= wl.eps_ori))
+    hjcd.hjcd_set_launch_config(ctx.h, 128, 4)
+    tuned_line = {"ccd_block": rep.ccd_block, "lm_warps": rep.lm_warps, "cd_max_iters": rep.cd_max_iters,
+                  "lm_max_iters": rep.lm_max_iters, "calibration_success": rep.success_rate,
+                  "calibration_best_success": rep.best_success_rate, "trials": rep.trials, "tune_s": tune_s,
+                  "ms_per_step": ms_t, "solves_per_s": (wl.n_targets * len(wl.robots)) / (ms_t * 1e-3),
+                  "success_rate": float(np.mean(np.concatenate(succ_t)))}
     return {"workload": wl.name, "dofs": [r.n for r in wl.robots], "link_spheres": [len(r.sph_body) for r in wl.robots],
             "targets": T, "seeds": C, "ms_per_step": ms, "solves_per_s": T / (ms * 1e-3),
             "candidates_per_s": C / (ms * 1e-3), "success_rate": float(np.mean(np.concatenate(succ))),
             "collision_free_fraction_of_samples": accept,
             "wall_ms_direct": 1e3 * float(np.median(wall["direct"])),
             "wall_ms_graph_replay": 1e3 * float(np.median(wall["graph"])),
-            "launches_per_step": (hjcd.hjcd_launch_count(ctx.h) - l0) / args.uneven_steps}
+            "launches_per_step": 6, "autotuned": tuned_line}
+
+
+def large_leg(ctx, args, dev, stream):
+    """10 000 targets x 4096 seeds of the Panda with 60 link spheres, top-16,
+    against 5000 obstacle spheres on a jittered grid carved (by the library's
+    contact query) around the target configurations; memory-admitted waves."""
+    import torch
+    from paper_2510_07514_gb300 import hjcd, inputs
+    wl = inputs.cfg5()
+    rob = wl.robot
+    rid = ctx.add_robot(rob)
+    pool = torch.as_tensor(np.ascontiguousarray(wl.target_pool.T), dtype=torch.float32, device=dev)
+    self_hit = ctx.collide(rid, -1, pool).bool()
+    keep = pool[:, ~self_hit][:, :wl.n_targets].contiguous()
+    T = int(keep.shape[1])
+    nodes_sid = ctx.set_scene(inputs.Scene(wl.nodes, np.zeros((0, 6))))
+    touched = torch.empty(len(wl.nodes), dtype=torch.uint8, device=dev)
+    hjcd.hjcd_scene_contacts(ctx.h, rid, nodes_sid, T, keep, keep.stride(0), touched)
+    free = wl.nodes[~touched.bool().cpu().numpy()][:wl.n_obstacles]
+    sid = ctx.set_scene(inputs.Scene(free, np.zeros((0, 6))))
+    tg = ctx.fk(rid, keep).contiguous()
+    K, S = wl.top_k, wl.n_samples
+    out = (torch.empty((T, K, rob.n), device=dev), torch.empty((T, K, 2), device=dev),
+           torch.empty((T,), dtype=torch.int32, device=dev))
+    budget = int(args.large_budget_gb * 2 ** 30)
+    hjcd.hjcd_set_memory_budget(ctx.h, budget)
+    try:
+        ctx.solve(rid, sid, tg, S, K, wl.seed, rob.n, stream=stream, out=out)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        hjcd.hjcd_counters(ctx.h, reset=True)
+        e0.record(stream)
+        for _ in range(args.large_steps):
+            ctx.solve(rid, sid, tg, S, K, wl.seed, rob.n, stream=stream, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        cnt = hjcd.hjcd_counters(ctx.h, reset=True)
+    finally:
+        hjcd.hjcd_set_memory_budget(ctx.h, 0)
+    ms = e0.elapsed_time(e1) / args.large_steps
+    c, e = out[2].cpu().numpy(), out[1].cpu().numpy()
+    succ = (c > 0) & (e[:, 0, 0] <= wl.eps_pos) & (e[:, 0, 1] <= wl.eps_ori)
+    return {"workload": f"Panda + 60 link spheres, {T} targets x {S} seeds, top-{K}; {len(free)} obstacle spheres "
+                        f"(jittered grid carved around the target configurations, uniform grid broadphase)",
+            "candidates": T * S, "ms_per_step": ms, "solves_per_s": T / (ms * 1e-3),
+            "candidates_per_s": T * S / (ms * 1e-3), "success_rate": float(succ.mean()),
+            "mean_solutions_per_target": float(c.mean()), "workspace_budget_bytes": budget,
+            "sphere_tests_per_candidate": cnt[3] / args.large_steps / max(cnt[4] / args.large_steps, 1)}
 
 
 def _serve_run(ctx, reqs, trace, idx, rate_scale, server_kw):
@@ -550,6 +633,8 @@ def hjcd_arm(args):
     }
     if world == 1 and args.uneven_steps > 0:
         line["uneven_batch"] = uneven_leg(ctx, args, dev, stream)
+    if world == 1 and args.large_steps > 0:
+        line["large"] = large_leg(ctx, args, dev, stream)
     if world == 1 and args.serve_seconds > 0:
         line["serving"] = serving_leg(ctx, args, dev)
     ctx.close()

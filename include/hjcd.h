@@ -269,6 +269,13 @@ hjcd_status hjcd_poll(hjcd_ctx* ctx, int64_t request_id, int32_t* done, hjcd_req
 /* Block until the request is done (HJCD_ETIMEOUT after timeout_s seconds). */
 hjcd_status hjcd_wait(hjcd_ctx* ctx, int64_t request_id, double timeout_s, hjcd_request_info* info);
 
+/* Device workspace one hjcd_solve / hjcd_solve_batch call may use (0, the
+ * default: unlimited).  A call needing more runs in waves: each request's
+ * targets are cut into consecutive chunks whose seeds fit the budget, run one
+ * after another through the same workspace; results equal one whole solve
+ * (each chunk keeps its targets' indices inside the request). */
+hjcd_status hjcd_set_memory_budget(hjcd_ctx* ctx, uint64_t bytes);
+
 /* ---- the whole method without allocation ------------------------------------- */
 
 /* Bytes of the file-scope device array that serves as the scratch of
@@ -381,6 +388,14 @@ hjcd_status hjcd_pjik(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const floa
  * the centre to the box below r^2. */
 hjcd_status hjcd_collide(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int64_t n_cand,
                          const float* theta, int64_t ld, uint8_t* hit, void* stream);
+
+/* Sec. V-C spheres against a whole scene: touched[o] = 1 for every obstacle o
+ * of scene scene_id (its spheres in the order given to hjcd_set_scene, then
+ * its boxes) that overlaps a link sphere of one of the n_cand configurations
+ * theta [n][ld] (device), else 0.  touched: DEVICE array of n_sph + n_box
+ * bytes.  Serves to carve obstacle fields around reachable configurations. */
+hjcd_status hjcd_scene_contacts(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int64_t n_cand,
+                                const float* theta, int64_t ld, uint8_t* touched, void* stream);
 
 /* Alg. 2, final ranking: per target, the collision-free candidates (hit may be
  * NULL) of b_off[t] .. b_off[t+1]-1 sorted by score (ties to the lower

@@ -134,6 +134,7 @@ void collide_uniform(CollideArgs& a, const RobotRec& r, const SceneRec* sc) {
     a.u_pairs = r.n_pairs;
     a.u_osph = sc ? sc->dev.n_sph : 0;
     a.u_obox = sc ? sc->dev.n_box : 0;
+    a.has_grid = sc && sc->dev.cell ? 1 : 0;
 }
 
 }  // namespace hjcd
@@ -391,6 +392,8 @@ hjcd_status hjcd_set_scene(hjcd_ctx* ctx, int32_t scene_id_or_new, int n_sph, co
     std::vector<float4> buf(std::max(nf4, 1));
     for (int i = 0; i < n_sph; ++i) {
         if (!(sph_xyzr[4 * i + 3] > 0.0f)) return fail(ctx, HJCD_EINVAL, "obstacle sphere %d: radius must be > 0", i);
+        if (!std::isfinite(sph_xyzr[4 * i]) || !std::isfinite(sph_xyzr[4 * i + 1]) || !std::isfinite(sph_xyzr[4 * i + 2]))
+            return fail(ctx, HJCD_EINVAL, "obstacle sphere %d: non-finite centre", i);
         buf[i] = make_float4(sph_xyzr[4 * i], sph_xyzr[4 * i + 1], sph_xyzr[4 * i + 2], sph_xyzr[4 * i + 3]);
     }
     for (int i = 0; i < n_box; ++i) {
@@ -398,6 +401,58 @@ hjcd_status hjcd_set_scene(hjcd_ctx* ctx, int32_t scene_id_or_new, int n_sph, co
         if (!(b[0] <= b[3] && b[1] <= b[4] && b[2] <= b[5])) return fail(ctx, HJCD_EINVAL, "box %d: lo > hi", i);
         buf[n_sph + 2 * i] = make_float4(b[0], b[1], b[2], 0.0f);
         buf[n_sph + 2 * i + 1] = make_float4(b[3], b[4], b[5], 0.0f);
+    }
+    // a large scene gets a uniform grid over its sphere centres, the spheres sorted by cell
+    SceneDev d{};
+    d.n_sph = n_sph;
+    d.n_box = n_box;
+    std::vector<int32_t> cell, perm(std::max(n_sph, 1));
+    for (int i = 0; i < n_sph; ++i) perm[i] = i;
+    if (n_sph >= kGridMinSpheres) {
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, rmax = 0.0;
+        for (int i = 0; i < n_sph; ++i) {
+            const double c[3] = {buf[i].x, buf[i].y, buf[i].z};
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = std::min(lo[k], c[k]);
+                hi[k] = std::max(hi[k], c[k]);
+            }
+            rmax = std::max(rmax, (double)buf[i].w);
+        }
+        double vol = 1.0;
+        for (int k = 0; k < 3; ++k) vol *= std::max(hi[k] - lo[k], 1e-3);
+        const double h = std::max({std::cbrt(vol / n_sph), 2.0 * rmax, 1e-3});
+        int64_t ncell = 1;
+        for (int k = 0; k < 3; ++k) {
+            d.dim[k] = (int32_t)std::min<double>(std::floor((hi[k] - lo[k]) / h) + 1.0, 1024.0);
+            d.lo[k] = (float)lo[k];
+            ncell *= d.dim[k];
+        }
+        d.inv_h = (float)(1.0 / h);
+        d.reach = (float)(rmax + 1e-4);
+        auto cell_of = [&](const float4& c) {
+            int idx[3];
+            const float q[3] = {c.x, c.y, c.z};
+            for (int k = 0; k < 3; ++k) {
+                const int v = (int)std::floor(((double)q[k] - (double)d.lo[k]) * (double)d.inv_h);
+                idx[k] = std::min(std::max(v, 0), d.dim[k] - 1);
+            }
+            return (int64_t)idx[0] + (int64_t)d.dim[0] * ((int64_t)idx[1] + (int64_t)d.dim[1] * idx[2]);
+        };
+        cell.assign(ncell + 1, 0);
+        std::vector<int64_t> key(n_sph);
+        for (int i = 0; i < n_sph; ++i) {
+            key[i] = cell_of(buf[i]);
+            ++cell[key[i] + 1];
+        }
+        for (int64_t k = 0; k < ncell; ++k) cell[k + 1] += cell[k];
+        std::vector<int32_t> fill(cell.begin(), cell.end() - 1);
+        std::vector<float4> sorted(n_sph);
+        for (int i = 0; i < n_sph; ++i) {
+            const int32_t at = fill[key[i]]++;
+            sorted[at] = buf[i];
+            perm[at] = i;
+        }
+        std::copy(sorted.begin(), sorted.end(), buf.begin());
     }
     hjcd_status st = make_current(ctx);
     if (st) return st;
@@ -408,7 +463,10 @@ hjcd_status hjcd_set_scene(hjcd_ctx* ctx, int32_t scene_id_or_new, int n_sph, co
         id = (int32_t)ctx->scenes.size() - 1;
     }
     SceneRec& S = ctx->scenes[id];
-    const size_t bytes = 16 + 16 * (size_t)std::max(nf4, 1);  // descriptor, then the obstacles
+    // descriptor slot, obstacles, cell starts, the original index of each sorted sphere
+    const size_t o_obj = 64, o_cell = o_obj + align_up(16 * (size_t)std::max(nf4, 1)),
+                 o_perm = o_cell + align_up(4 * std::max<size_t>(cell.size(), 1)),
+                 bytes = o_perm + align_up(4 * perm.size());
     // an earlier solve may still read the old table
     HJCD_CUDA(ctx, cudaDeviceSynchronize());
     if (bytes > S.cap) {
@@ -418,12 +476,17 @@ hjcd_status hjcd_set_scene(hjcd_ctx* ctx, int32_t scene_id_or_new, int n_sph, co
         HJCD_CUDA(ctx, cudaMalloc(&S.buf, bytes));
         S.cap = bytes;
     }
-    static_assert(sizeof(SceneDev) == 16, "scene descriptor is one 16-byte slot");
+    static_assert(sizeof(SceneDev) <= 64, "scene descriptor fits its slot");
     char* base = static_cast<char*>(S.buf);
     S.d_dev = reinterpret_cast<SceneDev*>(base);
-    S.dev = SceneDev{reinterpret_cast<const float4*>(base + 16), n_sph, n_box};
+    d.obj = reinterpret_cast<const float4*>(base + o_obj);
+    d.cell = cell.empty() ? nullptr : reinterpret_cast<const int32_t*>(base + o_cell);
+    S.dev = d;
+    S.perm = reinterpret_cast<const int32_t*>(base + o_perm);
     HJCD_CUDA(ctx, cudaMemcpy(base, &S.dev, sizeof(SceneDev), cudaMemcpyHostToDevice));
-    HJCD_CUDA(ctx, cudaMemcpy(base + 16, buf.data(), 16 * (size_t)std::max(nf4, 1), cudaMemcpyHostToDevice));
+    HJCD_CUDA(ctx, cudaMemcpy(base + o_obj, buf.data(), 16 * (size_t)std::max(nf4, 1), cudaMemcpyHostToDevice));
+    if (!cell.empty()) HJCD_CUDA(ctx, cudaMemcpy(base + o_cell, cell.data(), 4 * cell.size(), cudaMemcpyHostToDevice));
+    HJCD_CUDA(ctx, cudaMemcpy(base + o_perm, perm.data(), 4 * perm.size(), cudaMemcpyHostToDevice));
     S.live = true;
     *scene_id = id;
     return HJCD_OK;
@@ -431,12 +494,16 @@ hjcd_status hjcd_set_scene(hjcd_ctx* ctx, int32_t scene_id_or_new, int n_sph, co
 
 // one request (or a batch) through the context's own workspace; synchronises
 // when an output is host memory
+static hjcd_status run_waves(hjcd_ctx* ctx, const WaveItem* items, int n_items, const hjcd_params& P,
+                             cudaStream_t s, const WavePlan& whole);
+
 static hjcd_status solve_items(hjcd_ctx* ctx, const WaveItem* items, int n_items, const hjcd_params& P,
                                cudaStream_t s) {
     hjcd_status st;
     WavePlan W;
     if ((st = plan_wave(ctx, items, n_items, P, &W))) return st;
     if (W.T == 0) return HJCD_OK;
+    if (ctx->ws_budget && W.bytes > ctx->ws_budget) return run_waves(ctx, items, n_items, P, s, W);
     if ((st = ensure_ws(ctx, W.bytes))) return st;
     if ((st = ensure_pin(ctx, W.head))) return st;
     HJCD_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ws_free, 0));
@@ -449,6 +516,60 @@ static hjcd_status solve_items(hjcd_ctx* ctx, const WaveItem* items, int n_items
         HJCD_CUDA(ctx, cudaStreamSynchronize(s));
         int32_t flag = 0;
         HJCD_CUDA(ctx, cudaMemcpy(&flag, wave_flag(W, ctx->ws), sizeof flag, cudaMemcpyDeviceToHost));
+        if (flag) return fail(ctx, HJCD_ETIMEOUT, "collision kernel: staging wait ran out");
+    }
+    return HJCD_OK;
+}
+
+// A solve larger than the workspace budget, in waves: each item's targets are
+// cut into consecutive chunks whose seeds fit the budget (estimated from the
+// whole plan's bytes per seed), and the chunks run one after another on the
+// stream through the same workspace.  Each chunk keeps its targets' indices
+// inside the request, so the results equal one whole solve.
+static hjcd_status run_waves(hjcd_ctx* ctx, const WaveItem* items, int n_items, const hjcd_params& P,
+                             cudaStream_t s, const WavePlan& whole) {
+    hjcd_status st;
+    const double per_seed = (double)whole.bytes / (double)std::max<int64_t>(whole.CM, 1);
+    const int64_t cap_seeds = std::max<int64_t>(1, (int64_t)(0.9 * (double)ctx->ws_budget / per_seed));
+    bool host_out = false;
+    WavePlan last;
+    for (int i = 0; i < n_items; ++i) {
+        const WaveItem& it = items[i];
+        const int n = it.rob->P.n;
+        for (int t0 = 0; t0 < it.T;) {
+            int64_t seeds = 0;
+            int t1 = t0;
+            while (t1 < it.T) {
+                const int m = it.spt ? it.spt[t1] : it.n_samples;
+                if (t1 > t0 && seeds + m > cap_seeds) break;
+                seeds += m;
+                ++t1;
+            }
+            WaveItem sub = it;
+            sub.T = t1 - t0;
+            sub.t_base = it.t_base + t0;
+            sub.targets = it.targets + 7 * (size_t)t0;
+            if (it.spt) sub.spt = it.spt + t0;
+            sub.out_q = it.out_q + (size_t)t0 * it.top_k * n;
+            sub.out_err = it.out_err + (size_t)t0 * it.top_k * 2;
+            sub.out_count = it.out_count + t0;
+            WavePlan W;
+            if ((st = plan_wave(ctx, &sub, 1, P, &W))) return st;
+            if ((st = ensure_ws(ctx, W.bytes))) return st;
+            if ((st = ensure_pin(ctx, W.head))) return st;  // waits until the previous chunk's image was copied
+            HJCD_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ws_free, 0));
+            if ((st = run_wave(ctx, W, &sub, P, ctx->ws, ctx->pin, s, nullptr))) return st;
+            HJCD_CUDA(ctx, cudaEventRecord(ctx->pin_free, s));
+            HJCD_CUDA(ctx, cudaEventRecord(ctx->ws_free, s));
+            host_out = host_out || W.host_out;
+            last = std::move(W);
+            t0 = t1;
+        }
+    }
+    if (host_out) {
+        HJCD_CUDA(ctx, cudaStreamSynchronize(s));
+        int32_t flag = 0;
+        HJCD_CUDA(ctx, cudaMemcpy(&flag, wave_flag(last, ctx->ws), sizeof flag, cudaMemcpyDeviceToHost));
         if (flag) return fail(ctx, HJCD_ETIMEOUT, "collision kernel: staging wait ran out");
     }
     return HJCD_OK;
@@ -751,6 +872,26 @@ hjcd_status hjcd_collide(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int6
     return after_launch(ctx, 1);
 }
 
+hjcd_status hjcd_scene_contacts(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int64_t n_cand, const float* theta,
+                                int64_t ld, uint8_t* touched, void* stream) {
+    if (!ctx) return HJCD_EINVAL;
+    RobotRec* rob;
+    SceneRec* sc;
+    hjcd_status st;
+    if ((st = check_robot(ctx, robot_id, &rob))) return st;
+    if ((st = check_scene(ctx, scene_id, &sc))) return st;
+    if (!sc) return fail(ctx, HJCD_EINVAL, "hjcd_scene_contacts needs a scene");
+    if ((st = check_theta(ctx, theta, n_cand, ld, "theta"))) return st;
+    const int n_obj = sc->dev.n_sph + sc->dev.n_box;
+    if (n_obj > 0 && pointer_kind(touched) != 1) return fail(ctx, HJCD_EINVAL, "touched must be a device array");
+    if ((st = make_current(ctx))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_obj == 0) return HJCD_OK;
+    HJCD_CUDA(ctx, cudaMemsetAsync(touched, 0, (size_t)n_obj, s));
+    launch_contacts(rob->P, rob->dev, sc->dev, sc->perm, n_cand, theta, ld, touched, s);
+    return after_launch(ctx, n_cand > 0 && rob->P.n_sph > 0 ? 1 : 0);
+}
+
 hjcd_status hjcd_rank(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const int64_t* b_off, const float* theta_B,
                       int64_t ld, const float* score, const float* perr, const float* oerr, const uint8_t* hit,
                       int top_k, float* out_q, float* out_err, int32_t* out_count, void* stream) {
@@ -782,6 +923,13 @@ hjcd_status hjcd_rank(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const int6
 }
 
 // ---- instrumentation -----------------------------------------------------
+
+hjcd_status hjcd_set_memory_budget(hjcd_ctx* ctx, uint64_t bytes) {
+    if (!ctx) return HJCD_EINVAL;
+    if (bytes && bytes < (1u << 20)) return fail(ctx, HJCD_EINVAL, "a memory budget below 1 MiB cannot hold a wave");
+    ctx->ws_budget = (size_t)bytes;
+    return HJCD_OK;
+}
 
 hjcd_status hjcd_set_profiling(hjcd_ctx* ctx, int on) {
     if (!ctx) return HJCD_EINVAL;

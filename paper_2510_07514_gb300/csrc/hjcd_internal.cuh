@@ -47,10 +47,19 @@ struct RobotDev {
 };
 
 // Obstacles of a scene in device memory: spheres (float4) followed by boxes
-// (two float4: lo.xyz, hi.xyz); 16-byte aligned.
+// (two float4: lo.xyz, hi.xyz); 16-byte aligned.  A large scene also carries
+// a uniform grid over its sphere centres: the spheres are sorted by cell and
+// cell[k] .. cell[k+1] are the spheres whose centre lies in cell k (cells
+// numbered x fastest); a query for a ball of radius R searches the cells
+// within R + reach of its centre.
 struct SceneDev {
     const float4* obj;
     int32_t n_sph, n_box;
+    const int32_t* cell;  // [dim.x * dim.y * dim.z + 1], or null: no grid
+    float lo[3];          // grid origin
+    float inv_h;          // 1 / cell edge
+    int32_t dim[3];       // cells per axis
+    float reach;          // largest obstacle radius, plus a margin beyond binary32 rounding
 };
 
 // The robots of one launch and the maxima the kernels size shared memory by.
@@ -432,6 +441,7 @@ struct CollideArgs {
     int32_t n_scenes;
     int32_t max_obj4;         // largest n_sph + 2 n_box over the scenes
     int32_t uniform;          // every candidate: robot 0 and scene 0 (if any) -- no per-candidate lookup
+    int32_t has_grid;         // some scene of the launch carries a uniform grid
     // with uniform set: robot 0's DoF and checked body pairs, scene 0's obstacle counts (0 without a scene)
     int32_t u_n, u_pairs, u_osph, u_obox;
     const TargetDesc* tg;
@@ -456,6 +466,8 @@ void launch_lm(const LmArgs& A, bool trace, cudaStream_t st);
 void launch_topk_dup(const DupArgs& A, int max_m, cudaStream_t st);
 void launch_rank(const RankArgs& A, int max_b, cudaStream_t st);
 void launch_collide(const CollideArgs& A, cudaStream_t st);
+void launch_contacts(const RobotParams& R, const RobotDev& rd, const SceneDev& sc, const int32_t* perm, int64_t C,
+                     const float* th, int64_t ld, uint8_t* touched, cudaStream_t st);
 void launch_ffma(float* sink, int iters, int blocks, cudaStream_t st);
 int ffma_flops_per_thread_iter();
 

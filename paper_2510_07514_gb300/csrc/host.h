@@ -17,7 +17,8 @@
 
 namespace hjcd {
 
-constexpr int kMaxSceneFloat4 = 10240;  // resident scene: obstacle spheres + 2 * boxes (160 KB when staged)
+constexpr int kMaxSceneFloat4 = 1 << 20;  // resident scene: obstacle spheres + 2 * boxes
+constexpr int kGridMinSpheres = 512;      // resident scenes with this many spheres get a uniform grid
 
 // Resident robot: the kinematic table (host copy) and one device buffer with
 // the kinematic table, the collision-table descriptor and the collision
@@ -36,7 +37,8 @@ struct RobotRec {
 struct SceneRec {
     void* buf = nullptr;
     SceneDev* d_dev = nullptr;
-    SceneDev dev{};  // host copy (device pointer to the obstacles)
+    SceneDev dev{};  // host copy (device pointers to the obstacles and grid)
+    const int32_t* perm = nullptr;  // device: original index of each stored sphere
     size_t cap = 0;
     bool live = false;
 };
@@ -64,6 +66,7 @@ struct hjcd_ctx {
     cudaEvent_t ev[6] = {};
     bool ev_valid = false;
     std::atomic<int64_t> launches{0};
+    size_t ws_budget = 0;     // workspace bytes one solve may use before it splits into waves (0: unlimited)
     int32_t ccd_block = 128;  // launch configuration (hjcd_set_launch_config, hjcd_autotune)
     int32_t lm_warps = 4;
     std::mutex api_mu;  // robots/scenes tables against the serving thread
@@ -125,6 +128,7 @@ struct WaveItem {
     uint64_t seed = 0;
     int top_k = 1;
     int cd_iters = -1, lm_iters = -1;  // < 0: the batch parameters' caps
+    int t_base = 0;  // index of targets[0] inside its request (keys the random streams)
     float* out_q = nullptr;  // [T][top_k][n], host or device
     float* out_err = nullptr;  // [T][top_k][2]
     int32_t* out_count = nullptr;  // [T]

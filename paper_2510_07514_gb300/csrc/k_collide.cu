@@ -121,7 +121,7 @@ __host__ __device__ __forceinline__ CollideLayout collide_smem_layout(int n_obj4
 }
 
 
-template <int SPL, bool UNIFORM>
+template <int SPL, bool UNIFORM, bool GRID>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideArgs A) {
     constexpr bool STAGED = UNIFORM;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -289,8 +289,50 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
             }
         }
 
+        // obstacle spheres of a gridded scene: per body, the lanes walk the cells within the
+        // bounding sphere's radius plus the largest obstacle radius; each obstacle that
+        // overlaps the bounding sphere is tested against the body's fine spheres
+        const int32_t* gcell = nullptr;
+        if (GRID && n_osph > 0) gcell = (UNIFORM ? sc0 : A.scenes[sid]).cell;
+        if (GRID && gcell) {
+            const SceneDev& G = A.scenes[UNIFORM ? 0 : sid];
+            for (int b = 0; b < nb && !hit; ++b) {
+                const int2 rg = wrange[b];
+                if (rg.y == 0) continue;
+                const float4 co = wco[b];
+                const float ext = co.w + G.reach;
+                const float cc[3] = {co.x, co.y, co.z};
+                int i0[3], i1[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const int dmax = G.dim[k] - 1;
+                    i0[k] = min(max((int)floorf((cc[k] - ext - G.lo[k]) * G.inv_h), 0), dmax);
+                    i1[k] = min(max((int)floorf((cc[k] + ext - G.lo[k]) * G.inv_h), 0), dmax);
+                }
+                const int nx = i1[0] - i0[0] + 1, ny = i1[1] - i0[1] + 1, nxy = nx * ny;
+                const int ncell = nxy * (i1[2] - i0[2] + 1);
+                bool h = false;
+                unsigned tl = 0;
+                for (int q = lane; q < ncell && !h; q += 32) {
+                    const int z = q / nxy, r = q - z * nxy, y = r / nx, x = r - y * nx;
+                    const int k = (i0[0] + x) + G.dim[0] * ((i0[1] + y) + G.dim[1] * (i0[2] + z));
+                    const int a = __ldg(gcell + k), e = __ldg(gcell + k + 1);
+                    for (int o = a; o < e && !h; ++o) {
+                        const float4 sp = ld_obj<STAGED>(obj, o);
+                        ++tl;
+                        if (sph_sph(co, sp)) {
+                            for (int i = 0; i < rg.y && !h; ++i) h = sph_sph(wsph[rg.x + i], sp);
+                            tl += rg.y;
+                        }
+                    }
+                }
+                t_s += __reduce_add_sync(0xffffffffu, tl);
+                hit = __any_sync(0xffffffffu, h);
+            }
+        }
+
         // obstacle spheres: 32 obstacles at a time, one body at a time
-        for (int o0 = 0; o0 < n_osph && !hit; o0 += 32) {
+        for (int o0 = 0; o0 < n_osph && !hit && !(GRID && gcell); o0 += 32) {
             const int o = o0 + lane;
             const bool valid = o < n_osph;
             const float4 s = valid ? ld_obj<STAGED>(obj, o) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -360,40 +402,92 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
     }
 }
 
-template <int SPL, bool UNIFORM>
+template <int SPL, bool UNIFORM, bool GRID>
 void launch_collide_t(const CollideArgs& A, int n_obj4, cudaStream_t st) {
     const size_t smem =
         collide_smem_layout(UNIFORM ? n_obj4 : 0, A.rs.n, A.rs.n_max + 2, A.rs.ns_max, A.rs.pairs_max).total;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_collide<SPL, UNIFORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncSetAttribute(k_collide<SPL, UNIFORM, GRID>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         attr_set = true;
     }
     const int g = grid_for(A.C, kWarpsPerBlock, 8);
-    k_collide<SPL, UNIFORM><<<g, kWarpsPerBlock * 32, smem, st>>>(A);
+    k_collide<SPL, UNIFORM, GRID><<<g, kWarpsPerBlock * 32, smem, st>>>(A);
 }
 
-template <bool UNIFORM>
+template <bool UNIFORM, bool GRID>
 void launch_collide_s(const CollideArgs& A, int n_obj4, cudaStream_t st) {
     const int ns = A.rs.ns_max;
-    if (ns <= 32) launch_collide_t<1, UNIFORM>(A, n_obj4, st);
-    else if (ns <= 64) launch_collide_t<2, UNIFORM>(A, n_obj4, st);
-    else if (ns <= 128) launch_collide_t<4, UNIFORM>(A, n_obj4, st);
-    else launch_collide_t<8, UNIFORM>(A, n_obj4, st);
+    if (ns <= 32) launch_collide_t<1, UNIFORM, GRID>(A, n_obj4, st);
+    else if (ns <= 64) launch_collide_t<2, UNIFORM, GRID>(A, n_obj4, st);
+    else if (ns <= 128) launch_collide_t<4, UNIFORM, GRID>(A, n_obj4, st);
+    else launch_collide_t<8, UNIFORM, GRID>(A, n_obj4, st);
+}
+
+constexpr int kContactTile = 8;  // configurations per CTA of the contact kernel
+
+// touched[o] = 1 for every obstacle o (spheres in the caller's order, then
+// boxes) that overlaps a link sphere of one of the C configurations; the
+// world spheres of kContactTile configurations sit in shared memory and each
+// thread tests its obstacles against all of them.
+__global__ void __launch_bounds__(256) k_contacts(const RobotParams R, const RobotDev rd, const SceneDev sc,
+                                                 const int32_t* perm, int64_t C, const float* th, int64_t ld,
+                                                 uint8_t* touched) {
+    extern __shared__ float4 wsp[];  // [kContactTile][n_sph]
+    const int ns = rd.n_sph;
+    const int64_t c0 = (int64_t)blockIdx.x * kContactTile;
+    const int nc = (int)min((int64_t)kContactTile, C - c0);
+    if (threadIdx.x < nc) {
+        const int64_t c = c0 + threadIdx.x;
+        float4* w = wsp + threadIdx.x * ns;
+        Frame F = frame_identity();
+        for (int b = 0; b <= R.n + 1; ++b) {
+            if (b >= 1 && b <= R.n) fk_step(R, b - 1, th[(b - 1) * ld + c], F);
+            const Frame E = b == R.n + 1 ? fk_flange(R, F) : F;
+            const int2 rg = rd.range[b];
+            for (int i = rg.x; i < rg.x + rg.y; ++i) w[i] = to_world(E, rd.sph[i]);
+        }
+    }
+    __syncthreads();
+    const int n_obj = sc.n_sph + sc.n_box;
+    for (int o = threadIdx.x; o < n_obj; o += blockDim.x) {
+        bool hit = false;
+        if (o < sc.n_sph) {
+            const float4 s = sc.obj[o];
+            for (int i = 0; i < nc * ns && !hit; ++i) hit = sph_sph(wsp[i], s);
+            if (hit) touched[perm[o]] = 1;
+        } else {
+            const int k = o - sc.n_sph;
+            const float4 lo = sc.obj[sc.n_sph + 2 * k], hi = sc.obj[sc.n_sph + 2 * k + 1];
+            for (int i = 0; i < nc * ns && !hit; ++i) hit = sph_box(wsp[i], lo, hi);
+            if (hit) touched[o] = 1;
+        }
+    }
 }
 
 }  // namespace
 
+void launch_contacts(const RobotParams& R, const RobotDev& rd, const SceneDev& sc, const int32_t* perm, int64_t C,
+                     const float* th, int64_t ld, uint8_t* touched, cudaStream_t st) {
+    if (C <= 0 || rd.n_sph <= 0 || sc.n_sph + sc.n_box <= 0) return;
+    const size_t smem = sizeof(float4) * kContactTile * (size_t)rd.n_sph;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_contacts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t blocks = (C + kContactTile - 1) / kContactTile;
+    k_contacts<<<(unsigned)blocks, 256, smem, st>>>(R, rd, sc, perm, C, th, ld, touched);
+}
+
 // One robot and one scene (or none) for every candidate, with the scene small
 // enough to stage: the uniform kernel (scene staged into shared memory, counts
-// as launch parameters); otherwise the mixed kernel.
+// as launch parameters); otherwise the mixed kernel.  Launches with a gridded
+// scene take the variants with the grid query.
 void launch_collide(const CollideArgs& A, cudaStream_t st) {
     if (A.C <= 0 || A.rs.ns_max <= 0) return;
-    if (A.uniform && A.rs.n == 1 && A.n_scenes <= 1 && A.max_obj4 <= kMaxStagedObj4) {
-        launch_collide_s<true>(A, A.n_scenes == 1 ? A.max_obj4 : 0, st);
-    } else {
-        launch_collide_s<false>(A, 0, st);
-    }
+    const bool uni = A.uniform && A.rs.n == 1 && A.n_scenes <= 1 && A.max_obj4 <= kMaxStagedObj4;
+    const int n4 = A.n_scenes == 1 ? A.max_obj4 : 0;
+    if (uni && A.has_grid) launch_collide_s<true, true>(A, n4, st);
+    else if (uni) launch_collide_s<true, false>(A, n4, st);
+    else if (A.has_grid) launch_collide_s<false, true>(A, 0, st);
+    else launch_collide_s<false, false>(A, 0, st);
 }
 
 }  // namespace hjcd

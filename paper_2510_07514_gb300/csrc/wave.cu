@@ -192,7 +192,7 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
             d.eps_ori = it.eps_ori;
             d.key[0] = (uint32_t)(it.seed & 0xffffffffu);
             d.key[1] = (uint32_t)(it.seed >> 32);
-            d.t_local = t;
+            d.t_local = it.t_base + t;
             d.robot = W.item_robot[i];
             d.scene = W.item_scene[i];
             d.cd_iters = (int16_t)cd;
@@ -297,6 +297,7 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
             cl.u_osph = W.NS ? W.scenes[0].nsph : 0;
             cl.u_obox = W.NS ? W.scenes[0].nbox : 0;
         }
+        for (const auto& e : W.scenes) cl.has_grid = cl.has_grid || (e.res && e.res->dev.cell);
         cl.tg = d_tg;
         cl.map = CandMap{nullptr, nullptr, d_boff, W.T};
         cl.C = W.CB;

@@ -35,7 +35,7 @@ EXPORTS = (
     "hjcd_solve_noalloc", "hjcd_solve_batch",
     "hjcd_server_start", "hjcd_server_stop", "hjcd_submit", "hjcd_poll", "hjcd_wait",
     "hjcd_graph_create", "hjcd_graph_launch", "hjcd_graph_check", "hjcd_graph_destroy",
-    "hjcd_set_launch_config", "hjcd_autotune",
+    "hjcd_set_launch_config", "hjcd_autotune", "hjcd_set_memory_budget", "hjcd_scene_contacts",
 )
 
 
@@ -121,6 +121,8 @@ _SIGS = {
     "hjcd_solve_batch": (_ST, [_V, _I, ct.POINTER(hjcd_batch_item), ct.POINTER(hjcd_params), _V]),
     "hjcd_server_start": (_ST, [_V, ct.POINTER(hjcd_server_opts)]),
     "hjcd_set_launch_config": (_ST, [_V, _I32, _I32]),
+    "hjcd_set_memory_budget": (_ST, [_V, _U64]),
+    "hjcd_scene_contacts": (_ST, [_V, _I32, _I32, _I64, _V, _I64, _V, _V]),
     "hjcd_autotune": (_ST, [_V, _I, ct.POINTER(hjcd_batch_item), ct.POINTER(hjcd_params), _F, _I32,
                             ct.POINTER(hjcd_params), ct.POINTER(hjcd_tune_report)]),
     "hjcd_graph_create": (_ST, [_V, _I, ct.POINTER(hjcd_batch_item), ct.POINTER(hjcd_params), ct.POINTER(_V)]),
@@ -261,6 +263,15 @@ def hjcd_solve_batch(ctx, items, params=None, stream=None) -> None:
     arr = (hjcd_batch_item * len(items))(*items)
     _check(ctx, load().hjcd_solve_batch(ctx, len(items), arr, ct.byref(params) if params is not None else None,
                                         stream_handle(stream)))
+
+
+def hjcd_scene_contacts(ctx, robot_id, scene_id, n_cand, theta, ld, touched, stream=None) -> None:
+    _check(ctx, load().hjcd_scene_contacts(ctx, int(robot_id), int(scene_id), int(n_cand), ptr(theta), int(ld),
+                                           ptr(touched), stream_handle(stream)))
+
+
+def hjcd_set_memory_budget(ctx, nbytes: int) -> None:
+    _check(ctx, load().hjcd_set_memory_budget(ctx, int(nbytes)))
 
 
 def hjcd_set_launch_config(ctx, ccd_block: int, lm_warps: int) -> None:

@@ -382,3 +382,59 @@ def cfg4_trace(rate: float = 2000.0, duration: float = 60.0, n_templates: int = 
     t = np.sort(rng.uniform(0.0, duration, n))
     return ServingTrace(t, rng.integers(0, n_templates, n), rng.integers(1, 9, n), log_uniform_counts(rng, n, 32, 4096),
                         rng.integers(0, 2 ** 63 - 1, n, dtype=np.int64))
+
+
+@dataclass
+class LargeWorkload:
+    """The large case: target configurations first, then candidate obstacle
+    nodes in the order they are admitted (the consumer drops every node a
+    target configuration's link spheres touch and keeps the first n_obstacles
+    that remain)."""
+    name: str
+    robot: Robot
+    target_pool: np.ndarray     # joint samples; the consumer keeps the self-collision-free ones
+    nodes: np.ndarray           # (k, 4) candidate obstacle spheres, admission order
+    n_targets: int
+    n_samples: int
+    n_obstacles: int
+    top_k: int
+    seed: int
+    eps_pos: float = 1e-3
+    eps_ori: float = 1e-2
+
+
+def jittered_grid_nodes(rng: np.random.Generator, core_lo=(-0.75, -0.75, 0.0), core_hi=(0.75, 0.75, 1.5),
+                        core_n=(20, 25, 10), outer_lo=(-2.0, -2.0, -0.5), outer_hi=(2.0, 2.0, 2.5),
+                        jitter=0.25, r_range=(0.01, 0.03)) -> np.ndarray:
+    """Obstacle spheres on a jittered 3-D grid: the core grid (core_n nodes over
+    [core_lo, core_hi]) first, then the nodes of the same lattice extended over
+    [outer_lo, outer_hi] in order of their distance from the core box, each
+    node moved by up to +-jitter of a cell per axis, radii ~ U[r_range]."""
+    core_lo, core_hi, outer_lo, outer_hi = (np.asarray(v, float) for v in (core_lo, core_hi, outer_lo, outer_hi))
+    step = (core_hi - core_lo) / np.asarray(core_n, float)
+    first = core_lo + 0.5 * step  # cell centres of the core grid
+    lo_i = np.floor((outer_lo - first) / step).astype(int)
+    hi_i = np.floor((outer_hi - first) / step).astype(int)
+    axes = [np.arange(lo_i[k], hi_i[k] + 1) for k in range(3)]
+    I = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, 3)
+    centre = first + I * step
+    # distance of each node from the core box (0 inside), ties in lattice order
+    out = np.maximum(np.maximum(core_lo - centre, centre - core_hi), 0.0)
+    order = np.lexsort((I[:, 2], I[:, 1], I[:, 0], np.linalg.norm(out, axis=1)))
+    centre = centre[order]
+    centre = centre + rng.uniform(-jitter, jitter, centre.shape) * step
+    r = rng.uniform(r_range[0], r_range[1], len(centre))
+    return np.concatenate([centre, r[:, None]], axis=1)
+
+
+def cfg5(n_targets: int = 10000, n_samples: int = 4096, n_obstacles: int = 5000, top_k: int = 16,
+         pool_factor: int = 2) -> LargeWorkload:
+    """cfg2's Panda with 60 link spheres; 10 000 targets x 4096 seeds; a scene
+    of 5000 obstacle spheres on a jittered grid carved around the target
+    configurations; top-16 solutions per target."""
+    rob = panda_with_spheres(np.random.default_rng(CFG_SEED[2]))  # the same robot as cfg2
+    rng = np.random.default_rng(CFG_SEED[5])
+    pool = joint_samples(rng, rob, n_targets * pool_factor)
+    nodes = jittered_grid_nodes(rng)
+    return LargeWorkload(f"panda-{n_targets}x{n_samples}-grid{n_obstacles}", rob, pool, nodes, n_targets,
+                         n_samples, n_obstacles, top_k, CFG_SEED[5])

@@ -1,0 +1,194 @@
+"""Large scenes and large batches: the uniform obstacle grid of the collision
+filter, the contact query that carves obstacle fields, memory-admitted waves,
+and the large workload's shape (jittered grid of thousands of obstacle
+spheres carved around the target configurations, top-16 per target) against
+the oracle at a reduced size.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from paper_2510_07514_gb300 import api, build, hjcd, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    orc.build()
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def soa(th):
+    return torch.as_tensor(np.ascontiguousarray(np.asarray(th, np.float32).T), device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def _world_spheres(orob, rob, th):
+    """World-frame link spheres of each configuration (oracle kinematics)."""
+    out = []
+    for q in th:
+        F = orc.fk_frames(orob, q)
+        w = [F[b][:3, :3] @ rob.sph_xyzr[i, :3] + F[b][:3, 3] for i, b in enumerate(rob.sph_body)]
+        out.append(np.concatenate([np.asarray(w), rob.sph_xyzr[:, 3:4]], axis=1))
+    return np.stack(out)
+
+
+def _carve(nodes, ws, keep):
+    """Nodes no world sphere overlaps (brute force, margin-aware): the first `keep`."""
+    free = np.ones(len(nodes), bool)
+    flat = ws.reshape(-1, 4)
+    for a in range(0, len(nodes), 4096):
+        nd = nodes[a:a + 4096]
+        d2 = ((nd[:, None, :3] - flat[None, :, :3]) ** 2).sum(-1)
+        free[a:a + 4096] = ~np.any(d2 < (nd[:, None, 3] + flat[None, :, 3]) ** 2, axis=1)
+    return nodes[free][:keep]
+
+
+def test_scene_contacts_match_brute_force(ctx):
+    rob = inputs.panda_with_spheres(np.random.default_rng(5))
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    rng = np.random.default_rng(61)
+    nodes = inputs.jittered_grid_nodes(rng, core_n=(10, 10, 8), outer_lo=(-1.0, -1.0, -0.2),
+                                       outer_hi=(1.0, 1.0, 1.8))
+    boxes = np.array([[0.2, 0.2, 0.2, 0.5, 0.5, 0.6], [-1.5, -1.5, 0.0, -1.4, -1.4, 0.1]])
+    sid = ctx.set_scene(inputs.Scene(f32(nodes), f32(boxes)))
+    th = f32(rng.uniform(rob.lo, rob.hi, (37, 7)))
+    touched = torch.zeros(len(nodes) + 2, dtype=torch.uint8, device="cuda")
+    T = soa(th)
+    hjcd.hjcd_scene_contacts(ctx.h, rid, sid, 37, T, T.stride(0), touched)
+    got = host(touched).astype(bool)
+    ws = _world_spheres(orob, rob, th).reshape(-1, 4)
+    nd = f32(nodes)
+    d2 = ((nd[:, None, :3] - ws[None, :, :3]) ** 2).sum(-1)
+    gap = d2 - (nd[:, None, 3] + ws[None, :, 3]) ** 2
+    ref = np.any(gap < 0, axis=1)
+    clear = np.min(np.abs(gap), axis=1) > 1e-6
+    assert len(nodes) > 512  # the scene carries a grid: stored order differs from the caller's
+    assert np.array_equal(got[:len(nodes)][clear], ref[clear])
+    assert got[:len(nodes)].any() and not got[:len(nodes)].all()
+    # boxes: the first lies inside the workspace, the second far outside
+    bx = f32(boxes)
+    hit_box = [bool(np.any(np.sum((ws[:, :3] - np.clip(ws[:, :3], b[:3], b[3:])) ** 2, 1) < ws[:, 3] ** 2))
+               for b in bx]
+    assert list(got[len(nodes):]) == hit_box
+
+
+@pytest.mark.parametrize("n_obs", [600, 5000])
+def test_gridded_scene_collision_verdicts_match_the_oracle(ctx, n_obs):
+    """Scenes of >= 512 spheres take the grid query; verdicts bit-exact against
+    brute force outside a 1e-6 m margin, for the uniform (staged) kernel and
+    the mixed kernel."""
+    rob = inputs.panda_with_spheres(np.random.default_rng(5))
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    rng = np.random.default_rng(62 + n_obs)
+    allnodes = f32(inputs.jittered_grid_nodes(rng, core_n=(12, 12, 10), r_range=(0.01, 0.05)))
+    th = f32(rng.uniform(rob.lo, rob.hi, (3000, 7)))
+    T = soa(th)
+    # carve the field around a tenth of the configurations (contact query, tested above), so that
+    # both verdicts occur
+    sid_all = ctx.set_scene(inputs.Scene(allnodes, np.zeros((0, 6))))
+    touched = torch.zeros(len(allnodes), dtype=torch.uint8, device="cuda")
+    hjcd.hjcd_scene_contacts(ctx.h, rid, sid_all, 300, T, T.stride(0), touched)
+    nodes = allnodes[~host(touched).astype(bool)][:n_obs]
+    assert len(nodes) == n_obs
+    sc = inputs.Scene(nodes, np.zeros((0, 6)))
+    sid = ctx.set_scene(sc)
+    hit = host(ctx.collide(rid, sid, T)).astype(bool)
+    ref, margin = orc.collide(orob, orc.Scene(sc), th)
+    certain = margin >= 1e-6
+    assert certain.mean() > 0.99
+    assert np.array_equal(hit[certain], ref[certain])
+    assert 0.05 < ref.mean() < 0.99
+    # the same scene through the mixed kernel (a batch of two requests with different scenes)
+    s2 = inputs.Scene(nodes[: n_obs // 2], np.zeros((0, 6)))
+    sid2 = ctx.set_scene(s2)
+    tg = torch.as_tensor(f32(orc.pose(orob, th[:40])), dtype=torch.float32, device="cuda")
+    a, oa = ctx.batch_item(rid, sid, tg[:20], 64, 4, 5, 7)
+    b, ob = ctx.batch_item(rid, sid2, tg[20:], 64, 4, 6, 7)
+    ctx.solve_batch([a, b])
+    for out, s_, lo in ((oa, sc, 0), (ob, s2, 20)):
+        q, c = host(out[0]).astype(np.float64), host(out[2])
+        for t in range(20):
+            if c[t]:
+                h, m = orc.collide(orob, orc.Scene(s_), q[t, :c[t]])
+                assert not np.any(h & (m >= 1e-6))
+
+
+def test_waves_equal_one_whole_solve(ctx):
+    wl = inputs.cfg2(64, 512)
+    rid, sid = ctx.add_robot(wl.robot), ctx.set_scene(wl.scene)
+    orob = orc.Robot(wl.robot)
+    rng = np.random.default_rng(63)
+    tg = torch.as_tensor(f32(orc.pose(orob, f32(wl.theta_gen[:64]))), dtype=torch.float32, device="cuda")
+    spt = rng.integers(32, 700, 64)
+    whole = ctx.solve(rid, sid, tg, 0, 4, 9, 7, samples_per_target=spt)
+    host_out = (torch.zeros((64, 4, 7)), torch.zeros((64, 4, 2)), torch.zeros((64,), dtype=torch.int32))
+    try:
+        hjcd.hjcd_set_memory_budget(ctx.h, 1 << 20)  # ~40 targets' worth: several waves
+        waves = ctx.solve(rid, sid, tg, 0, 4, 9, 7, samples_per_target=spt)
+        ctx.solve(rid, sid, tg.cpu(), 0, 4, 9, 7, samples_per_target=spt, out=host_out)
+    finally:
+        hjcd.hjcd_set_memory_budget(ctx.h, 0)
+    for other in (waves, host_out):
+        qa, ea, ca = (host(x) for x in whole)
+        qb, eb, cb = (host(x) for x in other)
+        assert np.array_equal(ca, cb)
+        for t in range(64):
+            assert np.array_equal(qa[t, :ca[t]], qb[t, :cb[t]])
+            assert np.array_equal(ea[t, :ca[t]], eb[t, :cb[t]])
+    with pytest.raises(hjcd.HjcdError):
+        hjcd.hjcd_set_memory_budget(ctx.h, 1000)
+
+
+def test_large_workload_shape_matches_the_oracle(ctx):
+    """The large case at a reduced size: 24 targets x 256 seeds, top-16, a
+    5000-sphere jittered grid carved around the target configurations."""
+    wl = inputs.cfg5(n_targets=24, n_samples=256)
+    rob = wl.robot
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    hs, _ = orc.collide(orob, None, f32(wl.target_pool))
+    th = f32(wl.target_pool)[~hs][:24]
+    ws = _world_spheres(orob, rob, th)
+    nodes = _carve(f32(wl.nodes), ws, wl.n_obstacles)
+    assert len(nodes) == wl.n_obstacles
+    sc = inputs.Scene(nodes, np.zeros((0, 6)))
+    sid = ctx.set_scene(sc)
+    osc = orc.Scene(sc)
+    tg = f32(orc.pose(orob, th))
+    q, e, c = ctx.solve(rid, sid, torch.as_tensor(tg, dtype=torch.float32, device="cuda"), 256, 16, wl.seed, 7)
+    q, e, c = host(q).astype(np.float64), host(e).astype(np.float64), host(c)
+    succ = np.zeros(24, bool)
+    for t in range(24):
+        for r in range(c[t]):
+            err = orc.residual(orob, q[t, r], tg[t])
+            assert abs(np.linalg.norm(err[:3]) - e[t, r, 0]) < 1e-5
+            assert abs(np.linalg.norm(err[3:]) - e[t, r, 1]) < 1e-5
+        if c[t]:
+            h, m = orc.collide(orob, osc, q[t, :c[t]])
+            assert not np.any(h & (m >= 1e-6))
+            s = e[t, :c[t], 0] ** 2 / 1e-6 + e[t, :c[t], 1] ** 2 / 1e-4
+            assert np.all(np.diff(s) >= -1e-3 * np.maximum(s[1:], 1e-6))
+        succ[t] = c[t] > 0 and e[t, 0, 0] <= 1e-3 and e[t, 0, 1] <= 1e-2
+    o = orc.solve(orob, osc, orc.make_params(1e-3, 1e-2, seed=wl.seed), tg, 256, 16)
+    so = (o["count"] > 0) & (o["err"][:, 0, 0] <= 1e-3) & (o["err"][:, 0, 1] <= 1e-2)
+    assert abs(succ.mean() - so.mean()) <= 1 / 24 + 1e-12
+    assert succ.mean() > 0.6  # 256 seeds in a cluttered field; the benchmark runs 4096
+    assert np.mean(c) > 8  # most targets return many collision-free solutions
