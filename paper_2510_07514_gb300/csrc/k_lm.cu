@@ -114,6 +114,49 @@ __device__ __forceinline__ void chol6_solve(const float (&L)[21], const float (&
     }
 }
 
+struct Y6 {
+    float v[6];
+};
+
+// Solve M y = b with M the 6 x 6 sum over the joints of col col^T plus reg I,
+// for lane l's weighted Jacobian columns.  lm: the columns are first weighted
+// by the rows' W (and stored back, so the smem Jacobian becomes W J) and then
+// scaled to unit length (S = D^-1/2 of the push-through LM step); otherwise
+// they are used as stored (the dogleg's Gauss-Newton system on W J).
+__device__ __noinline__ Y6 normal_solve(const LmW S, int l, int n, bool lm, float reg, Y6 w, Y6 b) {
+    float M[21], inv[6];
+#pragma unroll
+    for (int q = 0; q < 21; ++q) M[q] = 0.0f;
+#pragma unroll 1
+    for (int i = 0; i < n; ++i) {
+        float col[6], dd = 1e-9f;
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            col[r] = S.jw(r, i, l);
+            if (lm) {
+                col[r] *= w.v[r];
+                S.jw(r, i, l) = col[r];
+                dd = fmaf(col[r], col[r], dd);
+            }
+        }
+        if (lm) {
+            const float rs = rsqrtf(dd);
+#pragma unroll
+            for (int r = 0; r < 6; ++r) col[r] *= rs;
+        }
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+#pragma unroll
+            for (int q = 0; q <= r; ++q) M[tri(r, q)] = fmaf(col[r], col[q], M[tri(r, q)]);
+    }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) M[tri(r, r)] += reg;
+    chol6(M, inv);
+    Y6 y;
+    chol6_solve(M, inv, b.v, y.v);
+    return y;
+}
+
 // alpha_i = 1 / beta^i by repeated division (the same bits on every lane)
 __device__ __forceinline__ float ls_alpha(int i, float beta) {
     float a = 1.0f;
@@ -122,8 +165,13 @@ __device__ __forceinline__ float ls_alpha(int i, float beta) {
 }
 
 // weighted cost 1/2 |W r|^2 at the trial point clamp(theta + alpha d) of lane s
-__device__ __forceinline__ float trial_cost(const RobotParams& R, const TargetDesc& T, const LmW& S, int s,
-                                            float alpha) {
+// (the kinematics passes, the 6 x 6 solve and the trial spreading each exist
+// once in the kernel, called from every branch that needs them, which keeps
+// the per-iteration body inside the instruction cache)
+__device__ __noinline__ float trial_cost(const RobotParams* rob, const TargetDesc* tg, int row, const LmW S, int s,
+                                        float alpha) {
+    const TargetDesc T = tg[row];
+    const RobotParams& R = rob[T.robot];
     Frame F = frame_identity();
 #pragma unroll 1
     for (int j = 0; j < R.n; ++j)
@@ -137,13 +185,13 @@ __device__ __forceinline__ float trial_cost(const RobotParams& R, const TargetDe
 }
 
 // theta <- clamp(theta + alpha d) for lane s (the trial point the cost was taken at)
-__device__ __forceinline__ void take_step(const RobotParams& R, const LmW& S, int s, float alpha) {
+__device__ __noinline__ void take_step(const RobotParams& R, const LmW S, int s, float alpha) {
 #pragma unroll 1
     for (int j = 0; j < R.n; ++j) S.th(j, s) = clampf(fmaf(alpha, S.d(j, s), S.th(j, s)), R.lo[j], R.hi[j]);
 }
 
 // Trials i = i0 .. A of every lane in `mask`, spread over the warp; results in S.ok(i, lane).
-__device__ __forceinline__ unsigned long long warp_trials(const RobotParams* rob, const TargetDesc* tg, const LmW& S,
+__device__ __noinline__ unsigned long long warp_trials(const RobotParams* rob, const TargetDesc* tg, const LmW S,
                                                           unsigned mask, int lane, int i0, int A, float beta) {
     const int per = A + 1 - i0;
     if (!mask || per <= 0) return 0;
@@ -153,8 +201,7 @@ __device__ __forceinline__ unsigned long long warp_trials(const RobotParams* rob
     unsigned long long cnt = 0;
     for (int w = lane; w < items; w += 32) {
         const int s = S.list(w / per), i = i0 + w % per;
-        const TargetDesc Ts = tg[S.t(s)];
-        S.ok(i, s) = trial_cost(rob[Ts.robot], Ts, S, s, ls_alpha(i, beta)) < S.cost0(s) ? 1 : 0;
+        S.ok(i, s) = trial_cost(rob, tg, S.t(s), S, s, ls_alpha(i, beta)) < S.cost0(s) ? 1 : 0;
         ++cnt;
     }
     __syncwarp();
@@ -280,30 +327,16 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                 S.cost0(lane) = 0.5f * cost0;
                 S.t(lane) = t;
                 // the push-through LM step on the weighted Jacobian
-                float M[21], inv[6], y[6];
+                Y6 wv, bv;
 #pragma unroll
-                for (int q = 0; q < 21; ++q) M[q] = 0.0f;
-#pragma unroll 1
-                for (int i = 0; i < n; ++i) {
-                    float col[6], dd = 1e-9f;
-#pragma unroll
-                    for (int r = 0; r < 6; ++r) {
-                        col[r] = S.jw(r, i, lane) * W[r];
-                        S.jw(r, i, lane) = col[r];
-                        dd = fmaf(col[r], col[r], dd);
-                    }
-                    const float rs = rsqrtf(dd);
-#pragma unroll
-                    for (int r = 0; r < 6; ++r) col[r] *= rs;
-#pragma unroll
-                    for (int r = 0; r < 6; ++r)
-#pragma unroll
-                        for (int q = 0; q <= r; ++q) M[tri(r, q)] = fmaf(col[r], col[q], M[tri(r, q)]);
+                for (int r = 0; r < 6; ++r) {
+                    wv.v[r] = W[r];
+                    bv.v[r] = b[r];
                 }
+                const Y6 yy = normal_solve(S, lane, n, true, P.lm_lambda, wv, bv);
+                float y[6];
 #pragma unroll
-                for (int r = 0; r < 6; ++r) M[tri(r, r)] += P.lm_lambda;
-                chol6(M, inv);
-                chol6_solve(M, inv, b, y);
+                for (int r = 0; r < 6; ++r) y[r] = yy.v[r];
 #pragma unroll 1
                 for (int i = 0; i < n; ++i) {
                     float a = 0.0f, dd = 1e-9f;
@@ -325,7 +358,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
         float alpha_acc = 0.0f;
         if (act) {
             ++n_fk;
-            if (trial_cost(R, T, S, lane, 1.0f) < S.cost0(lane)) {
+            if (trial_cost(rob, A.tg, t, S, lane, 1.0f) < S.cost0(lane)) {
                 take_step(R, S, lane, 1.0f);
                 branch = 0;
                 alpha_acc = 1.0f;
@@ -347,11 +380,14 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
         // ---- dogleg (owner) ----
         if (act && branch != 0) {
             float b[6];
+            Y6 bv, wv;
 #pragma unroll
-            for (int r = 0; r < 6; ++r) b[r] = S.b(r, lane);
-            float G[21], inv[6], y2[6], Jg[6];
-#pragma unroll
-            for (int q = 0; q < 21; ++q) G[q] = 0.0f;
+            for (int r = 0; r < 6; ++r) {
+                b[r] = S.b(r, lane);
+                bv.v[r] = b[r];
+                wv.v[r] = 1.0f;
+            }
+            float Jg[6];
 #pragma unroll
             for (int r = 0; r < 6; ++r) Jg[r] = 0.0f;
             float gg = 0.0f;
@@ -365,16 +401,12 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                 }
                 gg = fmaf(g, g, gg);
 #pragma unroll
-                for (int r = 0; r < 6; ++r) {
-#pragma unroll
-                    for (int q = 0; q <= r; ++q) G[tri(r, q)] = fmaf(col[r], col[q], G[tri(r, q)]);
-                    Jg[r] = fmaf(col[r], g, Jg[r]);
-                }
+                for (int r = 0; r < 6; ++r) Jg[r] = fmaf(col[r], g, Jg[r]);
             }
+            const Y6 yy2 = normal_solve(S, lane, n, false, P.lm_gn_reg, wv, bv);
+            float y2[6];
 #pragma unroll
-            for (int r = 0; r < 6; ++r) G[tri(r, r)] += P.lm_gn_reg;
-            chol6(G, inv);
-            chol6_solve(G, inv, b, y2);
+            for (int r = 0; r < 6; ++r) y2[r] = yy2.v[r];
             float jgjg = 0.0f;
 #pragma unroll
             for (int r = 0; r < 6; ++r) jgjg = fmaf(Jg[r], Jg[r], jgjg);
@@ -438,7 +470,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                 }
             }
             ++n_fk;
-            if (trial_cost(R, T, S, lane, 1.0f) < S.cost0(lane)) {
+            if (trial_cost(rob, A.tg, t, S, lane, 1.0f) < S.cost0(lane)) {
                 take_step(R, S, lane, 1.0f);
                 branch = 1;
             } else {
