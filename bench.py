@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--large-steps", type=int, default=2,
                     help="timed steps of the large case, 10000 targets x 4096 seeds (0: skip)")
     ap.add_argument("--large-budget-gb", type=float, default=2.0, help="workspace budget of the large case (waves)")
+    ap.add_argument("--dof-scaling", type=int, default=1, help="run the 7/12/18/24-DoF leg (0: skip)")
+    ap.add_argument("--tracking-frames", type=int, default=200, help="frames of the tracking loop (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="length of the served Poisson trace at 2000 req/s (0: skip the serving comparison)")
     return ap.parse_args()
@@ -414,6 +416,103 @@ def large_leg(ctx, args, dev, stream):
             "sphere_tests_per_candidate": cnt[3] / args.large_steps / max(cnt[4] / args.large_steps, 1)}
 
 
+def dof_scaling_leg(ctx, args, dev, stream):
+    """The Panda and its 12/18/24-DoF chained variants in an open world, B = 1000
+    seeds per target: single-target latency (one target per call, end to end
+    through hjcd_solve with pinned host buffers, median of 30) and batched
+    throughput (1000 targets x 1000 seeds, one launch per phase)."""
+    import torch
+    from paper_2510_07514_gb300 import inputs
+    rng = np.random.default_rng(inputs.CFG_SEED[1] + 77)
+    out = {}
+    for dof in inputs.DOF_SCALING:
+        rob = inputs.dof_scaling_robot(dof)
+        rid = ctx.add_robot(rob)
+        th = torch.as_tensor(np.ascontiguousarray(rng.uniform(rob.lo, rob.hi, (1000, dof)).T), dtype=torch.float32,
+                             device=dev)
+        tg = ctx.fk(rid, th).contiguous()
+        tg_h = tg.cpu().pin_memory()
+        h1 = (torch.empty((1, 1, dof)).pin_memory(), torch.empty((1, 1, 2)).pin_memory(),
+              torch.empty((1,), dtype=torch.int32).pin_memory())
+        lat = []
+        for i in range(35):
+            t0 = time.perf_counter()
+            ctx.solve(rid, -1, tg_h[i % 100:i % 100 + 1], 1000, 1, 1000 + i, dof, out=h1)
+            if i >= 5:
+                lat.append(1e3 * (time.perf_counter() - t0))
+        outs = (torch.empty((1000, 1, dof), device=dev), torch.empty((1000, 1, 2), device=dev),
+                torch.empty((1000,), dtype=torch.int32, device=dev))
+        ctx.solve(rid, -1, tg, 1000, 1, 7, dof, stream=stream, out=outs)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            ctx.solve(rid, -1, tg, 1000, 1, 7, dof, stream=stream, out=outs)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / 3
+        c, e = outs[2].cpu().numpy(), outs[1].cpu().numpy()
+        succ = (c > 0) & (e[:, 0, 0] <= 1e-3) & (e[:, 0, 1] <= 1e-2)
+        out[str(dof)] = {"single_target_latency_ms_p50": float(np.median(lat)),
+                         "single_target_latency_ms_p90": float(np.percentile(lat, 90)),
+                         "batch_1000x1000_ms": ms, "solves_per_s": 1000 / (ms * 1e-3),
+                         "success_rate": float(succ.mean()),
+                         "median_pos_err_m": float(np.median(e[succ, 0, 0])) if succ.any() else None,
+                         "median_ori_err_rad": float(np.median(e[succ, 0, 1])) if succ.any() else None}
+    return out
+
+
+def tracking_leg(ctx, args, dev):
+    """The tracking loop: every frame the obstacles move (the resident scene is
+    rewritten), the target moves along a circle, and one target x 1000 seeds is
+    solved with the solutions ranked nearest to the current configuration
+    (hjcd_solve_nearest); the arm moves to the first one.  Frame latency is host
+    wall time of scene update + solve with pinned host buffers.  The same frames
+    ranked by score show how much the nearest ranking smooths the motion."""
+    import torch
+    from paper_2510_07514_gb300 import inputs
+    rob = inputs.panda_with_spheres(np.random.default_rng(inputs.CFG_SEED[2]))
+    rid = ctx.add_robot(rob)
+    rng = np.random.default_rng(inputs.CFG_SEED[2] + 5)
+    q_home = np.array([0.0, -0.4, 0.0, -2.0, 0.0, 1.8, 0.8])
+    home = ctx.fk(rid, torch.as_tensor(q_home[:, None], dtype=torch.float32, device=dev)).cpu().numpy()[0]
+    ang = rng.uniform(0, 2 * np.pi, 24)
+    base = np.stack([0.75 * np.cos(ang), 0.75 * np.sin(ang), rng.uniform(0.2, 1.1, 24),
+                     rng.uniform(0.04, 0.08, 24)], 1)
+    sid = ctx.set_scene(inputs.Scene(base, np.zeros((0, 6))))
+    F = args.tracking_frames
+    res = {}
+    for mode in ("nearest", "score"):
+        q_cur = torch.as_tensor(q_home[None], dtype=torch.float32).pin_memory()
+        tgt = torch.empty((1, 7)).pin_memory()
+        out = (torch.empty((1, 1, 7)).pin_memory(), torch.empty((1, 1, 2)).pin_memory(),
+               torch.empty((1,), dtype=torch.int32).pin_memory())
+        lat, steps, ok = [], [], 0
+        for f in range(F):
+            ph = 2 * np.pi * f / F
+            obs = base.copy()
+            obs[:, 2] += 0.05 * np.sin(ph * 3 + np.arange(24))
+            pose = home.copy()
+            pose[0] += 0.12 * np.cos(ph) - 0.12
+            pose[1] += 0.12 * np.sin(ph)
+            tgt[0] = torch.as_tensor(pose)
+            t0 = time.perf_counter()
+            ctx.set_scene(inputs.Scene(obs, np.zeros((0, 6))), sid)
+            ctx.solve(rid, sid, tgt, 1000, 1, 100 + f, 7, out=out, q_current=q_cur if mode == "nearest" else None)
+            lat.append(1e3 * (time.perf_counter() - t0))
+            c, e = int(out[2][0]), out[1][0, 0].numpy()
+            if c > 0 and e[0] <= 1e-3 and e[1] <= 1e-2:
+                ok += 1
+                steps.append(float(torch.max(torch.abs(out[0][0, 0] - q_cur[0]))))
+                q_cur[0] = out[0][0, 0]
+        res[mode] = {"frame_ms_p50": float(np.median(lat[5:])), "frame_ms_p99": float(np.percentile(lat[5:], 99)),
+                     "success_rate": ok / F, "joint_step_rad_median": float(np.median(steps)) if steps else None,
+                     "joint_step_rad_max": float(np.max(steps)) if steps else None}
+    res["frames"] = F
+    res["workload"] = ("Panda + 60 link spheres, 24 obstacle spheres moving every frame, target on a 0.12 m circle, "
+                       "1 target x 1000 seeds per frame")
+    return res
+
+
 def _serve_run(ctx, reqs, trace, idx, rate_scale, server_kw):
     """Submit requests idx at the trace's arrival times (divided by rate_scale)
     to a server started with server_kw; per-request latency and throughput."""
@@ -635,6 +734,10 @@ def hjcd_arm(args):
         line["uneven_batch"] = uneven_leg(ctx, args, dev, stream)
     if world == 1 and args.large_steps > 0:
         line["large"] = large_leg(ctx, args, dev, stream)
+    if world == 1 and args.dof_scaling:
+        line["dof_scaling"] = dof_scaling_leg(ctx, args, dev, stream)
+    if world == 1 and args.tracking_frames > 0:
+        line["tracking"] = tracking_leg(ctx, args, dev)
     if world == 1 and args.serve_seconds > 0:
         line["serving"] = serving_leg(ctx, args, dev)
     ctx.close()

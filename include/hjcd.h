@@ -166,6 +166,7 @@ typedef struct hjcd_batch_item {
     float* out_q;
     float* out_err;
     int32_t* out_count;
+    const float* q_current;  /* NULL, or [n_targets][n] (host or device): rank as hjcd_solve_nearest */
 } hjcd_batch_item;
 
 /* Alg. 2 for several requests at once -- different robots (at most
@@ -275,6 +276,16 @@ hjcd_status hjcd_wait(hjcd_ctx* ctx, int64_t request_id, double timeout_s, hjcd_
  * after another through the same workspace; results equal one whole solve
  * (each chunk keeps its targets' indices inside the request). */
 hjcd_status hjcd_set_memory_budget(hjcd_ctx* ctx, uint64_t bytes);
+
+/* hjcd_solve for tracking (the paper's real-time use moves the arm toward the
+ * returned solution nearest its current configuration): the collision-free
+ * solutions within the request's tolerances come first, ordered by squared
+ * joint-space distance to q_current[t] ([n_targets][n], host or device),
+ * then the other collision-free candidates by score.  Everything else as for
+ * hjcd_solve. */
+hjcd_status hjcd_solve_nearest(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_targets,
+                               const float* targets_pq, const float* q_current, const hjcd_solve_opts* opts,
+                               float* out_q, float* out_err, int32_t* out_count, void* stream);
 
 /* ---- the whole method without allocation ------------------------------------- */
 

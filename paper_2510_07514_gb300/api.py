@@ -76,7 +76,7 @@ class Context:
 
     def solve(self, robot_id: int, scene_id: int, targets: torch.Tensor, n_samples: int, top_k: int, seed: int,
               n_dof: int, eps_pos=1e-3, eps_ori=1e-2, params=None, stream=None, out=None,
-              samples_per_target=None):
+              samples_per_target=None, q_current=None):
         """Solve `targets` ([T, 7] float32, host or device); results are
         allocated on the targets' device unless `out` = (q, err, count) is given."""
         T = int(targets.shape[0])
@@ -86,12 +86,16 @@ class Context:
                    torch.empty((T, top_k, 2), dtype=torch.float32, device=dev),
                    torch.zeros((T,), dtype=torch.int32, device=dev))
         o = self.opts(n_samples, top_k, seed, eps_pos, eps_ori, params, samples_per_target)
-        hjcd.hjcd_solve(self.h, robot_id, scene_id, T, targets, o, out[0], out[1], out[2], stream)
+        if q_current is None:
+            hjcd.hjcd_solve(self.h, robot_id, scene_id, T, targets, o, out[0], out[1], out[2], stream)
+        else:
+            hjcd.hjcd_solve_nearest(self.h, robot_id, scene_id, T, targets, q_current, o, out[0], out[1], out[2],
+                                    stream)
         return out
 
     def batch_item(self, robot_id: int, scene_id: int, targets, n_samples: int, top_k: int, seed: int, n_dof: int,
                    eps_pos=1e-3, eps_ori=1e-2, params=None, samples_per_target=None, spheres=None, boxes=None,
-                   device=None):
+                   device=None, q_current=None):
         """An hjcd_batch_item with freshly allocated outputs (returned beside it).
         `spheres` [k, 4] / `boxes` [k, 6] give the request's own obstacles
         (scene_id < 0).  Outputs live on `device` (default: the targets')."""
@@ -113,6 +117,9 @@ class Context:
             self._keep.append(bx)
             it.n_inline_boxes, it.inline_boxes = len(boxes), bx.ctypes.data
         it.out_q, it.out_err, it.out_count = (hjcd.ptr(x) for x in out)
+        if q_current is not None:
+            self._keep.append(q_current)
+            it.q_current = hjcd.ptr(q_current)
         self._keep.append(targets)
         return it, out
 

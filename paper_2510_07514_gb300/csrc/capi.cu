@@ -550,6 +550,7 @@ static hjcd_status run_waves(hjcd_ctx* ctx, const WaveItem* items, int n_items, 
             sub.t_base = it.t_base + t0;
             sub.targets = it.targets + 7 * (size_t)t0;
             if (it.spt) sub.spt = it.spt + t0;
+            if (it.q_ref) sub.q_ref = it.q_ref + (size_t)t0 * n;
             sub.out_q = it.out_q + (size_t)t0 * it.top_k * n;
             sub.out_err = it.out_err + (size_t)t0 * it.top_k * 2;
             sub.out_count = it.out_count + t0;
@@ -621,6 +622,25 @@ hjcd_status hjcd_solve(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_
     return solve_items(ctx, &it, 1, P, (cudaStream_t)stream);
 }
 
+hjcd_status hjcd_solve_nearest(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_targets,
+                               const float* targets_pq, const float* q_current, const hjcd_solve_opts* opts,
+                               float* out_q, float* out_err, int32_t* out_count, void* stream) {
+    if (!ctx) return HJCD_EINVAL;
+    hjcd_status st;
+    WaveItem it;
+    if ((st = item_from(ctx, robot_id, scene_id, n_targets, targets_pq, opts, out_q, out_err, out_count, &it)))
+        return st;
+    if (n_targets == 0) return HJCD_OK;
+    if (!q_current) return fail(ctx, HJCD_EINVAL, "null q_current");
+    it.q_ref = q_current;
+    hjcd_params P;
+    if (opts->params) P = *opts->params;
+    else hjcd_default_params(&P);
+    if ((st = check_params(ctx, P))) return st;
+    if ((st = make_current(ctx))) return st;
+    return solve_items(ctx, &it, 1, P, (cudaStream_t)stream);
+}
+
 hjcd_status hjcd_solve_batch(hjcd_ctx* ctx, int n_items, const hjcd_batch_item* items, const hjcd_params* params,
                              void* stream) {
     if (!ctx) return HJCD_EINVAL;
@@ -651,6 +671,7 @@ hjcd_status hjcd_solve_batch(hjcd_ctx* ctx, int n_items, const hjcd_batch_item* 
             w[i].cd_iters = b.opts.params->cd_max_iters;
             w[i].lm_iters = b.opts.params->lm_max_iters;
         }
+        w[i].q_ref = b.q_current;
     }
     if ((st = make_current(ctx))) return st;
     return solve_items(ctx, w.data(), n_items, P, (cudaStream_t)stream);

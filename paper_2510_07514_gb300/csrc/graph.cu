@@ -93,6 +93,11 @@ hjcd_status hjcd_graph_create(hjcd_ctx* ctx, int n_items, const hjcd_batch_item*
         it.out_q = b.out_q;
         it.out_err = b.out_err;
         it.out_count = b.out_count;
+        if (b.q_current && pointer_kind(b.q_current) != 1) {
+            release(G);
+            return fail(ctx, HJCD_EINVAL, "item %d: a graph takes q_current in device memory", i);
+        }
+        it.q_ref = b.q_current;
     }
     if ((st = plan_wave(ctx, G->items.data(), n_items, P, &G->plan))) {
         release(G);

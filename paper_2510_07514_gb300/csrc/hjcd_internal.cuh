@@ -85,8 +85,9 @@ struct __align__(16) TargetDesc {
     int32_t scene;     // row of the launch's scene table, -1: no obstacles
     int16_t cd_iters;  // PO-CCD iteration cap
     int16_t lm_iters;  // PJ-IK iteration cap
-    int32_t top_k;     // solutions returned
+    int32_t top_k;     // solutions returned; kNearestFlag set: ranked nearest-first (RankArgs::q_ref)
 };
+constexpr int32_t kNearestFlag = 1 << 30;
 static_assert(sizeof(TargetDesc) == 64, "TargetDesc layout");
 
 // Copy the launch's robot tables into shared memory (all threads of the CTA
@@ -428,6 +429,11 @@ struct RankArgs {
     float* out_q;
     float* out_err;
     int32_t* out_count;
+    // with q_ref set ([T][ld_ref], target t's reference configuration in row t): the candidates
+    // within the target's tolerances come first, nearest to the reference (squared joint
+    // distance), then the others by score
+    const float* q_ref;
+    int32_t ld_ref;
 };
 
 // Collision filter of C candidates.  With tg null or uniform set every

@@ -129,6 +129,7 @@ struct WaveItem {
     int top_k = 1;
     int cd_iters = -1, lm_iters = -1;  // < 0: the batch parameters' caps
     int t_base = 0;  // index of targets[0] inside its request (keys the random streams)
+    const float* q_ref = nullptr;  // [T][n] reference configurations (nearest-first ranking), host or device
     float* out_q = nullptr;  // [T][top_k][n], host or device
     float* out_err = nullptr;  // [T][top_k][2]
     int32_t* out_count = nullptr;  // [T]
@@ -150,10 +151,12 @@ struct WavePlan {
     std::vector<SceneEnt> scenes;
     std::vector<int> item_t0;
     std::vector<int64_t> item_q0, item_e0;
-    std::vector<char> dev_tgt, dev_q, dev_e, dev_c;
+    std::vector<char> dev_tgt, dev_q, dev_e, dev_c, dev_ref;
+    bool has_ref = false;
     int64_t q_total = 0, e_total = 0;
     // head: copied from the pinned image to the start of the workspace in one copy
-    size_t o_rp = 0, o_rd = 0, o_sd = 0, o_tg = 0, o_moff = 0, o_boff = 0, o_qe = 0, o_pq7 = 0, o_inl = 0, head = 0;
+    size_t o_rp = 0, o_rd = 0, o_sd = 0, o_tg = 0, o_moff = 0, o_boff = 0, o_qe = 0, o_pq7 = 0, o_ref = 0, o_inl = 0,
+           head = 0;
     // the rest of the workspace
     size_t o_thM = 0, o_sM = 0, o_thB = 0, o_sB = 0, o_pB = 0, o_oB = 0, o_hB = 0, o_q = 0, o_e = 0, o_c = 0,
            o_qf = 0, bytes = 0;

@@ -89,18 +89,41 @@ __global__ void __launch_bounds__(kSelThreads) k_rank(const RankArgs A) {
     int count = 0;
     if (B > 0) {
         const int N = pow2_at_least(B);
+        const int n = A.rs.rp[A.tg ? A.tg[t].robot : 0].n;
+        const int tk = A.tg ? A.tg[t].top_k : A.top_k;
+        const bool nearest = A.q_ref && (tk & kNearestFlag);
+        float ep = 0.0f, eo = 0.0f;
+        if (nearest) {
+            ep = A.tg[t].eps_pos;
+            eo = A.tg[t].eps_ori;
+        }
         for (int i = threadIdx.x; i < N; i += blockDim.x) {
             uint64_t k = kNoKey;
             if (i < B && !(A.hit && A.hit[b0 + i])) {
                 const float sc = A.score[b0 + i];
-                if (sc < __int_as_float(0x7f800000)) k = score_key(sc, (uint32_t)i);  // finite only
+                if (sc < __int_as_float(0x7f800000)) {  // finite only
+                    k = score_key(sc, (uint32_t)i);
+                    if (nearest) {
+                        // class bit 63: 0 = within tolerances (keyed by distance), 1 = the rest (by score)
+                        const int64_t g = b0 + i;
+                        if (A.perr[g] <= ep && A.oerr[g] <= eo) {
+                            float d2 = 0.0f;
+                            for (int j = 0; j < n; ++j) {
+                                const float dj = A.th[j * A.ld + g] - A.q_ref[(int64_t)t * A.ld_ref + j];
+                                d2 = fmaf(dj, dj, d2);
+                            }
+                            k = score_key(d2, (uint32_t)i);
+                        } else {
+                            k |= 1ull << 63;
+                        }
+                    }
+                }
             }
             keys[i] = k;
         }
         __syncthreads();
         bitonic_sort(keys, N);
-        const int top_k = A.tg ? A.tg[t].top_k : A.top_k;
-        const int n = A.rs.rp[A.tg ? A.tg[t].robot : 0].n;
+        const int top_k = tk & ~kNearestFlag;
         const int lim = min(top_k, B);
         for (int r = 0; r < lim; ++r) count += keys[r] != kNoKey;
         float* oq = A.out_q + (A.qe_off ? A.qe_off[2 * t] : (int64_t)t * top_k * n);

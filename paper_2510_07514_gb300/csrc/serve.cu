@@ -32,7 +32,7 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 struct Req {
     int64_t id = 0;
     int32_t robot_id = 0, scene_id = -1;
-    std::vector<float> targets, sph, box;
+    std::vector<float> targets, sph, box, q_ref;
     std::vector<int32_t> spt;
     hjcd_solve_opts opts{};
     int cd_iters = -1, lm_iters = -1;
@@ -159,6 +159,7 @@ bool Server::launch(Slot& sl, std::vector<Req*>& take) {
             it.top_k = r->opts.top_k;
             it.cd_iters = r->cd_iters;
             it.lm_iters = r->lm_iters;
+            it.q_ref = r->q_ref.empty() ? nullptr : r->q_ref.data();
         }
         // a first plan (without outputs) sizes the batch
         for (auto& it : items) {
@@ -402,6 +403,10 @@ hjcd_status hjcd_submit(hjcd_ctx* ctx, const hjcd_batch_item* req, int64_t* requ
         r->lm_iters = o.params->lm_max_iters;
     }
     r->targets.assign(req->targets_pq, req->targets_pq + 7 * (size_t)T);
+    if (req->q_current) {
+        if (pointer_kind(req->q_current) == 1) return fail(ctx, HJCD_EINVAL, "served requests take host buffers");
+        r->q_ref.assign(req->q_current, req->q_current + (size_t)T * r->n);
+    }
     for (int t = 0; t < T; ++t) {
         const int m = o.samples_per_target ? o.samples_per_target[t] : o.n_samples;
         if (m < 1 || m > HJCD_MAX_SAMPLES) return fail(ctx, HJCD_EINVAL, "target %d: seed count %d outside [1, %d]", t, m, HJCD_MAX_SAMPLES);

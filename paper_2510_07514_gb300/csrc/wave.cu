@@ -35,6 +35,7 @@ hjcd_status plan_wave(hjcd_ctx* ctx, const WaveItem* items, int n_items, const h
     W.dev_q.resize(n_items);
     W.dev_e.resize(n_items);
     W.dev_c.resize(n_items);
+    W.dev_ref.resize(n_items);
     size_t inl_bytes = 0;
     for (int i = 0; i < n_items; ++i) {
         const WaveItem& it = items[i];
@@ -83,6 +84,8 @@ hjcd_status plan_wave(hjcd_ctx* ctx, const WaveItem* items, int n_items, const h
         W.dev_q[i] = it.T > 0 && pointer_kind(it.out_q) == 1;
         W.dev_e[i] = it.T > 0 && pointer_kind(it.out_err) == 1;
         W.dev_c[i] = it.T > 0 && pointer_kind(it.out_count) == 1;
+        W.dev_ref[i] = it.T > 0 && it.q_ref && pointer_kind(it.q_ref) == 1;
+        W.has_ref = W.has_ref || (it.T > 0 && it.q_ref);
         W.host_out = W.host_out || (it.T > 0 && (!W.dev_q[i] || !W.dev_e[i] || !W.dev_c[i]));
         if (it.T > 0 && !W.dev_tgt[i]) {
             for (int t = 0; t < it.T; ++t) {
@@ -128,6 +131,7 @@ hjcd_status plan_wave(hjcd_ctx* ctx, const WaveItem* items, int n_items, const h
     W.o_boff = cv.take<int64_t>((size_t)W.T + 1);
     W.o_qe = cv.take<int64_t>(2 * (size_t)W.T);
     W.o_pq7 = cv.take<float>(7 * (size_t)W.T);
+    W.o_ref = cv.take<float>(W.has_ref ? (size_t)W.T * W.n_max : 0);
     W.o_inl = cv.take<char>(inl_bytes);
     W.head = cv.off;
     W.o_thM = cv.take<float>((size_t)W.n_max * W.CM);
@@ -197,7 +201,7 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
             d.scene = W.item_scene[i];
             d.cd_iters = (int16_t)cd;
             d.lm_iters = (int16_t)lm;
-            d.top_k = it.top_k;
+            d.top_k = it.top_k | (it.q_ref ? kNearestFlag : 0);
             h_tg[g] = d;
             const int m = it.spt ? it.spt[t] : it.n_samples;
             h_moff[g + 1] = h_moff[g] + m;
@@ -207,6 +211,14 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
         }
         if (!W.dev_tgt[i] && it.T > 0)
             std::memcpy(h_pq7 + 7 * (size_t)W.item_t0[i], it.targets, sizeof(float) * 7 * (size_t)it.T);
+        if (W.has_ref && it.T > 0) {
+            // reference rows at stride n_max (rows of requests without references are not read)
+            float* h_ref = reinterpret_cast<float*>(pin + W.o_ref) + (size_t)W.item_t0[i] * W.n_max;
+            for (int t = 0; t < it.T; ++t)
+                for (int j = 0; j < W.n_max; ++j)
+                    h_ref[(size_t)t * W.n_max + j] =
+                        (it.q_ref && !W.dev_ref[i] && j < n) ? it.q_ref[(size_t)t * n + j] : 0.0f;
+        }
     }
 
     // ---- host -> device ----
@@ -215,6 +227,12 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
         if (W.dev_tgt[i] && items[i].T > 0)
             HJCD_CUDA(ctx, cudaMemcpyAsync(ws + W.o_pq7 + sizeof(float) * 7 * (size_t)W.item_t0[i], items[i].targets,
                                            sizeof(float) * 7 * (size_t)items[i].T, cudaMemcpyDeviceToDevice, s));
+    for (int i = 0; i < W.n_items; ++i)
+        if (W.dev_ref[i])
+            HJCD_CUDA(ctx, cudaMemcpy2DAsync(ws + W.o_ref + sizeof(float) * (size_t)W.item_t0[i] * W.n_max,
+                                             sizeof(float) * W.n_max, items[i].q_ref,
+                                             sizeof(float) * items[i].rob->P.n, sizeof(float) * items[i].rob->P.n,
+                                             (size_t)items[i].T, cudaMemcpyDeviceToDevice, s));
     HJCD_CUDA(ctx, cudaMemsetAsync(ws + W.o_qf, 0, 16, s));
     HJCD_CUDA(ctx, cudaMemsetAsync(ws + W.o_q, 0xff, sizeof(float) * (size_t)W.q_total, s));  // unfilled rows: NaN
     HJCD_CUDA(ctx, cudaMemsetAsync(ws + W.o_e, 0xff, sizeof(float) * (size_t)W.e_total, s));
@@ -316,7 +334,8 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
     float* e_out = reinterpret_cast<float*>(ws + W.o_e);
     int32_t* c_out = reinterpret_cast<int32_t*>(ws + W.o_c);
     RankArgs ra{rs, d_tg, W.T, d_boff, thB, W.CB, sB, pB, oB, collide ? hB : nullptr, 0,
-                reinterpret_cast<const int64_t*>(ws + W.o_qe), q_out, e_out, c_out};
+                reinterpret_cast<const int64_t*>(ws + W.o_qe), q_out, e_out, c_out,
+                W.has_ref ? reinterpret_cast<const float*>(ws + W.o_ref) : nullptr, W.n_max};
     launch_rank(ra, W.max_b, s);
     if ((st = after_launch(ctx, 1))) return st;
     if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[5], s));

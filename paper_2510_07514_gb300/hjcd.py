@@ -32,7 +32,7 @@ EXPORTS = (
     "hjcd_create_robot", "hjcd_set_scene", "hjcd_solve", "hjcd_fk", "hjcd_sample_seeds",
     "hjcd_po_ccd", "hjcd_topk_dup", "hjcd_pjik", "hjcd_collide", "hjcd_rank",
     "hjcd_set_profiling", "hjcd_phase_times", "hjcd_counters", "hjcd_launch_count", "hjcd_ffma_probe",
-    "hjcd_solve_noalloc", "hjcd_solve_batch",
+    "hjcd_solve_noalloc", "hjcd_solve_batch", "hjcd_solve_nearest",
     "hjcd_server_start", "hjcd_server_stop", "hjcd_submit", "hjcd_poll", "hjcd_wait",
     "hjcd_graph_create", "hjcd_graph_launch", "hjcd_graph_check", "hjcd_graph_destroy",
     "hjcd_set_launch_config", "hjcd_autotune", "hjcd_set_memory_budget", "hjcd_scene_contacts",
@@ -69,7 +69,7 @@ class hjcd_batch_item(ct.Structure):
         ("robot_id", ct.c_int32), ("scene_id", ct.c_int32), ("n_inline_spheres", ct.c_int32),
         ("n_inline_boxes", ct.c_int32), ("inline_spheres", ct.c_void_p), ("inline_boxes", ct.c_void_p),
         ("n_targets", ct.c_int32), ("pad_", ct.c_int32), ("targets_pq", ct.c_void_p), ("opts", hjcd_solve_opts),
-        ("out_q", ct.c_void_p), ("out_err", ct.c_void_p), ("out_count", ct.c_void_p),
+        ("out_q", ct.c_void_p), ("out_err", ct.c_void_p), ("out_count", ct.c_void_p), ("q_current", ct.c_void_p),
     ]
 
 
@@ -119,6 +119,7 @@ _SIGS = {
     "hjcd_solve": (_ST, [_V, _I32, _I32, _I, _V, ct.POINTER(hjcd_solve_opts), _V, _V, _V, _V]),
     "hjcd_solve_noalloc": (_ST, [_V, _I32, _I32, _I, _V, ct.POINTER(hjcd_solve_opts), _V, _V, _V, _V]),
     "hjcd_solve_batch": (_ST, [_V, _I, ct.POINTER(hjcd_batch_item), ct.POINTER(hjcd_params), _V]),
+    "hjcd_solve_nearest": (_ST, [_V, _I32, _I32, _I, _V, _V, ct.POINTER(hjcd_solve_opts), _V, _V, _V, _V]),
     "hjcd_server_start": (_ST, [_V, ct.POINTER(hjcd_server_opts)]),
     "hjcd_set_launch_config": (_ST, [_V, _I32, _I32]),
     "hjcd_set_memory_budget": (_ST, [_V, _U64]),
@@ -255,6 +256,13 @@ def hjcd_solve_noalloc(ctx, robot_id, scene_id, n_targets, targets_pq, opts: hjc
     """hjcd_solve without allocation (device buffers; scratch in a static device array)."""
     _check(ctx, load().hjcd_solve_noalloc(ctx, int(robot_id), int(scene_id), int(n_targets), ptr(targets_pq),
                                           ct.byref(opts), ptr(out_q), ptr(out_err), ptr(out_count),
+                                          stream_handle(stream)))
+
+
+def hjcd_solve_nearest(ctx, robot_id, scene_id, n_targets, targets_pq, q_current, opts: hjcd_solve_opts, out_q,
+                       out_err, out_count, stream=None) -> None:
+    _check(ctx, load().hjcd_solve_nearest(ctx, int(robot_id), int(scene_id), int(n_targets), ptr(targets_pq),
+                                          ptr(q_current), ct.byref(opts), ptr(out_q), ptr(out_err), ptr(out_count),
                                           stream_handle(stream)))
 
 

@@ -127,6 +127,24 @@ def panda() -> Robot:
     )
 
 
+def panda_chain(copies: int) -> Robot:
+    """6 x copies joints: the Panda's first six DH rows and limits repeated
+    (the DoF-scaling variants of 12, 18 and 24 joints), flange 0.107 m along
+    the last axis.  Repeating the rows literally puts each copy's first joint
+    on the axis of the previous copy's sixth joint (a = 0, alpha = 0)."""
+    p = panda()
+    rep = lambda v: np.tile(np.asarray(v[:6], float), copies)
+    return Robot(n=6 * copies, a=rep(p.a), alpha=rep(p.alpha), d=rep(p.d), theta_off=np.zeros(6 * copies),
+                 flange=_trans_z(0.107), lo=rep(p.lo), hi=rep(p.hi))
+
+
+DOF_SCALING = (7, 12, 18, 24)  # the Panda and its chained variants
+
+
+def dof_scaling_robot(dof: int) -> Robot:
+    return panda() if dof == 7 else panda_chain(dof // 6)
+
+
 def planar(lengths) -> Robot:
     """Planar nR chain: all axes parallel to z, link i of length lengths[i]."""
     n = len(lengths)

@@ -62,7 +62,7 @@ def test_struct_layouts(lib):
     assert ctypes.sizeof(hjcd.hjcd_solve_opts) == 4 * 4 + 8 + 8 + 8
     assert ctypes.sizeof(hjcd.hjcd_ccd_trace) == 10 * 8
     assert ctypes.sizeof(hjcd.hjcd_lm_trace) == 5 * 8
-    assert ctypes.sizeof(hjcd.hjcd_batch_item) == 4 * 4 + 2 * 8 + 2 * 4 + 8 + ctypes.sizeof(hjcd.hjcd_solve_opts) + 3 * 8
+    assert ctypes.sizeof(hjcd.hjcd_batch_item) == 4 * 4 + 2 * 8 + 2 * 4 + 8 + ctypes.sizeof(hjcd.hjcd_solve_opts) + 4 * 8
     assert ctypes.sizeof(hjcd.hjcd_server_opts) == 4 + 4 + 8 + 8 + 8
     assert ctypes.sizeof(hjcd.hjcd_request_info) == 4 + 4 + 8 + 8
     assert ctypes.sizeof(hjcd.hjcd_tune_report) == 6 * 4 + 8 + 8

@@ -292,3 +292,41 @@ def test_autotune_picks_a_valid_configuration(ctx):
         assert abs(succ - rep.success_rate) < 1e-6
     finally:
         hjcd.hjcd_set_launch_config(ctx.h, 128, 4)
+
+
+def test_solve_nearest_ranks_by_distance_to_the_current_configuration(ctx):
+    """hjcd_solve_nearest returns the same collision-free candidates as
+    hjcd_solve, reordered: those within the tolerances first, nearest to
+    q_current (squared joint distance), then the rest by score."""
+    wl = inputs.cfg1()
+    rob = wl.robot
+    rid = ctx.add_robot(rob)
+    rng = np.random.default_rng(81)
+    T = 16
+    tg = dev(f32(orc.pose(orc.Robot(rob), f32(rng.uniform(rob.lo, rob.hi, (T, 7))))))
+    qref = f32(rng.uniform(rob.lo, rob.hi, (T, 7)))
+    q0, e0, c0 = (host(x) for x in ctx.solve(rid, -1, tg, 64, 64, 5, 7))
+    q1, e1, c1 = (host(x) for x in ctx.solve(rid, -1, tg, 64, 64, 5, 7, q_current=dev(qref)))
+    assert np.array_equal(c0, c1)
+    n_ok = 0
+    for t in range(T):
+        c = int(c0[t])
+        a = {tuple(r) for r in q0[t, :c]}
+        b = {tuple(r) for r in q1[t, :c]}
+        assert a == b
+        ok = (e1[t, :c, 0] <= 1e-3) & (e1[t, :c, 1] <= 1e-2)
+        k = int(ok.sum())
+        n_ok += k
+        assert np.all(ok[:k]) and not np.any(ok[k:])  # within-tolerance rows first
+        d = np.sum((q1[t, :k].astype(np.float32) - qref[t].astype(np.float32)) ** 2, axis=1)
+        assert np.all(np.diff(d) >= -1e-6 * np.maximum(d[1:], 1e-12))
+        rest = [tuple(r) for r in q1[t, k:c]]
+        order0 = [tuple(r) for r in q0[t, :c] if tuple(r) in set(rest)]
+        assert rest == order0  # the others keep the score order
+    assert n_ok > T
+    # in a batch, a request with references and one without: the latter keeps score order
+    it1, o1 = ctx.batch_item(rid, -1, tg, 64, 64, 5, 7, q_current=dev(qref))
+    it2, o2 = ctx.batch_item(rid, -1, tg, 64, 64, 5, 7)
+    ctx.solve_batch([it1, it2])
+    _same(o1, (dev(q1), dev(e1), torch.as_tensor(c1, device="cuda")))
+    _same(o2, (dev(q0), dev(e0), torch.as_tensor(c0, device="cuda")))

@@ -192,3 +192,29 @@ def test_large_workload_shape_matches_the_oracle(ctx):
     assert abs(succ.mean() - so.mean()) <= 1 / 24 + 1e-12
     assert succ.mean() > 0.6  # 256 seeds in a cluttered field; the benchmark runs 4096
     assert np.mean(c) > 8  # most targets return many collision-free solutions
+
+
+@pytest.mark.parametrize("dof", [12, 24])
+def test_dof_scaling_variants_match_the_oracle(ctx, dof):
+    """The chained-Panda variants (open world): success rates within 1/32 of the
+    oracle's on 32 targets x 256 seeds, every solution re-verified."""
+    rob = inputs.dof_scaling_robot(dof)
+    assert rob.n == dof
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    rng = np.random.default_rng(70 + dof)
+    tg = f32(orc.pose(orob, f32(rng.uniform(rob.lo, rob.hi, (32, dof)))))
+    q, e, c = ctx.solve(rid, -1, torch.as_tensor(tg, dtype=torch.float32, device="cuda"), 256, 2, 11, dof)
+    q, e, c = host(q).astype(np.float64), host(e).astype(np.float64), host(c)
+    succ = np.zeros(32, bool)
+    for t in range(32):
+        for r in range(c[t]):
+            err = orc.residual(orob, q[t, r], tg[t])
+            assert abs(np.linalg.norm(err[:3]) - e[t, r, 0]) < 2e-5
+            assert abs(np.linalg.norm(err[3:]) - e[t, r, 1]) < 2e-5
+            assert np.all(q[t, r] >= rob.lo - 1e-7) and np.all(q[t, r] <= rob.hi + 1e-7)
+        succ[t] = c[t] > 0 and e[t, 0, 0] <= 1e-3 and e[t, 0, 1] <= 1e-2
+    o = orc.solve(orob, None, orc.make_params(1e-3, 1e-2, seed=11), tg, 256, 2)
+    so = (o["count"] > 0) & (o["err"][:, 0, 0] <= 1e-3) & (o["err"][:, 0, 1] <= 1e-2)
+    assert abs(succ.mean() - so.mean()) <= 1 / 32 + 1e-12
+    assert succ.mean() > 0.9
