@@ -53,6 +53,8 @@ def parse():
                     help="timed steps of the large case, 10000 targets x 4096 seeds (0: skip)")
     ap.add_argument("--large-budget-gb", type=float, default=2.0, help="workspace budget of the large case (waves)")
     ap.add_argument("--dof-scaling", type=int, default=1, help="run the 7/12/18/24-DoF leg (0: skip)")
+    ap.add_argument("--ccd-baseline", type=int, default=1,
+                    help="also time the main workload with the position-only CCD initialiser (0: skip)")
     ap.add_argument("--tracking-frames", type=int, default=200, help="frames of the tracking loop (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="length of the served Poisson trace at 2000 req/s (0: skip the serving comparison)")
@@ -730,6 +732,24 @@ def hjcd_arm(args):
                 "ms_per_step": float(np.mean(e2e_ms))},
         "clocks": clk, "gpu_launches": int(launches),
     }
+    if world == 1 and args.ccd_baseline:
+        # the same step with the position-only CCD (Alg. 1) in place of PO-CCD (Alg. 3)
+        pb = api.make_params(cd_variant=1)
+        ctx.solve(rid, sid, tg, S, K, wl.seed, n, wl.eps_pos, wl.eps_ori, params=pb, stream=stream, out=out)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        b0.record(stream)
+        for _ in range(3):
+            ctx.solve(rid, sid, tg, S, K, wl.seed, n, wl.eps_pos, wl.eps_ori, params=pb, stream=stream, out=out)
+        b1.record(stream)
+        torch.cuda.synchronize(dev)
+        ph_b = hjcd.hjcd_phase_times(ctx.h)
+        cb, eb = out[2].cpu().numpy(), out[1].cpu().numpy()
+        line["ccd_baseline"] = {
+            "initialiser": "position-only CCD (Alg. 1), the rest of Alg. 2 unchanged",
+            "ms_per_step": b0.elapsed_time(b1) / 3, "solves_per_s": T / (b0.elapsed_time(b1) / 3 * 1e-3),
+            "success_rate": float(np.mean((cb > 0) & (eb[:, 0, 0] <= wl.eps_pos) & (eb[:, 0, 1] <= wl.eps_ori))),
+            "phase_ms_last_step": {nm: float(v) for nm, v in zip(names + ["step"], ph_b)}}
     if world == 1 and args.uneven_steps > 0:
         line["uneven_batch"] = uneven_leg(ctx, args, dev, stream)
     if world == 1 and args.large_steps > 0:

@@ -77,6 +77,8 @@ typedef struct hjcd_params {
     float lm_sigma;         /* std of the PJ-IK perturbation, rad [Sigma] */
     float lm_gn_reg;        /* regulariser of the minimum-norm Gauss-Newton step (Eq. dogleg) */
     float cd_tie;           /* greedy joint choice: a later joint wins only if its score is lower by this fraction */
+    int32_t cd_variant;     /* 0: PO-CCD (Alg. 3); 1: position-only CCD (Alg. 1: joints n..1, each rotated
+                               at once by Eq. theta_proj, break on the squared position error), a baseline */
 } hjcd_params;
 
 typedef struct hjcd_solve_opts {

@@ -59,6 +59,7 @@ class Params(ct.Structure):
         ("lm_A", ct.c_int32),
         ("lm_sigma", ct.c_double), ("lm_gn_reg", ct.c_double),
         ("cd_tie", ct.c_double),
+        ("cd_variant", ct.c_int32),
         ("key", ct.c_uint32 * 2),
     ]
 

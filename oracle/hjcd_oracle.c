@@ -505,6 +505,8 @@ static double ccd_position_delta(const double pee[3], const double pt[3], const 
 /* One iteration k of Alg. 3 for one candidate (theta updated in place).
  * Returns 1 when the coarse tolerance of Alg. 3 holds after the update. */
 static double score_of(const orc_params* P, double ep, double eo);
+static int ccd_classic_iteration(const orc_robot* R, const orc_params* P, const double tgt[7], double* th,
+                                 double* dp);
 
 static int ccd_iteration(const orc_robot* R, const orc_params* P, const double tgt[7], uint32_t t,
                          uint32_t c, int k, double* th, double* dp, double* ep_p, double* eo_p, double* dq,
@@ -642,6 +644,12 @@ void orc_ccd_iteration_batch(const orc_robot* R, const orc_params* P, const doub
     for (int64_t c = 0; c < C; ++c) {
         double th[ORC_MAXN];
         memcpy(th, th_in + c * n, (size_t)n * sizeof(double));
+        if (P->cd_variant == 1) {
+            const int cv = ccd_classic_iteration(R, P, targets + 7 * (int64_t)tgt[c], th, dp ? dp + c * n : NULL);
+            memcpy(th_out + c * n, th, (size_t)n * sizeof(double));
+            if (converged) converged[c] = (uint8_t)cv;
+            continue;
+        }
         int conv = ccd_iteration(R, P, targets + 7 * (int64_t)tgt[c], (uint32_t)tgt[c], (uint32_t)cand[c], k, th,
                                  dp ? dp + c * n : NULL, ep_p ? ep_p + c * n : NULL, eo_p ? eo_p + c * n : NULL,
                                  dq ? dq + c * n : NULL, ep_q ? ep_q + c * n : NULL, eo_q ? eo_q + c * n : NULL,
@@ -659,6 +667,30 @@ static double score_of(const orc_params* P, double ep, double eo) {
     return a * a + b * b;
 }
 
+/* Alg. 1, one iteration: joints from the last to the first, each rotated at
+ * once by its Eq. theta_proj step (kept inside the limits, reading c18), with a
+ * fresh kinematics pass before every joint; then the break test on the squared
+ * position error.  dp (may be NULL) receives the step applied to each joint.
+ * Returns 1 when the break test holds. */
+static int ccd_classic_iteration(const orc_robot* R, const orc_params* P, const double tgt[7], double* th,
+                                 double* dp) {
+    const int n = R->n;
+    const double pt[3] = {tgt[0], tgt[1], tgt[2]};
+    double F[MAXB * 16], pee[3], pj[3], rj[3];
+    for (int j = n - 1; j >= 0; --j) {
+        orc_fk_frames(R, th, F);
+        frame_pos(F + 16 * (n + 1), pee);
+        frame_pos(F + 16 * (j + 1), pj);
+        frame_col(F + 16 * (j + 1), 2, rj);
+        const double d = clampd(th[j] + ccd_position_delta(pee, pt, pj, rj, P->proj_eps), R->lo[j], R->hi[j]) - th[j];
+        th[j] += d;
+        if (dp) dp[j] = d;
+    }
+    double ep, eo;
+    pos_ori_err(R, th, tgt, &ep, &eo);
+    return ep * ep < P->cd_eps_pos2;
+}
+
 /* Alg. 3 for one candidate: seed, then at most max_iters iterations. */
 void orc_po_ccd_batch(const orc_robot* R, const orc_params* P, const double* targets,
                       int64_t C, const int32_t* tgt, const int32_t* cand,
@@ -671,8 +703,11 @@ void orc_po_ccd_batch(const orc_robot* R, const orc_params* P, const double* tar
         sample_seed(R, P, (uint32_t)tgt[c], (uint32_t)cand[c], th);
         int it = P->cd_max_iters;
         for (int k = 0; k < P->cd_max_iters; ++k) {
-            if (ccd_iteration(R, P, T, (uint32_t)tgt[c], (uint32_t)cand[c], k, th, NULL, NULL, NULL, NULL,
-                              NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL)) {
+            const int cv = P->cd_variant == 1
+                               ? ccd_classic_iteration(R, P, T, th, NULL)
+                               : ccd_iteration(R, P, T, (uint32_t)tgt[c], (uint32_t)cand[c], k, th, NULL, NULL, NULL,
+                                               NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
+            if (cv) {
                 it = k + 1;
                 break;
             }

@@ -111,6 +111,7 @@ hjcd_status check_params(hjcd_ctx* ctx, const hjcd_params& P) {
         return fail(ctx, HJCD_EINVAL, "perturbation scales must be >= 0");
     if (!(P.proj_eps >= 0.0f)) return fail(ctx, HJCD_EINVAL, "proj_eps must be >= 0");
     if (!(P.cd_tie >= 0.0f && P.cd_tie < 1.0f)) return fail(ctx, HJCD_EINVAL, "cd_tie must be in [0, 1)");
+    if (P.cd_variant != 0 && P.cd_variant != 1) return fail(ctx, HJCD_EINVAL, "cd_variant must be 0 or 1");
     return HJCD_OK;
 }
 
@@ -195,6 +196,7 @@ void hjcd_default_params(hjcd_params* o) {
     o->lm_sigma = 0.01f;
     o->lm_gn_reg = 1e-6f;
     o->cd_tie = 1e-4f;
+    o->cd_variant = 0;
 }
 
 hjcd_status hjcd_init(int device, hjcd_ctx** out) {

@@ -104,14 +104,43 @@ __global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
             const V3 e = pt - E.p;
             ep2 = dot(e, e);
             eo = quat_angle(qerr.w, dot(qerr.v, qerr.v));
-            // Alg. 3 coarse break, checked after each update
-            if (kk > 0 && ep2 < P.cd_eps_pos2 && eo * eo < P.cd_eps_ori2) {
+            // Alg. 3 coarse break, checked after each update (Alg. 1: the position part only)
+            if (kk > 0 && ep2 < P.cd_eps_pos2 && (P.cd_variant == 1 || eo * eo < P.cd_eps_ori2)) {
                 iters = kk;
                 break;
             }
             if (kk == cap) break;
             const int k = A.k0 + kk;
             const float ep0 = sqrtf(ep2);
+
+            if (P.cd_variant == 1) {
+                // Alg. 1: joints from the last to the first, each rotated at once by its Eq. theta_proj
+                // step; rotating joint j leaves the frames of joints <= j in place and moves the end
+                // effector about joint j's axis
+                V3 x = E.p;
+#pragma unroll 1
+                for (int j = n - 1; j >= 0; --j) {
+                    const float* f = col.fr(j);
+                    const V3 pj = v3(f[0 * kCcdThreads], f[1 * kCcdThreads], f[2 * kCcdThreads]);
+                    const V3 z = v3(f[3 * kCcdThreads], f[4 * kCcdThreads], f[5 * kCcdThreads]);
+                    const float thj = col.th(j);
+                    const V3 u = x - pj, v = pt - pj;
+                    const float uz = dot(u, z), vz = dot(v, z);
+                    const V3 up = fma3(-uz, z, u), vp = fma3(-vz, z, v);
+                    const float nu2 = dot(u, u), nv2 = dot(v, v), nup2 = dot(up, up), nvp2 = dot(vp, vp);
+                    const V3 zxu = cross(z, up);
+                    const bool deg = nu2 < 1e-24f || nv2 < 1e-24f || nup2 <= pe2 * nu2 || nvp2 <= pe2 * nv2;
+                    float d = deg ? 0.0f : atan2f(dot(zxu, vp), dot(up, vp));
+                    d = clampf(thj + d, R.lo[j], R.hi[j]) - thj;
+                    float sd, cd;
+                    sincos_red(d, &sd, &cd);  // |d| may exceed pi
+                    x = pj + fma3(uz, z, fma3(cd, up, sd * zxu));
+                    col.th(j) = thj + d;
+                    if (TRACE && kk == 0 && A.tr.dp) A.tr.dp[j * A.ld + c] = d;
+                }
+                ++n_it;
+                continue;
+            }
 
             // one position and one orientation proposal per joint, the
             // task residual each leaves, and the greedy choice by its score

@@ -53,7 +53,7 @@ class hjcd_params(ct.Structure):
         ("dup_ratio", ct.c_int32), ("dup_sigma", ct.c_float),
         ("lm_max_iters", ct.c_int32), ("lm_lambda", ct.c_float), ("lm_trust_R", ct.c_float),
         ("lm_beta", ct.c_float), ("lm_A", ct.c_int32), ("lm_sigma", ct.c_float), ("lm_gn_reg", ct.c_float),
-        ("cd_tie", ct.c_float),
+        ("cd_tie", ct.c_float), ("cd_variant", ct.c_int32),
     ]
 
 

@@ -58,7 +58,7 @@ def test_init_without_gpu_fails_cleanly(lib):
 
 def test_struct_layouts(lib):
     # field order and sizes of the structs passed by pointer
-    assert ctypes.sizeof(hjcd.hjcd_params) == 19 * 4
+    assert ctypes.sizeof(hjcd.hjcd_params) == 20 * 4
     assert ctypes.sizeof(hjcd.hjcd_solve_opts) == 4 * 4 + 8 + 8 + 8
     assert ctypes.sizeof(hjcd.hjcd_ccd_trace) == 10 * 8
     assert ctypes.sizeof(hjcd.hjcd_lm_trace) == 5 * 8

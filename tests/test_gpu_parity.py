@@ -608,3 +608,63 @@ def test_long_chain_solves(ctx):
     q, err, cnt = host(q), host(err), host(cnt).astype(int)
     succ = _verify(orob, None, rob, tg, q, err, cnt, 1e-3, 1e-2)
     assert succ.mean() >= 0.75
+
+
+# ----------------------------------------------------------------------------
+# the position-only CCD baseline (Alg. 1)
+
+@pytest.mark.parametrize("which", ["panda", "chain12"])
+def test_classic_ccd_matches_the_oracle(ctx, which):
+    """cd_variant = 1: one sweep from identical inputs (per-joint steps and the
+    resulting joint vector), then whole PO-CCD runs (break on the position
+    error only) -- steps agree to the binary32 sensitivity of the sweep, most
+    candidates to 1e-5."""
+    rob = dict(robots())[which]
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    rng = np.random.default_rng(91)
+    T, C = 11, 1500
+    tg = _targets(orob, rng, T, rob.lo, rob.hi)
+    tgt = rng.integers(0, T, C).astype(np.int32)
+    cand = rng.integers(0, 4096, C).astype(np.int32)
+    th = f32(rng.uniform(rob.lo, rob.hi, (C, rob.n)))
+    gp = api.make_params(cd_variant=1)
+    g = _ccd_gpu(ctx, rid, rob.n, tg, tgt, cand, th, 0, gp, 5)
+    o = orc.ccd_iteration(orob, orc.make_params(seed=5, cd_variant=1), tg, tgt, cand, 0, th)
+    tol = TOL * max(1.0, reach(rob) / 1.5)
+    err = np.max(np.abs(g["theta"] - o["theta"]), axis=1)
+    assert np.mean(err < tol) > 0.9, np.mean(err < tol)
+    assert np.all(np.abs(g["dp"] - o["dp"])[err < tol] < tol)
+    assert np.all(g["theta"] >= rob.lo - 1e-6) and np.all(g["theta"] <= rob.hi + 1e-6)
+    # whole runs: the same seeds, break on |e_p|^2 < cd_eps_pos2 only
+    S = 64
+    t2 = np.repeat(np.arange(T), S).astype(np.int32)
+    c2 = np.tile(np.arange(S), T).astype(np.int32)
+    C2 = T * S
+    th_o = torch.empty((rob.n, C2), device="cuda")
+    perr = torch.empty((C2,), device="cuda")
+    iters = torch.empty((C2,), dtype=torch.int32, device="cuda")
+    hjcd.hjcd_po_ccd(ctx.h, rid, T, dev(tg), 1e-3, 1e-2, 5, gp, C2, dev(t2, torch.int32), dev(c2, torch.int32),
+                     None, th_o, C2, 0, 32, None, perr, None, iters)
+    o2 = orc.po_ccd(orob, orc.make_params(seed=5, cd_variant=1), tg, t2, c2)
+    same = np.max(np.abs(host(th_o).T - o2["theta"]), axis=1) < 1e-3
+    assert same.mean() > 0.8, same.mean()
+    conv_g, conv_o = host(perr) ** 2 < 1e-4, o2["perr"] ** 2 < 1e-4
+    assert abs(conv_g.mean() - conv_o.mean()) < 0.03
+
+
+def test_classic_ccd_as_the_initialiser_of_the_whole_method(ctx):
+    """Alg. 2 with the position-only CCD in place of PO-CCD: success within 3
+    points of the oracle on 100 Panda targets x 128 seeds."""
+    wl = inputs.cfg1()
+    rob = wl.robot
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    rng = np.random.default_rng(92)
+    tg = f32(orc.pose(orob, f32(rng.uniform(rob.lo, rob.hi, (100, 7)))))
+    q, err, cnt = ctx.solve(rid, -1, dev(tg), 128, 1, 9, 7, params=api.make_params(cd_variant=1))
+    q, err, cnt = host(q), host(err), host(cnt).astype(int)
+    succ_g = _verify(orob, None, rob, tg, q, err, cnt, 1e-3, 1e-2)
+    o = orc.solve(orob, None, orc.make_params(1e-3, 1e-2, seed=9, cd_variant=1), tg, 128, 1)
+    succ_o = (o["count"] > 0) & (o["err"][:, 0, 0] <= 1e-3) & (o["err"][:, 0, 1] <= 1e-2)
+    assert abs(succ_g.mean() - succ_o.mean()) <= 0.03 + 1e-12

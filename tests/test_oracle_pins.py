@@ -621,3 +621,46 @@ def test_solve_round_trip_open_world(panda):
         assert np.all(np.diff(o["err"][t, :, 0] ** 2 / 1e-6 + o["err"][t, :, 1] ** 2 / 1e-4) >= -1e-12)
         succ += (o["err"][t, 0, 0] <= wl.eps_pos) and (o["err"][t, 0, 1] <= wl.eps_ori)
     assert succ >= 3
+
+
+# ----------------------------------------------------------------------------
+# the position-only CCD baseline (Alg. 1)
+
+def test_classic_ccd_sweep_order_by_hand():
+    """Planar 2R chain of unit links at theta = 0, target (0, 1.5): Alg. 1
+    turns the last joint first (about (1, 0): from direction (1, 0) to the
+    target's direction (-1, 1.5)), then the first joint (about the origin:
+    from the moved end effector's direction to the target's)."""
+    rob = orc.Robot(inputs.planar([1.0, 1.0]))
+    P = orc.make_params(seed=1, cd_variant=1)
+    tg = np.array([[0.0, 1.5, 0.0, 1.0, 0.0, 0.0, 0.0]])
+    tr = orc.ccd_iteration(rob, P, tg, [0], [0], 0, np.zeros((1, 2)))
+    d2 = math.atan2(1.5, -1.0)
+    ee = (1.0 + math.cos(d2), math.sin(d2))
+    d1 = math.atan2(1.5, 0.0) - math.atan2(ee[1], ee[0])
+    assert tr["dp"][0, 1] == pytest.approx(d2, abs=1e-12)
+    assert tr["dp"][0, 0] == pytest.approx(d1, abs=1e-12)
+    assert np.allclose(tr["theta"][0], [d1, d2], atol=1e-12)
+
+
+def test_classic_ccd_reaches_planar_targets_and_respects_limits():
+    """On a planar 3R chain the sweeps drive reachable targets to zero position
+    error (the break test ends the run); with tight limits every joint stays
+    inside them."""
+    chain = inputs.planar([0.5, 0.4, 0.3])
+    chain.lo, chain.hi = np.full(3, -20.0), np.full(3, 20.0)  # too wide to bind (no angle wrapping)
+    rob = orc.Robot(chain)
+    P = orc.make_params(seed=2, cd_variant=1, cd_max_iters=200, cd_eps_pos2=1e-16)
+    rng = np.random.default_rng(3)
+    th = rng.uniform(-math.pi, math.pi, (40, 3))
+    tg = _poses(rob, th)
+    out = orc.po_ccd(rob, P, tg, np.arange(40), np.zeros(40, np.int32))
+    # CCD can wind joints up or crawl near a singular pose; a wrong order or sign fails almost everywhere
+    assert np.mean(out["perr"] < 1e-8) > 0.9
+    assert np.mean(out["iters"] < 200) > 0.9
+    tight = inputs.planar([0.5, 0.4, 0.3])
+    tight.lo, tight.hi = np.full(3, -0.3), np.full(3, 0.3)
+    rt = orc.Robot(tight)
+    o2 = orc.po_ccd(rt, P, tg, np.arange(40), np.zeros(40, np.int32))
+    assert np.all(o2["theta"] >= -0.3 - 1e-15) and np.all(o2["theta"] <= 0.3 + 1e-15)
+    assert np.mean(o2["perr"] > 1e-3) > 0.5  # most of those targets lie outside the reachable set
