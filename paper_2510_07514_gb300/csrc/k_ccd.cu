@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
                     const float nu2 = dot(u, u), nv2 = dot(v, v), nup2 = dot(up, up), nvp2 = dot(vp, vp);
                     const V3 zxu = cross(z, up);
                     const bool deg = nu2 < 1e-24f || nv2 < 1e-24f || nup2 <= pe2 * nu2 || nvp2 <= pe2 * nv2;
-                    float d = deg ? 0.0f : atan2f(dot(zxu, vp), dot(up, vp));
+                    float d = deg ? 0.0f : atan2_all(dot(zxu, vp), dot(up, vp));
                     d = clampf(thj + d, R.lo[j], R.hi[j]) - thj;
                     float sd, cd;
                     sincos_red(d, &sd, &cd);  // |d| may exceed pi
@@ -148,7 +148,6 @@ __global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
             // choice only when its score is lower by more than the fraction cd_tie
             float best_p = 0.0f, dP = 0.0f, best_o = 0.0f, dO = 0.0f;
             int jp = 0, jo = 0;
-            V3 Pp = v3(0.f, 0.f, 0.f), Zp = Pp, Po = Pp, Zo = Pp;
             const float phi = eo;
 #pragma unroll 1
             for (int j = 0; j < n; ++j) {
@@ -173,7 +172,7 @@ __global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
                 // Eq. theta_proj, signed about the axis: atan2(z.(up x vp), up.vp) = atan2(zxu.vp, up.vp)
                 const float cs = dot(up, vp), sn = dot(zxu, vp);
                 const bool deg = nu2 < 1e-24f || nv2 < 1e-24f || nup2 <= pe2 * nu2 || nvp2 <= pe2 * nv2;
-                float d = deg ? 0.0f : atan2f(sn, cs);
+                float d = deg ? 0.0f : atan2_all(sn, cs);
                 d = clampf(thj + d, lo, hi) - thj;
                 float sh, ch;
                 __sincosf(0.5f * d, &sh, &ch);
@@ -187,8 +186,6 @@ __global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
                     best_p = sp;
                     jp = j;
                     dP = d;
-                    Pp = pj;
-                    Zp = z;
                 }
 
                 // Eq. ori_update: delta(k) sgn(a.z) phi
@@ -206,8 +203,6 @@ __global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
                     best_o = so;
                     jo = j;
                     dO = dq;
-                    Po = pj;
-                    Zo = z;
                 }
                 if (TRACE && kk == 0) {
                     if (A.tr.dp) A.tr.dp[j * A.ld + c] = d;
@@ -226,6 +221,13 @@ __global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
                 else aP = 0.0f;
             }
             // residual at theta_hat: the distal joint's rotation first, then the proximal one
+            // (the chosen joints' origins and axes are still in the shared-memory column)
+            const float* fp = col.fr(jp);
+            const float* fo = col.fr(jo);
+            const V3 Pp = v3(fp[0 * kCcdThreads], fp[1 * kCcdThreads], fp[2 * kCcdThreads]);
+            const V3 Zp = v3(fp[3 * kCcdThreads], fp[4 * kCcdThreads], fp[5 * kCcdThreads]);
+            const V3 Po = v3(fo[0 * kCcdThreads], fo[1 * kCcdThreads], fo[2 * kCcdThreads]);
+            const V3 Zo = v3(fo[3 * kCcdThreads], fo[4 * kCcdThreads], fo[5 * kCcdThreads]);
             const bool p_hi = jp > jo;
             const V3 Pa = p_hi ? Pp : Po, Za = p_hi ? Zp : Zo, Pb = p_hi ? Po : Pp, Zb = p_hi ? Zo : Zp;
             const float da = p_hi ? aP : aO, db = p_hi ? aO : aP;
