@@ -77,8 +77,12 @@ typedef struct hjcd_params {
     float lm_sigma;         /* std of the PJ-IK perturbation, rad [Sigma] */
     float lm_gn_reg;        /* regulariser of the minimum-norm Gauss-Newton step (Eq. dogleg) */
     float cd_tie;           /* greedy joint choice: a later joint wins only if its score is lower by this fraction */
-    int32_t cd_variant;     /* 0: PO-CCD (Alg. 3); 1: position-only CCD (Alg. 1: joints n..1, each rotated
-                               at once by Eq. theta_proj, break on the squared position error), a baseline */
+    int32_t cd_variant;     /* 0: PO-CCD (Alg. 3), each seed breaking on its own; 1: position-only CCD
+                               (Alg. 1: joints n..1, each rotated at once by Eq. theta_proj, break on the
+                               squared position error), a baseline; 2: PO-CCD with the target-wide break
+                               (all seeds of a target stop after the first iteration that leaves any of
+                               them inside the coarse tolerance; whole solves only, not hjcd_po_ccd or
+                               hjcd_solve_noalloc) */
 } hjcd_params;
 
 typedef struct hjcd_solve_opts {

@@ -691,11 +691,56 @@ static int ccd_classic_iteration(const orc_robot* R, const orc_params* P, const 
     return ep * ep < P->cd_eps_pos2;
 }
 
+/* cd_variant 2, reading of Sec. IV ("once a seed satisfies the thresholds the
+ * parallel loop is broken and all samples are returned"): the seeds of a
+ * target (the candidates with that target row, in input order) take
+ * iterations together; after the first iteration that leaves any of them
+ * inside the coarse tolerance, every seed of the target stops. */
+static void po_ccd_target_break(const orc_robot* R, const orc_params* P, const double* targets, int64_t C,
+                                const int32_t* tgt, const int32_t* cand, double* th_out, double* score,
+                                double* perr, double* oerr, int32_t* iters) {
+    const int n = R->n;
+    int32_t tmax = -1;
+    for (int64_t c = 0; c < C; ++c)
+        if (tgt[c] > tmax) tmax = tgt[c];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t t = 0; t <= tmax; ++t) {
+        const double* T = targets + 7 * (int64_t)t;
+        for (int64_t c = 0; c < C; ++c)
+            if (tgt[c] == t) sample_seed(R, P, (uint32_t)t, (uint32_t)cand[c], th_out + c * n);
+        int stop = P->cd_max_iters;
+        for (int k = 0; k < P->cd_max_iters; ++k) {
+            int any = 0;
+            for (int64_t c = 0; c < C; ++c)
+                if (tgt[c] == t)
+                    any |= ccd_iteration(R, P, T, (uint32_t)t, (uint32_t)cand[c], k, th_out + c * n, NULL, NULL, NULL,
+                                         NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
+            if (any) {
+                stop = k + 1;
+                break;
+            }
+        }
+        for (int64_t c = 0; c < C; ++c) {
+            if (tgt[c] != t) continue;
+            double ep, eo;
+            pos_ori_err(R, th_out + c * n, T, &ep, &eo);
+            if (score) score[c] = score_of(P, ep, eo);
+            if (perr) perr[c] = ep;
+            if (oerr) oerr[c] = eo;
+            if (iters) iters[c] = stop;
+        }
+    }
+}
+
 /* Alg. 3 for one candidate: seed, then at most max_iters iterations. */
 void orc_po_ccd_batch(const orc_robot* R, const orc_params* P, const double* targets,
                       int64_t C, const int32_t* tgt, const int32_t* cand,
                       double* th_out, double* score, double* perr, double* oerr, int32_t* iters) {
     const int n = R->n;
+    if (P->cd_variant == 2) {
+        po_ccd_target_break(R, P, targets, C, tgt, cand, th_out, score, perr, oerr, iters);
+        return;
+    }
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t c = 0; c < C; ++c) {
         const double* T = targets + 7 * (int64_t)tgt[c];

@@ -42,7 +42,8 @@ typedef struct {
     int32_t lm_A;
     double lm_sigma, lm_gn_reg;
     double cd_tie;                      /* relative tie tolerance of the greedy joint choice */
-    int32_t cd_variant;                 /* 0: PO-CCD (Alg. 3); 1: position-only CCD (Alg. 1) */
+    int32_t cd_variant;                 /* 0: PO-CCD (Alg. 3); 1: position-only CCD (Alg. 1);
+                                           2: PO-CCD with the target-wide break */
     uint32_t key[2];                    /* Philox key = request seed (lo, hi) */
 } orc_params;
 

@@ -111,7 +111,7 @@ hjcd_status check_params(hjcd_ctx* ctx, const hjcd_params& P) {
         return fail(ctx, HJCD_EINVAL, "perturbation scales must be >= 0");
     if (!(P.proj_eps >= 0.0f)) return fail(ctx, HJCD_EINVAL, "proj_eps must be >= 0");
     if (!(P.cd_tie >= 0.0f && P.cd_tie < 1.0f)) return fail(ctx, HJCD_EINVAL, "cd_tie must be in [0, 1)");
-    if (P.cd_variant != 0 && P.cd_variant != 1) return fail(ctx, HJCD_EINVAL, "cd_variant must be 0 or 1");
+    if (P.cd_variant < 0 || P.cd_variant > 2) return fail(ctx, HJCD_EINVAL, "cd_variant must be 0, 1 or 2");
     return HJCD_OK;
 }
 
@@ -755,6 +755,8 @@ hjcd_status hjcd_po_ccd(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const fl
     if ((st = check_theta(ctx, theta_out, n_cand, ld, "theta_out"))) return st;
     if (k0 < 0 || n_iters < 0) return fail(ctx, HJCD_EINVAL, "k0 and n_iters must be >= 0");
     if (trace && n_iters != 1) return fail(ctx, HJCD_EINVAL, "a trace needs n_iters == 1");
+    if (P.cd_variant == 2)
+        return fail(ctx, HJCD_EINVAL, "cd_variant 2 (target-wide break) runs whole targets: use hjcd_solve");
     CcdArgs a{};
     a.rs = single_robot_set(*rob);
     a.tg = d_tg;
@@ -1078,6 +1080,7 @@ extern "C" hjcd_status hjcd_solve_noalloc(hjcd_ctx* ctx, int32_t robot_id, int32
     if (opts->params) P = *opts->params;
     else hjcd_default_params(&P);
     if ((st = check_params(ctx, P))) return st;
+    if (P.cd_variant == 2) return fail(ctx, HJCD_EINVAL, "hjcd_solve_noalloc does not run cd_variant 2");
     if ((st = make_current(ctx))) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const RobotParams& R = rob->P;

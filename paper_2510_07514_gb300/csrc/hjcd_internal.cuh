@@ -403,6 +403,7 @@ struct CcdArgs {
     int64_t C, ld;
     const float* th_in;  // null: sample seeds
     float* th_out;
+    float* th_tmp;       // cd_variant = 2: a second [n][ld] buffer
     float *score, *perr, *oerr;
     int32_t* iters;
     int k0, n_iters;  // n_iters < 0: each target's cd_iters

@@ -158,7 +158,7 @@ struct WavePlan {
     size_t o_rp = 0, o_rd = 0, o_sd = 0, o_tg = 0, o_moff = 0, o_boff = 0, o_qe = 0, o_pq7 = 0, o_ref = 0, o_inl = 0,
            head = 0;
     // the rest of the workspace
-    size_t o_thM = 0, o_sM = 0, o_thB = 0, o_sB = 0, o_pB = 0, o_oB = 0, o_hB = 0, o_q = 0, o_e = 0, o_c = 0,
+    size_t o_thM = 0, o_thM2 = 0, o_sM = 0, o_thB = 0, o_sB = 0, o_pB = 0, o_oB = 0, o_hB = 0, o_q = 0, o_e = 0, o_c = 0,
            o_qf = 0, bytes = 0;
     bool host_out = false;  // some output goes to host memory
 };

@@ -48,6 +48,198 @@ __device__ __forceinline__ void sample_seed(const RobotParams& R, const TargetDe
     }
 }
 
+// One iteration of a candidate: kinematics with frames into the column, the
+// residual (ep2 = |e_p|^2, eo = |omega|), the break test (kk > 0) and the cap,
+// then the update of Alg. 3 (or Alg. 1 with cd_variant = 1) of the joint
+// vector in the column.  Returns 1 when the candidate has converged, 2 at the
+// cap (no update in either case), 0 after an update.
+template <bool TRACE, int TH>
+__device__ __forceinline__ int ccd_step(const RobotParams& R, const TargetDesc& T, const hjcd_params& P,
+                                        const ColT<TH>& col, const CcdArgs& A, int64_t c, uint32_t s, int kk, int cap,
+                                        float delta_k, const V3 pt, float pe2, float one_m_tie, float inv_p2,
+                                        float inv_o2, float& ep2, float& eo) {
+    constexpr int kCcdThreads = TH;
+    const int n = R.n;
+    // kinematics with frames
+    Frame F = frame_identity();
+#pragma unroll 1
+    for (int j = 0; j < n; ++j) {
+        fk_step(R, j, col.th(j), F);
+        float* f = col.fr(j);
+        f[0 * kCcdThreads] = F.p.x;
+        f[1 * kCcdThreads] = F.p.y;
+        f[2 * kCcdThreads] = F.p.z;
+        f[3 * kCcdThreads] = F.c2.x;
+        f[4 * kCcdThreads] = F.c2.y;
+        f[5 * kCcdThreads] = F.c2.z;
+    }
+    const Frame E = fk_flange(R, F);
+    const Q4 qerr = quat_error(T, quat_from_frame(E));
+    const V3 e = pt - E.p;
+    ep2 = dot(e, e);
+    eo = quat_angle(qerr.w, dot(qerr.v, qerr.v));
+    // Alg. 3 coarse break, checked after each update (Alg. 1: the position part only)
+    if (kk > 0 && ep2 < P.cd_eps_pos2 && (P.cd_variant == 1 || eo * eo < P.cd_eps_ori2)) return 1;
+    if (kk == cap) return 2;
+    const int k = A.k0 + kk;
+    const float ep0 = sqrtf(ep2);
+
+    if (P.cd_variant == 1) {
+        // Alg. 1: joints from the last to the first, each rotated at once by its Eq. theta_proj
+        // step; rotating joint j leaves the frames of joints <= j in place and moves the end
+        // effector about joint j's axis
+        V3 x = E.p;
+#pragma unroll 1
+        for (int j = n - 1; j >= 0; --j) {
+            const float* f = col.fr(j);
+            const V3 pj = v3(f[0 * kCcdThreads], f[1 * kCcdThreads], f[2 * kCcdThreads]);
+            const V3 z = v3(f[3 * kCcdThreads], f[4 * kCcdThreads], f[5 * kCcdThreads]);
+            const float thj = col.th(j);
+            const V3 u = x - pj, v = pt - pj;
+            const float uz = dot(u, z), vz = dot(v, z);
+            const V3 up = fma3(-uz, z, u), vp = fma3(-vz, z, v);
+            const float nu2 = dot(u, u), nv2 = dot(v, v), nup2 = dot(up, up), nvp2 = dot(vp, vp);
+            const V3 zxu = cross(z, up);
+            const bool deg = nu2 < 1e-24f || nv2 < 1e-24f || nup2 <= pe2 * nu2 || nvp2 <= pe2 * nv2;
+            float d = deg ? 0.0f : atan2_all(dot(zxu, vp), dot(up, vp));
+            d = clampf(thj + d, R.lo[j], R.hi[j]) - thj;
+            float sd, cd;
+            sincos_red(d, &sd, &cd);  // |d| may exceed pi
+            x = pj + fma3(uz, z, fma3(cd, up, sd * zxu));
+            col.th(j) = thj + d;
+            if (TRACE && kk == 0 && A.tr.dp) A.tr.dp[j * A.ld + c] = d;
+        }
+        return 0;
+    }
+
+    // one position and one orientation proposal per joint, the
+    // task residual each leaves, and the greedy choice by its score
+    // (|e_p|/eps_pos)^2 + (|omega|/eps_ori)^2; a later joint replaces the
+    // choice only when its score is lower by more than the fraction cd_tie
+    float best_p = 0.0f, dP = 0.0f, best_o = 0.0f, dO = 0.0f;
+    int jp = 0, jo = 0;
+    const float phi = eo;
+#pragma unroll 1
+    for (int j = 0; j < n; ++j) {
+        const float* f = col.fr(j);
+        const V3 pj = v3(f[0 * kCcdThreads], f[1 * kCcdThreads], f[2 * kCcdThreads]);
+        const V3 z = v3(f[3 * kCcdThreads], f[4 * kCcdThreads], f[5 * kCcdThreads]);
+        const float thj = col.th(j), lo = R.lo[j], hi = R.hi[j];
+        const V3 u = E.p - pj;
+        const V3 v = pt - pj;
+        const float uz = dot(u, z), vz = dot(v, z);
+        const V3 up = fma3(-uz, z, u);
+        const V3 vp = fma3(-vz, z, v);
+        const float nu2 = dot(u, u), nv2 = dot(v, v);
+        const float nup2 = dot(up, up), nvp2 = dot(vp, vp);
+        const V3 zxu = cross(z, up);
+        // rotating joint j by x: the end effector moves to pj + uz z + cos x up + sin x (z x up),
+        // the error quaternion becomes qerr [cos(x/2), -sin(x/2) z]
+        const V3 r0 = fma3(vz - uz, z, vp);
+        const float az = dot(qerr.v, z);
+        const V3 qz = fma3(qerr.w, z, cross(qerr.v, z));
+
+        // Eq. theta_proj, signed about the axis: atan2(z.(up x vp), up.vp) = atan2(zxu.vp, up.vp)
+        const float cs = dot(up, vp), sn = dot(zxu, vp);
+        const bool deg = nu2 < 1e-24f || nv2 < 1e-24f || nup2 <= pe2 * nu2 || nvp2 <= pe2 * nv2;
+        float d = deg ? 0.0f : atan2_all(sn, cs);
+        d = clampf(thj + d, lo, hi) - thj;
+        float sh, ch;
+        __sincosf(0.5f * d, &sh, &ch);
+        V3 r = fma3(-2.0f * sh * ch, zxu, fma3(-fmaf(-2.0f * sh, sh, 1.0f), up, r0));
+        const float rp2 = dot(r, r);
+        float w2 = fmaf(qerr.w, ch, sh * az);
+        V3 v2 = fma3(ch, qerr.v, (-sh) * qz);
+        const float op = quat_angle(w2, dot(v2, v2));
+        const float sp = fmaf(rp2, inv_p2, op * op * inv_o2);
+        if (j == 0 || sp < best_p * one_m_tie) {
+            best_p = sp;
+            jp = j;
+            dP = d;
+        }
+
+        // Eq. ori_update: delta(k) sgn(a.z) phi
+        const float sg = (az > 0.0f) ? 1.0f : ((az < 0.0f) ? -1.0f : 0.0f);
+        float dq = delta_k * sg * phi;
+        dq = clampf(thj + dq, lo, hi) - thj;
+        __sincosf(0.5f * dq, &sh, &ch);
+        r = fma3(-2.0f * sh * ch, zxu, fma3(-fmaf(-2.0f * sh, sh, 1.0f), up, r0));
+        const float pq2 = dot(r, r);
+        w2 = fmaf(qerr.w, ch, sh * az);
+        v2 = fma3(ch, qerr.v, (-sh) * qz);
+        const float rq = quat_angle(w2, dot(v2, v2));
+        const float so = fmaf(pq2, inv_p2, rq * rq * inv_o2);
+        if (j == 0 || so < best_o * one_m_tie) {
+            best_o = so;
+            jo = j;
+            dO = dq;
+        }
+        if (TRACE && kk == 0) {
+            if (A.tr.dp) A.tr.dp[j * A.ld + c] = d;
+            if (A.tr.rp) A.tr.rp[j * A.ld + c] = sqrtf(rp2);
+            if (A.tr.op) A.tr.op[j * A.ld + c] = op;
+            if (A.tr.dq) A.tr.dq[j * A.ld + c] = dq;
+            if (A.tr.pq) A.tr.pq[j * A.ld + c] = sqrtf(pq2);
+            if (A.tr.rq) A.tr.rq[j * A.ld + c] = rq;
+        }
+    }
+
+    // apply both; on the same joint the larger step
+    float aP = dP, aO = dO;
+    if (jp == jo) {
+        if (fabsf(dP) >= fabsf(dO)) aO = 0.0f;
+        else aP = 0.0f;
+    }
+    // residual at theta_hat: the distal joint's rotation first, then the proximal one
+    // (the chosen joints' origins and axes are still in the shared-memory column)
+    const float* fp = col.fr(jp);
+    const float* fo = col.fr(jo);
+    const V3 Pp = v3(fp[0 * kCcdThreads], fp[1 * kCcdThreads], fp[2 * kCcdThreads]);
+    const V3 Zp = v3(fp[3 * kCcdThreads], fp[4 * kCcdThreads], fp[5 * kCcdThreads]);
+    const V3 Po = v3(fo[0 * kCcdThreads], fo[1 * kCcdThreads], fo[2 * kCcdThreads]);
+    const V3 Zo = v3(fo[3 * kCcdThreads], fo[4 * kCcdThreads], fo[5 * kCcdThreads]);
+    const bool p_hi = jp > jo;
+    const V3 Pa = p_hi ? Pp : Po, Za = p_hi ? Zp : Zo, Pb = p_hi ? Po : Pp, Zb = p_hi ? Zo : Zp;
+    const float da = p_hi ? aP : aO, db = p_hi ? aO : aP;
+    float sa_, ca_, sb_, cb_;
+    __sincosf(0.5f * da, &sa_, &ca_);
+    __sincosf(0.5f * db, &sb_, &cb_);
+    V3 x = Pa + rotate_half(Za, sa_, ca_, E.p - Pa);
+    x = Pb + rotate_half(Zb, sb_, cb_, x - Pb);
+    Q4 q1 = qmul(qerr, Q4{ca_, (-sa_) * Za});
+    q1 = qmul(q1, Q4{cb_, (-sb_) * Zb});
+    const V3 e1 = pt - x;
+    const float ep1 = sqrtf(dot(e1, e1));
+    const float eo1 = quat_angle(q1.w, dot(q1.v, q1.v));
+    // acceptance (reading: an improvement above gamma in position or in orientation)
+    const bool acc = (ep0 - ep1 > P.cd_gamma_pos) || (eo - eo1 > P.cd_gamma_ori);
+
+    if (TRACE && kk == 0) {
+        if (A.tr.jp) A.tr.jp[c] = jp;
+        if (A.tr.jo) A.tr.jo[c] = jo;
+        if (A.tr.accepted) A.tr.accepted[c] = acc ? 1 : 0;
+        if (A.tr.th_hat) {
+#pragma unroll 1
+            for (int j = 0; j < n; ++j)
+                A.tr.th_hat[j * A.ld + c] = col.th(j) + (j == jp ? aP : 0.0f) + (j == jo ? aO : 0.0f);
+        }
+    }
+    if (acc) {
+        col.th(jp) += aP;
+        col.th(jo) += aO;
+    } else {
+        // rejection: theta + N(0, sigma^2 I), kept inside the limits
+#pragma unroll 1
+        for (int b = 0; 2 * b < n; ++b) {
+            const float2 z = normal_pair(T, (uint32_t)s, kPhaseCd, (uint32_t)k, b);
+            const int j0 = 2 * b, j1 = 2 * b + 1;
+            col.th(j0) = clampf(fmaf(P.cd_sigma, z.x, col.th(j0)), R.lo[j0], R.hi[j0]);
+            if (j1 < n) col.th(j1) = clampf(fmaf(P.cd_sigma, z.y, col.th(j1)), R.lo[j1], R.hi[j1]);
+        }
+    }
+    return 0;
+}
+
 template <bool TRACE, int TH>
 __global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
     using Col = ColT<TH>;
@@ -86,187 +278,10 @@ __global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
         const bool valid = T.eps_pos > 0.0f;
 
         for (int kk = 0; valid; ++kk) {
-            // kinematics with frames
-            Frame F = frame_identity();
-#pragma unroll 1
-            for (int j = 0; j < n; ++j) {
-                fk_step(R, j, col.th(j), F);
-                float* f = col.fr(j);
-                f[0 * kCcdThreads] = F.p.x;
-                f[1 * kCcdThreads] = F.p.y;
-                f[2 * kCcdThreads] = F.p.z;
-                f[3 * kCcdThreads] = F.c2.x;
-                f[4 * kCcdThreads] = F.c2.y;
-                f[5 * kCcdThreads] = F.c2.z;
-            }
-            const Frame E = fk_flange(R, F);
-            const Q4 qerr = quat_error(T, quat_from_frame(E));
-            const V3 e = pt - E.p;
-            ep2 = dot(e, e);
-            eo = quat_angle(qerr.w, dot(qerr.v, qerr.v));
-            // Alg. 3 coarse break, checked after each update (Alg. 1: the position part only)
-            if (kk > 0 && ep2 < P.cd_eps_pos2 && (P.cd_variant == 1 || eo * eo < P.cd_eps_ori2)) {
-                iters = kk;
-                break;
-            }
-            if (kk == cap) break;
-            const int k = A.k0 + kk;
-            const float ep0 = sqrtf(ep2);
-
-            if (P.cd_variant == 1) {
-                // Alg. 1: joints from the last to the first, each rotated at once by its Eq. theta_proj
-                // step; rotating joint j leaves the frames of joints <= j in place and moves the end
-                // effector about joint j's axis
-                V3 x = E.p;
-#pragma unroll 1
-                for (int j = n - 1; j >= 0; --j) {
-                    const float* f = col.fr(j);
-                    const V3 pj = v3(f[0 * kCcdThreads], f[1 * kCcdThreads], f[2 * kCcdThreads]);
-                    const V3 z = v3(f[3 * kCcdThreads], f[4 * kCcdThreads], f[5 * kCcdThreads]);
-                    const float thj = col.th(j);
-                    const V3 u = x - pj, v = pt - pj;
-                    const float uz = dot(u, z), vz = dot(v, z);
-                    const V3 up = fma3(-uz, z, u), vp = fma3(-vz, z, v);
-                    const float nu2 = dot(u, u), nv2 = dot(v, v), nup2 = dot(up, up), nvp2 = dot(vp, vp);
-                    const V3 zxu = cross(z, up);
-                    const bool deg = nu2 < 1e-24f || nv2 < 1e-24f || nup2 <= pe2 * nu2 || nvp2 <= pe2 * nv2;
-                    float d = deg ? 0.0f : atan2_all(dot(zxu, vp), dot(up, vp));
-                    d = clampf(thj + d, R.lo[j], R.hi[j]) - thj;
-                    float sd, cd;
-                    sincos_red(d, &sd, &cd);  // |d| may exceed pi
-                    x = pj + fma3(uz, z, fma3(cd, up, sd * zxu));
-                    col.th(j) = thj + d;
-                    if (TRACE && kk == 0 && A.tr.dp) A.tr.dp[j * A.ld + c] = d;
-                }
-                ++n_it;
-                continue;
-            }
-
-            // one position and one orientation proposal per joint, the
-            // task residual each leaves, and the greedy choice by its score
-            // (|e_p|/eps_pos)^2 + (|omega|/eps_ori)^2; a later joint replaces the
-            // choice only when its score is lower by more than the fraction cd_tie
-            float best_p = 0.0f, dP = 0.0f, best_o = 0.0f, dO = 0.0f;
-            int jp = 0, jo = 0;
-            const float phi = eo;
-#pragma unroll 1
-            for (int j = 0; j < n; ++j) {
-                const float* f = col.fr(j);
-                const V3 pj = v3(f[0 * kCcdThreads], f[1 * kCcdThreads], f[2 * kCcdThreads]);
-                const V3 z = v3(f[3 * kCcdThreads], f[4 * kCcdThreads], f[5 * kCcdThreads]);
-                const float thj = col.th(j), lo = R.lo[j], hi = R.hi[j];
-                const V3 u = E.p - pj;
-                const V3 v = pt - pj;
-                const float uz = dot(u, z), vz = dot(v, z);
-                const V3 up = fma3(-uz, z, u);
-                const V3 vp = fma3(-vz, z, v);
-                const float nu2 = dot(u, u), nv2 = dot(v, v);
-                const float nup2 = dot(up, up), nvp2 = dot(vp, vp);
-                const V3 zxu = cross(z, up);
-                // rotating joint j by x: the end effector moves to pj + uz z + cos x up + sin x (z x up),
-                // the error quaternion becomes qerr [cos(x/2), -sin(x/2) z]
-                const V3 r0 = fma3(vz - uz, z, vp);
-                const float az = dot(qerr.v, z);
-                const V3 qz = fma3(qerr.w, z, cross(qerr.v, z));
-
-                // Eq. theta_proj, signed about the axis: atan2(z.(up x vp), up.vp) = atan2(zxu.vp, up.vp)
-                const float cs = dot(up, vp), sn = dot(zxu, vp);
-                const bool deg = nu2 < 1e-24f || nv2 < 1e-24f || nup2 <= pe2 * nu2 || nvp2 <= pe2 * nv2;
-                float d = deg ? 0.0f : atan2_all(sn, cs);
-                d = clampf(thj + d, lo, hi) - thj;
-                float sh, ch;
-                __sincosf(0.5f * d, &sh, &ch);
-                V3 r = fma3(-2.0f * sh * ch, zxu, fma3(-fmaf(-2.0f * sh, sh, 1.0f), up, r0));
-                const float rp2 = dot(r, r);
-                float w2 = fmaf(qerr.w, ch, sh * az);
-                V3 v2 = fma3(ch, qerr.v, (-sh) * qz);
-                const float op = quat_angle(w2, dot(v2, v2));
-                const float sp = fmaf(rp2, inv_p2, op * op * inv_o2);
-                if (j == 0 || sp < best_p * one_m_tie) {
-                    best_p = sp;
-                    jp = j;
-                    dP = d;
-                }
-
-                // Eq. ori_update: delta(k) sgn(a.z) phi
-                const float sg = (az > 0.0f) ? 1.0f : ((az < 0.0f) ? -1.0f : 0.0f);
-                float dq = delta_k * sg * phi;
-                dq = clampf(thj + dq, lo, hi) - thj;
-                __sincosf(0.5f * dq, &sh, &ch);
-                r = fma3(-2.0f * sh * ch, zxu, fma3(-fmaf(-2.0f * sh, sh, 1.0f), up, r0));
-                const float pq2 = dot(r, r);
-                w2 = fmaf(qerr.w, ch, sh * az);
-                v2 = fma3(ch, qerr.v, (-sh) * qz);
-                const float rq = quat_angle(w2, dot(v2, v2));
-                const float so = fmaf(pq2, inv_p2, rq * rq * inv_o2);
-                if (j == 0 || so < best_o * one_m_tie) {
-                    best_o = so;
-                    jo = j;
-                    dO = dq;
-                }
-                if (TRACE && kk == 0) {
-                    if (A.tr.dp) A.tr.dp[j * A.ld + c] = d;
-                    if (A.tr.rp) A.tr.rp[j * A.ld + c] = sqrtf(rp2);
-                    if (A.tr.op) A.tr.op[j * A.ld + c] = op;
-                    if (A.tr.dq) A.tr.dq[j * A.ld + c] = dq;
-                    if (A.tr.pq) A.tr.pq[j * A.ld + c] = sqrtf(pq2);
-                    if (A.tr.rq) A.tr.rq[j * A.ld + c] = rq;
-                }
-            }
-
-            // apply both; on the same joint the larger step
-            float aP = dP, aO = dO;
-            if (jp == jo) {
-                if (fabsf(dP) >= fabsf(dO)) aO = 0.0f;
-                else aP = 0.0f;
-            }
-            // residual at theta_hat: the distal joint's rotation first, then the proximal one
-            // (the chosen joints' origins and axes are still in the shared-memory column)
-            const float* fp = col.fr(jp);
-            const float* fo = col.fr(jo);
-            const V3 Pp = v3(fp[0 * kCcdThreads], fp[1 * kCcdThreads], fp[2 * kCcdThreads]);
-            const V3 Zp = v3(fp[3 * kCcdThreads], fp[4 * kCcdThreads], fp[5 * kCcdThreads]);
-            const V3 Po = v3(fo[0 * kCcdThreads], fo[1 * kCcdThreads], fo[2 * kCcdThreads]);
-            const V3 Zo = v3(fo[3 * kCcdThreads], fo[4 * kCcdThreads], fo[5 * kCcdThreads]);
-            const bool p_hi = jp > jo;
-            const V3 Pa = p_hi ? Pp : Po, Za = p_hi ? Zp : Zo, Pb = p_hi ? Po : Pp, Zb = p_hi ? Zo : Zp;
-            const float da = p_hi ? aP : aO, db = p_hi ? aO : aP;
-            float sa_, ca_, sb_, cb_;
-            __sincosf(0.5f * da, &sa_, &ca_);
-            __sincosf(0.5f * db, &sb_, &cb_);
-            V3 x = Pa + rotate_half(Za, sa_, ca_, E.p - Pa);
-            x = Pb + rotate_half(Zb, sb_, cb_, x - Pb);
-            Q4 q1 = qmul(qerr, Q4{ca_, (-sa_) * Za});
-            q1 = qmul(q1, Q4{cb_, (-sb_) * Zb});
-            const V3 e1 = pt - x;
-            const float ep1 = sqrtf(dot(e1, e1));
-            const float eo1 = quat_angle(q1.w, dot(q1.v, q1.v));
-            // acceptance (reading: an improvement above gamma in position or in orientation)
-            const bool acc = (ep0 - ep1 > P.cd_gamma_pos) || (eo - eo1 > P.cd_gamma_ori);
-
-            if (TRACE && kk == 0) {
-                if (A.tr.jp) A.tr.jp[c] = jp;
-                if (A.tr.jo) A.tr.jo[c] = jo;
-                if (A.tr.accepted) A.tr.accepted[c] = acc ? 1 : 0;
-                if (A.tr.th_hat) {
-#pragma unroll 1
-                    for (int j = 0; j < n; ++j)
-                        A.tr.th_hat[j * A.ld + c] = col.th(j) + (j == jp ? aP : 0.0f) + (j == jo ? aO : 0.0f);
-                }
-            }
-            if (acc) {
-                col.th(jp) += aP;
-                col.th(jo) += aO;
-            } else {
-                // rejection: theta + N(0, sigma^2 I), kept inside the limits
-#pragma unroll 1
-                for (int b = 0; 2 * b < n; ++b) {
-                    const float2 z = normal_pair(T, (uint32_t)s, kPhaseCd, (uint32_t)k, b);
-                    const int j0 = 2 * b, j1 = 2 * b + 1;
-                    col.th(j0) = clampf(fmaf(P.cd_sigma, z.x, col.th(j0)), R.lo[j0], R.hi[j0]);
-                    if (j1 < n) col.th(j1) = clampf(fmaf(P.cd_sigma, z.y, col.th(j1)), R.lo[j1], R.hi[j1]);
-                }
-            }
+            const int r = ccd_step<TRACE, TH>(R, T, P, col, A, c, (uint32_t)s, kk, cap, delta_k, pt, pe2, one_m_tie,
+                                              inv_p2, inv_o2, ep2, eo);
+            if (r == 1) iters = kk;
+            if (r) break;
             delta_k *= P.cd_rho;
             ++n_it;
         }
@@ -290,6 +305,89 @@ __global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
         if ((threadIdx.x & 31) == 0) {
             atomicAdd(&A.cnt->v[0], n_it);
             atomicAdd(&A.cnt->v[5], n_cand);
+        }
+    }
+}
+
+// cd_variant = 2, the target-wide break: one CTA per target runs all of its
+// seeds in lock-step, iteration by iteration, and stops every seed once any
+// seed passes the coarse test.  Pass kk tests each seed's state after kk
+// updates and writes its update to the other buffer; when some seed passed,
+// the updates of that pass are dropped and every seed keeps its state after
+// kk updates.
+template <int TH>
+__global__ void __launch_bounds__(TH, 4) k_ccd_lock(const CcdArgs A) {
+    extern __shared__ __align__(16) float sm[];
+    __shared__ int any;
+    const RobotParams* rob = stage_robots(sm, A.rs);
+    float* const colbase = sm + robots_smem_bytes(A.rs.n) / sizeof(float) + threadIdx.x;
+    const int t = blockIdx.x;
+    const hjcd_params& P = A.P;
+    const TargetDesc T = A.tg[t];
+    const RobotParams& R = rob[T.robot];
+    const int n = R.n;
+    const ColT<TH> col{colbase, n};
+    const int64_t m0 = A.map.off[t];
+    const int M = (int)(A.map.off[t + 1] - m0);
+    const bool valid = T.eps_pos > 0.0f;
+    const int cap = A.n_iters >= 0 ? A.n_iters : T.cd_iters;
+    const V3 pt = v3(T.p[0], T.p[1], T.p[2]);
+    const float pe2 = P.proj_eps * P.proj_eps, one_m_tie = 1.0f - P.cd_tie;
+    const float inv_p2 = 1.0f / (T.eps_pos * T.eps_pos), inv_o2 = 1.0f / (T.eps_ori * T.eps_ori);
+    float* cur = A.th_out;
+    float* nxt = A.th_tmp;
+    for (int s = threadIdx.x; s < M; s += TH) {
+        const int64_t c = m0 + s;
+        if (A.th_in) {
+            for (int j = 0; j < n; ++j) cur[j * A.ld + c] = A.th_in[j * A.ld + c];
+        } else {
+            sample_seed(R, T, (uint32_t)s, col);
+            for (int j = 0; j < n; ++j) cur[j * A.ld + c] = col.th(j);
+        }
+    }
+    unsigned long long n_it = 0;
+    float delta_k = P.cd_delta0 * powf(P.cd_rho, (float)A.k0);
+    int kk = 0;
+    for (; valid; ++kk) {
+        if (threadIdx.x == 0) any = 0;
+        __syncthreads();
+        for (int s = threadIdx.x; s < M; s += TH) {
+            const int64_t c = m0 + s;
+#pragma unroll 1
+            for (int j = 0; j < n; ++j) col.th(j) = cur[j * A.ld + c];
+            float ep2 = 0.0f, eo = 0.0f;
+            const int r = ccd_step<false, TH>(R, T, P, col, A, c, (uint32_t)s, kk, cap, delta_k, pt, pe2, one_m_tie,
+                                              inv_p2, inv_o2, ep2, eo);
+            const float ep = sqrtf(ep2), a = ep / T.eps_pos, b = eo / T.eps_ori;
+            if (A.score) A.score[c] = fmaf(a, a, b * b);
+            if (A.perr) A.perr[c] = ep;
+            if (A.oerr) A.oerr[c] = eo;
+            if (r == 1) any = 1;
+            if (r == 0) {
+                ++n_it;
+#pragma unroll 1
+                for (int j = 0; j < n; ++j) nxt[j * A.ld + c] = col.th(j);
+            }
+        }
+        __syncthreads();
+        if (any || kk == cap) break;
+        float* sw = cur;
+        cur = nxt;
+        nxt = sw;
+        delta_k *= P.cd_rho;
+    }
+    for (int s = threadIdx.x; s < M; s += TH) {
+        const int64_t c = m0 + s;
+        if (cur != A.th_out)
+            for (int j = 0; j < n; ++j) A.th_out[j * A.ld + c] = cur[j * A.ld + c];
+        if (!valid && A.score) A.score[c] = __int_as_float(0x7f800000);
+        if (A.iters) A.iters[c] = valid ? kk : cap;
+    }
+    if (A.cnt) {
+        n_it = warp_sum(n_it);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&A.cnt->v[0], n_it);
+            if (threadIdx.x == 0) atomicAdd(&A.cnt->v[5], (unsigned long long)M);
         }
     }
 }
@@ -334,6 +432,17 @@ void launch_ccd_b(const CcdArgs& A, cudaStream_t st) {
 
 void launch_ccd(const CcdArgs& A, bool trace, cudaStream_t st) {
     if (A.C <= 0) return;
+    if (A.P.cd_variant == 2) {  // one CTA per target (offset maps only)
+        const size_t smem = robots_smem_bytes(A.rs.n) + sizeof(float) * 7 * A.rs.n_max * 128;
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_ccd_lock<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(robots_smem_bytes(kMaxLaunchRobots) + sizeof(float) * 7 * kMaxDof * 128));
+            attr = true;
+        }
+        k_ccd_lock<128><<<A.map.T, 128, smem, st>>>(A);
+        return;
+    }
     if (trace) launch_ccd_b<true>(A, st);
     else launch_ccd_b<false>(A, st);
 }

@@ -135,6 +135,7 @@ hjcd_status plan_wave(hjcd_ctx* ctx, const WaveItem* items, int n_items, const h
     W.o_inl = cv.take<char>(inl_bytes);
     W.head = cv.off;
     W.o_thM = cv.take<float>((size_t)W.n_max * W.CM);
+    W.o_thM2 = cv.take<float>(P.cd_variant == 2 ? (size_t)W.n_max * W.CM : 0);  // lock-step PO-CCD's second buffer
     W.o_sM = cv.take<float>(W.CM);
     W.o_thB = cv.take<float>((size_t)W.n_max * W.CB);
     W.o_sB = cv.take<float>(W.CB);
@@ -263,6 +264,7 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
     ca.C = W.CM;
     ca.ld = W.CM;
     ca.th_out = thM;
+    ca.th_tmp = reinterpret_cast<float*>(ws + W.o_thM2);
     ca.score = sM;
     ca.n_iters = -1;
     ca.P = P;

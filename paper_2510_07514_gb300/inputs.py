@@ -47,7 +47,7 @@ DEFAULT_PARAMS = dict(
     cd_rho=0.97,
     proj_eps=1e-4,            # projected-vector length (relative) below which Eq. theta_proj gives 0
     cd_tie=1e-4,              # greedy choice: a later joint wins only if its score is lower by this fraction
-    cd_variant=0,             # 0: PO-CCD (Alg. 3); 1: position-only CCD (Alg. 1), a baseline
+    cd_variant=0,             # 0: PO-CCD (Alg. 3); 1: position-only CCD (Alg. 1), a baseline; 2: PO-CCD, target-wide break
     # Top-K and duplication (Alg. 2)
     dup_ratio=4,              # K = max(1, floor(B / dup_ratio))
     dup_sigma=0.02,           # Sigma of the duplication perturbation (rad)

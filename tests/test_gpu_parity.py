@@ -668,3 +668,28 @@ def test_classic_ccd_as_the_initialiser_of_the_whole_method(ctx):
     o = orc.solve(orob, None, orc.make_params(1e-3, 1e-2, seed=9, cd_variant=1), tg, 128, 1)
     succ_o = (o["count"] > 0) & (o["err"][:, 0, 0] <= 1e-3) & (o["err"][:, 0, 1] <= 1e-2)
     assert abs(succ_g.mean() - succ_o.mean()) <= 0.03 + 1e-12
+
+
+def test_target_wide_break_solves_like_the_oracle(ctx):
+    """cd_variant 2 (lock-step PO-CCD per target, all seeds stop at the first
+    convergence) through the whole method: success within 3 points of the
+    oracle on cfg2's robot and scene (80 targets x 256 seeds), every solution
+    re-verified, and a target-wide iteration count no larger than the cap."""
+    wl = inputs.cfg2(80, 256)
+    rob, sc = wl.robot, wl.scene
+    rid, sid = ctx.add_robot(rob), ctx.set_scene(sc)
+    orob, osc = orc.Robot(rob), orc.Scene(sc)
+    tg = _cfg2_targets(ctx, rid, sid, orob, osc, wl, 80)
+    p2 = api.make_params(cd_variant=2)
+    q, err, cnt = ctx.solve(rid, sid, dev(tg), 256, 2, wl.seed, 7, params=p2)
+    q, err, cnt = host(q), host(err), host(cnt).astype(int)
+    succ_g = _verify(orob, osc, rob, tg, q, err, cnt, wl.eps_pos, wl.eps_ori)
+    o = orc.solve(orob, osc, orc.make_params(wl.eps_pos, wl.eps_ori, seed=wl.seed, cd_variant=2), tg, 256, 2)
+    succ_o = (o["count"] > 0) & (o["err"][:, 0, 0] <= wl.eps_pos) & (o["err"][:, 0, 1] <= wl.eps_ori)
+    assert abs(succ_g.mean() - succ_o.mean()) <= 0.03 + 1e-12
+    assert succ_g.mean() > 0.8
+    with pytest.raises(hjcd.HjcdError):  # per-candidate stage entry: not for whole targets
+        C = 8
+        th = torch.zeros((7, C), device="cuda")
+        hjcd.hjcd_po_ccd(ctx.h, rid, 1, dev(tg[:1]), 1e-3, 1e-2, 1, p2, C, dev(np.zeros(C), torch.int32),
+                         dev(np.arange(C), torch.int32), None, th, C, 0, 4)

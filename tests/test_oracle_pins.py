@@ -664,3 +664,30 @@ def test_classic_ccd_reaches_planar_targets_and_respects_limits():
     o2 = orc.po_ccd(rt, P, tg, np.arange(40), np.zeros(40, np.int32))
     assert np.all(o2["theta"] >= -0.3 - 1e-15) and np.all(o2["theta"] <= 0.3 + 1e-15)
     assert np.mean(o2["perr"] > 1e-3) > 0.5  # most of those targets lie outside the reachable set
+
+
+def test_target_wide_break_equals_per_seed_runs_capped_at_the_first_convergence(panda):
+    """cd_variant 2 stops every seed of a target after the first iteration that
+    leaves any of them inside the coarse tolerance.  Seeds do not interact
+    before that, so each seed's result is its own PO-CCD run capped at
+    K* = min over the target's converged seeds of their iteration count
+    (the whole cap when none converges) -- exactly, in double precision."""
+    rng = np.random.default_rng(17)
+    T, S = 6, 40
+    tg = _targets(panda, rng, T)
+    tgt = np.repeat(np.arange(T), S).astype(np.int32)
+    cand = np.tile(np.arange(S), T).astype(np.int32)
+    P0 = orc.make_params(seed=4)
+    full = orc.po_ccd(panda, P0, tg, tgt, cand)
+    conv = (full["perr"] ** 2 < P0.cd_eps_pos2) & (full["oerr"] ** 2 < P0.cd_eps_ori2)
+    brk = orc.po_ccd(panda, orc.make_params(seed=4, cd_variant=2), tg, tgt, cand)
+    n_break = 0
+    for t in range(T):
+        sel = tgt == t
+        ks = full["iters"][sel][conv[sel]]
+        kstar = int(ks.min()) if len(ks) else P0.cd_max_iters
+        n_break += kstar < P0.cd_max_iters
+        capped = orc.po_ccd(panda, orc.make_params(seed=4, cd_max_iters=kstar), tg, tgt[sel], cand[sel])
+        assert np.array_equal(brk["theta"][sel], capped["theta"])
+        assert np.all(brk["iters"][sel] == kstar)
+    assert n_break > 0
