@@ -231,6 +231,31 @@ typedef struct hjcd_tune_report {
 hjcd_status hjcd_autotune(hjcd_ctx* ctx, int n_items, const hjcd_batch_item* items, const hjcd_params* base,
                           float success_tol, int32_t repeats, hjcd_params* tuned, hjcd_tune_report* report);
 
+/* ---- the seeds of a target sharded across devices -------------------------------- */
+
+/* Alg. 2 with each target's M = opts->n_samples seeds split across devices
+ * (one exchange step; the paper runs one device).  Each device runs PO-CCD on
+ * seeds [seed_begin, seed_end) of every target (random streams keyed by the
+ * global seed index) and keeps its K = max(1, floor(M / dup_ratio)) best:
+ * hjcd_shard_topk writes, per target, scores [T][K], seed indices [T][K] (-1
+ * past its seeds) and joint vectors [T][K][n], best first.  The lists of all
+ * shards, gathered in any order, are merged by hjcd_topk_merge (input
+ * [L][T][K] and [L][T][K][n]; output the K best per target, ties to the lower
+ * seed index).  hjcd_solve_from_topk runs the rest of Alg. 2 from the merged
+ * joint vectors [T][K][n] (duplication, PJ-IK, collision filter, ranking):
+ * the results equal hjcd_solve's on the same targets and options, bit for bit.
+ * All arrays are DEVICE memory; targets and options must be the same on every
+ * device; opts->samples_per_target must be NULL; cd_variant 2 is refused. */
+hjcd_status hjcd_shard_topk(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const float* targets_pq,
+                            const hjcd_solve_opts* opts, int32_t seed_begin, int32_t seed_end,
+                            float* out_score, int32_t* out_index, float* out_theta, void* stream);
+hjcd_status hjcd_topk_merge(hjcd_ctx* ctx, int n_targets, int n_lists, int K, int n, const float* in_score,
+                            const int32_t* in_index, const float* in_theta, float* out_score,
+                            int32_t* out_index, float* out_theta, void* stream);
+hjcd_status hjcd_solve_from_topk(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_targets,
+                                 const float* targets_pq, const hjcd_solve_opts* opts, const float* kept_theta,
+                                 float* out_q, float* out_err, int32_t* out_count, void* stream);
+
 /* ---- serving: continuous batching ------------------------------------------ */
 
 /* Serving loop of a context (Sec. I and Sec. VI motivate interactive use; the

@@ -1175,3 +1175,177 @@ extern "C" hjcd_status hjcd_solve_noalloc(hjcd_ctx* ctx, int32_t robot_id, int32
     launch_rank(ra, (int)B, s);
     return after_launch(ctx, collide ? 5 : 4);
 }
+
+// ---- seeds of a target sharded across devices -----------------------------------
+
+namespace {
+
+hjcd_status shard_common(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const float* targets_pq,
+                         const hjcd_solve_opts* opts, RobotRec** rob, hjcd_params* P, int64_t* K) {
+    hjcd_status st;
+    if ((st = check_robot(ctx, robot_id, rob))) return st;
+    if (!opts || n_targets < 1 || pointer_kind(targets_pq) != 1)
+        return fail(ctx, HJCD_EINVAL, "need opts and n_targets >= 1 device target poses");
+    if (opts->samples_per_target) return fail(ctx, HJCD_EINVAL, "sharded solves take a uniform n_samples");
+    if (opts->n_samples < 1 || opts->n_samples > HJCD_MAX_SAMPLES)
+        return fail(ctx, HJCD_EINVAL, "n_samples outside [1, %d]", HJCD_MAX_SAMPLES);
+    if (!(opts->eps_pos > 0.0f) || !(opts->eps_ori > 0.0f)) return fail(ctx, HJCD_EINVAL, "tolerances must be > 0");
+    if (opts->params) *P = *opts->params;
+    else hjcd_default_params(P);
+    if ((st = check_params(ctx, *P))) return st;
+    if (P->cd_variant == 2) return fail(ctx, HJCD_EINVAL, "sharded seeds cannot take the target-wide break");
+    *K = std::max<int64_t>(1, opts->n_samples / P->dup_ratio);
+    return make_current(ctx);
+}
+
+}  // namespace
+
+extern "C" {
+
+hjcd_status hjcd_shard_topk(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const float* targets_pq,
+                            const hjcd_solve_opts* opts, int32_t seed_begin, int32_t seed_end, float* out_score,
+                            int32_t* out_index, float* out_theta, void* stream) {
+    if (!ctx) return HJCD_EINVAL;
+    RobotRec* rob;
+    hjcd_params P;
+    int64_t K;
+    hjcd_status st;
+    if ((st = shard_common(ctx, robot_id, n_targets, targets_pq, opts, &rob, &P, &K))) return st;
+    if (seed_begin < 0 || seed_end <= seed_begin || seed_end > opts->n_samples)
+        return fail(ctx, HJCD_EINVAL, "seed range [%d, %d) outside [0, %d)", seed_begin, seed_end, opts->n_samples);
+    if (pointer_kind(out_score) != 1 || pointer_kind(out_index) != 1 || pointer_kind(out_theta) != 1)
+        return fail(ctx, HJCD_EINVAL, "outputs must be device arrays");
+    const int T = n_targets, n = rob->P.n, Ms = seed_end - seed_begin;
+    const int64_t C = (int64_t)T * Ms;
+    Carve cv;
+    const size_t o_tg = cv.take<TargetDesc>(T), o_off = cv.take<int64_t>(2 * (size_t)(T + 1)),
+                 o_th = cv.take<float>((size_t)n * C), o_s = cv.take<float>(C);
+    if ((st = ensure_ws(ctx, cv.off))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    HJCD_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ws_free, 0));
+    char* W = ctx->ws;
+    TargetDesc* d_tg = reinterpret_cast<TargetDesc*>(W + o_tg);
+    int64_t* d_off = reinterpret_cast<int64_t*>(W + o_off);
+    k_uniform_offsets<<<(T + 256) / 256, 256, 0, s>>>(d_off, d_off + T + 1, T, Ms, Ms);
+    launch_pack_targets(targets_pq, T, nullptr,
+                        stage_template(opts->eps_pos, opts->eps_ori, opts->seed, P.cd_max_iters, P.lm_max_iters, 1, -1),
+                        d_tg, s);
+    CcdArgs ca{};
+    ca.rs = single_robot_set(*rob);
+    ca.tg = d_tg;
+    ca.map = CandMap{nullptr, nullptr, d_off, T};
+    ca.C = C;
+    ca.ld = C;
+    ca.th_out = reinterpret_cast<float*>(W + o_th);
+    ca.score = reinterpret_cast<float*>(W + o_s);
+    ca.n_iters = P.cd_max_iters;
+    ca.P = P;
+    ca.cnt = ctx->cnt;
+    ca.block = ctx->ccd_block;
+    ca.seed_base = seed_begin;
+    launch_ccd(ca, false, s);
+    ShardTopkArgs ta{single_robot_set(*rob), d_tg, T, (int32_t)K, seed_begin, d_off, ca.score, ca.th_out, C,
+                     out_score, out_index, out_theta, n};
+    launch_shard_topk(ta, Ms, s);
+    HJCD_CUDA(ctx, cudaEventRecord(ctx->ws_free, s));
+    return after_launch(ctx, 4);
+}
+
+hjcd_status hjcd_topk_merge(hjcd_ctx* ctx, int n_targets, int n_lists, int K, int n, const float* in_score,
+                            const int32_t* in_index, const float* in_theta, float* out_score, int32_t* out_index,
+                            float* out_theta, void* stream) {
+    if (!ctx) return HJCD_EINVAL;
+    if (n_targets < 1 || n_lists < 1 || K < 1 || n < 1 || n > HJCD_MAX_DOF || (int64_t)n_lists * K > HJCD_MAX_SAMPLES)
+        return fail(ctx, HJCD_EINVAL, "bad merge sizes");
+    if (pointer_kind(in_score) != 1 || pointer_kind(in_index) != 1 || pointer_kind(in_theta) != 1 ||
+        pointer_kind(out_score) != 1 || pointer_kind(out_index) != 1 || pointer_kind(out_theta) != 1)
+        return fail(ctx, HJCD_EINVAL, "merge buffers must be device arrays");
+    hjcd_status st;
+    if ((st = make_current(ctx))) return st;
+    MergeArgs a{n_targets, n_lists, K, n, in_score, in_index, in_theta, out_score, out_index, out_theta};
+    launch_topk_merge(a, (cudaStream_t)stream);
+    return after_launch(ctx, 1);
+}
+
+hjcd_status hjcd_solve_from_topk(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_targets,
+                                 const float* targets_pq, const hjcd_solve_opts* opts, const float* kept_theta,
+                                 float* out_q, float* out_err, int32_t* out_count, void* stream) {
+    if (!ctx) return HJCD_EINVAL;
+    RobotRec* rob;
+    SceneRec* sc;
+    hjcd_params P;
+    int64_t K;
+    hjcd_status st;
+    if ((st = shard_common(ctx, robot_id, n_targets, targets_pq, opts, &rob, &P, &K))) return st;
+    if ((st = check_scene(ctx, scene_id, &sc))) return st;
+    if (opts->top_k < 1 || opts->top_k > HJCD_MAX_TOPK) return fail(ctx, HJCD_EINVAL, "top_k outside [1, %d]", HJCD_MAX_TOPK);
+    if (pointer_kind(kept_theta) != 1 || pointer_kind(out_q) != 1 || pointer_kind(out_err) != 1 ||
+        pointer_kind(out_count) != 1)
+        return fail(ctx, HJCD_EINVAL, "kept_theta and the outputs must be device arrays");
+    const int T = n_targets, top_k = opts->top_k;
+    const int64_t B = dup_count(opts->n_samples, P.dup_ratio), CB = (int64_t)T * B;
+    Carve cv;
+    const size_t o_tg = cv.take<TargetDesc>(T), o_off = cv.take<int64_t>(2 * (size_t)(T + 1)),
+                 o_th = cv.take<float>((size_t)rob->P.n * CB), o_sB = cv.take<float>(CB), o_pB = cv.take<float>(CB),
+                 o_oB = cv.take<float>(CB), o_hB = cv.take<uint8_t>(CB), o_q = cv.take<unsigned long long>(2);
+    if ((st = ensure_ws(ctx, cv.off))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    HJCD_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ws_free, 0));
+    char* W = ctx->ws;
+    TargetDesc* d_tg = reinterpret_cast<TargetDesc*>(W + o_tg);
+    int64_t* d_boff = reinterpret_cast<int64_t*>(W + o_off);
+    float* thB = reinterpret_cast<float*>(W + o_th);
+    float* sB = reinterpret_cast<float*>(W + o_sB);
+    float* pB = reinterpret_cast<float*>(W + o_pB);
+    float* oB = reinterpret_cast<float*>(W + o_oB);
+    uint8_t* hB = reinterpret_cast<uint8_t*>(W + o_hB);
+    unsigned long long* queue = reinterpret_cast<unsigned long long*>(W + o_q);
+    HJCD_CUDA(ctx, cudaMemsetAsync(queue, 0, 16, s));
+    HJCD_CUDA(ctx, cudaMemsetAsync(out_q, 0xff, sizeof(float) * (size_t)T * top_k * rob->P.n, s));
+    HJCD_CUDA(ctx, cudaMemsetAsync(out_err, 0xff, sizeof(float) * (size_t)T * top_k * 2, s));
+    k_uniform_offsets<<<(T + 256) / 256, 256, 0, s>>>(d_boff + T + 1, d_boff, T, B, B);
+    launch_pack_targets(targets_pq, T, nullptr,
+                        stage_template(opts->eps_pos, opts->eps_ori, opts->seed, P.cd_max_iters, P.lm_max_iters,
+                                       top_k, sc ? 0 : -1),
+                        d_tg, s);
+    const RobotSet rs = single_robot_set(*rob);
+    KeptDupArgs da{rs, d_tg, T, (int32_t)K, kept_theta, d_boff, thB, CB, P.dup_sigma};
+    launch_dup_kept(da, s);
+    LmArgs la{};
+    la.rs = rs;
+    la.tg = d_tg;
+    la.map = CandMap{nullptr, nullptr, d_boff, T};
+    la.C = CB;
+    la.ld = CB;
+    la.th = thB;
+    la.score = sB;
+    la.perr = pB;
+    la.oerr = oB;
+    la.n_iters = -1;
+    la.P = P;
+    la.cnt = ctx->cnt;
+    la.queue = queue;
+    la.warps = ctx->lm_warps;
+    launch_lm(la, false, s);
+    const bool collide = rob->P.n_sph > 0;
+    if (collide) {
+        CollideArgs cl{};
+        collide_uniform(cl, *rob, sc);
+        cl.tg = d_tg;
+        cl.map = CandMap{nullptr, nullptr, d_boff, T};
+        cl.C = CB;
+        cl.ld = CB;
+        cl.th = thB;
+        cl.hit = hB;
+        cl.cnt = ctx->cnt;
+        cl.err_flag = reinterpret_cast<int32_t*>(queue + 1);
+        launch_collide(cl, s);
+    }
+    RankArgs ra{rs, d_tg, T, d_boff, thB, CB, sB, pB, oB, collide ? hB : nullptr, top_k, nullptr,
+                out_q, out_err, out_count};
+    launch_rank(ra, (int)B, s);
+    HJCD_CUDA(ctx, cudaEventRecord(ctx->ws_free, s));
+    return after_launch(ctx, collide ? 6 : 5);
+}
+
+}  // extern "C"

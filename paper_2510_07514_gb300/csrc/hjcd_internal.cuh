@@ -411,6 +411,7 @@ struct CcdArgs {
     hjcd_ccd_trace tr;
     Counters* cnt;
     int32_t block;  // threads (candidates) per CTA: 64, 128 (default, also for 0) or 256
+    int32_t seed_base;  // added to each candidate's index inside its target (a shard of the seeds)
 };
 
 struct LmArgs {
@@ -496,6 +497,52 @@ struct CollideArgs {
 // Fill p and q of the target rows from [T][7] poses (quaternion normalised; a
 // zero or non-finite one marks the row invalid with eps_pos = -1).  With meta
 // non-null the other fields come from meta[t], else from tmpl with t_local = t.
+// Per target t: the K = max(1, floor(M_full / ratio)) lowest scores of its
+// candidates [off[t], off[t+1]) (ties to the lower index), written as score,
+// seed index (seed_base + index in the target) and joint vector; +inf / -1
+// past the candidates.  out_th [T][K][ld_n], out_s / out_i [T][K].
+struct ShardTopkArgs {
+    RobotSet rs;
+    const TargetDesc* tg;
+    int32_t T, K, seed_base;
+    const int64_t* off;
+    const float* score;
+    const float* th;
+    int64_t ld;
+    float* out_s;
+    int32_t* out_i;
+    float* out_th;
+    int32_t ld_n;
+};
+void launch_shard_topk(const ShardTopkArgs& A, int max_m, cudaStream_t st);
+
+// Per target: the K best of L lists of K (score, seed index, joint vector),
+// ties to the lower seed index.
+struct MergeArgs {
+    int32_t T, L, K, n;
+    const float* in_s;   // [L][T][K]
+    const int32_t* in_i; // [L][T][K]
+    const float* in_th;  // [L][T][K][n]
+    float* out_s;
+    int32_t* out_i;
+    float* out_th;       // [T][K][n]
+};
+void launch_topk_merge(const MergeArgs& A, cudaStream_t st);
+
+// Alg. 2's duplication from kept seeds given per target ([T][K][n], best first):
+// copy r of seed i at index r K + i, perturbed as in k_topk_dup.
+struct KeptDupArgs {
+    RobotSet rs;
+    const TargetDesc* tg;
+    int32_t T, K;
+    const float* kept;   // [T][K][n]
+    const int64_t* b_off;
+    float* th_B;
+    int64_t ld_B;
+    float sigma;
+};
+void launch_dup_kept(const KeptDupArgs& A, cudaStream_t st);
+
 void launch_pack_targets(const float* pq7, int T, const TargetDesc* meta, const TargetDesc& tmpl, TargetDesc* out,
                          cudaStream_t st);
 void launch_fk(const RobotParams& R, int64_t C, const float* th, int64_t ld, float* out, cudaStream_t st);

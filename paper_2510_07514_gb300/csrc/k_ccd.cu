@@ -256,6 +256,7 @@ __global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
          c += (int64_t)gridDim.x * blockDim.x) {
         int32_t t, s;
         if (!A.map.lookup(c, t, s)) continue;
+        s += A.seed_base;
         const TargetDesc T = A.tg[t];
         const RobotParams& R = rob[T.robot];
         const int n = R.n;

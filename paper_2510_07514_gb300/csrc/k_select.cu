@@ -139,6 +139,95 @@ __global__ void __launch_bounds__(kSelThreads) k_rank(const RankArgs A) {
     if (threadIdx.x == 0) A.out_count[t] = count;
 }
 
+__global__ void __launch_bounds__(kSelThreads) k_shard_topk(const ShardTopkArgs A) {
+    extern __shared__ uint64_t keys[];
+    const int t = blockIdx.x;
+    const int64_t m0 = A.off[t];
+    const int M = (int)(A.off[t + 1] - m0);
+    const int N = pow2_at_least(M > 0 ? M : 1);
+    for (int i = threadIdx.x; i < N; i += blockDim.x)
+        keys[i] = i < M ? score_key(A.score[m0 + i], (uint32_t)i) : kNoKey;
+    __syncthreads();
+    bitonic_sort(keys, N);
+    const int n = A.rs.rp[A.tg[t].robot].n;
+    for (int q = threadIdx.x; q < A.K * (n + 2); q += blockDim.x) {
+        const int r = q / (n + 2), j = q % (n + 2);
+        const uint64_t key = r < N ? keys[r] : kNoKey;
+        const bool ok = r < M && key != kNoKey;
+        const uint32_t src = (uint32_t)(key & 0xffffffffu);
+        const int64_t o = (int64_t)t * A.K + r;
+        if (j < n) A.out_th[o * A.ld_n + j] = ok ? A.th[j * A.ld + m0 + src] : 0.0f;
+        else if (j == n) A.out_s[o] = ok ? A.score[m0 + src] : __int_as_float(0x7f800000);
+        else A.out_i[o] = ok ? A.seed_base + (int32_t)src : -1;
+    }
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_topk_merge(const MergeArgs A) {
+    extern __shared__ uint64_t keys[];
+    const int t = blockIdx.x;
+    const int LK = A.L * A.K;
+    const int N = pow2_at_least(LK);
+    // key: score bits, then the seed index (ties to the lower index); the list slot is found again below
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        uint64_t k = kNoKey;
+        if (i < LK) {
+            const int l = i / A.K, r = i % A.K;
+            const int64_t e = ((int64_t)l * A.T + t) * A.K + r;
+            const int32_t idx = A.in_i[e];
+            if (idx >= 0) k = score_key(A.in_s[e], (uint32_t)idx);
+        }
+        keys[i] = k;
+    }
+    __syncthreads();
+    bitonic_sort(keys, N);
+    // the i-th best: locate its list entry (seed indices are unique within a target)
+    for (int r = threadIdx.x; r < A.K; r += blockDim.x) {
+        const uint64_t key = keys[r];
+        const int64_t o = (int64_t)t * A.K + r;
+        if (key == kNoKey) {
+            A.out_s[o] = __int_as_float(0x7f800000);
+            A.out_i[o] = -1;
+            for (int j = 0; j < A.n; ++j) A.out_th[o * A.n + j] = 0.0f;
+            continue;
+        }
+        const int32_t idx = (int32_t)(key & 0xffffffffu);
+        int64_t e = -1;
+        for (int l = 0; l < A.L && e < 0; ++l)
+            for (int q = 0; q < A.K; ++q) {
+                const int64_t f = ((int64_t)l * A.T + t) * A.K + q;
+                if (A.in_i[f] == idx) {
+                    e = f;
+                    break;
+                }
+            }
+        A.out_s[o] = A.in_s[e];
+        A.out_i[o] = idx;
+        for (int j = 0; j < A.n; ++j) A.out_th[o * A.n + j] = A.in_th[e * A.n + j];
+    }
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_dup_kept(const KeptDupArgs A) {
+    const int t = blockIdx.x;
+    const int64_t b0 = A.b_off[t];
+    const int B = (int)(A.b_off[t + 1] - b0);
+    const TargetDesc T = A.tg[t];
+    const RobotParams& R = A.rs.rp[T.robot];
+    const int n = R.n;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        const int i = b % A.K;  // copy r = b / K of kept seed i
+        const float* src = A.kept + ((int64_t)t * A.K + i) * n;
+#pragma unroll 1
+        for (int q = 0; 2 * q < n; ++q) {
+            const float2 z = normal_pair(T, (uint32_t)b, kPhaseDup, 0, q);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = 2 * q + h;
+                if (j < n) A.th_B[j * A.ld_B + b0 + b] = clampf(fmaf(A.sigma, h ? z.y : z.x, src[j]), R.lo[j], R.hi[j]);
+            }
+        }
+    }
+}
+
 __global__ void k_pack_targets(const float* pq7, int T, const TargetDesc* meta, const TargetDesc tmpl,
                                TargetDesc* out) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -191,6 +280,25 @@ void launch_rank(const RankArgs& A, int max_b, cudaStream_t st) {
     const int sm = smem_for(max_b > 0 ? max_b : 1);
     allow_smem(k_rank, sm);
     k_rank<<<A.T, kSelThreads, sm, st>>>(A);
+}
+
+void launch_shard_topk(const ShardTopkArgs& A, int max_m, cudaStream_t st) {
+    if (A.T <= 0) return;
+    const int sm = smem_for(max_m > 0 ? max_m : 1);
+    allow_smem(k_shard_topk, sm);
+    k_shard_topk<<<A.T, kSelThreads, sm, st>>>(A);
+}
+
+void launch_topk_merge(const MergeArgs& A, cudaStream_t st) {
+    if (A.T <= 0 || A.L <= 0 || A.K <= 0) return;
+    const int sm = smem_for(A.L * A.K);
+    allow_smem(k_topk_merge, sm);
+    k_topk_merge<<<A.T, kSelThreads, sm, st>>>(A);
+}
+
+void launch_dup_kept(const KeptDupArgs& A, cudaStream_t st) {
+    if (A.T <= 0) return;
+    k_dup_kept<<<A.T, kSelThreads, 0, st>>>(A);
 }
 
 void launch_pack_targets(const float* pq7, int T, const TargetDesc* meta, const TargetDesc& tmpl, TargetDesc* out,

@@ -36,6 +36,7 @@ EXPORTS = (
     "hjcd_server_start", "hjcd_server_stop", "hjcd_submit", "hjcd_poll", "hjcd_wait",
     "hjcd_graph_create", "hjcd_graph_launch", "hjcd_graph_check", "hjcd_graph_destroy",
     "hjcd_set_launch_config", "hjcd_autotune", "hjcd_set_memory_budget", "hjcd_scene_contacts",
+    "hjcd_shard_topk", "hjcd_topk_merge", "hjcd_solve_from_topk",
 )
 
 
@@ -124,6 +125,9 @@ _SIGS = {
     "hjcd_set_launch_config": (_ST, [_V, _I32, _I32]),
     "hjcd_set_memory_budget": (_ST, [_V, _U64]),
     "hjcd_scene_contacts": (_ST, [_V, _I32, _I32, _I64, _V, _I64, _V, _V]),
+    "hjcd_shard_topk": (_ST, [_V, _I32, _I, _V, ct.POINTER(hjcd_solve_opts), _I32, _I32, _V, _V, _V, _V]),
+    "hjcd_topk_merge": (_ST, [_V, _I, _I, _I, _I, _V, _V, _V, _V, _V, _V, _V]),
+    "hjcd_solve_from_topk": (_ST, [_V, _I32, _I32, _I, _V, ct.POINTER(hjcd_solve_opts), _V, _V, _V, _V, _V]),
     "hjcd_autotune": (_ST, [_V, _I, ct.POINTER(hjcd_batch_item), ct.POINTER(hjcd_params), _F, _I32,
                             ct.POINTER(hjcd_params), ct.POINTER(hjcd_tune_report)]),
     "hjcd_graph_create": (_ST, [_V, _I, ct.POINTER(hjcd_batch_item), ct.POINTER(hjcd_params), ct.POINTER(_V)]),
@@ -276,6 +280,27 @@ def hjcd_solve_batch(ctx, items, params=None, stream=None) -> None:
 def hjcd_scene_contacts(ctx, robot_id, scene_id, n_cand, theta, ld, touched, stream=None) -> None:
     _check(ctx, load().hjcd_scene_contacts(ctx, int(robot_id), int(scene_id), int(n_cand), ptr(theta), int(ld),
                                            ptr(touched), stream_handle(stream)))
+
+
+def hjcd_shard_topk(ctx, robot_id, n_targets, targets_pq, opts, seed_begin, seed_end, out_score, out_index,
+                    out_theta, stream=None) -> None:
+    _check(ctx, load().hjcd_shard_topk(ctx, int(robot_id), int(n_targets), ptr(targets_pq), ct.byref(opts),
+                                       int(seed_begin), int(seed_end), ptr(out_score), ptr(out_index), ptr(out_theta),
+                                       stream_handle(stream)))
+
+
+def hjcd_topk_merge(ctx, n_targets, n_lists, K, n, in_score, in_index, in_theta, out_score, out_index, out_theta,
+                    stream=None) -> None:
+    _check(ctx, load().hjcd_topk_merge(ctx, int(n_targets), int(n_lists), int(K), int(n), ptr(in_score),
+                                       ptr(in_index), ptr(in_theta), ptr(out_score), ptr(out_index), ptr(out_theta),
+                                       stream_handle(stream)))
+
+
+def hjcd_solve_from_topk(ctx, robot_id, scene_id, n_targets, targets_pq, opts, kept_theta, out_q, out_err,
+                         out_count, stream=None) -> None:
+    _check(ctx, load().hjcd_solve_from_topk(ctx, int(robot_id), int(scene_id), int(n_targets), ptr(targets_pq),
+                                            ct.byref(opts), ptr(kept_theta), ptr(out_q), ptr(out_err),
+                                            ptr(out_count), stream_handle(stream)))
 
 
 def hjcd_set_memory_budget(ctx, nbytes: int) -> None:
