@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
     int lb[SPL];
     float4 lco = make_float4(0.f, 0.f, 0.f, 0.f);
     int cur = -1, n_m = 0, pairs_m = 0;  // robot of a mixed launch: DoF, checked pairs
+    unsigned bmask = 0;                  // its bodies that carry spheres (bit per body, n + 2 <= 26)
 
     unsigned long long tests = 0, btests = 0, ncand = 0;
     const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
@@ -216,6 +217,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
             for (int i = lane; i < nbr; i += 32) wrange[i] = __ldg(rd.range + i);
             for (int i = lane; i < pairs_m; i += 32) wpairs[i] = __ldg(rd.pairs + i);
             __syncwarp();
+            bmask = __ballot_sync(0xffffffffu, lane < nbr && wrange[lane].y > 0);  // bodies with spheres
         }
         const RobotParams& R = rob[rid];
         const int n = UNIFORM ? A.u_n : n_m, nb = n + 2, n_pairs = UNIFORM ? A.u_pairs : pairs_m;
@@ -331,19 +333,26 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
             }
         }
 
-        // obstacle spheres: 32 obstacles at a time, one body at a time
+        // obstacle spheres, 32 at a time: each lane tests its obstacle against every body's
+        // bounding sphere (a bit per body); only bodies some obstacle overlaps are visited, their
+        // overlapping obstacles compacted and the fine tests spread over the warp
+        const int nbs = __popc(bmask);
         for (int o0 = 0; o0 < n_osph && !hit && !(GRID && gcell); o0 += 32) {
             const int o = o0 + lane;
             const bool valid = o < n_osph;
             const float4 s = valid ? ld_obj<STAGED>(obj, o) : make_float4(0.f, 0.f, 0.f, 0.f);
-            const int nvalid = min(32, n_osph - o0);
-            for (int b = 0; b < nb && !hit; ++b) {
+            unsigned bm = 0;
+            if (valid)
+                for (unsigned bb = bmask; bb; bb &= bb - 1u) {
+                    const int b = __ffs(bb) - 1;
+                    if (sph_sph(wco[b], s)) bm |= 1u << b;
+                }
+            t_s += (unsigned long long)min(32, n_osph - o0) * nbs;
+            for (unsigned todo = __reduce_or_sync(0xffffffffu, bm); todo && !hit; todo &= todo - 1u) {
+                const int b = __ffs(todo) - 1;
                 const int2 rg = wrange[b];
-                if (rg.y == 0) continue;
-                const bool ch = valid && sph_sph(wco[b], s);
-                t_s += (unsigned long long)nvalid;
+                const bool ch = (bm >> b) & 1u;
                 const unsigned m = __ballot_sync(0xffffffffu, ch);
-                if (!m) continue;
                 if (ch) list[__popc(m & lt)] = o;
                 __syncwarp();
                 const int items = __popc(m) * rg.y;
@@ -358,21 +367,25 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
             }
         }
 
-        // obstacle boxes
+        // obstacle boxes, the same way
         const float4* box = obj + n_osph;
         for (int o0 = 0; o0 < n_obox && !hit; o0 += 32) {
             const int o = o0 + lane;
             const bool valid = o < n_obox;
             const float4 lo = valid ? ld_obj<STAGED>(box, 2 * o) : make_float4(0.f, 0.f, 0.f, 0.f);
             const float4 hi = valid ? ld_obj<STAGED>(box, 2 * o + 1) : lo;
-            const int nvalid = min(32, n_obox - o0);
-            for (int b = 0; b < nb && !hit; ++b) {
+            unsigned bm = 0;
+            if (valid)
+                for (unsigned bb = bmask; bb; bb &= bb - 1u) {
+                    const int b = __ffs(bb) - 1;
+                    if (sph_box(wco[b], lo, hi)) bm |= 1u << b;
+                }
+            t_b += (unsigned long long)min(32, n_obox - o0) * nbs;
+            for (unsigned todo = __reduce_or_sync(0xffffffffu, bm); todo && !hit; todo &= todo - 1u) {
+                const int b = __ffs(todo) - 1;
                 const int2 rg = wrange[b];
-                if (rg.y == 0) continue;
-                const bool ch = valid && sph_box(wco[b], lo, hi);
-                t_b += (unsigned long long)nvalid;
+                const bool ch = (bm >> b) & 1u;
                 const unsigned m = __ballot_sync(0xffffffffu, ch);
-                if (!m) continue;
                 if (ch) list[__popc(m & lt)] = o;
                 __syncwarp();
                 const int items = __popc(m) * rg.y;
