@@ -53,11 +53,13 @@ __device__ __forceinline__ void sample_seed(const RobotParams& R, const TargetDe
 // then the update of Alg. 3 (or Alg. 1 with cd_variant = 1) of the joint
 // vector in the column.  Returns 1 when the candidate has converged, 2 at the
 // cap (no update in either case), 0 after an update.
+constexpr int kSlotWords = 8;  // per-thread shared-memory slot of the cooperative perturbation
+
 template <bool TRACE, int TH>
-__device__ __forceinline__ int ccd_step(const RobotParams& R, const TargetDesc& T, const hjcd_params& P,
-                                        const ColT<TH>& col, const CcdArgs& A, int64_t c, uint32_t s, int kk, int cap,
-                                        float delta_k, const V3 pt, float pe2, float one_m_tie, float inv_p2,
-                                        float inv_o2, float& ep2, float& eo) {
+__device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParams& R, const TargetDesc& T,
+                                        const hjcd_params& P, const ColT<TH>& col, uint32_t* slots, const CcdArgs& A,
+                                        int64_t c, uint32_t s, int kk, int cap, float delta_k, const V3 pt, float pe2,
+                                        float one_m_tie, float inv_p2, float inv_o2, float& ep2, float& eo) {
     constexpr int kCcdThreads = TH;
     const int n = R.n;
     // kinematics with frames
@@ -227,15 +229,45 @@ __device__ __forceinline__ int ccd_step(const RobotParams& R, const TargetDesc& 
     if (acc) {
         col.th(jp) += aP;
         col.th(jo) += aO;
-    } else {
-        // rejection: theta + N(0, sigma^2 I), kept inside the limits
-#pragma unroll 1
-        for (int b = 0; 2 * b < n; ++b) {
-            const float2 z = normal_pair(T, (uint32_t)s, kPhaseCd, (uint32_t)k, b);
-            const int j0 = 2 * b, j1 = 2 * b + 1;
-            col.th(j0) = clampf(fmaf(P.cd_sigma, z.x, col.th(j0)), R.lo[j0], R.hi[j0]);
-            if (j1 < n) col.th(j1) = clampf(fmaf(P.cd_sigma, z.y, col.th(j1)), R.lo[j1], R.hi[j1]);
+    }
+    // rejection: theta + N(0, sigma^2 I), kept inside the limits.  Few lanes reject at a time,
+    // so the lanes executing here together share the work: each rejected lane publishes its
+    // stream (key, target index, candidate, iteration) and robot, and the (lane, normal pair)
+    // items are spread over all of them; every joint column lives in shared memory.
+    const unsigned am = __activemask();
+    const unsigned rej = __ballot_sync(am, !acc);
+    if (rej) {
+        const int lane = threadIdx.x & 31;
+        uint32_t* const slot = slots + (threadIdx.x & ~31u) * kSlotWords;  // this warp's slots
+        if (!acc) {
+            uint32_t* me = slot + lane * kSlotWords;
+            me[0] = T.key[0];
+            me[1] = T.key[1];
+            me[2] = (uint32_t)T.t_local;
+            me[3] = s;
+            me[4] = (uint32_t)k;
+            me[5] = (uint32_t)T.robot;
         }
+        const int NB = (int)__reduce_max_sync(am, acc ? 0u : (uint32_t)((n + 1) / 2));
+        __syncwarp(am);
+        const int items = __popc(rej) * NB, step = __popc(am);
+        for (int w = __popc(am & ((1u << lane) - 1u)); w < items; w += step) {
+            const int r = w / NB, b = w - r * NB;
+            const int sl = __fns(rej, 0, r + 1);
+            const uint32_t* q = slot + sl * kSlotWords;
+            const RobotParams& Rs = rob[q[5]];
+            if (2 * b >= Rs.n) continue;
+            TargetDesc Tq;
+            Tq.key[0] = q[0];
+            Tq.key[1] = q[1];
+            Tq.t_local = (int32_t)q[2];
+            const float2 z = normal_pair(Tq, q[3], kPhaseCd, q[4], b);
+            const ColT<TH> cs{col.base - lane + sl, Rs.n};
+            const int j0 = 2 * b, j1 = 2 * b + 1;
+            cs.th(j0) = clampf(fmaf(P.cd_sigma, z.x, cs.th(j0)), Rs.lo[j0], Rs.hi[j0]);
+            if (j1 < Rs.n) cs.th(j1) = clampf(fmaf(P.cd_sigma, z.y, cs.th(j1)), Rs.lo[j1], Rs.hi[j1]);
+        }
+        __syncwarp(am);
     }
     return 0;
 }
@@ -246,7 +278,8 @@ __global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
     constexpr int kCcdThreads = TH;
     extern __shared__ __align__(16) float sm[];
     const RobotParams* rob = stage_robots(sm, A.rs);
-    float* const colbase = sm + robots_smem_bytes(A.rs.n) / sizeof(float) + threadIdx.x;
+    uint32_t* const slots = reinterpret_cast<uint32_t*>(sm + robots_smem_bytes(A.rs.n) / sizeof(float));
+    float* const colbase = sm + robots_smem_bytes(A.rs.n) / sizeof(float) + TH * kSlotWords + threadIdx.x;
     const hjcd_params& P = A.P;
     const float pe2 = P.proj_eps * P.proj_eps;
     const float one_m_tie = 1.0f - P.cd_tie;
@@ -279,8 +312,8 @@ __global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
         const bool valid = T.eps_pos > 0.0f;
 
         for (int kk = 0; valid; ++kk) {
-            const int r = ccd_step<TRACE, TH>(R, T, P, col, A, c, (uint32_t)s, kk, cap, delta_k, pt, pe2, one_m_tie,
-                                              inv_p2, inv_o2, ep2, eo);
+            const int r = ccd_step<TRACE, TH>(rob, R, T, P, col, slots, A, c, (uint32_t)s, kk, cap, delta_k, pt, pe2,
+                                              one_m_tie, inv_p2, inv_o2, ep2, eo);
             if (r == 1) iters = kk;
             if (r) break;
             delta_k *= P.cd_rho;
@@ -321,7 +354,8 @@ __global__ void __launch_bounds__(TH, 4) k_ccd_lock(const CcdArgs A) {
     extern __shared__ __align__(16) float sm[];
     __shared__ int any;
     const RobotParams* rob = stage_robots(sm, A.rs);
-    float* const colbase = sm + robots_smem_bytes(A.rs.n) / sizeof(float) + threadIdx.x;
+    uint32_t* const slots = reinterpret_cast<uint32_t*>(sm + robots_smem_bytes(A.rs.n) / sizeof(float));
+    float* const colbase = sm + robots_smem_bytes(A.rs.n) / sizeof(float) + TH * kSlotWords + threadIdx.x;
     const int t = blockIdx.x;
     const hjcd_params& P = A.P;
     const TargetDesc T = A.tg[t];
@@ -357,8 +391,8 @@ __global__ void __launch_bounds__(TH, 4) k_ccd_lock(const CcdArgs A) {
 #pragma unroll 1
             for (int j = 0; j < n; ++j) col.th(j) = cur[j * A.ld + c];
             float ep2 = 0.0f, eo = 0.0f;
-            const int r = ccd_step<false, TH>(R, T, P, col, A, c, (uint32_t)s, kk, cap, delta_k, pt, pe2, one_m_tie,
-                                              inv_p2, inv_o2, ep2, eo);
+            const int r = ccd_step<false, TH>(rob, R, T, P, col, slots, A, c, (uint32_t)s, kk, cap, delta_k, pt, pe2,
+                                              one_m_tie, inv_p2, inv_o2, ep2, eo);
             const float ep = sqrtf(ep2), a = ep / T.eps_pos, b = eo / T.eps_ori;
             if (A.score) A.score[c] = fmaf(a, a, b * b);
             if (A.perr) A.perr[c] = ep;
@@ -412,11 +446,11 @@ __global__ void __launch_bounds__(kCcdThreads) k_sample(const RobotParams R, uin
 
 template <bool TRACE, int TH>
 void launch_ccd_t(const CcdArgs& A, cudaStream_t st) {
-    const size_t smem = robots_smem_bytes(A.rs.n) + sizeof(float) * 7 * A.rs.n_max * TH;
+    const size_t smem = robots_smem_bytes(A.rs.n) + sizeof(float) * (7 * A.rs.n_max + kSlotWords) * TH;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_ccd<TRACE, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(robots_smem_bytes(kMaxLaunchRobots) + sizeof(float) * 7 * kMaxDof * TH));
+                             (int)(robots_smem_bytes(kMaxLaunchRobots) + sizeof(float) * (7 * kMaxDof + kSlotWords) * TH));
         attr = true;
     }
     k_ccd<TRACE, TH><<<grid_for(A.C, TH, 16 * 128 / TH), TH, smem, st>>>(A);
@@ -434,11 +468,11 @@ void launch_ccd_b(const CcdArgs& A, cudaStream_t st) {
 void launch_ccd(const CcdArgs& A, bool trace, cudaStream_t st) {
     if (A.C <= 0) return;
     if (A.P.cd_variant == 2) {  // one CTA per target (offset maps only)
-        const size_t smem = robots_smem_bytes(A.rs.n) + sizeof(float) * 7 * A.rs.n_max * 128;
+        const size_t smem = robots_smem_bytes(A.rs.n) + sizeof(float) * (7 * A.rs.n_max + kSlotWords) * 128;
         static bool attr = false;
         if (!attr) {
             cudaFuncSetAttribute(k_ccd_lock<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(robots_smem_bytes(kMaxLaunchRobots) + sizeof(float) * 7 * kMaxDof * 128));
+                                 (int)(robots_smem_bytes(kMaxLaunchRobots) + sizeof(float) * (7 * kMaxDof + kSlotWords) * 128));
             attr = true;
         }
         k_ccd_lock<128><<<A.map.T, 128, smem, st>>>(A);
