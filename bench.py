@@ -40,7 +40,7 @@ DATA = "synthetic: seeded generators (no datasets or trained weights involved)"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("hjcd", "reference"), default="hjcd")
     ap.add_argument("--targets", type=int, default=1000)
@@ -52,10 +52,12 @@ def parse():
     ap.add_argument("--large-steps", type=int, default=2,
                     help="timed steps of the large case, 10000 targets x 4096 seeds (0: skip)")
     ap.add_argument("--large-budget-gb", type=float, default=2.0, help="workspace budget of the large case (waves)")
+    ap.add_argument("--large-targets", type=int, default=10000, help="targets of the large case (profiling: fewer)")
     ap.add_argument("--dof-scaling", type=int, default=1, help="run the 7/12/18/24-DoF leg (0: skip)")
     ap.add_argument("--ccd-baseline", type=int, default=1,
                     help="also time the main workload with the position-only CCD initialiser (0: skip)")
     ap.add_argument("--tracking-frames", type=int, default=200, help="frames of the tracking loop (0: skip)")
+    ap.add_argument("--latency", type=int, default=1, help="single-target latency leg (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="length of the served Poisson trace at 2000 req/s (0: skip the serving comparison)")
     return ap.parse_args()
@@ -115,12 +117,17 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        # nvidia-smi takes a moment to start: the timed region begins after its first sample
+        t0 = time.perf_counter()
+        while not self.lines and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.01)
+        self.lines.clear()
 
     def _read(self):
         for ln in self.proc.stdout:
@@ -376,7 +383,7 @@ def large_leg(ctx, args, dev, stream):
     contact query) around the target configurations; memory-admitted waves."""
     import torch
     from paper_2510_07514_gb300 import hjcd, inputs
-    wl = inputs.cfg5()
+    wl = inputs.cfg5(n_targets=args.large_targets)
     rob = wl.robot
     rid = ctx.add_robot(rob)
     pool = torch.as_tensor(np.ascontiguousarray(wl.target_pool.T), dtype=torch.float32, device=dev)
@@ -513,6 +520,44 @@ def tracking_leg(ctx, args, dev):
     res["workload"] = ("Panda + 60 link spheres, 24 obstacle spheres moving every frame, target on a 0.12 m circle, "
                        "1 target x 1000 seeds per frame")
     return res
+
+
+PAPER_CONTEXT = {
+    "hardware": "NVIDIA GeForce RTX 4060 laptop GPU (sm_89), per the paper; other hardware, context only",
+    "ms_per_solve_B1000": {"panda_open_world": 4.22, "panda_box_panda_collision_free": 5.04,
+                           "dof_7": 4.25, "dof_12": 4.55, "dof_18": 4.62, "dof_24": 4.66},
+    "note": "the paper reports wall time per solve (one target, B polished seeds); no throughput",
+}
+
+
+def latency_leg(ctx, args, dev):
+    """One target, 1000 seeds, top-1, end to end through hjcd_solve with pinned
+    host buffers (the paper's per-solve timing shape): the Panda in the open
+    world, and the Panda with 60 link spheres in the main workload's scene."""
+    import torch
+    from paper_2510_07514_gb300 import inputs
+    wl = inputs.cfg2(64, 1000)
+    out = {}
+    for name, rob, scene in (("panda_open_world", inputs.panda(), None),
+                             ("panda_spheres_in_scene", wl.robot, wl.scene)):
+        rid = ctx.add_robot(rob)
+        sid = ctx.set_scene(scene) if scene is not None else -1
+        tg, got, _ = collision_free_targets(ctx, rid, sid, rob, wl.theta_gen[:2000], 64, dev)
+        tg_h = tg.cpu().pin_memory()
+        h1 = (torch.empty((1, 1, 7)).pin_memory(), torch.empty((1, 1, 2)).pin_memory(),
+              torch.empty((1,), dtype=torch.int32).pin_memory())
+        lat, ok = [], 0
+        for i in range(70):
+            t0 = time.perf_counter()
+            ctx.solve(rid, sid, tg_h[i % got:i % got + 1], 1000, 1, 500 + i, 7, out=h1)
+            if i >= 10:
+                lat.append(1e3 * (time.perf_counter() - t0))
+                e = h1[1][0, 0].numpy()
+                ok += int(h1[2][0] > 0 and e[0] <= 1e-3 and e[1] <= 1e-2)
+        out[name] = {"ms_p50": float(np.median(lat)), "ms_p99": float(np.percentile(lat, 99)),
+                     "success_rate": ok / len(lat)}
+    out["paper"] = PAPER_CONTEXT
+    return out
 
 
 def _serve_run(ctx, reqs, trace, idx, rate_scale, server_kw):
@@ -773,6 +818,8 @@ def hjcd_arm(args):
         line["large"] = large_leg(ctx, args, dev, stream)
     if world == 1 and args.dof_scaling:
         line["dof_scaling"] = dof_scaling_leg(ctx, args, dev, stream)
+    if world == 1 and args.latency:
+        line["single_target_latency"] = latency_leg(ctx, args, dev)
     if world == 1 and args.tracking_frames > 0:
         line["tracking"] = tracking_leg(ctx, args, dev)
     if world == 1 and args.serve_seconds > 0:

@@ -500,19 +500,19 @@ def _cfg2_targets(ctx, rid, sid, orob, osc, wl, T):
 
 def test_solve_with_obstacles_matches_oracle(ctx):
     """cfg2 workload shape (Panda + 60 spheres, 200 spheres + 20 boxes) with
-    256 seeds on 100 targets."""
-    wl = inputs.cfg2(100, 256)
+    256 seeds on 200 targets: success within 1 point of the oracle."""
+    wl = inputs.cfg2(200, 256)
     rob, sc = wl.robot, wl.scene
     rid, sid = ctx.add_robot(rob), ctx.set_scene(sc)
     orob, osc = orc.Robot(rob), orc.Scene(sc)
-    T, S, k = 100, 256, 4
+    T, S, k = 200, 256, 4
     tg = _cfg2_targets(ctx, rid, sid, orob, osc, wl, T)
     q, err, cnt = ctx.solve(rid, sid, dev(tg), S, k, wl.seed, 7)
     q, err, cnt = host(q), host(err), host(cnt).astype(int)
     succ_g = _verify(orob, osc, rob, tg, q, err, cnt, wl.eps_pos, wl.eps_ori)
     o = orc.solve(orob, osc, orc.make_params(wl.eps_pos, wl.eps_ori, seed=wl.seed), tg, S, k)
     succ_o = (o["count"] > 0) & (o["err"][:, 0, 0] <= wl.eps_pos) & (o["err"][:, 0, 1] <= wl.eps_ori)
-    assert abs(succ_g.mean() - succ_o.mean()) <= 0.02 + 1e-12
+    assert abs(succ_g.mean() - succ_o.mean()) <= 0.01 + 1e-12
     assert succ_g.mean() > 0.8
 
 
