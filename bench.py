@@ -735,9 +735,8 @@ def hjcd_arm(args):
     d2h = T * K * (n + 2) * 4 + T * 4
 
     # roofline of the dominant kernel
-    ph = np.mean(np.asarray(phases), axis=0)  # ccd, dup, lm, collide, rank, whole
+    ph_raw = np.mean(np.asarray(phases), axis=0)  # ccd, dup, lm, collide, rank, whole
     names = ["po_ccd", "topk_dup", "pjik", "collide", "rank"]
-    dom = int(np.argmax(ph[:5]))
     steps = args.steps
     n_sph = len(rob.sph_body)
     fl = {
@@ -749,6 +748,11 @@ def hjcd_arm(args):
     props = torch.cuda.get_device_properties(dev)
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    # with the ranked collision filter (default) the collision work runs inside the rank phase
+    ph = np.array(ph_raw, dtype=float)
+    ph[names.index("collide")] += ph[names.index("rank")]
+    ph[names.index("rank")] = 0.0
+    dom = int(np.argmax(ph[:5]))
     dom_name = names[dom] if names[dom] in fl else max(fl, key=lambda k: fl[k] / max(ph[names.index(k)], 1e-9))
     dom_ms = ph[names.index(dom_name)]
     achieved = fl[dom_name] / (dom_ms * 1e-3) / 1e12
@@ -768,7 +772,8 @@ def hjcd_arm(args):
                    "tolerance": "1 mm / 0.01 rad", "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "candidates_per_s": value * S, "success_rate": success,
-        "phase_ms": {nm: float(v) for nm, v in zip(names + ["step"], ph)},
+        "phase_ms": {nm: float(v) for nm, v in zip(names + ["step"], ph_raw)},
+        "phase_note": "with the ranked collision filter (default) the collision checks run in the rank phase",
         "work_per_step": {"ccd_iters": cnt[0] / steps, "lm_iters": cnt[1] / steps, "lm_fk_passes": cnt[2] / steps,
                           "sphere_tests": cnt[3] / steps, "box_tests": cnt[6] / steps,
                           "collide_candidates": cnt[4] / steps},
@@ -777,6 +782,25 @@ def hjcd_arm(args):
                 "ms_per_step": float(np.mean(e2e_ms))},
         "clocks": clk, "gpu_launches": int(launches),
     }
+    if world == 1:
+        # the same step with the collision filter over every polished candidate (mode 0) instead of
+        # in rank order until top_k are found (mode 1, the default; identical results)
+        hjcd.hjcd_set_collision_mode(ctx.h, 0)
+        try:
+            step(tg, out)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            a0.record(stream)
+            for _ in range(3):
+                step(tg, out)
+            a1.record(stream)
+            torch.cuda.synchronize(dev)
+            ph_a = hjcd.hjcd_phase_times(ctx.h)
+        finally:
+            hjcd.hjcd_set_collision_mode(ctx.h, 1)
+        line["collision_all_candidates"] = {
+            "ms_per_step": a0.elapsed_time(a1) / 3, "solves_per_s": T / (a0.elapsed_time(a1) / 3 * 1e-3),
+            "phase_ms_last_step": {nm: float(v) for nm, v in zip(names + ["step"], ph_a)}}
     if world == 1 and args.ccd_baseline:
         # the same step with the position-only CCD (Alg. 1) in place of PO-CCD (Alg. 3)
         pb = api.make_params(cd_variant=1)

@@ -301,6 +301,14 @@ hjcd_status hjcd_poll(hjcd_ctx* ctx, int64_t request_id, int32_t* done, hjcd_req
 /* Block until the request is done (HJCD_ETIMEOUT after timeout_s seconds). */
 hjcd_status hjcd_wait(hjcd_ctx* ctx, int64_t request_id, double timeout_s, hjcd_request_info* info);
 
+/* How the whole-method entry points apply the collision filter (Alg. 2):
+ * 1 (default), in rank order -- each target's candidates are sorted by score
+ * first and checked in that order until top_k collision-free ones are found,
+ * which returns exactly the top_k of filtering every candidate; 0, every
+ * polished candidate is checked, then the survivors are ranked.  Results are
+ * identical; the work counters differ. */
+hjcd_status hjcd_set_collision_mode(hjcd_ctx* ctx, int32_t mode);
+
 /* Device workspace one hjcd_solve / hjcd_solve_batch call may use (0, the
  * default: unlimited).  A call needing more runs in waves: each request's
  * targets are cut into consecutive chunks whose seeds fit the budget, run one

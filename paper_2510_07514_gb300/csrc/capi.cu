@@ -949,6 +949,13 @@ hjcd_status hjcd_rank(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const int6
 
 // ---- instrumentation -----------------------------------------------------
 
+hjcd_status hjcd_set_collision_mode(hjcd_ctx* ctx, int32_t mode) {
+    if (!ctx) return HJCD_EINVAL;
+    if (mode != 0 && mode != 1) return fail(ctx, HJCD_EINVAL, "collision mode must be 0 (all candidates) or 1 (ranked)");
+    ctx->collide_lazy = mode == 1;
+    return HJCD_OK;
+}
+
 hjcd_status hjcd_set_memory_budget(hjcd_ctx* ctx, uint64_t bytes) {
     if (!ctx) return HJCD_EINVAL;
     if (bytes && bytes < (1u << 20)) return fail(ctx, HJCD_EINVAL, "a memory budget below 1 MiB cannot hold a wave");

@@ -394,6 +394,44 @@ inline int grid_for(int64_t items, int per_block, int per_sm = 64) {
 }
 
 // ----------------------------------------------------------------------------
+// per-target selection: 64-bit keys (score bits << 32 | index) sorted in
+// shared memory by a bitonic network; non-negative scores order like their
+// IEEE bit patterns, the index in the low word breaks ties toward the lower
+// candidate, and invalid entries get the all-ones key and sort last.
+
+constexpr uint64_t kNoKey = ~0ull;
+
+__device__ __forceinline__ uint64_t score_key(float s, uint32_t idx) {
+    if (!(s == s)) return kNoKey;  // NaN
+    const uint32_t bits = __float_as_uint(s + 0.0f);  // -0 -> +0
+    return ((uint64_t)bits << 32) | idx;
+}
+
+__device__ __forceinline__ void bitonic_sort(uint64_t* keys, int N) {
+    for (int size = 2; size <= N; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < (N >> 1); i += blockDim.x) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const uint64_t a = keys[lo], b = keys[hi];
+                if ((a > b) == up) {
+                    keys[lo] = b;
+                    keys[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__device__ __forceinline__ int pow2_at_least(int m) {
+    int N = 1;
+    while (N < m) N <<= 1;
+    return N;
+}
+
+// ----------------------------------------------------------------------------
 // host-side launch entry points (defined in the kernel translation units)
 
 struct CcdArgs {
@@ -470,6 +508,33 @@ struct RankArgs {
     const float* q_ref;
     int32_t ld_ref;
 };
+
+// Ranking key of candidate i of target t (candidates [b0, b0 + B), robot DoF
+// n): the score key of a finite score (with use_hit, never a colliding
+// candidate); with the target's nearest flag and A.q_ref, the candidates within
+// the target's tolerances in class 0 keyed by squared joint distance to the
+// reference, the rest in class 1 by score.  kNoKey past B.
+__device__ __forceinline__ uint64_t rank_key(const RankArgs& A, int t, int64_t b0, int B, int n, int i, bool use_hit) {
+    if (i >= B || (use_hit && A.hit && A.hit[b0 + i])) return kNoKey;
+    const float sc = A.score[b0 + i];
+    if (!(sc < __int_as_float(0x7f800000))) return kNoKey;  // finite only
+    uint64_t k = score_key(sc, (uint32_t)i);
+    const int tk = A.tg ? A.tg[t].top_k : A.top_k;
+    if (A.q_ref && (tk & kNearestFlag)) {
+        const int64_t g = b0 + i;
+        if (A.perr[g] <= A.tg[t].eps_pos && A.oerr[g] <= A.tg[t].eps_ori) {
+            float d2 = 0.0f;
+            for (int j = 0; j < n; ++j) {
+                const float dj = A.th[j * A.ld + g] - A.q_ref[(int64_t)t * A.ld_ref + j];
+                d2 = fmaf(dj, dj, d2);
+            }
+            k = score_key(d2, (uint32_t)i);
+        } else {
+            k |= 1ull << 63;
+        }
+    }
+    return k;
+}
 
 // Collision filter of C candidates.  With tg null or uniform set every
 // candidate is robot 0 against scene 0 (if any); otherwise candidate c belongs
@@ -553,6 +618,10 @@ void launch_lm(const LmArgs& A, bool trace, cudaStream_t st);
 void launch_topk_dup(const DupArgs& A, int max_m, cudaStream_t st);
 void launch_rank(const RankArgs& A, int max_b, cudaStream_t st);
 void launch_collide(const CollideArgs& A, cudaStream_t st);
+// The ranking with the collision filter applied lazily (k_rank_lazy); false
+// when it does not apply (no spheres, no target rows, or too large for shared
+// memory): use launch_collide + launch_rank.
+bool launch_rank_lazy(const CollideArgs& A, const RankArgs& R, int max_b, cudaStream_t st);
 void launch_contacts(const RobotParams& R, const RobotDev& rd, const SceneDev& sc, const int32_t* perm, int64_t C,
                      const float* th, int64_t ld, uint8_t* touched, cudaStream_t st);
 void launch_ffma(float* sink, int iters, int blocks, cudaStream_t st);

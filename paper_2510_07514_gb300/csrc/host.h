@@ -67,6 +67,7 @@ struct hjcd_ctx {
     bool ev_valid = false;
     std::atomic<int64_t> launches{0};
     size_t ws_budget = 0;     // workspace bytes one solve may use before it splits into waves (0: unlimited)
+    bool collide_lazy = true; // rank first, collision-check in rank order (hjcd_set_collision_mode)
     int32_t ccd_block = 128;  // launch configuration (hjcd_set_launch_config, hjcd_autotune)
     int32_t lm_warps = 4;
     std::mutex api_mu;  // robots/scenes tables against the serving thread

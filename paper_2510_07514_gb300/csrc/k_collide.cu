@@ -121,32 +121,254 @@ __host__ __device__ __forceinline__ CollideLayout collide_smem_layout(int n_obj4
 }
 
 
+// The warp's current robot: its lanes' link spheres (body frame) and bodies, the
+// bounding sphere of body `lane`, DoF, checked pairs and the bodies that carry spheres.
+template <int SPL>
+struct WarpRobot {
+    float4 ls[SPL];
+    int lb[SPL];
+    float4 lco;
+    int cur, n_m, pairs_m;
+    unsigned bmask;
+};
+
+// The warp's shared-memory buffers: world fine spheres, world bounding spheres,
+// the robot's body ranges and checked pairs, a list of 32 indices.
+struct WarpBufs {
+    float4* wsph;
+    float4* wco;
+    int2* wrange;
+    int2* wpairs;
+    int* list;
+};
+
+// Collision verdict of candidate c (robot row rid, scene row sid, -1: none),
+// warp-uniform; t_s / t_b accumulate the sphere and box tests.
 template <int SPL, bool UNIFORM, bool GRID>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideArgs A) {
+__device__ __forceinline__ bool warp_collides(const CollideArgs& A, const RobotParams* rob, const SceneDev& sc0,
+                                              const float4* s_scene, WarpRobot<SPL>& W, const WarpBufs& Bf, int64_t c,
+                                              int rid, int sid, unsigned long long& t_s, unsigned long long& t_b) {
     constexpr bool STAGED = UNIFORM;
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const SceneDev sc0 = A.n_scenes > 0 ? A.scenes[0] : SceneDev{nullptr, 0, 0};
-    const int n_obj4 = STAGED ? sc0.n_sph + 2 * sc0.n_box : 0;
-    if (n_obj4 > (STAGED ? A.max_obj4 : 0)) {  // the scene outgrew the shared memory the host sized
-        if (threadIdx.x == 0) atomicExch(A.err_flag, 2);
-        return;
+    float4* const wsph = Bf.wsph;
+    float4* const wco = Bf.wco;
+    int2* const wrange = Bf.wrange;
+    int2* const wpairs = Bf.wpairs;
+    int* const list = Bf.list;
+    if (rid != W.cur) {
+        W.cur = rid;
+        const RobotDev rd = A.rs.rd[rid];
+        W.n_m = rob[rid].n;
+        W.pairs_m = rd.n_pairs;
+        const int ns = rd.n_sph, nbr = W.n_m + 2;
+#pragma unroll
+        for (int q = 0; q < SPL; ++q) {
+            const int i = lane + 32 * q;
+            W.lb[q] = i < ns ? __ldg(rd.body + i) : -1;
+            W.ls[q] = i < ns ? __ldg(rd.sph + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        W.lco = lane < nbr ? __ldg(rd.coarse + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncwarp();
+        for (int i = lane; i < nbr; i += 32) wrange[i] = __ldg(rd.range + i);
+        for (int i = lane; i < W.pairs_m; i += 32) wpairs[i] = __ldg(rd.pairs + i);
+        __syncwarp();
+        W.bmask = __ballot_sync(0xffffffffu, lane < nbr && wrange[lane].y > 0);  // bodies with spheres
     }
-    const int nb_max = A.rs.n_max + 2;
-    const CollideLayout L = collide_smem_layout(n_obj4, A.rs.n, nb_max, A.rs.ns_max, A.rs.pairs_max);
+    const RobotParams& R = rob[rid];
+    const int n = UNIFORM ? A.u_n : W.n_m, nb = n + 2, n_pairs = UNIFORM ? A.u_pairs : W.pairs_m;
+    // obstacles: the staged copy (shared memory) or the scene's table (global, read-only path)
+    const float4* obj = s_scene;
+    int n_osph = 0, n_obox = 0;
+    if (UNIFORM) {
+        n_osph = A.u_osph;
+        n_obox = A.u_obox;
+    } else if (sid >= 0) {
+        const SceneDev sd = A.scenes[sid];
+        obj = sd.obj;
+        n_osph = sd.n_sph;
+        n_obox = sd.n_box;
+    }
+
+    // world frame: body 0 is the base (identity)
+    float4 ws[SPL];
+#pragma unroll
+    for (int q = 0; q < SPL; ++q) ws[q] = W.ls[q];
+    float4 wc = W.lco;
+    Frame F = frame_identity();
+#pragma unroll 1
+    for (int j = 0; j < n; ++j) {
+        fk_step(R, j, A.th[j * A.ld + c], F);
+#pragma unroll
+        for (int q = 0; q < SPL; ++q)
+            if (W.lb[q] == j + 1) ws[q] = to_world(F, W.ls[q]);
+        if (lane == j + 1) wc = to_world(F, W.lco);
+    }
+    const Frame E = fk_flange(R, F);
+#pragma unroll
+    for (int q = 0; q < SPL; ++q) {
+        if (W.lb[q] == n + 1) ws[q] = to_world(E, W.ls[q]);
+        if (W.lb[q] >= 0) wsph[lane + 32 * q] = ws[q];
+    }
+    if (lane == n + 1) wc = to_world(E, W.lco);
+    if (lane < nb) wco[lane] = wc;
+    __syncwarp();
+
+    bool hit = false;
+
+    // self-collision: bounding test per checked body pair, fine pairs spread over the warp
+    for (int p0 = 0; p0 < n_pairs && !hit; p0 += 32) {
+        const int p = p0 + lane;
+        int2 pr = make_int2(0, 0);
+        bool ch = false;
+        if (p < n_pairs) {
+            pr = wpairs[p];
+            ch = sph_sph(wco[pr.x], wco[pr.y]);
+        }
+        t_s += (unsigned long long)min(32, n_pairs - p0);
+        unsigned m = __ballot_sync(0xffffffffu, ch);
+        while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1u;
+            const int ba = __shfl_sync(0xffffffffu, pr.x, src), bb = __shfl_sync(0xffffffffu, pr.y, src);
+            const int2 ra = wrange[ba], rb = wrange[bb];
+            const int items = ra.y * rb.y;
+            bool h = false;
+            for (int w = lane; w < items; w += 32) {
+                const int i = w / rb.y;
+                h |= sph_sph(wsph[ra.x + i], wsph[rb.x + (w - i * rb.y)]);
+            }
+            t_s += (unsigned long long)items;
+            if (__any_sync(0xffffffffu, h)) {
+                hit = true;
+                break;
+            }
+        }
+    }
+
+    // obstacle spheres of a gridded scene: per body, the lanes walk the cells within the
+    // bounding sphere's radius plus the largest obstacle radius; each obstacle that
+    // overlaps the bounding sphere is tested against the body's fine spheres
+    const int32_t* gcell = nullptr;
+    if (GRID && n_osph > 0) gcell = (UNIFORM ? sc0 : A.scenes[sid]).cell;
+    if (GRID && gcell) {
+        const SceneDev& G = A.scenes[UNIFORM ? 0 : sid];
+        for (int b = 0; b < nb && !hit; ++b) {
+            const int2 rg = wrange[b];
+            if (rg.y == 0) continue;
+            const float4 co = wco[b];
+            const float ext = co.w + G.reach;
+            const float cc[3] = {co.x, co.y, co.z};
+            int i0[3], i1[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int dmax = G.dim[k] - 1;
+                i0[k] = min(max((int)floorf((cc[k] - ext - G.lo[k]) * G.inv_h), 0), dmax);
+                i1[k] = min(max((int)floorf((cc[k] + ext - G.lo[k]) * G.inv_h), 0), dmax);
+            }
+            const int nx = i1[0] - i0[0] + 1, ny = i1[1] - i0[1] + 1, nxy = nx * ny;
+            const int ncell = nxy * (i1[2] - i0[2] + 1);
+            bool h = false;
+            unsigned tl = 0;
+            for (int q = lane; q < ncell && !h; q += 32) {
+                const int z = q / nxy, r = q - z * nxy, y = r / nx, x = r - y * nx;
+                const int k = (i0[0] + x) + G.dim[0] * ((i0[1] + y) + G.dim[1] * (i0[2] + z));
+                const int a = __ldg(gcell + k), e = __ldg(gcell + k + 1);
+                for (int o = a; o < e && !h; ++o) {
+                    const float4 sp = ld_obj<STAGED>(obj, o);
+                    ++tl;
+                    if (sph_sph(co, sp)) {
+                        for (int i = 0; i < rg.y && !h; ++i) h = sph_sph(wsph[rg.x + i], sp);
+                        tl += rg.y;
+                    }
+                }
+            }
+            t_s += __reduce_add_sync(0xffffffffu, tl);
+            hit = __any_sync(0xffffffffu, h);
+        }
+    }
+
+    // obstacle spheres, 32 at a time: each lane tests its obstacle against every body's
+    // bounding sphere (a bit per body); only bodies some obstacle overlaps are visited, their
+    // overlapping obstacles compacted and the fine tests spread over the warp
+    const int nbs = __popc(W.bmask);
+    for (int o0 = 0; o0 < n_osph && !hit && !(GRID && gcell); o0 += 32) {
+        const int o = o0 + lane;
+        const bool valid = o < n_osph;
+        const float4 s = valid ? ld_obj<STAGED>(obj, o) : make_float4(0.f, 0.f, 0.f, 0.f);
+        unsigned bm = 0;
+        if (valid)
+            for (unsigned bb = W.bmask; bb; bb &= bb - 1u) {
+                const int b = __ffs(bb) - 1;
+                if (sph_sph(wco[b], s)) bm |= 1u << b;
+            }
+        t_s += (unsigned long long)min(32, n_osph - o0) * nbs;
+        for (unsigned todo = __reduce_or_sync(0xffffffffu, bm); todo && !hit; todo &= todo - 1u) {
+            const int b = __ffs(todo) - 1;
+            const int2 rg = wrange[b];
+            const bool ch = (bm >> b) & 1u;
+            const unsigned m = __ballot_sync(0xffffffffu, ch);
+            if (ch) list[__popc(m & lt)] = o;
+            __syncwarp();
+            const int items = __popc(m) * rg.y;
+            bool h = false;
+            for (int w = lane; w < items; w += 32) {
+                const int k = w / rg.y;
+                h |= sph_sph(wsph[rg.x + (w - k * rg.y)], ld_obj<STAGED>(obj, list[k]));
+            }
+            t_s += (unsigned long long)items;
+            hit = __any_sync(0xffffffffu, h);
+            __syncwarp();
+        }
+    }
+
+    // obstacle boxes, the same way
+    const float4* box = obj + n_osph;
+    for (int o0 = 0; o0 < n_obox && !hit; o0 += 32) {
+        const int o = o0 + lane;
+        const bool valid = o < n_obox;
+        const float4 lo = valid ? ld_obj<STAGED>(box, 2 * o) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 hi = valid ? ld_obj<STAGED>(box, 2 * o + 1) : lo;
+        unsigned bm = 0;
+        if (valid)
+            for (unsigned bb = W.bmask; bb; bb &= bb - 1u) {
+                const int b = __ffs(bb) - 1;
+                if (sph_box(wco[b], lo, hi)) bm |= 1u << b;
+            }
+        t_b += (unsigned long long)min(32, n_obox - o0) * nbs;
+        for (unsigned todo = __reduce_or_sync(0xffffffffu, bm); todo && !hit; todo &= todo - 1u) {
+            const int b = __ffs(todo) - 1;
+            const int2 rg = wrange[b];
+            const bool ch = (bm >> b) & 1u;
+            const unsigned m = __ballot_sync(0xffffffffu, ch);
+            if (ch) list[__popc(m & lt)] = o;
+            __syncwarp();
+            const int items = __popc(m) * rg.y;
+            bool h = false;
+            for (int w = lane; w < items; w += 32) {
+                const int k = w / rg.y, bo = list[k];
+                h |= sph_box(wsph[rg.x + (w - k * rg.y)], ld_obj<STAGED>(box, 2 * bo), ld_obj<STAGED>(box, 2 * bo + 1));
+            }
+            t_b += (unsigned long long)items;
+            hit = __any_sync(0xffffffffu, h);
+            __syncwarp();
+        }
+    }
+
+    return hit;
+}
+
+// CTA prologue of the collision kernels: the obstacles of a single scene
+// staged by one bulk copy (UNIFORM), the robots' kinematic tables with plain
+// loads.  False (error flag set) when the staging wait ran out or the scene
+// outgrew the shared memory the host sized; the CTA must return.
+template <bool UNIFORM>
+__device__ __forceinline__ bool collide_prologue(const CollideArgs& A, unsigned char* smem, const CollideLayout& L,
+                                                 const SceneDev& sc0, int n_obj4, const RobotParams** rob) {
     float4* s_scene = reinterpret_cast<float4*>(smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
-    unsigned char* wb = smem + L.warp + warp * L.warp_bytes;
-    float4* wsph = reinterpret_cast<float4*>(wb);
-    float4* wco = wsph + A.rs.ns_max;
-    int2* wrange = reinterpret_cast<int2*>(wco + nb_max);
-    int2* wpairs = wrange + nb_max;
-    int* list = reinterpret_cast<int*>(wpairs + A.rs.pairs_max);
-
-    // stage the obstacles with one bulk copy, the robots' kinematic tables with plain loads
     const uint32_t bytes = 16u * (uint32_t)n_obj4;
-    if (STAGED) {
+    if (UNIFORM) {
         if (threadIdx.x == 0) mbar_init(bar, 1);
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -158,27 +380,53 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
             }
         }
     }
-    const RobotParams* rob = stage_robots(smem + L.robots, A.rs);
-    if (STAGED) {
+    *rob = stage_robots(smem + L.robots, A.rs);
+    if (UNIFORM) {
         const bool staged = mbar_wait_bounded(bar, 0);
         if (__syncthreads_or(!staged)) {
-            // give up: flag the error, give the copy one more bounded wait, return
+            // give up: flag the error, give the copy one more bounded wait
             if (threadIdx.x == 0) {
                 atomicExch(A.err_flag, 1);
                 mbar_wait_bounded(bar, 0);
             }
-            return;
+            return false;
         }
     }
+    return true;
+}
 
-    // this lane's fine spheres (body frame) and bodies, its bounding sphere
-    // (body lane), for the robot of the warp's current candidate
-    float4 ls[SPL];
-    int lb[SPL];
-    float4 lco = make_float4(0.f, 0.f, 0.f, 0.f);
-    int cur = -1, n_m = 0, pairs_m = 0;  // robot of a mixed launch: DoF, checked pairs
-    unsigned bmask = 0;                  // its bodies that carry spheres (bit per body, n + 2 <= 26)
+__device__ __forceinline__ WarpBufs warp_bufs(unsigned char* smem, const CollideLayout& L, const CollideArgs& A) {
+    const int nb_max = A.rs.n_max + 2;
+    unsigned char* wb = smem + L.warp + (threadIdx.x >> 5) * L.warp_bytes;
+    WarpBufs B;
+    B.wsph = reinterpret_cast<float4*>(wb);
+    B.wco = B.wsph + A.rs.ns_max;
+    B.wrange = reinterpret_cast<int2*>(B.wco + nb_max);
+    B.wpairs = B.wrange + nb_max;
+    B.list = reinterpret_cast<int*>(B.wpairs + A.rs.pairs_max);
+    return B;
+}
 
+template <int SPL, bool UNIFORM, bool GRID>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideArgs A) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const SceneDev sc0 = A.n_scenes > 0 ? A.scenes[0] : SceneDev{nullptr, 0, 0};
+    const int n_obj4 = UNIFORM ? sc0.n_sph + 2 * sc0.n_box : 0;
+    if (n_obj4 > (UNIFORM ? A.max_obj4 : 0)) {  // the scene outgrew the shared memory the host sized
+        if (threadIdx.x == 0) atomicExch(A.err_flag, 2);
+        return;
+    }
+    const CollideLayout L = collide_smem_layout(n_obj4, A.rs.n, A.rs.n_max + 2, A.rs.ns_max, A.rs.pairs_max);
+    const RobotParams* rob;
+    if (!collide_prologue<UNIFORM>(A, smem, L, sc0, n_obj4, &rob)) return;
+    const WarpBufs Bf = warp_bufs(smem, L, A);
+    const float4* s_scene = reinterpret_cast<const float4*>(smem);
+
+    WarpRobot<SPL> W;
+    W.cur = -1;
+    W.n_m = W.pairs_m = 0;
+    W.bmask = 0;
     unsigned long long tests = 0, btests = 0, ncand = 0;
     const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
     int rid = 0, sid = 0;
@@ -200,206 +448,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
             if (lane == 0) A.hit[c] = 1;
             continue;
         }
-        if (rid != cur) {
-            cur = rid;
-            const RobotDev rd = A.rs.rd[rid];
-            n_m = rob[rid].n;
-            pairs_m = rd.n_pairs;
-            const int ns = rd.n_sph, nbr = n_m + 2;
-#pragma unroll
-            for (int q = 0; q < SPL; ++q) {
-                const int i = lane + 32 * q;
-                lb[q] = i < ns ? __ldg(rd.body + i) : -1;
-                ls[q] = i < ns ? __ldg(rd.sph + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            lco = lane < nbr ? __ldg(rd.coarse + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
-            __syncwarp();
-            for (int i = lane; i < nbr; i += 32) wrange[i] = __ldg(rd.range + i);
-            for (int i = lane; i < pairs_m; i += 32) wpairs[i] = __ldg(rd.pairs + i);
-            __syncwarp();
-            bmask = __ballot_sync(0xffffffffu, lane < nbr && wrange[lane].y > 0);  // bodies with spheres
-        }
-        const RobotParams& R = rob[rid];
-        const int n = UNIFORM ? A.u_n : n_m, nb = n + 2, n_pairs = UNIFORM ? A.u_pairs : pairs_m;
-        // obstacles: the staged copy (shared memory) or the scene's table (global, read-only path)
-        const float4* obj = s_scene;
-        int n_osph = 0, n_obox = 0;
-        if (UNIFORM) {
-            n_osph = A.u_osph;
-            n_obox = A.u_obox;
-        } else if (sid >= 0) {
-            const SceneDev sd = A.scenes[sid];
-            obj = sd.obj;
-            n_osph = sd.n_sph;
-            n_obox = sd.n_box;
-        }
-
-        // world frame: body 0 is the base (identity)
-        float4 ws[SPL];
-#pragma unroll
-        for (int q = 0; q < SPL; ++q) ws[q] = ls[q];
-        float4 wc = lco;
-        Frame F = frame_identity();
-#pragma unroll 1
-        for (int j = 0; j < n; ++j) {
-            fk_step(R, j, A.th[j * A.ld + c], F);
-#pragma unroll
-            for (int q = 0; q < SPL; ++q)
-                if (lb[q] == j + 1) ws[q] = to_world(F, ls[q]);
-            if (lane == j + 1) wc = to_world(F, lco);
-        }
-        const Frame E = fk_flange(R, F);
-#pragma unroll
-        for (int q = 0; q < SPL; ++q) {
-            if (lb[q] == n + 1) ws[q] = to_world(E, ls[q]);
-            if (lb[q] >= 0) wsph[lane + 32 * q] = ws[q];
-        }
-        if (lane == n + 1) wc = to_world(E, lco);
-        if (lane < nb) wco[lane] = wc;
-        __syncwarp();
-
-        bool hit = false;
         unsigned long long t_s = 0, t_b = 0;  // tests of this candidate (uniform over the warp)
-
-        // self-collision: bounding test per checked body pair, fine pairs spread over the warp
-        for (int p0 = 0; p0 < n_pairs && !hit; p0 += 32) {
-            const int p = p0 + lane;
-            int2 pr = make_int2(0, 0);
-            bool ch = false;
-            if (p < n_pairs) {
-                pr = wpairs[p];
-                ch = sph_sph(wco[pr.x], wco[pr.y]);
-            }
-            t_s += (unsigned long long)min(32, n_pairs - p0);
-            unsigned m = __ballot_sync(0xffffffffu, ch);
-            while (m) {
-                const int src = __ffs(m) - 1;
-                m &= m - 1u;
-                const int ba = __shfl_sync(0xffffffffu, pr.x, src), bb = __shfl_sync(0xffffffffu, pr.y, src);
-                const int2 ra = wrange[ba], rb = wrange[bb];
-                const int items = ra.y * rb.y;
-                bool h = false;
-                for (int w = lane; w < items; w += 32) {
-                    const int i = w / rb.y;
-                    h |= sph_sph(wsph[ra.x + i], wsph[rb.x + (w - i * rb.y)]);
-                }
-                t_s += (unsigned long long)items;
-                if (__any_sync(0xffffffffu, h)) {
-                    hit = true;
-                    break;
-                }
-            }
-        }
-
-        // obstacle spheres of a gridded scene: per body, the lanes walk the cells within the
-        // bounding sphere's radius plus the largest obstacle radius; each obstacle that
-        // overlaps the bounding sphere is tested against the body's fine spheres
-        const int32_t* gcell = nullptr;
-        if (GRID && n_osph > 0) gcell = (UNIFORM ? sc0 : A.scenes[sid]).cell;
-        if (GRID && gcell) {
-            const SceneDev& G = A.scenes[UNIFORM ? 0 : sid];
-            for (int b = 0; b < nb && !hit; ++b) {
-                const int2 rg = wrange[b];
-                if (rg.y == 0) continue;
-                const float4 co = wco[b];
-                const float ext = co.w + G.reach;
-                const float cc[3] = {co.x, co.y, co.z};
-                int i0[3], i1[3];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const int dmax = G.dim[k] - 1;
-                    i0[k] = min(max((int)floorf((cc[k] - ext - G.lo[k]) * G.inv_h), 0), dmax);
-                    i1[k] = min(max((int)floorf((cc[k] + ext - G.lo[k]) * G.inv_h), 0), dmax);
-                }
-                const int nx = i1[0] - i0[0] + 1, ny = i1[1] - i0[1] + 1, nxy = nx * ny;
-                const int ncell = nxy * (i1[2] - i0[2] + 1);
-                bool h = false;
-                unsigned tl = 0;
-                for (int q = lane; q < ncell && !h; q += 32) {
-                    const int z = q / nxy, r = q - z * nxy, y = r / nx, x = r - y * nx;
-                    const int k = (i0[0] + x) + G.dim[0] * ((i0[1] + y) + G.dim[1] * (i0[2] + z));
-                    const int a = __ldg(gcell + k), e = __ldg(gcell + k + 1);
-                    for (int o = a; o < e && !h; ++o) {
-                        const float4 sp = ld_obj<STAGED>(obj, o);
-                        ++tl;
-                        if (sph_sph(co, sp)) {
-                            for (int i = 0; i < rg.y && !h; ++i) h = sph_sph(wsph[rg.x + i], sp);
-                            tl += rg.y;
-                        }
-                    }
-                }
-                t_s += __reduce_add_sync(0xffffffffu, tl);
-                hit = __any_sync(0xffffffffu, h);
-            }
-        }
-
-        // obstacle spheres, 32 at a time: each lane tests its obstacle against every body's
-        // bounding sphere (a bit per body); only bodies some obstacle overlaps are visited, their
-        // overlapping obstacles compacted and the fine tests spread over the warp
-        const int nbs = __popc(bmask);
-        for (int o0 = 0; o0 < n_osph && !hit && !(GRID && gcell); o0 += 32) {
-            const int o = o0 + lane;
-            const bool valid = o < n_osph;
-            const float4 s = valid ? ld_obj<STAGED>(obj, o) : make_float4(0.f, 0.f, 0.f, 0.f);
-            unsigned bm = 0;
-            if (valid)
-                for (unsigned bb = bmask; bb; bb &= bb - 1u) {
-                    const int b = __ffs(bb) - 1;
-                    if (sph_sph(wco[b], s)) bm |= 1u << b;
-                }
-            t_s += (unsigned long long)min(32, n_osph - o0) * nbs;
-            for (unsigned todo = __reduce_or_sync(0xffffffffu, bm); todo && !hit; todo &= todo - 1u) {
-                const int b = __ffs(todo) - 1;
-                const int2 rg = wrange[b];
-                const bool ch = (bm >> b) & 1u;
-                const unsigned m = __ballot_sync(0xffffffffu, ch);
-                if (ch) list[__popc(m & lt)] = o;
-                __syncwarp();
-                const int items = __popc(m) * rg.y;
-                bool h = false;
-                for (int w = lane; w < items; w += 32) {
-                    const int k = w / rg.y;
-                    h |= sph_sph(wsph[rg.x + (w - k * rg.y)], ld_obj<STAGED>(obj, list[k]));
-                }
-                t_s += (unsigned long long)items;
-                hit = __any_sync(0xffffffffu, h);
-                __syncwarp();
-            }
-        }
-
-        // obstacle boxes, the same way
-        const float4* box = obj + n_osph;
-        for (int o0 = 0; o0 < n_obox && !hit; o0 += 32) {
-            const int o = o0 + lane;
-            const bool valid = o < n_obox;
-            const float4 lo = valid ? ld_obj<STAGED>(box, 2 * o) : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 hi = valid ? ld_obj<STAGED>(box, 2 * o + 1) : lo;
-            unsigned bm = 0;
-            if (valid)
-                for (unsigned bb = bmask; bb; bb &= bb - 1u) {
-                    const int b = __ffs(bb) - 1;
-                    if (sph_box(wco[b], lo, hi)) bm |= 1u << b;
-                }
-            t_b += (unsigned long long)min(32, n_obox - o0) * nbs;
-            for (unsigned todo = __reduce_or_sync(0xffffffffu, bm); todo && !hit; todo &= todo - 1u) {
-                const int b = __ffs(todo) - 1;
-                const int2 rg = wrange[b];
-                const bool ch = (bm >> b) & 1u;
-                const unsigned m = __ballot_sync(0xffffffffu, ch);
-                if (ch) list[__popc(m & lt)] = o;
-                __syncwarp();
-                const int items = __popc(m) * rg.y;
-                bool h = false;
-                for (int w = lane; w < items; w += 32) {
-                    const int k = w / rg.y, bo = list[k];
-                    h |= sph_box(wsph[rg.x + (w - k * rg.y)], ld_obj<STAGED>(box, 2 * bo), ld_obj<STAGED>(box, 2 * bo + 1));
-                }
-                t_b += (unsigned long long)items;
-                hit = __any_sync(0xffffffffu, h);
-                __syncwarp();
-            }
-        }
-
+        const bool hit = warp_collides<SPL, UNIFORM, GRID>(A, rob, sc0, s_scene, W, Bf, c, rid, sid, t_s, t_b);
         if (lane == 0) {
             A.hit[c] = hit ? 1 : 0;
             tests += t_s;
@@ -413,6 +463,125 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
         atomicAdd(&A.cnt->v[6], btests);
         atomicAdd(&A.cnt->v[4], ncand);
     }
+}
+
+// Ranking with the collision filter applied lazily (the top_k collision-free
+// candidates by score are the first top_k collision-free ones in score
+// order): one CTA per target sorts its candidates' keys, then its warps check
+// candidates in rank order, one candidate per warp and kWarpsPerBlock at a
+// time, until top_k collision-free ones are found or the ranked candidates
+// run out.  Same output as the collision filter over all candidates followed
+// by k_rank.
+template <int SPL, bool UNIFORM, bool GRID>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rank_lazy(const CollideArgs A, const RankArgs R,
+                                                                  uint32_t keys_off) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int verdict[kWarpsPerBlock];
+    __shared__ int picks[HJCD_MAX_TOPK];
+    __shared__ int n_found;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x;
+    const SceneDev sc0 = A.n_scenes > 0 ? A.scenes[0] : SceneDev{nullptr, 0, 0};
+    const int n_obj4 = UNIFORM ? sc0.n_sph + 2 * sc0.n_box : 0;
+    if (n_obj4 > (UNIFORM ? A.max_obj4 : 0)) {
+        if (threadIdx.x == 0) atomicExch(A.err_flag, 2);
+        return;
+    }
+    const CollideLayout L = collide_smem_layout(n_obj4, A.rs.n, A.rs.n_max + 2, A.rs.ns_max, A.rs.pairs_max);
+    const RobotParams* rob;
+    if (!collide_prologue<UNIFORM>(A, smem, L, sc0, n_obj4, &rob)) return;
+    const WarpBufs Bf = warp_bufs(smem, L, A);
+    const float4* s_scene = reinterpret_cast<const float4*>(smem);
+    uint64_t* keys = reinterpret_cast<uint64_t*>(smem + keys_off);
+
+    const TargetDesc& T = R.tg[t];
+    const int rid = T.robot, sid = UNIFORM ? 0 : T.scene;
+    const int n = rob[rid].n;
+    const int64_t b0 = R.b_off[t];
+    const int B = (int)(R.b_off[t + 1] - b0);
+    const int N = pow2_at_least(B > 0 ? B : 1);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) keys[i] = rank_key(R, t, b0, B, n, i, false);
+    __syncthreads();
+    bitonic_sort(keys, N);
+    int ranked = 0;  // candidates with a key (finite score)
+    for (int base = 0; base < N; base += blockDim.x)
+        ranked += __syncthreads_count(base + (int)threadIdx.x < N && keys[base + threadIdx.x] != kNoKey);
+    const int top_k = T.top_k & ~kNearestFlag;
+
+    WarpRobot<SPL> W;
+    W.cur = -1;
+    W.n_m = W.pairs_m = 0;
+    W.bmask = 0;
+    unsigned long long tests = 0, btests = 0, ncand = 0;
+    if (threadIdx.x == 0) n_found = 0;
+    __syncthreads();
+    for (int p0 = 0; p0 < ranked && n_found < top_k; p0 += kWarpsPerBlock) {
+        const int p = p0 + warp;
+        bool hit = true;
+        if (p < ranked) {
+            const int64_t c = b0 + (int64_t)(keys[p] & 0xffffffffu);
+            unsigned long long t_s = 0, t_b = 0;
+            hit = warp_collides<SPL, UNIFORM, GRID>(A, rob, sc0, s_scene, W, Bf, c, rid, sid, t_s, t_b);
+            if (lane == 0) {
+                tests += t_s;
+                btests += t_b;
+                ++ncand;
+            }
+        }
+        if (lane == 0) verdict[warp] = hit ? 1 : 0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int f = n_found;
+            for (int w = 0; w < kWarpsPerBlock && f < top_k; ++w)
+                if (p0 + w < ranked && !verdict[w]) picks[f++] = p0 + w;
+            n_found = f;
+        }
+        __syncthreads();
+    }
+    const int count = n_found;
+    float* oq = R.out_q + R.qe_off[2 * t];
+    float* oe = R.out_err + R.qe_off[2 * t + 1];
+    for (int q = threadIdx.x; q < count * (n + 2); q += blockDim.x) {
+        const int r = q / (n + 2), j = q % (n + 2);
+        const int64_t g = b0 + (int64_t)(keys[picks[r]] & 0xffffffffu);
+        if (j < n) oq[r * n + j] = R.th[j * R.ld + g];
+        else if (j == n) oe[r * 2] = R.perr[g];
+        else oe[r * 2 + 1] = R.oerr[g];
+    }
+    if (threadIdx.x == 0) R.out_count[t] = count;
+    if (A.cnt && lane == 0) {
+        atomicAdd(&A.cnt->v[3], tests);
+        atomicAdd(&A.cnt->v[6], btests);
+        atomicAdd(&A.cnt->v[4], ncand);
+    }
+}
+
+template <int SPL, bool UNIFORM, bool GRID>
+bool launch_rank_lazy_t(const CollideArgs& A, const RankArgs& R, int n_obj4, int max_b, cudaStream_t st) {
+    const CollideLayout L =
+        collide_smem_layout(UNIFORM ? n_obj4 : 0, A.rs.n, A.rs.n_max + 2, A.rs.ns_max, A.rs.pairs_max);
+    const uint32_t keys_off = (L.total + 15u) / 16u * 16u;
+    int N = 1;
+    while (N < max_b) N <<= 1;
+    const size_t smem = keys_off + 8 * (size_t)N;
+    if (smem > 220 * 1024) return false;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_rank_lazy<SPL, UNIFORM, GRID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             220 * 1024);
+        attr_set = true;
+    }
+    k_rank_lazy<SPL, UNIFORM, GRID><<<R.T, kWarpsPerBlock * 32, smem, st>>>(A, R, keys_off);
+    return true;
+}
+
+template <bool UNIFORM, bool GRID>
+bool launch_rank_lazy_s(const CollideArgs& A, const RankArgs& R, int n_obj4, int max_b, cudaStream_t st) {
+    const int ns = A.rs.ns_max;
+    if (ns <= 32) return launch_rank_lazy_t<1, UNIFORM, GRID>(A, R, n_obj4, max_b, st);
+    if (ns <= 64) return launch_rank_lazy_t<2, UNIFORM, GRID>(A, R, n_obj4, max_b, st);
+    if (ns <= 128) return launch_rank_lazy_t<4, UNIFORM, GRID>(A, R, n_obj4, max_b, st);
+    return launch_rank_lazy_t<8, UNIFORM, GRID>(A, R, n_obj4, max_b, st);
 }
 
 template <int SPL, bool UNIFORM, bool GRID>
@@ -487,6 +656,16 @@ void launch_contacts(const RobotParams& R, const RobotDev& rd, const SceneDev& s
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_contacts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int64_t blocks = (C + kContactTile - 1) / kContactTile;
     k_contacts<<<(unsigned)blocks, 256, smem, st>>>(R, rd, sc, perm, C, th, ld, touched);
+}
+
+bool launch_rank_lazy(const CollideArgs& A, const RankArgs& R, int max_b, cudaStream_t st) {
+    if (R.T <= 0 || A.rs.ns_max <= 0 || !R.tg || !R.qe_off) return false;
+    const bool uni = A.uniform && A.rs.n == 1 && A.n_scenes <= 1 && A.max_obj4 <= kMaxStagedObj4;
+    const int n4 = A.n_scenes == 1 ? A.max_obj4 : 0;
+    if (uni && A.has_grid) return launch_rank_lazy_s<true, true>(A, R, n4, max_b, st);
+    if (uni) return launch_rank_lazy_s<true, false>(A, R, n4, max_b, st);
+    if (A.has_grid) return launch_rank_lazy_s<false, true>(A, R, 0, max_b, st);
+    return launch_rank_lazy_s<false, false>(A, R, 0, max_b, st);
 }
 
 // One robot and one scene (or none) for every candidate, with the scene small

@@ -14,37 +14,6 @@ namespace hjcd {
 namespace {
 
 constexpr int kSelThreads = 512;
-constexpr uint64_t kNoKey = ~0ull;
-
-__device__ __forceinline__ uint64_t score_key(float s, uint32_t idx) {
-    if (!(s == s)) return kNoKey;  // NaN
-    const uint32_t bits = __float_as_uint(s + 0.0f);  // -0 -> +0
-    return ((uint64_t)bits << 32) | idx;
-}
-
-__device__ void bitonic_sort(uint64_t* keys, int N) {
-    for (int size = 2; size <= N; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = threadIdx.x; i < (N >> 1); i += blockDim.x) {
-                const int lo = 2 * i - (i & (stride - 1));
-                const int hi = lo + stride;
-                const bool up = (lo & size) == 0;
-                const uint64_t a = keys[lo], b = keys[hi];
-                if ((a > b) == up) {
-                    keys[lo] = b;
-                    keys[hi] = a;
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
-
-__device__ __forceinline__ int pow2_at_least(int m) {
-    int N = 1;
-    while (N < m) N <<= 1;
-    return N;
-}
 
 __global__ void __launch_bounds__(kSelThreads) k_topk_dup(const DupArgs A) {
     extern __shared__ uint64_t keys[];
@@ -91,36 +60,7 @@ __global__ void __launch_bounds__(kSelThreads) k_rank(const RankArgs A) {
         const int N = pow2_at_least(B);
         const int n = A.rs.rp[A.tg ? A.tg[t].robot : 0].n;
         const int tk = A.tg ? A.tg[t].top_k : A.top_k;
-        const bool nearest = A.q_ref && (tk & kNearestFlag);
-        float ep = 0.0f, eo = 0.0f;
-        if (nearest) {
-            ep = A.tg[t].eps_pos;
-            eo = A.tg[t].eps_ori;
-        }
-        for (int i = threadIdx.x; i < N; i += blockDim.x) {
-            uint64_t k = kNoKey;
-            if (i < B && !(A.hit && A.hit[b0 + i])) {
-                const float sc = A.score[b0 + i];
-                if (sc < __int_as_float(0x7f800000)) {  // finite only
-                    k = score_key(sc, (uint32_t)i);
-                    if (nearest) {
-                        // class bit 63: 0 = within tolerances (keyed by distance), 1 = the rest (by score)
-                        const int64_t g = b0 + i;
-                        if (A.perr[g] <= ep && A.oerr[g] <= eo) {
-                            float d2 = 0.0f;
-                            for (int j = 0; j < n; ++j) {
-                                const float dj = A.th[j * A.ld + g] - A.q_ref[(int64_t)t * A.ld_ref + j];
-                                d2 = fmaf(dj, dj, d2);
-                            }
-                            k = score_key(d2, (uint32_t)i);
-                        } else {
-                            k |= 1ull << 63;
-                        }
-                    }
-                }
-            }
-            keys[i] = k;
-        }
+        for (int i = threadIdx.x; i < N; i += blockDim.x) keys[i] = rank_key(A, t, b0, B, n, i, true);
         __syncthreads();
         bitonic_sort(keys, N);
         const int top_k = tk & ~kNearestFlag;

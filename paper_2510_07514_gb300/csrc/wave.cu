@@ -300,10 +300,16 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
     if ((st = after_launch(ctx, 1))) return st;
     if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[3], s));
 
-    // collision filter
+    // collision filter and ranking
     const bool collide = W.ns_max > 0;
+    float* q_out = reinterpret_cast<float*>(ws + W.o_q);
+    float* e_out = reinterpret_cast<float*>(ws + W.o_e);
+    int32_t* c_out = reinterpret_cast<int32_t*>(ws + W.o_c);
+    RankArgs ra{rs, d_tg, W.T, d_boff, thB, W.CB, sB, pB, oB, collide ? hB : nullptr, 0,
+                reinterpret_cast<const int64_t*>(ws + W.o_qe), q_out, e_out, c_out,
+                W.has_ref ? reinterpret_cast<const float*>(ws + W.o_ref) : nullptr, W.n_max};
+    CollideArgs cl{};
     if (collide) {
-        CollideArgs cl{};
         cl.rs = rs;
         cl.scenes = reinterpret_cast<const SceneDev*>(ws + W.o_sd);
         cl.n_scenes = W.NS;
@@ -326,20 +332,24 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
         cl.hit = hB;
         cl.cnt = ctx->cnt;
         cl.err_flag = wave_flag(W, ws);
-        launch_collide(cl, s);
+    }
+    // the top_k collision-free candidates by score are the first top_k collision-free ones in score
+    // order: check candidates in that order until they are found (same output as filtering all)
+    bool lazy = false;
+    if (collide && ctx->collide_lazy) {
+        if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[4], s));
+        lazy = launch_rank_lazy(cl, ra, W.max_b, s);
+        if (lazy && (st = after_launch(ctx, 1))) return st;
+    }
+    if (!lazy) {
+        if (collide) {
+            launch_collide(cl, s);
+            if ((st = after_launch(ctx, 1))) return st;
+        }
+        if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[4], s));
+        launch_rank(ra, W.max_b, s);
         if ((st = after_launch(ctx, 1))) return st;
     }
-    if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[4], s));
-
-    // rank the collision-free candidates
-    float* q_out = reinterpret_cast<float*>(ws + W.o_q);
-    float* e_out = reinterpret_cast<float*>(ws + W.o_e);
-    int32_t* c_out = reinterpret_cast<int32_t*>(ws + W.o_c);
-    RankArgs ra{rs, d_tg, W.T, d_boff, thB, W.CB, sB, pB, oB, collide ? hB : nullptr, 0,
-                reinterpret_cast<const int64_t*>(ws + W.o_qe), q_out, e_out, c_out,
-                W.has_ref ? reinterpret_cast<const float*>(ws + W.o_ref) : nullptr, W.n_max};
-    launch_rank(ra, W.max_b, s);
-    if ((st = after_launch(ctx, 1))) return st;
     if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[5], s));
 
     // each request's results to its own buffers

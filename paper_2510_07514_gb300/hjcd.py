@@ -36,7 +36,7 @@ EXPORTS = (
     "hjcd_server_start", "hjcd_server_stop", "hjcd_submit", "hjcd_poll", "hjcd_wait",
     "hjcd_graph_create", "hjcd_graph_launch", "hjcd_graph_check", "hjcd_graph_destroy",
     "hjcd_set_launch_config", "hjcd_autotune", "hjcd_set_memory_budget", "hjcd_scene_contacts",
-    "hjcd_shard_topk", "hjcd_topk_merge", "hjcd_solve_from_topk",
+    "hjcd_shard_topk", "hjcd_topk_merge", "hjcd_solve_from_topk", "hjcd_set_collision_mode",
 )
 
 
@@ -124,6 +124,7 @@ _SIGS = {
     "hjcd_server_start": (_ST, [_V, ct.POINTER(hjcd_server_opts)]),
     "hjcd_set_launch_config": (_ST, [_V, _I32, _I32]),
     "hjcd_set_memory_budget": (_ST, [_V, _U64]),
+    "hjcd_set_collision_mode": (_ST, [_V, _I32]),
     "hjcd_scene_contacts": (_ST, [_V, _I32, _I32, _I64, _V, _I64, _V, _V]),
     "hjcd_shard_topk": (_ST, [_V, _I32, _I, _V, ct.POINTER(hjcd_solve_opts), _I32, _I32, _V, _V, _V, _V]),
     "hjcd_topk_merge": (_ST, [_V, _I, _I, _I, _I, _V, _V, _V, _V, _V, _V, _V]),
@@ -301,6 +302,11 @@ def hjcd_solve_from_topk(ctx, robot_id, scene_id, n_targets, targets_pq, opts, k
     _check(ctx, load().hjcd_solve_from_topk(ctx, int(robot_id), int(scene_id), int(n_targets), ptr(targets_pq),
                                             ct.byref(opts), ptr(kept_theta), ptr(out_q), ptr(out_err),
                                             ptr(out_count), stream_handle(stream)))
+
+
+def hjcd_set_collision_mode(ctx, mode: int) -> None:
+    """1: collision-check candidates in rank order until top_k are found (default); 0: check all."""
+    _check(ctx, load().hjcd_set_collision_mode(ctx, int(mode)))
 
 
 def hjcd_set_memory_budget(ctx, nbytes: int) -> None:

@@ -218,3 +218,50 @@ def test_dof_scaling_variants_match_the_oracle(ctx, dof):
     so = (o["count"] > 0) & (o["err"][:, 0, 0] <= 1e-3) & (o["err"][:, 0, 1] <= 1e-2)
     assert abs(succ.mean() - so.mean()) <= 1 / 32 + 1e-12
     assert succ.mean() > 0.9
+
+
+@pytest.mark.parametrize("dense", [False, True])
+def test_ranked_collision_filter_equals_filtering_every_candidate(ctx, dense):
+    """Collision mode 1 (check candidates in rank order until top_k are
+    collision-free) returns exactly what mode 0 (check all, then rank)
+    returns -- also in a dense scene where the best candidates often collide,
+    and in a mixed batch -- with far fewer sphere tests."""
+    wl = inputs.cfg2(60, 512)
+    rob = wl.robot
+    rng = np.random.default_rng(95)
+    sc = inputs.random_scene(rng, 900 if dense else 200, 60 if dense else 20)
+    rid, sid = ctx.add_robot(rob), ctx.set_scene(sc)
+    # sparse scene: targets at configurations clear of it, so most targets find top_k
+    # collision-free solutions early; dense scene: any configurations, so many run out
+    orob = orc.Robot(rob)
+    pool = f32(wl.theta_gen)
+    if not dense:
+        hit, _ = orc.collide(orob, orc.Scene(sc), pool)
+        pool = pool[~hit]
+    tg = torch.as_tensor(f32(orc.pose(orob, pool[:60])), dtype=torch.float32, device="cuda")
+    outs, tests = [], []
+    try:
+        for mode in (0, 1):
+            hjcd.hjcd_set_collision_mode(ctx.h, mode)
+            hjcd.hjcd_counters(ctx.h, reset=True)
+            outs.append([host(x) for x in ctx.solve(rid, sid, tg, 512, 8, 21, 7)])
+            tests.append(hjcd.hjcd_counters(ctx.h, reset=True)[3])
+            it1, o1 = ctx.batch_item(rid, sid, tg[:30], 512, 3, 22, 7)
+            it2, o2 = ctx.batch_item(rid, -1, tg[30:], 256, 2, 23, 7, spheres=sc.sph_xyzr[:100])
+            ctx.solve_batch([it1, it2])
+            outs.append([host(x) for x in o1] + [host(x) for x in o2])
+    finally:
+        hjcd.hjcd_set_collision_mode(ctx.h, 1)
+    for a, b in ((outs[0], outs[2]), (outs[1], outs[3])):
+        for k in range(0, len(a), 3):
+            qa, ea, ca = a[k:k + 3]
+            qb, eb, cb = b[k:k + 3]
+            assert np.array_equal(ca, cb)
+            for t in range(len(ca)):
+                assert np.array_equal(qa[t, :ca[t]], qb[t, :cb[t]])
+                assert np.array_equal(ea[t, :ca[t]], eb[t, :cb[t]])
+    assert tests[1] <= tests[0]
+    if not dense:
+        assert tests[1] < tests[0] / 4
+    if dense:
+        assert np.mean(outs[0][2] < 8) > 0.2  # many targets lack 8 collision-free solutions: rounds run out
