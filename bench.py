@@ -321,7 +321,9 @@ def uneven_leg(ctx, args, dev, stream):
         wall = {"direct": [], "graph": []}
         for _ in range(args.uneven_steps):
             t0 = time.perf_counter()
+            l0 = hjcd.hjcd_launch_count(ctx.h)
             ctx.solve_batch(items, stream=stream)
+            launches_step = hjcd.hjcd_launch_count(ctx.h) - l0
             torch.cuda.synchronize(dev)
             wall["direct"].append(time.perf_counter() - t0)
             t0 = time.perf_counter()
@@ -374,7 +376,7 @@ def uneven_leg(ctx, args, dev, stream):
             "collision_free_fraction_of_samples": accept,
             "wall_ms_direct": 1e3 * float(np.median(wall["direct"])),
             "wall_ms_graph_replay": 1e3 * float(np.median(wall["graph"])),
-            "launches_per_step": 6, "autotuned": tuned_line}
+            "launches_per_step": int(launches_step), "autotuned": tuned_line}
 
 
 def large_leg(ctx, args, dev, stream):

@@ -20,6 +20,7 @@ struct hjcd_graph {
     cudaGraph_t g = nullptr;
     cudaGraphExec_t x = nullptr;
     cudaEvent_t done = nullptr;
+    int64_t kernels = 0;  // kernel launches of one replay
 };
 
 using namespace hjcd;
@@ -127,7 +128,10 @@ hjcd_status hjcd_graph_create(hjcd_ctx* ctx, int n_items, const hjcd_batch_item*
         release(G);
         return fail(ctx, HJCD_ECUDA, "graph capture: %s", cudaGetErrorString(e));
     }
+    const int64_t k0 = ctx->launches.load();
     st = run_wave(ctx, W, G->items.data(), P, G->ws, G->pin, G->s, nullptr);
+    G->kernels = ctx->launches.load() - k0;
+    ctx->launches -= G->kernels;  // captured, not launched
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(G->s, &g);
     G->g = g;
@@ -154,7 +158,7 @@ hjcd_status hjcd_graph_launch(hjcd_graph* G, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     HJCD_CUDA(ctx, cudaGraphLaunch(G->x, s));
     HJCD_CUDA(ctx, cudaEventRecord(G->done, s));
-    ctx->launches += G->plan.ns_max > 0 ? 6 : 5;
+    ctx->launches += G->kernels;
     return HJCD_OK;
 }
 

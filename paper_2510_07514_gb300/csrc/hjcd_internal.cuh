@@ -507,6 +507,10 @@ struct RankArgs {
     // distance), then the others by score
     const float* q_ref;
     int32_t ld_ref;
+    // with list set: block b ranks target list[b] when b < *n_list, else nothing (the targets
+    // that the bounded lazy pass left unfinished); k_rank_lazy appends those targets here
+    int32_t* list;
+    int32_t* n_list;
 };
 
 // Ranking key of candidate i of target t (candidates [b0, b0 + B), robot DoF
@@ -557,6 +561,13 @@ struct CollideArgs {
     uint8_t* hit;
     Counters* cnt;
     int32_t* err_flag;        // set when the bounded wait for the staged tables runs out
+    // with list set: only the candidates of the targets list[0 .. *n_list) whose hit entry is 2
+    // are checked, item i = (list entry i / list_bmax, candidate i % list_bmax of that target's
+    // b_off range)
+    const int32_t* list;
+    const int32_t* n_list;
+    const int64_t* b_off;
+    int32_t list_bmax;
 };
 
 // Fill p and q of the target rows from [T][7] poses (quaternion normalised; a
@@ -620,8 +631,11 @@ void launch_rank(const RankArgs& A, int max_b, cudaStream_t st);
 void launch_collide(const CollideArgs& A, cudaStream_t st);
 // The ranking with the collision filter applied lazily (k_rank_lazy); false
 // when it does not apply (no spheres, no target rows, or too large for shared
-// memory): use launch_collide + launch_rank.
-bool launch_rank_lazy(const CollideArgs& A, const RankArgs& R, int max_b, cudaStream_t st);
+// memory): use launch_collide + launch_rank.  With R.list set, a target whose
+// first `depth` ranked candidates hold fewer than top_k collision-free ones is
+// appended to R.list instead of ranked; launch_collide and launch_rank with
+// that list finish those targets.
+bool launch_rank_lazy(const CollideArgs& A, const RankArgs& R, int max_b, int depth, cudaStream_t st);
 void launch_contacts(const RobotParams& R, const RobotDev& rd, const SceneDev& sc, const int32_t* perm, int64_t C,
                      const float* th, int64_t ld, uint8_t* touched, cudaStream_t st);
 void launch_ffma(float* sink, int iters, int blocks, cudaStream_t st);

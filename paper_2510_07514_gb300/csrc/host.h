@@ -19,6 +19,7 @@ namespace hjcd {
 
 constexpr int kMaxSceneFloat4 = 1 << 20;  // resident scene: obstacle spheres + 2 * boxes
 constexpr int kGridMinSpheres = 512;      // resident scenes with this many spheres get a uniform grid
+constexpr int kLazyDepth = 64;            // ranked candidates a target's CTA checks before it hands over
 
 // Resident robot: the kinematic table (host copy) and one device buffer with
 // the kinematic table, the collision-table descriptor and the collision
@@ -160,7 +161,7 @@ struct WavePlan {
            head = 0;
     // the rest of the workspace
     size_t o_thM = 0, o_thM2 = 0, o_sM = 0, o_thB = 0, o_sB = 0, o_pB = 0, o_oB = 0, o_hB = 0, o_q = 0, o_e = 0, o_c = 0,
-           o_qf = 0, bytes = 0;
+           o_ul = 0, o_qf = 0, bytes = 0;
     bool host_out = false;  // some output goes to host memory
 };
 

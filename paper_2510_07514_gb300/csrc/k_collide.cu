@@ -417,6 +417,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
         if (threadIdx.x == 0) atomicExch(A.err_flag, 2);
         return;
     }
+    // list mode: the candidates of the listed targets only (none listed: nothing to stage)
+    const int64_t items = A.list ? (int64_t)*A.n_list * A.list_bmax : A.C;
+    if (items == 0) return;
     const CollideLayout L = collide_smem_layout(n_obj4, A.rs.n, A.rs.n_max + 2, A.rs.ns_max, A.rs.pairs_max);
     const RobotParams* rob;
     if (!collide_prologue<UNIFORM>(A, smem, L, sc0, n_obj4, &rob)) return;
@@ -431,7 +434,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
     const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
     int rid = 0, sid = 0;
     bool tvalid = true;
-    for (int64_t c = (int64_t)blockIdx.x * kWarpsPerBlock + warp; c < A.C; c += nwarps) {
+    for (int64_t it = (int64_t)blockIdx.x * kWarpsPerBlock + warp; it < items; it += nwarps) {
+        int64_t c = it;
+        if (A.list) {
+            const int t = A.list[it / A.list_bmax];
+            const int j = (int)(it % A.list_bmax);
+            const int64_t b0 = A.b_off[t];
+            if (j >= A.b_off[t + 1] - b0 || A.hit[b0 + j] != 2) continue;  // not ranked, or checked
+            c = b0 + j;
+        }
         if (!UNIFORM && A.tg) {
             int32_t t, s;
             tvalid = A.map.lookup(c, t, s);
@@ -474,7 +485,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_collide(const CollideAr
 // by k_rank.
 template <int SPL, bool UNIFORM, bool GRID>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rank_lazy(const CollideArgs A, const RankArgs R,
-                                                                  uint32_t keys_off) {
+                                                                  uint32_t keys_off, int depth) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int verdict[kWarpsPerBlock];
     __shared__ int picks[HJCD_MAX_TOPK];
@@ -515,7 +526,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rank_lazy(const Collide
     unsigned long long tests = 0, btests = 0, ncand = 0;
     if (threadIdx.x == 0) n_found = 0;
     __syncthreads();
-    for (int p0 = 0; p0 < ranked && n_found < top_k; p0 += kWarpsPerBlock) {
+    int p0 = 0;
+    for (; p0 < ranked && n_found < top_k && (!R.list || p0 < depth); p0 += kWarpsPerBlock) {
         const int p = p0 + warp;
         bool hit = true;
         if (p < ranked) {
@@ -539,6 +551,26 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rank_lazy(const Collide
         __syncthreads();
     }
     const int count = n_found;
+    if (A.cnt && lane == 0) {
+        atomicAdd(&A.cnt->v[3], tests);
+        atomicAdd(&A.cnt->v[6], btests);
+        atomicAdd(&A.cnt->v[4], ncand);
+    }
+    if (R.list && count < top_k && p0 < ranked) {
+        // deeper than the bound: the verdicts taken so far are kept (0 free, 1 colliding), the
+        // unchecked ranked candidates marked 2 for the collision filter over the listed targets,
+        // which spreads them over every SM; the ranking of the listed targets follows it
+        for (int q = threadIdx.x; q < ranked; q += blockDim.x) {
+            uint8_t v = 2;
+            if (q < p0) {
+                v = 1;
+                for (int r = 0; r < count; ++r) v = picks[r] == q ? 0 : v;
+            }
+            A.hit[b0 + (int64_t)(keys[q] & 0xffffffffu)] = v;
+        }
+        if (threadIdx.x == 0) R.list[atomicAdd(R.n_list, 1)] = t;
+        return;
+    }
     float* oq = R.out_q + R.qe_off[2 * t];
     float* oe = R.out_err + R.qe_off[2 * t + 1];
     for (int q = threadIdx.x; q < count * (n + 2); q += blockDim.x) {
@@ -549,15 +581,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rank_lazy(const Collide
         else oe[r * 2 + 1] = R.oerr[g];
     }
     if (threadIdx.x == 0) R.out_count[t] = count;
-    if (A.cnt && lane == 0) {
-        atomicAdd(&A.cnt->v[3], tests);
-        atomicAdd(&A.cnt->v[6], btests);
-        atomicAdd(&A.cnt->v[4], ncand);
-    }
 }
 
 template <int SPL, bool UNIFORM, bool GRID>
-bool launch_rank_lazy_t(const CollideArgs& A, const RankArgs& R, int n_obj4, int max_b, cudaStream_t st) {
+bool launch_rank_lazy_t(const CollideArgs& A, const RankArgs& R, int n_obj4, int max_b, int depth, cudaStream_t st) {
     const CollideLayout L =
         collide_smem_layout(UNIFORM ? n_obj4 : 0, A.rs.n, A.rs.n_max + 2, A.rs.ns_max, A.rs.pairs_max);
     const uint32_t keys_off = (L.total + 15u) / 16u * 16u;
@@ -571,17 +598,17 @@ bool launch_rank_lazy_t(const CollideArgs& A, const RankArgs& R, int n_obj4, int
                              220 * 1024);
         attr_set = true;
     }
-    k_rank_lazy<SPL, UNIFORM, GRID><<<R.T, kWarpsPerBlock * 32, smem, st>>>(A, R, keys_off);
+    k_rank_lazy<SPL, UNIFORM, GRID><<<R.T, kWarpsPerBlock * 32, smem, st>>>(A, R, keys_off, depth);
     return true;
 }
 
 template <bool UNIFORM, bool GRID>
-bool launch_rank_lazy_s(const CollideArgs& A, const RankArgs& R, int n_obj4, int max_b, cudaStream_t st) {
+bool launch_rank_lazy_s(const CollideArgs& A, const RankArgs& R, int n_obj4, int max_b, int depth, cudaStream_t st) {
     const int ns = A.rs.ns_max;
-    if (ns <= 32) return launch_rank_lazy_t<1, UNIFORM, GRID>(A, R, n_obj4, max_b, st);
-    if (ns <= 64) return launch_rank_lazy_t<2, UNIFORM, GRID>(A, R, n_obj4, max_b, st);
-    if (ns <= 128) return launch_rank_lazy_t<4, UNIFORM, GRID>(A, R, n_obj4, max_b, st);
-    return launch_rank_lazy_t<8, UNIFORM, GRID>(A, R, n_obj4, max_b, st);
+    if (ns <= 32) return launch_rank_lazy_t<1, UNIFORM, GRID>(A, R, n_obj4, max_b, depth, st);
+    if (ns <= 64) return launch_rank_lazy_t<2, UNIFORM, GRID>(A, R, n_obj4, max_b, depth, st);
+    if (ns <= 128) return launch_rank_lazy_t<4, UNIFORM, GRID>(A, R, n_obj4, max_b, depth, st);
+    return launch_rank_lazy_t<8, UNIFORM, GRID>(A, R, n_obj4, max_b, depth, st);
 }
 
 template <int SPL, bool UNIFORM, bool GRID>
@@ -658,14 +685,14 @@ void launch_contacts(const RobotParams& R, const RobotDev& rd, const SceneDev& s
     k_contacts<<<(unsigned)blocks, 256, smem, st>>>(R, rd, sc, perm, C, th, ld, touched);
 }
 
-bool launch_rank_lazy(const CollideArgs& A, const RankArgs& R, int max_b, cudaStream_t st) {
+bool launch_rank_lazy(const CollideArgs& A, const RankArgs& R, int max_b, int depth, cudaStream_t st) {
     if (R.T <= 0 || A.rs.ns_max <= 0 || !R.tg || !R.qe_off) return false;
     const bool uni = A.uniform && A.rs.n == 1 && A.n_scenes <= 1 && A.max_obj4 <= kMaxStagedObj4;
     const int n4 = A.n_scenes == 1 ? A.max_obj4 : 0;
-    if (uni && A.has_grid) return launch_rank_lazy_s<true, true>(A, R, n4, max_b, st);
-    if (uni) return launch_rank_lazy_s<true, false>(A, R, n4, max_b, st);
-    if (A.has_grid) return launch_rank_lazy_s<false, true>(A, R, 0, max_b, st);
-    return launch_rank_lazy_s<false, false>(A, R, 0, max_b, st);
+    if (uni && A.has_grid) return launch_rank_lazy_s<true, true>(A, R, n4, max_b, depth, st);
+    if (uni) return launch_rank_lazy_s<true, false>(A, R, n4, max_b, depth, st);
+    if (A.has_grid) return launch_rank_lazy_s<false, true>(A, R, 0, max_b, depth, st);
+    return launch_rank_lazy_s<false, false>(A, R, 0, max_b, depth, st);
 }
 
 // One robot and one scene (or none) for every candidate, with the scene small

@@ -52,7 +52,11 @@ __global__ void __launch_bounds__(kSelThreads) k_topk_dup(const DupArgs A) {
 
 __global__ void __launch_bounds__(kSelThreads) k_rank(const RankArgs A) {
     extern __shared__ uint64_t keys[];
-    const int t = blockIdx.x;
+    int t = blockIdx.x;
+    if (A.list) {  // the targets the bounded lazy pass left unfinished
+        if (t >= *A.n_list) return;
+        t = A.list[t];
+    }
     const int64_t b0 = A.b_off[t];
     const int B = (int)(A.b_off[t + 1] - b0);
     int count = 0;

@@ -145,7 +145,8 @@ hjcd_status plan_wave(hjcd_ctx* ctx, const WaveItem* items, int n_items, const h
     W.o_q = cv.take<float>(W.q_total);
     W.o_e = cv.take<float>(W.e_total);
     W.o_c = cv.take<int32_t>(W.T);
-    W.o_qf = cv.take<unsigned long long>(2);  // queue head, error flag
+    W.o_ul = cv.take<int32_t>(W.T);           // targets left to the second collision pass
+    W.o_qf = cv.take<unsigned long long>(2);  // queue head, error flag, count of o_ul
     W.bytes = cv.off;
     return HJCD_OK;
 }
@@ -335,11 +336,29 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
     }
     // the top_k collision-free candidates by score are the first top_k collision-free ones in score
     // order: check candidates in that order until they are found (same output as filtering all)
+    // A target whose first kLazyDepth ranked candidates hold fewer than top_k collision-free ones
+    // (a cluttered scene) would keep one CTA busy for its whole list while the other SMs idle: it
+    // is listed instead, and the filter over the listed targets' candidates and their ranking
+    // follow as two grid-wide launches.
     bool lazy = false;
     if (collide && ctx->collide_lazy) {
         if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[4], s));
-        lazy = launch_rank_lazy(cl, ra, W.max_b, s);
-        if (lazy && (st = after_launch(ctx, 1))) return st;
+        RankArgs rl = ra;
+        rl.list = reinterpret_cast<int32_t*>(ws + W.o_ul);
+        rl.n_list = reinterpret_cast<int32_t*>(ws + W.o_qf + 12);
+        lazy = launch_rank_lazy(cl, rl, W.max_b, kLazyDepth, s);
+        if (lazy) {
+            if ((st = after_launch(ctx, 1))) return st;
+            CollideArgs c2 = cl;
+            c2.list = rl.list;
+            c2.n_list = rl.n_list;
+            c2.b_off = d_boff;
+            c2.list_bmax = std::max(W.max_b, 1);
+            launch_collide(c2, s);
+            if ((st = after_launch(ctx, 1))) return st;
+            launch_rank(rl, W.max_b, s);
+            if ((st = after_launch(ctx, 1))) return st;
+        }
     }
     if (!lazy) {
         if (collide) {

@@ -260,7 +260,7 @@ def test_ranked_collision_filter_equals_filtering_every_candidate(ctx, dense):
             for t in range(len(ca)):
                 assert np.array_equal(qa[t, :ca[t]], qb[t, :cb[t]])
                 assert np.array_equal(ea[t, :ca[t]], eb[t, :cb[t]])
-    assert tests[1] <= tests[0]
+    assert tests[1] <= tests[0]  # a candidate is checked at most once
     if not dense:
         assert tests[1] < tests[0] / 4
     if dense:
