@@ -178,6 +178,7 @@ def flops_fk_trial(n):
     return 56 * n + 166
 
 
+FLOPS_COORD_TRIAL = 108  # PJ-IK single-coordinate trial in closed form (rotation about one axis)
 FLOPS_SPHERE_TEST = 10
 FLOPS_BOX_TEST = 8
 
@@ -743,7 +744,8 @@ def hjcd_arm(args):
     n_sph = len(rob.sph_body)
     fl = {
         "po_ccd": cnt[0] / steps * flops_ccd_iter(n),
-        "pjik": cnt[1] / steps * flops_lm_iter(n) + (cnt[2] - cnt[1]) / steps * flops_fk_trial(n),
+        "pjik": cnt[1] / steps * flops_lm_iter(n) + (cnt[2] - cnt[1]) / steps * flops_fk_trial(n)
+                + cnt[7] / steps * FLOPS_COORD_TRIAL,
         "collide": (cnt[3] * FLOPS_SPHERE_TEST + cnt[6] * FLOPS_BOX_TEST) / steps
                    + cnt[4] / steps * flops_collide_cand(n, n_sph),
     }
@@ -777,6 +779,7 @@ def hjcd_arm(args):
         "phase_ms": {nm: float(v) for nm, v in zip(names + ["step"], ph_raw)},
         "phase_note": "with the ranked collision filter (default) the collision checks run in the rank phase",
         "work_per_step": {"ccd_iters": cnt[0] / steps, "lm_iters": cnt[1] / steps, "lm_fk_passes": cnt[2] / steps,
+                          "lm_coord_trials": cnt[7] / steps,
                           "sphere_tests": cnt[3] / steps, "box_tests": cnt[6] / steps,
                           "collide_candidates": cnt[4] / steps},
         "roofline": roof, "ffma_probe_tflops": ffma,

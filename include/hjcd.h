@@ -465,10 +465,12 @@ hjcd_status hjcd_set_profiling(hjcd_ctx* ctx, int on);
 hjcd_status hjcd_phase_times(hjcd_ctx* ctx, float ms[6]);
 /* Work counters accumulated by the kernels since the last reset:
  * [0] PO-CCD iterations, [1] PJ-IK iterations, [2] forward-kinematics passes
- * inside PJ-IK (frames + line-search/dogleg trials), [3] sphere-sphere tests
- * executed by the collision kernel (self pairs and obstacle spheres), [4]
- * candidates checked for collision, [5] PO-CCD candidates, [6] sphere-box
- * tests.  Synchronises the device; ETIMEOUT when a bounded device wait ran
+ * inside PJ-IK (frames, full-step, line-search and dogleg trials, counted as
+ * the sequential method takes them), [3] sphere-sphere tests executed by the
+ * collision kernel (self pairs and obstacle spheres), [4] candidates checked
+ * for collision, [5] PO-CCD candidates, [6] sphere-box tests, [7] PJ-IK
+ * single-coordinate trials (evaluated in closed form, without a kinematics
+ * pass).  Synchronises the device; ETIMEOUT when a bounded device wait ran
  * out since the context was created. */
 hjcd_status hjcd_counters(hjcd_ctx* ctx, uint64_t out[8], int reset);
 /* Kernel launches issued by this context since creation. */

@@ -14,14 +14,25 @@
 // (Eq. single-coord) with the same line search, and finally a random
 // perturbation.
 //
-// Mapping.  Each lane of a warp owns one candidate at a time and takes the
-// next one from a global queue when its candidate finishes, so lanes never
-// idle while work remains.  Line-search trials are where candidates diverge
-// (a failing candidate needs up to 2(A+1)+1 extra kinematics passes), so only
-// the full-step trial is evaluated by its owner; the remaining trials of all
-// failing lanes of the warp are spread over the 32 lanes (each trial is an
-// independent kinematics pass), and each owner then takes the first trial
-// that lowered its cost -- the same step the sequential search accepts.
+// Mapping.  Each lane of a warp owns one candidate (a slot of per-lane state)
+// at a time and takes the next one from a global queue when its candidate
+// finishes, so lanes never idle while work remains.  The full-step trial is
+// evaluated by each owner.  The failure path is where candidates diverge (a
+// third or more of the iterations fail the full step, and such a candidate
+// needs up to 2(A+1) more trials), so the warps of a CTA iterate in lock step
+// and the failing slots of all of them are compacted into one list that all
+// the CTA's threads work through: each failing slot's dogleg and
+// single-coordinate steps (whether or not a shorter step will succeed), then
+// its remaining line-search trials and the dogleg trial as independent
+// kinematics passes, one per thread, then per slot the first of them, in the
+// order of Alg. 4, that lowered its cost -- the step the sequential method
+// accepts.  Failing those, the single-coordinate line search runs in closed
+// form: turning one joint by x about its axis z moves the end effector by
+// (1 - cos x) (v x z) + sin x v, with v = z x (p_ee - p_j) the joint's
+// Jacobian column, and composes the orientation error with the half-angle
+// quaternion [cos x/2, -sin x/2 z], so each of its trials costs a handful of
+// operations instead of a kinematics pass.  The perturbation's normal pairs of
+// the slots that found no step are spread over the CTA as well.
 // Per-lane state (joint vector, trial direction, weighted Jacobian, W, W r,
 // cost, target row, trial outcomes) lives in shared memory as structure of
 // arrays over the lanes, laid out for the largest chain of the launch; joint
@@ -38,30 +49,50 @@ namespace hjcd {
 namespace {
 
 constexpr int kLmWarps = 4;  // default warps per CTA; 2 and 8 also built
-constexpr int kMaxTrials = 32;  // A + 1 <= 32 (validated by the host)
+constexpr int kMaxLsDepth = 31;  // A (validated by the host)
 
 __host__ __device__ constexpr int tri(int r, int c) { return r * (r + 1) / 2 + c; }
 
-// words of per-warp shared state for an n-joint chain
-__host__ __device__ constexpr int lm_warp_words(int n) { return (8 * n + 14) * 32 + kMaxTrials * 32 / 4 + 32; }
+// words of per-warp shared state for an n-joint chain and line-search depth A
+// W[6], b[6], cost0, t, s, kk, sc_j, sc_step, e[3], q_err[4], sc_z[3], sc_v[3], branch, alpha
+constexpr int kLmScalars = 33;
+__host__ __device__ constexpr int lm_warp_words(int n, int A) { return (8 * n + kLmScalars) * 32 + (A + 1) * 8; }
+
+// trial directions: the LM (or line-search) direction d, the dogleg step d2,
+// the single coordinate (joint sc_j by sc_step)
+enum TrialKind { kDirLm = 0, kDirDogleg = 1 };
 
 // Per-warp state, field[...][lane] (each lane's own accesses conflict-free);
-// n is the layout's chain length (the launch's largest).
+// n is the layout's chain length (the launch's largest).  The dogleg step d2
+// shares its words with row 0 of the weighted Jacobian: it is written column
+// by column after that column's last read, and the Jacobian is not read again
+// before the next iteration rebuilds it.
 struct LmW {
     float* f;
     int n;
     __device__ __forceinline__ float& th(int j, int l) const { return f[j * 32 + l]; }
     __device__ __forceinline__ float& d(int j, int l) const { return f[(n + j) * 32 + l]; }
     __device__ __forceinline__ float& jw(int r, int i, int l) const { return f[(2 * n + r * n + i) * 32 + l]; }
+    __device__ __forceinline__ float& d2(int j, int l) const { return jw(0, j, l); }
     __device__ __forceinline__ float& W(int r, int l) const { return f[(8 * n + r) * 32 + l]; }
     __device__ __forceinline__ float& b(int r, int l) const { return f[(8 * n + 6 + r) * 32 + l]; }
     __device__ __forceinline__ float& cost0(int l) const { return f[(8 * n + 12) * 32 + l]; }
     __device__ __forceinline__ int& t(int l) const { return reinterpret_cast<int*>(f)[(8 * n + 13) * 32 + l]; }
+    __device__ __forceinline__ int& s(int l) const { return reinterpret_cast<int*>(f)[(8 * n + 14) * 32 + l]; }
+    __device__ __forceinline__ int& kk(int l) const { return reinterpret_cast<int*>(f)[(8 * n + 15) * 32 + l]; }
+    __device__ __forceinline__ int& sc_j(int l) const { return reinterpret_cast<int*>(f)[(8 * n + 16) * 32 + l]; }
+    __device__ __forceinline__ float& sc_step(int l) const { return f[(8 * n + 17) * 32 + l]; }
+    // position error and error quaternion at the iteration's configuration; the single
+    // coordinate's axis and position Jacobian column (unweighted)
+    __device__ __forceinline__ float& e(int r, int l) const { return f[(8 * n + 18 + r) * 32 + l]; }
+    __device__ __forceinline__ float& qe(int r, int l) const { return f[(8 * n + 21 + r) * 32 + l]; }
+    __device__ __forceinline__ float& sc_z(int r, int l) const { return f[(8 * n + 25 + r) * 32 + l]; }
+    __device__ __forceinline__ float& sc_v(int r, int l) const { return f[(8 * n + 28 + r) * 32 + l]; }
+    // the failure path's outcome for the owner: Alg. 4 branch and accepted alpha
+    __device__ __forceinline__ int& br(int l) const { return reinterpret_cast<int*>(f)[(8 * n + 31) * 32 + l]; }
+    __device__ __forceinline__ float& al(int l) const { return f[(8 * n + 32) * 32 + l]; }
     __device__ __forceinline__ uint8_t& ok(int i, int l) const {
-        return reinterpret_cast<uint8_t*>(f + (8 * n + 14) * 32)[i * 32 + l];
-    }
-    __device__ __forceinline__ int& list(int l) const {
-        return reinterpret_cast<int*>(f + (8 * n + 14) * 32 + kMaxTrials * 32 / 4)[l];
+        return reinterpret_cast<uint8_t*>(f + (8 * n + kLmScalars) * 32)[i * 32 + l];
     }
 };
 
@@ -119,11 +150,10 @@ struct Y6 {
 };
 
 // Solve M y = b with M the 6 x 6 sum over the joints of col col^T plus reg I,
-// for lane l's weighted Jacobian columns.  lm: the columns are first weighted
-// by the rows' W (and stored back, so the smem Jacobian becomes W J) and then
-// scaled to unit length (S = D^-1/2 of the push-through LM step); otherwise
-// they are used as stored (the dogleg's Gauss-Newton system on W J).
-__device__ __noinline__ Y6 normal_solve(const LmW S, int l, int n, bool lm, float reg, Y6 w, Y6 b) {
+// for lane l's Jacobian columns, each first weighted by the rows' W (and
+// stored back, so the smem Jacobian becomes W J) and then scaled to unit
+// length (S = D^-1/2 of the push-through LM step).
+__device__ __noinline__ Y6 normal_solve(const LmW S, int l, int n, float reg, Y6 w, Y6 b) {
     float M[21], inv[6];
 #pragma unroll
     for (int q = 0; q < 21; ++q) M[q] = 0.0f;
@@ -132,18 +162,13 @@ __device__ __noinline__ Y6 normal_solve(const LmW S, int l, int n, bool lm, floa
         float col[6], dd = 1e-9f;
 #pragma unroll
         for (int r = 0; r < 6; ++r) {
-            col[r] = S.jw(r, i, l);
-            if (lm) {
-                col[r] *= w.v[r];
-                S.jw(r, i, l) = col[r];
-                dd = fmaf(col[r], col[r], dd);
-            }
+            col[r] = S.jw(r, i, l) * w.v[r];
+            S.jw(r, i, l) = col[r];
+            dd = fmaf(col[r], col[r], dd);
         }
-        if (lm) {
-            const float rs = rsqrtf(dd);
+        const float rs = rsqrtf(dd);
 #pragma unroll
-            for (int r = 0; r < 6; ++r) col[r] *= rs;
-        }
+        for (int r = 0; r < 6; ++r) col[r] *= rs;
 #pragma unroll
         for (int r = 0; r < 6; ++r)
 #pragma unroll
@@ -164,18 +189,40 @@ __device__ __forceinline__ float ls_alpha(int i, float beta) {
     return a;
 }
 
-// weighted cost 1/2 |W r|^2 at the trial point clamp(theta + alpha d) of lane s
+// CTA-wide lists of the failure path (after the warps' state): per warp its mask of failing
+// lanes, the failing slots compacted, the slots left to the perturbation and their count.
+template <int WARPS>
+struct LmCta {
+    unsigned* wm;
+    int* fl;
+    int* pl;
+    int* np;
+};
+template <int WARPS>
+__host__ __device__ constexpr int lm_cta_words() { return WARPS + 2 * WARPS * 32 + 1; }
+template <int WARPS>
+__device__ __forceinline__ LmCta<WARPS> lm_cta(float* f) {
+    int* b = reinterpret_cast<int*>(f);
+    return LmCta<WARPS>{reinterpret_cast<unsigned*>(b), b + WARPS, b + WARPS + WARPS * 32, b + WARPS + 2 * WARPS * 32};
+}
+
+// component j of lane s's trial direction of the given kind
+__device__ __forceinline__ float trial_dir(const LmW& S, int s, int kind, int j) {
+    return kind == kDirDogleg ? S.d2(j, s) : S.d(j, s);
+}
+
+// weighted cost 1/2 |W r|^2 at the trial point clamp(theta + alpha dir) of lane s
 // (the kinematics passes, the 6 x 6 solve and the trial spreading each exist
 // once in the kernel, called from every branch that needs them, which keeps
 // the per-iteration body inside the instruction cache)
 __device__ __noinline__ float trial_cost(const RobotParams* rob, const TargetDesc* tg, int row, const LmW S, int s,
-                                        float alpha) {
+                                        float alpha, int kind) {
     const TargetDesc T = tg[row];
     const RobotParams& R = rob[T.robot];
     Frame F = frame_identity();
 #pragma unroll 1
     for (int j = 0; j < R.n; ++j)
-        fk_step(R, j, clampf(fmaf(alpha, S.d(j, s), S.th(j, s)), R.lo[j], R.hi[j]), F);
+        fk_step(R, j, clampf(fmaf(alpha, trial_dir(S, s, kind, j), S.th(j, s)), R.lo[j], R.hi[j]), F);
     const Frame E = fk_flange(R, F);
     const V3 w = quat_log(quat_error(T, quat_from_frame(E)));
     const float e0 = S.W(0, s) * (T.p[0] - E.p.x), e1 = S.W(1, s) * (T.p[1] - E.p.y);
@@ -184,28 +231,154 @@ __device__ __noinline__ float trial_cost(const RobotParams* rob, const TargetDes
     return 0.5f * fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, fmaf(e4, e4, e5 * e5)))));
 }
 
-// theta <- clamp(theta + alpha d) for lane s (the trial point the cost was taken at)
-__device__ __noinline__ void take_step(const RobotParams& R, const LmW S, int s, float alpha) {
+// theta <- clamp(theta + alpha dir) for lane s (the trial point the cost was taken at)
+__device__ __noinline__ void take_step(const RobotParams& R, const LmW S, int s, float alpha, int kind) {
 #pragma unroll 1
-    for (int j = 0; j < R.n; ++j) S.th(j, s) = clampf(fmaf(alpha, S.d(j, s), S.th(j, s)), R.lo[j], R.hi[j]);
+    for (int j = 0; j < R.n; ++j)
+        S.th(j, s) = clampf(fmaf(alpha, trial_dir(S, s, kind, j), S.th(j, s)), R.lo[j], R.hi[j]);
 }
 
-// Trials i = i0 .. A of every lane in `mask`, spread over the warp; results in S.ok(i, lane).
-__device__ __noinline__ unsigned long long warp_trials(const RobotParams* rob, const TargetDesc* tg, const LmW S,
-                                                          unsigned mask, int lane, int i0, int A, float beta) {
-    const int per = A + 1 - i0;
-    if (!mask || per <= 0) return 0;
-    if ((mask >> lane) & 1u) S.list(__popc(mask & ((1u << lane) - 1u))) = lane;
-    __syncwarp();
-    const int items = __popc(mask) * per;
-    unsigned long long cnt = 0;
-    for (int w = lane; w < items; w += 32) {
-        const int s = S.list(w / per), i = i0 + w % per;
-        S.ok(i, s) = trial_cost(rob, tg, S.t(s), S, s, ls_alpha(i, beta)) < S.cost0(s) ? 1 : 0;
-        ++cnt;
+// The kinematics-pass trials that follow a failed full step, in the order Alg. 4
+// takes them: item i < A is the line-search trial alpha = 1/beta^(i+1) along d,
+// item A the dogleg step.
+__device__ __forceinline__ void trial_item(int i, int A, float beta, int* kind, float* alpha) {
+    *kind = i < A ? kDirLm : kDirDogleg;
+    *alpha = i < A ? ls_alpha(i + 1, beta) : 1.0f;
+}
+
+// Weighted cost of lane l's configuration with its single coordinate turned by x (the end
+// effector rotated by x about the joint's axis; see the mapping notes above).
+__device__ __noinline__ float coord_cost(const LmW S, int l, float x) {
+    float sh, ch;
+    sincos_red(0.5f * x, &sh, &ch);
+    const V3 z = v3(S.sc_z(0, l), S.sc_z(1, l), S.sc_z(2, l));
+    const V3 v = v3(S.sc_v(0, l), S.sc_v(1, l), S.sc_v(2, l));
+    const V3 up = cross(v, z);  // component of p_ee - p_j normal to the axis
+    const float a = 2.0f * sh * sh, b = 2.0f * sh * ch;  // 1 - cos x, sin x
+    const V3 e = fma3(a, up, fma3(-b, v, v3(S.e(0, l), S.e(1, l), S.e(2, l))));
+    const Q4 q{S.qe(0, l), v3(S.qe(1, l), S.qe(2, l), S.qe(3, l))};
+    Q4 q2{fmaf(q.w, ch, sh * dot(q.v, z)), fma3(ch, q.v, (-sh) * fma3(q.w, z, cross(q.v, z)))};
+    if (q2.w < 0.0f) {
+        q2.w = -q2.w;
+        q2.v = (-1.0f) * q2.v;
     }
-    __syncwarp();
-    return cnt;
+    const V3 w = quat_log(q2);
+    const float e0 = S.W(0, l) * e.x, e1 = S.W(1, l) * e.y, e2 = S.W(2, l) * e.z;
+    const float e3 = S.W(3, l) * w.x, e4 = S.W(4, l) * w.y, e5 = S.W(5, l) * w.z;
+    return 0.5f * fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, fmaf(e4, e4, e5 * e5)))));
+}
+
+// The dogleg step of Eq. dogleg and the single-coordinate step of Eq. single-coord for lane l,
+// from its weighted Jacobian W J (columns in shared memory) and W r: into S.d2, S.sc_j,
+// S.sc_step.  With M0 = (WJ)(WJ)^T the Gauss-Newton step is (WJ)^T y2, y2 = (M0 + reg I)^-1 W r,
+// and the quantities of the dogleg reduce to 6 x 6 forms: J g = M0 W r, |g|^2 = (W r).M0 W r,
+// |d_gn|^2 = y2.M0 y2; one more pass over the columns forms the step.
+__device__ __noinline__ void dogleg_prepare(const LmW S, int l, int n, float Rt, float gn_reg) {
+    float M0[21], M[21], inv[6], b[6];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) b[r] = S.b(r, l);
+#pragma unroll
+    for (int q = 0; q < 21; ++q) M0[q] = 0.0f;
+#pragma unroll 1
+    for (int i = 0; i < n; ++i) {
+        float col[6];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) col[r] = S.jw(r, i, l);
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+#pragma unroll
+            for (int q = 0; q <= r; ++q) M0[tri(r, q)] = fmaf(col[r], col[q], M0[tri(r, q)]);
+    }
+#pragma unroll
+    for (int q = 0; q < 21; ++q) M[q] = M0[q];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) M[tri(r, r)] += gn_reg;
+    chol6(M, inv);
+    float y2[6];
+    chol6_solve(M, inv, b, y2);
+    // symmetric products with M0
+    float Jg[6], My[6];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+        float a = 0.0f, c = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const float m = r >= q ? M0[tri(r, q)] : M0[tri(q, r)];
+            a = fmaf(m, b[q], a);
+            c = fmaf(m, y2[q], c);
+        }
+        Jg[r] = a;
+        My[r] = c;
+    }
+    float gg = 0.0f, jgjg = 0.0f, ngn2 = 0.0f;
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+        gg = fmaf(b[r], Jg[r], gg);
+        jgjg = fmaf(Jg[r], Jg[r], jgjg);
+        ngn2 = fmaf(y2[r], My[r], ngn2);
+    }
+    const float ac = jgjg > 0.0f ? gg / jgjg : 0.0f;
+    const float ngd2 = ac * ac * gg, R2 = Rt * Rt;
+    float wgn = 1.0f, wgd = 0.0f;  // step = wgn * dgn + wgd * g
+    if (ngn2 <= R2) {
+        wgn = 1.0f;
+        wgd = 0.0f;
+    } else if (ngd2 >= R2) {
+        wgn = 0.0f;
+        wgd = ngd2 > 0.0f ? Rt * rsqrtf(ngd2) * ac : 0.0f;
+    } else {
+        // the point of the segment from the Cauchy point to the Gauss-Newton step on the boundary
+        float qa = 0.0f, qb = 0.0f;
+#pragma unroll 1
+        for (int i = 0; i < n; ++i) {
+            float dgn = 0.0f, g = 0.0f;
+#pragma unroll
+            for (int r = 0; r < 6; ++r) {
+                dgn = fmaf(S.jw(r, i, l), y2[r], dgn);
+                g = fmaf(S.jw(r, i, l), b[r], g);
+            }
+            const float di = fmaf(ac, g, -dgn);
+            qa = fmaf(di, di, qa);
+            qb = fmaf(2.0f * dgn, di, qb);
+        }
+        const float qc = ngn2 - R2;
+        const float disc = fmaxf(fmaf(qb, qb, -4.0f * qa * qc), 0.0f);
+        const float tau = (2.0f * qc) / (sqrtf(disc) - qb);  // smaller root, stable form
+        wgn = 1.0f - tau;
+        wgd = tau * ac;
+    }
+    // the step, and the single coordinate: the joint with the largest |g_i| (the first of
+    // equals), a 1-D Gauss-Newton step on it clamped to R
+    int is = 0;
+    float gbest = -1.0f, cn = 0.0f, gsel = 0.0f, csel[6];
+#pragma unroll 1
+    for (int i = 0; i < n; ++i) {
+        float dgn = 0.0f, g = 0.0f, q2 = 0.0f, col[6];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            col[r] = S.jw(r, i, l);
+            dgn = fmaf(col[r], y2[r], dgn);
+            g = fmaf(col[r], b[r], g);
+            q2 = fmaf(col[r], col[r], q2);
+        }
+        S.d2(i, l) = fmaf(wgn, dgn, wgd * g);
+        if (fabsf(g) > gbest) {
+            gbest = fabsf(g);
+            is = i;
+            gsel = g;
+            cn = q2;
+#pragma unroll
+            for (int r = 0; r < 6; ++r) csel[r] = col[r];
+        }
+    }
+    S.sc_j(l) = is;
+    S.sc_step(l) = cn > 0.0f ? clampf(gsel / cn, -Rt, Rt) : 0.0f;
+    // the chosen joint's position column and axis without the row weights
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        S.sc_v(r, l) = csel[r] / S.W(r, l);
+        S.sc_z(r, l) = csel[3 + r] / S.W(3 + r, l);
+    }
 }
 
 template <bool TRACE, int WARPS>
@@ -213,11 +386,16 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
     extern __shared__ __align__(16) float smem_f[];
     const RobotParams* rob = stage_robots(smem_f, A.rs);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const LmW S{smem_f + robots_smem_bytes(A.rs.n) / sizeof(float) + warp * lm_warp_words(A.rs.n_max), A.rs.n_max};
+    float* const warps_f = smem_f + robots_smem_bytes(A.rs.n) / sizeof(float);
+    const int words = lm_warp_words(A.rs.n_max, A.P.lm_A);
+    const LmW S{warps_f + warp * words, A.rs.n_max};
+    // the state of slot sl = warp * 32 + lane, whichever thread works on it
+    auto slot_state = [&](int sl) { return LmW{warps_f + (sl >> 5) * words, A.rs.n_max}; };
+    const LmCta<WARPS> CL = lm_cta<WARPS>(warps_f + WARPS * words);
 
     const hjcd_params& P = A.P;
     const float Rt = P.lm_trust_R;
-    unsigned long long n_it = 0, n_fk = 0;
+    unsigned long long n_it = 0, n_fk = 0, n_sc = 0;
 
     bool has = false;
     int64_t c = 0;
@@ -252,9 +430,9 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                 }
             }
         }
-        if (!__any_sync(0xffffffffu, has)) {
-            // every lane asked for work: stop once the queue is drained, else ask again
-            if (!__any_sync(0xffffffffu, c < A.C)) break;
+        if (!__syncthreads_or(has)) {
+            // every lane of the CTA asked for work: stop once the queue is drained, else ask again
+            if (!__syncthreads_or(c < A.C)) break;
             continue;
         }
 
@@ -278,7 +456,8 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
             const Frame E = fk_flange(R, F);
             ++n_fk;
             const V3 pt = v3(T.p[0], T.p[1], T.p[2]);
-            const V3 om = quat_log(quat_error(T, quat_from_frame(E)));
+            const Q4 qerr = quat_error(T, quat_from_frame(E));
+            const V3 om = quat_log(qerr);
             const V3 epv = pt - E.p;
             const float ep = sqrtf(dot(epv, epv)), eo = sqrtf(dot(om, om));
             if ((kk > 0 && ep < T.eps_pos && eo < T.eps_ori) || kk == cap) {
@@ -326,6 +505,13 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                 }
                 S.cost0(lane) = 0.5f * cost0;
                 S.t(lane) = t;
+                S.e(0, lane) = epv.x;
+                S.e(1, lane) = epv.y;
+                S.e(2, lane) = epv.z;
+                S.qe(0, lane) = qerr.w;
+                S.qe(1, lane) = qerr.v.x;
+                S.qe(2, lane) = qerr.v.y;
+                S.qe(3, lane) = qerr.v.z;
                 // the push-through LM step on the weighted Jacobian
                 Y6 wv, bv;
 #pragma unroll
@@ -333,7 +519,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                     wv.v[r] = W[r];
                     bv.v[r] = b[r];
                 }
-                const Y6 yy = normal_solve(S, lane, n, true, P.lm_lambda, wv, bv);
+                const Y6 yy = normal_solve(S, lane, n, P.lm_lambda, wv, bv);
                 float y[6];
 #pragma unroll
                 for (int r = 0; r < 6; ++r) y[r] = yy.v[r];
@@ -353,155 +539,117 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
             }
         }
 
-        // ---- line search; the full step by its owner, the rest spread ----
+        // ---- the full step by its owner ----
         int branch = 3;
         float alpha_acc = 0.0f;
         if (act) {
             ++n_fk;
-            if (trial_cost(rob, A.tg, t, S, lane, 1.0f) < S.cost0(lane)) {
-                take_step(R, S, lane, 1.0f);
+            if (trial_cost(rob, A.tg, t, S, lane, 1.0f, kDirLm) < S.cost0(lane)) {
+                take_step(R, S, lane, 1.0f, kDirLm);
                 branch = 0;
                 alpha_acc = 1.0f;
             }
         }
-        unsigned fail = __ballot_sync(0xffffffffu, act && branch != 0);
-        n_fk += warp_trials(rob, A.tg, S, fail, lane, 1, P.lm_A, P.lm_beta);
-        if (act && branch != 0) {
-            for (int i = 1; i <= P.lm_A; ++i) {
-                if (S.ok(i, lane)) {
-                    alpha_acc = ls_alpha(i, P.lm_beta);
-                    take_step(R, S, lane, alpha_acc);
-                    branch = 0;
-                    break;
-                }
-            }
+        const bool failed = act && branch != 0;
+        if (failed) {
+            S.s(lane) = s;
+            S.kk(lane) = kk;
         }
 
-        // ---- dogleg (owner) ----
-        if (act && branch != 0) {
-            float b[6];
-            Y6 bv, wv;
+        // ---- the failure path over the CTA: the failing slots of all warps, compacted ----
+        const unsigned fail = __ballot_sync(0xffffffffu, failed);
+        if (lane == 0) CL.wm[warp] = fail;
+        __syncthreads();
+        int nf = 0, before = 0;
 #pragma unroll
-            for (int r = 0; r < 6; ++r) {
-                b[r] = S.b(r, lane);
-                bv.v[r] = b[r];
-                wv.v[r] = 1.0f;
+        for (int w = 0; w < WARPS; ++w) {
+            const int k = __popc(CL.wm[w]);
+            before += w < warp ? k : 0;
+            nf += k;
+        }
+        if (failed) CL.fl[before + __popc(fail & ((1u << lane) - 1u))] = threadIdx.x;
+        if (threadIdx.x == 0) CL.np[0] = 0;
+        __syncthreads();
+        if (nf > 0) {
+            // dogleg and single-coordinate steps of each failing slot
+            for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+                const int sl = CL.fl[i], l = sl & 31;
+                const LmW Sx = slot_state(sl);
+                dogleg_prepare(Sx, l, rob[A.tg[Sx.t(l)].robot].n, Rt, P.lm_gn_reg);
             }
-            float Jg[6];
-#pragma unroll
-            for (int r = 0; r < 6; ++r) Jg[r] = 0.0f;
-            float gg = 0.0f;
-#pragma unroll 1
-            for (int i = 0; i < n; ++i) {
-                float col[6], g = 0.0f;
-#pragma unroll
-                for (int r = 0; r < 6; ++r) {
-                    col[r] = S.jw(r, i, lane);
-                    g = fmaf(col[r], b[r], g);
-                }
-                gg = fmaf(g, g, gg);
-#pragma unroll
-                for (int r = 0; r < 6; ++r) Jg[r] = fmaf(col[r], g, Jg[r]);
+            __syncthreads();
+            // the remaining line-search trials and the dogleg trial, one kinematics pass each
+            const int per = P.lm_A + 1;
+            for (int w = threadIdx.x; w < nf * per; w += blockDim.x) {
+                const int sl = CL.fl[w / per], l = sl & 31, i = w % per;
+                const LmW Sx = slot_state(sl);
+                int kind;
+                float alpha;
+                trial_item(i, P.lm_A, P.lm_beta, &kind, &alpha);
+                Sx.ok(i, l) = trial_cost(rob, A.tg, Sx.t(l), Sx, l, alpha, kind) < Sx.cost0(l) ? 1 : 0;
             }
-            const Y6 yy2 = normal_solve(S, lane, n, false, P.lm_gn_reg, wv, bv);
-            float y2[6];
-#pragma unroll
-            for (int r = 0; r < 6; ++r) y2[r] = yy2.v[r];
-            float jgjg = 0.0f;
-#pragma unroll
-            for (int r = 0; r < 6; ++r) jgjg = fmaf(Jg[r], Jg[r], jgjg);
-            const float ac = jgjg > 0.0f ? gg / jgjg : 0.0f;
-            // g_i = (WJ)_i . W r and dgn_i = (WJ)_i . y2 are recomputed where needed
-            float ngn2 = 0.0f;
-#pragma unroll 1
-            for (int i = 0; i < n; ++i) {
-                float a = 0.0f;
-#pragma unroll
-                for (int r = 0; r < 6; ++r) a = fmaf(S.jw(r, i, lane), y2[r], a);
-                ngn2 = fmaf(a, a, ngn2);
-            }
-            const float ngd2 = ac * ac * gg, R2 = Rt * Rt;
-            float wgn = 1.0f, wgd = 0.0f;  // step = wgn * dgn + wgd * g
-            if (ngn2 <= R2) {
-                wgn = 1.0f;
-                wgd = 0.0f;
-            } else if (ngd2 >= R2) {
-                wgn = 0.0f;
-                wgd = ngd2 > 0.0f ? Rt * rsqrtf(ngd2) * ac : 0.0f;
-            } else {
-                float qa = 0.0f, qb = 0.0f;
-#pragma unroll 1
-                for (int i = 0; i < n; ++i) {
-                    float dgn = 0.0f, g = 0.0f;
-#pragma unroll
-                    for (int r = 0; r < 6; ++r) {
-                        dgn = fmaf(S.jw(r, i, lane), y2[r], dgn);
-                        g = fmaf(S.jw(r, i, lane), b[r], g);
+            __syncthreads();
+            // each slot's first successful trial in the order of Alg. 4, else its
+            // single-coordinate line search (trials in closed form), else the perturbation
+            for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+                const int sl = CL.fl[i], l = sl & 31;
+                const LmW Sx = slot_state(sl);
+                const RobotParams& Rx = rob[A.tg[Sx.t(l)].robot];
+                int pick = per;
+                for (int q = 0; q < per; ++q)
+                    if (Sx.ok(q, l)) {
+                        pick = q;
+                        break;
                     }
-                    const float di = fmaf(ac, g, -dgn);
-                    qa = fmaf(di, di, qa);
-                    qb = fmaf(2.0f * dgn, di, qb);
+                n_fk += pick < per ? pick + 1 : per;  // the passes the sequential method evaluates
+                int br = 3;
+                float al = 0.0f;
+                if (pick < per) {
+                    int kind;
+                    trial_item(pick, P.lm_A, P.lm_beta, &kind, &al);
+                    take_step(Rx, Sx, l, al, kind);
+                    br = kind == kDirLm ? 0 : 1;
+                    if (kind == kDirDogleg) al = 0.0f;  // no line-search alpha (as traced)
+                } else {
+                    const int j = Sx.sc_j(l);
+                    const float th0 = Sx.th(j, l), st = Sx.sc_step(l), c0 = Sx.cost0(l);
+                    for (int q = 0; q <= P.lm_A; ++q) {
+                        const float a = ls_alpha(q, P.lm_beta);
+                        const float thj = clampf(fmaf(a, st, th0), Rx.lo[j], Rx.hi[j]);
+                        ++n_sc;
+                        if (coord_cost(Sx, l, thj - th0) < c0) {
+                            Sx.th(j, l) = thj;
+                            br = 2;
+                            al = a;
+                            break;
+                        }
+                    }
+                    if (br == 3) CL.pl[atomicAdd(CL.np, 1)] = sl;
                 }
-                const float qc = ngn2 - R2;
-                const float disc = fmaxf(fmaf(qb, qb, -4.0f * qa * qc), 0.0f);
-                const float tau = (2.0f * qc) / (sqrtf(disc) - qb);  // smaller root, stable form
-                wgn = 1.0f - tau;
-                wgd = tau * ac;
+                Sx.br(l) = br;
+                Sx.al(l) = al;
             }
-            // dogleg step as the trial direction, evaluated at alpha = 1
-            int is = 0;
-            float gbest = -1.0f, cn = 0.0f, gsel = 0.0f;
-#pragma unroll 1
-            for (int i = 0; i < n; ++i) {
-                float dgn = 0.0f, g = 0.0f, q2 = 0.0f;
-#pragma unroll
-                for (int r = 0; r < 6; ++r) {
-                    const float v = S.jw(r, i, lane);
-                    dgn = fmaf(v, y2[r], dgn);
-                    g = fmaf(v, b[r], g);
-                    q2 = fmaf(v, v, q2);
+            __syncthreads();
+            // the perturbation of Alg. 4: normal pairs of every slot that found no step
+            const int np = CL.np[0];
+            if (np > 0) {
+                const int pp = (A.rs.n_max + 1) / 2;
+                for (int w = threadIdx.x; w < np * pp; w += blockDim.x) {
+                    const int sl = CL.pl[w / pp], l = sl & 31, q = w % pp;
+                    const LmW Sx = slot_state(sl);
+                    const TargetDesc& Tx = A.tg[Sx.t(l)];
+                    const RobotParams& Rx = rob[Tx.robot];
+                    const int j0 = 2 * q, j1 = 2 * q + 1;
+                    if (j0 >= Rx.n) continue;
+                    const float2 z = normal_pair(Tx, (uint32_t)Sx.s(l), kPhaseLm, (uint32_t)A.k0 + (uint32_t)Sx.kk(l), q);
+                    Sx.th(j0, l) = clampf(fmaf(P.lm_sigma, z.x, Sx.th(j0, l)), Rx.lo[j0], Rx.hi[j0]);
+                    if (j1 < Rx.n) Sx.th(j1, l) = clampf(fmaf(P.lm_sigma, z.y, Sx.th(j1, l)), Rx.lo[j1], Rx.hi[j1]);
                 }
-                S.d(i, lane) = fmaf(wgn, dgn, wgd * g);
-                if (fabsf(g) > gbest) {  // single-coordinate choice
-                    gbest = fabsf(g);
-                    is = i;
-                    gsel = g;
-                    cn = q2;
-                }
+                __syncthreads();
             }
-            ++n_fk;
-            if (trial_cost(rob, A.tg, t, S, lane, 1.0f) < S.cost0(lane)) {
-                take_step(R, S, lane, 1.0f);
-                branch = 1;
-            } else {
-                // single coordinate: the joint with the largest |g_i|, a 1-D Gauss-Newton step on
-                // it clamped to R; its line-search trials are spread over the warp below
-                const float sstep = cn > 0.0f ? clampf(gsel / cn, -Rt, Rt) : 0.0f;
-#pragma unroll 1
-                for (int j = 0; j < n; ++j) S.d(j, lane) = (j == is) ? sstep : 0.0f;
-            }
-        }
-        fail = __ballot_sync(0xffffffffu, act && branch == 3);
-        n_fk += warp_trials(rob, A.tg, S, fail, lane, 0, P.lm_A, P.lm_beta);
-        if (act && branch == 3) {
-            for (int i = 0; i <= P.lm_A; ++i) {
-                if (S.ok(i, lane)) {
-                    alpha_acc = ls_alpha(i, P.lm_beta);
-                    take_step(R, S, lane, alpha_acc);
-                    branch = 2;
-                    break;
-                }
-            }
-        }
-        if (act && branch == 3) {
-            // random perturbation when every update fails
-            const uint32_t k = (uint32_t)(A.k0 + kk);
-#pragma unroll 1
-            for (int q = 0; 2 * q < n; ++q) {
-                const float2 z = normal_pair(T, (uint32_t)s, kPhaseLm, k, q);
-                const int j0 = 2 * q, j1 = 2 * q + 1;
-                S.th(j0, lane) = clampf(fmaf(P.lm_sigma, z.x, S.th(j0, lane)), R.lo[j0], R.hi[j0]);
-                if (j1 < n) S.th(j1, lane) = clampf(fmaf(P.lm_sigma, z.y, S.th(j1, lane)), R.lo[j1], R.hi[j1]);
+            if (failed) {
+                branch = S.br(lane);
+                alpha_acc = S.al(lane);
             }
         }
         if (act) {
@@ -517,22 +665,23 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
     if (A.cnt) {
         n_it = warp_sum(n_it);
         n_fk = warp_sum(n_fk);
+        n_sc = warp_sum(n_sc);
         if (lane == 0) {
             atomicAdd(&A.cnt->v[1], n_it);
             atomicAdd(&A.cnt->v[2], n_fk);
+            atomicAdd(&A.cnt->v[7], n_sc);
         }
     }
 }
 
 template <bool TRACE, int WARPS>
 void launch_lm_t(const LmArgs& A, cudaStream_t st) {
-    const size_t smem = robots_smem_bytes(A.rs.n) + sizeof(float) * (size_t)lm_warp_words(A.rs.n_max) * WARPS;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_lm<TRACE, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(robots_smem_bytes(kMaxLaunchRobots) +
-                                   sizeof(float) * lm_warp_words(kMaxDof) * WARPS));
-        attr = true;
+    const size_t smem = robots_smem_bytes(A.rs.n) +
+                        sizeof(float) * ((size_t)lm_warp_words(A.rs.n_max, A.P.lm_A) * WARPS + lm_cta_words<WARPS>());
+    static size_t attr = 48 * 1024;  // dynamic shared memory the kernel is allowed so far
+    if (smem > attr) {
+        cudaFuncSetAttribute(k_lm<TRACE, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = smem;
     }
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lm<TRACE, WARPS>, WARPS * 32, smem);
@@ -544,8 +693,19 @@ void launch_lm_t(const LmArgs& A, cudaStream_t st) {
 
 template <bool TRACE>
 void launch_lm_w(const LmArgs& A, cudaStream_t st) {
-    if (A.warps == 2) launch_lm_t<TRACE, 2>(A, st);
-    else if (A.warps == 8) launch_lm_t<TRACE, 8>(A, st);
+    // fewer warps per CTA when the requested count's state does not fit in shared memory
+    static int optin = 0;
+    if (!optin) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    }
+    const size_t per_warp = sizeof(float) * (size_t)lm_warp_words(A.rs.n_max, A.P.lm_A);
+    int warps = A.warps == 2 || A.warps == 8 ? A.warps : kLmWarps;
+    while (warps > 2 && robots_smem_bytes(A.rs.n) + (per_warp + sizeof(float) * 65) * warps + 4 > (size_t)optin)
+        warps /= 2;
+    if (warps == 2) launch_lm_t<TRACE, 2>(A, st);
+    else if (warps == 8) launch_lm_t<TRACE, 8>(A, st);
     else launch_lm_t<TRACE, kLmWarps>(A, st);
 }
 
