@@ -109,9 +109,26 @@ struct CandMap {
     const int32_t* cand;  // explicit [C]
     const int64_t* off;   // [T+1] prefix offsets, used when tgt is null
     int32_t T;
+    int32_t stride;       // > 0: every target has this many candidates (off[t] = t * stride)
 
     // false when an explicit target row is outside [0, T): the candidate is skipped
     __device__ __forceinline__ bool lookup(int64_t c, int32_t& t, int32_t& s) const {
+        if (!tgt && stride > 0) {  // no search: a division
+            if (c < 0x7fffffff) {
+                const uint32_t q = (uint32_t)c / (uint32_t)stride;
+                t = (int32_t)q;
+                s = (int32_t)((uint32_t)c - q * (uint32_t)stride);
+            } else {
+                t = (int32_t)(c / stride);
+                s = (int32_t)(c - (int64_t)t * stride);
+            }
+            return true;
+        }
+        return lookup_search(c, t, s);
+    }
+
+    // the same without the stride (kernels that look a candidate up once)
+    __device__ __forceinline__ bool lookup_search(int64_t c, int32_t& t, int32_t& s) const {
         if (tgt) {
             t = tgt[c];
             s = cand[c];

@@ -140,7 +140,7 @@ struct WaveItem {
 struct WavePlan {
     int n_items = 0, T = 0, NR = 0, NS = 0;
     int64_t CM = 0, CB = 0;
-    int max_m = 0, max_b = 0;
+    int max_m = 0, max_b = 0, min_m = 0;  // min_m == max_m: every target has max_m seeds
     int n_max = 0, ns_max = 0, pairs_max = 0, obj4_max = 0;
     std::vector<const RobotRec*> robots;  // the wave's robot table
     std::vector<int> item_robot, item_scene;

@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < A.C;
          c += (int64_t)gridDim.x * blockDim.x) {
         int32_t t, s;
-        if (!A.map.lookup(c, t, s)) continue;
+        if (!A.map.lookup_search(c, t, s)) continue;
         s += A.seed_base;
         const TargetDesc T = A.tg[t];
         const RobotParams& R = rob[T.robot];

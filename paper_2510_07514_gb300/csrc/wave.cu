@@ -105,6 +105,7 @@ hjcd_status plan_wave(hjcd_ctx* ctx, const WaveItem* items, int n_items, const h
             const int64_t b = dup_count(m, P.dup_ratio);
             W.CM += m;
             W.CB += b;
+            W.min_m = W.CM == m ? m : std::min(W.min_m, m);
             W.max_m = std::max(W.max_m, m);
             W.max_b = std::max(W.max_b, (int)b);
         }
@@ -261,7 +262,8 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
     CcdArgs ca{};
     ca.rs = rs;
     ca.tg = d_tg;
-    ca.map = CandMap{nullptr, nullptr, d_moff, W.T};
+    const bool uni_m = W.T > 0 && W.min_m == W.max_m;  // offsets t * max_b for PJ-IK and the filter
+    ca.map = CandMap{nullptr, nullptr, d_moff, W.T, 0};
     ca.C = W.CM;
     ca.ld = W.CM;
     ca.th_out = thM;
@@ -285,7 +287,7 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
     LmArgs la{};
     la.rs = rs;
     la.tg = d_tg;
-    la.map = CandMap{nullptr, nullptr, d_boff, W.T};
+    la.map = CandMap{nullptr, nullptr, d_boff, W.T, uni_m ? W.max_b : 0};
     la.C = W.CB;
     la.ld = W.CB;
     la.th = thB;
@@ -326,7 +328,7 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
         }
         for (const auto& e : W.scenes) cl.has_grid = cl.has_grid || (e.res && e.res->dev.cell);
         cl.tg = d_tg;
-        cl.map = CandMap{nullptr, nullptr, d_boff, W.T};
+        cl.map = CandMap{nullptr, nullptr, d_boff, W.T, uni_m ? W.max_b : 0};
         cl.C = W.CB;
         cl.ld = W.CB;
         cl.th = thB;
