@@ -365,7 +365,7 @@ def uneven_leg(ctx, args, dev, stream):
     for out in outs:
         c, e = out[2].cpu().numpy(), out[1].cpu().numpy()
         succ_t.append((c > 0) & (e[:, 0, 0] <= wl.eps_pos) & (e[:, 0, 1] <= wl.eps_ori))
-    hjcd.hjcd_set_launch_config(ctx.h, 128, 4)
+    hjcd.hjcd_set_launch_config(ctx.h, 64, 8)  # the defaults
     tuned_line = {"ccd_block": rep.ccd_block, "lm_warps": rep.lm_warps, "cd_max_iters": rep.cd_max_iters,
                   "lm_max_iters": rep.lm_max_iters, "calibration_success": rep.success_rate,
                   "calibration_best_success": rep.best_success_rate, "trials": rep.trials, "tune_s": tune_s,

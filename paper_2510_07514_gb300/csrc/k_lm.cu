@@ -48,7 +48,7 @@ namespace hjcd {
 
 namespace {
 
-constexpr int kLmWarps = 4;  // default warps per CTA; 2 and 8 also built
+constexpr int kLmWarps = 8;  // default warps per CTA; 2 and 4 also built
 constexpr int kMaxLsDepth = 31;  // A (validated by the host)
 
 __host__ __device__ constexpr int tri(int r, int c) { return r * (r + 1) / 2 + c; }
@@ -701,12 +701,12 @@ void launch_lm_w(const LmArgs& A, cudaStream_t st) {
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     }
     const size_t per_warp = sizeof(float) * (size_t)lm_warp_words(A.rs.n_max, A.P.lm_A);
-    int warps = A.warps == 2 || A.warps == 8 ? A.warps : kLmWarps;
+    int warps = A.warps == 2 || A.warps == 4 || A.warps == 8 ? A.warps : kLmWarps;
     while (warps > 2 && robots_smem_bytes(A.rs.n) + (per_warp + sizeof(float) * 65) * warps + 4 > (size_t)optin)
         warps /= 2;
     if (warps == 2) launch_lm_t<TRACE, 2>(A, st);
-    else if (warps == 8) launch_lm_t<TRACE, 8>(A, st);
-    else launch_lm_t<TRACE, kLmWarps>(A, st);
+    else if (warps == 4) launch_lm_t<TRACE, 4>(A, st);
+    else launch_lm_t<TRACE, 8>(A, st);
 }
 
 }  // namespace

@@ -269,7 +269,7 @@ def test_launch_configuration_does_not_change_results(ctx):
         with pytest.raises(hjcd.HjcdError):
             hjcd.hjcd_set_launch_config(ctx.h, 96, 4)
     finally:
-        hjcd.hjcd_set_launch_config(ctx.h, 128, 4)
+        hjcd.hjcd_set_launch_config(ctx.h, 64, 8)  # the defaults
 
 
 def test_autotune_picks_a_valid_configuration(ctx):
@@ -291,7 +291,7 @@ def test_autotune_picks_a_valid_configuration(ctx):
         succ = np.mean((c > 0) & (e[:, 0, 0] <= 1e-3) & (e[:, 0, 1] <= 1e-2))
         assert abs(succ - rep.success_rate) < 1e-6
     finally:
-        hjcd.hjcd_set_launch_config(ctx.h, 128, 4)
+        hjcd.hjcd_set_launch_config(ctx.h, 64, 8)  # the defaults
 
 
 def test_solve_nearest_ranks_by_distance_to_the_current_configuration(ctx):
