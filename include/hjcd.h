@@ -24,7 +24,10 @@
  *     Calls taking device buffers only enqueue work and return before it
  *     completes; hjcd_solve with host buffers returns after its results have
  *     been copied back.
- *   - Threads: a context is used by one host thread at a time.
+ *   - Threads: a context is used by one host thread at a time; while a
+ *     server runs (hjcd_server_start), its scheduler thread launches work on
+ *     the same context, and the caller may still submit, poll, wait and
+ *     change the launch configuration and collision mode.
  *   - Random draws: Philox4x32-10 keyed by the request seed, counter
  *     (candidate, target, phase << 24 | iteration, block), so results do not
  *     depend on how work is batched.

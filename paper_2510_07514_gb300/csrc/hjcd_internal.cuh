@@ -9,6 +9,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "hjcd.h"
 
 namespace hjcd {
@@ -390,18 +393,53 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
     return v;
 }
 
+// Per-device values looked up once (host threads may launch concurrently: the
+// serving scheduler and callers; a process may drive several devices).
+constexpr int kMaxDevices = 64;
+
+inline int current_device() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return dev;
+}
+
+// SM count of the current device.
+inline int sm_count() {
+    static std::atomic<int> sms[kMaxDevices];
+    const int dev = current_device();
+    const int i = dev >= 0 && dev < kMaxDevices ? dev : 0;
+    int v = sms[i].load(std::memory_order_relaxed);
+    if (v <= 0) {
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        if (v <= 0) v = 1;
+        sms[i].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
+// Largest dynamic shared memory a kernel has been allowed on each device; allow_dyn_smem raises
+// the kernel's limit on the current device to `bytes` when it is above what was set before (under
+// a lock, so that no thread launches between another's check and its attribute call, and a limit
+// never goes down).
+struct SmemLimit {
+    std::mutex mu;
+    int bytes[kMaxDevices] = {};
+};
+
+template <typename K>
+inline void allow_dyn_smem(K kernel, SmemLimit& lim, size_t bytes) {
+    if (bytes <= 48 * 1024) return;
+    const int dev = current_device();
+    const int i = dev >= 0 && dev < kMaxDevices ? dev : 0;
+    std::lock_guard<std::mutex> g(lim.mu);
+    if ((int)bytes > lim.bytes[i] || i != dev) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        lim.bytes[i] = (int)bytes;
+    }
+}
+
 // Grid for a grid-stride kernel: one thread (or warp) per item, capped at
 // `per_sm` blocks per SM.
-inline int sm_count() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    return sms;
-}
 
 inline int grid_for(int64_t items, int per_block, int per_sm = 64) {
     int64_t b = (items + per_block - 1) / per_block;

@@ -68,9 +68,10 @@ struct hjcd_ctx {
     bool ev_valid = false;
     std::atomic<int64_t> launches{0};
     size_t ws_budget = 0;     // workspace bytes one solve may use before it splits into waves (0: unlimited)
-    bool collide_lazy = true; // rank first, collision-check in rank order (hjcd_set_collision_mode)
-    int32_t ccd_block = 64;  // launch configuration (hjcd_set_launch_config, hjcd_autotune)
-    int32_t lm_warps = 8;
+    // settings read by the serving thread's launches while a caller may change them
+    std::atomic<bool> collide_lazy{true};  // rank first, collision-check in rank order (hjcd_set_collision_mode)
+    std::atomic<int32_t> ccd_block{64};    // launch configuration (hjcd_set_launch_config, hjcd_autotune)
+    std::atomic<int32_t> lm_warps{8};
     std::mutex api_mu;  // robots/scenes tables against the serving thread
     hjcd::Server* server = nullptr;  // owned; freed by server_stop
 };

@@ -447,12 +447,8 @@ __global__ void __launch_bounds__(kCcdThreads) k_sample(const RobotParams R, uin
 template <bool TRACE, int TH>
 void launch_ccd_t(const CcdArgs& A, cudaStream_t st) {
     const size_t smem = robots_smem_bytes(A.rs.n) + sizeof(float) * (7 * A.rs.n_max + kSlotWords) * TH;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_ccd<TRACE, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(robots_smem_bytes(kMaxLaunchRobots) + sizeof(float) * (7 * kMaxDof + kSlotWords) * TH));
-        attr = true;
-    }
+    static SmemLimit lim;
+    allow_dyn_smem(k_ccd<TRACE, TH>, lim, smem);
     k_ccd<TRACE, TH><<<grid_for(A.C, TH, 16 * 128 / TH), TH, smem, st>>>(A);
 }
 
@@ -469,12 +465,8 @@ void launch_ccd(const CcdArgs& A, bool trace, cudaStream_t st) {
     if (A.C <= 0) return;
     if (A.P.cd_variant == 2) {  // one CTA per target (offset maps only)
         const size_t smem = robots_smem_bytes(A.rs.n) + sizeof(float) * (7 * A.rs.n_max + kSlotWords) * 128;
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_ccd_lock<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(robots_smem_bytes(kMaxLaunchRobots) + sizeof(float) * (7 * kMaxDof + kSlotWords) * 128));
-            attr = true;
-        }
+        static SmemLimit lim;
+        allow_dyn_smem(k_ccd_lock<128>, lim, smem);
         k_ccd_lock<128><<<A.map.T, 128, smem, st>>>(A);
         return;
     }

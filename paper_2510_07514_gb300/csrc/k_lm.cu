@@ -678,11 +678,8 @@ template <bool TRACE, int WARPS>
 void launch_lm_t(const LmArgs& A, cudaStream_t st) {
     const size_t smem = robots_smem_bytes(A.rs.n) +
                         sizeof(float) * ((size_t)lm_warp_words(A.rs.n_max, A.P.lm_A) * WARPS + lm_cta_words<WARPS>());
-    static size_t attr = 48 * 1024;  // dynamic shared memory the kernel is allowed so far
-    if (smem > attr) {
-        cudaFuncSetAttribute(k_lm<TRACE, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = smem;
-    }
+    static SmemLimit lim;
+    allow_dyn_smem(k_lm<TRACE, WARPS>, lim, smem);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lm<TRACE, WARPS>, WARPS * 32, smem);
     if (per_sm < 1) per_sm = 1;
@@ -694,12 +691,8 @@ void launch_lm_t(const LmArgs& A, cudaStream_t st) {
 template <bool TRACE>
 void launch_lm_w(const LmArgs& A, cudaStream_t st) {
     // fewer warps per CTA when the requested count's state does not fit in shared memory
-    static int optin = 0;
-    if (!optin) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    }
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, current_device());
     const size_t per_warp = sizeof(float) * (size_t)lm_warp_words(A.rs.n_max, A.P.lm_A);
     int warps = A.warps == 2 || A.warps == 4 || A.warps == 8 ? A.warps : kLmWarps;
     while (warps > 2 && robots_smem_bytes(A.rs.n) + (per_warp + sizeof(float) * 65) * warps + 4 > (size_t)optin)

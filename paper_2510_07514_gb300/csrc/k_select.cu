@@ -205,38 +205,38 @@ int smem_for(int m) {
     return N * (int)sizeof(uint64_t);
 }
 
-template <typename K>
-void allow_smem(K kernel, int bytes) {
-    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
 
 }  // namespace
 
 void launch_topk_dup(const DupArgs& A, int max_m, cudaStream_t st) {
     if (A.T <= 0 || max_m <= 0) return;
     const int sm = smem_for(max_m);
-    allow_smem(k_topk_dup, sm);
+    static SmemLimit lim;
+    allow_dyn_smem(k_topk_dup, lim, sm);
     k_topk_dup<<<A.T, kSelThreads, sm, st>>>(A);
 }
 
 void launch_rank(const RankArgs& A, int max_b, cudaStream_t st) {
     if (A.T <= 0) return;
     const int sm = smem_for(max_b > 0 ? max_b : 1);
-    allow_smem(k_rank, sm);
+    static SmemLimit lim;
+    allow_dyn_smem(k_rank, lim, sm);
     k_rank<<<A.T, kSelThreads, sm, st>>>(A);
 }
 
 void launch_shard_topk(const ShardTopkArgs& A, int max_m, cudaStream_t st) {
     if (A.T <= 0) return;
     const int sm = smem_for(max_m > 0 ? max_m : 1);
-    allow_smem(k_shard_topk, sm);
+    static SmemLimit lim;
+    allow_dyn_smem(k_shard_topk, lim, sm);
     k_shard_topk<<<A.T, kSelThreads, sm, st>>>(A);
 }
 
 void launch_topk_merge(const MergeArgs& A, cudaStream_t st) {
     if (A.T <= 0 || A.L <= 0 || A.K <= 0) return;
     const int sm = smem_for(A.L * A.K);
-    allow_smem(k_topk_merge, sm);
+    static SmemLimit lim;
+    allow_dyn_smem(k_topk_merge, lim, sm);
     k_topk_merge<<<A.T, kSelThreads, sm, st>>>(A);
 }
 
