@@ -210,8 +210,9 @@ void hjcd_graph_destroy(hjcd_graph* graph);
 /* ---- launch configuration and autotuning --------------------------------------- */
 
 /* Candidates per CTA of the PO-CCD kernel (64, 128 or 256; default 64) and
- * warps per CTA of the PJ-IK kernel (2, 4 or 8; default 8) for every later
- * launch of the context.  Results do not depend on them. */
+ * warps per CTA of the PJ-IK kernel (2, 4 or 8; default 8; a PJ-IK launch of
+ * at most 64 candidates per SM always takes 2) for every later launch of the
+ * context.  Results do not depend on them. */
 hjcd_status hjcd_set_launch_config(hjcd_ctx* ctx, int32_t ccd_block, int32_t lm_warps);
 
 typedef struct hjcd_tune_report {

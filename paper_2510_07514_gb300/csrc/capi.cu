@@ -27,10 +27,10 @@ hjcd_status fail(hjcd_ctx* ctx, hjcd_status code, const char* fmt, ...) {
     return code;
 }
 
-hjcd_status after_launch(hjcd_ctx* ctx, int kernels) {
+hjcd_status after_launch(hjcd_ctx* ctx, int kernels, const char* what) {
     ctx->launches += kernels;
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return fail(ctx, HJCD_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(ctx, HJCD_ECUDA, "%s launch: %s", what, cudaGetErrorString(e));
     return HJCD_OK;
 }
 

@@ -417,25 +417,30 @@ inline int sm_count() {
     return v;
 }
 
-// Largest dynamic shared memory a kernel has been allowed on each device; allow_dyn_smem raises
-// the kernel's limit on the current device to `bytes` when it is above what was set before (under
-// a lock, so that no thread launches between another's check and its attribute call, and a limit
-// never goes down).
+// A kernel's dynamic shared-memory limit, raised once per device, at the kernel's first launch
+// there, to the most any launch of it takes (clamped to what the device allows beside the
+// kernel's static shared memory).  Raising it later, when a launch first needed more than 48 KB,
+// made that launch fail ("invalid argument") while smaller launches of the kernel were running
+// on other streams.  Under a lock: host threads may launch concurrently.
 struct SmemLimit {
     std::mutex mu;
-    int bytes[kMaxDevices] = {};
+    bool set[kMaxDevices] = {};
 };
 
 template <typename K>
-inline void allow_dyn_smem(K kernel, SmemLimit& lim, size_t bytes) {
-    if (bytes <= 48 * 1024) return;
+inline void allow_dyn_smem(K kernel, SmemLimit& lim, size_t most) {
     const int dev = current_device();
     const int i = dev >= 0 && dev < kMaxDevices ? dev : 0;
     std::lock_guard<std::mutex> g(lim.mu);
-    if ((int)bytes > lim.bytes[i] || i != dev) {
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        lim.bytes[i] = (int)bytes;
-    }
+    if (lim.set[i] && i == dev) return;
+    lim.set[i] = true;
+    if (most <= 48 * 1024) return;
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, kernel);
+    const size_t cap = optin > (int)fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : most;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(most < cap ? most : cap));
 }
 
 // Grid for a grid-stride kernel: one thread (or warp) per item, capped at

@@ -100,7 +100,7 @@ struct Carve {
     }
 };
 
-hjcd_status after_launch(hjcd_ctx* ctx, int kernels);
+hjcd_status after_launch(hjcd_ctx* ctx, int kernels, const char* what = "kernel");
 int pointer_kind(const void* p);  // 1 device/managed, 0 host, -1 null
 bool pinned_host(const void* p);
 hjcd_status make_current(hjcd_ctx* ctx);

@@ -448,7 +448,8 @@ template <bool TRACE, int TH>
 void launch_ccd_t(const CcdArgs& A, cudaStream_t st) {
     const size_t smem = robots_smem_bytes(A.rs.n) + sizeof(float) * (7 * A.rs.n_max + kSlotWords) * TH;
     static SmemLimit lim;
-    allow_dyn_smem(k_ccd<TRACE, TH>, lim, smem);
+    allow_dyn_smem(k_ccd<TRACE, TH>, lim,
+                   robots_smem_bytes(kMaxLaunchRobots) + sizeof(float) * (7 * kMaxDof + kSlotWords) * TH);
     k_ccd<TRACE, TH><<<grid_for(A.C, TH, 16 * 128 / TH), TH, smem, st>>>(A);
 }
 
@@ -466,7 +467,8 @@ void launch_ccd(const CcdArgs& A, bool trace, cudaStream_t st) {
     if (A.P.cd_variant == 2) {  // one CTA per target (offset maps only)
         const size_t smem = robots_smem_bytes(A.rs.n) + sizeof(float) * (7 * A.rs.n_max + kSlotWords) * 128;
         static SmemLimit lim;
-        allow_dyn_smem(k_ccd_lock<128>, lim, smem);
+        allow_dyn_smem(k_ccd_lock<128>, lim,
+                       robots_smem_bytes(kMaxLaunchRobots) + sizeof(float) * (7 * kMaxDof + kSlotWords) * 128);
         k_ccd_lock<128><<<A.map.T, 128, smem, st>>>(A);
         return;
     }

@@ -593,7 +593,7 @@ bool launch_rank_lazy_t(const CollideArgs& A, const RankArgs& R, int n_obj4, int
     const size_t smem = keys_off + 8 * (size_t)N;
     if (smem > 220 * 1024) return false;
     static SmemLimit lim;
-    allow_dyn_smem(k_rank_lazy<SPL, UNIFORM, GRID>, lim, smem);
+    allow_dyn_smem(k_rank_lazy<SPL, UNIFORM, GRID>, lim, 220 * 1024);
     k_rank_lazy<SPL, UNIFORM, GRID><<<R.T, kWarpsPerBlock * 32, smem, st>>>(A, R, keys_off, depth);
     return true;
 }
@@ -612,7 +612,7 @@ void launch_collide_t(const CollideArgs& A, int n_obj4, cudaStream_t st) {
     const size_t smem =
         collide_smem_layout(UNIFORM ? n_obj4 : 0, A.rs.n, A.rs.n_max + 2, A.rs.ns_max, A.rs.pairs_max).total;
     static SmemLimit lim;
-    allow_dyn_smem(k_collide<SPL, UNIFORM, GRID>, lim, smem);
+    allow_dyn_smem(k_collide<SPL, UNIFORM, GRID>, lim, 227 * 1024);
     const int g = grid_for(A.C, kWarpsPerBlock, 8);
     k_collide<SPL, UNIFORM, GRID><<<g, kWarpsPerBlock * 32, smem, st>>>(A);
 }
@@ -674,7 +674,7 @@ void launch_contacts(const RobotParams& R, const RobotDev& rd, const SceneDev& s
     if (C <= 0 || rd.n_sph <= 0 || sc.n_sph + sc.n_box <= 0) return;
     const size_t smem = sizeof(float4) * kContactTile * (size_t)rd.n_sph;
     static SmemLimit lim;
-    allow_dyn_smem(k_contacts, lim, smem);
+    allow_dyn_smem(k_contacts, lim, sizeof(float4) * kContactTile * (size_t)HJCD_MAX_SPHERES);
     const int64_t blocks = (C + kContactTile - 1) / kContactTile;
     k_contacts<<<(unsigned)blocks, 256, smem, st>>>(R, rd, sc, perm, C, th, ld, touched);
 }

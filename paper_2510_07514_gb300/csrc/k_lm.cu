@@ -679,7 +679,9 @@ void launch_lm_t(const LmArgs& A, cudaStream_t st) {
     const size_t smem = robots_smem_bytes(A.rs.n) +
                         sizeof(float) * ((size_t)lm_warp_words(A.rs.n_max, A.P.lm_A) * WARPS + lm_cta_words<WARPS>());
     static SmemLimit lim;
-    allow_dyn_smem(k_lm<TRACE, WARPS>, lim, smem);
+    allow_dyn_smem(k_lm<TRACE, WARPS>, lim,
+                   robots_smem_bytes(kMaxLaunchRobots) +
+                       sizeof(float) * ((size_t)lm_warp_words(kMaxDof, kMaxLsDepth) * WARPS + lm_cta_words<WARPS>()));
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lm<TRACE, WARPS>, WARPS * 32, smem);
     if (per_sm < 1) per_sm = 1;
@@ -695,6 +697,9 @@ void launch_lm_w(const LmArgs& A, cudaStream_t st) {
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, current_device());
     const size_t per_warp = sizeof(float) * (size_t)lm_warp_words(A.rs.n_max, A.P.lm_A);
     int warps = A.warps == 2 || A.warps == 4 || A.warps == 8 ? A.warps : kLmWarps;
+    // a batch too small to give every SM a CTA of two warps (a single target, say): two-warp CTAs,
+    // spread over more SMs with shorter lock-step stages (latency, not throughput, is at stake)
+    if (A.C <= (int64_t)sm_count() * 64) warps = 2;
     while (warps > 2 && robots_smem_bytes(A.rs.n) + (per_warp + sizeof(float) * 65) * warps + 4 > (size_t)optin)
         warps /= 2;
     if (warps == 2) launch_lm_t<TRACE, 2>(A, st);

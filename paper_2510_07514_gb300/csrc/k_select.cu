@@ -212,7 +212,7 @@ void launch_topk_dup(const DupArgs& A, int max_m, cudaStream_t st) {
     if (A.T <= 0 || max_m <= 0) return;
     const int sm = smem_for(max_m);
     static SmemLimit lim;
-    allow_dyn_smem(k_topk_dup, lim, sm);
+    allow_dyn_smem(k_topk_dup, lim, smem_for(HJCD_MAX_SAMPLES));
     k_topk_dup<<<A.T, kSelThreads, sm, st>>>(A);
 }
 
@@ -220,7 +220,7 @@ void launch_rank(const RankArgs& A, int max_b, cudaStream_t st) {
     if (A.T <= 0) return;
     const int sm = smem_for(max_b > 0 ? max_b : 1);
     static SmemLimit lim;
-    allow_dyn_smem(k_rank, lim, sm);
+    allow_dyn_smem(k_rank, lim, smem_for(HJCD_MAX_SAMPLES));
     k_rank<<<A.T, kSelThreads, sm, st>>>(A);
 }
 
@@ -228,7 +228,7 @@ void launch_shard_topk(const ShardTopkArgs& A, int max_m, cudaStream_t st) {
     if (A.T <= 0) return;
     const int sm = smem_for(max_m > 0 ? max_m : 1);
     static SmemLimit lim;
-    allow_dyn_smem(k_shard_topk, lim, sm);
+    allow_dyn_smem(k_shard_topk, lim, smem_for(HJCD_MAX_SAMPLES));
     k_shard_topk<<<A.T, kSelThreads, sm, st>>>(A);
 }
 
@@ -236,7 +236,7 @@ void launch_topk_merge(const MergeArgs& A, cudaStream_t st) {
     if (A.T <= 0 || A.L <= 0 || A.K <= 0) return;
     const int sm = smem_for(A.L * A.K);
     static SmemLimit lim;
-    allow_dyn_smem(k_topk_merge, lim, sm);
+    allow_dyn_smem(k_topk_merge, lim, 227 * 1024);
     k_topk_merge<<<A.T, kSelThreads, sm, st>>>(A);
 }
 

@@ -256,7 +256,7 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
 
     if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[0], s));
     launch_pack_targets(reinterpret_cast<const float*>(ws + W.o_pq7), W.T, d_tg, TargetDesc{}, d_tg, s);
-    if ((st = after_launch(ctx, 1))) return st;
+    if ((st = after_launch(ctx, 1, "k_pack_targets"))) return st;
 
     // Alg. 2: PO-CCD from uniform seeds
     CcdArgs ca{};
@@ -274,13 +274,13 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
     ca.cnt = ctx->cnt;
     ca.block = ctx->ccd_block;
     launch_ccd(ca, false, s);
-    if ((st = after_launch(ctx, 1))) return st;
+    if ((st = after_launch(ctx, 1, "k_ccd"))) return st;
     if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[1], s));
 
     // top-K and perturbed duplication
     DupArgs da{rs, d_tg, W.T, d_moff, sM, thM, W.CM, d_boff, thB, W.CB, nullptr, P.dup_ratio, P.dup_sigma};
     launch_topk_dup(da, W.max_m, s);
-    if ((st = after_launch(ctx, 1))) return st;
+    if ((st = after_launch(ctx, 1, "k_topk_dup"))) return st;
     if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[2], s));
 
     // PJ-IK
@@ -300,7 +300,7 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
     la.queue = queue;
     la.warps = ctx->lm_warps;
     launch_lm(la, false, s);
-    if ((st = after_launch(ctx, 1))) return st;
+    if ((st = after_launch(ctx, 1, "k_lm"))) return st;
     if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[3], s));
 
     // collision filter and ranking
@@ -350,26 +350,26 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
         rl.n_list = reinterpret_cast<int32_t*>(ws + W.o_qf + 12);
         lazy = launch_rank_lazy(cl, rl, W.max_b, kLazyDepth, s);
         if (lazy) {
-            if ((st = after_launch(ctx, 1))) return st;
+            if ((st = after_launch(ctx, 1, "k_rank_lazy"))) return st;
             CollideArgs c2 = cl;
             c2.list = rl.list;
             c2.n_list = rl.n_list;
             c2.b_off = d_boff;
             c2.list_bmax = std::max(W.max_b, 1);
             launch_collide(c2, s);
-            if ((st = after_launch(ctx, 1))) return st;
+            if ((st = after_launch(ctx, 1, "k_collide (list)"))) return st;
             launch_rank(rl, W.max_b, s);
-            if ((st = after_launch(ctx, 1))) return st;
+            if ((st = after_launch(ctx, 1, "k_rank (list)"))) return st;
         }
     }
     if (!lazy) {
         if (collide) {
             launch_collide(cl, s);
-            if ((st = after_launch(ctx, 1))) return st;
+            if ((st = after_launch(ctx, 1, "k_collide"))) return st;
         }
         if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[4], s));
         launch_rank(ra, W.max_b, s);
-        if ((st = after_launch(ctx, 1))) return st;
+        if ((st = after_launch(ctx, 1, "k_rank"))) return st;
     }
     if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[5], s));
 

@@ -123,3 +123,48 @@ def test_stop_finishes_admitted_requests_and_rejects_bad_ones(ctx):
         _same(out, _alone(ctx, rids, sid, robs, r))
     with pytest.raises(hjcd.HjcdError):
         hjcd.hjcd_submit(ctx.h, pairs[0][0])  # no server
+
+
+_FRESH_PROCESS = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_2510_07514_gb300 import api, hjcd, inputs
+wl = inputs.cfg2(16, 64)
+ctx = api.Context(0)
+rid, sid = ctx.add_robot(wl.robot), ctx.set_scene(wl.scene)
+th = torch.as_tensor(np.ascontiguousarray(wl.theta_gen[:16].T), dtype=torch.float32, device="cuda")
+tg = ctx.fk(rid, th).cpu()
+hjcd.hjcd_server_start(ctx.h, max_inflight=3)
+ids, outs = [], []
+try:
+    # small requests first (the kernels' first launches need little shared memory), then large
+    # ones while those still run
+    for k, (T, S) in enumerate([(2, 64)] * 6 + [(4, 8192)] * 4):
+        it, out = ctx.batch_item(rid, sid, tg[:T].contiguous(), S, 1, 100 + k, wl.robot.n, device=torch.device("cpu"))
+        ids.append(hjcd.hjcd_submit(ctx.h, it))
+        outs.append((it, out))
+    infos = [hjcd.hjcd_wait(ctx.h, i, 120.0) for i in ids]
+finally:
+    hjcd.hjcd_server_stop(ctx.h)
+bad = [inf.status for inf in infos if inf.status != 0]
+print("statuses", [inf.status for inf in infos])
+sys.exit(1 if bad else 0)
+"""
+
+
+def test_first_launches_small_then_large_on_concurrent_streams():
+    """In a fresh process, small requests are served first and large ones
+    (more than 48 KB of shared memory in the ranking kernel) arrive while they
+    run on other streams: every request must succeed (a kernel's shared-memory
+    limit raised at a later launch used to make that launch fail)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+    import subprocess
+    import sys
+    build.build()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FRESH_PROCESS, root], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
