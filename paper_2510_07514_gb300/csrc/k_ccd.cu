@@ -48,6 +48,63 @@ __device__ __forceinline__ void sample_seed(const RobotParams& R, const TargetDe
     }
 }
 
+// Both trials of joint j (origin pj, unit axis z, angle thj in [lo, hi]) against the end
+// effector at Ep and the error quaternion qerr (angle phi): the position step d of Eq.
+// theta_proj and the orientation step dq of Eq. ori_update, each clamped to the limits, with the
+// task residual each leaves (position error squared, orientation angle) and its score.  Rotating
+// joint j by x moves the end effector to pj + uz z + cos x up + sin x (z x up) and turns the error
+// quaternion into qerr [cos(x/2), -sin(x/2) z].
+struct CcdTrials {
+    float d, rp2, op, sp;   // position trial
+    float dq, pq2, rq, so;  // orientation trial
+};
+
+__device__ __forceinline__ CcdTrials ccd_joint_trials(const V3 pj, const V3 z, float thj, float lo, float hi,
+                                                      const V3 Ep, const V3 pt, const Q4 qerr, float phi,
+                                                      float delta_k, float pe2, float inv_p2, float inv_o2) {
+    CcdTrials o;
+    const V3 u = Ep - pj;
+    const V3 v = pt - pj;
+    const float uz = dot(u, z), vz = dot(v, z);
+    const V3 up = fma3(-uz, z, u);
+    const V3 vp = fma3(-vz, z, v);
+    const float nu2 = dot(u, u), nv2 = dot(v, v);
+    const float nup2 = dot(up, up), nvp2 = dot(vp, vp);
+    const V3 zxu = cross(z, up);
+    const V3 r0 = fma3(vz - uz, z, vp);
+    const float az = dot(qerr.v, z);
+    const V3 qz = fma3(qerr.w, z, cross(qerr.v, z));
+
+    // Eq. theta_proj, signed about the axis: atan2(z.(up x vp), up.vp) = atan2(zxu.vp, up.vp)
+    const float cs = dot(up, vp), sn = dot(zxu, vp);
+    const bool deg = nu2 < 1e-24f || nv2 < 1e-24f || nup2 <= pe2 * nu2 || nvp2 <= pe2 * nv2;
+    float d = deg ? 0.0f : atan2_all(sn, cs);
+    d = clampf(thj + d, lo, hi) - thj;
+    float sh, ch;
+    __sincosf(0.5f * d, &sh, &ch);
+    V3 r = fma3(-2.0f * sh * ch, zxu, fma3(-fmaf(-2.0f * sh, sh, 1.0f), up, r0));
+    o.d = d;
+    o.rp2 = dot(r, r);
+    float w2 = fmaf(qerr.w, ch, sh * az);
+    V3 v2 = fma3(ch, qerr.v, (-sh) * qz);
+    o.op = quat_angle(w2, dot(v2, v2));
+    o.sp = fmaf(o.rp2, inv_p2, o.op * o.op * inv_o2);
+
+    // Eq. ori_update: delta(k) sgn(a.z) phi
+    const float sg = (az > 0.0f) ? 1.0f : ((az < 0.0f) ? -1.0f : 0.0f);
+    float dq = delta_k * sg * phi;
+    dq = clampf(thj + dq, lo, hi) - thj;
+    __sincosf(0.5f * dq, &sh, &ch);
+    r = fma3(-2.0f * sh * ch, zxu, fma3(-fmaf(-2.0f * sh, sh, 1.0f), up, r0));
+    o.dq = dq;
+    o.pq2 = dot(r, r);
+    w2 = fmaf(qerr.w, ch, sh * az);
+    v2 = fma3(ch, qerr.v, (-sh) * qz);
+    o.rq = quat_angle(w2, dot(v2, v2));
+    o.so = fmaf(o.pq2, inv_p2, o.rq * o.rq * inv_o2);
+    return o;
+}
+
 // One iteration of a candidate: kinematics with frames into the column, the
 // residual (ep2 = |e_p|^2, eo = |omega|), the break test (kk > 0) and the cap,
 // then the update of Alg. 3 (or Alg. 1 with cd_variant = 1) of the joint
@@ -126,63 +183,25 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
         const float* f = col.fr(j);
         const V3 pj = v3(f[0 * kCcdThreads], f[1 * kCcdThreads], f[2 * kCcdThreads]);
         const V3 z = v3(f[3 * kCcdThreads], f[4 * kCcdThreads], f[5 * kCcdThreads]);
-        const float thj = col.th(j), lo = R.lo[j], hi = R.hi[j];
-        const V3 u = E.p - pj;
-        const V3 v = pt - pj;
-        const float uz = dot(u, z), vz = dot(v, z);
-        const V3 up = fma3(-uz, z, u);
-        const V3 vp = fma3(-vz, z, v);
-        const float nu2 = dot(u, u), nv2 = dot(v, v);
-        const float nup2 = dot(up, up), nvp2 = dot(vp, vp);
-        const V3 zxu = cross(z, up);
-        // rotating joint j by x: the end effector moves to pj + uz z + cos x up + sin x (z x up),
-        // the error quaternion becomes qerr [cos(x/2), -sin(x/2) z]
-        const V3 r0 = fma3(vz - uz, z, vp);
-        const float az = dot(qerr.v, z);
-        const V3 qz = fma3(qerr.w, z, cross(qerr.v, z));
-
-        // Eq. theta_proj, signed about the axis: atan2(z.(up x vp), up.vp) = atan2(zxu.vp, up.vp)
-        const float cs = dot(up, vp), sn = dot(zxu, vp);
-        const bool deg = nu2 < 1e-24f || nv2 < 1e-24f || nup2 <= pe2 * nu2 || nvp2 <= pe2 * nv2;
-        float d = deg ? 0.0f : atan2_all(sn, cs);
-        d = clampf(thj + d, lo, hi) - thj;
-        float sh, ch;
-        __sincosf(0.5f * d, &sh, &ch);
-        V3 r = fma3(-2.0f * sh * ch, zxu, fma3(-fmaf(-2.0f * sh, sh, 1.0f), up, r0));
-        const float rp2 = dot(r, r);
-        float w2 = fmaf(qerr.w, ch, sh * az);
-        V3 v2 = fma3(ch, qerr.v, (-sh) * qz);
-        const float op = quat_angle(w2, dot(v2, v2));
-        const float sp = fmaf(rp2, inv_p2, op * op * inv_o2);
-        if (j == 0 || sp < best_p * one_m_tie) {
-            best_p = sp;
+        const CcdTrials tr =
+            ccd_joint_trials(pj, z, col.th(j), R.lo[j], R.hi[j], E.p, pt, qerr, phi, delta_k, pe2, inv_p2, inv_o2);
+        if (j == 0 || tr.sp < best_p * one_m_tie) {
+            best_p = tr.sp;
             jp = j;
-            dP = d;
+            dP = tr.d;
         }
-
-        // Eq. ori_update: delta(k) sgn(a.z) phi
-        const float sg = (az > 0.0f) ? 1.0f : ((az < 0.0f) ? -1.0f : 0.0f);
-        float dq = delta_k * sg * phi;
-        dq = clampf(thj + dq, lo, hi) - thj;
-        __sincosf(0.5f * dq, &sh, &ch);
-        r = fma3(-2.0f * sh * ch, zxu, fma3(-fmaf(-2.0f * sh, sh, 1.0f), up, r0));
-        const float pq2 = dot(r, r);
-        w2 = fmaf(qerr.w, ch, sh * az);
-        v2 = fma3(ch, qerr.v, (-sh) * qz);
-        const float rq = quat_angle(w2, dot(v2, v2));
-        const float so = fmaf(pq2, inv_p2, rq * rq * inv_o2);
-        if (j == 0 || so < best_o * one_m_tie) {
-            best_o = so;
+        if (j == 0 || tr.so < best_o * one_m_tie) {
+            best_o = tr.so;
             jo = j;
-            dO = dq;
+            dO = tr.dq;
         }
         if (TRACE && kk == 0) {
-            if (A.tr.dp) A.tr.dp[j * A.ld + c] = d;
-            if (A.tr.rp) A.tr.rp[j * A.ld + c] = sqrtf(rp2);
-            if (A.tr.op) A.tr.op[j * A.ld + c] = op;
-            if (A.tr.dq) A.tr.dq[j * A.ld + c] = dq;
-            if (A.tr.pq) A.tr.pq[j * A.ld + c] = sqrtf(pq2);
-            if (A.tr.rq) A.tr.rq[j * A.ld + c] = rq;
+            if (A.tr.dp) A.tr.dp[j * A.ld + c] = tr.d;
+            if (A.tr.rp) A.tr.rp[j * A.ld + c] = sqrtf(tr.rp2);
+            if (A.tr.op) A.tr.op[j * A.ld + c] = tr.op;
+            if (A.tr.dq) A.tr.dq[j * A.ld + c] = tr.dq;
+            if (A.tr.pq) A.tr.pq[j * A.ld + c] = sqrtf(tr.pq2);
+            if (A.tr.rq) A.tr.rq[j * A.ld + c] = tr.rq;
         }
     }
 
@@ -443,6 +462,7 @@ __global__ void __launch_bounds__(kCcdThreads) k_sample(const RobotParams R, uin
         for (int j = 0; j < R.n; ++j) th_out[j * ld + c] = col.th(j);
     }
 }
+
 
 template <bool TRACE, int TH>
 void launch_ccd_t(const CcdArgs& A, cudaStream_t st) {
