@@ -336,6 +336,16 @@ __device__ __forceinline__ Q4 quat_error(const TargetDesc& T, Q4 qe) {
     return e;
 }
 
+// Square root by the hardware approximation (PTX sqrt.approx.f32, a few ulp):
+// for the angles and norms that rank trials and test tolerances, where the
+// IEEE-rounded sqrtf's correction steps cost issue slots of issue-bound
+// kernels and buy no decision the binary32 kinematics can resolve.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Arctangent of t in [0, 1] as t P(t^2), P of degree 7: coefficients fitted
 // near-minimax on [0, 1] (least squares on Chebyshev nodes, reweighted toward
 // the largest errors); |error| < 4e-8 rad in exact arithmetic and < 1.5e-7
@@ -371,12 +381,12 @@ __device__ __forceinline__ float atan2_all(float y, float x) {
 
 // rotation angle of a (not necessarily unit-normalised) error quaternion,
 // 2 atan2(|v|, |w|): the norm of omega in Eq. quat_diff
-__device__ __forceinline__ float quat_angle(float w, float vv) { return 2.0f * atan2_q1(sqrtf(vv), fabsf(w)); }
+__device__ __forceinline__ float quat_angle(float w, float vv) { return 2.0f * atan2_q1(sqrt_approx(vv), fabsf(w)); }
 
 // omega of Eq. quat_diff
 __device__ __forceinline__ V3 quat_log(Q4 e) {
     const float vv = dot(e.v, e.v);
-    const float f = (vv > 1e-30f) ? 2.0f * atan2_q1(sqrtf(vv), e.w) * rsqrtf(vv) : 2.0f / e.w;  // e.w >= 0
+    const float f = (vv > 1e-30f) ? 2.0f * atan2_q1(sqrt_approx(vv), e.w) * rsqrtf(vv) : 2.0f / e.w;  // e.w >= 0
     return f * e.v;
 }
 

@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
             const Q4 qerr = quat_error(T, quat_from_frame(E));
             const V3 om = quat_log(qerr);
             const V3 epv = pt - E.p;
-            const float ep = sqrtf(dot(epv, epv)), eo = sqrtf(dot(om, om));
+            const float ep = sqrt_approx(dot(epv, epv)), eo = sqrt_approx(dot(om, om));
             if ((kk > 0 && ep < T.eps_pos && eo < T.eps_ori) || kk == cap) {
                 // Alg. 4 break (checked after each update) or the iteration cap
 #pragma unroll 1
@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                 float W[6], b[6], cost0 = 0.0f;
 #pragma unroll
                 for (int r = 0; r < 6; ++r) {
-                    W[r] = (r < 3 ? 1.0f : wo) / fmaxf(sqrtf(rn[r]), 1e-6f);
+                    W[r] = (r < 3 ? 1.0f : wo) * rsqrtf(fmaxf(rn[r], 1e-12f));  // c / max(|row|, 1e-6)
                     b[r] = W[r] * e[r];
                     cost0 = fmaf(b[r], b[r], cost0);
                     S.W(r, lane) = W[r];
@@ -532,7 +532,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                         a = fmaf(v, y[r], a);
                         dd = fmaf(v, v, dd);
                     }
-                    const float st = clampf(a / dd, -Rt, Rt);  // trust region
+                    const float st = clampf(__fdividef(a, dd), -Rt, Rt);  // trust region
                     S.d(i, lane) = st;
                     if (TRACE && kk == 0 && A.tr.d_lm) A.tr.d_lm[i * A.ld + c] = st;
                 }
