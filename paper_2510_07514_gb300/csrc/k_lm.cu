@@ -182,11 +182,14 @@ __device__ __noinline__ Y6 normal_solve(const LmW S, int l, int n, float reg, Y6
     return y;
 }
 
-// alpha_i = 1 / beta^i by repeated division (the same bits on every lane)
-__device__ __forceinline__ float ls_alpha(int i, float beta) {
+// alpha_i = 1 / beta^i by repeated division, i = 0 .. A, into a table of the CTA (one set of bits
+// for every thread)
+__device__ __forceinline__ void ls_alphas(float* tab, int A, float beta) {
     float a = 1.0f;
-    for (int q = 0; q < i; ++q) a = a / beta;
-    return a;
+    for (int i = 0; i <= A; ++i) {
+        tab[i] = a;
+        a = a / beta;
+    }
 }
 
 // CTA-wide lists of the failure path (after the warps' state): per warp its mask of failing
@@ -241,9 +244,9 @@ __device__ __noinline__ void take_step(const RobotParams& R, const LmW S, int s,
 // The kinematics-pass trials that follow a failed full step, in the order Alg. 4
 // takes them: item i < A is the line-search trial alpha = 1/beta^(i+1) along d,
 // item A the dogleg step.
-__device__ __forceinline__ void trial_item(int i, int A, float beta, int* kind, float* alpha) {
+__device__ __forceinline__ void trial_item(int i, int A, const float* alphas, int* kind, float* alpha) {
     *kind = i < A ? kDirLm : kDirDogleg;
-    *alpha = i < A ? ls_alpha(i + 1, beta) : 1.0f;
+    *alpha = i < A ? alphas[i + 1] : 1.0f;
 }
 
 // Weighted cost of lane l's configuration with its single coordinate turned by x (the end
@@ -384,6 +387,8 @@ __device__ __noinline__ void dogleg_prepare(const LmW S, int l, int n, float Rt,
 template <bool TRACE, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
     extern __shared__ __align__(16) float smem_f[];
+    __shared__ float alphas[kMaxLsDepth + 1];
+    if (threadIdx.x == 0) ls_alphas(alphas, A.P.lm_A, A.P.lm_beta);  // visible after the staging barrier
     const RobotParams* rob = stage_robots(smem_f, A.rs);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* const warps_f = smem_f + robots_smem_bytes(A.rs.n) / sizeof(float);
@@ -585,7 +590,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                 const LmW Sx = slot_state(sl);
                 int kind;
                 float alpha;
-                trial_item(i, P.lm_A, P.lm_beta, &kind, &alpha);
+                trial_item(i, P.lm_A, alphas, &kind, &alpha);
                 Sx.ok(i, l) = trial_cost(rob, A.tg, Sx.t(l), Sx, l, alpha, kind) < Sx.cost0(l) ? 1 : 0;
             }
             __syncthreads();
@@ -606,7 +611,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                 float al = 0.0f;
                 if (pick < per) {
                     int kind;
-                    trial_item(pick, P.lm_A, P.lm_beta, &kind, &al);
+                    trial_item(pick, P.lm_A, alphas, &kind, &al);
                     take_step(Rx, Sx, l, al, kind);
                     br = kind == kDirLm ? 0 : 1;
                     if (kind == kDirDogleg) al = 0.0f;  // no line-search alpha (as traced)
@@ -614,7 +619,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                     const int j = Sx.sc_j(l);
                     const float th0 = Sx.th(j, l), st = Sx.sc_step(l), c0 = Sx.cost0(l);
                     for (int q = 0; q <= P.lm_A; ++q) {
-                        const float a = ls_alpha(q, P.lm_beta);
+                        const float a = alphas[q];
                         const float thj = clampf(fmaf(a, st, th0), Rx.lo[j], Rx.hi[j]);
                         ++n_sc;
                         if (coord_cost(Sx, l, thj - th0) < c0) {
@@ -700,7 +705,8 @@ void launch_lm_w(const LmArgs& A, cudaStream_t st) {
     // a batch too small to give every SM a CTA of two warps (a single target, say): two-warp CTAs,
     // spread over more SMs with shorter lock-step stages (latency, not throughput, is at stake)
     if (A.C <= (int64_t)sm_count() * 64) warps = 2;
-    while (warps > 2 && robots_smem_bytes(A.rs.n) + (per_warp + sizeof(float) * 65) * warps + 4 > (size_t)optin)
+    // (the CTA lists: 65 words per warp and one; 256 bytes kept for the kernel's static arrays)
+    while (warps > 2 && robots_smem_bytes(A.rs.n) + (per_warp + sizeof(float) * 65) * warps + 4 + 256 > (size_t)optin)
         warps /= 2;
     if (warps == 2) launch_lm_t<TRACE, 2>(A, st);
     else if (warps == 4) launch_lm_t<TRACE, 4>(A, st);
