@@ -285,38 +285,28 @@ struct Q4 {
 
 // Unit quaternion of the rotation with columns c0 c1 c2 (Shepperd's method:
 // the largest of 4w^2, 4x^2, 4y^2, 4z^2 from the diagonal, the rest from the
-// off-diagonal sums), returned with w >= 0.
+// off-diagonal sums), returned with w >= 0.  The pivot is chosen first and one
+// square root serves every case, so lanes with different pivots do not
+// diverge; the pivot t = 4 max(w^2, x^2, y^2, z^2) is at least 1, and with
+// rs = 1/sqrt(t) the pivot component is t rs / 2 and the others are sums
+// times rs / 2.
 __device__ __forceinline__ Q4 quat_from_frame(const Frame& E) {
     const float m00 = E.c0.x, m10 = E.c0.y, m20 = E.c0.z;
     const float m01 = E.c1.x, m11 = E.c1.y, m21 = E.c1.z;
     const float m02 = E.c2.x, m12 = E.c2.y, m22 = E.c2.z;
     const float tr = m00 + m11 + m22;
-    float w, x, y, z;
-    if (tr >= m00 && tr >= m11 && tr >= m22) {
-        const float s = 2.0f * sqrtf(1.0f + tr), r = 1.0f / s;
-        w = 0.25f * s;
-        x = (m21 - m12) * r;
-        y = (m02 - m20) * r;
-        z = (m10 - m01) * r;
-    } else if (m00 >= m11 && m00 >= m22) {
-        const float s = 2.0f * sqrtf(1.0f + m00 - m11 - m22), r = 1.0f / s;
-        w = (m21 - m12) * r;
-        x = 0.25f * s;
-        y = (m01 + m10) * r;
-        z = (m02 + m20) * r;
-    } else if (m11 >= m22) {
-        const float s = 2.0f * sqrtf(1.0f + m11 - m00 - m22), r = 1.0f / s;
-        w = (m02 - m20) * r;
-        x = (m01 + m10) * r;
-        y = 0.25f * s;
-        z = (m12 + m21) * r;
-    } else {
-        const float s = 2.0f * sqrtf(1.0f + m22 - m00 - m11), r = 1.0f / s;
-        w = (m10 - m01) * r;
-        x = (m02 + m20) * r;
-        y = (m12 + m21) * r;
-        z = 0.25f * s;
-    }
+    const bool b0 = tr >= m00 && tr >= m11 && tr >= m22;
+    const bool b1 = !b0 && m00 >= m11 && m00 >= m22;
+    const bool b2 = !b0 && !b1 && m11 >= m22;
+    const float t = b0 ? 1.0f + tr : (b1 ? 1.0f + m00 - m11 - m22 : (b2 ? 1.0f + m11 - m00 - m22 : 1.0f + m22 - m00 - m11));
+    const float rs = rsqrtf(t);
+    const float h = 0.5f * t * rs, r = 0.5f * rs;
+    const float a = (m21 - m12) * r, bq = (m02 - m20) * r, c = (m10 - m01) * r;
+    const float d = (m01 + m10) * r, e = (m02 + m20) * r, f = (m12 + m21) * r;
+    const float w = b0 ? h : (b1 ? a : (b2 ? bq : c));
+    const float x = b0 ? a : (b1 ? h : (b2 ? d : e));
+    const float y = b0 ? bq : (b1 ? d : (b2 ? h : f));
+    const float z = b0 ? c : (b1 ? e : (b2 ? f : h));
     const float sg = (w < 0.0f) ? -1.0f : 1.0f;
     return Q4{sg * w, v3(sg * x, sg * y, sg * z)};
 }
