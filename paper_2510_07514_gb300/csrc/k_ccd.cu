@@ -141,7 +141,7 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
     if (kk > 0 && ep2 < P.cd_eps_pos2 && (P.cd_variant == 1 || eo * eo < P.cd_eps_ori2)) return 1;
     if (kk == cap) return 2;
     const int k = A.k0 + kk;
-    const float ep0 = sqrtf(ep2);
+    const float ep0 = sqrt_approx(ep2);
 
     if (P.cd_variant == 1) {
         // Alg. 1: joints from the last to the first, each rotated at once by its Eq. theta_proj
@@ -230,7 +230,7 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
     Q4 q1 = qmul(qerr, Q4{ca_, (-sa_) * Za});
     q1 = qmul(q1, Q4{cb_, (-sb_) * Zb});
     const V3 e1 = pt - x;
-    const float ep1 = sqrtf(dot(e1, e1));
+    const float ep1 = sqrt_approx(dot(e1, e1));
     const float eo1 = quat_angle(q1.w, dot(q1.v, q1.v));
     // acceptance (reading: an improvement above gamma in position or in orientation)
     const bool acc = (ep0 - ep1 > P.cd_gamma_pos) || (eo - eo1 > P.cd_gamma_ori);

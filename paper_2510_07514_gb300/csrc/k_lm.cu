@@ -320,7 +320,7 @@ __device__ __noinline__ void dogleg_prepare(const LmW S, int l, int n, float Rt,
         jgjg = fmaf(Jg[r], Jg[r], jgjg);
         ngn2 = fmaf(y2[r], My[r], ngn2);
     }
-    const float ac = jgjg > 0.0f ? gg / jgjg : 0.0f;
+    const float ac = jgjg > 0.0f ? __fdividef(gg, jgjg) : 0.0f;
     const float ngd2 = ac * ac * gg, R2 = Rt * Rt;
     float wgn = 1.0f, wgd = 0.0f;  // step = wgn * dgn + wgd * g
     if (ngn2 <= R2) {
@@ -375,12 +375,12 @@ __device__ __noinline__ void dogleg_prepare(const LmW S, int l, int n, float Rt,
         }
     }
     S.sc_j(l) = is;
-    S.sc_step(l) = cn > 0.0f ? clampf(gsel / cn, -Rt, Rt) : 0.0f;
+    S.sc_step(l) = cn > 0.0f ? clampf(__fdividef(gsel, cn), -Rt, Rt) : 0.0f;
     // the chosen joint's position column and axis without the row weights
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        S.sc_v(r, l) = csel[r] / S.W(r, l);
-        S.sc_z(r, l) = csel[3 + r] / S.W(3 + r, l);
+        S.sc_v(r, l) = __fdividef(csel[r], S.W(r, l));
+        S.sc_z(r, l) = __fdividef(csel[3 + r], S.W(3 + r, l));
     }
 }
 
