@@ -376,7 +376,8 @@ __device__ __forceinline__ float quat_angle(float w, float vv) { return 2.0f * a
 // omega of Eq. quat_diff
 __device__ __forceinline__ V3 quat_log(Q4 e) {
     const float vv = dot(e.v, e.v);
-    const float f = (vv > 1e-30f) ? 2.0f * atan2_q1(sqrt_approx(vv), e.w) * rsqrtf(vv) : 2.0f / e.w;  // e.w >= 0
+    const float rs = rsqrtf(vv);  // |v| = vv rs
+    const float f = (vv > 1e-30f) ? 2.0f * atan2_q1(vv * rs, e.w) * rs : __fdividef(2.0f, e.w);  // e.w >= 0
     return f * e.v;
 }
 

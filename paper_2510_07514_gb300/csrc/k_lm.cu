@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                     }
                 }
                 const float e[6] = {epv.x, epv.y, epv.z, om.x, om.y, om.z};
-                const float wo = T.eps_pos / T.eps_ori;
+                const float wo = __fdividef(T.eps_pos, T.eps_ori);
                 float W[6], b[6], cost0 = 0.0f;
 #pragma unroll
                 for (int r = 0; r < 6; ++r) {
