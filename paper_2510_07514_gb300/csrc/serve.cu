@@ -103,7 +103,15 @@ void CUDART_CB on_batch_done(void* p) {
     delete a;
 }
 
-size_t grow(size_t need) { return align_up(need + need / 4, 1 << 20); }
+// Capacities double when a batch outgrows them (each regrowth frees and allocates while other
+// streams run, so it should be rare).
+size_t grow(size_t need) { return align_up(2 * need, 1 << 20); }
+
+// Initial capacities of a slot, allocated when the server starts so that the first requests do
+// not pay for allocation: 256 MB of device workspace (or the slot's budget), 4 MB of pinned
+// head image and of pinned results.
+constexpr size_t kSlotWs0 = size_t(256) << 20;
+constexpr size_t kSlotPin0 = size_t(4) << 20;
 
 }  // namespace
 
@@ -183,11 +191,12 @@ bool Server::launch(Slot& sl, std::vector<Req*>& take) {
         if (st == HJCD_OK && W.bytes > slot_budget) st = HJCD_ENOMEM;
         const size_t res_bytes = 4 * (size_t)(W.q_total + W.e_total + W.T) + 16;
         if (st == HJCD_OK && W.bytes > sl.ws_cap) {
-            if (sl.ws) cudaFree(sl.ws);
+            // stream-ordered: freeing the old workspace does not wait for the other streams
+            if (sl.ws) cudaFreeAsync(sl.ws, sl.s);
             sl.ws = nullptr;
             sl.ws_cap = 0;
             const size_t cap = std::min(grow(W.bytes), std::max(slot_budget, W.bytes));
-            if (cudaMalloc(&sl.ws, cap) != cudaSuccess) {
+            if (cudaMallocAsync(reinterpret_cast<void**>(&sl.ws), cap, sl.s) != cudaSuccess) {
                 cudaGetLastError();
                 st = HJCD_ENOMEM;
             } else {
@@ -310,7 +319,8 @@ void server_stop(hjcd_ctx* ctx) {
     if (sv->th.joinable()) sv->th.join();
     for (Slot& sl : sv->slots) {
         if (sl.s) cudaStreamSynchronize(sl.s);
-        if (sl.ws) cudaFree(sl.ws);
+        if (sl.ws) cudaFreeAsync(sl.ws, sl.s);
+        if (sl.s) cudaStreamSynchronize(sl.s);
         if (sl.pin) cudaFreeHost(sl.pin);
         if (sl.pout) cudaFreeHost(sl.pout);
         if (sl.s) cudaStreamDestroy(sl.s);
@@ -353,7 +363,14 @@ hjcd_status hjcd_server_start(hjcd_ctx* ctx, const hjcd_server_opts* opts) {
     }
     sv->slot_budget = budget / (size_t)sv->max_inflight;
     sv->slots.resize(sv->max_inflight);
-    for (Slot& sl : sv->slots) HJCD_CUDA(ctx, cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking));
+    for (Slot& sl : sv->slots) {
+        HJCD_CUDA(ctx, cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking));
+        const size_t ws0 = std::min(kSlotWs0, sv->slot_budget);
+        if (cudaMallocAsync(reinterpret_cast<void**>(&sl.ws), ws0, sl.s) == cudaSuccess) sl.ws_cap = ws0;
+        if (cudaMallocHost(&sl.pin, kSlotPin0) == cudaSuccess) sl.pin_cap = kSlotPin0;
+        if (cudaMallocHost(&sl.pout, kSlotPin0) == cudaSuccess) sl.pout_cap = kSlotPin0;
+        cudaGetLastError();  // a failed reservation is retried, sized to the batch, when one needs it
+    }
     Server* raw = sv.release();
     ctx->server = raw;
     raw->th = std::thread([raw] { raw->run(); });
