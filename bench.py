@@ -188,10 +188,12 @@ def flops_collide_cand(n, n_sph):
 
 
 def kernel_source_hash():
+    """sha256 of the device code (csrc/k_*.cu and the shared *.cuh), first 12 hex digits: a
+    committed ncu figure counts only while it matches."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2510_07514_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
+        if (f.startswith("k_") and f.endswith(".cu")) or f.endswith(".cuh"):
             h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:12]
 
