@@ -769,6 +769,8 @@ def hjcd_arm(args):
             "per_kernel": {k: {"ms": float(ph[names.index(k)]), "gflop": fl[k] / 1e9,
                                "tflops": fl[k] / (ph[names.index(k)] * 1e-3) / 1e12} for k in fl}}
     ffma = hjcd.hjcd_ffma_probe(ctx.h, 2048, stream)
+    # the same against the FP32 rate an FFMA loop measures on this GPU in this run (of measured)
+    roof["frac_of_measured_ffma"] = achieved / ffma if ffma > 0 else None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
