@@ -384,6 +384,38 @@ def test_pjik_converges_like_the_oracle(ctx):
     assert np.all(gth >= rob.lo - 1e-7) and np.all(gth <= rob.hi + 1e-7)
 
 
+@pytest.mark.parametrize("A,beta", [(0, 2.0), (2, 3.0), (7, 2.0)])
+def test_pjik_line_search_depths(ctx, A, beta):
+    """Other line-search depths A and ratios beta (the trial rows, the alpha
+    table and the single-coordinate search all follow A): convergence as the
+    oracle's with the same parameters, every claimed solution verified."""
+    rob = inputs.panda()
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    rng = np.random.default_rng(40 + A)
+    T, C = 16, 1024
+    tth = rng.uniform(rob.lo, rob.hi, (T, 7))
+    tg = f32(orc.pose(orob, f32(tth)))
+    tgt = np.repeat(np.arange(T), C // T).astype(np.int32)
+    cand = np.tile(np.arange(C // T), T).astype(np.int32)
+    th = f32(np.clip(tth[tgt] + rng.normal(0, 0.1, (C, 7)), rob.lo, rob.hi))
+    theta = soa(th)
+    perr = torch.empty((C,), device="cuda")
+    oerr = torch.empty((C,), device="cuda")
+    P = api.make_params(lm_A=A, lm_beta=beta)
+    hjcd.hjcd_pjik(ctx.h, rid, T, dev(tg), 1e-3, 1e-2, 7, P, C, dev(tgt, torch.int32), dev(cand, torch.int32),
+                   theta, C, 0, P.lm_max_iters, None, perr, oerr)
+    o = orc.pjik(orob, orc.make_params(seed=7, lm_A=A, lm_beta=beta), tg, tgt, cand, th)
+    ok_g = (host(perr) < 1e-3) & (host(oerr) < 1e-2)
+    ok_o = (o["perr"] < 1e-3) & (o["oerr"] < 1e-2)
+    assert abs(ok_g.mean() - ok_o.mean()) < 0.02
+    gth = host(theta).T
+    for c in np.nonzero(ok_g)[0][:200]:
+        e = orc.residual(orob, gth[c], tg[tgt[c]])
+        assert np.linalg.norm(e[:3]) < 1e-3 + 1e-5 and np.linalg.norm(e[3:]) < 1e-2 + 1e-5
+    assert np.all(gth >= rob.lo - 1e-7) and np.all(gth <= rob.hi + 1e-7)
+
+
 # ----------------------------------------------------------------------------
 # a7: collision filter
 
