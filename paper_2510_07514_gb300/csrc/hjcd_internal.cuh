@@ -511,6 +511,15 @@ struct CcdArgs {
     Counters* cnt;
     int32_t block;  // threads (candidates) per CTA: 64, 128 (default, also for 0) or 256
     int32_t seed_base;  // added to each candidate's index inside its target (a shard of the seeds)
+    // Iteration segments (no trace, th_out set): this launch runs iterations [seg_begin, seg_end)
+    // (seg_end 0: to the cap) of every candidate, or of the candidates list_in[0 .. *n_in) whose
+    // state th_out holds; a candidate still iterating at seg_end keeps its state in th_out and is
+    // appended to list_out (count *n_out) instead of writing its results.
+    int32_t seg_begin, seg_end;
+    const int32_t* list_in;
+    const int32_t* n_in;
+    int32_t* list_out;
+    int32_t* n_out;
 };
 
 struct LmArgs {

@@ -162,7 +162,7 @@ struct WavePlan {
            head = 0;
     // the rest of the workspace
     size_t o_thM = 0, o_thM2 = 0, o_sM = 0, o_thB = 0, o_sB = 0, o_pB = 0, o_oB = 0, o_hB = 0, o_q = 0, o_e = 0, o_c = 0,
-           o_ul = 0, o_qf = 0, bytes = 0;
+           o_ul = 0, o_sg = 0, o_qf = 0, bytes = 0;
     bool host_out = false;  // some output goes to host memory
 };
 

@@ -304,8 +304,13 @@ __global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
     const float one_m_tie = 1.0f - P.cd_tie;
     unsigned long long n_it = 0, n_cand = 0;
 
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < A.C;
-         c += (int64_t)gridDim.x * blockDim.x) {
+    // a segment of the iterations (seg_end > 0): candidates still iterating at seg_end are handed
+    // to the next launch through list_out, which runs them from there (list_in)
+    const int64_t items = A.list_in ? (int64_t)*A.n_in : A.C;
+    const int k_end = A.seg_end > 0 ? A.seg_end : 0x7fffffff;
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < items;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = A.list_in ? (int64_t)A.list_in[it] : it;
         int32_t t, s;
         if (!A.map.lookup_search(c, t, s)) continue;
         s += A.seed_base;
@@ -314,9 +319,12 @@ __global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
         const int n = R.n;
         const Col col{colbase, n};
         const V3 pt = v3(T.p[0], T.p[1], T.p[2]);
-        ++n_cand;
+        if (!A.list_in) ++n_cand;
 
-        if (A.th_in) {
+        if (A.list_in) {  // the state the previous segment left
+#pragma unroll 1
+            for (int j = 0; j < n; ++j) col.th(j) = A.th_out[j * A.ld + c];
+        } else if (A.th_in) {
 #pragma unroll 1
             for (int j = 0; j < n; ++j) col.th(j) = A.th_in[j * A.ld + c];
         } else {
@@ -325,12 +333,26 @@ __global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
 
         const int cap = A.n_iters >= 0 ? A.n_iters : T.cd_iters;
         float delta_k = P.cd_delta0 * powf(P.cd_rho, (float)A.k0);
+#pragma unroll 1
+        for (int q = 0; q < A.seg_begin; ++q) delta_k *= P.cd_rho;  // the bits of one run from k0
         const float inv_p2 = 1.0f / (T.eps_pos * T.eps_pos), inv_o2 = 1.0f / (T.eps_ori * T.eps_ori);
         int iters = cap;
         float ep2 = 0.0f, eo = 0.0f;
         const bool valid = T.eps_pos > 0.0f;
+        bool handed = false;
 
-        for (int kk = 0; valid; ++kk) {
+        for (int kk = A.seg_begin; valid; ++kk) {
+            if (kk == k_end && kk < cap) {
+                // still iterating at the segment's end: keep the state, list the candidate
+                const unsigned m = __activemask();
+                const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(A.n_out, __popc(m));
+                base = __shfl_sync(m, base, leader);
+                A.list_out[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)c;
+                handed = true;
+                break;
+            }
             const int r = ccd_step<TRACE, TH>(rob, R, T, P, col, slots, A, c, (uint32_t)s, kk, cap, delta_k, pt, pe2,
                                               one_m_tie, inv_p2, inv_o2, ep2, eo);
             if (r == 1) iters = kk;
@@ -339,6 +361,11 @@ __global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
             ++n_it;
         }
 
+        if (handed) {
+#pragma unroll 1
+            for (int j = 0; j < n; ++j) A.th_out[j * A.ld + c] = col.th(j);
+            continue;
+        }
         if (A.th_out) {
 #pragma unroll 1
             for (int j = 0; j < n; ++j) A.th_out[j * A.ld + c] = col.th(j);

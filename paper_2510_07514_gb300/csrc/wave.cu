@@ -147,7 +147,8 @@ hjcd_status plan_wave(hjcd_ctx* ctx, const WaveItem* items, int n_items, const h
     W.o_e = cv.take<float>(W.e_total);
     W.o_c = cv.take<int32_t>(W.T);
     W.o_ul = cv.take<int32_t>(W.T);           // targets left to the second collision pass
-    W.o_qf = cv.take<unsigned long long>(2);  // queue head, error flag, count of o_ul
+    W.o_sg = cv.take<int32_t>(2 * (size_t)W.CM);  // PO-CCD candidates handed between segments
+    W.o_qf = cv.take<unsigned long long>(3);  // queue head, error flag, count of o_ul, counts of o_sg
     W.bytes = cv.off;
     return HJCD_OK;
 }
@@ -236,7 +237,7 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
                                              sizeof(float) * W.n_max, items[i].q_ref,
                                              sizeof(float) * items[i].rob->P.n, sizeof(float) * items[i].rob->P.n,
                                              (size_t)items[i].T, cudaMemcpyDeviceToDevice, s));
-    HJCD_CUDA(ctx, cudaMemsetAsync(ws + W.o_qf, 0, 16, s));
+    HJCD_CUDA(ctx, cudaMemsetAsync(ws + W.o_qf, 0, 24, s));
     HJCD_CUDA(ctx, cudaMemsetAsync(ws + W.o_q, 0xff, sizeof(float) * (size_t)W.q_total, s));  // unfilled rows: NaN
     HJCD_CUDA(ctx, cudaMemsetAsync(ws + W.o_e, 0xff, sizeof(float) * (size_t)W.e_total, s));
 
@@ -273,8 +274,31 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
     ca.P = P;
     ca.cnt = ctx->cnt;
     ca.block = ctx->ccd_block;
-    launch_ccd(ca, false, s);
-    if ((st = after_launch(ctx, 1, "k_ccd"))) return st;
+    // Iteration segments: a lane whose candidate meets the coarse tolerance waits for the rest of
+    // its warp, so the iterations run in three launches ([0, cap/2), [cap/2, 3 cap/4), the rest)
+    // and the candidates still iterating are packed afresh into full warps for the next (the same
+    // results: each candidate's state, iteration index and random streams carry over).
+    int cap_max = 0;
+    for (int i = 0; i < W.n_items; ++i) cap_max = std::max(cap_max, items[i].cd_iters >= 0 ? items[i].cd_iters : P.cd_max_iters);
+    if (P.cd_variant != 2 && cap_max >= 8) {
+        int32_t* lists = reinterpret_cast<int32_t*>(ws + W.o_sg);
+        int32_t* counts = reinterpret_cast<int32_t*>(ws + W.o_qf + 16);
+        const int seg[3] = {0, cap_max / 2, (3 * cap_max) / 4};
+        for (int g = 0; g < 3; ++g) {
+            CcdArgs cg = ca;
+            cg.seg_begin = seg[g];
+            cg.seg_end = g < 2 ? seg[g + 1] : 0;
+            cg.list_in = g > 0 ? lists + (size_t)((g - 1) & 1) * W.CM : nullptr;
+            cg.n_in = g > 0 ? counts + ((g - 1) & 1) : nullptr;
+            cg.list_out = g < 2 ? lists + (size_t)(g & 1) * W.CM : nullptr;
+            cg.n_out = g < 2 ? counts + (g & 1) : nullptr;
+            launch_ccd(cg, false, s);
+            if ((st = after_launch(ctx, 1, "k_ccd"))) return st;
+        }
+    } else {
+        launch_ccd(ca, false, s);
+        if ((st = after_launch(ctx, 1, "k_ccd"))) return st;
+    }
     if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[1], s));
 
     // top-K and perturbed duplication
