@@ -277,10 +277,13 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
     // Iteration segments: a lane whose candidate meets the coarse tolerance waits for the rest of
     // its warp, so the iterations run in three launches ([0, cap/2), [cap/2, 3 cap/4), the rest)
     // and the candidates still iterating are packed afresh into full warps for the next (the same
-    // results: each candidate's state, iteration index and random streams carry over).
+    // results: each candidate's state, iteration index and random streams carry over).  Only for
+    // waves that fill the GPU many times over with equal seed counts: a small wave pays the extra
+    // launches in latency, and the mixed eight-chain batch (unequal counts) measured slower.
     int cap_max = 0;
     for (int i = 0; i < W.n_items; ++i) cap_max = std::max(cap_max, items[i].cd_iters >= 0 ? items[i].cd_iters : P.cd_max_iters);
-    if (P.cd_variant != 2 && cap_max >= 8) {
+    const bool segments = P.cd_variant != 2 && cap_max >= 8 && W.min_m == W.max_m && W.CM >= (int64_t)sm_count() * 2048;
+    if (segments) {
         int32_t* lists = reinterpret_cast<int32_t*>(ws + W.o_sg);
         int32_t* counts = reinterpret_cast<int32_t*>(ws + W.o_qf + 16);
         const int seg[3] = {0, cap_max / 2, (3 * cap_max) / 4};
