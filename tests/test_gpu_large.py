@@ -265,3 +265,36 @@ def test_ranked_collision_filter_equals_filtering_every_candidate(ctx, dense):
         assert tests[1] < tests[0] / 4
     if dense:
         assert np.mean(outs[0][2] < 8) > 0.2  # many targets lack 8 collision-free solutions: rounds run out
+
+
+def test_po_ccd_iteration_segments_equal_one_launch(ctx):
+    """A wave of equal seed counts that fills every SM with 2048+ seeds runs
+    PO-CCD in three launches (iteration segments, the candidates still
+    iterating repacked between them); one target with a seed fewer makes the
+    counts unequal and the wave runs PO-CCD in one launch.  Every other
+    target's results are bit-identical (each candidate's state, iteration
+    index and random streams carry across the segments)."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    M = 1000
+    T = -(-sms * 2048 // M) + 8
+    wl = inputs.cfg2(T, M)
+    rid, sid = ctx.add_robot(wl.robot), ctx.set_scene(wl.scene)
+    orob = orc.Robot(wl.robot)
+    pool = f32(wl.theta_gen)
+    hit, _ = orc.collide(orob, orc.Scene(wl.scene), pool)
+    tg = torch.as_tensor(f32(orc.pose(orob, pool[~hit][:T])), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    n0 = hjcd.hjcd_launch_count(ctx.h)
+    seg = [host(x) for x in ctx.solve(rid, sid, tg, M, 4, 17, 7)]
+    n1 = hjcd.hjcd_launch_count(ctx.h)
+    spt = np.full(T, M)
+    spt[-1] = M - 1
+    one = [host(x) for x in ctx.solve(rid, sid, tg, 0, 4, 17, 7, samples_per_target=spt)]
+    n2 = hjcd.hjcd_launch_count(ctx.h)
+    assert (n1 - n0) - (n2 - n1) == 2
+    (qa, ea, ca), (qb, eb, cb) = seg, one
+    assert np.array_equal(ca[:-1], cb[:-1])
+    assert ca.sum() > 2 * T  # targets at collision-free configurations: most find solutions
+    for t in range(T - 1):
+        assert np.array_equal(qa[t, :ca[t]], qb[t, :cb[t]])
+        assert np.array_equal(ea[t, :ca[t]], eb[t, :cb[t]])
