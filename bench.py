@@ -18,6 +18,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -187,14 +188,23 @@ def flops_collide_cand(n, n_sph):
     return 18 * n_sph + 54 * n + 63
 
 
+def _strip_comments(src: str) -> str:
+    """C++ source without its comments, trailing blanks and blank lines (the kernel sources hold
+    no comment markers inside string literals)."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+
+
 def kernel_source_hash():
-    """sha256 of the device code (csrc/k_*.cu and the shared *.cuh), first 12 hex digits: a
-    committed ncu figure counts only while it matches."""
+    """sha256 of the device code (csrc/k_*.cu and the shared *.cuh, comments and blank lines
+    removed), first 12 hex digits: a committed ncu figure counts only while it matches."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2510_07514_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
         if (f.startswith("k_") and f.endswith(".cu")) or f.endswith(".cuh"):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+            h.update(f.encode() + b"\0")
+            h.update(_strip_comments(open(os.path.join(csrc, f), encoding="utf-8").read()).encode())
     return h.hexdigest()[:12]
 
 

@@ -59,6 +59,41 @@ struct CcdTrials {
     float dq, pq2, rq, so;  // orientation trial
 };
 
+// The two trials of a joint share their arithmetic once the steps are known, so from there on
+// they run as pairs (.x the position trial, .y the orientation trial) on the packed FP32
+// instructions of sm_100+ (two IEEE operations per instruction, each half rounded on its own), in
+// the order of the scalar helpers (dot, fma3, quat_angle); where the compiler contracts the scalar
+// helpers differently the results differ by an ulp.
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// p(t^2) of atan01 for both halves (atan t = t p(t^2), t in [0, 1])
+__device__ __forceinline__ float2 atan_poly2(float2 t) {
+    const float2 s = mul2(t, t);
+    float2 p = fma2(bc2(-4.054563120e-03f), s, bc2(2.186294831e-02f));
+    p = fma2(p, s, bc2(-5.591232702e-02f));
+    p = fma2(p, s, bc2(9.642198682e-02f));
+    p = fma2(p, s, bc2(-1.390863061e-01f));
+    p = fma2(p, s, bc2(1.994656622e-01f));
+    p = fma2(p, s, bc2(-3.332985938e-01f));
+    return fma2(p, s, bc2(9.999993443e-01f));
+}
+
+// quat_angle of both halves: 2 atan2(sqrt(vv), |w|); the reflection about pi/4 takes the last
+// product into one rounding, 2 (pi/2 - t p) = pi - 2 t p
+__device__ __forceinline__ float2 quat_angle2(float2 w, float2 vv) {
+    const float yx = sqrt_approx(vv.x), yy = sqrt_approx(vv.y);
+    const float xx = fabsf(w.x), xy = fabsf(w.y);
+    const float mxx = fmaxf(xx, yx), mnx = fminf(xx, yx), mxy = fmaxf(xy, yy), mny = fminf(xy, yy);
+    const float2 t = make_float2(mxx > 0.0f ? __fdividef(mnx, mxx) : 0.0f, mxy > 0.0f ? __fdividef(mny, mxy) : 0.0f);
+    const float2 p = atan_poly2(t);
+    const float2 a = mul2(mul2(bc2(2.0f), t), p);                                      // 2 t p
+    const float2 r = fma2(mul2(bc2(-2.0f), t), p, bc2(2.0f * 1.57079632679489662f));  // pi - 2 t p
+    return make_float2(yx > xx ? r.x : a.x, yy > xy ? r.y : a.y);
+}
+
 __device__ __forceinline__ CcdTrials ccd_joint_trials(const V3 pj, const V3 z, float thj, float lo, float hi,
                                                       const V3 Ep, const V3 pt, const Q4 qerr, float phi,
                                                       float delta_k, float pe2, float inv_p2, float inv_o2) {
@@ -78,30 +113,45 @@ __device__ __forceinline__ CcdTrials ccd_joint_trials(const V3 pj, const V3 z, f
     // Eq. theta_proj, signed about the axis: atan2(z.(up x vp), up.vp) = atan2(zxu.vp, up.vp)
     const float cs = dot(up, vp), sn = dot(zxu, vp);
     const bool deg = nu2 < 1e-24f || nv2 < 1e-24f || nup2 <= pe2 * nu2 || nvp2 <= pe2 * nv2;
-    float d = deg ? 0.0f : atan2_all(sn, cs);
-    d = clampf(thj + d, lo, hi) - thj;
-    float sh, ch;
-    __sincosf(0.5f * d, &sh, &ch);
-    V3 r = fma3(-2.0f * sh * ch, zxu, fma3(-fmaf(-2.0f * sh, sh, 1.0f), up, r0));
-    o.d = d;
-    o.rp2 = dot(r, r);
-    float w2 = fmaf(qerr.w, ch, sh * az);
-    V3 v2 = fma3(ch, qerr.v, (-sh) * qz);
-    o.op = quat_angle(w2, dot(v2, v2));
-    o.sp = fmaf(o.rp2, inv_p2, o.op * o.op * inv_o2);
-
+    const float d = deg ? 0.0f : atan2_all(sn, cs);
     // Eq. ori_update: delta(k) sgn(a.z) phi
     const float sg = (az > 0.0f) ? 1.0f : ((az < 0.0f) ? -1.0f : 0.0f);
-    float dq = delta_k * sg * phi;
-    dq = clampf(thj + dq, lo, hi) - thj;
-    __sincosf(0.5f * dq, &sh, &ch);
-    r = fma3(-2.0f * sh * ch, zxu, fma3(-fmaf(-2.0f * sh, sh, 1.0f), up, r0));
-    o.dq = dq;
-    o.pq2 = dot(r, r);
-    w2 = fmaf(qerr.w, ch, sh * az);
-    v2 = fma3(ch, qerr.v, (-sh) * qz);
-    o.rq = quat_angle(w2, dot(v2, v2));
-    o.so = fmaf(o.pq2, inv_p2, o.rq * o.rq * inv_o2);
+    const float dq = delta_k * sg * phi;
+
+    // both steps clamped to the limits
+    float2 st = add2(bc2(thj), make_float2(d, dq));
+    st = make_float2(clampf(st.x, lo, hi), clampf(st.y, lo, hi));
+    st = add2(st, bc2(-thj));
+    o.d = st.x;
+    o.dq = st.y;
+    const float2 hs = mul2(bc2(0.5f), st);
+    float2 sh, ch;
+    __sincosf(hs.x, &sh.x, &ch.x);
+    __sincosf(hs.y, &sh.y, &ch.y);
+    const float2 m2sh = mul2(bc2(-2.0f), sh);
+    const float2 msn = mul2(m2sh, ch);             // -sin(step)
+    const float2 cst = fma2(m2sh, sh, bc2(1.0f));  // cos(step)
+    // position residual of each trial
+    const V3 rp = fma3(msn.x, zxu, fma3(-cst.x, up, r0));
+    const V3 rq = fma3(msn.y, zxu, fma3(-cst.y, up, r0));
+    float2 r2 = mul2(make_float2(rp.z, rq.z), make_float2(rp.z, rq.z));
+    r2 = fma2(make_float2(rp.y, rq.y), make_float2(rp.y, rq.y), r2);
+    r2 = fma2(make_float2(rp.x, rq.x), make_float2(rp.x, rq.x), r2);
+    // error quaternion of each trial: qerr [cos, -sin z]
+    const float2 w2 = fma2(bc2(qerr.w), ch, mul2(sh, bc2(az)));
+    const float2 nsh = mul2(bc2(-1.0f), sh);
+    const float2 vx = fma2(ch, bc2(qerr.v.x), mul2(nsh, bc2(qz.x)));
+    const float2 vy = fma2(ch, bc2(qerr.v.y), mul2(nsh, bc2(qz.y)));
+    const float2 vz2 = fma2(ch, bc2(qerr.v.z), mul2(nsh, bc2(qz.z)));
+    const float2 vv = fma2(vx, vx, fma2(vy, vy, mul2(vz2, vz2)));
+    const float2 ang = quat_angle2(w2, vv);
+    const float2 sc = fma2(r2, bc2(inv_p2), mul2(mul2(ang, ang), bc2(inv_o2)));
+    o.rp2 = r2.x;
+    o.op = ang.x;
+    o.sp = sc.x;
+    o.pq2 = r2.y;
+    o.rq = ang.y;
+    o.so = sc.y;
     return o;
 }
 
@@ -294,7 +344,6 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
 template <bool TRACE, int TH>
 __global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
     using Col = ColT<TH>;
-    constexpr int kCcdThreads = TH;
     extern __shared__ __align__(16) float sm[];
     const RobotParams* rob = stage_robots(sm, A.rs);
     uint32_t* const slots = reinterpret_cast<uint32_t*>(sm + robots_smem_bytes(A.rs.n) / sizeof(float));
