@@ -330,3 +330,41 @@ def test_solve_nearest_ranks_by_distance_to_the_current_configuration(ctx):
     ctx.solve_batch([it1, it2])
     _same(o1, (dev(q1), dev(e1), torch.as_tensor(c1, device="cuda")))
     _same(o2, (dev(q0), dev(e0), torch.as_tensor(c0, device="cuda")))
+
+
+def test_segmented_mixed_robot_batch_equals_each_request_alone(ctx):
+    """Two robots (7 and 12 joints) with equal seed counts and enough seeds in
+    total to fill every SM with 2048+ run PO-CCD as three iteration segments,
+    whose hand-over lists then mix the robots' candidates; alone, each request
+    is below that size and runs PO-CCD in one launch.  Same bits either way."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    M = 1000
+    T1 = sms * 2048 // (2 * M) + 8   # each request alone stays below sms * 2048 seeds
+    T2 = sms * 2048 // M - T1 + 8    # together they exceed it
+    robs = _robots()
+    rng = np.random.default_rng(77)
+    rA, rB = ctx.add_robot(robs[0]), ctx.add_robot(robs[2])
+    sid = ctx.set_scene(inputs.random_scene(rng, 40, 4))
+    tA = dev(f32(orc.pose(orc.Robot(robs[0]), f32(rng.uniform(robs[0].lo, robs[0].hi, (T1, robs[0].n))))))
+    tB = dev(f32(orc.pose(orc.Robot(robs[2]), f32(rng.uniform(robs[2].lo, robs[2].hi, (T2, robs[2].n))))))
+    assert (T1 + T2) * M >= sms * 2048 and max(T1, T2) * M < sms * 2048
+    itA, oA = ctx.batch_item(rA, sid, tA, M, 3, 31, robs[0].n)
+    itB, oB = ctx.batch_item(rB, -1, tB, M, 2, 32, robs[2].n)
+    torch.cuda.synchronize()
+    n0 = hjcd.hjcd_launch_count(ctx.h)
+    ctx.solve_batch([itA, itB])
+    torch.cuda.synchronize()
+    n1 = hjcd.hjcd_launch_count(ctx.h)
+    aloneA = ctx.solve(rA, sid, tA, M, 3, 31, robs[0].n)
+    torch.cuda.synchronize()
+    n2 = hjcd.hjcd_launch_count(ctx.h)
+    aloneB = ctx.solve(rB, -1, tB, M, 2, 32, robs[2].n)
+    assert (n1 - n0) - (n2 - n1) == 2  # the batch's PO-CCD took three launches, the request alone one
+    for got, ref in ((oA, aloneA), (oB, aloneB)):
+        (qa, ea, ca), (qb, eb, cb) = [host(x) for x in got], [host(x) for x in ref]
+        ca, cb = ca.astype(np.int64), cb.astype(np.int64)
+        assert np.array_equal(ca, cb)
+        assert ca.sum() > 0
+        for t in range(len(ca)):
+            assert np.array_equal(qa[t, :ca[t]], qb[t, :cb[t]])
+            assert np.array_equal(ea[t, :ca[t]], eb[t, :cb[t]])

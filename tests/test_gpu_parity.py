@@ -169,7 +169,7 @@ def _ccd_gpu(ctx, rid, n, tg, tgt, cand, th, k, params, seed):
     return out
 
 
-@pytest.mark.parametrize("which", ["panda", "chain12", "chain20"])
+@pytest.mark.parametrize("which", ["panda", "chain3", "chain12", "chain20", "chain24"])
 def test_ccd_iteration_trace_parity(ctx, which):
     rob = dict(robots())[which]
     rid = ctx.add_robot(rob)
@@ -318,7 +318,7 @@ def _cond(J, W, lam):
     return ev[-1] / ev[0]
 
 
-@pytest.mark.parametrize("which", ["panda", "chain12", "chain20"])
+@pytest.mark.parametrize("which", ["panda", "chain12", "chain20", "chain24"])
 def test_lm_iteration_trace_parity(ctx, which):
     rob = dict(robots())[which]
     rid = ctx.add_robot(rob)
