@@ -162,6 +162,11 @@ __device__ __forceinline__ CcdTrials ccd_joint_trials(const V3 pj, const V3 z, f
 // cap (no update in either case), 0 after an update.
 constexpr int kSlotWords = 8;  // per-thread shared-memory slot of the cooperative perturbation
 
+// w / nb = (w * kDivMagic[nb]) >> 16 exactly for 1 <= nb <= 12 and 0 <= w < 32 nb (the normal
+// pairs of a joint vector, at most 12, times the lanes of a warp); kDivMagic[nb] = ceil(2^16 / nb)
+__constant__ uint32_t kDivMagic[13] = {0, 65536, 32768, 21846, 16384, 13108, 10923, 9363, 8192, 7282, 6554, 5958, 5462};
+static_assert((kMaxDof + 1) / 2 <= 12, "the normal pairs of a joint vector index kDivMagic");
+
 template <bool TRACE, int TH>
 __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParams& R, const TargetDesc& T,
                                         const hjcd_params& P, const ColT<TH>& col, uint32_t* slots, const CcdArgs& A,
@@ -320,8 +325,9 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
         const int NB = (int)__reduce_max_sync(am, acc ? 0u : (uint32_t)((n + 1) / 2));
         __syncwarp(am);
         const int items = __popc(rej) * NB, step = __popc(am);
+        const uint32_t magic = kDivMagic[NB];
         for (int w = __popc(am & ((1u << lane) - 1u)); w < items; w += step) {
-            const int r = w / NB, b = w - r * NB;
+            const int r = (int)(((uint32_t)w * magic) >> 16), b = w - r * NB;
             const int sl = __fns(rej, 0, r + 1);
             const uint32_t* q = slot + sl * kSlotWords;
             const RobotParams& Rs = rob[q[5]];
