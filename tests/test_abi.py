@@ -120,3 +120,27 @@ def test_device_arctangent_polynomial_error_bound():
     Y, X = np.meshgrid(g, g)
     ref = np.arctan2(Y.astype(np.float64), X.astype(np.float64))
     assert np.max(np.abs(atan2_all(Y, X) - ref)) < 3e-7
+
+
+def test_device_ccd_constants():
+    """Constants of the PO-CCD kernel read from its source: the table that
+    replaces the division of the perturbation items (k_ccd.cu, kDivMagic) gives
+    w / nb exactly, without overflowing 32 bits, for every item w < 32 nb of
+    1..12 normal pairs; and the packed arctangent of the trials uses the
+    coefficients of the scalar one (hjcd_internal.cuh, atan01)."""
+    import re
+    csrc = os.path.join(ROOT, "paper_2510_07514_gb300", "csrc")
+    ccd = open(os.path.join(csrc, "k_ccd.cu")).read()
+    table = re.search(r"kDivMagic\[13\] = \{([^}]*)\}", ccd).group(1)
+    magic = [int(x) for x in table.split(",")]
+    assert len(magic) == 13
+    for nb in range(1, 13):
+        w = np.arange(32 * nb, dtype=np.uint64)
+        prod = w * np.uint64(magic[nb])
+        assert int(prod.max()) < 2 ** 32
+        assert np.array_equal(prod >> np.uint64(16), w // np.uint64(nb)), nb
+    coef = r"([-+]?\d\.\d+e[-+]\d+)f"
+    inc = open(os.path.join(csrc, "hjcd_internal.cuh")).read()
+    scalar = re.findall(coef, inc[inc.index("float atan01(float t)"):inc.index("float atan2_q1(")])
+    packed = re.findall(coef, ccd[ccd.index("float2 atan_poly2(float2 t)"):ccd.index("float2 quat_angle2(")])
+    assert len(scalar) == 8 and packed == scalar
