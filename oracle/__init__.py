@@ -95,13 +95,15 @@ _SIGS = {
     "orc_dup_layout": (ct.c_int64, [ct.c_int64, ct.c_int32, _I64, _I64]),
     "orc_topk_dup": (None, [_P, ct.POINTER(Params), ct.c_int64, _I64, _D, _D, _I64, _D, _I32]),
     "orc_lm_iteration_batch": (None, [_P, ct.POINTER(Params), _D, ct.c_int64, _I32, _I32, ct.c_int,
-                                      _D, _D, _D, _D, _D, _I32, _D, _D, _U8]),
+                                      _D, _D, _D, _D, _D, _I32, _D, _D, _U8, _D, _I32, _D]),
     "orc_lm_step": (None, [ct.c_int, _D, _D, ct.c_double, ct.c_double, _D]),
     "orc_dogleg_step": (None, [ct.c_int, _D, _D, ct.c_double, ct.c_double, _D]),
+    "orc_single_coord_step": (None, [ct.c_int, _D, _D, ct.c_double, _I32, _D]),
     "orc_pjik_batch": (None, [_P, ct.POINTER(Params), _D, ct.c_int64, _I32, _I32, _D, _D, _D, _D, _I32]),
     "orc_collide_batch": (None, [_P, _P, ct.c_int64, _D, _U8, _D]),
-    "orc_rank": (None, [_P, ct.c_int64, _I64, _D, _D, _D, _D, _U8, ct.c_int, _D, _D, _I32]),
-    "orc_solve": (None, [_P, _P, ct.POINTER(Params), ct.c_int64, _D, _I64, ct.c_int, _D, _D, _I32]),
+    "orc_rank": (None, [_P, ct.c_int64, _I64, _D, _D, _D, _D, _U8, ct.c_double, ct.c_double, _D, ct.c_int,
+                        _D, _D, _I32]),
+    "orc_solve": (None, [_P, _P, ct.POINTER(Params), ct.c_int64, _D, _I64, _D, ct.c_int, _D, _D, _I32]),
 }
 
 
@@ -329,17 +331,24 @@ def topk_dup(rob: Robot, P: Params, m_off, score_M, theta_M) -> dict:
 
 
 def lm_iteration(rob: Robot, P: Params, targets, tgt, cand, k: int, theta) -> dict:
-    """One PJ-IK iteration per candidate, with its trace."""
+    """One PJ-IK iteration per candidate, with its trace: J, W, the clamped LM
+    step d_lm, the dogleg step d_dog, the single-coordinate joint sc_joint and
+    step sc_step (all three computed whether or not the LM step succeeds), the
+    branch taken (0 LM, 1 dogleg, 2 single coordinate, 3 perturbation), the
+    accepted line-search alpha and the smallest relative cost gap of the trials
+    evaluated (ls_margin)."""
     t, c = _idx(tgt, cand)
     C, n = len(t), rob.n
     tg = _f64(targets, (-1, 7))
     th = _f64(theta, (C, n))
     o = dict(theta=np.zeros((C, n)), J=np.zeros((C, 6, n)), W=np.zeros((C, 6)), d_lm=np.zeros((C, n)),
              branch=np.zeros(C, np.int32), alpha=np.zeros(C), ls_margin=np.zeros(C),
-             converged=np.zeros(C, np.uint8))
+             converged=np.zeros(C, np.uint8), d_dog=np.zeros((C, n)), sc_joint=np.zeros(C, np.int32),
+             sc_step=np.zeros(C))
     lib().orc_lm_iteration_batch(rob.ptr, ct.byref(P), _d(tg), C, _i32(t), _i32(c), int(k), _d(th),
                                  _d(o["theta"]), _d(o["J"]), _d(o["W"]), _d(o["d_lm"]), _i32(o["branch"]),
-                                 _d(o["alpha"]), _d(o["ls_margin"]), _u8(o["converged"]))
+                                 _d(o["alpha"]), _d(o["ls_margin"]), _u8(o["converged"]), _d(o["d_dog"]),
+                                 _i32(o["sc_joint"]), _d(o["sc_step"]))
     return o
 
 
@@ -359,6 +368,16 @@ def dogleg_step(Jw, b, R: float, gn_reg: float) -> np.ndarray:
     out = np.zeros(n)
     lib().orc_dogleg_step(n, _d(Jw), _d(_f64(b, (6,))), float(R), float(gn_reg), _d(out))
     return out
+
+
+def single_coord_step(Jw, b, R: float) -> tuple[int, np.ndarray]:
+    """Joint i* and step of Eq. single-coord, clamped to +-R."""
+    Jw = _f64(Jw)
+    n = Jw.shape[1]
+    out = np.zeros(n)
+    i = ct.c_int32()
+    lib().orc_single_coord_step(n, _d(Jw), _d(_f64(b, (6,))), float(R), ct.byref(i), _d(out))
+    return int(i.value), out
 
 
 def pjik(rob: Robot, P: Params, targets, tgt, cand, theta) -> dict:
@@ -382,24 +401,32 @@ def collide(rob: Robot, scene: Scene | None, theta) -> tuple[np.ndarray, np.ndar
     return hit.astype(bool), margin
 
 
-def rank(rob: Robot, b_off, theta_B, score, perr, oerr, hit, top_k: int) -> dict:
+def rank(rob: Robot, b_off, theta_B, score, perr, oerr, hit, top_k: int, eps_pos: float, eps_ori: float,
+         q_ref=None) -> dict:
+    """Final ranking of Alg. 2: per target the collision-free candidates, those
+    within (eps_pos, eps_ori) first, each group by score -- or, with q_ref
+    ([T][n]), the group within the tolerances by joint distance to q_ref[t]."""
     b_off = np.ascontiguousarray(b_off, np.int64)
     T = len(b_off) - 1
     n = rob.n
     th = _f64(theta_B, (-1, n))
     h = None if hit is None else np.ascontiguousarray(hit, np.uint8)
+    qr = None if q_ref is None else _f64(q_ref, (T, n))
     o = dict(q=np.zeros((T, top_k, n)), err=np.zeros((T, top_k, 2)), count=np.zeros(T, np.int32))
     lib().orc_rank(rob.ptr, T, _i64(b_off), _d(th), _d(_f64(score)), _d(_f64(perr)), _d(_f64(oerr)),
-                   _u8(h), int(top_k), _d(o["q"]), _d(o["err"]), _i32(o["count"]))
+                   _u8(h), float(eps_pos), float(eps_ori), _d(qr), int(top_k), _d(o["q"]), _d(o["err"]),
+                   _i32(o["count"]))
     return o
 
 
-def solve(rob: Robot, scene: Scene | None, P: Params, targets, samples, top_k: int) -> dict:
+def solve(rob: Robot, scene: Scene | None, P: Params, targets, samples, top_k: int, q_ref=None) -> dict:
+    """The whole method (Alg. 2); q_ref ([T][n]) ranks as the tracking loop does."""
     tg = _f64(targets, (-1, 7))
     T = tg.shape[0]
     s = np.ascontiguousarray(np.broadcast_to(np.asarray(samples, np.int64), (T,)), np.int64)
     n = rob.n
+    qr = None if q_ref is None else _f64(q_ref, (T, n))
     o = dict(q=np.zeros((T, top_k, n)), err=np.zeros((T, top_k, 2)), count=np.zeros(T, np.int32))
     lib().orc_solve(rob.ptr, scene.ptr if scene is not None else None, ct.byref(P), T, _d(tg), _i64(s),
-                    int(top_k), _d(o["q"]), _d(o["err"]), _i32(o["count"]))
+                    _d(qr), int(top_k), _d(o["q"]), _d(o["err"]), _i32(o["count"]))
     return o

@@ -898,6 +898,28 @@ void orc_dogleg_step(int n, const double* Jw, const double* b, double R, double 
     }
 }
 
+/* Eq. single-coord.  The paper moves the one joint with the largest gradient
+ * component; read here as i* = argmax_i |g_i| of g = (WJ)^T W r, the gradient
+ * of -1/2 |W r|^2 (ties to the lower joint), and on that joint the
+ * one-dimensional Gauss-Newton step g_i* / |(WJ)_{:,i*}|^2 -- the minimiser of
+ * the linearised cost 1/2 |W r - x (WJ)_{:,i*}|^2 -- clamped to the trust
+ * region.  step receives the n-vector (zero except at i*). */
+void orc_single_coord_step(int n, const double* Jw, const double* b, double R, int* i_star, double* step) {
+    double g[ORC_MAXN];
+    for (int i = 0; i < n; ++i) {
+        g[i] = 0.0;
+        for (int r = 0; r < 6; ++r) g[i] += Jw[r * n + i] * b[r];
+    }
+    int is = 0;
+    for (int i = 1; i < n; ++i)
+        if (fabs(g[i]) > fabs(g[is])) is = i;
+    double cn = 0.0;
+    for (int r = 0; r < 6; ++r) cn += Jw[r * n + is] * Jw[r * n + is];
+    for (int i = 0; i < n; ++i) step[i] = 0.0;
+    step[is] = (cn > 0.0) ? clampd(g[is] / cn, -R, R) : 0.0;
+    *i_star = is;
+}
+
 typedef struct {
     const orc_robot* R;
     const orc_params* P;
@@ -943,7 +965,8 @@ static double line_search(const lm_ctx* L, const double* th, const double* step,
  * tolerance of Alg. 4 holds after the update. */
 static int lm_iteration(const orc_robot* R, const orc_params* P, const double tgt[7], uint32_t t,
                         uint32_t c, int k, double* th, double* J_out, double* W_out, double* dlm_out,
-                        int32_t* branch_out, double* alpha_out, double* margin_out) {
+                        int32_t* branch_out, double* alpha_out, double* margin_out, double* ddog_out,
+                        int32_t* scj_out, double* scs_out) {
     const int n = R->n;
     lm_ctx L = {R, P, tgt, {0}};
     double e[6], J[6 * ORC_MAXN];
@@ -966,12 +989,15 @@ static int lm_iteration(const orc_robot* R, const orc_params* P, const double tg
     double cost0 = 0.5 * (b[0] * b[0] + b[1] * b[1] + b[2] * b[2] + b[3] * b[3] + b[4] * b[4] + b[5] * b[5]);
 
     /* Eq. normal-eqs (see orc_lm_step), then the trust region of Alg. 4 */
-    double g[ORC_MAXN], step[ORC_MAXN];
-    for (int i = 0; i < n; ++i) {
-        g[i] = 0.0;
-        for (int r = 0; r < 6; ++r) g[i] += Jw[r * n + i] * b[r];
-    }
+    double step[ORC_MAXN];
     orc_lm_step(n, Jw, b, P->lm_lambda, P->lm_trust_R, step);
+
+    /* the fallback steps of Alg. 4, taken below in its order when the LM step fails
+     * (computed here in any case so that a trace can show them) */
+    double dd[ORC_MAXN], sstep[ORC_MAXN];
+    int is = 0;
+    orc_dogleg_step(n, Jw, b, P->lm_trust_R, P->lm_gn_reg, dd);
+    orc_single_coord_step(n, Jw, b, P->lm_trust_R, &is, sstep);
 
     double margin = INFINITY, th_new[ORC_MAXN];
     int branch;
@@ -980,8 +1006,6 @@ static int lm_iteration(const orc_robot* R, const orc_params* P, const double tg
         memcpy(th, th_new, (size_t)n * sizeof(double));
         branch = BR_LM;
     } else {
-        double dd[ORC_MAXN];
-        orc_dogleg_step(n, Jw, b, P->lm_trust_R, P->lm_gn_reg, dd);
         double trial[ORC_MAXN];
         for (int i = 0; i < n; ++i) trial[i] = th[i] + dd[i];
         clamp_limits(R, trial);
@@ -992,17 +1016,7 @@ static int lm_iteration(const orc_robot* R, const orc_params* P, const double tg
             memcpy(th, trial, (size_t)n * sizeof(double));
             branch = BR_DOGLEG;
         } else {
-            /* Eq. single-coord: the joint with the largest gradient magnitude of
-             * 1/2 |W r|^2; a one-dimensional Gauss-Newton step on it (clamped to
-             * the trust region), then the same line search */
-            int is = 0;
-            for (int i = 1; i < n; ++i)
-                if (fabs(g[i]) > fabs(g[is])) is = i;
-            double cn = 0.0;
-            for (int r = 0; r < 6; ++r) cn += Jw[r * n + is] * Jw[r * n + is];
-            double sstep[ORC_MAXN];
-            for (int i = 0; i < n; ++i) sstep[i] = 0.0;
-            sstep[is] = (cn > 0.0) ? clampd(g[is] / cn, -P->lm_trust_R, P->lm_trust_R) : 0.0;
+            /* Eq. single-coord (step from orc_single_coord_step), then the same line search */
             double a2 = line_search(&L, th, sstep, cost0, th_new, &margin);
             if (a2 > 0.0) {
                 memcpy(th, th_new, (size_t)n * sizeof(double));
@@ -1023,6 +1037,9 @@ static int lm_iteration(const orc_robot* R, const orc_params* P, const double tg
     if (branch_out) *branch_out = branch;
     if (alpha_out) *alpha_out = alpha;
     if (margin_out) *margin_out = margin;
+    if (ddog_out) memcpy(ddog_out, dd, (size_t)n * sizeof(double));
+    if (scj_out) *scj_out = is;
+    if (scs_out) *scs_out = sstep[is];
 
     /* Alg. 4 break */
     double ep, eo;
@@ -1034,7 +1051,8 @@ void orc_lm_iteration_batch(const orc_robot* R, const orc_params* P, const doubl
                             int64_t C, const int32_t* tgt, const int32_t* cand, int k,
                             const double* th_in, double* th_out,
                             double* J, double* W, double* d_lm, int32_t* branch,
-                            double* alpha, double* ls_margin, uint8_t* converged) {
+                            double* alpha, double* ls_margin, uint8_t* converged,
+                            double* d_dog, int32_t* sc_joint, double* sc_step) {
     const int n = R->n;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t c = 0; c < C; ++c) {
@@ -1043,7 +1061,9 @@ void orc_lm_iteration_batch(const orc_robot* R, const orc_params* P, const doubl
         int conv = lm_iteration(R, P, targets + 7 * (int64_t)tgt[c], (uint32_t)tgt[c], (uint32_t)cand[c], k, th,
                                 J ? J + c * 6 * n : NULL, W ? W + c * 6 : NULL,
                                 d_lm ? d_lm + c * n : NULL, branch ? branch + c : NULL,
-                                alpha ? alpha + c : NULL, ls_margin ? ls_margin + c : NULL);
+                                alpha ? alpha + c : NULL, ls_margin ? ls_margin + c : NULL,
+                                d_dog ? d_dog + c * n : NULL, sc_joint ? sc_joint + c : NULL,
+                                sc_step ? sc_step + c : NULL);
         memcpy(th_out + c * n, th, (size_t)n * sizeof(double));
         if (converged) converged[c] = (uint8_t)conv;
     }
@@ -1061,7 +1081,7 @@ void orc_pjik_batch(const orc_robot* R, const orc_params* P, const double* targe
         int it = P->lm_max_iters;
         for (int k = 0; k < P->lm_max_iters; ++k) {
             if (lm_iteration(R, P, T, (uint32_t)tgt[c], (uint32_t)cand[c], k, th, NULL, NULL, NULL, NULL,
-                             NULL, NULL)) {
+                             NULL, NULL, NULL, NULL, NULL)) {
                 it = k + 1;
                 break;
             }
@@ -1144,23 +1164,52 @@ void orc_collide_batch(const orc_robot* R, const orc_scene* S, int64_t C, const 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Alg. 2, final step: collision-free candidates ranked by score           */
+/* Alg. 2, final step: collision-free candidates ranked                      */
+
+/* Alg. 2 returns the best collision-free candidates of each target.  Reading
+ * (c20): the candidates inside the request's tolerances (|e_p| <= eps_pos and
+ * |omega| <= eps_ori) come before the others, each group by the score of
+ * reading c4, ties to the lower candidate index.  Reading (c24, the tracking
+ * use of Sec. VI-D): with q_ref ([T][n]) the group inside the tolerances is
+ * ordered by squared joint-space distance to q_ref[t] instead of the score.
+ * Selection by repeated minimum over the untaken candidates. */
+static int rank_before(int conv_a, double key_a, int64_t ia, int conv_b, double key_b, int64_t ib) {
+    if (conv_a != conv_b) return conv_a > conv_b;
+    if (key_a != key_b) return key_a < key_b;
+    return ia < ib;
+}
 
 void orc_rank(const orc_robot* R, int64_t T, const int64_t* b_off, const double* th_B,
               const double* score, const double* perr, const double* oerr, const uint8_t* hit,
+              double eps_pos, double eps_ori, const double* q_ref,
               int top_k, double* out_q, double* out_err, int32_t* out_count) {
     const int n = R->n;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t t = 0; t < T; ++t) {
         int64_t B = b_off[t + 1] - b_off[t];
         uint8_t* taken = (uint8_t*)calloc((size_t)(B > 0 ? B : 1), 1);
+        int* conv = (int*)malloc((size_t)(B > 0 ? B : 1) * sizeof(int));
+        double* key = (double*)malloc((size_t)(B > 0 ? B : 1) * sizeof(double));
+        for (int64_t b = 0; b < B; ++b) {
+            int64_t g = b_off[t] + b;
+            conv[b] = perr[g] <= eps_pos && oerr[g] <= eps_ori;
+            key[b] = score[g];
+            if (q_ref && conv[b]) {
+                double d2 = 0.0;
+                for (int j = 0; j < n; ++j) {
+                    double dj = th_B[g * n + j] - q_ref[t * n + j];
+                    d2 += dj * dj;
+                }
+                key[b] = d2;
+            }
+        }
         int cnt = 0;
         for (int r = 0; r < top_k; ++r) {
             int64_t best = -1;
             for (int64_t b = 0; b < B; ++b) {
                 int64_t g = b_off[t] + b;
                 if (taken[b] || (hit && hit[g])) continue;
-                if (best < 0 || score[g] < score[b_off[t] + best]) best = b;
+                if (best < 0 || rank_before(conv[b], key[b], b, conv[best], key[best], best)) best = b;
             }
             if (best < 0) break;
             taken[best] = 1;
@@ -1172,6 +1221,8 @@ void orc_rank(const orc_robot* R, int64_t T, const int64_t* b_off, const double*
         }
         out_count[t] = cnt;
         free(taken);
+        free(conv);
+        free(key);
     }
 }
 
@@ -1179,7 +1230,7 @@ void orc_rank(const orc_robot* R, int64_t T, const int64_t* b_off, const double*
 /* Alg. 2: the whole method                                                 */
 
 void orc_solve(const orc_robot* R, const orc_scene* S, const orc_params* P, int64_t T,
-               const double* targets, const int64_t* samples, int top_k,
+               const double* targets, const int64_t* samples, const double* q_ref, int top_k,
                double* out_q, double* out_err, int32_t* out_count) {
     const int n = R->n;
     int64_t* m_off = (int64_t*)malloc((size_t)(T + 1) * sizeof(int64_t));
@@ -1214,7 +1265,8 @@ void orc_solve(const orc_robot* R, const orc_scene* S, const orc_params* P, int6
         }
     orc_pjik_batch(R, P, targets, CB, tg, cd, thB, sB, pB, oB, NULL);         /* PJ-IK */
     if (R->n_sph > 0) orc_collide_batch(R, S, CB, thB, hB, NULL);              /* collision filter */
-    orc_rank(R, T, b_off, thB, sB, pB, oB, hB, top_k, out_q, out_err, out_count); /* ranking */
+    orc_rank(R, T, b_off, thB, sB, pB, oB, hB, P->eps_pos, P->eps_ori, q_ref, top_k, out_q, out_err,
+             out_count);                                                          /* ranking */
 
     free(m_off);
     free(b_off);

@@ -95,9 +95,11 @@ void orc_lm_iteration_batch(const orc_robot* R, const orc_params* P, const doubl
                             int64_t C, const int32_t* tgt, const int32_t* cand, int k,
                             const double* th_in, double* th_out,
                             double* J, double* W, double* d_lm, int32_t* branch,
-                            double* alpha, double* ls_margin, uint8_t* converged);
+                            double* alpha, double* ls_margin, uint8_t* converged,
+                            double* d_dog, int32_t* sc_joint, double* sc_step);
 void orc_lm_step(int n, const double* Jw, const double* b, double lambda, double R, double* step);
 void orc_dogleg_step(int n, const double* Jw, const double* b, double R, double gn_reg, double* step);
+void orc_single_coord_step(int n, const double* Jw, const double* b, double R, int* i_star, double* step);
 void orc_pjik_batch(const orc_robot* R, const orc_params* P, const double* targets,
                     int64_t C, const int32_t* tgt, const int32_t* cand, double* theta,
                     double* score, double* perr, double* oerr, int32_t* iters);
@@ -105,12 +107,13 @@ void orc_collide_batch(const orc_robot* R, const orc_scene* S, int64_t C, const 
                        uint8_t* hit, double* min_abs_margin);
 void orc_rank(const orc_robot* R, int64_t T, const int64_t* b_off, const double* th_B,
               const double* score, const double* perr, const double* oerr, const uint8_t* hit,
+              double eps_pos, double eps_ori, const double* q_ref /* [T][n] or NULL */,
               int top_k, double* out_q, double* out_err, int32_t* out_count);
 
 /* Whole method (Alg. 2) for T targets; samples[t] = M = B seeds of target t. */
 void orc_solve(const orc_robot* R, const orc_scene* S, const orc_params* P, int64_t T,
-               const double* targets, const int64_t* samples, int top_k,
-               double* out_q, double* out_err, int32_t* out_count);
+               const double* targets, const int64_t* samples, const double* q_ref /* [T][n] or NULL */,
+               int top_k, double* out_q, double* out_err, int32_t* out_count);
 
 #ifdef __cplusplus
 }

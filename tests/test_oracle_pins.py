@@ -496,6 +496,145 @@ def test_lm_iteration_weights_step_and_line_search(panda):
     assert np.mean(tr["branch"] == 0) > 0.5
 
 
+def test_single_coordinate_step_is_the_1d_gauss_newton_minimiser():
+    """Eq. single-coord (reading c16): the joint whose cost derivative at 0 is
+    steepest -- measured by central differences of 1/2 |b - x (WJ)_j|^2, not
+    from the gradient formula -- and on it the minimiser of that 1-D cost,
+    found by a dense scan, clamped to the trust region."""
+    rng = np.random.default_rng(21)
+    for n in (3, 7, 12, 24):
+        for trial in range(4):
+            Jw = rng.normal(size=(6, n))
+            b = rng.normal(size=6)
+            q = lambda j, x: 0.5 * np.sum((b[:, None] - np.outer(Jw[:, j], np.atleast_1d(x))) ** 2, axis=0)
+            h = 1e-6
+            slope = np.array([abs(q(j, h)[0] - q(j, -h)[0]) / (2 * h) for j in range(n)])
+            i, st = orc.single_coord_step(Jw, b, 1e9)
+            assert slope[i] >= slope.max() * (1 - 1e-6)
+            xs = np.linspace(-10, 10, 2_000_001)
+            x_best = xs[np.argmin(q(i, xs))]
+            assert st[i] == pytest.approx(x_best, abs=2e-5)
+            assert np.count_nonzero(st) <= 1
+            # clamped: the scan restricted to [-R, R]
+            R = 0.25 * abs(x_best)
+            _, st_r = orc.single_coord_step(Jw, b, R)
+            xr = np.linspace(-R, R, 200_001)
+            assert st_r[i] == pytest.approx(xr[np.argmin(q(i, xr))], abs=1e-9)
+    # ties between equally steep joints go to the lower one
+    Jw = 0.1 * rng.normal(size=(6, 7))
+    Jw[:, 2] = Jw[:, 5] = 2.0 * np.array([1.0, -0.5, 0.25, 0.0, 0.3, -0.2])
+    b = np.array([1.0, -0.5, 0.25, 0.0, 0.3, -0.2])
+    assert orc.single_coord_step(Jw, b, 1e9)[0] == 2
+    Jw[:, 5] *= -1  # same magnitude, opposite sign: still a tie on |g|
+    assert orc.single_coord_step(Jw, b, 1e9)[0] == 2
+
+
+def test_single_coordinate_step_recovers_a_small_joint_motion():
+    """A one-joint arm whose target is its own pose after turning the joint by
+    delta: the residual is then zero at the answer, so the Gauss-Newton step of
+    Eq. single-coord equals delta up to O(delta^2) (a dropped term or a wrong
+    sign leaves an O(delta) error)."""
+    rob = orc.Robot(inputs.planar([0.7]))
+    P = orc.make_params(seed=1)
+    errs = []
+    for delta in (1e-1, 1e-2, 1e-3):
+        th0 = np.array([0.3])
+        tgt = orc.pose(rob, th0 + delta)
+        tr = orc.lm_iteration(rob, P, tgt, [0], [0], 0, th0)
+        assert tr["sc_joint"][0] == 0
+        errs.append(abs(tr["sc_step"][0] - delta) / delta ** 2)
+    assert max(errs) < 1.0
+
+
+def _lm_cost(rob, th, tgt, W):
+    e = orc.residual(rob, th, tgt)
+    return 0.5 * np.sum((W * e) ** 2)
+
+
+def _lm_expected(rob, P, tgt, th, tr, c):
+    """The outcome Alg. 4 prescribes for candidate c, recomputed from pinned
+    parts (the residual, the LM step checked against LAPACK, the dogleg step
+    checked against pinv, the single-coordinate step checked by a scan): the
+    first of LM line search, dogleg, single-coordinate line search that strictly
+    lowers the weighted cost; else the perturbation.  Returns (branch, alpha, theta)."""
+    W = tr["W"][c]
+    clip = lambda x: np.clip(x, rob.lo, rob.hi)
+    c0 = _lm_cost(rob, th, tgt, W)
+    alphas = [1.0 / P.lm_beta ** i for i in range(P.lm_A + 1)]
+    for a in alphas:
+        if _lm_cost(rob, clip(th + a * tr["d_lm"][c]), tgt, W) < c0:
+            return 0, a, clip(th + a * tr["d_lm"][c])
+    if _lm_cost(rob, clip(th + tr["d_dog"][c]), tgt, W) < c0:
+        return 1, 0.0, clip(th + tr["d_dog"][c])
+    sc = np.zeros(rob.n)
+    sc[tr["sc_joint"][c]] = tr["sc_step"][c]
+    for a in alphas:
+        if _lm_cost(rob, clip(th + a * sc), tgt, W) < c0:
+            return 2, a, clip(th + a * sc)
+    return 3, 0.0, None
+
+
+def test_lm_iteration_follows_the_branch_order_of_alg4(panda):
+    """Alg. 4's fallback chain on candidates part-way through PJ-IK from
+    uniform seeds (where a third or more of the iterations fail the full step):
+    each candidate's dogleg and single-coordinate steps equal the pinned step
+    functions on its weighted Jacobian, and the branch, alpha and new theta are
+    the first successful step in the order LM, dogleg, single coordinate, else
+    the perturbation drawn from the PJ-IK normal stream."""
+    rng = np.random.default_rng(22)
+    T, C, k = 6, 400, 10
+    tth = rng.uniform(panda.lo, panda.hi, (T, 7))
+    tg = _poses(panda, tth)
+    tgt = rng.integers(0, T, C)
+    cand = np.arange(C)
+    seen = set()
+    for A in (4, 0):
+        P = orc.make_params(seed=9, lm_A=A, lm_max_iters=k)
+        th = orc.pjik(panda, P, tg, tgt, cand, rng.uniform(panda.lo, panda.hi, (C, 7)))["theta"]
+        tr = orc.lm_iteration(panda, P, tg, tgt, cand, k, th)
+        for c in range(C):
+            J = orc.jacobian(panda, th[c])
+            assert np.array_equal(tr["J"][c], J)
+            Jw = tr["W"][c][:, None] * J
+            bw = tr["W"][c] * orc.residual(panda, th[c], tg[tgt[c]])
+            assert np.array_equal(tr["d_dog"][c], orc.dogleg_step(Jw, bw, P.lm_trust_R, P.lm_gn_reg))
+            i, st = orc.single_coord_step(Jw, bw, P.lm_trust_R)
+            assert tr["sc_joint"][c] == i and tr["sc_step"][c] == st[i]
+            br, al, th_new = _lm_expected(panda, P, tg[tgt[c]], th[c], tr, c)
+            assert tr["branch"][c] == br, c
+            assert tr["alpha"][c] == al
+            if br < 3:
+                assert np.array_equal(tr["theta"][c], th_new)
+            else:
+                z = _normal_stream(P, c, tgt[c], inputs.PHASE_LM, k, 7)
+                assert np.allclose(tr["theta"][c], np.clip(th[c] + P.lm_sigma * z, panda.lo, panda.hi), atol=1e-15)
+            seen.add(br)
+    assert seen >= {0, 1, 2}
+
+
+def test_lm_perturbation_when_no_step_lowers_the_cost():
+    """A stretched planar arm with its target straight ahead beyond reach and
+    the same orientation: the gradient (WJ)^T W r is exactly zero (the
+    position Jacobian is orthogonal to the error), so the LM, dogleg and
+    single-coordinate steps are zero and none lowers the cost; Alg. 4 then
+    perturbs with N(0, sigma^2 I) from the PJ-IK stream (phase 4) of the
+    candidate's counter, and iteration k keys the draw."""
+    rob = orc.Robot(inputs.planar([0.5, 0.4, 0.3]))
+    th = np.zeros((2, 3))
+    tgt = orc.pose(rob, th[:1]).copy()
+    assert np.allclose(tgt[0, 3:], [1, 0, 0, 0])
+    tgt[0, 0] += 0.6
+    for k in (0, 7):
+        P = orc.make_params(seed=3)
+        tr = orc.lm_iteration(rob, P, tgt, [0, 0], [0, 5], k, th)
+        assert np.all(tr["branch"] == 3)
+        assert np.all(tr["d_lm"] == 0) and np.all(tr["d_dog"] == 0) and np.all(tr["sc_step"] == 0)
+        for c, cand in enumerate((0, 5)):
+            z = _normal_stream(P, cand, 0, inputs.PHASE_LM, k, 3)
+            assert np.allclose(tr["theta"][c], np.clip(P.lm_sigma * z, rob.lo, rob.hi), atol=1e-15)
+        assert not np.allclose(tr["theta"][0], tr["theta"][1])
+
+
 def test_pjik_converges_from_nearby_seeds(panda):
     rng = np.random.default_rng(17)
     C = 32
@@ -586,22 +725,82 @@ def test_collision_matches_pairwise_distances():
 # ----------------------------------------------------------------------------
 # ranking (Alg. 2) and the whole method
 
+def _rank_reference(th, score, perr, oerr, hit, b_off, k, eps_pos, eps_ori, q_ref=None):
+    """Alg. 2's final ranking by a stable library sort: per target the
+    collision-free candidates, those within the tolerances first (reading c20),
+    each group by score -- or by joint distance to q_ref[t] (reading c24)."""
+    out = []
+    for t in range(len(b_off) - 1):
+        g = np.arange(b_off[t], b_off[t + 1])
+        g = g[~hit[g]]
+        conv = (perr[g] <= eps_pos) & (oerr[g] <= eps_ori)
+        key = score[g].copy()
+        if q_ref is not None:
+            key = np.where(conv, np.sum((th[g] - q_ref[t]) ** 2, axis=1), key)
+        order = np.lexsort((g, key, ~conv))
+        out.append(g[order][:k])
+    return out
+
+
 def test_rank_matches_sorted_collision_free(panda):
     rng = np.random.default_rng(18)
     T, B, k = 4, 50, 5
     b_off = np.arange(T + 1) * B
     th = rng.uniform(panda.lo, panda.hi, (T * B, 7))
     score = np.round(rng.uniform(0, 3, T * B), 1)
-    perr, oerr = rng.uniform(0, 1, T * B), rng.uniform(0, 1, T * B)
+    perr, oerr = rng.uniform(0, 2e-3, T * B), rng.uniform(0, 2e-2, T * B)
     hit = rng.uniform(size=T * B) < 0.7
     hit[B:2 * B] = True       # a target with no collision-free candidate
-    o = orc.rank(panda, b_off, th, score, perr, oerr, hit, k)
+    o = orc.rank(panda, b_off, th, score, perr, oerr, hit, k, 1e-3, 1e-2)
+    ref = _rank_reference(th, score, perr, oerr, hit, b_off, k, 1e-3, 1e-2)
     for t in range(T):
-        idx = [t * B + i for i in np.argsort(score[t * B:(t + 1) * B], kind="stable") if not hit[t * B + i]][:k]
-        assert o["count"][t] == len(idx)
-        for r, g in enumerate(idx):
+        assert o["count"][t] == len(ref[t])
+        for r, g in enumerate(ref[t]):
             assert np.array_equal(o["q"][t, r], th[g])
             assert np.array_equal(o["err"][t, r], [perr[g], oerr[g]])
+
+
+def test_rank_puts_converged_candidates_first(panda):
+    """Reading c20: a candidate just outside the position tolerance can have a
+    lower score than one inside both tolerances (|e_p| = 1.05 eps_pos, omega = 0
+    gives s = 1.1025; 0.9 eps_pos and 0.9 eps_ori give s = 1.62); the converged
+    one is returned first, so the target counts as solved."""
+    th = np.array([[0.1] * 7, [0.2] * 7, [0.3] * 7])
+    perr = np.array([1.05e-3, 0.9e-3, 3e-3])
+    oerr = np.array([0.0, 0.9e-2, 0.0])
+    score = (perr / 1e-3) ** 2 + (oerr / 1e-2) ** 2
+    assert score[0] < score[1] < score[2]
+    o = orc.rank(panda, [0, 3], th, score, perr, oerr, None, 3, 1e-3, 1e-2)
+    assert o["count"][0] == 3
+    assert np.array_equal(o["q"][0, :, 0], [0.2, 0.1, 0.3])
+    # exactly on the tolerance counts as inside it (the success test is <=)
+    o = orc.rank(panda, [0, 2], th[:2], score[:2], np.array([1.05e-3, 1e-3]), np.array([0.0, 1e-2]), None, 1,
+                 1e-3, 1e-2)
+    assert o["q"][0, 0, 0] == 0.2
+
+
+def test_rank_nearest_orders_converged_by_joint_distance(panda):
+    """Reading c24 (tracking): inside the tolerances by squared joint distance
+    to the reference configuration, then the rest by score; collisions never."""
+    rng = np.random.default_rng(19)
+    T, B, k = 3, 40, 12
+    b_off = np.arange(T + 1) * B
+    th = rng.uniform(panda.lo, panda.hi, (T * B, 7))
+    q_ref = rng.uniform(panda.lo, panda.hi, (T, 7))
+    score = rng.uniform(0, 3, T * B)
+    perr, oerr = rng.uniform(0, 2e-3, T * B), rng.uniform(0, 2e-2, T * B)
+    hit = rng.uniform(size=T * B) < 0.3
+    o = orc.rank(panda, b_off, th, score, perr, oerr, hit, k, 1e-3, 1e-2, q_ref=q_ref)
+    ref = _rank_reference(th, score, perr, oerr, hit, b_off, k, 1e-3, 1e-2, q_ref=q_ref)
+    for t in range(T):
+        assert o["count"][t] == len(ref[t])
+        assert np.array_equal(o["q"][t, :len(ref[t])], th[ref[t]])
+        # the converged prefix is nearest-first, measured independently of the oracle
+        conv = (o["err"][t, :o["count"][t], 0] <= 1e-3) & (o["err"][t, :o["count"][t], 1] <= 1e-2)
+        nconv = int(conv.sum())
+        assert np.all(conv[:nconv]) and not np.any(conv[nconv:])
+        d = np.linalg.norm(o["q"][t, :nconv] - q_ref[t], axis=1)
+        assert np.all(np.diff(d) >= 0)
 
 
 def test_solve_round_trip_open_world(panda):
@@ -618,7 +817,12 @@ def test_solve_round_trip_open_world(panda):
             assert np.all(q >= panda.lo) and np.all(q <= panda.hi)
             e = orc.residual(panda, q, tg[t])
             assert np.allclose([np.linalg.norm(e[:3]), np.linalg.norm(e[3:])], o["err"][t, r], atol=1e-15)
-        assert np.all(np.diff(o["err"][t, :, 0] ** 2 / 1e-6 + o["err"][t, :, 1] ** 2 / 1e-4) >= -1e-12)
+        # converged rows first (reading c20), each group by score
+        conv = (o["err"][t, :, 0] <= wl.eps_pos) & (o["err"][t, :, 1] <= wl.eps_ori)
+        assert np.all(np.diff(conv.astype(int)) <= 0)
+        s_ = o["err"][t, :, 0] ** 2 / wl.eps_pos ** 2 + o["err"][t, :, 1] ** 2 / wl.eps_ori ** 2
+        for grp in (conv, ~conv):
+            assert np.all(np.diff(s_[grp]) >= -1e-12)
         succ += (o["err"][t, 0, 0] <= wl.eps_pos) and (o["err"][t, 0, 1] <= wl.eps_ori)
     assert succ >= 3
 
