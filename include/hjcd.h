@@ -142,7 +142,8 @@ hjcd_status hjcd_set_scene(hjcd_ctx* ctx, int32_t scene_id_or_new, int n_sph, co
 /* Solve n_targets poses (targets_pq, 7 floats each).  Per target: M seeds
  * through PO-CCD, top-K + perturbed duplication to B, PJ-IK, the collision
  * filter (self-collision when the robot has spheres, plus the scene when
- * scene_id >= 0) and the ranking of the collision-free candidates by the score
+ * scene_id >= 0) and the ranking of the collision-free candidates: those within the
+ * tolerances first, each group by the score
  * (|e_p|/eps_pos)^2 + (|omega|/eps_ori)^2.
  * Outputs: out_q [n_targets][top_k][n] joint vectors, out_err
  * [n_targets][top_k][2] (|e_p| m, |omega| rad), out_count [n_targets] the
@@ -356,10 +357,15 @@ hjcd_status hjcd_solve_nearest(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id
  *     overlap on the GPU -- on different streams, or from several contexts --
  *     race and corrupt each other's results;
  *   - the first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture begins;
+ *     (cudaGetSymbolAddress) with that device current and keeps it for the
+ *     life of the process; make that first call before any stream capture
+ *     begins, and make no call on a device after cudaDeviceReset there (the
+ *     kept address then refers to a module that is gone);
+ *   - rows past out_count are NaN, as hjcd_solve leaves them;
  *   - work counters are not updated, and a staging wait of the collision
- *     kernel that runs out is not reported (the call does not synchronise). */
+ *     kernel that runs out is not reported (the call does not synchronise):
+ *     the candidates of a collision CTA that gave up count as colliding, so
+ *     such a call returns fewer solutions, never a colliding one. */
 hjcd_status hjcd_solve_noalloc(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_targets,
                                const float* targets_pq, const hjcd_solve_opts* opts,
                                float* out_q, float* out_err, int32_t* out_count, void* stream);
@@ -421,13 +427,21 @@ hjcd_status hjcd_topk_dup(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const 
 /* Alg. 4: PJ-IK, iterations k0 .. k0+n_iters-1, theta updated in place.
  * Trace (one iteration): J [6n][ld] (row r, joint i at (r*n+i)*ld + c),
  * W [6][ld], d_lm [n][ld] the clamped LM step, branch (0 LM, 1 dogleg,
- * 2 single-coordinate, 3 perturbation), alpha the accepted line-search step. */
+ * 2 single-coordinate, 3 perturbation), alpha the accepted line-search step
+ * (0 for the dogleg and the perturbation).  For the candidates whose full LM
+ * step failed (left untouched for the others): d_dog [n][ld] the dogleg step
+ * of Eq. dogleg, sc_joint the joint i* of Eq. single-coord (largest |g_i| of
+ * g = (WJ)^T W r, ties to the lower joint) and sc_step its clamped 1-D
+ * Gauss-Newton step g_i* / |(WJ)_i*|^2. */
 typedef struct hjcd_lm_trace {
     float* J;
     float* W;
     float* d_lm;
     int32_t* branch;
     float* alpha;
+    float* d_dog;
+    int32_t* sc_joint;
+    float* sc_step;
 } hjcd_lm_trace;
 hjcd_status hjcd_pjik(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const float* targets_pq,
                       float eps_pos, float eps_ori, uint64_t seed, const hjcd_params* params,
@@ -452,14 +466,37 @@ hjcd_status hjcd_scene_contacts(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_i
                                 const float* theta, int64_t ld, uint8_t* touched, void* stream);
 
 /* Alg. 2, final ranking: per target, the collision-free candidates (hit may be
- * NULL) of b_off[t] .. b_off[t+1]-1 sorted by score (ties to the lower
- * index), first top_k written as in hjcd_solve. */
+ * NULL) of b_off[t] .. b_off[t+1]-1, those within the tolerances
+ * (perr <= eps_pos and oerr <= eps_ori) first, each group by score (ties to
+ * the lower index); the first top_k written as in hjcd_solve (rows past
+ * out_count NaN).  With q_ref ([n_targets][n] device, or NULL) the group within
+ * the tolerances is ordered by squared joint distance to q_ref[t] instead, as
+ * hjcd_solve_nearest ranks. */
 hjcd_status hjcd_rank(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const int64_t* b_off,
                       const float* theta_B, int64_t ld, const float* score, const float* perr,
-                      const float* oerr, const uint8_t* hit, int top_k,
+                      const float* oerr, const uint8_t* hit, float eps_pos, float eps_ori,
+                      const float* q_ref, int top_k,
                       float* out_q, float* out_err, int32_t* out_count, void* stream);
 
+/* Philox4x32-10 (Salmon et al., SC'11), the generator of every random draw
+ * of the method (seeds of Alg. 3, perturbations of Alg. 2-4): out[i] = the
+ * four 32-bit words of the block at counter ctr[i] (four words) under the key
+ * (key & 0xffffffff, key >> 32), computed by the kernels' own generator.
+ * ctr and out: DEVICE arrays of n_blocks x 4 uint32. */
+hjcd_status hjcd_philox(hjcd_ctx* ctx, int64_t n_blocks, const uint32_t* ctr, uint64_t key, uint32_t* out,
+                        void* stream);
+
 /* ---- instrumentation ------------------------------------------------------ */
+
+/* Polls of the collision kernels' first wait for their bulk-copied obstacle
+ * tables, for later launches of the context's hjcd_collide, hjcd_solve,
+ * hjcd_solve_batch, graph and serving calls (polls < 0: the default 2^22,
+ * far longer than any copy takes).  0 makes that wait run out at once, which
+ * exercises the timeout path (Sec. V-C has none; a bounded wait is this
+ * library's): the kernel sets its error flag, waits for its copy to land with
+ * the full limit, returns without verdicts, and the call reports
+ * HJCD_ETIMEOUT (hjcd_collide through hjcd_counters).  For tests only. */
+hjcd_status hjcd_set_wait_limit(hjcd_ctx* ctx, int64_t polls);
 
 /* Record CUDA events around each phase of hjcd_solve (0 = off). */
 hjcd_status hjcd_set_profiling(hjcd_ctx* ctx, int on);

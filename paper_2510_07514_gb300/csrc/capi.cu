@@ -893,6 +893,7 @@ hjcd_status hjcd_collide(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int6
     a.hit = hit;
     a.cnt = ctx->cnt;
     a.err_flag = ctx->err_flag;
+    a.first_wait_polls = ctx->first_wait_polls.load();
     launch_collide(a, s);
     return after_launch(ctx, 1);
 }
@@ -919,15 +920,18 @@ hjcd_status hjcd_scene_contacts(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_i
 
 hjcd_status hjcd_rank(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const int64_t* b_off, const float* theta_B,
                       int64_t ld, const float* score, const float* perr, const float* oerr, const uint8_t* hit,
-                      int top_k, float* out_q, float* out_err, int32_t* out_count, void* stream) {
+                      float eps_pos, float eps_ori, const float* q_ref, int top_k, float* out_q, float* out_err,
+                      int32_t* out_count, void* stream) {
     if (!ctx) return HJCD_EINVAL;
     RobotRec* rob;
     hjcd_status st;
     if ((st = check_robot(ctx, robot_id, &rob))) return st;
     if (n_targets < 1 || top_k < 1 || top_k > HJCD_MAX_TOPK) return fail(ctx, HJCD_EINVAL, "bad n_targets or top_k");
+    if (!(eps_pos > 0.0f) || !(eps_ori > 0.0f)) return fail(ctx, HJCD_EINVAL, "tolerances must be > 0");
     if (pointer_kind(b_off) != 1 || pointer_kind(theta_B) != 1 || pointer_kind(score) != 1 ||
         pointer_kind(perr) != 1 || pointer_kind(oerr) != 1 || (hit && pointer_kind(hit) != 1) ||
-        pointer_kind(out_q) != 1 || pointer_kind(out_err) != 1 || pointer_kind(out_count) != 1)
+        (q_ref && pointer_kind(q_ref) != 1) || pointer_kind(out_q) != 1 || pointer_kind(out_err) != 1 ||
+        pointer_kind(out_count) != 1)
         return fail(ctx, HJCD_EINVAL, "rank buffers must be device arrays");
     if ((st = make_current(ctx))) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -942,9 +946,28 @@ hjcd_status hjcd_rank(hjcd_ctx* ctx, int32_t robot_id, int n_targets, const int6
     }
     if (bo[n_targets] > ld) return fail(ctx, HJCD_EINVAL, "ld smaller than the candidate count");
     RankArgs a{single_robot_set(*rob), nullptr, n_targets, b_off, theta_B, ld, score, perr, oerr, hit, top_k,
-               nullptr, out_q, out_err, out_count};
+               nullptr, out_q, out_err, out_count, q_ref, rob->P.n};
+    a.eps_pos = eps_pos;
+    a.eps_ori = eps_ori;
+    // rows past a target's count read NaN, as hjcd_solve leaves them
+    HJCD_CUDA(ctx, cudaMemsetAsync(out_q, 0xff, sizeof(float) * (size_t)n_targets * top_k * rob->P.n, s));
+    HJCD_CUDA(ctx, cudaMemsetAsync(out_err, 0xff, sizeof(float) * (size_t)n_targets * top_k * 2, s));
     launch_rank(a, max_b, s);
     return after_launch(ctx, 1);
+}
+
+hjcd_status hjcd_philox(hjcd_ctx* ctx, int64_t n_blocks, const uint32_t* ctr, uint64_t key, uint32_t* out,
+                        void* stream) {
+    if (!ctx) return HJCD_EINVAL;
+    if (n_blocks < 0) return fail(ctx, HJCD_EINVAL, "n_blocks < 0");
+    if (n_blocks == 0) return HJCD_OK;
+    if (pointer_kind(ctr) != 1 || pointer_kind(out) != 1) return fail(ctx, HJCD_EINVAL, "ctr and out must be device arrays");
+    if ((reinterpret_cast<uintptr_t>(ctr) | reinterpret_cast<uintptr_t>(out)) & 15u)
+        return fail(ctx, HJCD_EINVAL, "ctr and out must be 16-byte aligned");
+    hjcd_status st;
+    if ((st = make_current(ctx))) return st;
+    launch_philox(n_blocks, ctr, key, out, (cudaStream_t)stream);
+    return after_launch(ctx, 1, "k_philox");
 }
 
 // ---- instrumentation -----------------------------------------------------
@@ -953,6 +976,12 @@ hjcd_status hjcd_set_collision_mode(hjcd_ctx* ctx, int32_t mode) {
     if (!ctx) return HJCD_EINVAL;
     if (mode != 0 && mode != 1) return fail(ctx, HJCD_EINVAL, "collision mode must be 0 (all candidates) or 1 (ranked)");
     ctx->collide_lazy = mode == 1;
+    return HJCD_OK;
+}
+
+hjcd_status hjcd_set_wait_limit(hjcd_ctx* ctx, int64_t polls) {
+    if (!ctx) return HJCD_EINVAL;
+    ctx->first_wait_polls = polls < 0 ? -1 : polls;
     return HJCD_OK;
 }
 
@@ -1140,20 +1169,21 @@ extern "C" hjcd_status hjcd_solve_noalloc(hjcd_ctx* ctx, int32_t robot_id, int32
     CcdArgs ca{};
     ca.rs = rs;
     ca.tg = d_tg;
-    ca.map = CandMap{nullptr, nullptr, d_moff, T};
+    ca.map = CandMap{nullptr, nullptr, d_moff, T, M};  // every target has M seeds: no search
     ca.C = CM;
     ca.ld = CM;
     ca.th_out = thM;
     ca.score = sM;
     ca.n_iters = P.cd_max_iters;
     ca.P = P;
+    ca.block = ctx->ccd_block;
     launch_ccd(ca, false, s);
     DupArgs da{rs, d_tg, T, d_moff, sM, thM, CM, d_boff, thB, CB, nullptr, P.dup_ratio, P.dup_sigma};
     launch_topk_dup(da, M, s);
     LmArgs la{};
     la.rs = rs;
     la.tg = d_tg;
-    la.map = CandMap{nullptr, nullptr, d_boff, T};
+    la.map = CandMap{nullptr, nullptr, d_boff, T, (int32_t)B};
     la.C = CB;
     la.ld = CB;
     la.th = thB;
@@ -1163,13 +1193,17 @@ extern "C" hjcd_status hjcd_solve_noalloc(hjcd_ctx* ctx, int32_t robot_id, int32
     la.n_iters = P.lm_max_iters;
     la.P = P;
     la.queue = queue;
+    la.warps = ctx->lm_warps;
     launch_lm(la, false, s);
     const bool collide = R.n_sph > 0;
     if (collide) {
+        // a collision CTA whose staging wait runs out returns without verdicts: its candidates
+        // must then count as colliding, not keep the previous call's verdicts
+        HJCD_CUDA(ctx, cudaMemsetAsync(hB, 1, (size_t)CB, s));
         CollideArgs cl{};
         collide_uniform(cl, *rob, sc);
         cl.tg = d_tg;
-        cl.map = CandMap{nullptr, nullptr, d_boff, T};
+        cl.map = CandMap{nullptr, nullptr, d_boff, T, (int32_t)B};
         cl.C = CB;
         cl.ld = CB;
         cl.th = thB;
@@ -1179,6 +1213,9 @@ extern "C" hjcd_status hjcd_solve_noalloc(hjcd_ctx* ctx, int32_t robot_id, int32
     }
     RankArgs ra{rs, d_tg, T, d_boff, thB, CB, sB, pB, oB, collide ? hB : nullptr, top_k, nullptr,
                 out_q, out_err, out_count};
+    // rows past a target's count are NaN, as hjcd_solve leaves them (stream-ordered, no allocation)
+    HJCD_CUDA(ctx, cudaMemsetAsync(out_q, 0xff, sizeof(float) * (size_t)T * top_k * n, s));
+    HJCD_CUDA(ctx, cudaMemsetAsync(out_err, 0xff, sizeof(float) * (size_t)T * top_k * 2, s));
     launch_rank(ra, (int)B, s);
     return after_launch(ctx, collide ? 5 : 4);
 }
@@ -1346,6 +1383,7 @@ hjcd_status hjcd_solve_from_topk(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_
         cl.hit = hB;
         cl.cnt = ctx->cnt;
         cl.err_flag = reinterpret_cast<int32_t*>(queue + 1);
+        cl.first_wait_polls = ctx->first_wait_polls.load();
         launch_collide(cl, s);
     }
     RankArgs ra{rs, d_tg, T, d_boff, thB, CB, sB, pB, oB, collide ? hB : nullptr, top_k, nullptr,

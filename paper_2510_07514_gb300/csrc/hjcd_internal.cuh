@@ -336,21 +336,22 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return r;
 }
 
-// Arctangent of t in [0, 1] as t P(t^2), P of degree 7: coefficients fitted
-// near-minimax on [0, 1] (least squares on Chebyshev nodes, reweighted toward
-// the largest errors); |error| < 4e-8 rad in exact arithmetic and < 1.5e-7
-// rad evaluated in binary32 (checked against float64 over [0, 1] by the test
-// suite, which reads these coefficients from this file).
+// Arctangent of t in [0, 1] as t P(t^2), P of degree 7: the coefficients
+// minimise the largest absolute error on a dense grid of [0, 1] (a linear
+// program; fit_atan.py beside this file regenerates them); |error| < 3e-8 rad
+// in exact arithmetic and < 1.5e-7 rad evaluated in binary32 (checked against
+// float64 over [0, 1] by the test suite, which reads these coefficients from
+// this file and compares them with the script's output).
 __device__ __forceinline__ float atan01(float t) {
     const float s = t * t;
-    float p = -4.054563120e-03f;
-    p = fmaf(p, s, 2.186294831e-02f);
-    p = fmaf(p, s, -5.591232702e-02f);
-    p = fmaf(p, s, 9.642198682e-02f);
-    p = fmaf(p, s, -1.390863061e-01f);
-    p = fmaf(p, s, 1.994656622e-01f);
-    p = fmaf(p, s, -3.332985938e-01f);
-    p = fmaf(p, s, 9.999993443e-01f);
+    float p = -4.166443301e-03f;
+    p = fmaf(p, s, 2.232482877e-02f);
+    p = fmaf(p, s, -5.666722692e-02f);
+    p = fmaf(p, s, 9.704074739e-02f);
+    p = fmaf(p, s, -1.393516270e-01f);
+    p = fmaf(p, s, 1.995220255e-01f);
+    p = fmaf(p, s, -3.333036250e-01f);
+    p = fmaf(p, s, 9.999994549e-01f);
     return t * p;
 }
 
@@ -509,7 +510,7 @@ struct CcdArgs {
     hjcd_params P;
     hjcd_ccd_trace tr;
     Counters* cnt;
-    int32_t block;  // threads (candidates) per CTA: 64, 128 (default, also for 0) or 256
+    int32_t block;  // threads (candidates) per CTA: 64, 128 or 256 (anything else: 128; contexts pass 64 by default)
     int32_t seed_base;  // added to each candidate's index inside its target (a shard of the seeds)
     // Iteration segments (no trace, th_out set): this launch runs iterations [seg_begin, seg_end)
     // (seg_end 0: to the cap) of every candidate, or of the candidates list_in[0 .. *n_in) whose
@@ -535,7 +536,7 @@ struct LmArgs {
     hjcd_lm_trace tr;
     Counters* cnt;
     unsigned long long* queue;  // candidate queue head, zero at launch
-    int32_t warps;  // warps per CTA: 2, 4 (default, also for 0) or 8
+    int32_t warps;  // warps per CTA: 2, 4 or 8 (anything else: 8, the contexts' default)
 };
 
 struct DupArgs {
@@ -581,33 +582,36 @@ struct RankArgs {
     // that the bounded lazy pass left unfinished); k_rank_lazy appends those targets here
     int32_t* list;
     int32_t* n_list;
+    // tolerances of every target when tg is null (with tg: each target row's own)
+    float eps_pos, eps_ori;
 };
 
 // Ranking key of candidate i of target t (candidates [b0, b0 + B), robot DoF
-// n): the score key of a finite score (with use_hit, never a colliding
-// candidate); with the target's nearest flag and A.q_ref, the candidates within
-// the target's tolerances in class 0 keyed by squared joint distance to the
-// reference, the rest in class 1 by score.  kNoKey past B.
+// n), never for a colliding candidate (with use_hit) or a non-finite score.
+// Reading c20 of Alg. 2's final step: the candidates within the target's
+// tolerances (|e_p| <= eps_pos and |omega| <= eps_ori) form class 0, the rest
+// class 1 (the top key bit), each class ordered by score and then index.  With
+// the target's nearest flag (with tg null: whenever q_ref is set), class 0 is
+// ordered by squared joint distance to the reference q_ref[t] instead
+// (reading c24).  kNoKey past B.
 __device__ __forceinline__ uint64_t rank_key(const RankArgs& A, int t, int64_t b0, int B, int n, int i, bool use_hit) {
     if (i >= B || (use_hit && A.hit && A.hit[b0 + i])) return kNoKey;
-    const float sc = A.score[b0 + i];
+    const int64_t g = b0 + i;
+    const float sc = A.score[g];
     if (!(sc < __int_as_float(0x7f800000))) return kNoKey;  // finite only
-    uint64_t k = score_key(sc, (uint32_t)i);
-    const int tk = A.tg ? A.tg[t].top_k : A.top_k;
-    if (A.q_ref && (tk & kNearestFlag)) {
-        const int64_t g = b0 + i;
-        if (A.perr[g] <= A.tg[t].eps_pos && A.oerr[g] <= A.tg[t].eps_ori) {
-            float d2 = 0.0f;
-            for (int j = 0; j < n; ++j) {
-                const float dj = A.th[j * A.ld + g] - A.q_ref[(int64_t)t * A.ld_ref + j];
-                d2 = fmaf(dj, dj, d2);
-            }
-            k = score_key(d2, (uint32_t)i);
-        } else {
-            k |= 1ull << 63;
+    const float ep = A.tg ? A.tg[t].eps_pos : A.eps_pos, eo = A.tg ? A.tg[t].eps_ori : A.eps_ori;
+    const bool conv = A.perr[g] <= ep && A.oerr[g] <= eo;
+    const bool nearest = A.q_ref && (!A.tg || (A.tg[t].top_k & kNearestFlag));
+    if (conv && nearest) {
+        float d2 = 0.0f;
+        for (int j = 0; j < n; ++j) {
+            const float dj = A.th[j * A.ld + g] - A.q_ref[(int64_t)t * A.ld_ref + j];
+            d2 = fmaf(dj, dj, d2);
         }
+        return score_key(d2, (uint32_t)i);
     }
-    return k;
+    const uint64_t k = score_key(sc, (uint32_t)i);
+    return conv ? k : (k | (1ull << 63));
 }
 
 // Collision filter of C candidates.  With tg null or uniform set every
@@ -631,6 +635,9 @@ struct CollideArgs {
     uint8_t* hit;
     Counters* cnt;
     int32_t* err_flag;        // set when the bounded wait for the staged tables runs out
+    // polls of the first wait for the staged tables (< 0: the kernels' default limit); 0 makes
+    // that wait run out at once, which only tests of the timeout path ask for
+    int64_t first_wait_polls = -1;
     // with list set: only the candidates of the targets list[0 .. *n_list) whose hit entry is 2
     // are checked, item i = (list entry i / list_bmax, candidate i % list_bmax of that target's
     // b_off range)
@@ -709,6 +716,7 @@ bool launch_rank_lazy(const CollideArgs& A, const RankArgs& R, int max_b, int de
 void launch_contacts(const RobotParams& R, const RobotDev& rd, const SceneDev& sc, const int32_t* perm, int64_t C,
                      const float* th, int64_t ld, uint8_t* touched, cudaStream_t st);
 void launch_ffma(float* sink, int iters, int blocks, cudaStream_t st);
+void launch_philox(int64_t n, const uint32_t* ctr, uint64_t key, uint32_t* out, cudaStream_t st);
 int ffma_flops_per_thread_iter();
 
 }  // namespace hjcd

@@ -72,6 +72,7 @@ struct hjcd_ctx {
     std::atomic<bool> collide_lazy{true};  // rank first, collision-check in rank order (hjcd_set_collision_mode)
     std::atomic<int32_t> ccd_block{64};    // launch configuration (hjcd_set_launch_config, hjcd_autotune)
     std::atomic<int32_t> lm_warps{8};
+    std::atomic<int64_t> first_wait_polls{-1};  // collision kernels' first staging wait (hjcd_set_wait_limit)
     std::mutex api_mu;  // robots/scenes tables against the serving thread
     hjcd::Server* server = nullptr;  // owned; freed by server_stop
 };

@@ -23,7 +23,9 @@ namespace hjcd {
 
 namespace {
 
-constexpr int kCcdThreads = 128;  // default CTA size (candidates per CTA); 64 and 256 also built
+// CTA size of the seed-sampling kernel, and of the PO-CCD kernel when the launch names none of
+// 64, 128, 256 (a context starts at 64 candidates per CTA: hjcd_set_launch_config)
+constexpr int kCcdThreads = 128;
 
 // shared-memory column of a thread in a CTA of TH threads: theta[n], then
 // (px py pz zx zy zz) per joint
@@ -72,13 +74,13 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 // p(t^2) of atan01 for both halves (atan t = t p(t^2), t in [0, 1])
 __device__ __forceinline__ float2 atan_poly2(float2 t) {
     const float2 s = mul2(t, t);
-    float2 p = fma2(bc2(-4.054563120e-03f), s, bc2(2.186294831e-02f));
-    p = fma2(p, s, bc2(-5.591232702e-02f));
-    p = fma2(p, s, bc2(9.642198682e-02f));
-    p = fma2(p, s, bc2(-1.390863061e-01f));
-    p = fma2(p, s, bc2(1.994656622e-01f));
-    p = fma2(p, s, bc2(-3.332985938e-01f));
-    return fma2(p, s, bc2(9.999993443e-01f));
+    float2 p = fma2(bc2(-4.166443301e-03f), s, bc2(2.232482877e-02f));
+    p = fma2(p, s, bc2(-5.666722692e-02f));
+    p = fma2(p, s, bc2(9.704074739e-02f));
+    p = fma2(p, s, bc2(-1.393516270e-01f));
+    p = fma2(p, s, bc2(1.995220255e-01f));
+    p = fma2(p, s, bc2(-3.333036250e-01f));
+    return fma2(p, s, bc2(9.999994549e-01f));
 }
 
 // quat_angle of both halves: 2 atan2(sqrt(vv), |w|); the reflection about pi/4 takes the last

@@ -71,8 +71,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kWaitLimit; ++i)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit = kWaitLimit) {
+    for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -382,9 +382,12 @@ __device__ __forceinline__ bool collide_prologue(const CollideArgs& A, unsigned 
     }
     *rob = stage_robots(smem + L.robots, A.rs);
     if (UNIFORM) {
-        const bool staged = mbar_wait_bounded(bar, 0);
+        const uint32_t polls = A.first_wait_polls < 0 ? kWaitLimit
+                               : (uint32_t)(A.first_wait_polls < (int64_t)kWaitLimit ? A.first_wait_polls : kWaitLimit);
+        const bool staged = mbar_wait_bounded(bar, 0, polls);
         if (__syncthreads_or(!staged)) {
-            // give up: flag the error, give the copy one more bounded wait
+            // give up: flag the error, give the copy one more bounded wait (the full limit: the
+            // copy must land before the CTA's shared memory is released)
             if (threadIdx.x == 0) {
                 atomicExch(A.err_flag, 1);
                 mbar_wait_bounded(bar, 0);

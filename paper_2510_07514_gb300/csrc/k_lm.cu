@@ -661,6 +661,13 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
             if (TRACE && kk == 0) {
                 if (A.tr.branch) A.tr.branch[c] = branch;
                 if (A.tr.alpha) A.tr.alpha[c] = alpha_acc;
+                if (failed) {  // the fallback steps exist for the slots whose full step failed
+                    if (A.tr.d_dog)
+#pragma unroll 1
+                        for (int j = 0; j < n; ++j) A.tr.d_dog[j * A.ld + c] = S.d2(j, lane);
+                    if (A.tr.sc_joint) A.tr.sc_joint[c] = S.sc_j(lane);
+                    if (A.tr.sc_step) A.tr.sc_step[c] = S.sc_step(lane);
+                }
             }
             ++kk;
             ++n_it;

@@ -1,5 +1,6 @@
-// k_misc.cu -- forward-kinematics stage kernel (Eq. fk) and the FP32 FMA
-// throughput probe used as the CUDA-core roofline denominator.
+// k_misc.cu -- forward-kinematics stage kernel (Eq. fk), raw blocks of the
+// kernels' Philox generator, and the FP32 FMA throughput probe used as the
+// CUDA-core roofline denominator.
 #include "hjcd_internal.cuh"
 
 namespace hjcd {
@@ -23,6 +24,12 @@ __global__ void __launch_bounds__(128) k_fk(const RobotParams R, int64_t C, cons
         o[5] = q.v.y;
         o[6] = q.v.z;
     }
+}
+
+// out[i] = Philox4x32-10 block at counter ctr[i] under (k0, k1): the generator every kernel draws from
+__global__ void __launch_bounds__(256) k_philox(int64_t n, const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = philox(ctr[i], k0, k1);
 }
 
 constexpr int kChains = 8, kUnroll = 16;
@@ -50,6 +57,12 @@ __global__ void __launch_bounds__(256) k_ffma(float* sink, int iters) {
 void launch_fk(const RobotParams& R, int64_t C, const float* th, int64_t ld, float* out, cudaStream_t st) {
     if (C <= 0) return;
     k_fk<<<grid_for(C, 128), 128, 0, st>>>(R, C, th, ld, out);
+}
+
+void launch_philox(int64_t n, const uint32_t* ctr, uint64_t key, uint32_t* out, cudaStream_t st) {
+    if (n <= 0) return;
+    k_philox<<<grid_for(n, 256), 256, 0, st>>>(n, reinterpret_cast<const uint4*>(ctr), (uint32_t)key,
+                                               (uint32_t)(key >> 32), reinterpret_cast<uint4*>(out));
 }
 
 void launch_ffma(float* sink, int iters, int blocks, cudaStream_t st) { k_ffma<<<blocks, 256, 0, st>>>(sink, iters); }

@@ -362,6 +362,7 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
         cl.hit = hB;
         cl.cnt = ctx->cnt;
         cl.err_flag = wave_flag(W, ws);
+        cl.first_wait_polls = ctx->first_wait_polls.load();
     }
     // the top_k collision-free candidates by score are the first top_k collision-free ones in score
     // order: check candidates in that order until they are found (same output as filtering all)

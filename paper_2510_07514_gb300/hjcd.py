@@ -37,6 +37,7 @@ EXPORTS = (
     "hjcd_graph_create", "hjcd_graph_launch", "hjcd_graph_check", "hjcd_graph_destroy",
     "hjcd_set_launch_config", "hjcd_autotune", "hjcd_set_memory_budget", "hjcd_scene_contacts",
     "hjcd_shard_topk", "hjcd_topk_merge", "hjcd_solve_from_topk", "hjcd_set_collision_mode",
+    "hjcd_philox", "hjcd_set_wait_limit",
 )
 
 
@@ -98,7 +99,7 @@ class hjcd_ccd_trace(ct.Structure):
 
 
 class hjcd_lm_trace(ct.Structure):
-    _fields_ = [(k, ct.c_void_p) for k in ("J", "W", "d_lm", "branch", "alpha")]
+    _fields_ = [(k, ct.c_void_p) for k in ("J", "W", "d_lm", "branch", "alpha", "d_dog", "sc_joint", "sc_step")]
 
 
 _V = ct.c_void_p
@@ -147,7 +148,9 @@ _SIGS = {
     "hjcd_pjik": (_ST, [_V, _I32, _I, _V, _F, _F, _U64, ct.POINTER(hjcd_params), _I64, _V, _V, _V, _I64, _I, _I,
                         _V, _V, _V, _V, ct.POINTER(hjcd_lm_trace), _V]),
     "hjcd_collide": (_ST, [_V, _I32, _I32, _I64, _V, _I64, _V, _V]),
-    "hjcd_rank": (_ST, [_V, _I32, _I, _V, _V, _I64, _V, _V, _V, _V, _I, _V, _V, _V, _V]),
+    "hjcd_rank": (_ST, [_V, _I32, _I, _V, _V, _I64, _V, _V, _V, _V, _F, _F, _V, _I, _V, _V, _V, _V]),
+    "hjcd_philox": (_ST, [_V, _I64, _V, _U64, _V, _V]),
+    "hjcd_set_wait_limit": (_ST, [_V, _I64]),
     "hjcd_set_profiling": (_ST, [_V, _I]),
     "hjcd_phase_times": (_ST, [_V, ct.POINTER(_F)]),
     "hjcd_counters": (_ST, [_V, ct.POINTER(_U64), _I]),
@@ -423,11 +426,20 @@ def hjcd_collide(ctx, robot_id, scene_id, n_cand, theta, ld, hit, stream=None) -
                                     stream_handle(stream)))
 
 
-def hjcd_rank(ctx, robot_id, n_targets, b_off, theta_B, ld, score, perr, oerr, hit, top_k, out_q, out_err,
-              out_count, stream=None) -> None:
+def hjcd_rank(ctx, robot_id, n_targets, b_off, theta_B, ld, score, perr, oerr, hit, eps_pos, eps_ori, q_ref,
+              top_k, out_q, out_err, out_count, stream=None) -> None:
     _check(ctx, load().hjcd_rank(ctx, int(robot_id), int(n_targets), ptr(b_off), ptr(theta_B), int(ld), ptr(score),
-                                 ptr(perr), ptr(oerr), ptr(hit), int(top_k), ptr(out_q), ptr(out_err),
-                                 ptr(out_count), stream_handle(stream)))
+                                 ptr(perr), ptr(oerr), ptr(hit), float(eps_pos), float(eps_ori), ptr(q_ref),
+                                 int(top_k), ptr(out_q), ptr(out_err), ptr(out_count), stream_handle(stream)))
+
+
+def hjcd_philox(ctx, n_blocks, ctr, key, out, stream=None) -> None:
+    _check(ctx, load().hjcd_philox(ctx, int(n_blocks), ptr(ctr), int(key) & (2 ** 64 - 1), ptr(out),
+                                   stream_handle(stream)))
+
+
+def hjcd_set_wait_limit(ctx, polls: int) -> None:
+    _check(ctx, load().hjcd_set_wait_limit(ctx, int(polls)))
 
 
 def hjcd_set_profiling(ctx, on: bool) -> None:

@@ -27,13 +27,18 @@ def target_range(T: int, rank: int, world: int) -> tuple[int, int]:
 
 def allgather_lists(score: torch.Tensor, index: torch.Tensor, theta: torch.Tensor, group=None):
     """Every rank's (score [T,K], seed index [T,K], joint vectors [T,K,n]),
-    stacked in rank order: ([L,T,K], [L,T,K], [L,T,K,n])."""
+    stacked in rank order: ([L,T,K], [L,T,K], [L,T,K,n]), on the inputs'
+    device.  Over a gloo group device tensors travel through host memory (gloo
+    gathers host tensors); over NCCL they stay on the device."""
     world = dist.get_world_size(group)
+    via_host = score.is_cuda and dist.get_backend(group) == "gloo"
     out = []
     for x in (score, index, theta):
-        parts = [torch.empty_like(x) for _ in range(world)]
-        dist.all_gather(parts, x.contiguous(), group=group)
-        out.append(torch.stack(parts))
+        y = x.contiguous().cpu() if via_host else x.contiguous()
+        parts = [torch.empty_like(y) for _ in range(world)]
+        dist.all_gather(parts, y, group=group)
+        st = torch.stack(parts)
+        out.append(st.to(x.device) if via_host else st)
     return tuple(out)
 
 

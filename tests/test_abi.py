@@ -61,7 +61,7 @@ def test_struct_layouts(lib):
     assert ctypes.sizeof(hjcd.hjcd_params) == 20 * 4
     assert ctypes.sizeof(hjcd.hjcd_solve_opts) == 4 * 4 + 8 + 8 + 8
     assert ctypes.sizeof(hjcd.hjcd_ccd_trace) == 10 * 8
-    assert ctypes.sizeof(hjcd.hjcd_lm_trace) == 5 * 8
+    assert ctypes.sizeof(hjcd.hjcd_lm_trace) == 8 * 8
     assert ctypes.sizeof(hjcd.hjcd_batch_item) == 4 * 4 + 2 * 8 + 2 * 4 + 8 + ctypes.sizeof(hjcd.hjcd_solve_opts) + 4 * 8
     assert ctypes.sizeof(hjcd.hjcd_server_opts) == 4 + 4 + 8 + 8 + 8
     assert ctypes.sizeof(hjcd.hjcd_request_info) == 4 + 4 + 8 + 8
@@ -120,6 +120,22 @@ def test_device_arctangent_polynomial_error_bound():
     Y, X = np.meshgrid(g, g)
     ref = np.arctan2(Y.astype(np.float64), X.astype(np.float64))
     assert np.max(np.abs(atan2_all(Y, X) - ref)) < 3e-7
+
+
+def test_arctangent_coefficients_are_the_fitting_scripts():
+    """The kernels' arctangent coefficients are what csrc/fit_atan.py computes
+    (the minimax fit of t P(t^2) to atan on [0, 1]), digit for digit."""
+    import importlib.util
+    import re
+    csrc = os.path.join(ROOT, "paper_2510_07514_gb300", "csrc")
+    spec = importlib.util.spec_from_file_location("fit_atan", os.path.join(csrc, "fit_atan.py"))
+    fa = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(fa)
+    c, z = fa.fit()
+    assert z < 3e-8
+    inc = open(os.path.join(csrc, "hjcd_internal.cuh")).read()
+    got = re.findall(r"([-+]?\d\.\d+e[-+]\d+)f", inc[inc.index("float atan01(float t)"):inc.index("float atan2_q1(")])
+    assert got == fa.formatted(c)
 
 
 def test_device_ccd_constants():

@@ -368,3 +368,113 @@ def test_segmented_mixed_robot_batch_equals_each_request_alone(ctx):
         for t in range(len(ca)):
             assert np.array_equal(qa[t, :ca[t]], qb[t, :cb[t]])
             assert np.array_equal(ea[t, :ca[t]], eb[t, :cb[t]])
+
+
+def test_autotuned_caps_match_the_oracle_with_the_same_caps(ctx):
+    """The autotuner changes results only through the iteration caps it picks
+    (reading c9 and c17 leave them as parameters): with the tuned caps the
+    mixed-robot batch must solve like the oracle run with the same caps --
+    success within one point per robot class, every solution re-verified."""
+    rng = np.random.default_rng(57)
+    chains = inputs.cfg3_chains()
+    robs = [inputs.panda_with_spheres(np.random.default_rng(5)), chains[1], chains[3]]
+    rids = [ctx.add_robot(r) for r in robs]
+    scene = inputs.random_scene(rng, 60, 6)
+    sid = ctx.set_scene(scene)
+    S = 128
+    cal = []
+    for i, rob in enumerate(robs):
+        tg = f32(orc.pose(orc.Robot(rob), f32(rng.uniform(rob.lo, rob.hi, (24, rob.n)))))
+        cal.append(ctx.batch_item(rids[i], -1, dev(tg), S, 1, 500 + i, rob.n)[0])
+    try:
+        tuned, rep = hjcd.hjcd_autotune(ctx.h, cal, None, 0.02, 1)
+    finally:
+        hjcd.hjcd_set_launch_config(ctx.h, 64, 8)
+    caps = dict(cd_max_iters=int(tuned.cd_max_iters), lm_max_iters=int(tuned.lm_max_iters))
+    T = 300
+    items, outs, meta = [], [], []
+    for i, rob in enumerate(robs):
+        sc = scene if i == 0 else None
+        orob, osc = orc.Robot(rob), (orc.Scene(sc) if sc is not None else None)
+        pool = f32(rng.uniform(rob.lo, rob.hi, (20 * T, rob.n)))
+        keep = pool[~orc.collide(orob, osc, pool)[0]][:T] if len(rob.sph_body) else pool[:T]
+        assert len(keep) == T
+        tg = f32(orc.pose(orob, keep))
+        it, out = ctx.batch_item(rids[i], sid if i == 0 else -1, dev(tg), S, 1, 600 + i, rob.n,
+                                 params=api.make_params(**caps))
+        items.append(it)
+        outs.append(out)
+        meta.append((rob, orob, osc, tg))
+    ctx.solve_batch(items, params=tuned)
+    sg_all, so_all = [], []
+    for i, (rob, orob, osc, tg) in enumerate(meta):
+        q, e, c = (host(x) for x in outs[i])
+        sg = _verify(orob, osc, rob, tg, q, e, c.astype(int), 1e-3, 1e-2)
+        o = orc.solve(orob, osc, orc.make_params(1e-3, 1e-2, seed=600 + i, **caps), tg, S, 1)
+        so = (o["count"] > 0) & (o["err"][:, 0, 0] <= 1e-3) & (o["err"][:, 0, 1] <= 1e-2)
+        assert abs(sg.mean() - so.mean()) <= 0.03 + 1e-12, (i, caps, sg.mean(), so.mean())
+        sg_all.append(sg)
+        so_all.append(so)
+    sg, so = np.concatenate(sg_all), np.concatenate(so_all)
+    assert abs(sg.mean() - so.mean()) <= 0.01 + 1e-12, (caps, sg.mean(), so.mean())
+
+
+def test_solve_nearest_matches_the_oracle(ctx):
+    """hjcd_solve_nearest against the oracle's whole method with the same
+    reference configurations (reading c24): success rates within one point,
+    every returned solution re-verified, and the converged rows nearest-first."""
+    wl = inputs.cfg1()
+    rob = wl.robot
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    rng = np.random.default_rng(83)
+    T, S, k = 300, 128, 4
+    tg = f32(orc.pose(orob, f32(rng.uniform(rob.lo, rob.hi, (T, 7)))))
+    qref = f32(rng.uniform(rob.lo, rob.hi, (T, 7)))
+    q, e, c = (host(x) for x in ctx.solve(rid, -1, dev(tg), S, k, 19, 7, q_current=dev(qref)))
+    c = c.astype(int)
+    sg = _verify(orob, None, rob, tg, q, e, c, 1e-3, 1e-2)
+    o = orc.solve(orob, None, orc.make_params(1e-3, 1e-2, seed=19), tg, S, k, q_ref=qref)
+    so = (o["count"] > 0) & (o["err"][:, 0, 0] <= 1e-3) & (o["err"][:, 0, 1] <= 1e-2)
+    assert abs(sg.mean() - so.mean()) <= 0.01 + 1e-12, (sg.mean(), so.mean())
+    for src_q, src_e, src_c in ((q, e, c), (o["q"], o["err"], o["count"])):
+        for t in range(T):
+            ok = (src_e[t, :src_c[t], 0] <= 1e-3) & (src_e[t, :src_c[t], 1] <= 1e-2)
+            m = int(ok.sum())
+            assert np.all(ok[:m])
+            d = np.linalg.norm(src_q[t, :m] - qref[t], axis=1)
+            assert np.all(np.diff(d) >= -1e-6)
+
+
+def test_tracking_loop_follows_a_scene_rewritten_every_frame(ctx):
+    """The tracking use (Sec. VI-D): each frame the obstacle scene is replaced
+    in place (hjcd_set_scene on the same id) and the next pose is solved from
+    the current configuration.  Each frame's solutions must be collision-free
+    in that frame's scene under the oracle's brute force, and equal a solve
+    in a fresh context holding only that scene."""
+    rng = np.random.default_rng(87)
+    rob = inputs.panda_with_spheres(np.random.default_rng(5))
+    orob = orc.Robot(rob)
+    rid = ctx.add_robot(rob)
+    sid = ctx.set_scene(inputs.random_scene(rng, 10, 2))
+    fresh = api.Context(0)
+    try:
+        frid = fresh.add_robot(rob)
+        q_cur = f32(rng.uniform(rob.lo, rob.hi, (1, 7)))
+        for frame in range(4):
+            scene = inputs.random_scene(rng, 24, 2)
+            osc = orc.Scene(scene)
+            ctx.set_scene(scene, scene_id=sid)
+            pool = f32(np.clip(q_cur + rng.normal(0, 0.2, (400, 7)), rob.lo, rob.hi))
+            keep = pool[~orc.collide(orob, osc, pool)[0]][:1]
+            assert len(keep) == 1
+            tg = f32(orc.pose(orob, keep))
+            got = ctx.solve(rid, sid, dev(tg), 256, 2, 700 + frame, 7, q_current=dev(q_cur))
+            q, e, c = (host(x) for x in got)
+            _verify(orob, osc, rob, tg, q, e, c.astype(int), 1e-3, 1e-2)
+            fsid = fresh.set_scene(scene)
+            _same(got, fresh.solve(frid, fsid, dev(tg), 256, 2, 700 + frame, 7, q_current=dev(q_cur)))
+            if c[0] > 0:
+                q_cur = f32(q[0, :1])
+    finally:
+        fresh.close()

@@ -12,6 +12,7 @@ Collision verdicts are compared bit-exactly where the oracle's verdict margin
 is at least 1e-6 m.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -299,11 +300,16 @@ def _lm_gpu(ctx, rid, n, tg, tgt, cand, th, k, params, seed):
     d = torch.zeros((n, C), device="cuda")
     br = torch.zeros((C,), dtype=torch.int32, device="cuda")
     al = torch.zeros((C,), device="cuda")
-    tr = hjcd.hjcd_lm_trace(*[hjcd.ptr(x) for x in (J, W, d, br, al)])
+    # the fallback steps are written only where the full step failed: NaN / -1 elsewhere
+    dd = torch.full((n, C), float("nan"), device="cuda")
+    sj = torch.full((C,), -1, dtype=torch.int32, device="cuda")
+    ss = torch.full((C,), float("nan"), device="cuda")
+    tr = hjcd.hjcd_lm_trace(*[hjcd.ptr(x) for x in (J, W, d, br, al, dd, sj, ss)])
     hjcd.hjcd_pjik(ctx.h, rid, len(tg), dev(tg), 1e-3, 1e-2, seed, params, C, dev(tgt, torch.int32),
                    dev(cand, torch.int32), theta, C, k, 1, trace=tr)
     return dict(J=host(J).T.reshape(C, 6, n), W=host(W).T, d_lm=host(d).T, branch=host(br).astype(int),
-                alpha=host(al), theta=host(theta).T)
+                alpha=host(al), theta=host(theta).T, d_dog=host(dd).T, sc_joint=host(sj).astype(int),
+                sc_step=host(ss))
 
 
 def _cond(J, W, lam):
@@ -353,6 +359,101 @@ def test_lm_iteration_trace_parity(ctx, which):
     assert np.array_equal(g["alpha"][robust], o["alpha"][robust].astype(np.float32).astype(np.float64))
     assert np.max(np.abs(g["theta"] - o["theta"])[robust]) < tol
     assert set(np.unique(o["branch"][robust])) >= {0}
+
+
+def _cond_gn(J, W, mu):
+    """Condition number of the dogleg's 6x6 Gauss-Newton system
+    (WJ)(WJ)^T + mu I after diagonal equilibration."""
+    Jw = W[:, None] * J
+    M = Jw @ Jw.T + mu * np.eye(6)
+    s = 1 / np.sqrt(np.diag(M))
+    ev = np.linalg.eigvalsh(M * s[:, None] * s[None, :])
+    return ev[-1] / max(ev[0], 1e-300)
+
+
+@pytest.mark.parametrize("which", ["panda", "chain12", "chain20", "chain24"])
+def test_lm_fallback_branch_trace_parity(ctx, which):
+    """Alg. 4's failure path, branch by branch.  Inputs: candidates after 10
+    oracle PJ-IK iterations from uniform seeds, where a third or more of the
+    iterations fail the full step.  Where the full step failed on the GPU the
+    trace holds its dogleg step (Eq. dogleg), its single-coordinate joint and
+    step (Eq. single-coord); they are compared with the oracle's, and where
+    the oracle's decisions are clear so are the branch, the accepted alpha
+    and the new theta.  The dogleg (branch 1) and the single coordinate
+    (branch 2) must both occur among the compared candidates (the
+    perturbation, branch 3, has its own forced case below)."""
+    rob = dict(robots())[which]
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    rng = np.random.default_rng(61)
+    T, C, k, seed = 11, 1031, 10, 5
+    tg = f32(orc.pose(orob, f32(rng.uniform(rob.lo, rob.hi, (T, rob.n)))))
+    tgt = rng.integers(0, T, C).astype(np.int32)
+    cand = np.arange(C).astype(np.int32)
+    P64 = orc.make_params(seed=seed, lm_max_iters=k)
+    th = f32(orc.pjik(orob, P64, tg, tgt, cand, rng.uniform(rob.lo, rob.hi, (C, rob.n)))["theta"])
+    g = _lm_gpu(ctx, rid, rob.n, tg, tgt, cand, th, k, api.make_params(), seed)
+    o = orc.lm_iteration(orob, P64, tg, tgt, cand, k, th)
+    tol = TOL * max(1.0, reach(rob) / 1.5)
+    u = 2.0 ** -24
+    fell = g["sc_joint"] >= 0                     # the GPU took the failure path
+    assert np.array_equal(fell, (g["branch"] != 0) | (g["alpha"] < 1))
+    assert fell.mean() > 0.2
+    cond_lm = np.array([_cond(o["J"][c], o["W"][c], P64.lm_lambda) for c in range(C)])
+    cond_gn = np.array([_cond_gn(o["J"][c], o["W"][c], P64.lm_gn_reg) for c in range(C)])
+    # dogleg step: 1e-5 where the 6x6 solve is well conditioned, else the derived bound
+    ddog_err = np.max(np.abs(g["d_dog"] - o["d_dog"]), axis=1)
+    ddog_bound = tol + 8 * cond_gn * u * np.max(np.abs(o["d_dog"]), axis=1)
+    assert np.all(ddog_err[fell] < ddog_bound[fell])
+    well_gn = fell & (cond_gn < 100)
+    assert well_gn.sum() > 20
+    assert np.max(ddog_err[well_gn]) < tol
+    # single coordinate: the joint wherever the largest |g_i| is clear, the step on that joint
+    gr = np.einsum("cri,cr->ci", o["W"][:, :, None] * o["J"], o["W"] * np.array(
+        [orc.residual(orob, th[c], tg[tgt[c]]) for c in range(C)]))
+    ag = np.sort(np.abs(gr), axis=1)
+    clear = fell & ((ag[:, -1] - ag[:, -2]) > 1e-4 * ag[:, -1])
+    assert clear.sum() > 20
+    assert np.array_equal(g["sc_joint"][clear], o["sc_joint"][clear])
+    # the 1-D step g_i / |(WJ)_i|^2: its rounding grows with the cancellation in g_i
+    Jw = o["W"][:, :, None] * o["J"]
+    i_s = o["sc_joint"]
+    canc = np.array([np.sum(np.abs(Jw[c, :, i_s[c]] * o["W"][c] * orc.residual(orob, th[c], tg[tgt[c]])))
+                     / max(abs(gr[c, i_s[c]]), 1e-300) for c in range(C)])
+    sc_bound = tol + 16 * canc * u * np.abs(o["sc_step"])
+    assert np.all(np.abs(g["sc_step"] - o["sc_step"])[clear] < sc_bound[clear])
+    # decisions where the oracle's cost comparisons are clear and every step is accurate
+    robust = fell & clear & (cond_lm < 100) & (cond_gn < 100) & (o["ls_margin"] > 1e-4)
+    assert np.array_equal(g["branch"][robust], o["branch"][robust])
+    assert np.array_equal(g["alpha"][robust], o["alpha"][robust].astype(np.float32).astype(np.float64))
+    moved = robust & (o["branch"] < 3)
+    assert np.max(np.abs(g["theta"] - o["theta"])[moved]) < tol
+    br = set(np.unique(o["branch"][robust]))
+    assert {1, 2} <= br, br
+
+
+def test_lm_perturbation_branch_parity(ctx):
+    """Branch 3 of Alg. 4, forced: a stretched planar arm whose target lies
+    straight ahead beyond reach with the same orientation has a zero gradient,
+    so the LM, dogleg and single-coordinate steps are zero on both sides and no
+    trial lowers the cost; both perturb with the candidate's PJ-IK normal
+    stream, whose draws must agree."""
+    rob = inputs.planar([0.5, 0.4, 0.3])
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    C, seed = 64, 21
+    th = np.zeros((C, 3))
+    tg = f32(orc.pose(orob, th[:1]))
+    tg[0, 0] += 0.6
+    tgt = np.zeros(C, np.int32)
+    cand = np.arange(C).astype(np.int32)
+    for k in (0, 13):
+        g = _lm_gpu(ctx, rid, 3, tg, tgt, cand, th, k, api.make_params(), seed)
+        o = orc.lm_iteration(orob, orc.make_params(seed=seed), tg, tgt, cand, k, th)
+        assert np.all(o["branch"] == 3) and np.all(g["branch"] == 3)
+        assert np.all(g["d_lm"] == 0) and np.all(g["d_dog"] == 0) and np.all(g["sc_step"] == 0)
+        assert np.max(np.abs(g["theta"] - o["theta"])) < TOL
+        assert np.std(g["theta"]) > 0.005  # the draws differ per candidate
 
 
 def test_pjik_converges_like_the_oracle(ctx):
@@ -452,7 +553,22 @@ def test_collision_verdict_parity(ctx, case):
 # ----------------------------------------------------------------------------
 # a8: ranking
 
+def _rank_gpu(ctx, rid, b_off, th, score, perr, oerr, hit, k, eps, q_ref=None):
+    T, CB = len(b_off) - 1, int(b_off[-1])
+    n = th.shape[1]
+    oq = torch.zeros((T, k, n), device="cuda")
+    oe = torch.zeros((T, k, 2), device="cuda")
+    oc = torch.zeros((T,), dtype=torch.int32, device="cuda")
+    hjcd.hjcd_rank(ctx.h, rid, T, dev(b_off, torch.int64), soa(th), CB, dev(score), dev(perr), dev(oerr),
+                   None if hit is None else dev(hit, torch.uint8), eps[0], eps[1],
+                   None if q_ref is None else dev(q_ref), k, oq, oe, oc)
+    return host(oq), host(oe), host(oc).astype(int)
+
+
 def test_rank_parity(ctx):
+    """Alg. 2's final ranking, bit-exact: collision-free candidates, those
+    within the tolerances first (reading c20), each group by score, ties to the
+    lower index; rows past the count NaN."""
     rob = inputs.panda()
     rid = ctx.add_robot(rob)
     orob = orc.Robot(rob)
@@ -462,24 +578,99 @@ def test_rank_parity(ctx):
     CB = int(b_off[-1])
     th = f32(rng.uniform(rob.lo, rob.hi, (CB, 7)))
     score = np.round(rng.uniform(0, 3, CB), 1).astype(np.float32)
-    perr = rng.uniform(0, 1e-3, CB).astype(np.float32)
-    oerr = rng.uniform(0, 1e-2, CB).astype(np.float32)
+    perr = rng.uniform(0, 2e-3, CB).astype(np.float32)
+    oerr = rng.uniform(0, 2e-2, CB).astype(np.float32)
+    # a converged candidate whose score is above a non-converged one's, at the head of target 0
+    perr[0:2], oerr[0:2], score[0:2] = [1.05e-3, 0.9e-3], [0.0, 0.9e-2], [0.0, 0.05]
     hit = (rng.uniform(size=CB) < 0.6).astype(np.uint8)
+    hit[0:2] = 0
     hit[b_off[1]:b_off[2]] = 1
     k = 16
     T = len(Bs)
-    oq = torch.zeros((T, k, 7), device="cuda")
-    oe = torch.zeros((T, k, 2), device="cuda")
-    oc = torch.zeros((T,), dtype=torch.int32, device="cuda")
-    hjcd.hjcd_rank(ctx.h, rid, T, dev(b_off, torch.int64), soa(th), CB, dev(score), dev(perr), dev(oerr),
-                   dev(hit, torch.uint8), k, oq, oe, oc)
-    o = orc.rank(orob, b_off, th, score.astype(np.float64), f32(perr), f32(oerr), hit, k)
-    cnt = host(oc).astype(int)
+    eps = (np.float32(1e-3), np.float32(1e-2))  # both sides compare in binary32 values
+    q, e, cnt = _rank_gpu(ctx, rid, b_off, th, score, perr, oerr, hit, k, eps)
+    o = orc.rank(orob, b_off, th, score.astype(np.float64), f32(perr), f32(oerr), hit, k,
+                 float(eps[0]), float(eps[1]))
     assert np.array_equal(cnt, o["count"])
-    q, e = host(oq), host(oe)
+    assert np.array_equal(q[0, 0], th[1])  # converged first although its score is higher
     for t in range(T):
         assert np.array_equal(q[t, :cnt[t]], o["q"][t, :cnt[t]])
         assert np.array_equal(e[t, :cnt[t]], o["err"][t, :cnt[t]])
+        assert np.all(np.isnan(q[t, cnt[t]:])) and np.all(np.isnan(e[t, cnt[t]:]))
+    # without a collision mask every target fills its rows
+    q2, e2, c2 = _rank_gpu(ctx, rid, b_off, th, score, perr, oerr, None, k, eps)
+    o2 = orc.rank(orob, b_off, th, score.astype(np.float64), f32(perr), f32(oerr), None, k,
+                  float(eps[0]), float(eps[1]))
+    assert np.array_equal(c2, o2["count"]) and np.array_equal(q2[:, :1], o2["q"][:, :1])
+
+
+def test_rank_nearest_parity(ctx):
+    """The tracking ranking (reading c24) against the oracle's: within the
+    tolerances by squared joint distance to the reference, then by score.  The
+    distances are sums in binary32 on the GPU and in double in the oracle, so
+    the order is compared where consecutive distances differ clearly."""
+    rob = inputs.panda()
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    rng = np.random.default_rng(12)
+    Bs = np.array([64, 300, 1, 2000], np.int64)
+    b_off = np.concatenate([[0], np.cumsum(Bs)])
+    CB, T, k = int(b_off[-1]), len(Bs), 24
+    th = f32(rng.uniform(rob.lo, rob.hi, (CB, 7)))
+    q_ref = f32(rng.uniform(rob.lo, rob.hi, (T, 7)))
+    score = rng.uniform(0, 3, CB).astype(np.float32)
+    perr = rng.uniform(0, 2e-3, CB).astype(np.float32)
+    oerr = rng.uniform(0, 2e-2, CB).astype(np.float32)
+    hit = (rng.uniform(size=CB) < 0.3).astype(np.uint8)
+    eps = (np.float32(1e-3), np.float32(1e-2))
+    q, e, cnt = _rank_gpu(ctx, rid, b_off, th, score, perr, oerr, hit, k, eps, q_ref=q_ref)
+    o = orc.rank(orob, b_off, th, score.astype(np.float64), f32(perr), f32(oerr), hit, k,
+                 float(eps[0]), float(eps[1]), q_ref=q_ref)
+    assert np.array_equal(cnt, o["count"])
+    compared = 0
+    for t in range(T):
+        c = cnt[t]
+        conv = (o["err"][t, :c, 0] <= eps[0]) & (o["err"][t, :c, 1] <= eps[1])
+        d = np.sum((o["q"][t, :c] - q_ref[t]) ** 2, axis=1)
+        # rows whose distance is clear of both neighbours' (relative 1e-5) must match exactly
+        gap = np.full(c, np.inf)
+        dd = np.abs(np.diff(d)) / np.maximum(d[1:], 1e-12)
+        gap[1:] = np.minimum(gap[1:], dd)
+        gap[:-1] = np.minimum(gap[:-1], dd)
+        sure = ~conv | (gap > 1e-5)
+        assert np.array_equal(q[t, :c][sure], o["q"][t, :c][sure])
+        compared += int((sure & conv).sum())
+    assert compared > 20
+
+
+def test_philox_blocks_are_bit_exact(ctx):
+    """The kernels' Philox4x32-10 generator, word for word: the published
+    known-answer vectors and the oracle's generator on the counters of every
+    phase of the method's streams."""
+    gold = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")) as f:
+        for ln in f:
+            if ln.strip() and not ln.startswith("#"):
+                gold.append([int(x, 16) for x in ln.split()])
+    assert len(gold) == 3
+    for r in gold:
+        ctr = torch.tensor(np.array(r[0:4], np.uint32).view(np.int32), dtype=torch.int32, device="cuda")
+        out = torch.zeros(4, dtype=torch.int32, device="cuda")
+        hjcd.hjcd_philox(ctx.h, 1, ctr, r[4] | (r[5] << 32), out)
+        got = out.cpu().numpy().view(np.uint32)
+        assert [int(x) for x in got] == r[6:10]
+    rng = np.random.default_rng(13)
+    N = 4096
+    ctr = rng.integers(0, 2 ** 32, (N, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:512, 2] = (rng.integers(1, 5, 512) << 24) | rng.integers(0, 64, 512)  # phase << 24 | iteration
+    key = int(rng.integers(0, 2 ** 63)) * 2 + 1
+    d_ctr = torch.tensor(ctr.view(np.int32), device="cuda")
+    d_out = torch.zeros((N, 4), dtype=torch.int32, device="cuda")
+    hjcd.hjcd_philox(ctx.h, N, d_ctr, key, d_out)
+    got = d_out.cpu().numpy().view(np.uint32)
+    kw = np.array([key & 0xFFFFFFFF, key >> 32], np.uint32)
+    for i in range(N):
+        assert np.array_equal(got[i], orc.philox(ctr[i], kw)), i
 
 
 # ----------------------------------------------------------------------------

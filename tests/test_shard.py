@@ -118,3 +118,92 @@ def test_sharded_seeds_equal_the_single_device_solve():
         assert t0 == 0 and np.array_equal(c1.cpu().numpy(), a[2])
     finally:
         c.close()
+
+
+def _cfg2_free_targets(T):
+    """Poses of the first T joint samples of the 1000 x 1000 workload's
+    generator that the oracle finds collision-free (a witness exists)."""
+    import oracle as orc
+    from paper_2510_07514_gb300 import inputs
+    wl = inputs.cfg2(T, 512)
+    orob, osc = orc.Robot(wl.robot), orc.Scene(wl.scene)
+    pool = np.asarray(wl.theta_gen, np.float32).astype(np.float64)
+    hit, _ = orc.collide(orob, osc, pool)
+    keep = pool[~hit][:T]
+    assert len(keep) == T
+    return wl, np.asarray(orc.pose(orob, keep), np.float32)
+
+
+def _gpu_worker(rank, world, port, q, T, M, k, seed):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2510_07514_gb300 import api
+        wl, tg = _cfg2_free_targets(T)
+        c = api.Context(0)
+        try:
+            rid, sid = c.add_robot(wl.robot), c.set_scene(wl.scene)
+            t0, qq, ee, cc = shard.solve_sharded(c, rid, sid, torch.as_tensor(tg, device="cuda"), c.opts(M, k, seed),
+                                                 7, rank, world)
+            torch.cuda.synchronize()
+            q.put((rank, t0, qq.cpu().numpy(), ee.cpu().numpy(), cc.cpu().numpy()))
+        finally:
+            c.close()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.gpu
+def test_sharded_solve_on_two_ranks_matches_the_oracle():
+    """Two processes (gloo ranks; both on the one GPU, their kernels
+    independent) each run PO-CCD on half of every target's seeds, exchange
+    their top-K lists, merge them and polish half of the targets.  Together
+    their results equal the single-device solve bit for bit and solve like
+    the oracle's whole method: success within one point, every solution
+    re-verified by oracle kinematics and brute-force collision."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle as orc
+    from paper_2510_07514_gb300 import api, build
+    build.build()
+    orc.build()
+    T, M, k, seed = 200, 512, 2, 29
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_gpu_worker, args=(r, 2, port, q, T, M, k, seed)) for r in range(2)]
+    for p in ps:
+        p.start()
+    parts = sorted((q.get(timeout=600) for _ in ps), key=lambda x: x[1])
+    for p in ps:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert [x[1] for x in parts] == [0, T // 2]
+    qs = np.concatenate([x[2] for x in parts])
+    es = np.concatenate([x[3] for x in parts])
+    cs = np.concatenate([x[4] for x in parts]).astype(int)
+    wl, tg = _cfg2_free_targets(T)
+    c = api.Context(0)
+    try:
+        rid, sid = c.add_robot(wl.robot), c.set_scene(wl.scene)
+        ref = [x.cpu().numpy() for x in c.solve(rid, sid, torch.as_tensor(tg, device="cuda"), M, k, seed, 7)]
+    finally:
+        c.close()
+    assert np.array_equal(cs, ref[2])
+    for t in range(T):
+        assert np.array_equal(qs[t, :cs[t]], ref[0][t, :cs[t]])
+        assert np.array_equal(es[t, :cs[t]], ref[1][t, :cs[t]])
+    orob, osc = orc.Robot(wl.robot), orc.Scene(wl.scene)
+    tg64 = tg.astype(np.float64)
+    for t in range(T):
+        for r in range(cs[t]):
+            e = orc.residual(orob, qs[t, r].astype(np.float64), tg64[t])
+            assert abs(np.linalg.norm(e[:3]) - es[t, r, 0]) < 1e-5 and abs(np.linalg.norm(e[3:]) - es[t, r, 1]) < 1e-5
+            assert np.all(qs[t, r] >= wl.robot.lo - 1e-7) and np.all(qs[t, r] <= wl.robot.hi + 1e-7)
+        if cs[t]:
+            hit, margin = orc.collide(orob, osc, qs[t, :cs[t]].astype(np.float64))
+            assert not np.any(hit & (margin >= 1e-6))
+    sg = (cs > 0) & (es[:, 0, 0] <= 1e-3) & (es[:, 0, 1] <= 1e-2)
+    o = orc.solve(orob, osc, orc.make_params(1e-3, 1e-2, seed=seed), tg64, M, k)
+    so = (o["count"] > 0) & (o["err"][:, 0, 0] <= 1e-3) & (o["err"][:, 0, 1] <= 1e-2)
+    assert abs(sg.mean() - so.mean()) <= 0.01 + 1e-12, (sg.mean(), so.mean())

@@ -45,6 +45,9 @@ def _same(a, b):
     for t in range(len(ca)):
         assert np.allclose(qa[t, :ca[t]], qb[t, :cb[t]], atol=TOL, rtol=0)
         assert np.allclose(ea[t, :ca[t]], eb[t, :cb[t]], atol=TOL, rtol=0)
+        # rows past the count are NaN on both paths, whatever the buffers held before
+        for x in (qa, ea, qb, eb):
+            assert np.all(np.isnan(x[t, ca[t]:]))
 
 
 def test_noalloc_matches_solve_on_consecutive_calls(setup):
@@ -58,6 +61,20 @@ def test_noalloc_matches_solve_on_consecutive_calls(setup):
         torch.cuda.synchronize()
         _same(ref, got)
         assert got[2].min().item() >= 1
+
+
+def test_noalloc_fills_rows_past_the_count(setup):
+    """Fewer collision-free solutions than top_k (8 seeds, top_k 20): the rows
+    past each target's count read NaN, as hjcd_solve leaves them, on two calls
+    in a row."""
+    ctx, wl, rid, sid, tg = setup
+    n = wl.robot.n
+    for seed in (3, 4):
+        ref = ctx.solve(rid, sid, tg[:16], 8, 20, seed, n)
+        got = _noalloc(ctx, rid, sid, tg[:16], 8, 20, seed, n)
+        torch.cuda.synchronize()
+        _same(ref, got)
+        assert got[2].max().item() < 20
 
 
 def test_noalloc_rejects_work_beyond_its_scratch(setup):
