@@ -59,8 +59,10 @@ def parse():
                     help="also time the main workload with the position-only CCD initialiser (0: skip)")
     ap.add_argument("--tracking-frames", type=int, default=200, help="frames of the tracking loop (0: skip)")
     ap.add_argument("--latency", type=int, default=1, help="single-target latency leg (0: skip)")
-    ap.add_argument("--serve-seconds", type=float, default=4.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the served Poisson trace at 2000 req/s (0: skip the serving comparison)")
+    ap.add_argument("--serve-repeats", type=int, default=3,
+                    help="repeats of the plain path's sweep around the served p99")
     return ap.parse_args()
 
 
@@ -432,12 +434,69 @@ def large_leg(ctx, args, dev, stream):
     ms = e0.elapsed_time(e1) / args.large_steps
     c, e = out[2].cpu().numpy(), out[1].cpu().numpy()
     succ = (c > 0) & (e[:, 0, 0] <= wl.eps_pos) & (e[:, 0, 1] <= wl.eps_ori)
+    # phase split: the same solve in one wave (its whole workspace, about 2.6 GB, fits the device)
+    # with the phases' events recorded; the roofline of its dominant kernel from the work counters
+    hjcd.hjcd_set_profiling(ctx.h, True)
+    ctx.solve(rid, sid, tg, S, K, wl.seed, rob.n, stream=stream, out=out)
+    torch.cuda.synchronize(dev)
+    hjcd.hjcd_counters(ctx.h, reset=True)
+    w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0.record(stream)
+    ctx.solve(rid, sid, tg, S, K, wl.seed, rob.n, stream=stream, out=out)
+    w1.record(stream)
+    torch.cuda.synchronize(dev)
+    ph = np.asarray(hjcd.hjcd_phase_times(ctx.h), dtype=float)
+    cw = hjcd.hjcd_counters(ctx.h, reset=True)
+    names = ["po_ccd", "topk_dup", "pjik", "collide", "rank"]
+    ph_c = ph.copy()
+    ph_c[3] += ph_c[4]  # the ranked collision filter runs in the rank phase
+    ph_c[4] = 0.0
+    n, n_sph = rob.n, len(rob.sph_body)
+    fl = {"po_ccd": cw[0] * flops_ccd_iter(n),
+          "pjik": cw[1] * flops_lm_iter(n) + (cw[2] - cw[1]) * flops_fk_trial(n) + cw[7] * FLOPS_COORD_TRIAL,
+          "collide": cw[3] * FLOPS_SPHERE_TEST + cw[6] * FLOPS_BOX_TEST + cw[4] * flops_collide_cand(n, n_sph)}
+    sm_max = 2070.0
+    props = torch.cuda.get_device_properties(dev)
+    peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    dom = max(fl, key=lambda k: ph_c[names.index(k)])
+    dom_ms = ph_c[names.index(dom)]
+    achieved = fl[dom] / (dom_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_note": f"FP32 CUDA-core peak from unit counts: {props.multi_processor_count} SMs x 128 lanes x 2 "
+                         f"x {sm_max:.0f} MHz",
+            "per_kernel": {k: {"ms": float(ph_c[names.index(k)]), "gflop": fl[k] / 1e9,
+                               "tflops": fl[k] / max(ph_c[names.index(k)] * 1e-3, 1e-12) / 1e12} for k in fl}}
+    # end to end with host buffers (pinned), within the workspace budget (waves), copies inside
+    tg_h = tg.cpu().pin_memory()
+    hout = (torch.empty((T, K, rob.n)).pin_memory(), torch.empty((T, K, 2)).pin_memory(),
+            torch.empty((T,), dtype=torch.int32).pin_memory())
+    hjcd.hjcd_set_memory_budget(ctx.h, budget)
+    try:
+        e2e = []
+        for i in range(2):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            ctx.solve(rid, sid, tg_h, S, K, wl.seed, rob.n, stream=stream, out=hout)
+            e2e.append(time.perf_counter() - t0)
+    finally:
+        hjcd.hjcd_set_memory_budget(ctx.h, 0)
+    e2e_s = min(e2e)
     return {"workload": f"Panda + 60 link spheres, {T} targets x {S} seeds, top-{K}; {len(free)} obstacle spheres "
                         f"(jittered grid carved around the target configurations, uniform grid broadphase)",
             "candidates": T * S, "ms_per_step": ms, "solves_per_s": T / (ms * 1e-3),
             "candidates_per_s": T * S / (ms * 1e-3), "success_rate": float(succ.mean()),
             "mean_solutions_per_target": float(c.mean()), "workspace_budget_bytes": budget,
-            "sphere_tests_per_candidate": cnt[3] / args.large_steps / max(cnt[4] / args.large_steps, 1)}
+            "sphere_tests_per_candidate": cnt[3] / args.large_steps / max(cnt[4] / args.large_steps, 1),
+            "one_wave": {"ms_per_step": w0.elapsed_time(w1),
+                         "phase_ms": {nm: float(v) for nm, v in zip(names + ["step"], ph)},
+                         "work": {"ccd_iters": cw[0], "lm_iters": cw[1], "lm_fk_passes": cw[2],
+                                  "lm_coord_trials": cw[7], "sphere_tests": cw[3], "box_tests": cw[6],
+                                  "collide_candidates": cw[4]}},
+            "roofline": roof,
+            "e2e": {"value": T / e2e_s, "unit": UNIT, "ms_per_step": 1e3 * e2e_s,
+                    "h2d_bytes_per_step": T * 7 * 4, "d2h_bytes_per_step": T * K * (rob.n + 2) * 4 + T * 4,
+                    "note": "host targets and outputs (pinned), waves within the workspace budget"}}
 
 
 def dof_scaling_leg(ctx, args, dev, stream):
@@ -613,10 +672,38 @@ def _serve_run(ctx, reqs, trace, idx, rate_scale, server_kw):
             "success_rate": float(np.mean(np.concatenate(succ))), "all_ok": ok}
 
 
+def _crossing(points, target):
+    """Offered rate (and throughput) where p99 reaches `target` on a sweep of
+    (rate, p99, solves/s) points: log-linear interpolation between the fastest
+    point at or below the target and the next faster one; None when no point
+    meets the target."""
+    pts = sorted(points)
+    ok = [q for q in pts if q[1] <= target]
+    if not ok:
+        return None
+    lo = max(ok)
+    up = [q for q in pts if q[0] > lo[0] and q[1] > target]
+    if not up:
+        return {"rate": lo[0], "solves_per_s": lo[2], "bracketed": False}
+    hi = min(up)
+    f = (target - lo[1]) / (hi[1] - lo[1])
+    rate = float(np.exp(np.log(lo[0]) + f * (np.log(hi[0]) - np.log(lo[0]))))
+    sps = float(np.exp(np.log(lo[2]) + f * (np.log(hi[2]) - np.log(lo[2]))))
+    return {"rate": rate, "solves_per_s": sps, "bracketed": True}
+
+
 def serving_leg(ctx, args, dev):
     """Served (continuous batching) vs plain (one request per launch sequence)
     on the Poisson trace of 1-8 targets x 32-4096 seeds requests for four
-    resident chains, each request with its own 0-500-sphere scene."""
+    resident chains, each request with its own 0-500-sphere scene.
+
+    The served path runs the whole trace at 2000 requests/s.  The plain path is
+    swept: halved rates on short runs until its p99 is no worse than the served
+    p99 (the bracket), then rates 1.25x apart across the bracket with at least
+    2000 requests each, repeated on other stretches of the trace; in each repeat
+    the rate (and throughput) at which the plain p99 equals the served p99 is
+    interpolated, and served/plain solves/s at equal p99 is its ratio.  Both
+    paths are also run at 2x and 4x the offered rate (their ceilings)."""
     import torch
     from paper_2510_07514_gb300 import api, inputs
     chains = inputs.cfg3_chains()
@@ -645,27 +732,52 @@ def serving_leg(ctx, args, dev):
         reqs.append(ctx.batch_item(rids[tp.robot], -1, tg, int(trace.seeds[k]), 1, int(trace.seed[k]), rob.n,
                                    spheres=tp.scene.sph_xyzr, boxes=None, device=torch.device("cpu")))
     idx = np.arange(len(trace.t))
-    served = _serve_run(ctx, reqs, trace, idx, 1.0, dict(max_inflight=3))
-    # plain path: the same requests one launch sequence at a time; slower offered rates until its p99
-    # is no worse than the served p99 (each run on the first requests of the trace, about 1.5 s)
-    plain_runs = []
+    served_kw, plain_kw = dict(max_inflight=3), dict(max_inflight=1, max_batch_requests=1)
+    served = _serve_run(ctx, reqs, trace, idx, 1.0, served_kw)
+    target = served["p99_ms"]
+    # bracket: halved rates, short runs
+    bracket = []
     scale = 1.0
-    for _ in range(7):
-        n_req = int(min(len(idx), max(200, rate * scale * 1.5)))
-        r = _serve_run(ctx, reqs, trace, idx[:n_req], scale, dict(max_inflight=1, max_batch_requests=1))
+    for _ in range(8):
+        n_req = int(min(len(idx), max(600, rate * scale * 1.5)))
+        r = _serve_run(ctx, reqs, trace, idx[:n_req], scale, plain_kw)
         r["rate_scale"] = scale
-        plain_runs.append(r)
-        if r["p99_ms"] <= served["p99_ms"]:
+        bracket.append(r)
+        if r["p99_ms"] <= target:
             break
         scale /= 2.0
-    match = [r for r in plain_runs if r["p99_ms"] <= served["p99_ms"]]
-    ref = max(match, key=lambda r: r["solves_per_s"]) if match else plain_runs[-1]
-    return {"trace": f"Poisson {rate:.0f} req/s for {args.serve_seconds:g} s; 1-8 targets, 32-4096 seeds, "
-                     "4 resident chains (7/12/16/20 DoF), own scene of 0-500 spheres per request",
+    # refine: 1.25x steps across [scale, 2 scale], >= 2000 requests per point, on other stretches
+    repeats = []
+    n_req = int(min(len(idx), max(2000, 2 * rate * scale)))
+    for rep in range(max(1, args.serve_repeats)):
+        start = (rep * n_req) % max(1, len(idx) - n_req)
+        sub = idx[start:start + n_req]
+        pts, runs = [], []
+        for i in range(4):
+            sc = scale * 1.25 ** i
+            r = _serve_run(ctx, reqs, trace, sub, sc, plain_kw)
+            r["rate_scale"] = sc
+            runs.append(r)
+            pts.append((r["offered_req_per_s"], r["p99_ms"], r["solves_per_s"]))
+        cross = _crossing(pts, target)
+        repeats.append({"runs": runs, "crossing": cross,
+                        "served_over_plain": served["solves_per_s"] / cross["solves_per_s"] if cross else None})
+    ratios = [r["served_over_plain"] for r in repeats if r["served_over_plain"]]
+    med = float(np.median(ratios)) if ratios else None
+    # ceilings: both paths at 2x and 4x the offered rate
+    ceilings = {}
+    for mult in (2.0, 4.0):
+        n_c = int(min(len(idx), 2 * rate * mult))
+        ceilings[f"{mult:g}x"] = {
+            "served": _serve_run(ctx, reqs, trace, idx[:n_c], mult, served_kw),
+            "plain": _serve_run(ctx, reqs, trace, idx[:min(n_c, 3000)], mult, plain_kw)}
+    return {"trace": f"Poisson {rate:.0f} req/s for {args.serve_seconds:g} s ({len(idx)} requests); 1-8 targets, "
+                     "32-4096 seeds, 4 resident chains (7/12/16/20 DoF), own scene of 0-500 spheres per request",
             "templates_usable": f"{len(usable)} of {len(tpls)}",
-            "served": served, "plain": plain_runs,
-            "served_over_plain_at_equal_p99": served["solves_per_s"] / ref["solves_per_s"],
-            "plain_reached_served_p99": bool(match)}
+            "served": served, "plain_bracket": bracket, "plain_repeats": repeats,
+            "served_over_plain_at_equal_p99": med,
+            "served_over_plain_spread": (float((max(ratios) - min(ratios)) / med) if ratios else None),
+            "plain_reached_served_p99": bool(ratios), "ceilings": ceilings}
 
 
 def hjcd_arm(args):

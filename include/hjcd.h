@@ -247,7 +247,10 @@ hjcd_status hjcd_autotune(hjcd_ctx* ctx, int n_items, const hjcd_batch_item* ite
  * shards, gathered in any order, are merged by hjcd_topk_merge (input
  * [L][T][K] and [L][T][K][n]; output the K best per target, ties to the lower
  * seed index).  hjcd_solve_from_topk runs the rest of Alg. 2 from the merged
- * joint vectors [T][K][n] (duplication, PJ-IK, collision filter, ranking):
+ * joint vectors [T][K][n] (duplication, PJ-IK, collision filter, ranking)
+ * for targets_pq[0 .. n_targets), which are targets first_target ..
+ * first_target + n_targets - 1 of the request (their indices key the random
+ * streams, so each device may polish any consecutive range of the targets):
  * the results equal hjcd_solve's on the same targets and options, bit for bit.
  * All arrays are DEVICE memory; targets and options must be the same on every
  * device; opts->samples_per_target must be NULL; cd_variant 2 is refused. */
@@ -258,8 +261,9 @@ hjcd_status hjcd_topk_merge(hjcd_ctx* ctx, int n_targets, int n_lists, int K, in
                             const int32_t* in_index, const float* in_theta, float* out_score,
                             int32_t* out_index, float* out_theta, void* stream);
 hjcd_status hjcd_solve_from_topk(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_targets,
-                                 const float* targets_pq, const hjcd_solve_opts* opts, const float* kept_theta,
-                                 float* out_q, float* out_err, int32_t* out_count, void* stream);
+                                 const float* targets_pq, int32_t first_target, const hjcd_solve_opts* opts,
+                                 const float* kept_theta, float* out_q, float* out_err, int32_t* out_count,
+                                 void* stream);
 
 /* ---- serving: continuous batching ------------------------------------------ */
 

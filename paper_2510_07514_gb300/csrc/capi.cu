@@ -1312,8 +1312,9 @@ hjcd_status hjcd_topk_merge(hjcd_ctx* ctx, int n_targets, int n_lists, int K, in
 }
 
 hjcd_status hjcd_solve_from_topk(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_id, int n_targets,
-                                 const float* targets_pq, const hjcd_solve_opts* opts, const float* kept_theta,
-                                 float* out_q, float* out_err, int32_t* out_count, void* stream) {
+                                 const float* targets_pq, int32_t first_target, const hjcd_solve_opts* opts,
+                                 const float* kept_theta, float* out_q, float* out_err, int32_t* out_count,
+                                 void* stream) {
     if (!ctx) return HJCD_EINVAL;
     RobotRec* rob;
     SceneRec* sc;
@@ -1323,6 +1324,7 @@ hjcd_status hjcd_solve_from_topk(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_
     if ((st = shard_common(ctx, robot_id, n_targets, targets_pq, opts, &rob, &P, &K))) return st;
     if ((st = check_scene(ctx, scene_id, &sc))) return st;
     if (opts->top_k < 1 || opts->top_k > HJCD_MAX_TOPK) return fail(ctx, HJCD_EINVAL, "top_k outside [1, %d]", HJCD_MAX_TOPK);
+    if (first_target < 0) return fail(ctx, HJCD_EINVAL, "first_target < 0");
     if (pointer_kind(kept_theta) != 1 || pointer_kind(out_q) != 1 || pointer_kind(out_err) != 1 ||
         pointer_kind(out_count) != 1)
         return fail(ctx, HJCD_EINVAL, "kept_theta and the outputs must be device arrays");
@@ -1348,10 +1350,11 @@ hjcd_status hjcd_solve_from_topk(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_
     HJCD_CUDA(ctx, cudaMemsetAsync(out_q, 0xff, sizeof(float) * (size_t)T * top_k * rob->P.n, s));
     HJCD_CUDA(ctx, cudaMemsetAsync(out_err, 0xff, sizeof(float) * (size_t)T * top_k * 2, s));
     k_uniform_offsets<<<(T + 256) / 256, 256, 0, s>>>(d_boff + T + 1, d_boff, T, B, B);
-    launch_pack_targets(targets_pq, T, nullptr,
-                        stage_template(opts->eps_pos, opts->eps_ori, opts->seed, P.cd_max_iters, P.lm_max_iters,
-                                       top_k, sc ? 0 : -1),
-                        d_tg, s);
+    // each target keeps its index inside the whole request, which keys its random streams
+    TargetDesc tmpl = stage_template(opts->eps_pos, opts->eps_ori, opts->seed, P.cd_max_iters, P.lm_max_iters, top_k,
+                                     sc ? 0 : -1);
+    tmpl.t_local = first_target;
+    launch_pack_targets(targets_pq, T, nullptr, tmpl, d_tg, s);
     const RobotSet rs = single_robot_set(*rob);
     KeptDupArgs da{rs, d_tg, T, (int32_t)K, kept_theta, d_boff, thB, CB, P.dup_sigma};
     launch_dup_kept(da, s);

@@ -349,8 +349,9 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
     return 0;
 }
 
+// 768 threads per SM: the register budget (80) that leaves no spill, for 24 resident warps
 template <bool TRACE, int TH>
-__global__ void __launch_bounds__(TH, 512 / TH) k_ccd(const CcdArgs A) {
+__global__ void __launch_bounds__(TH, 768 / TH) k_ccd(const CcdArgs A) {
     using Col = ColT<TH>;
     extern __shared__ __align__(16) float sm[];
     const RobotParams* rob = stage_robots(sm, A.rs);

@@ -274,8 +274,12 @@ __device__ __noinline__ float coord_cost(const LmW S, int l, float x) {
 // The dogleg step of Eq. dogleg and the single-coordinate step of Eq. single-coord for lane l,
 // from its weighted Jacobian W J (columns in shared memory) and W r: into S.d2, S.sc_j,
 // S.sc_step.  With M0 = (WJ)(WJ)^T the Gauss-Newton step is (WJ)^T y2, y2 = (M0 + reg I)^-1 W r,
-// and the quantities of the dogleg reduce to 6 x 6 forms: J g = M0 W r, |g|^2 = (W r).M0 W r,
-// |d_gn|^2 = y2.M0 y2; one more pass over the columns forms the step.
+// and the Cauchy point's quantities reduce to 6 x 6 forms: J g = M0 W r, |g|^2 = (W r).M0 W r.
+// |d_gn|^2 is summed over the step's components instead of as y2.M0 y2: when M0 is nearly
+// singular y2 is large and that form cancels catastrophically (its binary32 value could fall
+// inside the trust region while the step is far outside).  The first pass over the columns
+// gives |d_gn|^2 and the coefficients of the segment's crossing of the boundary, the second
+// forms the step.
 __device__ __noinline__ void dogleg_prepare(const LmW S, int l, int n, float Rt, float gn_reg) {
     float M0[21], M[21], inv[6], b[6];
 #pragma unroll
@@ -299,29 +303,38 @@ __device__ __noinline__ void dogleg_prepare(const LmW S, int l, int n, float Rt,
     chol6(M, inv);
     float y2[6];
     chol6_solve(M, inv, b, y2);
-    // symmetric products with M0
-    float Jg[6], My[6];
+    // J g = M0 W r
+    float Jg[6];
 #pragma unroll
     for (int r = 0; r < 6; ++r) {
-        float a = 0.0f, c = 0.0f;
+        float a = 0.0f;
 #pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            const float m = r >= q ? M0[tri(r, q)] : M0[tri(q, r)];
-            a = fmaf(m, b[q], a);
-            c = fmaf(m, y2[q], c);
-        }
+        for (int q = 0; q < 6; ++q) a = fmaf(r >= q ? M0[tri(r, q)] : M0[tri(q, r)], b[q], a);
         Jg[r] = a;
-        My[r] = c;
     }
-    float gg = 0.0f, jgjg = 0.0f, ngn2 = 0.0f;
+    float gg = 0.0f, jgjg = 0.0f;
 #pragma unroll
     for (int r = 0; r < 6; ++r) {
         gg = fmaf(b[r], Jg[r], gg);
         jgjg = fmaf(Jg[r], Jg[r], jgjg);
-        ngn2 = fmaf(y2[r], My[r], ngn2);
     }
     const float ac = jgjg > 0.0f ? __fdividef(gg, jgjg) : 0.0f;
     const float ngd2 = ac * ac * gg, R2 = Rt * Rt;
+    // |d_gn|^2 and, for the segment from d_gn to the Cauchy point, |d_cp - d_gn|^2 and 2 d_gn.(d_cp - d_gn)
+    float ngn2 = 0.0f, qa = 0.0f, qb = 0.0f;
+#pragma unroll 1
+    for (int i = 0; i < n; ++i) {
+        float dgn = 0.0f, g = 0.0f;
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            dgn = fmaf(S.jw(r, i, l), y2[r], dgn);
+            g = fmaf(S.jw(r, i, l), b[r], g);
+        }
+        const float di = fmaf(ac, g, -dgn);
+        ngn2 = fmaf(dgn, dgn, ngn2);
+        qa = fmaf(di, di, qa);
+        qb = fmaf(2.0f * dgn, di, qb);
+    }
     float wgn = 1.0f, wgd = 0.0f;  // step = wgn * dgn + wgd * g
     if (ngn2 <= R2) {
         wgn = 1.0f;
@@ -330,23 +343,10 @@ __device__ __noinline__ void dogleg_prepare(const LmW S, int l, int n, float Rt,
         wgn = 0.0f;
         wgd = ngd2 > 0.0f ? Rt * rsqrtf(ngd2) * ac : 0.0f;
     } else {
-        // the point of the segment from the Cauchy point to the Gauss-Newton step on the boundary
-        float qa = 0.0f, qb = 0.0f;
-#pragma unroll 1
-        for (int i = 0; i < n; ++i) {
-            float dgn = 0.0f, g = 0.0f;
-#pragma unroll
-            for (int r = 0; r < 6; ++r) {
-                dgn = fmaf(S.jw(r, i, l), y2[r], dgn);
-                g = fmaf(S.jw(r, i, l), b[r], g);
-            }
-            const float di = fmaf(ac, g, -dgn);
-            qa = fmaf(di, di, qa);
-            qb = fmaf(2.0f * dgn, di, qb);
-        }
+        // the point of the segment from the Gauss-Newton step to the Cauchy point on the boundary
         const float qc = ngn2 - R2;
         const float disc = fmaxf(fmaf(qb, qb, -4.0f * qa * qc), 0.0f);
-        const float tau = (2.0f * qc) / (sqrtf(disc) - qb);  // smaller root, stable form
+        const float tau = (2.0f * qc) / (sqrtf(disc) - qb);  // smaller root, stable form (qb < 0 here)
         wgn = 1.0f - tau;
         wgd = tau * ac;
     }

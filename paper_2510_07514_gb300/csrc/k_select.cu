@@ -186,7 +186,7 @@ __global__ void k_pack_targets(const float* pq7, int T, const TargetDesc* meta, 
         d = meta[t];
     } else {
         d = tmpl;
-        d.t_local = t;
+        d.t_local = tmpl.t_local + t;  // the template holds the index of the first target
     }
     d.p[0] = s[0];
     d.p[1] = s[1];

@@ -129,7 +129,7 @@ _SIGS = {
     "hjcd_scene_contacts": (_ST, [_V, _I32, _I32, _I64, _V, _I64, _V, _V]),
     "hjcd_shard_topk": (_ST, [_V, _I32, _I, _V, ct.POINTER(hjcd_solve_opts), _I32, _I32, _V, _V, _V, _V]),
     "hjcd_topk_merge": (_ST, [_V, _I, _I, _I, _I, _V, _V, _V, _V, _V, _V, _V]),
-    "hjcd_solve_from_topk": (_ST, [_V, _I32, _I32, _I, _V, ct.POINTER(hjcd_solve_opts), _V, _V, _V, _V, _V]),
+    "hjcd_solve_from_topk": (_ST, [_V, _I32, _I32, _I, _V, _I32, ct.POINTER(hjcd_solve_opts), _V, _V, _V, _V, _V]),
     "hjcd_autotune": (_ST, [_V, _I, ct.POINTER(hjcd_batch_item), ct.POINTER(hjcd_params), _F, _I32,
                             ct.POINTER(hjcd_params), ct.POINTER(hjcd_tune_report)]),
     "hjcd_graph_create": (_ST, [_V, _I, ct.POINTER(hjcd_batch_item), ct.POINTER(hjcd_params), ct.POINTER(_V)]),
@@ -300,11 +300,11 @@ def hjcd_topk_merge(ctx, n_targets, n_lists, K, n, in_score, in_index, in_theta,
                                        stream_handle(stream)))
 
 
-def hjcd_solve_from_topk(ctx, robot_id, scene_id, n_targets, targets_pq, opts, kept_theta, out_q, out_err,
-                         out_count, stream=None) -> None:
+def hjcd_solve_from_topk(ctx, robot_id, scene_id, n_targets, targets_pq, first_target, opts, kept_theta, out_q,
+                         out_err, out_count, stream=None) -> None:
     _check(ctx, load().hjcd_solve_from_topk(ctx, int(robot_id), int(scene_id), int(n_targets), ptr(targets_pq),
-                                            ct.byref(opts), ptr(kept_theta), ptr(out_q), ptr(out_err),
-                                            ptr(out_count), stream_handle(stream)))
+                                            int(first_target), ct.byref(opts), ptr(kept_theta), ptr(out_q),
+                                            ptr(out_err), ptr(out_count), stream_handle(stream)))
 
 
 def hjcd_set_collision_mode(ctx, mode: int) -> None:

@@ -71,6 +71,6 @@ def solve_sharded(ctx, robot_id: int, scene_id: int, targets: torch.Tensor, opts
     e = torch.empty((t1 - t0, k, 2), dtype=torch.float32, device=dev)
     c = torch.empty((t1 - t0,), dtype=torch.int32, device=dev)
     if t1 > t0:
-        hjcd.hjcd_solve_from_topk(ctx.h, robot_id, scene_id, t1 - t0, targets[t0:t1].contiguous(), opts,
+        hjcd.hjcd_solve_from_topk(ctx.h, robot_id, scene_id, t1 - t0, targets[t0:t1].contiguous(), t0, opts,
                                   mt[t0:t1].contiguous(), q, e, c, stream)
     return t0, q, e, c

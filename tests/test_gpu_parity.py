@@ -361,18 +361,35 @@ def test_lm_iteration_trace_parity(ctx, which):
     assert set(np.unique(o["branch"][robust])) >= {0}
 
 
-def _cond_gn(J, W, mu):
-    """Condition number of the dogleg's 6x6 Gauss-Newton system
-    (WJ)(WJ)^T + mu I after diagonal equilibration."""
-    Jw = W[:, None] * J
-    M = Jw @ Jw.T + mu * np.eye(6)
-    s = 1 / np.sqrt(np.diag(M))
-    ev = np.linalg.eigvalsh(M * s[:, None] * s[None, :])
-    return ev[-1] / max(ev[0], 1e-300)
+def _dogleg_sensitivity(J, e, wo, R, mu, reach_m, rng, ulps):
+    """How far the dogleg step of Eq. dogleg moves when its inputs carry the
+    errors of binary32 kinematics: absolute errors of `ulps` u reach on the
+    Jacobian's position rows and the position residual, `ulps` u on its axis
+    rows and the orientation residual (u = 2^-24), with W recomputed from the
+    perturbed Jacobian; the largest change of the oracle's step over eight
+    random perturbations.  The step is continuous but not Lipschitz where the
+    dogleg segment touches the trust-region sphere (the boundary point moves
+    like the square root of the input error) and it amplifies errors by the
+    condition of the Gauss-Newton system, so no fixed tolerance fits every
+    candidate."""
+    u = 2.0 ** -24
+    scale = np.array([reach_m] * 3 + [1.0] * 3) * ulps * u
+    wc = np.array([1.0, 1.0, 1.0, wo, wo, wo])
+
+    def step(J_, e_):
+        W = wc / np.maximum(np.linalg.norm(J_, axis=1), 1e-6)
+        return orc.dogleg_step(W[:, None] * J_, W * e_, R, mu)
+
+    d0 = step(J, e)
+    worst = 0.0
+    for _ in range(8):
+        d1 = step(J + scale[:, None] * rng.standard_normal(J.shape), e + scale * rng.standard_normal(6))
+        worst = max(worst, float(np.max(np.abs(d1 - d0))))
+    return worst
 
 
-@pytest.mark.parametrize("which", ["panda", "chain12", "chain20", "chain24"])
-def test_lm_fallback_branch_trace_parity(ctx, which):
+@pytest.mark.parametrize("which,A", [("panda", 4), ("chain12", 4), ("chain20", 1), ("chain24", 0)])
+def test_lm_fallback_branch_trace_parity(ctx, which, A):
     """Alg. 4's failure path, branch by branch.  Inputs: candidates after 10
     oracle PJ-IK iterations from uniform seeds, where a third or more of the
     iterations fail the full step.  Where the full step failed on the GPU the
@@ -381,53 +398,68 @@ def test_lm_fallback_branch_trace_parity(ctx, which):
     the oracle's decisions are clear so are the branch, the accepted alpha
     and the new theta.  The dogleg (branch 1) and the single coordinate
     (branch 2) must both occur among the compared candidates (the
-    perturbation, branch 3, has its own forced case below)."""
+    perturbation, branch 3, has its own forced case below); the longer chains
+    fail the full step less often, so they run with a shallower line search
+    (depth A) to reach the fallbacks."""
     rob = dict(robots())[which]
     rid = ctx.add_robot(rob)
     orob = orc.Robot(rob)
     rng = np.random.default_rng(61)
-    T, C, k, seed = 11, 1031, 10, 5
+    T, C, k, seed = 11, 4099, 10, 5
     tg = f32(orc.pose(orob, f32(rng.uniform(rob.lo, rob.hi, (T, rob.n)))))
     tgt = rng.integers(0, T, C).astype(np.int32)
     cand = np.arange(C).astype(np.int32)
-    P64 = orc.make_params(seed=seed, lm_max_iters=k)
+    P64 = orc.make_params(seed=seed, lm_max_iters=k, lm_A=A)
     th = f32(orc.pjik(orob, P64, tg, tgt, cand, rng.uniform(rob.lo, rob.hi, (C, rob.n)))["theta"])
-    g = _lm_gpu(ctx, rid, rob.n, tg, tgt, cand, th, k, api.make_params(), seed)
+    g = _lm_gpu(ctx, rid, rob.n, tg, tgt, cand, th, k, api.make_params(lm_A=A), seed)
     o = orc.lm_iteration(orob, P64, tg, tgt, cand, k, th)
     tol = TOL * max(1.0, reach(rob) / 1.5)
     u = 2.0 ** -24
     fell = g["sc_joint"] >= 0                     # the GPU took the failure path
     assert np.array_equal(fell, (g["branch"] != 0) | (g["alpha"] < 1))
-    assert fell.mean() > 0.2
+    assert fell.sum() > 100
     cond_lm = np.array([_cond(o["J"][c], o["W"][c], P64.lm_lambda) for c in range(C)])
-    cond_gn = np.array([_cond_gn(o["J"][c], o["W"][c], P64.lm_gn_reg) for c in range(C)])
-    # dogleg step: 1e-5 where the 6x6 solve is well conditioned, else the derived bound
+    res = np.array([orc.residual(orob, th[c], tg[tgt[c]]) for c in range(C)])
+    Jw = o["W"][:, :, None] * o["J"]
+    bw = o["W"] * res
+    # dogleg step: 1e-5 where it moves less than a third of that under 16-ulp input errors,
+    # everywhere the tolerance plus twenty times that movement (the device's own binary32
+    # solve and sums add errors of their own beyond those of its inputs)
+    sens = np.zeros(C)
+    srng = np.random.default_rng(62)
+    for c in np.nonzero(fell)[0]:
+        sens[c] = _dogleg_sensitivity(o["J"][c], res[c], P64.eps_pos / P64.eps_ori, P64.lm_trust_R,
+                                      P64.lm_gn_reg, max(1.0, reach(rob)), srng, 16)
     ddog_err = np.max(np.abs(g["d_dog"] - o["d_dog"]), axis=1)
-    ddog_bound = tol + 8 * cond_gn * u * np.max(np.abs(o["d_dog"]), axis=1)
-    assert np.all(ddog_err[fell] < ddog_bound[fell])
-    well_gn = fell & (cond_gn < 100)
-    assert well_gn.sum() > 20
-    assert np.max(ddog_err[well_gn]) < tol
+    assert np.all(ddog_err[fell] < (tol + 20 * sens)[fell])
+    steady = fell & (sens < 0.3 * tol)
+    assert steady.sum() > 25
+    assert np.max(ddog_err[steady]) < tol
+    # the device's steps stay in the trust region, up to the rounding of the boundary point (a
+    # binary32 |d_gn|^2 taken as the 6x6 form y2.M0 y2 once let Gauss-Newton steps of norm 2.7
+    # through with R = 0.3)
+    assert np.all(np.linalg.norm(g["d_dog"][fell], axis=1) <= P64.lm_trust_R * 1.01)
     # single coordinate: the joint wherever the largest |g_i| is clear, the step on that joint
-    gr = np.einsum("cri,cr->ci", o["W"][:, :, None] * o["J"], o["W"] * np.array(
-        [orc.residual(orob, th[c], tg[tgt[c]]) for c in range(C)]))
+    gr = np.einsum("cri,cr->ci", Jw, bw)
     ag = np.sort(np.abs(gr), axis=1)
     clear = fell & ((ag[:, -1] - ag[:, -2]) > 1e-4 * ag[:, -1])
-    assert clear.sum() > 20
+    assert clear.sum() > 50
     assert np.array_equal(g["sc_joint"][clear], o["sc_joint"][clear])
     # the 1-D step g_i / |(WJ)_i|^2: its rounding grows with the cancellation in g_i
-    Jw = o["W"][:, :, None] * o["J"]
     i_s = o["sc_joint"]
-    canc = np.array([np.sum(np.abs(Jw[c, :, i_s[c]] * o["W"][c] * orc.residual(orob, th[c], tg[tgt[c]])))
-                     / max(abs(gr[c, i_s[c]]), 1e-300) for c in range(C)])
+    canc = np.array([np.sum(np.abs(Jw[c, :, i_s[c]] * bw[c])) / max(abs(gr[c, i_s[c]]), 1e-300) for c in range(C)])
     sc_bound = tol + 16 * canc * u * np.abs(o["sc_step"])
     assert np.all(np.abs(g["sc_step"] - o["sc_step"])[clear] < sc_bound[clear])
-    # decisions where the oracle's cost comparisons are clear and every step is accurate
-    robust = fell & clear & (cond_lm < 100) & (cond_gn < 100) & (o["ls_margin"] > 1e-4)
+    # decisions where the oracle's cost comparisons are clear (relative margin 1e-4) and the
+    # steps they compare are known well: the LM step well conditioned, the dogleg step within
+    # 1e-3; the new theta within the tolerance of the step taken
+    ddog_bound = tol + 20 * sens
+    robust = fell & clear & (cond_lm < 100) & (ddog_bound < 1e-3) & (o["ls_margin"] > 1e-4)
     assert np.array_equal(g["branch"][robust], o["branch"][robust])
     assert np.array_equal(g["alpha"][robust], o["alpha"][robust].astype(np.float32).astype(np.float64))
-    moved = robust & (o["branch"] < 3)
-    assert np.max(np.abs(g["theta"] - o["theta"])[moved]) < tol
+    dth = np.max(np.abs(g["theta"] - o["theta"]), axis=1)
+    assert np.all(dth[robust & ((o["branch"] == 0) | (o["branch"] == 2))] < tol)
+    assert np.all(dth[robust & (o["branch"] == 1)] < ddog_bound[robust & (o["branch"] == 1)])
     br = set(np.unique(o["branch"][robust]))
     assert {1, 2} <= br, br
 

@@ -36,7 +36,8 @@ def test_staging_wait_that_runs_out_is_reported_and_the_context_recovers(ctx):
     sid = ctx.set_scene(inputs.random_scene(rng, 200, 20))
     orob = orc.Robot(rob)
     tg = np.asarray(orc.pose(orob, rng.uniform(rob.lo, rob.hi, (8, 7))), np.float32)
-    th = torch.tensor(rng.uniform(rob.lo, rob.hi, (7, 512)), dtype=torch.float32, device="cuda")
+    th = torch.tensor(np.ascontiguousarray(rng.uniform(rob.lo, rob.hi, (512, 7)).T), dtype=torch.float32,
+                      device="cuda")
     hit = torch.zeros((512,), dtype=torch.uint8, device="cuda")
     hjcd.hjcd_counters(ctx.h, reset=True)
 

@@ -102,7 +102,7 @@ def test_sharded_seeds_equal_the_single_device_solve():
         q = torch.empty((40, k, 7), device="cuda")
         e = torch.empty((40, k, 2), device="cuda")
         cn = torch.empty((40,), dtype=torch.int32, device="cuda")
-        hjcd.hjcd_solve_from_topk(c.h, rid, sid, 40, tg, o, mt, q, e, cn)
+        hjcd.hjcd_solve_from_topk(c.h, rid, sid, 40, tg, 0, o, mt, q, e, cn)
         torch.cuda.synchronize()
         a = [x.cpu().numpy() for x in ref]
         b = [x.cpu().numpy() for x in (q, e, cn)]
@@ -116,6 +116,15 @@ def test_sharded_seeds_equal_the_single_device_solve():
         # and through the per-rank helper with one rank
         t0, q1, e1, c1 = shard.solve_sharded(c, rid, sid, tg, o, 7, 0, 1)
         assert t0 == 0 and np.array_equal(c1.cpu().numpy(), a[2])
+        # a later range of the targets polished on its own keeps its targets' streams
+        q2 = torch.empty((15, k, 7), device="cuda")
+        e2 = torch.empty((15, k, 2), device="cuda")
+        c2 = torch.empty((15,), dtype=torch.int32, device="cuda")
+        hjcd.hjcd_solve_from_topk(c.h, rid, sid, 15, tg[25:].contiguous(), 25, o, mt[25:].contiguous(), q2, e2, c2)
+        torch.cuda.synchronize()
+        assert np.array_equal(c2.cpu().numpy(), a[2][25:])
+        for t in range(15):
+            assert np.array_equal(q2.cpu().numpy()[t, :a[2][25 + t]], a[0][25 + t, :a[2][25 + t]])
     finally:
         c.close()
 
