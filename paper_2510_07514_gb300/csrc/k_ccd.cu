@@ -349,9 +349,13 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
     return 0;
 }
 
-// 768 threads per SM: the register budget (80) that leaves no spill, for 24 resident warps
+// resident threads per SM the register allocation aims at: 768 gives 80 registers, the budget
+// that leaves no spill, for 24 resident warps
+#ifndef HJCD_CCD_THREADS_PER_SM
+#define HJCD_CCD_THREADS_PER_SM 768
+#endif
 template <bool TRACE, int TH>
-__global__ void __launch_bounds__(TH, 768 / TH) k_ccd(const CcdArgs A) {
+__global__ void __launch_bounds__(TH, HJCD_CCD_THREADS_PER_SM / TH) k_ccd(const CcdArgs A) {
     using Col = ColT<TH>;
     extern __shared__ __align__(16) float sm[];
     const RobotParams* rob = stage_robots(sm, A.rs);
