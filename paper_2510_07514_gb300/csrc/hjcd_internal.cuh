@@ -149,6 +149,21 @@ struct CandMap {
     }
 };
 
+// Copy joint vector c (structure of arrays, src[j * ld + c], j < n) into dst(j), K loads in
+// flight at a time: a rolled loop would wait out one global-memory latency per joint.
+template <int K, class Dst>
+__device__ __forceinline__ void load_joints(const float* src, int64_t ld, int64_t c, int n, Dst dst) {
+#pragma unroll 1
+    for (int j0 = 0; j0 < n; j0 += K) {
+        float v[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) v[q] = j0 + q < n ? src[(int64_t)(j0 + q) * ld + c] : 0.0f;
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+            if (j0 + q < n) dst(j0 + q, v[q]);
+    }
+}
+
 // Device work counters (see hjcd_counters).
 struct Counters {
     unsigned long long v[8];

@@ -423,9 +423,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                     cap = A.n_iters >= 0 ? A.n_iters : T.lm_iters;
                     if (T.eps_pos > 0.0f) {
                         has = true;
-                        const int nl = rob[T.robot].n;
-#pragma unroll 1
-                        for (int j = 0; j < nl; ++j) S.th(j, lane) = A.th[j * A.ld + c];
+                        load_joints<8>(A.th, A.ld, c, rob[T.robot].n, [&](int j, float v) { S.th(j, lane) = v; });
                     } else {  // invalid target: no iterations, infinite score
                         if (A.score) A.score[c] = __int_as_float(0x7f800000);
                         if (A.perr) A.perr[c] = 0.0f;
