@@ -893,6 +893,11 @@ def hjcd_arm(args):
     ffma = hjcd.hjcd_ffma_probe(ctx.h, 2048, stream)
     # the same against the FP32 rate an FFMA loop measures on this GPU in this run (of measured)
     roof["frac_of_measured_ffma"] = achieved / ffma if ffma > 0 else None
+    # and by the coarser pre-implementation estimate of a PO-CCD iteration, 210 n flops (FK 90 n and
+    # 2n trials of about 60 flops), which leaves out part of what each trial computes
+    if dom_name == "po_ccd":
+        ach_s = cnt[0] / steps * 210 * n / (dom_ms * 1e-3) / 1e12
+        roof["by_coarse_count"] = {"flop_per_iter": 210 * n, "achieved": ach_s, "frac": ach_s / peak}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
