@@ -160,3 +160,25 @@ def test_device_ccd_constants():
     scalar = re.findall(coef, inc[inc.index("float atan01(float t)"):inc.index("float atan2_q1(")])
     packed = re.findall(coef, ccd[ccd.index("float2 atan_poly2(float2 t)"):ccd.index("float2 quat_angle2(")])
     assert len(scalar) == 8 and packed == scalar
+
+
+def test_serving_crossing_interpolation():
+    """The bench's equal-p99 crossing: log-linear between the fastest point at
+    or below the target p99 and the next faster one; unbracketed and
+    unreachable sweeps reported as such."""
+    import bench
+    pts = [(100.0, 1.5, 400.0), (125.0, 1.7, 500.0), (156.0, 1.9, 625.0), (195.0, 2.4, 780.0)]
+    r = bench._crossing(pts, 1.8)
+    assert r["bracketed"]
+    f = (1.8 - 1.7) / (1.9 - 1.7)
+    assert r["rate"] == pytest.approx(np.exp(np.log(125.0) + f * np.log(156.0 / 125.0)), rel=1e-12)
+    assert r["solves_per_s"] == pytest.approx(np.exp(np.log(500.0) + f * np.log(625.0 / 500.0)), rel=1e-12)
+    assert 125.0 < r["rate"] < 156.0
+    # every point meets the target: the fastest one, not bracketed
+    r = bench._crossing(pts, 3.0)
+    assert not r["bracketed"] and r["rate"] == 195.0
+    # no point meets it
+    assert bench._crossing(pts, 1.0) is None
+    # a non-monotone sweep: the fastest point at or below the target decides
+    r = bench._crossing([(100.0, 1.5, 1.0), (125.0, 1.9, 1.2), (156.0, 1.7, 1.5), (195.0, 2.5, 2.0)], 1.8)
+    assert r["bracketed"] and 156.0 < r["rate"] < 195.0
