@@ -14,6 +14,20 @@ from paper_2510_07514_gb300 import api, build, hjcd, inputs
 pytestmark = pytest.mark.gpu
 
 
+def ranked_order_ok(err, eps_pos, eps_ori):
+    """Rows of one target in the order of Alg. 2's final step (reading c20):
+    those within the tolerances first, each group by non-decreasing score."""
+    conv = (err[:, 0] <= eps_pos) & (err[:, 1] <= eps_ori)
+    if np.any(np.diff(conv.astype(int)) > 0):
+        return False
+    s = err[:, 0] ** 2 / eps_pos ** 2 + err[:, 1] ** 2 / eps_ori ** 2
+    for grp in (conv, ~conv):
+        g = s[grp]
+        if np.any(np.diff(g) < -1e-3 * np.maximum(g[1:], 1e-6)):
+            return False
+    return True
+
+
 @pytest.fixture(scope="module")
 def ctx():
     if not torch.cuda.is_available():
@@ -184,8 +198,7 @@ def test_large_workload_shape_matches_the_oracle(ctx):
         if c[t]:
             h, m = orc.collide(orob, osc, q[t, :c[t]])
             assert not np.any(h & (m >= 1e-6))
-            s = e[t, :c[t], 0] ** 2 / 1e-6 + e[t, :c[t], 1] ** 2 / 1e-4
-            assert np.all(np.diff(s) >= -1e-3 * np.maximum(s[1:], 1e-6))
+            assert ranked_order_ok(e[t, :c[t]], 1e-3, 1e-2), t
         succ[t] = c[t] > 0 and e[t, 0, 0] <= 1e-3 and e[t, 0, 1] <= 1e-2
     o = orc.solve(orob, osc, orc.make_params(1e-3, 1e-2, seed=wl.seed), tg, 256, 16)
     so = (o["count"] > 0) & (o["err"][:, 0, 0] <= 1e-3) & (o["err"][:, 0, 1] <= 1e-2)

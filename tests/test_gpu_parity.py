@@ -23,6 +23,20 @@ from paper_2510_07514_gb300 import api, build, hjcd, inputs
 
 pytestmark = pytest.mark.gpu
 
+
+def ranked_order_ok(err, eps_pos, eps_ori):
+    """Rows of one target in the order of Alg. 2's final step (reading c20):
+    those within the tolerances first, each group by non-decreasing score."""
+    conv = (err[:, 0] <= eps_pos) & (err[:, 1] <= eps_ori)
+    if np.any(np.diff(conv.astype(int)) > 0):
+        return False
+    s = err[:, 0] ** 2 / eps_pos ** 2 + err[:, 1] ** 2 / eps_ori ** 2
+    for grp in (conv, ~conv):
+        g = s[grp]
+        if np.any(np.diff(g) < -1e-3 * np.maximum(g[1:], 1e-6)):
+            return False
+    return True
+
 TOL = 1e-5
 MARGIN = 1e-5
 
@@ -787,8 +801,7 @@ def test_solve_full_size_sampled_verification(ctx):
     assert succ.mean() > 0.8
     # ranking invariants over all targets
     for t in range(wl.n_targets):
-        s = err[t, :cnt[t], 0] ** 2 / 1e-6 + err[t, :cnt[t], 1] ** 2 / 1e-4
-        assert np.all(np.diff(s) >= -1e-3 * np.maximum(s[1:], 1e-6))
+        assert ranked_order_ok(err[t, :cnt[t]], wl.eps_pos, wl.eps_ori), t
 
 
 # ----------------------------------------------------------------------------
