@@ -494,9 +494,9 @@ hjcd_status hjcd_philox(hjcd_ctx* ctx, int64_t n_blocks, const uint32_t* ctr, ui
 
 /* Polls of the collision kernels' first wait for their bulk-copied obstacle
  * tables, for later launches of the context's hjcd_collide, hjcd_solve,
- * hjcd_solve_batch, hjcd_solve_from_topk, graph and serving calls (polls < 0:
- * the default 2^22, far longer than any copy takes; hjcd_solve_noalloc always
- * takes the default).  0 makes that wait run out at once, which
+ * hjcd_solve_batch, graph and serving calls (polls < 0: the default 2^22, far
+ * longer than any copy takes; hjcd_solve_noalloc and hjcd_solve_from_topk
+ * always take the default).  0 makes that wait run out at once, which
  * exercises the timeout path (Sec. V-C has none; a bounded wait is this
  * library's): the kernel sets its error flag, waits for its copy to land with
  * the full limit, returns without verdicts, and the call reports

@@ -1376,6 +1376,9 @@ hjcd_status hjcd_solve_from_topk(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_
     launch_lm(la, false, s);
     const bool collide = rob->P.n_sph > 0;
     if (collide) {
+        // a collision CTA whose staging wait runs out returns without verdicts (this call does not
+        // report it): its candidates then count as colliding instead of keeping stale verdicts
+        HJCD_CUDA(ctx, cudaMemsetAsync(hB, 1, (size_t)CB, s));
         CollideArgs cl{};
         collide_uniform(cl, *rob, sc);
         cl.tg = d_tg;
@@ -1386,7 +1389,6 @@ hjcd_status hjcd_solve_from_topk(hjcd_ctx* ctx, int32_t robot_id, int32_t scene_
         cl.hit = hB;
         cl.cnt = ctx->cnt;
         cl.err_flag = reinterpret_cast<int32_t*>(queue + 1);
-        cl.first_wait_polls = ctx->first_wait_polls.load();
         launch_collide(cl, s);
     }
     RankArgs ra{rs, d_tg, T, d_boff, thB, CB, sB, pB, oB, collide ? hB : nullptr, top_k, nullptr,
