@@ -96,29 +96,38 @@ __device__ __forceinline__ float2 quat_angle2(float2 w, float2 vv) {
     return make_float2(yx > xx ? r.x : a.x, yy > xy ? r.y : a.y);
 }
 
+// Both residual parts of a trial in closed form.  With r = p_t - p_ee, split along z and the
+// plane normal to it, the rotated end effector leaves the axial part r.z and, in the plane,
+// v_p - cos x u_p - sin x (z x u_p); u_p and z x u_p are orthogonal with equal norms, so the
+// in-plane part squared is ((u_p.v_p - cos x |u_p|^2)^2 + ((z x u_p).v_p - sin x |u_p|^2)^2) / |u_p|^2.
+// The error quaternion's vector part, split the same way into a_z z + q_perp, becomes
+// (cos a_z - sin w) z + cos q_perp - sin (q_perp x z), of squared norm (cos a_z - sin w)^2 + |q_perp|^2
+// (cos, sin of x/2).  The only differences are those that form the residual's own components, as
+// in the direct evaluation, and the squares are summed, so the closed form is as accurate (a float32
+// emulation against the float64 method agrees to 2e-7 on Panda).
 __device__ __forceinline__ CcdTrials ccd_joint_trials(const V3 pj, const V3 z, float thj, float lo, float hi,
-                                                      const V3 Ep, const V3 pt, const Q4 qerr, float phi,
-                                                      float delta_k, float pe2, float inv_p2, float inv_o2) {
+                                                      const V3 Ep, const V3 pt, const Q4 qerr, float nqw,
+                                                      float dphi, float pe2, float inv_p2, float inv_o2) {
     CcdTrials o;
     const V3 u = Ep - pj;
     const V3 v = pt - pj;
     const float uz = dot(u, z), vz = dot(v, z);
     const V3 up = fma3(-uz, z, u);
     const V3 vp = fma3(-vz, z, v);
-    const float nu2 = dot(u, u), nv2 = dot(v, v);
     const float nup2 = dot(up, up), nvp2 = dot(vp, vp);
+    const float nu2 = fmaf(uz, uz, nup2), nv2 = fmaf(vz, vz, nvp2);
     const V3 zxu = cross(z, up);
-    const V3 r0 = fma3(vz - uz, z, vp);
+    const float ez = vz - uz;
     const float az = dot(qerr.v, z);
-    const V3 qz = fma3(qerr.w, z, cross(qerr.v, z));
+    const V3 qp = fma3(-az, z, qerr.v);
+    const float qp2 = dot(qp, qp);
 
     // Eq. theta_proj, signed about the axis: atan2(z.(up x vp), up.vp) = atan2(zxu.vp, up.vp)
     const float cs = dot(up, vp), sn = dot(zxu, vp);
     const bool deg = nu2 < 1e-24f || nv2 < 1e-24f || nup2 <= pe2 * nu2 || nvp2 <= pe2 * nv2;
     const float d = deg ? 0.0f : atan2_all(sn, cs);
     // Eq. ori_update: delta(k) sgn(a.z) phi
-    const float sg = (az > 0.0f) ? 1.0f : ((az < 0.0f) ? -1.0f : 0.0f);
-    const float dq = delta_k * sg * phi;
+    const float dq = (az > 0.0f) ? dphi : ((az < 0.0f) ? -dphi : 0.0f);
 
     // both steps clamped to the limits
     float2 st = add2(bc2(thj), make_float2(d, dq));
@@ -133,19 +142,23 @@ __device__ __forceinline__ CcdTrials ccd_joint_trials(const V3 pj, const V3 z, f
     const float2 m2sh = mul2(bc2(-2.0f), sh);
     const float2 msn = mul2(m2sh, ch);             // -sin(step)
     const float2 cst = fma2(m2sh, sh, bc2(1.0f));  // cos(step)
-    // position residual of each trial
-    const V3 rp = fma3(msn.x, zxu, fma3(-cst.x, up, r0));
-    const V3 rq = fma3(msn.y, zxu, fma3(-cst.y, up, r0));
-    float2 r2 = mul2(make_float2(rp.z, rq.z), make_float2(rp.z, rq.z));
-    r2 = fma2(make_float2(rp.y, rq.y), make_float2(rp.y, rq.y), r2);
-    r2 = fma2(make_float2(rp.x, rq.x), make_float2(rp.x, rq.x), r2);
+    // position residual of each trial.  Where u_p is at the rounding level of u (the end effector
+    // on the axis, as the flange on a last joint's axis) its direction is noise that leaves the
+    // plane, and the quotient would drop part of v_p; there the expanded form
+    // |v_p|^2 + |u_p|^2 - 2 (cos u_p.v_p + sin (z x u_p).v_p), which cannot cancel while
+    // |u_p| << |u|, is taken instead.
+    float2 r2;
+    if (nup2 <= 1e-6f * nu2) {
+        r2 = fma2(bc2(2.0f), fma2(msn, bc2(sn), mul2(cst, bc2(-cs))), bc2(fmaf(ez, ez, nvp2 + nup2)));
+    } else {
+        const float2 ex = fma2(cst, bc2(-nup2), bc2(cs));
+        const float2 ey = fma2(msn, bc2(nup2), bc2(sn));
+        r2 = fma2(fma2(ex, ex, mul2(ey, ey)), bc2(__fdividef(1.0f, nup2)), bc2(ez * ez));
+    }
     // error quaternion of each trial: qerr [cos, -sin z]
     const float2 w2 = fma2(bc2(qerr.w), ch, mul2(sh, bc2(az)));
-    const float2 nsh = mul2(bc2(-1.0f), sh);
-    const float2 vx = fma2(ch, bc2(qerr.v.x), mul2(nsh, bc2(qz.x)));
-    const float2 vy = fma2(ch, bc2(qerr.v.y), mul2(nsh, bc2(qz.y)));
-    const float2 vz2 = fma2(ch, bc2(qerr.v.z), mul2(nsh, bc2(qz.z)));
-    const float2 vv = fma2(vx, vx, fma2(vy, vy, mul2(vz2, vz2)));
+    const float2 tz = fma2(ch, bc2(az), mul2(sh, bc2(nqw)));
+    const float2 vv = fma2(tz, tz, bc2(qp2));
     const float2 ang = quat_angle2(w2, vv);
     const float2 sc = fma2(r2, bc2(inv_p2), mul2(mul2(ang, ang), bc2(inv_o2)));
     o.rp2 = r2.x;
@@ -234,14 +247,14 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
     // choice only when its score is lower by more than the fraction cd_tie
     float best_p = 0.0f, dP = 0.0f, best_o = 0.0f, dO = 0.0f;
     int jp = 0, jo = 0;
-    const float phi = eo;
+    const float dphi = delta_k * eo, nqw = -qerr.w;
 #pragma unroll 1
     for (int j = 0; j < n; ++j) {
         const float* f = col.fr(j);
         const V3 pj = v3(f[0 * kCcdThreads], f[1 * kCcdThreads], f[2 * kCcdThreads]);
         const V3 z = v3(f[3 * kCcdThreads], f[4 * kCcdThreads], f[5 * kCcdThreads]);
         const CcdTrials tr =
-            ccd_joint_trials(pj, z, col.th(j), R.lo[j], R.hi[j], E.p, pt, qerr, phi, delta_k, pe2, inv_p2, inv_o2);
+            ccd_joint_trials(pj, z, col.th(j), R.lo[j], R.hi[j], E.p, pt, qerr, nqw, dphi, pe2, inv_p2, inv_o2);
         if (j == 0 || tr.sp < best_p * one_m_tie) {
             best_p = tr.sp;
             jp = j;
@@ -302,9 +315,9 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
                 A.tr.th_hat[j * A.ld + c] = col.th(j) + (j == jp ? aP : 0.0f) + (j == jo ? aO : 0.0f);
         }
     }
-    if (acc) {
-        col.th(jp) += aP;
-        col.th(jo) += aO;
+    if (acc) {  // clamped again: theta + (clamp(theta + d) - theta) can round an ulp past a limit
+        col.th(jp) = clampf(col.th(jp) + aP, R.lo[jp], R.hi[jp]);
+        col.th(jo) = clampf(col.th(jo) + aO, R.lo[jo], R.hi[jo]);
     }
     // rejection: theta + N(0, sigma^2 I), kept inside the limits.  Few lanes reject at a time,
     // so the lanes executing here together share the work: each rejected lane publishes its
