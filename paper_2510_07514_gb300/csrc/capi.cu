@@ -277,10 +277,8 @@ hjcd_status hjcd_create_robot(hjcd_ctx* ctx, int n, const float* dh_a, const flo
         if (!(q_lo[i] < q_hi[i])) return fail(ctx, HJCD_EINVAL, "joint %d: q_lo must be < q_hi", i);
         if (!std::isfinite(dh_a[i]) || !std::isfinite(dh_alpha[i]) || !std::isfinite(dh_d[i]))
             return fail(ctx, HJCD_EINVAL, "joint %d: non-finite DH entry", i);
-        P.ca[i] = (float)std::cos((double)dh_alpha[i]);
-        P.sa[i] = (float)std::sin((double)dh_alpha[i]);
-        P.a[i] = dh_a[i];
-        P.d[i] = dh_d[i];
+        P.dh[i] = make_float4((float)std::cos((double)dh_alpha[i]), (float)std::sin((double)dh_alpha[i]), dh_a[i],
+                              dh_d[i]);
         P.off[i] = dh_theta_off ? dh_theta_off[i] : 0.0f;
         P.lo[i] = q_lo[i];
         P.hi[i] = q_hi[i];

@@ -23,17 +23,19 @@ constexpr int kMaxLaunchRobots = HJCD_MAX_BATCH_ROBOTS;  // robots one launch ca
 // Philox stream phases (third counter word, high byte).
 enum : uint32_t { kPhaseSeed = 1, kPhaseCd = 2, kPhaseDup = 3, kPhaseLm = 4 };
 
-// Robot as seen by the kernels: modified-DH table with cos/sin of alpha,
-// limits, flange transform (728 bytes).
-struct RobotParams {
+// Robot as seen by the kernels: modified-DH table, limits, flange transform
+// (736 bytes).  A joint's cos alpha, sin alpha, a and d sit together, so one
+// 16-byte load per kinematics step fetches them.
+struct __align__(16) RobotParams {
     int32_t n;
     int32_t n_sph;
-    float ca[kMaxDof], sa[kMaxDof], a[kMaxDof], d[kMaxDof], off[kMaxDof];
+    float4 dh[kMaxDof];  // cos alpha, sin alpha, a, d
+    float off[kMaxDof];
     float lo[kMaxDof], hi[kMaxDof];
     float fl_r[9];  // flange rotation, row-major
     float fl_p[3];  // flange translation
 };
-static_assert(sizeof(RobotParams) % 8 == 0, "RobotParams is copied to shared memory in 8-byte words");
+static_assert(sizeof(RobotParams) % 16 == 0, "RobotParams tables are 16-byte aligned in shared memory");
 
 // Collision tables of a robot in device memory: spheres grouped by body
 // (float4 x y z r in the body frame) with their bodies, per-body
@@ -96,9 +98,9 @@ static_assert(sizeof(TargetDesc) == 64, "TargetDesc layout");
 // Copy the launch's robot tables into shared memory (all threads of the CTA
 // take part; ends with a barrier).
 __device__ __forceinline__ const RobotParams* stage_robots(void* smem, const RobotSet& rs) {
-    const uint2* src = reinterpret_cast<const uint2*>(rs.rp);
-    uint2* dst = reinterpret_cast<uint2*>(smem);
-    const int words = rs.n * (int)(sizeof(RobotParams) / 8);
+    const uint4* src = reinterpret_cast<const uint4*>(rs.rp);
+    uint4* dst = reinterpret_cast<uint4*>(smem);
+    const int words = rs.n * (int)(sizeof(RobotParams) / 16);
     for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = __ldg(src + i);
     __syncthreads();
     return reinterpret_cast<const RobotParams*>(smem);
@@ -256,18 +258,30 @@ __device__ __forceinline__ Frame frame_identity() {
     return Frame{v3(1.f, 0.f, 0.f), v3(0.f, 1.f, 0.f), v3(0.f, 0.f, 1.f), v3(0.f, 0.f, 0.f)};
 }
 
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 xy(V3 a) { return make_float2(a.x, a.y); }
+
+// The x and y components run as packed FP32 pairs, the operations of the scalar form in its order.
 __device__ __forceinline__ void fk_step(const RobotParams& R, int j, float theta, Frame& F) {
-    const float ca = R.ca[j], sa = R.sa[j];
-    const V3 b1 = fma3(ca, F.c1, sa * F.c2);
-    const V3 b2 = fma3(ca, F.c2, (-sa) * F.c1);
-    F.p = fma3(R.d[j], b2, fma3(R.a[j], F.c0, F.p));
+    const float4 g = R.dh[j];
+    const float ca = g.x, sa = g.y;
+    const float2 b1 = fma2(bc2(ca), xy(F.c1), mul2(bc2(sa), xy(F.c2)));
+    const float b1z = fmaf(ca, F.c1.z, sa * F.c2.z);
+    const float2 b2 = fma2(bc2(ca), xy(F.c2), mul2(bc2(-sa), xy(F.c1)));
+    const float b2z = fmaf(ca, F.c2.z, (-sa) * F.c1.z);
+    const float2 p = fma2(bc2(g.w), b2, fma2(bc2(g.z), xy(F.c0), xy(F.p)));
+    F.p = v3(p.x, p.y, fmaf(g.w, b2z, fmaf(g.z, F.c0.z, F.p.z)));
     float s, c;
     sincos_red(theta + R.off[j], &s, &c);
-    const V3 n0 = fma3(c, F.c0, s * b1);
-    const V3 n1 = fma3(c, b1, (-s) * F.c0);
-    F.c0 = n0;
-    F.c1 = n1;
-    F.c2 = b2;
+    const float2 n0 = fma2(bc2(c), xy(F.c0), mul2(bc2(s), b1));
+    const float2 n1 = fma2(bc2(c), b1, mul2(bc2(-s), xy(F.c0)));
+    const float n0z = fmaf(c, F.c0.z, s * b1z), n1z = fmaf(c, b1z, (-s) * F.c0.z);
+    F.c0 = v3(n0.x, n0.y, n0z);
+    F.c1 = v3(n1.x, n1.y, n1z);
+    F.c2 = v3(b2.x, b2.y, b2z);
 }
 
 // flange frame from the last joint frame

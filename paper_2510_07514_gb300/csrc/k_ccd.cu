@@ -66,10 +66,6 @@ struct CcdTrials {
 // instructions of sm_100+ (two IEEE operations per instruction, each half rounded on its own), in
 // the order of the scalar helpers (dot, fma3, quat_angle); where the compiler contracts the scalar
 // helpers differently the results differ by an ulp.
-__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
 // p(t^2) of atan01 for both halves (atan t = t p(t^2), t in [0, 1])
 __device__ __forceinline__ float2 atan_poly2(float2 t) {
