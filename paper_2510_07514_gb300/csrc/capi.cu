@@ -280,8 +280,8 @@ hjcd_status hjcd_create_robot(hjcd_ctx* ctx, int n, const float* dh_a, const flo
         P.dh[i] = make_float4((float)std::cos((double)dh_alpha[i]), (float)std::sin((double)dh_alpha[i]), dh_a[i],
                               dh_d[i]);
         P.off[i] = dh_theta_off ? dh_theta_off[i] : 0.0f;
-        P.lo[i] = q_lo[i];
-        P.hi[i] = q_hi[i];
+        P.lim[i].x = q_lo[i];
+        P.lim[i].y = q_hi[i];
     }
     // flange: rigid transform check
     for (int i = 0; i < 3; ++i)

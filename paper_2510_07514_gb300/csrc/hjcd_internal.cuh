@@ -31,7 +31,7 @@ struct __align__(16) RobotParams {
     int32_t n_sph;
     float4 dh[kMaxDof];  // cos alpha, sin alpha, a, d
     float off[kMaxDof];
-    float lo[kMaxDof], hi[kMaxDof];
+    float2 lim[kMaxDof];  // joint limits lo, hi
     float fl_r[9];  // flange rotation, row-major
     float fl_p[3];  // flange translation
 };
@@ -388,7 +388,7 @@ __device__ __forceinline__ float atan01(float t) {
 // argument in [0, 1], reflected about pi/4 when y > x
 __device__ __forceinline__ float atan2_q1(float y, float x) {
     const float mx = fmaxf(x, y), mn = fminf(x, y);
-    const float a = atan01(mx > 0.0f ? __fdividef(mn, mx) : 0.0f);
+    const float a = atan01(__fdividef(mn, fmaxf(mx, 1e-30f)));  // 0 at the origin
     return y > x ? 1.57079632679489662f - a : a;
 }
 

@@ -45,7 +45,7 @@ __device__ __forceinline__ void sample_seed(const RobotParams& R, const TargetDe
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int j = 4 * b + q;
-            if (j < R.n) col.th(j) = fmaf(u01(word(w, q)), R.hi[j] - R.lo[j], R.lo[j]);
+            if (j < R.n) col.th(j) = fmaf(u01(word(w, q)), R.lim[j].y - R.lim[j].x, R.lim[j].x);
         }
     }
 }
@@ -84,8 +84,9 @@ __device__ __forceinline__ float2 atan_poly2(float2 t) {
 __device__ __forceinline__ float2 quat_angle2(float2 w, float2 vv) {
     const float yx = sqrt_approx(vv.x), yy = sqrt_approx(vv.y);
     const float xx = fabsf(w.x), xy = fabsf(w.y);
-    const float mxx = fmaxf(xx, yx), mnx = fminf(xx, yx), mxy = fmaxf(xy, yy), mny = fminf(xy, yy);
-    const float2 t = make_float2(mxx > 0.0f ? __fdividef(mnx, mxx) : 0.0f, mxy > 0.0f ? __fdividef(mny, mxy) : 0.0f);
+    const float mxx = fmaxf(fmaxf(xx, yx), 1e-30f), mnx = fminf(xx, yx);
+    const float mxy = fmaxf(fmaxf(xy, yy), 1e-30f), mny = fminf(xy, yy);
+    const float2 t = make_float2(__fdividef(mnx, mxx), __fdividef(mny, mxy));
     const float2 p = atan_poly2(t);
     const float2 a = mul2(mul2(bc2(2.0f), t), p);                                      // 2 t p
     const float2 r = fma2(mul2(bc2(-2.0f), t), p, bc2(2.0f * 1.57079632679489662f));  // pi - 2 t p
@@ -227,7 +228,7 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
             const V3 zxu = cross(z, up);
             const bool deg = nu2 < 1e-24f || nv2 < 1e-24f || nup2 <= pe2 * nu2 || nvp2 <= pe2 * nv2;
             float d = deg ? 0.0f : atan2_all(dot(zxu, vp), dot(up, vp));
-            d = clampf(thj + d, R.lo[j], R.hi[j]) - thj;
+            d = clampf(thj + d, R.lim[j].x, R.lim[j].y) - thj;
             float sd, cd;
             sincos_red(d, &sd, &cd);  // |d| may exceed pi
             x = pj + fma3(uz, z, fma3(cd, up, sd * zxu));
@@ -241,7 +242,7 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
     // task residual each leaves, and the greedy choice by its score
     // (|e_p|/eps_pos)^2 + (|omega|/eps_ori)^2; a later joint replaces the
     // choice only when its score is lower by more than the fraction cd_tie
-    float best_p = 0.0f, dP = 0.0f, best_o = 0.0f, dO = 0.0f;
+    float best_p = __int_as_float(0x7f800000), dP = 0.0f, best_o = __int_as_float(0x7f800000), dO = 0.0f;
     int jp = 0, jo = 0;
     const float dphi = delta_k * eo, nqw = -qerr.w;
 #pragma unroll 1
@@ -250,13 +251,13 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
         const V3 pj = v3(f[0 * kCcdThreads], f[1 * kCcdThreads], f[2 * kCcdThreads]);
         const V3 z = v3(f[3 * kCcdThreads], f[4 * kCcdThreads], f[5 * kCcdThreads]);
         const CcdTrials tr =
-            ccd_joint_trials(pj, z, col.th(j), R.lo[j], R.hi[j], E.p, pt, qerr, nqw, dphi, pe2, inv_p2, inv_o2);
-        if (j == 0 || tr.sp < best_p * one_m_tie) {
+            ccd_joint_trials(pj, z, col.th(j), R.lim[j].x, R.lim[j].y, E.p, pt, qerr, nqw, dphi, pe2, inv_p2, inv_o2);
+        if (tr.sp < best_p * one_m_tie) {  // joint 0 against +inf
             best_p = tr.sp;
             jp = j;
             dP = tr.d;
         }
-        if (j == 0 || tr.so < best_o * one_m_tie) {
+        if (tr.so < best_o * one_m_tie) {
             best_o = tr.so;
             jo = j;
             dO = tr.dq;
@@ -312,8 +313,8 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
         }
     }
     if (acc) {  // clamped again: theta + (clamp(theta + d) - theta) can round an ulp past a limit
-        col.th(jp) = clampf(col.th(jp) + aP, R.lo[jp], R.hi[jp]);
-        col.th(jo) = clampf(col.th(jo) + aO, R.lo[jo], R.hi[jo]);
+        col.th(jp) = clampf(col.th(jp) + aP, R.lim[jp].x, R.lim[jp].y);
+        col.th(jo) = clampf(col.th(jo) + aO, R.lim[jo].x, R.lim[jo].y);
     }
     // rejection: theta + N(0, sigma^2 I), kept inside the limits.  Few lanes reject at a time,
     // so the lanes executing here together share the work: each rejected lane publishes its
@@ -350,8 +351,8 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
             const float2 z = normal_pair(Tq, q[3], kPhaseCd, q[4], b);
             const ColT<TH> cs{col.base - lane + sl, Rs.n};
             const int j0 = 2 * b, j1 = 2 * b + 1;
-            cs.th(j0) = clampf(fmaf(P.cd_sigma, z.x, cs.th(j0)), Rs.lo[j0], Rs.hi[j0]);
-            if (j1 < Rs.n) cs.th(j1) = clampf(fmaf(P.cd_sigma, z.y, cs.th(j1)), Rs.lo[j1], Rs.hi[j1]);
+            cs.th(j0) = clampf(fmaf(P.cd_sigma, z.x, cs.th(j0)), Rs.lim[j0].x, Rs.lim[j0].y);
+            if (j1 < Rs.n) cs.th(j1) = clampf(fmaf(P.cd_sigma, z.y, cs.th(j1)), Rs.lim[j1].x, Rs.lim[j1].y);
         }
         __syncwarp(am);
     }

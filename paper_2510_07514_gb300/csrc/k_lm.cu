@@ -225,7 +225,7 @@ __device__ __noinline__ float trial_cost(const RobotParams* rob, const TargetDes
     Frame F = frame_identity();
 #pragma unroll 1
     for (int j = 0; j < R.n; ++j)
-        fk_step(R, j, clampf(fmaf(alpha, trial_dir(S, s, kind, j), S.th(j, s)), R.lo[j], R.hi[j]), F);
+        fk_step(R, j, clampf(fmaf(alpha, trial_dir(S, s, kind, j), S.th(j, s)), R.lim[j].x, R.lim[j].y), F);
     const Frame E = fk_flange(R, F);
     const V3 w = quat_log(quat_error(T, quat_from_frame(E)));
     const float e0 = S.W(0, s) * (T.p[0] - E.p.x), e1 = S.W(1, s) * (T.p[1] - E.p.y);
@@ -238,7 +238,7 @@ __device__ __noinline__ float trial_cost(const RobotParams* rob, const TargetDes
 __device__ __noinline__ void take_step(const RobotParams& R, const LmW S, int s, float alpha, int kind) {
 #pragma unroll 1
     for (int j = 0; j < R.n; ++j)
-        S.th(j, s) = clampf(fmaf(alpha, trial_dir(S, s, kind, j), S.th(j, s)), R.lo[j], R.hi[j]);
+        S.th(j, s) = clampf(fmaf(alpha, trial_dir(S, s, kind, j), S.th(j, s)), R.lim[j].x, R.lim[j].y);
 }
 
 // The kinematics-pass trials that follow a failed full step, in the order Alg. 4
@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                     const float th0 = Sx.th(j, l), st = Sx.sc_step(l), c0 = Sx.cost0(l);
                     for (int q = 0; q <= P.lm_A; ++q) {
                         const float a = alphas[q];
-                        const float thj = clampf(fmaf(a, st, th0), Rx.lo[j], Rx.hi[j]);
+                        const float thj = clampf(fmaf(a, st, th0), Rx.lim[j].x, Rx.lim[j].y);
                         ++n_sc;
                         if (coord_cost(Sx, l, thj - th0) < c0) {
                             Sx.th(j, l) = thj;
@@ -645,8 +645,8 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                     const int j0 = 2 * q, j1 = 2 * q + 1;
                     if (j0 >= Rx.n) continue;
                     const float2 z = normal_pair(Tx, (uint32_t)Sx.s(l), kPhaseLm, (uint32_t)A.k0 + (uint32_t)Sx.kk(l), q);
-                    Sx.th(j0, l) = clampf(fmaf(P.lm_sigma, z.x, Sx.th(j0, l)), Rx.lo[j0], Rx.hi[j0]);
-                    if (j1 < Rx.n) Sx.th(j1, l) = clampf(fmaf(P.lm_sigma, z.y, Sx.th(j1, l)), Rx.lo[j1], Rx.hi[j1]);
+                    Sx.th(j0, l) = clampf(fmaf(P.lm_sigma, z.x, Sx.th(j0, l)), Rx.lim[j0].x, Rx.lim[j0].y);
+                    if (j1 < Rx.n) Sx.th(j1, l) = clampf(fmaf(P.lm_sigma, z.y, Sx.th(j1, l)), Rx.lim[j1].x, Rx.lim[j1].y);
                 }
                 __syncthreads();
             }

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kSelThreads) k_topk_dup(const DupArgs A) {
                 const int j = 2 * q + h;
                 if (j < n)
                     A.th_B[j * A.ld_B + b0 + b] =
-                        clampf(fmaf(A.sigma, h ? z.y : z.x, A.th_M[j * A.ld_M + m0 + src]), R.lo[j], R.hi[j]);
+                        clampf(fmaf(A.sigma, h ? z.y : z.x, A.th_M[j * A.ld_M + m0 + src]), R.lim[j].x, R.lim[j].y);
             }
         }
         if (A.src_B) A.src_B[b0 + b] = (int32_t)src;
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kSelThreads) k_dup_kept(const KeptDupArgs A) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int j = 2 * q + h;
-                if (j < n) A.th_B[j * A.ld_B + b0 + b] = clampf(fmaf(A.sigma, h ? z.y : z.x, src[j]), R.lo[j], R.hi[j]);
+                if (j < n) A.th_B[j * A.ld_B + b0 + b] = clampf(fmaf(A.sigma, h ? z.y : z.x, src[j]), R.lim[j].x, R.lim[j].y);
             }
         }
     }
