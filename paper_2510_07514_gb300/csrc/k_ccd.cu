@@ -280,14 +280,13 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
     }
     // residual at theta_hat: the distal joint's rotation first, then the proximal one
     // (the chosen joints' origins and axes are still in the shared-memory column)
-    const float* fp = col.fr(jp);
-    const float* fo = col.fr(jo);
-    const V3 Pp = v3(fp[0 * kCcdThreads], fp[1 * kCcdThreads], fp[2 * kCcdThreads]);
-    const V3 Zp = v3(fp[3 * kCcdThreads], fp[4 * kCcdThreads], fp[5 * kCcdThreads]);
-    const V3 Po = v3(fo[0 * kCcdThreads], fo[1 * kCcdThreads], fo[2 * kCcdThreads]);
-    const V3 Zo = v3(fo[3 * kCcdThreads], fo[4 * kCcdThreads], fo[5 * kCcdThreads]);
     const bool p_hi = jp > jo;
-    const V3 Pa = p_hi ? Pp : Po, Za = p_hi ? Zp : Zo, Pb = p_hi ? Po : Pp, Zb = p_hi ? Zo : Zp;
+    const float* fa = col.fr(p_hi ? jp : jo);  // the distal joint
+    const float* fb = col.fr(p_hi ? jo : jp);
+    const V3 Pa = v3(fa[0 * kCcdThreads], fa[1 * kCcdThreads], fa[2 * kCcdThreads]);
+    const V3 Za = v3(fa[3 * kCcdThreads], fa[4 * kCcdThreads], fa[5 * kCcdThreads]);
+    const V3 Pb = v3(fb[0 * kCcdThreads], fb[1 * kCcdThreads], fb[2 * kCcdThreads]);
+    const V3 Zb = v3(fb[3 * kCcdThreads], fb[4 * kCcdThreads], fb[5 * kCcdThreads]);
     const float da = p_hi ? aP : aO, db = p_hi ? aO : aP;
     float sa_, ca_, sb_, cb_;
     __sincosf(0.5f * da, &sa_, &ca_);
