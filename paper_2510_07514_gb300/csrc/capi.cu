@@ -122,7 +122,7 @@ int64_t dup_count(int64_t M, int ratio) {
 }
 
 RobotSet single_robot_set(const RobotRec& r) {
-    return RobotSet{r.d_params, r.d_dev, 1, r.P.n, r.P.n_sph, r.n_pairs};
+    return RobotSet{r.d_params, r.d_dev, 1, r.P.n, r.P.n_sph, r.n_pairs, r.P.in_pi};
 }
 
 void collide_uniform(CollideArgs& a, const RobotRec& r, const SceneRec* sc) {
@@ -283,6 +283,12 @@ hjcd_status hjcd_create_robot(hjcd_ctx* ctx, int n, const float* dh_a, const flo
         P.lim[i].x = q_lo[i];
         P.lim[i].y = q_hi[i];
     }
+    // theta + offset within (-pi, pi) over the limits, with a margin far above binary32 rounding:
+    // the kinematics then need no range reduction
+    P.in_pi = 1;
+    for (int i = 0; i < n; ++i)
+        if (!(std::fabs((double)P.lim[i].x + P.off[i]) <= 3.1415 && std::fabs((double)P.lim[i].y + P.off[i]) <= 3.1415))
+            P.in_pi = 0;
     // flange: rigid transform check
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
@@ -1175,6 +1181,7 @@ extern "C" hjcd_status hjcd_solve_noalloc(hjcd_ctx* ctx, int32_t robot_id, int32
     ca.n_iters = P.cd_max_iters;
     ca.P = P;
     ca.block = ctx->ccd_block;
+    ca.in_limits = 1;  // sampled seeds
     launch_ccd(ca, false, s);
     DupArgs da{rs, d_tg, T, d_moff, sM, thM, CM, d_boff, thB, CB, nullptr, P.dup_ratio, P.dup_sigma};
     launch_topk_dup(da, M, s);
@@ -1192,6 +1199,7 @@ extern "C" hjcd_status hjcd_solve_noalloc(hjcd_ctx* ctx, int32_t robot_id, int32
     la.P = P;
     la.queue = queue;
     la.warps = ctx->lm_warps;
+    la.in_limits = 1;  // PO-CCD's joint vectors and their clamped duplicates
     launch_lm(la, false, s);
     const bool collide = R.n_sph > 0;
     if (collide) {
@@ -1285,6 +1293,7 @@ hjcd_status hjcd_shard_topk(hjcd_ctx* ctx, int32_t robot_id, int n_targets, cons
     ca.cnt = ctx->cnt;
     ca.block = ctx->ccd_block;
     ca.seed_base = seed_begin;
+    ca.in_limits = 1;  // sampled seeds
     launch_ccd(ca, false, s);
     ShardTopkArgs ta{single_robot_set(*rob), d_tg, T, (int32_t)K, seed_begin, d_off, ca.score, ca.th_out, C,
                      out_score, out_index, out_theta, n};

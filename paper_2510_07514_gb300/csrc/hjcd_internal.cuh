@@ -29,6 +29,7 @@ enum : uint32_t { kPhaseSeed = 1, kPhaseCd = 2, kPhaseDup = 3, kPhaseLm = 4 };
 struct __align__(16) RobotParams {
     int32_t n;
     int32_t n_sph;
+    int32_t in_pi;  // 1: theta + offset stays inside (-pi, pi) for every theta within the limits
     float4 dh[kMaxDof];  // cos alpha, sin alpha, a, d
     float off[kMaxDof];
     float2 lim[kMaxDof];  // joint limits lo, hi
@@ -75,6 +76,7 @@ struct RobotSet {
     int32_t n_max;          // largest DoF
     int32_t ns_max;         // most link spheres
     int32_t pairs_max;      // most self-collision body pairs
+    int32_t in_pi = 0;      // 1: every robot of the set has in_pi (see RobotParams)
 };
 
 // One target pose with its request's tolerances, random-stream key, robot,
@@ -265,6 +267,10 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 xy(V3 a) { return make_float2(a.x, a.y); }
 
 // The x and y components run as packed FP32 pairs, the operations of the scalar form in its order.
+// RED = false leaves out the range reduction of theta + offset: the caller guarantees theta within
+// the limits of a robot with in_pi, where the reduction's multiple of 2 pi is 0 and it returns its
+// argument unchanged (the same bits either way).
+template <bool RED = true>
 __device__ __forceinline__ void fk_step(const RobotParams& R, int j, float theta, Frame& F) {
     const float4 g = R.dh[j];
     const float ca = g.x, sa = g.y;
@@ -275,7 +281,8 @@ __device__ __forceinline__ void fk_step(const RobotParams& R, int j, float theta
     const float2 p = fma2(bc2(g.w), b2, fma2(bc2(g.z), xy(F.c0), xy(F.p)));
     F.p = v3(p.x, p.y, fmaf(g.w, b2z, fmaf(g.z, F.c0.z, F.p.z)));
     float s, c;
-    sincos_red(theta + R.off[j], &s, &c);
+    if (RED) sincos_red(theta + R.off[j], &s, &c);
+    else __sincosf(theta + R.off[j], &s, &c);
     const float2 n0 = fma2(bc2(c), xy(F.c0), mul2(bc2(s), b1));
     const float2 n1 = fma2(bc2(c), b1, mul2(bc2(-s), xy(F.c0)));
     const float n0z = fmaf(c, F.c0.z, s * b1z), n1z = fmaf(c, b1z, (-s) * F.c0.z);
@@ -546,6 +553,7 @@ struct CcdArgs {
     // state th_out holds; a candidate still iterating at seg_end keeps its state in th_out and is
     // appended to list_out (count *n_out) instead of writing its results.
     int32_t seg_begin, seg_end;
+    int32_t in_limits;  // 1: every joint vector the launch reads lies within its robot's limits
     const int32_t* list_in;
     const int32_t* n_in;
     int32_t* list_out;
@@ -566,6 +574,7 @@ struct LmArgs {
     Counters* cnt;
     unsigned long long* queue;  // candidate queue head, zero at launch
     int32_t warps;  // warps per CTA: 2, 4 or 8 (anything else: 8, the contexts' default)
+    int32_t in_limits;  // 1: every joint vector the launch reads lies within its robot's limits
 };
 
 struct DupArgs {

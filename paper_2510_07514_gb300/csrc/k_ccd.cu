@@ -179,7 +179,7 @@ constexpr int kSlotWords = 8;  // per-thread shared-memory slot of the cooperati
 __constant__ uint32_t kDivMagic[13] = {0, 65536, 32768, 21846, 16384, 13108, 10923, 9363, 8192, 7282, 6554, 5958, 5462};
 static_assert((kMaxDof + 1) / 2 <= 12, "the normal pairs of a joint vector index kDivMagic");
 
-template <bool TRACE, int TH>
+template <bool TRACE, int TH, bool RED = true>
 __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParams& R, const TargetDesc& T,
                                         const hjcd_params& P, const ColT<TH>& col, uint32_t* slots, const CcdArgs& A,
                                         int64_t c, uint32_t s, int kk, int cap, float delta_k, const V3 pt, float pe2,
@@ -190,7 +190,7 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
     Frame F = frame_identity();
 #pragma unroll 1
     for (int j = 0; j < n; ++j) {
-        fk_step(R, j, col.th(j), F);
+        fk_step<RED>(R, j, col.th(j), F);
         float* f = col.fr(j);
         f[0 * kCcdThreads] = F.p.x;
         f[1 * kCcdThreads] = F.p.y;
@@ -363,7 +363,9 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
 #ifndef HJCD_CCD_THREADS_PER_SM
 #define HJCD_CCD_THREADS_PER_SM 768
 #endif
-template <bool TRACE, int TH>
+// RED = false: the launch's joint vectors lie within the limits of robots with in_pi (no range
+// reduction in the kinematics steps; the same bits)
+template <bool TRACE, int TH, bool RED>
 __global__ void __launch_bounds__(TH, HJCD_CCD_THREADS_PER_SM / TH) k_ccd(const CcdArgs A) {
     using Col = ColT<TH>;
     extern __shared__ __align__(16) float sm[];
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(TH, HJCD_CCD_THREADS_PER_SM / TH) k_ccd(const 
                 handed = true;
                 break;
             }
-            const int r = ccd_step<TRACE, TH>(rob, R, T, P, col, slots, A, c, (uint32_t)s, kk, cap, delta_k, pt, pe2,
+            const int r = ccd_step<TRACE, TH, RED>(rob, R, T, P, col, slots, A, c, (uint32_t)s, kk, cap, delta_k, pt, pe2,
                                               one_m_tie, inv_p2, inv_o2, ep2, eo);
             if (r == 1) iters = kk;
             if (r) break;
@@ -562,20 +564,20 @@ __global__ void __launch_bounds__(kCcdThreads) k_sample(const RobotParams R, uin
 }
 
 
-template <bool TRACE, int TH>
+template <bool TRACE, int TH, bool RED>
 void launch_ccd_t(const CcdArgs& A, cudaStream_t st) {
     const size_t smem = robots_smem_bytes(A.rs.n) + sizeof(float) * (7 * A.rs.n_max + kSlotWords) * TH;
     static SmemLimit lim;
-    allow_dyn_smem(k_ccd<TRACE, TH>, lim,
+    allow_dyn_smem(k_ccd<TRACE, TH, RED>, lim,
                    robots_smem_bytes(kMaxLaunchRobots) + sizeof(float) * (7 * kMaxDof + kSlotWords) * TH);
-    k_ccd<TRACE, TH><<<grid_for(A.C, TH, 16 * 128 / TH), TH, smem, st>>>(A);
+    k_ccd<TRACE, TH, RED><<<grid_for(A.C, TH, 16 * 128 / TH), TH, smem, st>>>(A);
 }
 
-template <bool TRACE>
+template <bool TRACE, bool RED>
 void launch_ccd_b(const CcdArgs& A, cudaStream_t st) {
-    if (A.block == 64) launch_ccd_t<TRACE, 64>(A, st);
-    else if (A.block == 256) launch_ccd_t<TRACE, 256>(A, st);
-    else launch_ccd_t<TRACE, 128>(A, st);
+    if (A.block == 64) launch_ccd_t<TRACE, 64, RED>(A, st);
+    else if (A.block == 256) launch_ccd_t<TRACE, 256, RED>(A, st);
+    else launch_ccd_t<TRACE, 128, RED>(A, st);
 }
 
 }  // namespace
@@ -590,8 +592,9 @@ void launch_ccd(const CcdArgs& A, bool trace, cudaStream_t st) {
         k_ccd_lock<128><<<A.map.T, 128, smem, st>>>(A);
         return;
     }
-    if (trace) launch_ccd_b<true>(A, st);
-    else launch_ccd_b<false>(A, st);
+    if (trace) launch_ccd_b<true, true>(A, st);
+    else if (A.in_limits && A.rs.in_pi) launch_ccd_b<false, false>(A, st);
+    else launch_ccd_b<false, true>(A, st);
 }
 
 void launch_sample(const RobotParams& R, uint64_t seed, CandMap map, int64_t C, float* th, int64_t ld,

@@ -218,6 +218,7 @@ __device__ __forceinline__ float trial_dir(const LmW& S, int s, int kind, int j)
 // (the kinematics passes, the 6 x 6 solve and the trial spreading each exist
 // once in the kernel, called from every branch that needs them, which keeps
 // the per-iteration body inside the instruction cache)
+template <bool RED>
 __device__ __noinline__ float trial_cost(const RobotParams* rob, const TargetDesc* tg, int row, const LmW S, int s,
                                         float alpha, int kind) {
     const TargetDesc T = tg[row];
@@ -225,7 +226,7 @@ __device__ __noinline__ float trial_cost(const RobotParams* rob, const TargetDes
     Frame F = frame_identity();
 #pragma unroll 1
     for (int j = 0; j < R.n; ++j)
-        fk_step(R, j, clampf(fmaf(alpha, trial_dir(S, s, kind, j), S.th(j, s)), R.lim[j].x, R.lim[j].y), F);
+        fk_step<RED>(R, j, clampf(fmaf(alpha, trial_dir(S, s, kind, j), S.th(j, s)), R.lim[j].x, R.lim[j].y), F);
     const Frame E = fk_flange(R, F);
     const V3 w = quat_log(quat_error(T, quat_from_frame(E)));
     const float e0 = S.W(0, s) * (T.p[0] - E.p.x), e1 = S.W(1, s) * (T.p[1] - E.p.y);
@@ -384,7 +385,9 @@ __device__ __noinline__ void dogleg_prepare(const LmW S, int l, int n, float Rt,
     }
 }
 
-template <bool TRACE, int WARPS>
+// RED = false: the launch's joint vectors lie within the limits of robots with in_pi (no range
+// reduction in the kinematics steps; the same bits)
+template <bool TRACE, int WARPS, bool RED>
 __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
     extern __shared__ __align__(16) float smem_f[];
     __shared__ float alphas[kMaxLsDepth + 1];
@@ -448,7 +451,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
             Frame F = frame_identity();
 #pragma unroll 1
             for (int j = 0; j < n; ++j) {
-                fk_step(R, j, S.th(j, lane), F);
+                fk_step<RED>(R, j, S.th(j, lane), F);
                 S.jw(0, j, lane) = F.p.x;
                 S.jw(1, j, lane) = F.p.y;
                 S.jw(2, j, lane) = F.p.z;
@@ -547,7 +550,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
         float alpha_acc = 0.0f;
         if (act) {
             ++n_fk;
-            if (trial_cost(rob, A.tg, t, S, lane, 1.0f, kDirLm) < S.cost0(lane)) {
+            if (trial_cost<RED>(rob, A.tg, t, S, lane, 1.0f, kDirLm) < S.cost0(lane)) {
                 take_step(R, S, lane, 1.0f, kDirLm);
                 branch = 0;
                 alpha_acc = 1.0f;
@@ -589,7 +592,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                 int kind;
                 float alpha;
                 trial_item(i, P.lm_A, alphas, &kind, &alpha);
-                Sx.ok(i, l) = trial_cost(rob, A.tg, Sx.t(l), Sx, l, alpha, kind) < Sx.cost0(l) ? 1 : 0;
+                Sx.ok(i, l) = trial_cost<RED>(rob, A.tg, Sx.t(l), Sx, l, alpha, kind) < Sx.cost0(l) ? 1 : 0;
             }
             __syncthreads();
             // each slot's first successful trial in the order of Alg. 4, else its
@@ -684,23 +687,23 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
     }
 }
 
-template <bool TRACE, int WARPS>
+template <bool TRACE, int WARPS, bool RED>
 void launch_lm_t(const LmArgs& A, cudaStream_t st) {
     const size_t smem = robots_smem_bytes(A.rs.n) +
                         sizeof(float) * ((size_t)lm_warp_words(A.rs.n_max, A.P.lm_A) * WARPS + lm_cta_words<WARPS>());
     static SmemLimit lim;
-    allow_dyn_smem(k_lm<TRACE, WARPS>, lim,
+    allow_dyn_smem(k_lm<TRACE, WARPS, RED>, lim,
                    robots_smem_bytes(kMaxLaunchRobots) +
                        sizeof(float) * ((size_t)lm_warp_words(kMaxDof, kMaxLsDepth) * WARPS + lm_cta_words<WARPS>()));
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lm<TRACE, WARPS>, WARPS * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lm<TRACE, WARPS, RED>, WARPS * 32, smem);
     if (per_sm < 1) per_sm = 1;
     const int64_t want = (A.C + 32 * WARPS - 1) / (32 * WARPS);
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * per_sm));
-    k_lm<TRACE, WARPS><<<g, WARPS * 32, smem, st>>>(A);
+    k_lm<TRACE, WARPS, RED><<<g, WARPS * 32, smem, st>>>(A);
 }
 
-template <bool TRACE>
+template <bool TRACE, bool RED>
 void launch_lm_w(const LmArgs& A, cudaStream_t st) {
     // fewer warps per CTA when the requested count's state does not fit in shared memory
     int optin = 0;
@@ -713,17 +716,18 @@ void launch_lm_w(const LmArgs& A, cudaStream_t st) {
     // (the CTA lists: 65 words per warp and one; 256 bytes kept for the kernel's static arrays)
     while (warps > 2 && robots_smem_bytes(A.rs.n) + (per_warp + sizeof(float) * 65) * warps + 4 + 256 > (size_t)optin)
         warps /= 2;
-    if (warps == 2) launch_lm_t<TRACE, 2>(A, st);
-    else if (warps == 4) launch_lm_t<TRACE, 4>(A, st);
-    else launch_lm_t<TRACE, 8>(A, st);
+    if (warps == 2) launch_lm_t<TRACE, 2, RED>(A, st);
+    else if (warps == 4) launch_lm_t<TRACE, 4, RED>(A, st);
+    else launch_lm_t<TRACE, 8, RED>(A, st);
 }
 
 }  // namespace
 
 void launch_lm(const LmArgs& A, bool trace, cudaStream_t st) {
     if (A.C <= 0) return;
-    if (trace) launch_lm_w<true>(A, st);
-    else launch_lm_w<false>(A, st);
+    if (trace) launch_lm_w<true, true>(A, st);
+    else if (A.in_limits && A.rs.in_pi) launch_lm_w<false, false>(A, st);
+    else launch_lm_w<false, true>(A, st);
 }
 
 }  // namespace hjcd

@@ -254,6 +254,8 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
     unsigned long long* queue = reinterpret_cast<unsigned long long*>(ws + W.o_qf);
     RobotSet rs{reinterpret_cast<const RobotParams*>(ws + W.o_rp), reinterpret_cast<const RobotDev*>(ws + W.o_rd),
                 W.NR, W.n_max, W.ns_max, W.pairs_max};
+    rs.in_pi = 1;
+    for (int r = 0; r < W.NR; ++r) rs.in_pi &= W.robots[r]->P.in_pi;
 
     if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[0], s));
     launch_pack_targets(reinterpret_cast<const float*>(ws + W.o_pq7), W.T, d_tg, TargetDesc{}, d_tg, s);
@@ -274,6 +276,7 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
     ca.P = P;
     ca.cnt = ctx->cnt;
     ca.block = ctx->ccd_block;
+    ca.in_limits = 1;  // seeds sampled inside the limits, every update clamped to them
     // Iteration segments: a lane whose candidate meets the coarse tolerance waits for the rest of
     // its warp, so the iterations run in three launches ([0, cap/2), [cap/2, 3 cap/4), the rest)
     // and the candidates still iterating are packed afresh into full warps for the next (the same
@@ -326,6 +329,7 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
     la.cnt = ctx->cnt;
     la.queue = queue;
     la.warps = ctx->lm_warps;
+    la.in_limits = 1;  // PO-CCD's joint vectors and their clamped duplicates
     launch_lm(la, false, s);
     if ((st = after_launch(ctx, 1, "k_lm"))) return st;
     if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[3], s));

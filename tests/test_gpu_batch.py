@@ -446,6 +446,30 @@ def test_solve_nearest_matches_the_oracle(ctx):
             assert np.all(np.diff(d) >= -1e-6)
 
 
+def test_solve_with_angles_past_pi_matches_the_oracle(ctx):
+    """Joint offsets put theta + offset outside (-pi, pi) for part of every
+    joint's range, so the kinematics take their range reduction inside the
+    solve (the kernels leave it out only when every robot of a launch keeps
+    its angles inside): success within one point of the oracle's whole method,
+    every solution re-verified."""
+    import dataclasses
+
+    base = inputs.panda()
+    rob = dataclasses.replace(base, theta_off=np.array([1.5, -1.2, 0.8, 2.0, -1.7, 1.1, 0.6]))
+    assert np.max(np.abs(np.r_[rob.lo + rob.theta_off, rob.hi + rob.theta_off])) > np.pi
+    rid = ctx.add_robot(rob)
+    orob = orc.Robot(rob)
+    rng = np.random.default_rng(89)
+    T, S, k = 300, 128, 2
+    tg = f32(orc.pose(orob, f32(rng.uniform(rob.lo, rob.hi, (T, 7)))))
+    q, e, c = (host(x) for x in ctx.solve(rid, -1, dev(tg), S, k, 23, 7))
+    sg = _verify(orob, None, rob, tg, q, e, c.astype(int), 1e-3, 1e-2)
+    o = orc.solve(orob, None, orc.make_params(1e-3, 1e-2, seed=23), tg, S, k)
+    so = (o["count"] > 0) & (o["err"][:, 0, 0] <= 1e-3) & (o["err"][:, 0, 1] <= 1e-2)
+    assert sg.mean() >= 0.9
+    assert abs(sg.mean() - so.mean()) <= 0.01 + 1e-12, (sg.mean(), so.mean())
+
+
 def test_tracking_loop_follows_a_scene_rewritten_every_frame(ctx):
     """The tracking use (Sec. VI-D): each frame the obstacle scene is replaced
     in place (hjcd_set_scene on the same id) and the next pose is solved from
