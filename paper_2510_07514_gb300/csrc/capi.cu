@@ -285,6 +285,8 @@ hjcd_status hjcd_create_robot(hjcd_ctx* ctx, int n, const float* dh_a, const flo
     }
     // theta + offset within (-pi, pi) over the limits, with a margin far above binary32 rounding:
     // the kinematics then need no range reduction
+    P.fl_eye = flange[0] == 1.0f && flange[5] == 1.0f && flange[10] == 1.0f && flange[1] == 0.0f && flange[2] == 0.0f &&
+               flange[4] == 0.0f && flange[6] == 0.0f && flange[8] == 0.0f && flange[9] == 0.0f;
     P.in_pi = 1;
     for (int i = 0; i < n; ++i)
         if (!(std::fabs((double)P.lim[i].x + P.off[i]) <= 3.1415 && std::fabs((double)P.lim[i].y + P.off[i]) <= 3.1415))

@@ -30,6 +30,7 @@ struct __align__(16) RobotParams {
     int32_t n;
     int32_t n_sph;
     int32_t in_pi;  // 1: theta + offset stays inside (-pi, pi) for every theta within the limits
+    int32_t fl_eye; // 1: the flange rotation is the identity (the flange frame's axes are the last joint's)
     float4 dh[kMaxDof];  // cos alpha, sin alpha, a, d
     float off[kMaxDof];
     float2 lim[kMaxDof];  // joint limits lo, hi
@@ -294,6 +295,13 @@ __device__ __forceinline__ void fk_step(const RobotParams& R, int j, float theta
 // flange frame from the last joint frame
 __device__ __forceinline__ Frame fk_flange(const RobotParams& R, const Frame& F) {
     Frame E;
+    if (R.fl_eye) {  // the general form's products with 1 and 0 (up to the sign of an exact zero)
+        E.c0 = F.c0;
+        E.c1 = F.c1;
+        E.c2 = F.c2;
+        E.p = fma3(R.fl_p[2], F.c2, fma3(R.fl_p[1], F.c1, fma3(R.fl_p[0], F.c0, F.p)));
+        return E;
+    }
     E.c0 = fma3(R.fl_r[6], F.c2, fma3(R.fl_r[3], F.c1, R.fl_r[0] * F.c0));
     E.c1 = fma3(R.fl_r[7], F.c2, fma3(R.fl_r[4], F.c1, R.fl_r[1] * F.c0));
     E.c2 = fma3(R.fl_r[8], F.c2, fma3(R.fl_r[5], F.c1, R.fl_r[2] * F.c0));
