@@ -446,17 +446,26 @@ def test_solve_nearest_matches_the_oracle(ctx):
             assert np.all(np.diff(d) >= -1e-6)
 
 
-def test_solve_with_angles_past_pi_matches_the_oracle(ctx):
-    """Joint offsets put theta + offset outside (-pi, pi) for part of every
-    joint's range, so the kinematics take their range reduction inside the
-    solve (the kernels leave it out only when every robot of a launch keeps
-    its angles inside): success within one point of the oracle's whole method,
-    every solution re-verified."""
+@pytest.mark.parametrize("case", ["offsets_past_pi", "rotated_flange"])
+def test_solve_with_general_kinematics_matches_the_oracle(ctx, case):
+    """The kinematics' general forms inside a solve: joint offsets that put
+    theta + offset outside (-pi, pi) for part of every joint's range (the
+    range reduction, which the kernels leave out only when every robot of a
+    launch keeps its angles inside), and a flange whose rotation is not the
+    identity (the kernels take the last joint's axes directly only when it
+    is).  Success within one point of the oracle's whole method, every
+    solution re-verified."""
     import dataclasses
 
     base = inputs.panda()
-    rob = dataclasses.replace(base, theta_off=np.array([1.5, -1.2, 0.8, 2.0, -1.7, 1.1, 0.6]))
-    assert np.max(np.abs(np.r_[rob.lo + rob.theta_off, rob.hi + rob.theta_off])) > np.pi
+    if case == "offsets_past_pi":
+        rob = dataclasses.replace(base, theta_off=np.array([1.5, -1.2, 0.8, 2.0, -1.7, 1.1, 0.6]))
+        assert np.max(np.abs(np.r_[rob.lo + rob.theta_off, rob.hi + rob.theta_off])) > np.pi
+    else:
+        c, s_ = np.cos(-np.pi / 4), np.sin(-np.pi / 4)  # a hand turned -45 degrees about the last axis
+        fl = np.array(base.flange, float).reshape(4, 4).copy()
+        fl[:3, :3] = [[c, -s_, 0.0], [s_, c, 0.0], [0.0, 0.0, 1.0]]
+        rob = dataclasses.replace(base, flange=fl.reshape(np.shape(base.flange)))
     rid = ctx.add_robot(rob)
     orob = orc.Robot(rob)
     rng = np.random.default_rng(89)
