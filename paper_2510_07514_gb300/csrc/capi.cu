@@ -122,7 +122,7 @@ int64_t dup_count(int64_t M, int ratio) {
 }
 
 RobotSet single_robot_set(const RobotRec& r) {
-    return RobotSet{r.d_params, r.d_dev, 1, r.P.n, r.P.n_sph, r.n_pairs, r.P.in_pi};
+    return RobotSet{r.d_params, r.d_dev, 1, r.P.n, r.P.n_sph, r.n_pairs, r.P.plain};
 }
 
 void collide_uniform(CollideArgs& a, const RobotRec& r, const SceneRec* sc) {
@@ -283,14 +283,14 @@ hjcd_status hjcd_create_robot(hjcd_ctx* ctx, int n, const float* dh_a, const flo
         P.lim[i].x = q_lo[i];
         P.lim[i].y = q_hi[i];
     }
-    // theta + offset within (-pi, pi) over the limits, with a margin far above binary32 rounding:
-    // the kinematics then need no range reduction
     P.fl_eye = flange[0] == 1.0f && flange[5] == 1.0f && flange[10] == 1.0f && flange[1] == 0.0f && flange[2] == 0.0f &&
                flange[4] == 0.0f && flange[6] == 0.0f && flange[8] == 0.0f && flange[9] == 0.0f;
-    P.in_pi = 1;
+    // plain: no joint offsets, and theta within (-pi, pi) over the limits with a margin far above
+    // binary32 rounding; the kinematics then need neither the offset nor a range reduction
+    P.plain = 1;
     for (int i = 0; i < n; ++i)
-        if (!(std::fabs((double)P.lim[i].x + P.off[i]) <= 3.1415 && std::fabs((double)P.lim[i].y + P.off[i]) <= 3.1415))
-            P.in_pi = 0;
+        if (!(P.off[i] == 0.0f && std::fabs((double)P.lim[i].x) <= 3.1415 && std::fabs((double)P.lim[i].y) <= 3.1415))
+            P.plain = 0;
     // flange: rigid transform check
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {

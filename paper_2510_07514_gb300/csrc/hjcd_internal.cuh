@@ -29,7 +29,7 @@ enum : uint32_t { kPhaseSeed = 1, kPhaseCd = 2, kPhaseDup = 3, kPhaseLm = 4 };
 struct __align__(16) RobotParams {
     int32_t n;
     int32_t n_sph;
-    int32_t in_pi;  // 1: theta + offset stays inside (-pi, pi) for every theta within the limits
+    int32_t plain;  // 1: every joint offset is 0 and every theta within the limits lies inside (-pi, pi)
     int32_t fl_eye; // 1: the flange rotation is the identity (the flange frame's axes are the last joint's)
     float4 dh[kMaxDof];  // cos alpha, sin alpha, a, d
     float off[kMaxDof];
@@ -77,7 +77,7 @@ struct RobotSet {
     int32_t n_max;          // largest DoF
     int32_t ns_max;         // most link spheres
     int32_t pairs_max;      // most self-collision body pairs
-    int32_t in_pi = 0;      // 1: every robot of the set has in_pi (see RobotParams)
+    int32_t plain = 0;      // 1: every robot of the set is plain (see RobotParams)
 };
 
 // One target pose with its request's tolerances, random-stream key, robot,
@@ -268,9 +268,10 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 xy(V3 a) { return make_float2(a.x, a.y); }
 
 // The x and y components run as packed FP32 pairs, the operations of the scalar form in its order.
-// RED = false leaves out the range reduction of theta + offset: the caller guarantees theta within
-// the limits of a robot with in_pi, where the reduction's multiple of 2 pi is 0 and it returns its
-// argument unchanged (the same bits either way).
+// RED = false leaves out the offset and the range reduction of theta + offset: the caller
+// guarantees theta within the limits of a plain robot, whose offsets are 0 and where the
+// reduction's multiple of 2 pi is 0, so both return their argument unchanged (the same bits either
+// way, up to the sign of an exact zero).
 template <bool RED = true>
 __device__ __forceinline__ void fk_step(const RobotParams& R, int j, float theta, Frame& F) {
     const float4 g = R.dh[j];
@@ -283,7 +284,7 @@ __device__ __forceinline__ void fk_step(const RobotParams& R, int j, float theta
     F.p = v3(p.x, p.y, fmaf(g.w, b2z, fmaf(g.z, F.c0.z, F.p.z)));
     float s, c;
     if (RED) sincos_red(theta + R.off[j], &s, &c);
-    else __sincosf(theta + R.off[j], &s, &c);
+    else __sincosf(theta, &s, &c);
     const float2 n0 = fma2(bc2(c), xy(F.c0), mul2(bc2(s), b1));
     const float2 n1 = fma2(bc2(c), b1, mul2(bc2(-s), xy(F.c0)));
     const float n0z = fmaf(c, F.c0.z, s * b1z), n1z = fmaf(c, b1z, (-s) * F.c0.z);

@@ -363,8 +363,8 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
 #ifndef HJCD_CCD_THREADS_PER_SM
 #define HJCD_CCD_THREADS_PER_SM 768
 #endif
-// RED = false: the launch's joint vectors lie within the limits of robots with in_pi (no range
-// reduction in the kinematics steps; the same bits)
+// RED = false: the launch's joint vectors lie within the limits of plain robots (no offsets and
+// no range reduction in the kinematics steps; the same bits)
 template <bool TRACE, int TH, bool RED>
 __global__ void __launch_bounds__(TH, HJCD_CCD_THREADS_PER_SM / TH) k_ccd(const CcdArgs A) {
     using Col = ColT<TH>;
@@ -593,7 +593,7 @@ void launch_ccd(const CcdArgs& A, bool trace, cudaStream_t st) {
         return;
     }
     if (trace) launch_ccd_b<true, true>(A, st);
-    else if (A.in_limits && A.rs.in_pi) launch_ccd_b<false, false>(A, st);
+    else if (A.in_limits && A.rs.plain) launch_ccd_b<false, false>(A, st);
     else launch_ccd_b<false, true>(A, st);
 }
 

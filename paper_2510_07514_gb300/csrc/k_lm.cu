@@ -385,8 +385,8 @@ __device__ __noinline__ void dogleg_prepare(const LmW S, int l, int n, float Rt,
     }
 }
 
-// RED = false: the launch's joint vectors lie within the limits of robots with in_pi (no range
-// reduction in the kinematics steps; the same bits)
+// RED = false: the launch's joint vectors lie within the limits of plain robots (no offsets and
+// no range reduction in the kinematics steps; the same bits)
 template <bool TRACE, int WARPS, bool RED>
 __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
     extern __shared__ __align__(16) float smem_f[];
@@ -726,7 +726,7 @@ void launch_lm_w(const LmArgs& A, cudaStream_t st) {
 void launch_lm(const LmArgs& A, bool trace, cudaStream_t st) {
     if (A.C <= 0) return;
     if (trace) launch_lm_w<true, true>(A, st);
-    else if (A.in_limits && A.rs.in_pi) launch_lm_w<false, false>(A, st);
+    else if (A.in_limits && A.rs.plain) launch_lm_w<false, false>(A, st);
     else launch_lm_w<false, true>(A, st);
 }
 

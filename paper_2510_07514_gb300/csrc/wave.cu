@@ -254,8 +254,8 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
     unsigned long long* queue = reinterpret_cast<unsigned long long*>(ws + W.o_qf);
     RobotSet rs{reinterpret_cast<const RobotParams*>(ws + W.o_rp), reinterpret_cast<const RobotDev*>(ws + W.o_rd),
                 W.NR, W.n_max, W.ns_max, W.pairs_max};
-    rs.in_pi = 1;
-    for (int r = 0; r < W.NR; ++r) rs.in_pi &= W.robots[r]->P.in_pi;
+    rs.plain = 1;
+    for (int r = 0; r < W.NR; ++r) rs.plain &= W.robots[r]->P.plain;
 
     if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[0], s));
     launch_pack_targets(reinterpret_cast<const float*>(ws + W.o_pq7), W.T, d_tg, TargetDesc{}, d_tg, s);
