@@ -230,9 +230,30 @@ __device__ __forceinline__ uint4 rnd_block(const TargetDesc& T, uint32_t cand, u
 // ((x >> 9) + 1/2) * 2^-23: exact in binary32, inside (0, 1)
 __device__ __forceinline__ float u01(uint32_t x) { return ((float)(x >> 9) + 0.5f) * 1.1920928955078125e-07f; }
 
-// Box-Muller, cosine branch
+// Square root by the hardware approximation (PTX sqrt.approx.f32, a few ulp):
+// for the angles and norms that rank trials and test tolerances, where the
+// IEEE-rounded sqrtf's correction steps cost issue slots of issue-bound
+// kernels and buy no decision the binary32 kinematics can resolve.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// ln u of u = u01(x) in (0, 1).  The hardware logarithm's absolute error (at most 2^-21.4) would
+// dominate ln u near 1, so below v = 1 - u = 2^-8 (v exact for u >= 1/2) three terms of
+// -ln(1 - v) = v + v^2/2 + v^3/3 + ... take over (truncation below 2e-8 of ln u).
+__device__ __forceinline__ float ln_u01(uint32_t x) {
+    const float u = u01(x);
+    const float v = 1.0f - u;
+    return v < 0.00390625f ? -v * fmaf(v, fmaf(v, 0.333333343f, 0.5f), 1.0f) : __logf(u);
+}
+
+// N(0, 1) by Box-Muller, cosine branch: sqrt(-2 ln u0) cos(2 pi u1), with the hardware
+// approximations (the angle taken as 2 pi (u1 - 1/2) in [-pi, pi), whose cosine is the negated
+// one); the absolute error stays below 5e-6 against the exact mapping.
 __device__ __forceinline__ float normal01(uint32_t a, uint32_t b) {
-    return sqrtf(-2.0f * logf(u01(a))) * cospif(2.0f * u01(b));
+    return sqrt_approx(-2.0f * ln_u01(a)) * -__cosf(6.28318530718f * (u01(b) - 0.5f));
 }
 
 __device__ __forceinline__ uint32_t word(uint4 w, int i) { return i == 0 ? w.x : (i == 1 ? w.y : (i == 2 ? w.z : w.w)); }
@@ -371,15 +392,6 @@ __device__ __forceinline__ Q4 quat_error(const TargetDesc& T, Q4 qe) {
     return e;
 }
 
-// Square root by the hardware approximation (PTX sqrt.approx.f32, a few ulp):
-// for the angles and norms that rank trials and test tolerances, where the
-// IEEE-rounded sqrtf's correction steps cost issue slots of issue-bound
-// kernels and buy no decision the binary32 kinematics can resolve.
-__device__ __forceinline__ float sqrt_approx(float x) {
-    float r;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 
 // Arctangent of t in [0, 1] as t P(t^2), P of degree 7: the coefficients
 // minimise the largest absolute error on a dense grid of [0, 1] (a linear
