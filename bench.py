@@ -226,6 +226,14 @@ def recorded_traffic(kernel: str):
 
 # ----------------------------------------------------------------------------
 
+def step_config(args, world: int) -> dict:
+    """The workload of one step, the same for both arms (the reference arm times a bounded sample
+    of it and says so in its cpu_baseline)."""
+    return {"workload": WORKLOAD, "targets": args.targets, "seeds_per_target": args.seeds, "top_k": args.top_k,
+            "tolerance": "1 mm / 0.01 rad", "l2": "flushed between timed steps (256 MB write)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def cpu_baseline(sample_targets: int, seeds: int) -> dict:
     """The FP64 oracle, as it stands, on the host cores: a bounded sample of
     the same workload (its own FK and collision checks choose the targets)."""
@@ -277,11 +285,11 @@ def reference_arm(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": DATA,
-        "config": {"workload": WORKLOAD, "targets_per_step": sample, "seeds_per_target": args.seeds,
-                   "top_k": args.top_k, "note": "each step is a bounded sample of the workload's targets"},
+        "config": step_config(args, world),
         "success_rate": float(np.mean(succ)),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.threads(), "kind": "oracle",
-                         "sample": f"{sample} targets x {args.seeds} seeds per step"},
+                         "sample": f"{sample} of the {args.targets} targets x {args.seeds} seeds per step "
+                                   "(a bounded sample of the workload; value scaled to solves/s)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -903,9 +911,7 @@ def hjcd_arm(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": DATA,
-        "config": {"workload": WORKLOAD, "targets": T, "seeds_per_target": S, "top_k": K,
-                   "tolerance": "1 mm / 0.01 rad", "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": step_config(args, world),
         "candidates_per_s": value * S, "success_rate": success,
         "phase_ms": {nm: float(v) for nm, v in zip(names + ["step"], ph_raw)},
         "phase_note": "with the ranked collision filter (default) the collision checks run in the rank phase",
