@@ -579,6 +579,9 @@ struct CcdArgs {
     const int32_t* n_in;
     int32_t* list_out;
     int32_t* n_out;
+    // null: the items in a grid stride; else a zeroed queue head the warps take items from
+    // (cd_variant 0 and 1)
+    unsigned long long* queue;
 };
 
 struct LmArgs {

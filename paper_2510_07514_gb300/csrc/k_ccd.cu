@@ -17,6 +17,8 @@
 // which keeps the kernel small enough for the instruction cache at any n.
 // The robot tables of the launch sit in shared memory in front of the
 // columns; each candidate uses its target's robot.
+#include <algorithm>
+
 #include "hjcd_internal.cuh"
 
 namespace hjcd {
@@ -381,11 +383,23 @@ __global__ void __launch_bounds__(TH, HJCD_CCD_THREADS_PER_SM / TH) k_ccd(const 
     // to the next launch through list_out, which runs them from there (list_in)
     const int64_t items = A.list_in ? (int64_t)*A.n_in : A.C;
     const int k_end = A.seg_end > 0 ? A.seg_end : 0x7fffffff;
-    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < items;
-         it += (int64_t)gridDim.x * blockDim.x) {
+    // the order of the items: a grid stride, or (A.queue set, a grid of resident CTAs) 32
+    // consecutive items per warp from the queue at a time, so that every SM keeps working until
+    // the queue is drained whatever the number of waves the items would fill
+    const bool dyn = A.queue != nullptr;
+    const int wl = threadIdx.x & 31;
+    int64_t wbase = 0;
+    if (dyn) {
+        unsigned long long b0 = 0;
+        if (wl == 0) b0 = atomicAdd(A.queue, 32ull);
+        wbase = (int64_t)__shfl_sync(0xffffffffu, b0, 0);
+    }
+    for (int64_t it = dyn ? wbase + wl : blockIdx.x * (int64_t)blockDim.x + threadIdx.x; dyn ? wbase < items : it < items;) {
+      do {  // one item (break: done with it)
+        if (it >= items) break;  // past the end in the queue's last batch
         const int64_t c = A.list_in ? (int64_t)A.list_in[it] : it;
         int32_t t, s;
-        if (!A.map.lookup_search(c, t, s)) continue;
+        if (!A.map.lookup_search(c, t, s)) break;
         s += A.seed_base;
         const TargetDesc T = A.tg[t];
         const RobotParams& R = rob[T.robot];
@@ -437,7 +451,7 @@ __global__ void __launch_bounds__(TH, HJCD_CCD_THREADS_PER_SM / TH) k_ccd(const 
         if (handed) {
 #pragma unroll 1
             for (int j = 0; j < n; ++j) A.th_out[j * A.ld + c] = col.th(j);
-            continue;
+            break;
         }
         if (A.th_out) {
 #pragma unroll 1
@@ -451,6 +465,16 @@ __global__ void __launch_bounds__(TH, HJCD_CCD_THREADS_PER_SM / TH) k_ccd(const 
         if (A.perr) A.perr[c] = ep;
         if (A.oerr) A.oerr[c] = eo;
         if (A.iters) A.iters[c] = iters;
+      } while (0);
+        if (dyn) {
+            __syncwarp();
+            unsigned long long b0 = 0;
+            if (wl == 0) b0 = atomicAdd(A.queue, 32ull);
+            wbase = (int64_t)__shfl_sync(0xffffffffu, b0, 0);
+            it = wbase + wl;
+        } else {
+            it += (int64_t)gridDim.x * blockDim.x;
+        }
     }
     if (A.cnt) {
         n_it = warp_sum(n_it);
@@ -570,7 +594,13 @@ void launch_ccd_t(const CcdArgs& A, cudaStream_t st) {
     static SmemLimit lim;
     allow_dyn_smem(k_ccd<TRACE, TH, RED>, lim,
                    robots_smem_bytes(kMaxLaunchRobots) + sizeof(float) * (7 * kMaxDof + kSlotWords) * TH);
-    k_ccd<TRACE, TH, RED><<<grid_for(A.C, TH, 16 * 128 / TH), TH, smem, st>>>(A);
+    int g = grid_for(A.C, TH, 16 * 128 / TH);
+    if (A.queue) {  // the resident CTAs only: the queue spreads the items
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ccd<TRACE, TH, RED>, TH, smem);
+        g = std::min(g, sm_count() * std::max(per_sm, 1));
+    }
+    k_ccd<TRACE, TH, RED><<<g, TH, smem, st>>>(A);
 }
 
 template <bool TRACE, bool RED>

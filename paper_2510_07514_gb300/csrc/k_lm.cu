@@ -24,14 +24,15 @@
 // the CTA's threads work through: each failing slot's dogleg and
 // single-coordinate steps (whether or not a shorter step will succeed), then
 // its remaining line-search trials and the dogleg trial as independent
-// kinematics passes, one per thread, then per slot the first of them, in the
-// order of Alg. 4, that lowered its cost -- the step the sequential method
-// accepts.  Failing those, the single-coordinate line search runs in closed
-// form: turning one joint by x about its axis z moves the end effector by
-// (1 - cos x) (v x z) + sin x v, with v = z x (p_ee - p_j) the joint's
-// Jacobian column, and composes the orientation error with the half-angle
-// quaternion [cos x/2, -sin x/2 z], so each of its trials costs a handful of
-// operations instead of a kinematics pass.  The perturbation's normal pairs of
+// kinematics passes, and the trials of its single-coordinate line search, one
+// per thread, then per slot the first of them, in the order of Alg. 4, that
+// lowered its cost -- the step the sequential method accepts.  The
+// single-coordinate trials run in closed form: turning one joint by x about
+// its axis z moves the end effector by (1 - cos x) (v x z) + sin x v, with
+// v = z x (p_ee - p_j) the joint's Jacobian column, and composes the
+// orientation error with the half-angle quaternion [cos x/2, -sin x/2 z], so
+// each costs a handful of operations instead of a kinematics pass, and they
+// fill the threads the kinematics passes leave idle.  The perturbation's normal pairs of
 // the slots that found no step are spread over the CTA as well.
 // Per-lane state (joint vector, trial direction, weighted Jacobian, W, W r,
 // cost, target row, trial outcomes) lives in shared memory as structure of
@@ -54,9 +55,10 @@ constexpr int kMaxLsDepth = 31;  // A (validated by the host)
 __host__ __device__ constexpr int tri(int r, int c) { return r * (r + 1) / 2 + c; }
 
 // words of per-warp shared state for an n-joint chain and line-search depth A
-// W[6], b[6], cost0, t, s, kk, sc_j, sc_step, e[3], q_err[4], sc_z[3], sc_v[3], branch, alpha
+// W[6], b[6], cost0, t, s, kk, sc_j, sc_step, e[3], q_err[4], sc_z[3], sc_v[3], branch, alpha;
+// then one byte per lane and trial: the A + 1 kinematics trials, the A + 1 single-coordinate trials
 constexpr int kLmScalars = 33;
-__host__ __device__ constexpr int lm_warp_words(int n, int A) { return (8 * n + kLmScalars) * 32 + (A + 1) * 8; }
+__host__ __device__ constexpr int lm_warp_words(int n, int A) { return (8 * n + kLmScalars) * 32 + (A + 1) * 16; }
 
 // trial directions: the LM (or line-search) direction d, the dogleg step d2,
 // the single coordinate (joint sc_j by sc_step)
@@ -91,6 +93,7 @@ struct LmW {
     // the failure path's outcome for the owner: Alg. 4 branch and accepted alpha
     __device__ __forceinline__ int& br(int l) const { return reinterpret_cast<int*>(f)[(8 * n + 31) * 32 + l]; }
     __device__ __forceinline__ float& al(int l) const { return f[(8 * n + 32) * 32 + l]; }
+    // trial i lowered the cost (i < A + 1: kinematics trial i; else single-coordinate trial i - A - 1)
     __device__ __forceinline__ uint8_t& ok(int i, int l) const {
         return reinterpret_cast<uint8_t*>(f + (8 * n + kLmScalars) * 32)[i * 32 + l];
     }
@@ -584,19 +587,32 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                 dogleg_prepare(Sx, l, rob[A.tg[Sx.t(l)].robot].n, Rt, P.lm_gn_reg);
             }
             __syncthreads();
-            // the remaining line-search trials and the dogleg trial, one kinematics pass each
+            // the remaining line-search trials and the dogleg trial, one kinematics pass each, then
+            // the single-coordinate line search's trials in closed form (each slot's A + 1 of
+            // them, whether or not the sequential method gets that far: they take the threads the
+            // kinematics passes leave idle)
             const int per = P.lm_A + 1;
-            for (int w = threadIdx.x; w < nf * per; w += blockDim.x) {
-                const int sl = CL.fl[w / per], l = sl & 31, i = w % per;
+            const int nk = nf * per;
+            for (int w = threadIdx.x; w < 2 * nk; w += blockDim.x) {
+                const int wi = w < nk ? w : w - nk;
+                const int sl = CL.fl[wi / per], l = sl & 31, i = wi % per;
                 const LmW Sx = slot_state(sl);
-                int kind;
-                float alpha;
-                trial_item(i, P.lm_A, alphas, &kind, &alpha);
-                Sx.ok(i, l) = trial_cost<RED>(rob, A.tg, Sx.t(l), Sx, l, alpha, kind) < Sx.cost0(l) ? 1 : 0;
+                if (w < nk) {
+                    int kind;
+                    float alpha;
+                    trial_item(i, P.lm_A, alphas, &kind, &alpha);
+                    Sx.ok(i, l) = trial_cost<RED>(rob, A.tg, Sx.t(l), Sx, l, alpha, kind) < Sx.cost0(l) ? 1 : 0;
+                } else {
+                    const RobotParams& Rx = rob[A.tg[Sx.t(l)].robot];
+                    const int j = Sx.sc_j(l);
+                    const float th0 = Sx.th(j, l);
+                    const float thj = clampf(fmaf(alphas[i], Sx.sc_step(l), th0), Rx.lim[j].x, Rx.lim[j].y);
+                    Sx.ok(per + i, l) = coord_cost(Sx, l, thj - th0) < Sx.cost0(l) ? 1 : 0;
+                }
             }
             __syncthreads();
-            // each slot's first successful trial in the order of Alg. 4, else its
-            // single-coordinate line search (trials in closed form), else the perturbation
+            // each slot's first successful trial in the order of Alg. 4, else the first successful
+            // trial of its single-coordinate line search, else the perturbation
             for (int i = threadIdx.x; i < nf; i += blockDim.x) {
                 const int sl = CL.fl[i], l = sl & 31;
                 const LmW Sx = slot_state(sl);
@@ -617,20 +633,22 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                     br = kind == kDirLm ? 0 : 1;
                     if (kind == kDirDogleg) al = 0.0f;  // no line-search alpha (as traced)
                 } else {
-                    const int j = Sx.sc_j(l);
-                    const float th0 = Sx.th(j, l), st = Sx.sc_step(l), c0 = Sx.cost0(l);
-                    for (int q = 0; q <= P.lm_A; ++q) {
-                        const float a = alphas[q];
-                        const float thj = clampf(fmaf(a, st, th0), Rx.lim[j].x, Rx.lim[j].y);
-                        ++n_sc;
-                        if (coord_cost(Sx, l, thj - th0) < c0) {
-                            Sx.th(j, l) = thj;
-                            br = 2;
-                            al = a;
+                    int qc = per;
+                    for (int q = 0; q < per; ++q)
+                        if (Sx.ok(per + q, l)) {
+                            qc = q;
                             break;
                         }
+                    n_sc += qc < per ? qc + 1 : per;  // the trials the sequential method evaluates
+                    if (qc < per) {
+                        const int j = Sx.sc_j(l);
+                        const float th0 = Sx.th(j, l);
+                        Sx.th(j, l) = clampf(fmaf(alphas[qc], Sx.sc_step(l), th0), Rx.lim[j].x, Rx.lim[j].y);
+                        br = 2;
+                        al = alphas[qc];
+                    } else {
+                        CL.pl[atomicAdd(CL.np, 1)] = sl;
                     }
-                    if (br == 3) CL.pl[atomicAdd(CL.np, 1)] = sl;
                 }
                 Sx.br(l) = br;
                 Sx.al(l) = al;

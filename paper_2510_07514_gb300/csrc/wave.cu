@@ -148,7 +148,8 @@ hjcd_status plan_wave(hjcd_ctx* ctx, const WaveItem* items, int n_items, const h
     W.o_c = cv.take<int32_t>(W.T);
     W.o_ul = cv.take<int32_t>(W.T);           // targets left to the second collision pass
     W.o_sg = cv.take<int32_t>(2 * (size_t)W.CM);  // PO-CCD candidates handed between segments
-    W.o_qf = cv.take<unsigned long long>(3);  // queue head, error flag, count of o_ul, counts of o_sg
+    // queue head, error flag, count of o_ul, counts of o_sg; the PO-CCD segments' queue heads
+    W.o_qf = cv.take<unsigned long long>(6);
     W.bytes = cv.off;
     return HJCD_OK;
 }
@@ -237,7 +238,7 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
                                              sizeof(float) * W.n_max, items[i].q_ref,
                                              sizeof(float) * items[i].rob->P.n, sizeof(float) * items[i].rob->P.n,
                                              (size_t)items[i].T, cudaMemcpyDeviceToDevice, s));
-    HJCD_CUDA(ctx, cudaMemsetAsync(ws + W.o_qf, 0, 24, s));
+    HJCD_CUDA(ctx, cudaMemsetAsync(ws + W.o_qf, 0, 48, s));
     HJCD_CUDA(ctx, cudaMemsetAsync(ws + W.o_q, 0xff, sizeof(float) * (size_t)W.q_total, s));  // unfilled rows: NaN
     HJCD_CUDA(ctx, cudaMemsetAsync(ws + W.o_e, 0xff, sizeof(float) * (size_t)W.e_total, s));
 
@@ -298,11 +299,14 @@ hjcd_status run_wave(hjcd_ctx* ctx, const WavePlan& W, const WaveItem* items, co
             cg.n_in = g > 0 ? counts + ((g - 1) & 1) : nullptr;
             cg.list_out = g < 2 ? lists + (size_t)(g & 1) * W.CM : nullptr;
             cg.n_out = g < 2 ? counts + (g & 1) : nullptr;
+            cg.queue = reinterpret_cast<unsigned long long*>(ws + W.o_qf + 24) + g;
             launch_ccd(cg, false, s);
             if ((st = after_launch(ctx, 1, "k_ccd"))) return st;
         }
     } else {
-        launch_ccd(ca, false, s);
+        CcdArgs c1 = ca;
+        c1.queue = reinterpret_cast<unsigned long long*>(ws + W.o_qf + 24);
+        launch_ccd(c1, false, s);
         if ((st = after_launch(ctx, 1, "k_ccd"))) return st;
     }
     if (ev) HJCD_CUDA(ctx, cudaEventRecord(ev[1], s));
