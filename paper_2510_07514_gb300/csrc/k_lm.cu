@@ -439,12 +439,6 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                 }
             }
         }
-        if (!__syncthreads_or(has)) {
-            // every lane of the CTA asked for work: stop once the queue is drained, else ask again
-            if (!__syncthreads_or(c < A.C)) break;
-            continue;
-        }
-
         // ---- phase A: kinematics with frames, residual, LM step (owner) ----
         const RobotParams& R = rob[T.robot];
         const int n = R.n;
@@ -566,9 +560,11 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
         }
 
         // ---- the failure path over the CTA: the failing slots of all warps, compacted ----
+        // (the same barrier ends the loop once no lane holds a candidate and the queue is drained:
+        // a lane whose candidate just finished still holds an index below C and asks again)
         const unsigned fail = __ballot_sync(0xffffffffu, failed);
         if (lane == 0) CL.wm[warp] = fail;
-        __syncthreads();
+        if (!__syncthreads_or(has || c < A.C)) break;
         int nf = 0, before = 0;
 #pragma unroll
         for (int w = 0; w < WARPS; ++w) {
