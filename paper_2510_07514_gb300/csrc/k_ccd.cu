@@ -29,14 +29,38 @@ namespace {
 // 64, 128, 256 (a context starts at 64 candidates per CTA: hjcd_set_launch_config)
 constexpr int kCcdThreads = 128;
 
-// shared-memory column of a thread in a CTA of TH threads: theta[n], then
-// (px py pz zx zy zz) per joint
+// shared-memory column of a thread in a CTA of TH threads, laid out [quantity][thread] (a warp's
+// accesses hit 32 different banks): per joint j the pairs (px, py), (pz, theta_j), (zx, zy),
+// (zz, -) of joint j's frame after its kinematics step, 8 n words in all; each pair moves as one
+// 64-bit access
 template <int TH>
 struct ColT {
+    float2* base;  // this thread's first pair
+    __device__ __forceinline__ float2& a(int j) const { return base[4 * j * TH]; }
+    __device__ __forceinline__ float2& b(int j) const { return base[(4 * j + 1) * TH]; }
+    __device__ __forceinline__ float2& c(int j) const { return base[(4 * j + 2) * TH]; }
+    __device__ __forceinline__ float& zz(int j) const { return base[(4 * j + 3) * TH].x; }
+    __device__ __forceinline__ float& th(int j) const { return b(j).y; }
+    // joint j's origin and axis
+    __device__ __forceinline__ void frame(int j, V3& p, V3& z) const {
+        const float2 pa = a(j), pb = b(j), za = c(j);
+        p = v3(pa.x, pa.y, pb.x);
+        z = v3(za.x, za.y, zz(j));
+    }
+    __device__ __forceinline__ void set_frame(int j, const Frame& F, float theta) const {
+        a(j) = make_float2(F.p.x, F.p.y);
+        b(j) = make_float2(F.p.z, theta);
+        c(j) = make_float2(F.c2.x, F.c2.y);
+        zz(j) = F.c2.z;
+    }
+};
+constexpr int kColWordsPerJoint = 8;
+
+// the joint vector alone, theta[n] (the seed-sampling kernel)
+template <int TH>
+struct ThetaCol {
     float* base;
-    int n;
     __device__ __forceinline__ float& th(int j) const { return base[j * TH]; }
-    __device__ __forceinline__ float* fr(int j) const { return base + (n + 6 * j) * TH; }
 };
 
 template <class Col>
@@ -186,20 +210,14 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
                                         const hjcd_params& P, const ColT<TH>& col, uint32_t* slots, const CcdArgs& A,
                                         int64_t c, uint32_t s, int kk, int cap, float delta_k, const V3 pt, float pe2,
                                         float one_m_tie, float inv_p2, float inv_o2, float& ep2, float& eo) {
-    constexpr int kCcdThreads = TH;
     const int n = R.n;
     // kinematics with frames
     Frame F = frame_identity();
 #pragma unroll 1
     for (int j = 0; j < n; ++j) {
-        fk_step<RED>(R, j, col.th(j), F);
-        float* f = col.fr(j);
-        f[0 * kCcdThreads] = F.p.x;
-        f[1 * kCcdThreads] = F.p.y;
-        f[2 * kCcdThreads] = F.p.z;
-        f[3 * kCcdThreads] = F.c2.x;
-        f[4 * kCcdThreads] = F.c2.y;
-        f[5 * kCcdThreads] = F.c2.z;
+        const float thj = col.th(j);
+        fk_step<RED>(R, j, thj, F);
+        col.set_frame(j, F, thj);
     }
     const Frame E = fk_flange(R, F);
     const Q4 qerr = quat_error(T, quat_from_frame(E));
@@ -219,9 +237,8 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
         V3 x = E.p;
 #pragma unroll 1
         for (int j = n - 1; j >= 0; --j) {
-            const float* f = col.fr(j);
-            const V3 pj = v3(f[0 * kCcdThreads], f[1 * kCcdThreads], f[2 * kCcdThreads]);
-            const V3 z = v3(f[3 * kCcdThreads], f[4 * kCcdThreads], f[5 * kCcdThreads]);
+            V3 pj, z;
+            col.frame(j, pj, z);
             const float thj = col.th(j);
             const V3 u = x - pj, v = pt - pj;
             const float uz = dot(u, z), vz = dot(v, z);
@@ -249,11 +266,11 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
     const float dphi = delta_k * eo, nqw = -qerr.w;
 #pragma unroll 1
     for (int j = 0; j < n; ++j) {
-        const float* f = col.fr(j);
-        const V3 pj = v3(f[0 * kCcdThreads], f[1 * kCcdThreads], f[2 * kCcdThreads]);
-        const V3 z = v3(f[3 * kCcdThreads], f[4 * kCcdThreads], f[5 * kCcdThreads]);
+        const float2 pa = col.a(j), pb = col.b(j), za = col.c(j);
+        const V3 pj = v3(pa.x, pa.y, pb.x);
+        const V3 z = v3(za.x, za.y, col.zz(j));
         const CcdTrials tr =
-            ccd_joint_trials(pj, z, col.th(j), R.lim[j].x, R.lim[j].y, E.p, pt, qerr, nqw, dphi, pe2, inv_p2, inv_o2);
+            ccd_joint_trials(pj, z, pb.y, R.lim[j].x, R.lim[j].y, E.p, pt, qerr, nqw, dphi, pe2, inv_p2, inv_o2);
         if (tr.sp < best_p * one_m_tie) {  // joint 0 against +inf
             best_p = tr.sp;
             jp = j;
@@ -283,12 +300,9 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
     // residual at theta_hat: the distal joint's rotation first, then the proximal one
     // (the chosen joints' origins and axes are still in the shared-memory column)
     const bool p_hi = jp > jo;
-    const float* fa = col.fr(p_hi ? jp : jo);  // the distal joint
-    const float* fb = col.fr(p_hi ? jo : jp);
-    const V3 Pa = v3(fa[0 * kCcdThreads], fa[1 * kCcdThreads], fa[2 * kCcdThreads]);
-    const V3 Za = v3(fa[3 * kCcdThreads], fa[4 * kCcdThreads], fa[5 * kCcdThreads]);
-    const V3 Pb = v3(fb[0 * kCcdThreads], fb[1 * kCcdThreads], fb[2 * kCcdThreads]);
-    const V3 Zb = v3(fb[3 * kCcdThreads], fb[4 * kCcdThreads], fb[5 * kCcdThreads]);
+    V3 Pa, Za, Pb, Zb;
+    col.frame(p_hi ? jp : jo, Pa, Za);  // the distal joint
+    col.frame(p_hi ? jo : jp, Pb, Zb);
     const float da = p_hi ? aP : aO, db = p_hi ? aO : aP;
     float sa_, ca_, sb_, cb_;
     __sincosf(0.5f * da, &sa_, &ca_);
@@ -350,7 +364,7 @@ __device__ __forceinline__ int ccd_step(const RobotParams* rob, const RobotParam
             Tq.key[1] = q[1];
             Tq.t_local = (int32_t)q[2];
             const float2 z = normal_pair(Tq, q[3], kPhaseCd, q[4], b);
-            const ColT<TH> cs{col.base - lane + sl, Rs.n};
+            const ColT<TH> cs{col.base - lane + sl};
             const int j0 = 2 * b, j1 = 2 * b + 1;
             cs.th(j0) = clampf(fmaf(P.cd_sigma, z.x, cs.th(j0)), Rs.lim[j0].x, Rs.lim[j0].y);
             if (j1 < Rs.n) cs.th(j1) = clampf(fmaf(P.cd_sigma, z.y, cs.th(j1)), Rs.lim[j1].x, Rs.lim[j1].y);
@@ -373,7 +387,8 @@ __global__ void __launch_bounds__(TH, HJCD_CCD_THREADS_PER_SM / TH) k_ccd(const 
     extern __shared__ __align__(16) float sm[];
     const RobotParams* rob = stage_robots(sm, A.rs);
     uint32_t* const slots = reinterpret_cast<uint32_t*>(sm + robots_smem_bytes(A.rs.n) / sizeof(float));
-    float* const colbase = sm + robots_smem_bytes(A.rs.n) / sizeof(float) + TH * kSlotWords + threadIdx.x;
+    float2* const colbase =
+        reinterpret_cast<float2*>(sm + robots_smem_bytes(A.rs.n) / sizeof(float) + TH * kSlotWords) + threadIdx.x;
     const hjcd_params& P = A.P;
     const float pe2 = P.proj_eps * P.proj_eps;
     const float one_m_tie = 1.0f - P.cd_tie;
@@ -404,7 +419,7 @@ __global__ void __launch_bounds__(TH, HJCD_CCD_THREADS_PER_SM / TH) k_ccd(const 
         const TargetDesc T = A.tg[t];
         const RobotParams& R = rob[T.robot];
         const int n = R.n;
-        const Col col{colbase, n};
+        const Col col{colbase};
         const V3 pt = v3(T.p[0], T.p[1], T.p[2]);
         if (!A.list_in) ++n_cand;
 
@@ -498,13 +513,14 @@ __global__ void __launch_bounds__(TH, 4) k_ccd_lock(const CcdArgs A) {
     __shared__ int any;
     const RobotParams* rob = stage_robots(sm, A.rs);
     uint32_t* const slots = reinterpret_cast<uint32_t*>(sm + robots_smem_bytes(A.rs.n) / sizeof(float));
-    float* const colbase = sm + robots_smem_bytes(A.rs.n) / sizeof(float) + TH * kSlotWords + threadIdx.x;
+    float2* const colbase =
+        reinterpret_cast<float2*>(sm + robots_smem_bytes(A.rs.n) / sizeof(float) + TH * kSlotWords) + threadIdx.x;
     const int t = blockIdx.x;
     const hjcd_params& P = A.P;
     const TargetDesc T = A.tg[t];
     const RobotParams& R = rob[T.robot];
     const int n = R.n;
-    const ColT<TH> col{colbase, n};
+    const ColT<TH> col{colbase};
     const int64_t m0 = A.map.off[t];
     const int M = (int)(A.map.off[t + 1] - m0);
     const bool valid = T.eps_pos > 0.0f;
@@ -573,7 +589,7 @@ __global__ void __launch_bounds__(TH, 4) k_ccd_lock(const CcdArgs A) {
 __global__ void __launch_bounds__(kCcdThreads) k_sample(const RobotParams R, uint32_t k0, uint32_t k1, CandMap map,
                                                         int64_t C, float* th_out, int64_t ld) {
     extern __shared__ float sm[];
-    const ColT<kCcdThreads> col{sm + threadIdx.x, R.n};
+    const ThetaCol<kCcdThreads> col{sm + threadIdx.x};
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
         int32_t t, s;
         map.lookup(c, t, s);  // only the row index keys the stream
@@ -590,10 +606,11 @@ __global__ void __launch_bounds__(kCcdThreads) k_sample(const RobotParams R, uin
 
 template <bool TRACE, int TH, bool RED>
 void launch_ccd_t(const CcdArgs& A, cudaStream_t st) {
-    const size_t smem = robots_smem_bytes(A.rs.n) + sizeof(float) * (7 * A.rs.n_max + kSlotWords) * TH;
+    const size_t smem =
+        robots_smem_bytes(A.rs.n) + sizeof(float) * (kColWordsPerJoint * A.rs.n_max + kSlotWords) * TH;
     static SmemLimit lim;
     allow_dyn_smem(k_ccd<TRACE, TH, RED>, lim,
-                   robots_smem_bytes(kMaxLaunchRobots) + sizeof(float) * (7 * kMaxDof + kSlotWords) * TH);
+                   robots_smem_bytes(kMaxLaunchRobots) + sizeof(float) * (kColWordsPerJoint * kMaxDof + kSlotWords) * TH);
     int g = grid_for(A.C, TH, 16 * 128 / TH);
     if (A.queue) {  // the resident CTAs only: the queue spreads the items
         int per_sm = 0;
@@ -615,10 +632,12 @@ void launch_ccd_b(const CcdArgs& A, cudaStream_t st) {
 void launch_ccd(const CcdArgs& A, bool trace, cudaStream_t st) {
     if (A.C <= 0) return;
     if (A.P.cd_variant == 2) {  // one CTA per target (offset maps only)
-        const size_t smem = robots_smem_bytes(A.rs.n) + sizeof(float) * (7 * A.rs.n_max + kSlotWords) * 128;
+        const size_t smem =
+            robots_smem_bytes(A.rs.n) + sizeof(float) * (kColWordsPerJoint * A.rs.n_max + kSlotWords) * 128;
         static SmemLimit lim;
         allow_dyn_smem(k_ccd_lock<128>, lim,
-                       robots_smem_bytes(kMaxLaunchRobots) + sizeof(float) * (7 * kMaxDof + kSlotWords) * 128);
+                       robots_smem_bytes(kMaxLaunchRobots) +
+                           sizeof(float) * (kColWordsPerJoint * kMaxDof + kSlotWords) * 128);
         k_ccd_lock<128><<<A.map.T, 128, smem, st>>>(A);
         return;
     }
