@@ -65,16 +65,39 @@ __host__ __device__ constexpr int lm_warp_words(int n, int A) { return (8 * n + 
 enum TrialKind { kDirLm = 0, kDirDogleg = 1 };
 
 // Per-warp state, field[...][lane] (each lane's own accesses conflict-free);
-// n is the layout's chain length (the launch's largest).  The dogleg step d2
+// n is the layout's chain length (the launch's largest).  A joint's angle and
+// trial direction, and rows 2q and 2q + 1 of a Jacobian column, are pairs
+// [...][lane][2] that move as one 64-bit access.  The dogleg step d2
 // shares its words with row 0 of the weighted Jacobian: it is written column
 // by column after that column's last read, and the Jacobian is not read again
 // before the next iteration rebuilds it.
 struct LmW {
     float* f;
     int n;
-    __device__ __forceinline__ float& th(int j, int l) const { return f[j * 32 + l]; }
-    __device__ __forceinline__ float& d(int j, int l) const { return f[(n + j) * 32 + l]; }
-    __device__ __forceinline__ float& jw(int r, int i, int l) const { return f[(2 * n + r * n + i) * 32 + l]; }
+    // joint j's angle and LM (or line-search) direction as one pair (one 64-bit access)
+    __device__ __forceinline__ float2& thd(int j, int l) const { return reinterpret_cast<float2*>(f)[j * 32 + l]; }
+    __device__ __forceinline__ float& th(int j, int l) const { return thd(j, l).x; }
+    __device__ __forceinline__ float& d(int j, int l) const { return thd(j, l).y; }
+    // rows 2q and 2q + 1 of column i of the weighted Jacobian as one pair (one 64-bit access)
+    __device__ __forceinline__ float2& jw2(int q, int i, int l) const {
+        return reinterpret_cast<float2*>(f + 2 * n * 32)[(q * n + i) * 32 + l];
+    }
+    __device__ __forceinline__ float& jw(int r, int i, int l) const {
+        return reinterpret_cast<float*>(&jw2(r >> 1, i, l))[r & 1];
+    }
+    // column i's six rows
+    __device__ __forceinline__ void col6(int i, int l, float (&c)[6]) const {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float2 v = jw2(q, i, l);
+            c[2 * q] = v.x;
+            c[2 * q + 1] = v.y;
+        }
+    }
+    __device__ __forceinline__ void set_col6(int i, int l, const float (&c)[6]) const {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) jw2(q, i, l) = make_float2(c[2 * q], c[2 * q + 1]);
+    }
     __device__ __forceinline__ float& d2(int j, int l) const { return jw(0, j, l); }
     __device__ __forceinline__ float& W(int r, int l) const { return f[(8 * n + r) * 32 + l]; }
     __device__ __forceinline__ float& b(int r, int l) const { return f[(8 * n + 6 + r) * 32 + l]; }
@@ -163,12 +186,13 @@ __device__ __noinline__ Y6 normal_solve(const LmW S, int l, int n, float reg, Y6
 #pragma unroll 1
     for (int i = 0; i < n; ++i) {
         float col[6], dd = 1e-9f;
+        S.col6(i, l, col);
 #pragma unroll
         for (int r = 0; r < 6; ++r) {
-            col[r] = S.jw(r, i, l) * w.v[r];
-            S.jw(r, i, l) = col[r];
+            col[r] *= w.v[r];
             dd = fmaf(col[r], col[r], dd);
         }
+        S.set_col6(i, l, col);
         const float rs = rsqrtf(dd);
 #pragma unroll
         for (int r = 0; r < 6; ++r) col[r] *= rs;
@@ -212,11 +236,6 @@ __device__ __forceinline__ LmCta<WARPS> lm_cta(float* f) {
     return LmCta<WARPS>{reinterpret_cast<unsigned*>(b), b + WARPS, b + WARPS + WARPS * 32, b + WARPS + 2 * WARPS * 32};
 }
 
-// component j of lane s's trial direction of the given kind
-__device__ __forceinline__ float trial_dir(const LmW& S, int s, int kind, int j) {
-    return kind == kDirDogleg ? S.d2(j, s) : S.d(j, s);
-}
-
 // weighted cost 1/2 |W r|^2 at the trial point clamp(theta + alpha dir) of lane s
 // (the kinematics passes, the 6 x 6 solve and the trial spreading each exist
 // once in the kernel, called from every branch that needs them, which keeps
@@ -228,8 +247,11 @@ __device__ __noinline__ float trial_cost(const RobotParams* rob, const TargetDes
     const RobotParams& R = rob[T.robot];
     Frame F = frame_identity();
 #pragma unroll 1
-    for (int j = 0; j < R.n; ++j)
-        fk_step<RED>(R, j, clampf(fmaf(alpha, trial_dir(S, s, kind, j), S.th(j, s)), R.lim[j].x, R.lim[j].y), F);
+    for (int j = 0; j < R.n; ++j) {
+        const float2 td = S.thd(j, s);
+        const float dir = kind == kDirDogleg ? S.d2(j, s) : td.y;
+        fk_step<RED>(R, j, clampf(fmaf(alpha, dir, td.x), R.lim[j].x, R.lim[j].y), F);
+    }
     const Frame E = fk_flange(R, F);
     const V3 w = quat_log(quat_error(T, quat_from_frame(E)));
     const float e0 = S.W(0, s) * (T.p[0] - E.p.x), e1 = S.W(1, s) * (T.p[1] - E.p.y);
@@ -241,8 +263,11 @@ __device__ __noinline__ float trial_cost(const RobotParams* rob, const TargetDes
 // theta <- clamp(theta + alpha dir) for lane s (the trial point the cost was taken at)
 __device__ __noinline__ void take_step(const RobotParams& R, const LmW S, int s, float alpha, int kind) {
 #pragma unroll 1
-    for (int j = 0; j < R.n; ++j)
-        S.th(j, s) = clampf(fmaf(alpha, trial_dir(S, s, kind, j), S.th(j, s)), R.lim[j].x, R.lim[j].y);
+    for (int j = 0; j < R.n; ++j) {
+        const float2 td = S.thd(j, s);
+        const float dir = kind == kDirDogleg ? S.d2(j, s) : td.y;
+        S.th(j, s) = clampf(fmaf(alpha, dir, td.x), R.lim[j].x, R.lim[j].y);
+    }
 }
 
 // The kinematics-pass trials that follow a failed full step, in the order Alg. 4
@@ -293,8 +318,7 @@ __device__ __noinline__ void dogleg_prepare(const LmW S, int l, int n, float Rt,
 #pragma unroll 1
     for (int i = 0; i < n; ++i) {
         float col[6];
-#pragma unroll
-        for (int r = 0; r < 6; ++r) col[r] = S.jw(r, i, l);
+        S.col6(i, l, col);
 #pragma unroll
         for (int r = 0; r < 6; ++r)
 #pragma unroll
@@ -328,11 +352,12 @@ __device__ __noinline__ void dogleg_prepare(const LmW S, int l, int n, float Rt,
     float ngn2 = 0.0f, qa = 0.0f, qb = 0.0f;
 #pragma unroll 1
     for (int i = 0; i < n; ++i) {
-        float dgn = 0.0f, g = 0.0f;
+        float dgn = 0.0f, g = 0.0f, col[6];
+        S.col6(i, l, col);
 #pragma unroll
         for (int r = 0; r < 6; ++r) {
-            dgn = fmaf(S.jw(r, i, l), y2[r], dgn);
-            g = fmaf(S.jw(r, i, l), b[r], g);
+            dgn = fmaf(col[r], y2[r], dgn);
+            g = fmaf(col[r], b[r], g);
         }
         const float di = fmaf(ac, g, -dgn);
         ngn2 = fmaf(dgn, dgn, ngn2);
@@ -361,9 +386,9 @@ __device__ __noinline__ void dogleg_prepare(const LmW S, int l, int n, float Rt,
 #pragma unroll 1
     for (int i = 0; i < n; ++i) {
         float dgn = 0.0f, g = 0.0f, q2 = 0.0f, col[6];
+        S.col6(i, l, col);
 #pragma unroll
         for (int r = 0; r < 6; ++r) {
-            col[r] = S.jw(r, i, l);
             dgn = fmaf(col[r], y2[r], dgn);
             g = fmaf(col[r], b[r], g);
             q2 = fmaf(col[r], col[r], q2);
@@ -449,12 +474,9 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
 #pragma unroll 1
             for (int j = 0; j < n; ++j) {
                 fk_step<RED>(R, j, S.th(j, lane), F);
-                S.jw(0, j, lane) = F.p.x;
-                S.jw(1, j, lane) = F.p.y;
-                S.jw(2, j, lane) = F.p.z;
-                S.jw(3, j, lane) = F.c2.x;
-                S.jw(4, j, lane) = F.c2.y;
-                S.jw(5, j, lane) = F.c2.z;
+                S.jw2(0, j, lane) = make_float2(F.p.x, F.p.y);
+                S.jw2(1, j, lane) = make_float2(F.p.z, F.c2.x);
+                S.jw2(2, j, lane) = make_float2(F.c2.y, F.c2.z);
             }
             const Frame E = fk_flange(R, F);
             ++n_fk;
@@ -481,12 +503,13 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                 float rn[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll 1
                 for (int i = 0; i < n; ++i) {
-                    const V3 Pi = v3(S.jw(0, i, lane), S.jw(1, i, lane), S.jw(2, i, lane));
-                    const V3 Zi = v3(S.jw(3, i, lane), S.jw(4, i, lane), S.jw(5, i, lane));
+                    float fr[6];
+                    S.col6(i, lane, fr);
+                    const V3 Pi = v3(fr[0], fr[1], fr[2]);
+                    const V3 Zi = v3(fr[3], fr[4], fr[5]);
                     const V3 jp = cross(Zi, E.p - Pi);
-                    S.jw(0, i, lane) = jp.x;
-                    S.jw(1, i, lane) = jp.y;
-                    S.jw(2, i, lane) = jp.z;
+                    S.jw2(0, i, lane) = make_float2(jp.x, jp.y);
+                    S.jw2(1, i, lane) = make_float2(jp.z, Zi.x);
                     const float col[6] = {jp.x, jp.y, jp.z, Zi.x, Zi.y, Zi.z};
 #pragma unroll
                     for (int r = 0; r < 6; ++r) {
@@ -528,12 +551,12 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) k_lm(const LmArgs A) {
                 for (int r = 0; r < 6; ++r) y[r] = yy.v[r];
 #pragma unroll 1
                 for (int i = 0; i < n; ++i) {
-                    float a = 0.0f, dd = 1e-9f;
+                    float a = 0.0f, dd = 1e-9f, cl[6];
+                    S.col6(i, lane, cl);
 #pragma unroll
                     for (int r = 0; r < 6; ++r) {
-                        const float v = S.jw(r, i, lane);
-                        a = fmaf(v, y[r], a);
-                        dd = fmaf(v, v, dd);
+                        a = fmaf(cl[r], y[r], a);
+                        dd = fmaf(cl[r], cl[r], dd);
                     }
                     const float st = clampf(__fdividef(a, dd), -Rt, Rt);  // trust region
                     S.d(i, lane) = st;
